@@ -1,0 +1,250 @@
+"""FP64 CPU oracle of the Kalman-filter track finder (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg import this package.  It wraps ``kf_oracle.cpp`` (plain double-precision
+C++, full 6x6 matrices, no shared code with the CUDA path) through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kf_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with g++ (host code, any architecture)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Detector(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("radius", ctypes.c_double * 64),
+                ("x0", ctypes.c_double * 64), ("z_max", ctypes.c_double), ("bz", ctypes.c_double),
+                ("sigma_rphi", ctypes.c_double), ("sigma_z", ctypes.c_double)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("max_cands", ctypes.c_int), ("max_holes", ctypes.c_int), ("chi2_cut", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            L = _lib
+            L.orc_propagate.argtypes = [ctypes.c_double, _P, ctypes.c_double, _P, _P]
+            L.orc_path_length.argtypes = [ctypes.c_double, _P, ctypes.c_double, _P]
+            L.orc_propagate_ad.argtypes = [ctypes.c_double, _P, ctypes.c_double, _P]
+            L.orc_transport.argtypes = [_P, _P, _P]
+            L.orc_update.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P]
+            L.orc_highland.argtypes = [_P, ctypes.c_double]
+            L.orc_highland.restype = ctypes.c_double
+            L.orc_add_ms.argtypes = [_P, _P, ctypes.c_double]
+            L.orc_fit.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_long, _P, _P, ctypes.c_int,
+                                  _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]
+            L.orc_fit_grad.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_long, _P, _P, ctypes.c_int,
+                                       _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_find_event.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
+                                         ctypes.c_long, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
+                                         _P, _P, _P, _P, _P, _P]
+            L.orc_dedup.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int, _P]
+        return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def make_detector(det) -> Detector:
+    """ctypes detector from a synth.Detector; values rounded to float32 first,
+    so the oracle sees exactly the numbers the float32 path is given."""
+    d = Detector()
+    d.n_layers = det.n_layers
+    for i, r in enumerate(det.radius):
+        d.radius[i] = float(np.float32(r))
+        d.x0[i] = float(np.float32(det.x0[i]))
+    d.z_max = float(np.float32(det.z_max))
+    d.bz = float(np.float32(det.bz))
+    d.sigma_rphi = float(np.float32(det.sigma_rphi))
+    d.sigma_z = float(np.float32(det.sigma_z))
+    return d
+
+
+def make_config(max_cands=6, max_holes=3, chi2_cut=30.0) -> Config:
+    return Config(max_cands, max_holes, float(np.float32(chi2_cut)))
+
+
+# ------------------------------------------------------------ single-state pins
+def propagate(bz: float, p, R: float):
+    p = _c(p, np.float64)
+    q = np.zeros(6)
+    J = np.zeros(36)
+    ok = lib().orc_propagate(bz, _ptr(p), R, _ptr(q), _ptr(J))
+    return bool(ok), q, J.reshape(6, 6)
+
+
+def path_length(bz: float, p, R: float):
+    p = _c(p, np.float64)
+    s = np.zeros(1)
+    ok = lib().orc_path_length(bz, _ptr(p), R, _ptr(s))
+    return bool(ok), float(s[0])
+
+
+def propagate_ad(bz: float, p, R: float):
+    p = _c(p, np.float64)
+    J = np.zeros(36)
+    ok = lib().orc_propagate_ad(bz, _ptr(p), R, _ptr(J))
+    return bool(ok), J.reshape(6, 6)
+
+
+def transport(J, C):
+    J = _c(J, np.float64)
+    C = _c(C, np.float64)
+    out = np.zeros(36)
+    lib().orc_transport(_ptr(J), _ptr(C), _ptr(out))
+    return out.reshape(6, 6)
+
+
+def update(p, C, m, vr, vz):
+    p = _c(p, np.float64); C = _c(C, np.float64); m = _c(m, np.float64)
+    po, Co, c2, r = np.zeros(6), np.zeros(36), np.zeros(1), np.zeros(2)
+    ok = lib().orc_update(_ptr(p), _ptr(C), _ptr(m), vr, vz, _ptr(po), _ptr(Co), _ptr(c2), _ptr(r))
+    return bool(ok), po, Co.reshape(6, 6), float(c2[0]), r
+
+
+def highland(p, x0):
+    p = _c(p, np.float64)
+    return lib().orc_highland(_ptr(p), x0)
+
+
+def add_ms(p, C, x0):
+    p = _c(p, np.float64)
+    C = _c(C, np.float64).copy()
+    lib().orc_add_ms(_ptr(p), _ptr(C), x0)
+    return C.reshape(6, 6)
+
+
+def sym_to_full(c21):
+    c21 = np.asarray(c21)
+    out = np.zeros(c21.shape[:-1] + (6, 6))
+    k = 0
+    for i in range(6):
+        for j in range(i, 6):
+            out[..., i, j] = c21[..., k]
+            out[..., j, i] = c21[..., k]
+            k += 1
+    return out
+
+
+# ------------------------------------------------------------ batch entry points
+def fit(det, prior_p, prior_C, hit_lists, n_hits, hx, hy, hz, hlayer, align=None,
+        ms_after_last=False, want_each=False):
+    """Kalman fit of tracks (inputs promoted to float64): prior_p [6][n], prior_C [21][n] (SoA), hit_lists
+    [n][max_len] indices into hx/hy/hz/hlayer.  Returns (p [n][6], C [n][21],
+    chi2 [n], status [n]) and per-hit chi2 if want_each."""
+    prior_p = _c(prior_p, np.float64); prior_C = _c(prior_C, np.float64)
+    n = prior_p.shape[1]
+    hit_lists = _c(hit_lists, np.int32); n_hits = _c(n_hits, np.int32)
+    max_len = hit_lists.shape[1]
+    hx, hy, hz = _c(hx, np.float64), _c(hy, np.float64), _c(hz, np.float64)
+    hlayer = _c(hlayer, np.int32)
+    align = _c(np.zeros((det.n_layers, 2)) if align is None else align, np.float64)
+    p = np.zeros((n, 6)); C = np.zeros((n, 21)); c2 = np.zeros(n); st = np.zeros(n, np.int32)
+    each = np.zeros((n, max_len)) if want_each else None
+    d = make_detector(det)
+    lib().orc_fit(ctypes.byref(d), n, _ptr(prior_p), _ptr(prior_C), n, _ptr(hit_lists),
+                  _ptr(n_hits), max_len, _ptr(hx), _ptr(hy), _ptr(hz), _ptr(hlayer), _ptr(align),
+                  int(ms_after_last), _ptr(p), _ptr(C), _ptr(c2),
+                  _ptr(each) if want_each else None, _ptr(st))
+    if want_each:
+        return p, C, c2, st, each
+    return p, C, c2, st
+
+
+def fit_grad(det, prior_p, prior_C, hit_lists, n_hits, hx, hy, hz, hlayer, align=None):
+    """Summed fit chi2 and its gradient (forward-mode dual numbers).
+    Returns (chi2_total, g_align [L][2], g_hits [n_hit_arrays][3], g_seed [n][6], chi2 [n])."""
+    prior_p = _c(prior_p, np.float64); prior_C = _c(prior_C, np.float64)
+    n = prior_p.shape[1]
+    hit_lists = _c(hit_lists, np.int32); n_hits = _c(n_hits, np.int32)
+    hx, hy, hz = _c(hx, np.float64), _c(hy, np.float64), _c(hz, np.float64)
+    hlayer = _c(hlayer, np.int32)
+    align = _c(np.zeros((det.n_layers, 2)) if align is None else align, np.float64)
+    tot = np.zeros(1); ga = np.zeros((det.n_layers, 2)); gh = np.zeros((hx.size, 3))
+    gs = np.zeros((n, 6)); each = np.zeros(n)
+    d = make_detector(det)
+    rc = lib().orc_fit_grad(ctypes.byref(d), n, _ptr(prior_p), _ptr(prior_C), n, _ptr(hit_lists),
+                            _ptr(n_hits), hit_lists.shape[1], _ptr(hx), _ptr(hy), _ptr(hz),
+                            _ptr(hlayer), _ptr(align), _ptr(tot), _ptr(ga), _ptr(gh), _ptr(gs),
+                            _ptr(each))
+    if rc != 0:
+        raise RuntimeError(f"orc_fit_grad failed: {rc}")
+    return float(tot[0]), ga, gh, gs, each
+
+
+def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=None, brute=False,
+               align=None):
+    """Combinatorial finding for event e of a synth.Batch (optionally a subset
+    of its seeds, event-local indices [a, b)).  Returns a dict with hits
+    [n][L] (event-local, -1 padded), n_found, chi2, p [n][6], C [n][21] and
+    counters."""
+    det = batch.det
+    L = det.n_layers
+    x, y, z, lay = batch.event_hits(e)
+    prm, cov, sh = batch.event_seeds(e)
+    prm = _c(prm, np.float64); cov = _c(cov, np.float64); sh = _c(sh, np.int32)
+    ns = prm.shape[1]
+    a, b = (0, ns) if seeds is None else seeds
+    n = b - a
+    out_hits = np.full((n, L), -1, np.int32)
+    out_n = np.zeros(n, np.int32)
+    out_c2 = np.zeros(n)
+    out_p = np.zeros((n, 6))
+    out_C = np.zeros((n, 21))
+    cnt = np.zeros(8, np.int64)
+    mc = batch.cfg["max_cands"] if max_cands is None else max_cands
+    d = make_detector(det)
+    cfg = make_config(mc, max_holes, chi2_cut)
+    al = _c(batch.align if align is None else align, np.float64)
+    x, y, z, lay = _c(x, np.float64), _c(y, np.float64), _c(z, np.float64), _c(lay, np.int32)
+    lib().orc_find_event(ctypes.byref(d), ctypes.byref(cfg), x.size, _ptr(x), _ptr(y), _ptr(z),
+                         _ptr(lay), _ptr(prm), _ptr(cov), _ptr(sh), ns, a, b, _ptr(al), int(brute),
+                         _ptr(out_hits), _ptr(out_n), _ptr(out_c2), _ptr(out_p), _ptr(out_C),
+                         _ptr(cnt))
+    return dict(hits=out_hits, n_found=out_n, chi2=out_c2, p=out_p, C=out_C,
+                counters=dict(steps=int(cnt[0]), prop_calls=int(cnt[1]), updates=int(cnt[2]),
+                              ms=int(cnt[3]), chi2_evals=int(cnt[4]), seeds=int(cnt[5]),
+                              children=int(cnt[6])))
+
+
+def dedup(hits, n_hits, chi2, frac=0.5, brute=False):
+    """Greedy duplicate removal over one event's tracks; returns keep flags (uint8)."""
+    hits = _c(hits, np.int32); n_hits = _c(n_hits, np.int32); chi2 = _c(chi2, np.float64)
+    n = n_hits.size
+    keep = np.zeros(n, np.uint8)
+    lib().orc_dedup(n, _ptr(hits), _ptr(n_hits), _ptr(chi2), hits.shape[1] if n else 1,
+                    float(frac), int(brute), _ptr(keep))
+    return keep

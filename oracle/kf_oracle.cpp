@@ -1,0 +1,901 @@
+// FP64 CPU oracle of the batched Kalman-filter track finder and fitter.
+//
+// TEST INFRASTRUCTURE ONLY.  The parity tests, the smoke check and the
+// benchmark's CPU-baseline leg call this code; the library's product path
+// never does.  It shares no code with the CUDA kernels.
+//
+// What it computes (the paper gives the method in outline only: Sec. 2 for the
+// Kalman filter building, Sec. 3 for the geometry, Sec. 4.2 for duplicate
+// removal, Sec. 4.3 for candidate scores; every formula below is the standard
+// Kalman-filter reading recorded in the design notes):
+//   * state p = (x, y, z, q/pT, phi, theta), symmetric 6x6 covariance C;
+//   * helix propagation to a cylinder of radius R in a uniform field Bz, with
+//     the exact Jacobian J = dF/dp + dF/ds ds/dp;
+//   * covariance transport C <- J C J^T;
+//   * 2D tangent-frame measurement (r-phi, z) of a 3D hit on the cylinder, chi2;
+//   * gain K = C H^T S^-1, p <- p + K r, C <- C - K H C;
+//   * thin-scatterer multiple scattering after each layer (Highland width);
+//   * combinatorial finding with per-seed top-N candidates (Sec. 2);
+//   * greedy duplicate removal on shared-hit fraction (Sec. 4.2);
+//   * the full re-fit and the summed chi2, with forward-mode dual numbers for
+//     d(chi2)/d(alignment, hits, seed parameters).
+// Matrices are full 6x6 arrays and products are plain triple loops: no
+// sparsity, blocking or fusion.
+//
+// Parity status: every function here is pinned by tests under tests/ (closed
+// forms, Runge-Kutta integration, finite differences, brute force, least
+// squares, pull widths).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+namespace {
+
+constexpr double KCURV = 0.00299792458;  // 1/rho[1/cm] = KCURV * B[T] / pT[GeV]
+constexpr double MPION = 0.13957;        // mass hypothesis for beta (GeV)
+constexpr double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- dual numbers
+// Forward-mode derivatives: value v plus derivatives d[0..g_nd) with respect to
+// g_nd independent inputs.  Branches compare values only.
+constexpr int DMAX = 112;
+int g_nd = 0;
+
+struct Dual {
+  double v;
+  double d[DMAX];
+  Dual() : v(0.0) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }
+  Dual(double x) : v(x) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }  // NOLINT implicit
+};
+inline Dual make_var(double x, int k) {
+  Dual r(x);
+  r.d[k] = 1.0;
+  return r;
+}
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v + b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v - b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+inline Dual operator-(const Dual& a) {
+  Dual r; r.v = -a.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v * b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v / b.v;
+  const double ib = 1.0 / b.v;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
+inline Dual operator+(double a, const Dual& b) { return b + a; }
+inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
+inline Dual operator-(double a, const Dual& b) { return (-b) + a; }
+inline Dual operator*(const Dual& a, double b) {
+  Dual r; r.v = a.v * b;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * b;
+  return r;
+}
+inline Dual operator*(double a, const Dual& b) { return b * a; }
+inline Dual operator/(const Dual& a, double b) { return a * (1.0 / b); }
+inline Dual operator/(double a, const Dual& b) { return Dual(a) / b; }
+inline Dual& operator+=(Dual& a, const Dual& b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, const Dual& b) { a = a - b; return a; }
+
+inline Dual chain(const Dual& a, double f, double df) {
+  Dual r; r.v = f;
+  for (int i = 0; i < g_nd; ++i) r.d[i] = df * a.d[i];
+  return r;
+}
+inline Dual sin(const Dual& a) { return chain(a, std::sin(a.v), std::cos(a.v)); }
+inline Dual cos(const Dual& a) { return chain(a, std::cos(a.v), -std::sin(a.v)); }
+inline Dual atan(const Dual& a) { return chain(a, std::atan(a.v), 1.0 / (1.0 + a.v * a.v)); }
+inline Dual sqrt(const Dual& a) { double s = std::sqrt(a.v); return chain(a, s, 0.5 / s); }
+inline Dual log(const Dual& a) { return chain(a, std::log(a.v), 1.0 / a.v); }
+inline Dual fabs(const Dual& a) { return a.v < 0 ? -a : a; }
+inline Dual atan2(const Dual& y, const Dual& x) {
+  const double r2 = x.v * x.v + y.v * y.v;
+  Dual r; r.v = std::atan2(y.v, x.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = (x.v * y.d[i] - y.v * x.d[i]) / r2;
+  return r;
+}
+
+using std::atan;
+using std::atan2;
+using std::cos;
+using std::fabs;
+using std::log;
+using std::sin;
+using std::sqrt;
+
+// ---------------------------------------------------------------- detector
+struct Det {
+  int n_layers;
+  double radius[64];
+  double x0[64];
+  double z_max;
+  double bz;
+  double sigma_rphi;
+  double sigma_z;
+};
+
+struct Cfg {
+  int max_cands;
+  int max_holes;
+  double chi2_cut;
+};
+
+inline int sym_index(int i, int j) {  // upper triangle, row-major
+  if (i > j) std::swap(i, j);
+  return i * 6 - i * (i - 1) / 2 + (j - i);
+}
+
+// ---------------------------------------------------------------- helix
+// Series-safe helpers of psi = h*s:
+//   sinc(psi) = sin(psi)/psi, cosc(psi) = (1-cos psi)/psi,
+//   f1(psi) = (psi cos psi - sin psi)/psi^2 = d(sin(hs)/h)/dh / s^2,
+//   f2(psi) = (psi sin psi - 1 + cos psi)/psi^2 = d((1-cos hs)/h)/dh / s^2.
+template <class T>
+void helix_functions(const T& psi, T& sc, T& cc, T& f1, T& f2) {
+  if (std::fabs(val(psi)) < 0.1) {
+    T p2 = psi * psi;
+    sc = 1.0 - p2 / 6.0 + p2 * p2 / 120.0 - p2 * p2 * p2 / 5040.0 + p2 * p2 * p2 * p2 / 362880.0;
+    cc = psi * (0.5 - p2 / 24.0 + p2 * p2 / 720.0 - p2 * p2 * p2 / 40320.0 +
+                p2 * p2 * p2 * p2 / 3628800.0);
+    f1 = psi * (-1.0 / 3.0 + p2 / 30.0 - p2 * p2 / 840.0 + p2 * p2 * p2 / 45360.0);
+    f2 = 0.5 - p2 / 8.0 + p2 * p2 / 144.0 - p2 * p2 * p2 / 5760.0 + p2 * p2 * p2 * p2 / 403200.0;
+  } else {
+    T sn = sin(psi), cs = cos(psi);
+    sc = sn / psi;
+    cc = (1.0 - cs) / psi;
+    f1 = (psi * cs - sn) / (psi * psi);
+    f2 = (psi * sn - 1.0 + cs) / (psi * psi);
+  }
+}
+
+// Path length s > 0 (transverse arc length) to the first crossing of the
+// cylinder x^2 + y^2 = R^2.  With psi = h s, b = p_xy . t, a = p_xy . n
+// (t the direction, n its left normal) the crossing condition is
+//   A sin(psi) + B (1 - cos psi) = E,  A = b h, B = a h + 1, E = h^2 (R^2 - r0^2)/2,
+// solved with tau = tan(psi/2):  (2B - E) tau^2 + 2 A tau - E = 0.
+// h = 0 is the straight line s^2 + 2 b s - (R^2 - r0^2) = 0.
+template <class T>
+bool path_to_cylinder(const T& x, const T& y, const T& h, const T& phi, double R, T& s) {
+  T cf = cos(phi), sf = sin(phi);
+  T b = x * cf + y * sf;
+  T a = -x * sf + y * cf;
+  T r0 = sqrt(x * x + y * y);
+  T dR2 = (R - r0) * (R + r0);
+  if (val(h) == 0.0) {
+    T disc = b * b + dR2;
+    if (val(disc) < 0.0) return false;
+    T sq = sqrt(disc);
+    // Roots lo = -b - sq <= hi = -b + sq, each in its cancellation-free form.
+    T lo, hi;
+    if (val(b) > 0.0) {
+      lo = -(b + sq);
+      hi = dR2 / (b + sq);
+    } else {
+      hi = sq - b;
+      lo = (val(hi) == 0.0) ? T(0.0) : -dR2 / hi;
+    }
+    if (val(lo) > 0.0) { s = lo; return true; }
+    if (val(hi) > 0.0) { s = hi; return true; }
+    return false;
+  }
+  T A = b * h, B = a * h + 1.0, E = 0.5 * h * h * dR2;
+  T D = A * A + E * (2.0 * B - E);
+  if (val(D) < 0.0) return false;
+  T sq = sqrt(D);
+  T den = 2.0 * B - E;
+  T num[2], dnm[2];
+  if (val(A) >= 0.0) {
+    num[0] = E; dnm[0] = A + sq;
+    num[1] = -(A + sq); dnm[1] = den;
+  } else {
+    num[0] = sq - A; dnm[0] = den;
+    num[1] = E; dnm[1] = A - sq;
+  }
+  const double turn = 2.0 * PI / std::fabs(val(h));
+  bool found = false;
+  T best(0.0);
+  for (int k = 0; k < 2; ++k) {
+    T psi;
+    if (val(dnm[k]) == 0.0) {
+      if (val(num[k]) == 0.0) continue;
+      psi = T(PI);
+    } else {
+      psi = 2.0 * atan(num[k] / dnm[k]);
+    }
+    T sk = psi / h;
+    if (val(sk) <= 0.0) sk = sk + turn;
+    if (!found || val(sk) < val(best)) { best = sk; found = true; }
+  }
+  if (!found) return false;
+  s = best;
+  return true;
+}
+
+// Propagate p to the cylinder of radius R; q = F(p), J = dq/dp (exact).
+template <class T>
+bool propagate(double bz, const T p[6], double R, T q[6], T J[6][6]) {
+  const T& x = p[0];
+  const T& y = p[1];
+  const T& z = p[2];
+  const T& kap = p[3];
+  const T& phi = p[4];
+  const T& th = p[5];
+  const double kb = -KCURV * bz;
+  T h = kb * kap;
+  T s;
+  if (!path_to_cylinder(x, y, h, phi, R, s)) return false;
+  T psi = h * s;
+  T sc, cc, f1, f2;
+  helix_functions(psi, sc, cc, f1, f2);
+  T cf = cos(phi), sf = sin(phi);
+  T Sx = s * sc, Cx = s * cc;
+  T cot = cos(th) / sin(th);
+  q[0] = x + cf * Sx - sf * Cx;
+  q[1] = y + sf * Sx + cf * Cx;
+  q[2] = z + s * cot;
+  q[3] = kap;
+  q[4] = phi + psi;
+  q[5] = th;
+  // Partial derivatives at fixed s.
+  T F[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) F[i][j] = T(i == j ? 1.0 : 0.0);
+  T dSdh = s * s * f1, dCdh = s * s * f2;
+  F[0][3] = kb * (cf * dSdh - sf * dCdh);
+  F[0][4] = -(q[1] - y);
+  F[1][3] = kb * (sf * dSdh + cf * dCdh);
+  F[1][4] = q[0] - x;
+  T sth = sin(th);
+  F[2][5] = -s / (sth * sth);
+  F[4][3] = kb * s;
+  // Implicit path length: g(p, s) = x'^2 + y'^2 - R^2 = 0.
+  T cp = cos(q[4]), sp = sin(q[4]);
+  T dgds = q[0] * cp + q[1] * sp;
+  T dsdp[6];
+  for (int j = 0; j < 6; ++j) dsdp[j] = -(q[0] * F[0][j] + q[1] * F[1][j]) / dgds;
+  T dqds[6] = {cp, sp, cot, T(0.0), h, T(0.0)};
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) J[i][j] = F[i][j] + dqds[i] * dsdp[j];
+  return true;
+}
+
+template <class T>
+void transport(const T J[6][6], T C[6][6]) {  // C <- J C J^T
+  T JC[6][6], out[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      T acc(0.0);
+      for (int k = 0; k < 6; ++k) acc += J[i][k] * C[k][j];
+      JC[i][j] = acc;
+    }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      T acc(0.0);
+      for (int k = 0; k < 6; ++k) acc += JC[i][k] * J[j][k];
+      out[i][j] = acc;
+    }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) C[i][j] = 0.5 * (out[i][j] + out[j][i]);
+}
+
+// ---------------------------------------------------------------- measurement
+// Hit m (alignment-corrected) against prediction p: r = (u.(m_xy - p_xy), m_z - z)
+// with u = (-sin phi_p, cos phi_p), phi_p = atan2(y, x).  Hits on the far half
+// of the cylinder (m_xy . p_xy <= 0) are incompatible.
+template <class T>
+struct Meas {
+  T r[2];
+  T H[2][6];
+  T S[2][2];
+  T Sinv[2][2];
+  T chi2;
+};
+
+template <class T>
+bool measure(const T p[6], const T C[6][6], const T m[3], double vr, double vz, Meas<T>& o) {
+  if (val(m[0]) * val(p[0]) + val(m[1]) * val(p[1]) <= 0.0) return false;
+  T phip = atan2(p[1], p[0]);
+  T su = sin(phip), cu = cos(phip);
+  o.r[0] = -su * (m[0] - p[0]) + cu * (m[1] - p[1]);
+  o.r[1] = m[2] - p[2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 6; ++j) o.H[i][j] = T(0.0);
+  o.H[0][0] = -su;
+  o.H[0][1] = cu;
+  o.H[1][2] = T(1.0);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      T acc(0.0);
+      for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) acc += o.H[a][i] * C[i][j] * o.H[b][j];
+      o.S[a][b] = acc;
+    }
+  o.S[0][0] += vr;
+  o.S[1][1] += vz;
+  T det = o.S[0][0] * o.S[1][1] - o.S[0][1] * o.S[1][0];
+  o.Sinv[0][0] = o.S[1][1] / det;
+  o.Sinv[1][1] = o.S[0][0] / det;
+  o.Sinv[0][1] = -o.S[0][1] / det;
+  o.Sinv[1][0] = -o.S[1][0] / det;
+  o.chi2 = T(0.0);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) o.chi2 += o.r[a] * o.Sinv[a][b] * o.r[b];
+  return true;
+}
+
+template <class T>
+void kf_update(T p[6], T C[6][6], const Meas<T>& m) {
+  T CHt[6][2], K[6][2], HC[2][6];
+  for (int i = 0; i < 6; ++i)
+    for (int a = 0; a < 2; ++a) {
+      T acc(0.0);
+      for (int j = 0; j < 6; ++j) acc += C[i][j] * m.H[a][j];
+      CHt[i][a] = acc;
+    }
+  for (int i = 0; i < 6; ++i)
+    for (int a = 0; a < 2; ++a) K[i][a] = CHt[i][0] * m.Sinv[0][a] + CHt[i][1] * m.Sinv[1][a];
+  for (int a = 0; a < 2; ++a)
+    for (int j = 0; j < 6; ++j) {
+      T acc(0.0);
+      for (int i = 0; i < 6; ++i) acc += m.H[a][i] * C[i][j];
+      HC[a][j] = acc;
+    }
+  for (int i = 0; i < 6; ++i) p[i] += K[i][0] * m.r[0] + K[i][1] * m.r[1];
+  T out[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) out[i][j] = C[i][j] - (K[i][0] * HC[0][j] + K[i][1] * HC[1][j]);
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) C[i][j] = 0.5 * (out[i][j] + out[j][i]);
+}
+
+// Multiple scattering in a thin layer of x0 radiation lengths at the current
+// position: Highland width theta0 = 0.0136/(beta p) sqrt(t) (1 + 0.038 ln t),
+// t = x0 / |sin(theta) cos(phi - phi_p)|, p = pT/sin(theta), pion mass for beta.
+template <class T>
+T highland(const T p[6], double x0) {
+  T st = sin(p[5]);
+  T pm = 1.0 / (fabs(p[3]) * st);
+  T beta = pm / sqrt(pm * pm + MPION * MPION);
+  T phip = atan2(p[1], p[0]);
+  T t = x0 / fabs(st * cos(p[4] - phip));
+  return 0.0136 / (beta * pm) * sqrt(t) * (1.0 + 0.038 * log(t));
+}
+
+template <class T>
+void add_ms(const T p[6], T C[6][6], double x0) {
+  if (val(p[3]) == 0.0 || x0 <= 0.0) return;
+  T th0 = highland(p, x0);
+  T st = sin(p[5]);
+  T v = th0 * th0;
+  C[4][4] += v / (st * st);
+  C[5][5] += v;
+}
+
+// Alignment correction of a raw hit on layer L: rotate by -a_rphi/R_L about z,
+// then z -= a_z.
+template <class T>
+void correct_hit(const T raw[3], const T& a_rphi, const T& a_z, double R, T m[3]) {
+  T ang = -a_rphi / R;
+  T ca = cos(ang), sa = sin(ang);
+  m[0] = ca * raw[0] - sa * raw[1];
+  m[1] = sa * raw[0] + ca * raw[1];
+  m[2] = raw[2] - a_z;
+}
+
+// Kalman fit over hits (raw positions, per-hit layer), from prior (p0, C0)
+// placed at the first hit: no propagation before the first update, MS after
+// each update except (optionally) the last.  Returns 0 or a negative status.
+template <class T>
+int fit_track(const Det& det, const T p0[6], const double C0[6][6], int n, const T (*raw)[3],
+              const int* layers, const T (*align)[2], bool ms_after_last, T p[6], T C[6][6],
+              T& chi2, T* chi2_each = nullptr) {
+  for (int i = 0; i < 6; ++i) {
+    p[i] = p0[i];
+    for (int j = 0; j < 6; ++j) C[i][j] = T(C0[i][j]);
+  }
+  chi2 = T(0.0);
+  const double vr = det.sigma_rphi * det.sigma_rphi, vz = det.sigma_z * det.sigma_z;
+  for (int k = 0; k < n; ++k) {
+    const int L = layers[k];
+    const double R = det.radius[L];
+    if (k > 0) {
+      T q[6], J[6][6];
+      if (!propagate(det.bz, p, R, q, J)) return -1;
+      for (int i = 0; i < 6; ++i) p[i] = q[i];
+      transport(J, C);
+    }
+    T m[3];
+    correct_hit(raw[k], align[L][0], align[L][1], R, m);
+    Meas<T> ms;
+    if (!measure(p, C, m, vr, vz, ms)) return -2;
+    chi2 += ms.chi2;
+    if (chi2_each) chi2_each[k] = ms.chi2;
+    kf_update(p, C, ms);
+    if (k + 1 < n || ms_after_last) add_ms(p, C, det.x0[L]);
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------- finding
+struct Cand {
+  double p[6];
+  double C[6][6];
+  int n_found;
+  int n_holes;
+  double chi2;
+  bool finished;
+  std::vector<int> hits;
+};
+
+enum Kind { KIND_HIT = 0, KIND_HOLE = 1, KIND_CARRIED = 2 };
+
+struct Child {
+  int n_found;
+  double chi2;
+  int parent;
+  int kind;
+  int hit;
+  double hit_chi2;
+};
+
+// Ranking key of the candidate score: more hits first, then lower chi2 sum,
+// then parent rank, then hit before hole, then lower hit index.
+bool child_less(const Child& a, const Child& b) {
+  if (a.n_found != b.n_found) return a.n_found > b.n_found;
+  if (a.chi2 != b.chi2) return a.chi2 < b.chi2;
+  if (a.parent != b.parent) return a.parent < b.parent;
+  if (a.kind != b.kind) return a.kind < b.kind;
+  return a.hit < b.hit;
+}
+
+struct LayerIndex {  // hits of one layer sorted by z (exact chi2 pre-selection)
+  std::vector<int> idx;
+  std::vector<double> z;
+};
+
+struct Counters {
+  long long steps;        // candidate propagated, transported and tested on a layer
+  long long prop_calls;   // propagations attempted
+  long long updates;      // kept hit-children updated
+  long long ms;           // multiple-scattering applications
+  long long chi2_evals;   // hits whose chi2 was evaluated
+  long long seeds;
+  long long children;     // children ranked
+  long long reserved;
+};
+
+void seed_state(const double* params, const double* cov, long stride, long i, double p[6],
+                double C[6][6]) {
+  for (int k = 0; k < 6; ++k) p[k] = params[k * stride + i];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) C[a][b] = cov[sym_index(a, b) * stride + i];
+}
+
+void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* hy, const double* hz,
+               const int* hlayer, const std::vector<LayerIndex>& lidx, bool brute, int n_hits,
+               const double p0[6], const double C0[6][6], const int sh[3], const double (*align)[2],
+               int* out_hits, int* out_n, double* out_chi2, double* out_p, double* out_C,
+               Counters& cnt) {
+  const int L = det.n_layers;
+  const double vr = det.sigma_rphi * det.sigma_rphi, vz = det.sigma_z * det.sigma_z;
+  Cand c0;
+  {
+    double raw[3][3];
+    int lays[3];
+    for (int k = 0; k < 3; ++k) {
+      raw[k][0] = hx[sh[k]]; raw[k][1] = hy[sh[k]]; raw[k][2] = hz[sh[k]];
+      lays[k] = hlayer[sh[k]];
+    }
+    double chi2;
+    int st = fit_track<double>(det, p0, C0, 3, raw, lays, align, true, c0.p, c0.C, chi2);
+    c0.n_found = 3;
+    c0.n_holes = 0;
+    c0.chi2 = chi2;
+    c0.finished = st != 0;
+    c0.hits = {sh[0], sh[1], sh[2]};
+    if (st == 0) cnt.ms += 3;
+  }
+  std::vector<Cand> cands{c0};
+  const int start = hlayer[sh[2]] + 1;
+  for (int Lyr = start; Lyr < L; ++Lyr) {
+    const double R = det.radius[Lyr];
+    std::vector<Child> children;
+    std::vector<Cand> predicted(cands.size());
+    for (size_t r = 0; r < cands.size(); ++r) {
+      const Cand& c = cands[r];
+      if (c.finished) {
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0.0});
+        continue;
+      }
+      Cand& pc = predicted[r];
+      pc = c;
+      double J[6][6];
+      ++cnt.prop_calls;
+      if (!propagate(det.bz, c.p, R, pc.p, J) || std::fabs(pc.p[2]) > det.z_max) {
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0.0});
+        continue;
+      }
+      transport(J, pc.C);
+      ++cnt.steps;
+      int n_children = 0;
+      // Window on z: chi2 >= r_z^2 / S_zz for a 2x2 positive-definite S, so
+      // hits with |m_z - z| > sqrt(cut * S_zz) cannot pass the cut.
+      const double szz = pc.C[2][2] + vz;
+      double lo_z = -1e300, hi_z = 1e300;
+      if (!brute) {
+        // corrected z = raw z - a_z, so the raw-z interval is shifted by a_z
+        const double w = std::sqrt(cfg.chi2_cut * szz) + 1e-9;
+        lo_z = pc.p[2] + align[Lyr][1] - w;
+        hi_z = pc.p[2] + align[Lyr][1] + w;
+      }
+      const LayerIndex& li = lidx[Lyr];
+      size_t b = std::lower_bound(li.z.begin(), li.z.end(), lo_z) - li.z.begin();
+      for (size_t k = b; k < li.idx.size() && li.z[k] <= hi_z; ++k) {
+        const int hidx = li.idx[k];
+        double raw[3] = {hx[hidx], hy[hidx], hz[hidx]}, m[3];
+        correct_hit(raw, align[Lyr][0], align[Lyr][1], R, m);
+        Meas<double> ms;
+        ++cnt.chi2_evals;
+        if (!measure(pc.p, pc.C, m, vr, vz, ms)) continue;
+        if (ms.chi2 < cfg.chi2_cut) {
+          children.push_back({c.n_found + 1, c.chi2 + ms.chi2, (int)r, KIND_HIT, hidx, ms.chi2});
+          ++n_children;
+        }
+      }
+      if (c.n_holes < cfg.max_holes) {
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_HOLE, -1, 0.0});
+        ++n_children;
+      }
+      if (n_children == 0) {  // no compatible hit and no hole left: the candidate stops
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0.0});
+      }
+    }
+    cnt.children += (long long)children.size();
+    std::sort(children.begin(), children.end(), child_less);
+    const size_t keep = std::min(children.size(), (size_t)cfg.max_cands);
+    std::vector<Cand> next;
+    next.reserve(keep);
+    for (size_t k = 0; k < keep; ++k) {
+      const Child& ch = children[k];
+      if (ch.kind == KIND_CARRIED) {
+        Cand c = cands[ch.parent];
+        c.finished = true;
+        next.push_back(c);
+        continue;
+      }
+      Cand c = predicted[ch.parent];
+      if (ch.kind == KIND_HIT) {
+        double raw[3] = {hx[ch.hit], hy[ch.hit], hz[ch.hit]}, m[3];
+        correct_hit(raw, align[Lyr][0], align[Lyr][1], R, m);
+        Meas<double> ms;
+        measure(c.p, c.C, m, vr, vz, ms);
+        kf_update(c.p, c.C, ms);
+        c.n_found += 1;
+        c.chi2 = ch.chi2;
+        c.hits.push_back(ch.hit);
+        ++cnt.updates;
+      } else {
+        c.n_holes += 1;
+      }
+      add_ms(c.p, c.C, det.x0[Lyr]);
+      ++cnt.ms;
+      next.push_back(c);
+    }
+    cands.swap(next);
+  }
+  const Cand& best = cands[0];
+  for (int k = 0; k < L; ++k) out_hits[k] = k < (int)best.hits.size() ? best.hits[k] : -1;
+  *out_n = (int)best.hits.size();
+  *out_chi2 = best.chi2;
+  for (int k = 0; k < 6; ++k) out_p[k] = best.p[k];
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) out_C[sym_index(a, b)] = best.C[a][b];
+  ++cnt.seeds;
+  (void)n_hits;
+}
+
+}  // namespace
+
+// ====================================================================== C API
+extern "C" {
+
+struct orc_detector {
+  int n_layers;
+  double radius[64];
+  double x0[64];
+  double z_max;
+  double bz;
+  double sigma_rphi;
+  double sigma_z;
+};
+
+struct orc_config {
+  int max_cands;
+  int max_holes;
+  double chi2_cut;
+};
+
+static Det to_det(const orc_detector* d) {
+  Det o;
+  o.n_layers = d->n_layers;
+  for (int i = 0; i < 64; ++i) { o.radius[i] = d->radius[i]; o.x0[i] = d->x0[i]; }
+  o.z_max = d->z_max;
+  o.bz = d->bz;
+  o.sigma_rphi = d->sigma_rphi;
+  o.sigma_z = d->sigma_z;
+  return o;
+}
+
+// Propagation of one state to radius R.  J is row-major 6x6.  Returns 1 if a
+// crossing exists, 0 otherwise.
+int orc_propagate(double bz, const double* p, double R, double* q, double* J) {
+  double Jm[6][6];
+  if (!propagate<double>(bz, p, R, q, Jm)) return 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) J[i * 6 + j] = Jm[i][j];
+  return 1;
+}
+
+// Path length to the crossing (pins of the closed form).
+int orc_path_length(double bz, const double* p, double R, double* s) {
+  return path_to_cylinder<double>(p[0], p[1], -KCURV * bz * p[3], p[4], R, *s) ? 1 : 0;
+}
+
+// Jacobian of the propagated state by forward-mode differentiation of the
+// propagation itself (independent of the hand-derived J).
+int orc_propagate_ad(double bz, const double* p, double R, double* Jad) {
+  g_nd = 6;
+  Dual pd[6], qd[6], Jd[6][6];
+  for (int k = 0; k < 6; ++k) pd[k] = make_var(p[k], k);
+  const bool ok = propagate<Dual>(bz, pd, R, qd, Jd);
+  if (ok)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) Jad[i * 6 + j] = qd[i].d[j];
+  g_nd = 0;
+  return ok ? 1 : 0;
+}
+
+// C_out = J C J^T for full row-major 6x6 matrices.
+void orc_transport(const double* J, const double* C, double* C_out) {
+  double Jm[6][6], Cm[6][6];
+  for (int i = 0; i < 36; ++i) { Jm[i / 6][i % 6] = J[i]; Cm[i / 6][i % 6] = C[i]; }
+  transport(Jm, Cm);
+  for (int i = 0; i < 36; ++i) C_out[i] = Cm[i / 6][i % 6];
+}
+
+// One measurement + update at the current state.  Returns 0 if the hit is on
+// the far side, 1 otherwise.
+int orc_update(const double* p, const double* C, const double* m, double vr, double vz,
+               double* p_out, double* C_out, double* chi2, double* resid) {
+  double pp[6], Cm[6][6];
+  for (int i = 0; i < 6; ++i) pp[i] = p[i];
+  for (int i = 0; i < 36; ++i) Cm[i / 6][i % 6] = C[i];
+  Meas<double> ms;
+  if (!measure(pp, Cm, m, vr, vz, ms)) return 0;
+  kf_update(pp, Cm, ms);
+  for (int i = 0; i < 6; ++i) p_out[i] = pp[i];
+  for (int i = 0; i < 36; ++i) C_out[i] = Cm[i / 6][i % 6];
+  *chi2 = ms.chi2;
+  if (resid) { resid[0] = ms.r[0]; resid[1] = ms.r[1]; }
+  return 1;
+}
+
+double orc_highland(const double* p, double x0) { return highland<double>(p, x0); }
+
+void orc_add_ms(const double* p, double* C, double x0) {
+  double Cm[6][6];
+  for (int i = 0; i < 36; ++i) Cm[i / 6][i % 6] = C[i];
+  add_ms(p, Cm, x0);
+  for (int i = 0; i < 36; ++i) C[i] = Cm[i / 6][i % 6];
+}
+
+// Kalman fit of n_tracks tracks.  prior_p [6][stride], prior_C [21][stride]
+// (structure of arrays, seeds index t), hit_lists [n_tracks][max_len] of
+// indices into hx/hy/hz/hlayer, n_hits [n_tracks], align [n_layers][2].
+// Outputs: p_out [n][6], C_out [n][21], chi2 [n], chi2_each [n][max_len]
+// (optional), status [n].
+int orc_fit(const orc_detector* dptr, int n_tracks, const double* prior_p, const double* prior_C,
+            long stride, const int* hit_lists, const int* n_hits, int max_len, const double* hx,
+            const double* hy, const double* hz, const int* hlayer, const double* align,
+            int ms_after_last, double* p_out, double* C_out, double* chi2, double* chi2_each,
+            int* status) {
+  const Det det = to_det(dptr);
+  double al[64][2];
+  for (int i = 0; i < det.n_layers; ++i) { al[i][0] = align[2 * i]; al[i][1] = align[2 * i + 1]; }
+  std::vector<double> raw(3 * (size_t)max_len);
+  std::vector<int> lays(max_len);
+  for (int t = 0; t < n_tracks; ++t) {
+    double p0[6], C0[6][6], p[6], C[6][6], c2;
+    seed_state(prior_p, prior_C, stride, t, p0, C0);
+    const int n = n_hits[t];
+    for (int k = 0; k < n; ++k) {
+      const int hidx = hit_lists[(size_t)t * max_len + k];
+      raw[3 * k] = hx[hidx]; raw[3 * k + 1] = hy[hidx]; raw[3 * k + 2] = hz[hidx];
+      lays[k] = hlayer[hidx];
+    }
+    status[t] = fit_track<double>(det, p0, C0, n, reinterpret_cast<const double(*)[3]>(raw.data()),
+                                  lays.data(), al, ms_after_last != 0, p, C, c2,
+                                  chi2_each ? chi2_each + (size_t)t * max_len : nullptr);
+    for (int k = 0; k < 6; ++k) p_out[6 * t + k] = p[k];
+    for (int a = 0; a < 6; ++a)
+      for (int b = a; b < 6; ++b) C_out[21 * (size_t)t + sym_index(a, b)] = C[a][b];
+    chi2[t] = c2;
+  }
+  return 0;
+}
+
+// Summed chi2 of the fits and its gradient by forward-mode dual numbers:
+// g_align [n_layers][2], g_hits [n_hit_arrays][3] (accumulated over tracks
+// sharing a hit), g_seed [n_tracks][6].
+int orc_fit_grad(const orc_detector* dptr, int n_tracks, const double* prior_p,
+                 const double* prior_C, long stride, const int* hit_lists, const int* n_hits,
+                 int max_len, const double* hx, const double* hy, const double* hz,
+                 const int* hlayer, const double* align, double* chi2_total, double* g_align,
+                 double* g_hits, double* g_seed, double* chi2_each) {
+  const Det det = to_det(dptr);
+  const int L = det.n_layers;
+  double total = 0.0;
+  for (int t = 0; t < n_tracks; ++t) {
+    const int n = n_hits[t];
+    g_nd = 6 + 3 * n + 2 * L;
+    if (g_nd > DMAX) { g_nd = 0; return -1; }
+    Dual p0[6];
+    double C0[6][6], p0v[6];
+    seed_state(prior_p, prior_C, stride, t, p0v, C0);
+    for (int k = 0; k < 6; ++k) p0[k] = make_var(p0v[k], k);
+    std::vector<Dual> rawv(3 * (size_t)n);
+    std::vector<int> lays(n);
+    for (int k = 0; k < n; ++k) {
+      const int hidx = hit_lists[(size_t)t * max_len + k];
+      rawv[3 * k] = make_var(hx[hidx], 6 + 3 * k);
+      rawv[3 * k + 1] = make_var(hy[hidx], 6 + 3 * k + 1);
+      rawv[3 * k + 2] = make_var(hz[hidx], 6 + 3 * k + 2);
+      lays[k] = hlayer[hidx];
+    }
+    std::vector<Dual> alv(2 * (size_t)L);
+    for (int i = 0; i < L; ++i) {
+      alv[2 * i] = make_var(align[2 * i], 6 + 3 * n + 2 * i);
+      alv[2 * i + 1] = make_var(align[2 * i + 1], 6 + 3 * n + 2 * i + 1);
+    }
+    Dual p[6], C[6][6], c2;
+    const int st = fit_track<Dual>(det, p0, C0, n, reinterpret_cast<const Dual(*)[3]>(rawv.data()),
+                                   lays.data(), reinterpret_cast<const Dual(*)[2]>(alv.data()),
+                                   false, p, C, c2);
+    if (st != 0) { g_nd = 0; return -2 - t; }
+    total += c2.v;
+    if (chi2_each) chi2_each[t] = c2.v;
+    for (int k = 0; k < 6; ++k) g_seed[6 * (size_t)t + k] = c2.d[k];
+    for (int k = 0; k < n; ++k) {
+      const int hidx = hit_lists[(size_t)t * max_len + k];
+      for (int c = 0; c < 3; ++c) g_hits[3 * (size_t)hidx + c] += c2.d[6 + 3 * k + c];
+    }
+    for (int i = 0; i < 2 * L; ++i) g_align[i] += c2.d[6 + 3 * n + i];
+  }
+  *chi2_total = total;
+  g_nd = 0;
+  return 0;
+}
+
+// Combinatorial finding for seeds [s_begin, s_end) of one event.  Hits are
+// the event's arrays (event-local indices); seeds are structure-of-arrays with
+// the given stride; seed_hits [3][stride].  out_hits [n][n_layers] (padded -1),
+// out_p [n][6], out_C [n][21].  counters: see Counters.  brute != 0 tests every
+// hit of the layer instead of the exact z pre-selection.
+int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits, const double* hx,
+                   const double* hy, const double* hz, const int* hlayer, const double* params,
+                   const double* cov, const int* seed_hits, long stride, int s_begin, int s_end,
+                   const double* align, int brute, int* out_hits, int* out_n, double* out_chi2,
+                   double* out_p, double* out_C, long long* counters) {
+  const Det det = to_det(dptr);
+  Cfg cfg{cfgp->max_cands, cfgp->max_holes, cfgp->chi2_cut};
+  const int L = det.n_layers;
+  double al[64][2];
+  for (int i = 0; i < L; ++i) { al[i][0] = align[2 * i]; al[i][1] = align[2 * i + 1]; }
+  std::vector<LayerIndex> lidx(L);
+  for (int h = 0; h < n_hits; ++h)
+    if (hlayer[h] >= 0 && hlayer[h] < L) lidx[hlayer[h]].idx.push_back(h);
+  for (int l = 0; l < L; ++l) {
+    LayerIndex& li = lidx[l];
+    if (!brute)
+      std::stable_sort(li.idx.begin(), li.idx.end(), [&](int a, int b) { return hz[a] < hz[b]; });
+    for (int h : li.idx) li.z.push_back(brute ? 0.0 : (double)hz[h]);
+  }
+  Counters cnt{};
+  for (int s = s_begin; s < s_end; ++s) {
+    double p0[6], C0[6][6];
+    seed_state(params, cov, stride, s, p0, C0);
+    const int sh[3] = {seed_hits[0 * stride + s], seed_hits[1 * stride + s],
+                       seed_hits[2 * stride + s]};
+    const int o = s - s_begin;
+    find_seed(det, cfg, hx, hy, hz, hlayer, lidx, brute != 0, n_hits, p0, C0, sh, al,
+              out_hits + (size_t)o * L, out_n + o, out_chi2 + o, out_p + 6 * (size_t)o,
+              out_C + 21 * (size_t)o, cnt);
+  }
+  if (counters) {
+    counters[0] += cnt.steps; counters[1] += cnt.prop_calls; counters[2] += cnt.updates;
+    counters[3] += cnt.ms; counters[4] += cnt.chi2_evals; counters[5] += cnt.seeds;
+    counters[6] += cnt.children;
+  }
+  return 0;
+}
+
+// Duplicate removal for one event's tracks: walk tracks by (more hits, lower
+// chi2, lower index); keep a track unless it shares more than frac*min(nA, nB)
+// hits with a track already kept.  hits [n][max_len] event-local indices.
+// brute != 0 compares against every kept track directly.
+int orc_dedup(int n_tracks, const int* hits, const int* n_hits, const double* chi2, int max_len,
+              double frac, int brute, unsigned char* keep) {
+  std::vector<int> order(n_tracks);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (n_hits[a] != n_hits[b]) return n_hits[a] > n_hits[b];
+    if (chi2[a] != chi2[b]) return chi2[a] < chi2[b];
+    return a < b;
+  });
+  std::vector<int> kept;
+  // hit -> kept tracks holding it (index form of the same comparison)
+  std::vector<std::pair<int, int>> owner;  // (hit, track), kept sorted by hit
+  for (int t = 0; t < n_tracks; ++t) keep[t] = 0;
+  std::vector<int> shared(n_tracks, 0);
+  for (int t : order) {
+    bool dup = false;
+    const int* ht = hits + (size_t)t * max_len;
+    if (brute) {
+      for (int k : kept) {
+        const int* hk = hits + (size_t)k * max_len;
+        int nsh = 0;
+        for (int a = 0; a < n_hits[t]; ++a)
+          for (int b = 0; b < n_hits[k]; ++b) nsh += ht[a] == hk[b];
+        if (nsh > frac * std::min(n_hits[t], n_hits[k])) { dup = true; break; }
+      }
+    } else {
+      std::vector<int> touched;
+      for (int a = 0; a < n_hits[t]; ++a) {
+        auto it = std::lower_bound(owner.begin(), owner.end(), std::make_pair(ht[a], -1));
+        for (; it != owner.end() && it->first == ht[a]; ++it) {
+          if (shared[it->second]++ == 0) touched.push_back(it->second);
+        }
+      }
+      for (int k : touched) {
+        if (shared[k] > frac * std::min(n_hits[t], n_hits[k])) dup = true;
+        shared[k] = 0;
+      }
+    }
+    if (!dup) {
+      keep[t] = 1;
+      kept.push_back(t);
+      if (!brute) {
+        for (int a = 0; a < n_hits[t]; ++a) {
+          auto pr = std::make_pair(ht[a], t);
+          owner.insert(std::upper_bound(owner.begin(), owner.end(), pr), pr);
+        }
+      }
+    }
+  }
+  return 0;
+}
+
+}  // extern "C"
