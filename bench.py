@@ -1,0 +1,393 @@
+"""Benchmark: batched Kalman-filter track finding + duplicate removal + re-fit.
+
+Workload: PU-200-like batch, 100 events x 8,000 generated tracks, 17 barrel
+layers, 20% noise hits, up to 10 candidates per seed (synthetic, seeded).
+One step = bin hits, find tracks for every seed, remove duplicates, re-fit the
+kept tracks, replayed as one captured CUDA graph over the whole batch.
+
+Prints one JSON line: seeds/s (whole job), candidate-layer steps/s, the plain
+per-event launch form for comparison, the end-to-end rate through the C ABI
+with host buffers, the FP32 roofline of the find kernel and the FP64 oracle's
+rate on the host cores (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "seeds/s and candidate-layer KF updates/s at PU-200, batched vs plain; % FP32 peak"
+UNIT = "seeds/s"
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic FP32 operations per unit of work (an FMA counts 2), counted on
+# the minimal sparse formulation of each step; see the design notes.
+F_STEP = 443      # propagation + exact Jacobian + sparse J C J^T + frame + window
+F_HIT = 25        # alignment correction + residual + chi2 of one hit in a window
+F_UPDATE = 195    # frame + gain + state/covariance update of a kept hit-child
+F_MS = 25         # multiple-scattering term
+F_SEED = 1436     # seed fit over three hits
+F_FIT_HIT = 608   # re-fit: propagation + transport + update + scattering per hit
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, s[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(name, rank, n_events=None):
+    from synth import make_batch
+    # per-rank distinct events: shift the configuration seed by the rank
+    from synth.events import CONFIGS
+    seed = CONFIGS[name]["seed"] + 7919 * rank
+    return make_batch(name, n_events=n_events, seed=seed)
+
+
+def tracker_for(b, **cfg):
+    from paper_1906_11744_gb300 import Tracker, make_config, make_detector
+    d = b.det
+    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z)
+    c = dict(max_cands=b.cfg["max_cands"])
+    c.update(cfg)
+    return Tracker(det, make_config(**c))
+
+
+def oracle_sample(b, budget_s=15.0):
+    """The FP64 oracle (find + duplicate removal + re-fit, one host core) on
+    whole events of the batch until about budget_s seconds of work."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    seeds = 0
+    events = 0
+    steps = 0
+    for e in range(b.n_events):
+        r = oracle.find_event(b, e)
+        keep = oracle.dedup(r["hits"], r["n_found"], r["chi2"], 0.5)
+        x, y, z, lay = b.event_hits(e)
+        prm, cov, sh = b.event_seeds(e)
+        k = np.nonzero(keep)[0]
+        oracle.fit(b.det, prm[:, k], cov[:, k], r["hits"][k], r["n_found"][k], x, y, z, lay, align=b.align)
+        seeds += prm.shape[1]
+        steps += r["counters"]["steps"]
+        events += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=seeds / dt, unit=UNIT, cores=1, kind="oracle", seconds=dt,
+                sample=f"{events} of {b.n_events} events ({seeds} seeds), find + dedup + fit, FP64, 1 thread",
+                steps_per_s=steps / dt)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    b = make_inputs(args.config, 0, n_events=min(args.ref_events, 100))
+    times = []
+    seeds = 0
+    for _ in range(args.warmup + args.steps):
+        r = oracle_sample(b, budget_s=args.ref_budget / max(1, args.steps))
+        times.append(r)
+    timed = times[args.warmup:]
+    value = statistics.mean(t["value"] for t in timed)
+    seeds = sum(int(t["sample"].split("(")[1].split()[0]) for t in timed)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 * statistics.mean(t["seconds"] for t in timed),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_desc(args.config)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": timed[0]["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def workload_desc(name):
+    from synth.events import CONFIGS
+    c = CONFIGS[name]
+    tr = c["tracks"] if c["tracks"] != "pileup" else f"50xPU{c['pileup_range']}"
+    return (f"{name}: {c['n_events']} events x {tr} tracks, {c['n_layers']} barrel layers, "
+            f"{int(100 * c['noise'])}% noise, N={c['max_cands']} candidates, 64x1024 eta-phi bins")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c4")
+    ap.add_argument("--events", type=int, default=None, help="override the number of events")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=60.0)
+    ap.add_argument("--ref-events", type=int, default=20)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1906_11744_gb300 import KF_FIT_FOUND
+
+    b = make_inputs(args.config, rank, n_events=args.events)
+    n_seeds = b.n_seeds
+    stream = torch.cuda.Stream(device=dev)
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d_in = dict(x=tt(b.x), y=tt(b.y), z=tt(b.z), layer=tt(b.layer), params=tt(b.params),
+                cov=tt(b.cov), seed_hits=tt(b.seed_hits))
+    torch.cuda.synchronize()
+
+    t = tracker_for(b, persistent=1, per_event=0)
+    t.load_hits(b.hit_off, d_in["x"], d_in["y"], d_in["z"], d_in["layer"], stream)
+    t.load_seeds(b.seed_off, d_in["params"], d_in["cov"], d_in["seed_hits"], stream)
+    t.set_alignment(b.align, stream)
+    tune = None
+    if not args.no_autotune:
+        tune = t.autotune(stream)
+    t.set_stage_timing(True)
+    t.capture_graph(stream=stream)
+    n_kernels = t.graph_kernel_count()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+
+    for _ in range(args.warmup):
+        t.launch_graph(stream)
+    stream.synchronize()
+    counters = t.counters(stream)
+
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = {"bin": 0.0, "find": 0.0, "dedup": 0.0, "fit": 0.0}
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush_l2()
+        ev_a[k].record(stream)
+        t.launch_graph(stream)
+        ev_b[k].record(stream)
+        st = t.stage_ms(stream)  # synchronizes the stream
+        for key in stage:
+            stage[key] += st[key]
+    torch.cuda.synchronize()
+    clocks.stop()
+    step_ms = [a.elapsed_time(bb) for a, bb in zip(ev_a, ev_b)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tm = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tm.item())
+    seeds_all = n_seeds * world
+    value = seeds_all * args.steps / (total_ms / 1e3)
+    steps_per_s = counters["steps"] * world * args.steps / (total_ms / 1e3)
+
+    # roofline of the find kernel (ALU bound: FP32 FMA pipe)
+    find_ms = stage["find"] / args.steps
+    find_flops = (counters["steps"] * F_STEP + counters["chi2_evals"] * F_HIT + counters["updates"] * F_UPDATE
+                  + (counters["updates"] + counters["holes"]) * F_MS + counters["seeds"] * F_SEED)
+    achieved = find_flops / (find_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_find",
+                "flops_per_launch": find_flops, "find_ms": find_ms,
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts x max clock)"}
+
+    # plain per-event launches (no graph), same work
+    plain = None
+    if not args.no_plain:
+        tp = tracker_for(b, persistent=0, per_event=1,
+                         lanes_per_seed=int(tune[np.argmin(tune[:, 4])][0]) if tune is not None and len(tune) else 0)
+        tp.load_hits(b.hit_off, d_in["x"], d_in["y"], d_in["z"], d_in["layer"], stream)
+        tp.load_seeds(b.seed_off, d_in["params"], d_in["cov"], d_in["seed_hits"], stream)
+        tp.set_alignment(b.align, stream)
+
+        def plain_step():
+            tp.find_tracks(stream)
+            tp.remove_duplicates(stream)
+            tp.fit_tracks(KF_FIT_FOUND, stream=stream)
+
+        for _ in range(args.warmup):
+            plain_step()
+        stream.synchronize()
+        pa = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        pb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush_l2()
+            pa[k].record(stream)
+            plain_step()
+            pb[k].record(stream)
+        stream.synchronize()
+        pms = sum(a.elapsed_time(bb) for a, bb in zip(pa, pb))
+        plain = {"value": seeds_all * args.steps / (pms / 1e3), "unit": UNIT,
+                 "ms_per_step": pms / args.steps, "form": "per-event launches of bin/find/dedup, one fit, no graph"}
+        tp.close()
+
+    # end to end through the C ABI with host buffers (pinned), host<->device copies inside
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        h = dict(x=pin(b.x), y=pin(b.y), z=pin(b.z), layer=pin(b.layer), params=pin(b.params),
+                 cov=pin(b.cov), seed_hits=pin(b.seed_hits))
+        L = b.det.n_layers
+        outs = dict(hits=torch.empty((n_seeds, L), dtype=torch.int32).pin_memory(),
+                    n_found=torch.empty(n_seeds, dtype=torch.int32).pin_memory(),
+                    chi2=torch.empty(n_seeds, dtype=torch.float32).pin_memory(),
+                    keep=torch.empty(n_seeds, dtype=torch.uint8).pin_memory())
+        fouts = dict(params=torch.empty((6, n_seeds), dtype=torch.float32).pin_memory(),
+                     chi2=torch.empty(n_seeds, dtype=torch.float32).pin_memory(),
+                     status=torch.empty(n_seeds, dtype=torch.int32).pin_memory())
+        from paper_1906_11744_gb300 import kf_get_fit, kf_get_tracks
+
+        def e2e_step():
+            t.load_hits(b.hit_off, h["x"], h["y"], h["z"], h["layer"], stream)
+            t.load_seeds(b.seed_off, h["params"], h["cov"], h["seed_hits"], stream)
+            t.launch_graph(stream)
+            kf_get_tracks(t.ctx, **outs, stream=stream)
+            kf_get_fit(t.ctx, **fouts, stream=stream)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            tm = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(tm.item())
+        bi = sum(v.numel() * v.element_size() for v in h.values())
+        bo = sum(v.numel() * v.element_size() for v in outs.values()) + \
+            sum(v.numel() * v.element_size() for v in fouts.values())
+        e2e = {"value": seeds_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_oracle:
+        cpu = oracle_sample(b, budget_s=args.oracle_budget)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": workload_desc(args.config) + (f" (events={args.events})" if args.events else ""),
+                          "seeds_per_gpu": n_seeds, "hits_per_gpu": b.n_hits,
+                          "l2": "flushed (2x L2 write) before every timed step",
+                          "launch": "one CUDA graph per step: bin(5 kernels) + find + dedup + fit",
+                          "autotuned": None if tune is None else {
+                              "lanes_per_seed": int(tune[np.argmin(tune[:, 4])][0]),
+                              "block_threads": int(tune[np.argmin(tune[:, 4])][1]),
+                              "persistent": int(tune[np.argmin(tune[:, 4])][2]),
+                              "register_cap": int(tune[np.argmin(tune[:, 4])][3]),
+                              "candidates_tried": int(len(tune))}},
+               "candidate_layer_steps_per_s": steps_per_s,
+               "stage_ms": {k: v / args.steps for k, v in stage.items()},
+               "counters_per_step": counters,
+               "plain": plain,
+               "e2e": e2e,
+               "gpu_launches": n_kernels * args.steps,
+               "roofline": roofline,
+               "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+               "clocks": clocks.summary()}
+        print(json.dumps(out))
+    t.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * kf.h - C ABI of the GB300 batched Kalman-filter track finder and fitter.
+ *
+ * The library implements the data-parallel core of the vectorized Kalman
+ * filter tracking of Cerati et al., "Speeding up Particle Track
+ * Reconstruction in the CMS Detector using a Vectorized and Parallelized
+ * Kalman Filter Algorithm" (arXiv:1906.11744):
+ *   - load hits and seeds (Sec. 3: the input conversion step of the build);
+ *   - find tracks: combinatorial Kalman-filter building with per-seed
+ *     candidate ranking (Sec. 2; candidate scores, Sec. 4.3);
+ *   - remove duplicates: the post-processing step on shared hits (Sec. 4.2);
+ *   - fit tracks: the Kalman re-fit of the built tracks (Sec. 5, "fitting");
+ *   - the gradient of the summed fit chi2 with respect to layer alignment
+ *     offsets, hit positions and seed parameters (adjoint of the fit).
+ *
+ * Track state p = (x, y, z, q/pT, phi, theta) in cm, GeV and rad; the
+ * symmetric 6x6 covariance is stored as its 21-element upper triangle,
+ * row-major: (0,0) (0,1) ... (0,5) (1,1) ... (1,5) (2,2) ... (5,5).
+ * Structure-of-arrays buffers are [component][n] with n the number of seeds.
+ *
+ * Conventions for every call:
+ *   - Return value: KF_OK (0) or a negative KF_ERR_* code; kf_last_error()
+ *     gives a message.  No C++ exception crosses this boundary.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.
+ *   - `device_ptrs` = 1: the array arguments are device pointers read (or
+ *     written) in stream order; 0: they are host pointers, copied inside the
+ *     call (host-to-device before, device-to-host after; the call then
+ *     synchronizes the stream before returning).
+ *   - Input buffers stay owned by the caller; the context owns its device
+ *     buffers, sized at load time (loads that grow a buffer allocate; later
+ *     loads of equal or smaller size do not).
+ *   - One context per host thread at a time.  Contexts are independent.
+ *   - Errors raised inside kernels (capacity overflow) set a status word on
+ *     the device; they are reported by the next call that synchronizes
+ *     (kf_get_*, kf_sync).
+ */
+#ifndef KF_H_
+#define KF_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KF_OK 0
+#define KF_ERR_ARG (-1)      /* invalid argument */
+#define KF_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define KF_ERR_CAPACITY (-3) /* a size exceeds a documented limit */
+#define KF_ERR_TIMEOUT (-4)  /* a bounded device-side loop gave up */
+#define KF_ERR_STATE (-5)    /* calls made out of order */
+
+#define KF_MAX_LAYERS 32       /* barrel layers */
+#define KF_MAX_CANDS 16        /* candidates kept per seed */
+#define KF_MAX_EVENT_HITS (1 << 21) /* hits per event (21-bit hit index in ranking keys) */
+
+/* Fit sources for kf_fit_tracks. */
+#define KF_FIT_FOUND 0 /* hit lists produced by kf_find_tracks (kept tracks only after dedup) */
+#define KF_FIT_GIVEN 1 /* caller hit lists */
+
+/* Status values of kf_get_fit's status array. */
+#define KF_FIT_OK 0
+#define KF_FIT_SKIPPED 1   /* track removed as duplicate, not fitted */
+#define KF_FIT_NO_CROSS (-1) /* propagation found no crossing of a hit's layer */
+#define KF_FIT_FAR_SIDE (-2) /* a hit lies on the far half of the cylinder */
+
+typedef struct kf_ctx kf_ctx;
+
+/* Geometry (Sec. 3): concentric barrel cylinders in a uniform field along z. */
+typedef struct {
+  int n_layers;                 /* 1..KF_MAX_LAYERS, radii increasing */
+  float radius[KF_MAX_LAYERS];  /* cm */
+  float x0[KF_MAX_LAYERS];      /* thickness in radiation lengths at normal incidence */
+  float z_max;                  /* half-length of every layer, cm */
+  float bz;                     /* field, tesla (0 = straight tracks) */
+  float sigma_rphi;             /* hit resolution along r-phi, cm */
+  float sigma_z;                /* hit resolution along z, cm */
+} kf_detector;
+
+/* Algorithm settings (Sec. 2 and Sec. 4.3: windows, scores, duplicate cuts). */
+typedef struct {
+  int max_cands;          /* candidates kept per seed, 1..KF_MAX_CANDS */
+  int max_holes;          /* layers without a hit allowed per candidate */
+  float chi2_cut;         /* a hit is compatible if its chi2 is below this */
+  float dup_shared_frac;  /* duplicate if shared hits > frac * min(nA, nB) */
+  int n_eta_bins;         /* hit grid per layer: eta bins (1..256) ... */
+  int n_phi_bins;         /* ... times phi bins */
+  int lanes_per_seed;     /* 0 = automatic; else one of 4, 6, 8, 10, 12, 16 and >= max_cands */
+  int block_threads;      /* 0 = automatic (128); multiple of 32, <= 256 */
+  int persistent;         /* 1 = persistent work-queue launch, 0 = one warp per seed tile */
+  int per_event;          /* 1 = bin, find and remove duplicates with one launch per event
+                             (the plain form); 0 = one launch per step over the whole batch */
+  int ckpt_stride;        /* layers between forward checkpoints of the adjoint (>= 1) */
+} kf_config;
+
+/* Create a context for a detector and configuration.  Allocates nothing on
+ * the device yet.  Errors: KF_ERR_ARG for out-of-range fields. */
+int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out);
+
+/* Release every device buffer, graph and stream-independent resource. */
+int kf_destroy(kf_ctx* ctx);
+
+/* Load hits of n_events events.
+ * ev_offsets: HOST array [n_events+1], CSR offsets into the hit arrays.
+ * x, y, z: float [n_hits] global positions (cm); layer: int [n_hits] in
+ * [0, n_layers).  A hit is referred to by its index within its event
+ * (0 .. ev_offsets[e+1]-ev_offsets[e]-1), in the order given here.
+ * Errors: KF_ERR_ARG, KF_ERR_CAPACITY (an event above KF_MAX_EVENT_HITS). */
+int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* x,
+                 const float* y, const float* z, const int* layer, int device_ptrs, void* stream);
+
+/* Load seeds: prior state at the first seed hit and three seed hits.
+ * ev_offsets: HOST array [n_events+1] (same n_events as the hits).
+ * params: float [6][n_seeds]; cov: float [21][n_seeds]; seed_hits: int
+ * [3][n_seeds] event-local hit indices on increasing layers. */
+int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* params,
+                  const float* cov, const int* seed_hits, int device_ptrs, void* stream);
+
+/* Layer alignment offsets float [n_layers][2] = (a_rphi, a_z) in cm.  A hit
+ * on layer L is used after rotating it by -a_rphi/R_L about z and shifting
+ * z by -a_z.  Zero after kf_create. */
+int kf_set_alignment(kf_ctx* ctx, const float* offsets, int device_ptrs, void* stream);
+
+/* Bin hits and run the combinatorial Kalman-filter finding for every seed
+ * (Sec. 2): seed fit over the three seed hits, then per layer propagation,
+ * covariance transport, chi2 of every compatible hit, per-seed top-N
+ * ranking, update and multiple scattering.  Asynchronous. */
+int kf_find_tracks(kf_ctx* ctx, void* stream);
+
+/* Duplicate removal over the found tracks of each event (Sec. 4.2).
+ * Asynchronous.  Requires kf_find_tracks. */
+int kf_remove_duplicates(kf_ctx* ctx, void* stream);
+
+/* Kalman re-fit from each seed's prior over a hit list.
+ * source = KF_FIT_FOUND: the found tracks (only kept ones once duplicates
+ * were removed); KF_FIT_GIVEN: hit_lists int [n_seeds][max_len]
+ * (event-local indices on increasing layers) with n_hits int [n_seeds].
+ * The result is the state after the last hit, before its scattering.
+ * Asynchronous (host hit lists are copied before the call returns). */
+int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hits, int max_len,
+                  int device_ptrs, void* stream);
+
+/* Gradient of the summed chi2 of the last kf_fit_tracks with respect to the
+ * alignment offsets (g_align float [n_layers][2]), hit positions (g_hits
+ * float [n_hits][3], global hit order, may be NULL) and seed parameters
+ * (g_seed float [6][n_seeds], may be NULL).  Forward states are recomputed
+ * from checkpoints every ckpt_stride layers. */
+int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs,
+                   void* stream);
+
+/* Copy out the found tracks.  hits int [n_seeds][n_layers] (event-local
+ * indices, -1 padded), n_found int [n_seeds], chi2 float [n_seeds], params
+ * float [6][n_seeds], cov float [21][n_seeds], keep uint8 [n_seeds] (1 when
+ * duplicate removal did not run).  Any pointer may be NULL. */
+int kf_get_tracks(kf_ctx* ctx, int* hits, int* n_found, float* chi2, float* params, float* cov,
+                  unsigned char* keep, int device_ptrs, void* stream);
+
+/* Copy out the fit results: params float [6][n_seeds], cov float
+ * [21][n_seeds], chi2 float [n_seeds], status int [n_seeds] (KF_FIT_*). */
+int kf_get_fit(kf_ctx* ctx, float* params, float* cov, float* chi2, int* status, int device_ptrs,
+               void* stream);
+
+/* Capture find + duplicate removal + fit (+ adjoint if with_adjoint) on the
+ * stream into a CUDA graph owned by the context; kf_launch_graph replays it.
+ * Loads between launches must not grow any buffer. */
+int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream);
+int kf_launch_graph(kf_ctx* ctx, void* stream);
+
+/* Time every lanes-per-seed / block-size / register-budget / launch-form
+ * choice of the finding kernel on the loaded inputs and keep the fastest in
+ * the context.  Synchronous.  results (may be NULL) receives up to
+ * max_results rows of 5 floats (lanes, threads, persistent, register cap, ms). */
+int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, void* stream);
+
+/* Counters of the last kf_find_tracks, synchronous (8 values):
+ * [0] candidate-layer steps (a live candidate propagated, transported and
+ * window-searched on one layer), [1] hit-children updated, [2] hits whose
+ * chi2 was evaluated, [3] seeds, [4] hole-children (scattering only),
+ * [5..7] reserved (0). */
+int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream);
+
+/* Stage timing: with enable = 1, CUDA events are recorded around the
+ * binning, finding, duplicate removal and fit launches (also inside a
+ * captured graph).  kf_get_stage_ms (synchronous) returns the durations of
+ * the last completed run: ms4 = {bin, find, dedup, fit}. */
+int kf_set_stage_timing(kf_ctx* ctx, int enable);
+int kf_get_stage_ms(kf_ctx* ctx, float* ms4, void* stream);
+
+/* Number of kernel nodes in the captured graph (launches per replay). */
+int kf_graph_kernel_count(kf_ctx* ctx, int* n_kernels);
+
+/* Wait for the stream and report a sticky device-side error, if any. */
+int kf_sync(kf_ctx* ctx, void* stream);
+
+/* Message of the last error on this context (static storage, never NULL). */
+const char* kf_last_error(const kf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KF_H_ */

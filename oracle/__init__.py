@@ -65,6 +65,7 @@ def lib():
             L.orc_find_event.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                          ctypes.c_long, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
                                          _P, _P, _P, _P, _P, _P]
+            L.orc_replay.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
             L.orc_dedup.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, _P]
         return _lib
@@ -248,3 +249,35 @@ def dedup(hits, n_hits, chi2, frac=0.5, brute=False):
     lib().orc_dedup(n, _ptr(hits), _ptr(n_hits), _ptr(chi2), hits.shape[1] if n else 1,
                     float(frac), int(brute), _ptr(keep))
     return keep
+
+
+def replay_path(batch, e: int, seed: int, hits_row, align=None):
+    """Replay, in the oracle, the finding path that produced the hit list
+    `hits_row` (event-local indices, -1 padded) for event-local seed `seed`.
+    Returns (status, chi2 sum, n_found, per-layer chi2)."""
+    det = batch.det
+    L = det.n_layers
+    x, y, z, lay = batch.event_hits(e)
+    prm, cov, sh = batch.event_seeds(e)
+    x, y, z = _c(x, np.float64), _c(y, np.float64), _c(z, np.float64)
+    lay = _c(lay, np.int32)
+    hits = [h for h in hits_row if h >= 0]
+    dec = np.full(L, -2, np.int32)
+    last = int(lay[hits[2]])
+    for h in hits[3:]:
+        last = max(last, int(lay[h]))
+    for l in range(int(lay[hits[2]]) + 1, last + 1):
+        dec[l] = -1
+    for h in hits[3:]:
+        dec[int(lay[h])] = h
+    p0 = _c(prm[:, seed], np.float64)
+    c0 = _c(cov[:, seed], np.float64)
+    s3 = _c(sh[:, seed], np.int32)
+    al = _c(batch.align if align is None else align, np.float64)
+    chi2l = np.zeros(L)
+    tot = np.zeros(1)
+    nf = np.zeros(1, np.int32)
+    d = make_detector(det)
+    st = lib().orc_replay(ctypes.byref(d), _ptr(x), _ptr(y), _ptr(z), _ptr(lay), _ptr(p0), _ptr(c0),
+                          _ptr(s3), _ptr(dec), _ptr(al), _ptr(chi2l), _ptr(tot), _ptr(nf))
+    return int(st), float(tot[0]), int(nf[0]), chi2l

@@ -842,6 +842,58 @@ int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits,
   return 0;
 }
 
+// Replay one candidate path of the finding: seed fit over the three seed
+// hits (scattering after the last), then for each layer from the one after
+// the third seed hit: decisions[l] = hit index (update), -1 (hole) or -2
+// (stop).  Scattering follows every update and every hole, as in finding.
+// chi2_layer[l] receives each hit's chi2.  Returns 0, or -1 when the
+// propagation finds no crossing, -2 for a far-side hit.
+int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, const double* hz,
+               const int* hlayer, const double* p0v, const double* C0v, const int* sh,
+               const int* decisions, const double* align, double* chi2_layer, double* chi2sum,
+               int* n_found) {
+  const Det det = to_det(dptr);
+  const int L = det.n_layers;
+  double al[64][2];
+  for (int i = 0; i < L; ++i) { al[i][0] = align[2 * i]; al[i][1] = align[2 * i + 1]; }
+  double p0[6], C0[6][6], p[6], C[6][6], chi2;
+  for (int k = 0; k < 6; ++k) p0[k] = p0v[k];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) C0[a][b] = C0v[sym_index(a, b)];
+  double raw[3][3];
+  int lays[3];
+  for (int k = 0; k < 3; ++k) {
+    raw[k][0] = hx[sh[k]]; raw[k][1] = hy[sh[k]]; raw[k][2] = hz[sh[k]];
+    lays[k] = hlayer[sh[k]];
+  }
+  int st = fit_track<double>(det, p0, C0, 3, raw, lays, al, true, p, C, chi2);
+  *n_found = 3;
+  for (int l = 0; l < L; ++l) chi2_layer[l] = 0.0;
+  if (st != 0) { *chi2sum = chi2; return st; }
+  const double vr = det.sigma_rphi * det.sigma_rphi, vz = det.sigma_z * det.sigma_z;
+  for (int l = lays[2] + 1; l < L; ++l) {
+    if (decisions[l] == -2) break;
+    double q[6], J[6][6];
+    if (!propagate(det.bz, p, det.radius[l], q, J)) { *chi2sum = chi2; return -1; }
+    for (int i = 0; i < 6; ++i) p[i] = q[i];
+    transport(J, C);
+    if (decisions[l] >= 0) {
+      const int h = decisions[l];
+      double rw[3] = {hx[h], hy[h], hz[h]}, m[3];
+      correct_hit(rw, al[l][0], al[l][1], det.radius[l], m);
+      Meas<double> ms;
+      if (!measure(p, C, m, vr, vz, ms)) { *chi2sum = chi2; return -2; }
+      chi2_layer[l] = ms.chi2;
+      chi2 += ms.chi2;
+      kf_update(p, C, ms);
+      *n_found += 1;
+    }
+    add_ms(p, C, det.x0[l]);
+  }
+  *chi2sum = chi2;
+  return 0;
+}
+
 // Duplicate removal for one event's tracks: walk tracks by (more hits, lower
 // chi2, lower index); keep a track unless it shares more than frac*min(nA, nB)
 // hits with a track already kept.  hits [n][max_len] event-local indices.

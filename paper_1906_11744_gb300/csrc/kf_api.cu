@@ -1,0 +1,750 @@
+// C ABI (include/kf.h): context, device buffers, launches, CUDA graph and
+// autotuner.  The calls follow the paper's problem statement: load hits and
+// seeds (Sec. 3), find tracks (Sec. 2), remove duplicates (Sec. 4.2), fit
+// tracks (Sec. 5).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kf_internal.h"
+
+using namespace kfg;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct kf_ctx {
+  kf_detector det;
+  kf_config cfg;
+  DevGeom g;
+  int lanes = 0, threads = 0, persistent = 1, per_event = 0, regcap = 0;
+  int num_sms = 0;
+  int blocks_per_sm = 1;
+  int n_events = 0, n_hits = 0, n_seeds = 0, n_seed_events = -1;
+  std::vector<int> hit_off_h, seed_off_h, seed_event_h;
+  size_t n_bins_total = 0;
+  // inputs
+  DevBuf hx, hy, hz, hlayer, hit_off, seed_off, sp, sc, sh, seed_event, align_raw, align4, eta_edges;
+  // binning
+  DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp;
+  // finding
+  DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status;
+  // duplicate removal scratch
+  DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state;
+  // fit
+  DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status;
+  int given_max_len = 0;
+  bool found = false, deduped = false, fitted = false;
+  int fit_source = KF_FIT_FOUND;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int stage_timing = 0;
+  cudaEvent_t ev[8] = {};  // bin start/end, find start/end, dedup start/end, fit start/end
+  std::string err = "";
+};
+
+namespace {
+
+int fail(kf_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, KF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+cudaError_t grow(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+
+template <class T>
+T* ptr(const DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Copy n bytes into a device buffer from a host or device source.
+cudaError_t put(void* dst, const void* src, size_t n, int device_ptrs, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, n, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t get(void* dst, const void* src, size_t n, int device_ptrs, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, n, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+__global__ void k_align(const float* off, const DevGeom g, Align4* out) {
+  const int l = threadIdx.x;
+  if (l >= g.n_layers) return;
+  const float R = g.radius[l];
+  const float ar = off ? off[2 * l] : 0.f, az = off ? off[2 * l + 1] : 0.f;
+  float s, c;
+  sincosf(-ar / R, &s, &c);
+  out[l] = Align4{c, s, ar / R, az};
+}
+
+bool supported_lanes(int lanes) { return find_lanes_supported(lanes); }
+
+int auto_lanes(int n) {
+  const int opts[] = {4, 6, 8, 10, 12, 16};
+  for (int o : opts)
+    if (o >= n) return o;
+  return 16;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kf_last_error(const kf_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
+  kf_ctx* ctx = nullptr;
+  if (!det || !cfg || !out) return KF_ERR_ARG;
+  *out = nullptr;
+  if (det->n_layers < 1 || det->n_layers > KF_MAX_LAYERS) return KF_ERR_ARG;
+  for (int l = 0; l < det->n_layers; ++l) {
+    if (!(det->radius[l] > 0.f) || (l > 0 && !(det->radius[l] > det->radius[l - 1]))) return KF_ERR_ARG;
+    if (!(det->x0[l] >= 0.f)) return KF_ERR_ARG;
+  }
+  if (!(det->z_max > 0.f) || !(det->sigma_rphi > 0.f) || !(det->sigma_z > 0.f) || !std::isfinite(det->bz))
+    return KF_ERR_ARG;
+  if (cfg->max_cands < 1 || cfg->max_cands > KF_MAX_CANDS || cfg->max_holes < 0 || !(cfg->chi2_cut > 0.f) ||
+      !(cfg->dup_shared_frac >= 0.f) || cfg->n_eta_bins < 1 || cfg->n_eta_bins > MAX_ETA_BINS ||
+      cfg->n_phi_bins < 1 ||
+      (size_t)cfg->n_eta_bins * cfg->n_phi_bins > (1u << 24))
+    return KF_ERR_ARG;
+  int lanes = cfg->lanes_per_seed ? cfg->lanes_per_seed : auto_lanes(cfg->max_cands);
+  if (!supported_lanes(lanes) || lanes < cfg->max_cands) return KF_ERR_ARG;
+  int threads = cfg->block_threads ? cfg->block_threads : 128;
+  if (threads < 32 || threads > 256 || threads % 32) return KF_ERR_ARG;
+  ctx = new kf_ctx();
+  ctx->det = *det;
+  ctx->cfg = *cfg;
+  ctx->lanes = lanes;
+  ctx->threads = threads;
+  ctx->persistent = cfg->persistent ? 1 : 0;
+  ctx->per_event = cfg->per_event ? 1 : 0;
+  DevGeom& g = ctx->g;
+  std::memset(&g, 0, sizeof(g));
+  g.n_layers = det->n_layers;
+  g.max_cands = cfg->max_cands;
+  g.max_holes = cfg->max_holes;
+  g.n_eta = cfg->n_eta_bins;
+  g.n_phi = cfg->n_phi_bins;
+  g.z_max = det->z_max;
+  g.kb = -KCURV * det->bz;
+  g.vr = det->sigma_rphi * det->sigma_rphi;
+  g.vz = det->sigma_z * det->sigma_z;
+  g.chi2_cut = cfg->chi2_cut;
+  for (int l = 0; l < det->n_layers; ++l) {
+    g.radius[l] = det->radius[l];
+    g.x0[l] = det->x0[l];
+    g.eta_max[l] = asinhf(det->z_max / det->radius[l]);
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = find_prepare(ctx->lanes, ctx->regcap, ctx->threads, &ctx->blocks_per_sm);
+  if (e == cudaSuccess) e = grow(ctx->align4, sizeof(Align4) * KF_MAX_LAYERS);
+  if (e == cudaSuccess) {
+    // z edges of the eta bins per layer: edge_k = R sinh(-eta_max + k * 2 eta_max / n_eta)
+    std::vector<float> edges((size_t)KF_MAX_LAYERS * (MAX_ETA_BINS + 1), 0.f);
+    for (int l = 0; l < det->n_layers; ++l) {
+      const double R = det->radius[l], em = std::asinh((double)det->z_max / R);
+      for (int k = 0; k <= cfg->n_eta_bins; ++k)
+        edges[(size_t)l * (MAX_ETA_BINS + 1) + k] =
+            (float)(R * std::sinh(-em + 2.0 * em * k / cfg->n_eta_bins));
+    }
+    e = grow(ctx->eta_edges, sizeof(float) * edges.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ctx->eta_edges.p, edges.data(), sizeof(float) * edges.size(), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = grow(ctx->queue, 64);
+  if (e == cudaSuccess) e = grow(ctx->counters, 64);
+  if (e == cudaSuccess) e = grow(ctx->status, 64);
+  if (e == cudaSuccess) {
+    k_align<<<1, KF_MAX_LAYERS>>>(nullptr, g, ptr<Align4>(ctx->align4));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemset(ctx->status.p, 0, 64);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    kf_destroy(ctx);
+    return KF_ERR_CUDA;
+  }
+  if (ctx->blocks_per_sm < 1) ctx->blocks_per_sm = 1;
+  *out = ctx;
+  return KF_OK;
+}
+
+int kf_destroy(kf_ctx* ctx) {
+  if (!ctx) return KF_ERR_ARG;
+  for (cudaEvent_t& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  DevBuf* bufs[] = {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
+                    &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->hb,
+                    &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->out_hits,
+                    &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue,
+                    &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
+                    &ctx->dd_nconf, &ctx->dd_state, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
+                    &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status};
+  for (DevBuf* b : bufs) release(*b);
+  delete ctx;
+  return KF_OK;
+}
+
+int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* x, const float* y,
+                 const float* z, const int* layer, int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (n_events < 1 || !ev_offsets || !x || !y || !z || !layer)
+    return fail(ctx, KF_ERR_ARG, "kf_load_hits: null argument or n_events < 1");
+  if (ev_offsets[0] != 0) return fail(ctx, KF_ERR_ARG, "kf_load_hits: ev_offsets[0] must be 0");
+  for (int e = 0; e < n_events; ++e) {
+    const long long n = (long long)ev_offsets[e + 1] - ev_offsets[e];
+    if (n < 0) return fail(ctx, KF_ERR_ARG, "kf_load_hits: decreasing ev_offsets");
+    if (n > KF_MAX_EVENT_HITS) return fail(ctx, KF_ERR_CAPACITY, "kf_load_hits: event above KF_MAX_EVENT_HITS");
+  }
+  const int n = ev_offsets[n_events];
+  const size_t nb = (size_t)ctx->g.n_eta * ctx->g.n_phi;
+  const size_t n_bins = (size_t)n_events * ctx->g.n_layers * nb;
+  if (n_bins >= 0xFFFFFFFFull) return fail(ctx, KF_ERR_CAPACITY, "kf_load_hits: too many hit-grid cells");
+  if (!device_ptrs)
+    for (int i = 0; i < n; ++i)
+      if (layer[i] < 0 || layer[i] >= ctx->g.n_layers)
+        return fail(ctx, KF_ERR_ARG, "kf_load_hits: layer index out of range");
+  cudaStream_t st = S(stream);
+  CK(grow(ctx->hx, sizeof(float) * n));
+  CK(grow(ctx->hy, sizeof(float) * n));
+  CK(grow(ctx->hz, sizeof(float) * n));
+  CK(grow(ctx->hlayer, sizeof(int) * n));
+  CK(grow(ctx->hit_off, sizeof(int) * (n_events + 1)));
+  CK(grow(ctx->hb, sizeof(float4) * n));
+  CK(grow(ctx->bin_key, sizeof(unsigned) * n));
+  CK(grow(ctx->bin_rank, sizeof(unsigned) * n));
+  CK(grow(ctx->bin_cnt, sizeof(unsigned) * (n_bins + 1)));
+  CK(grow(ctx->scan_tmp, sizeof(unsigned) * scan_tmp_elems(n_bins)));
+  CK(grow(ctx->dd_hit_cnt, sizeof(unsigned) * ((size_t)n + n_events)));
+  CK(put(ctx->hx.p, x, sizeof(float) * n, device_ptrs, st));
+  CK(put(ctx->hy.p, y, sizeof(float) * n, device_ptrs, st));
+  CK(put(ctx->hz.p, z, sizeof(float) * n, device_ptrs, st));
+  CK(put(ctx->hlayer.p, layer, sizeof(int) * n, device_ptrs, st));
+  ctx->hit_off_h.assign(ev_offsets, ev_offsets + n_events + 1);
+  CK(cudaMemcpyAsync(ctx->hit_off.p, ctx->hit_off_h.data(), sizeof(int) * (n_events + 1),
+                     cudaMemcpyHostToDevice, st));
+  ctx->n_events = n_events;
+  ctx->n_hits = n;
+  ctx->n_bins_total = n_bins;
+  ctx->found = ctx->deduped = ctx->fitted = false;
+  if (!device_ptrs) CK(cudaStreamSynchronize(st));  // host staging vector stays valid until here
+  else CK(cudaStreamSynchronize(st));
+  return KF_OK;
+}
+
+int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* params, const float* cov,
+                  const int* seed_hits, int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (n_events < 1 || !ev_offsets || !params || !cov || !seed_hits)
+    return fail(ctx, KF_ERR_ARG, "kf_load_seeds: null argument");
+  if (n_events != ctx->n_events) return fail(ctx, KF_ERR_STATE, "kf_load_seeds: load hits of the same events first");
+  if (ev_offsets[0] != 0) return fail(ctx, KF_ERR_ARG, "kf_load_seeds: ev_offsets[0] must be 0");
+  std::vector<int> sev;
+  for (int e = 0; e < n_events; ++e) {
+    if (ev_offsets[e + 1] < ev_offsets[e]) return fail(ctx, KF_ERR_ARG, "kf_load_seeds: decreasing ev_offsets");
+    for (int s = ev_offsets[e]; s < ev_offsets[e + 1]; ++s) sev.push_back(e);
+  }
+  const int n = ev_offsets[n_events];
+  if (!device_ptrs) {
+    for (int s = 0; s < n; ++s) {
+      const int e = sev[s];
+      const int nh = ctx->hit_off_h[e + 1] - ctx->hit_off_h[e];
+      for (int k = 0; k < 3; ++k) {
+        const int h = seed_hits[(size_t)k * n + s];
+        if (h < 0 || h >= nh) return fail(ctx, KF_ERR_ARG, "kf_load_seeds: seed hit index out of range");
+      }
+    }
+  }
+  cudaStream_t st = S(stream);
+  const int L = ctx->g.n_layers;
+  CK(grow(ctx->sp, sizeof(float) * 6 * (size_t)n));
+  CK(grow(ctx->sc, sizeof(float) * 21 * (size_t)n));
+  CK(grow(ctx->sh, sizeof(int) * 3 * (size_t)n));
+  CK(grow(ctx->seed_event, sizeof(int) * (size_t)n));
+  CK(grow(ctx->seed_off, sizeof(int) * (n_events + 1)));
+  CK(grow(ctx->out_hits, sizeof(int) * (size_t)n * L));
+  CK(grow(ctx->out_n, sizeof(int) * (size_t)n));
+  CK(grow(ctx->out_chi2, sizeof(float) * (size_t)n));
+  CK(grow(ctx->out_p, sizeof(float) * 6 * (size_t)n));
+  CK(grow(ctx->out_C, sizeof(float) * 21 * (size_t)n));
+  CK(grow(ctx->keep, (size_t)n));
+  CK(grow(ctx->dd_owners, sizeof(int) * (size_t)n * L));
+  CK(grow(ctx->dd_conf, sizeof(int) * (size_t)n * DEDUP_CONF_CAP));
+  CK(grow(ctx->dd_nconf, sizeof(int) * (size_t)n));
+  CK(grow(ctx->dd_state, (size_t)n));
+  CK(grow(ctx->fit_p, sizeof(float) * 6 * (size_t)n));
+  CK(grow(ctx->fit_C, sizeof(float) * 21 * (size_t)n));
+  CK(grow(ctx->fit_chi2, sizeof(float) * (size_t)n));
+  CK(grow(ctx->fit_status, sizeof(int) * (size_t)n));
+  CK(put(ctx->sp.p, params, sizeof(float) * 6 * (size_t)n, device_ptrs, st));
+  CK(put(ctx->sc.p, cov, sizeof(float) * 21 * (size_t)n, device_ptrs, st));
+  CK(put(ctx->sh.p, seed_hits, sizeof(int) * 3 * (size_t)n, device_ptrs, st));
+  ctx->seed_off_h.assign(ev_offsets, ev_offsets + n_events + 1);
+  ctx->seed_event_h = sev;
+  CK(cudaMemcpyAsync(ctx->seed_off.p, ctx->seed_off_h.data(), sizeof(int) * (n_events + 1),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->seed_event.p, sev.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(ctx->keep.p, 1, (size_t)n, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->n_seeds = n;
+  ctx->n_seed_events = n_events;
+  ctx->found = ctx->deduped = ctx->fitted = false;
+  return KF_OK;
+}
+
+int kf_set_alignment(kf_ctx* ctx, const float* offsets, int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  cudaStream_t st = S(stream);
+  const int L = ctx->g.n_layers;
+  CK(grow(ctx->align_raw, sizeof(float) * 2 * KF_MAX_LAYERS));
+  if (offsets) CK(put(ctx->align_raw.p, offsets, sizeof(float) * 2 * L, device_ptrs, st));
+  k_align<<<1, KF_MAX_LAYERS, 0, st>>>(offsets ? ptr<float>(ctx->align_raw) : nullptr, ctx->g,
+                                       ptr<Align4>(ctx->align4));
+  CK(cudaGetLastError());
+  if (!device_ptrs) CK(cudaStreamSynchronize(st));
+  return KF_OK;
+}
+
+static void stage_mark(kf_ctx* ctx, int i, cudaStream_t st) {
+  // External record: inside stream capture this becomes an event-record node.
+  if (ctx->stage_timing && ctx->ev[i]) cudaEventRecordWithFlags(ctx->ev[i], st, cudaEventRecordExternal);
+}
+
+static FindParams find_params(kf_ctx* ctx) {
+  FindParams P;
+  P.g = ctx->g;
+  P.hx = ptr<float>(ctx->hx);
+  P.hy = ptr<float>(ctx->hy);
+  P.hz = ptr<float>(ctx->hz);
+  P.hlayer = ptr<int>(ctx->hlayer);
+  P.hit_off = ptr<int>(ctx->hit_off);
+  P.hb = ptr<float4>(ctx->hb);
+  P.bin_off = ptr<unsigned>(ctx->bin_cnt);
+  P.eta_edges = ptr<float>(ctx->eta_edges);
+  P.sp = ptr<float>(ctx->sp);
+  P.sc = ptr<float>(ctx->sc);
+  P.sh = ptr<int>(ctx->sh);
+  P.seed_event = ptr<int>(ctx->seed_event);
+  P.align = ptr<Align4>(ctx->align4);
+  P.ns = ctx->n_seeds;
+  P.s_begin = 0;
+  P.s_end = ctx->n_seeds;
+  P.out_hits = ptr<int>(ctx->out_hits);
+  P.out_n = ptr<int>(ctx->out_n);
+  P.out_chi2 = ptr<float>(ctx->out_chi2);
+  P.out_p = ptr<float>(ctx->out_p);
+  P.out_C = ptr<float>(ctx->out_C);
+  P.queue = ptr<unsigned>(ctx->queue);
+  P.counters = ptr<unsigned long long>(ctx->counters);
+  P.persistent = ctx->persistent;
+  return P;
+}
+
+static BinParams bin_params(kf_ctx* ctx) {
+  BinParams B;
+  B.g = ctx->g;
+  B.hx = ptr<float>(ctx->hx);
+  B.hy = ptr<float>(ctx->hy);
+  B.hz = ptr<float>(ctx->hz);
+  B.hlayer = ptr<int>(ctx->hlayer);
+  B.hit_off = ptr<int>(ctx->hit_off);
+  B.n_events = ctx->n_events;
+  B.h_begin = 0;
+  B.h_end = ctx->n_hits;
+  B.cnt = ptr<unsigned>(ctx->bin_cnt);
+  B.key = ptr<unsigned>(ctx->bin_key);
+  B.rank = ptr<unsigned>(ctx->bin_rank);
+  B.hb = ptr<float4>(ctx->hb);
+  B.eta_edges = ptr<float>(ctx->eta_edges);
+  return B;
+}
+
+int kf_find_tracks(kf_ctx* ctx, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (ctx->n_hits < 0 || ctx->n_seed_events != ctx->n_events || ctx->n_events < 1)
+    return fail(ctx, KF_ERR_STATE, "kf_find_tracks: load hits and seeds first");
+  cudaStream_t st = S(stream);
+  const size_t cells = (size_t)ctx->g.n_layers * ctx->g.n_eta * ctx->g.n_phi;
+  CK(cudaMemsetAsync(ctx->counters.p, 0, 64, st));
+  CK(cudaMemsetAsync(ctx->keep.p, 1, (size_t)ctx->n_seeds, st));
+  const int grid_cap = ctx->num_sms * ctx->blocks_per_sm;
+  if (!ctx->per_event) {
+    BinParams B = bin_params(ctx);
+    stage_mark(ctx, 0, st);
+    CK(launch_bin(B, 0, ctx->n_bins_total, 0u, ptr<unsigned>(ctx->scan_tmp),
+                  ctx->scan_tmp.bytes / sizeof(unsigned), st));
+    stage_mark(ctx, 1, st);
+    FindParams P = find_params(ctx);
+    if (P.persistent) CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
+    stage_mark(ctx, 2, st);
+    CK(launch_find(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
+    stage_mark(ctx, 3, st);
+  } else {
+    for (int e = 0; e < ctx->n_events; ++e) {
+      BinParams B = bin_params(ctx);
+      B.h_begin = ctx->hit_off_h[e];
+      B.h_end = ctx->hit_off_h[e + 1];
+      CK(launch_bin(B, (size_t)e * cells, cells, (unsigned)ctx->hit_off_h[e], ptr<unsigned>(ctx->scan_tmp),
+                    ctx->scan_tmp.bytes / sizeof(unsigned), st));
+      FindParams P = find_params(ctx);
+      P.s_begin = ctx->seed_off_h[e];
+      P.s_end = ctx->seed_off_h[e + 1];
+      if (P.persistent) CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
+      CK(launch_find(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
+    }
+  }
+  ctx->found = true;
+  ctx->deduped = false;
+  return KF_OK;
+}
+
+int kf_remove_duplicates(kf_ctx* ctx, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_remove_duplicates: run kf_find_tracks first");
+  cudaStream_t st = S(stream);
+  DedupParams D;
+  D.out_hits = ptr<int>(ctx->out_hits);
+  D.out_n = ptr<int>(ctx->out_n);
+  D.out_chi2 = ptr<float>(ctx->out_chi2);
+  D.hit_off = ptr<int>(ctx->hit_off);
+  D.seed_off = ptr<int>(ctx->seed_off);
+  D.L = ctx->g.n_layers;
+  D.ns = ctx->n_seeds;
+  D.frac = ctx->cfg.dup_shared_frac;
+  D.e_begin = 0;
+  D.hit_cnt = ptr<unsigned>(ctx->dd_hit_cnt);
+  D.owners = ptr<int>(ctx->dd_owners);
+  D.conf = ptr<int>(ctx->dd_conf);
+  D.n_conf = ptr<int>(ctx->dd_nconf);
+  D.state = ptr<unsigned char>(ctx->dd_state);
+  D.keep = ptr<unsigned char>(ctx->keep);
+  D.status = ptr<int>(ctx->status);
+  if (!ctx->per_event) {
+    stage_mark(ctx, 4, st);
+    CK(launch_dedup(D, ctx->n_events, st));
+    stage_mark(ctx, 5, st);
+  } else {
+    for (int e = 0; e < ctx->n_events; ++e) {
+      D.e_begin = e;
+      CK(launch_dedup(D, 1, st));
+    }
+  }
+  ctx->deduped = true;
+  return KF_OK;
+}
+
+int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hits, int max_len,
+                  int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (ctx->n_seeds < 0 || ctx->n_seed_events != ctx->n_events)
+    return fail(ctx, KF_ERR_STATE, "kf_fit_tracks: load hits and seeds first");
+  cudaStream_t st = S(stream);
+  FitParams F;
+  F.g = ctx->g;
+  F.hx = ptr<float>(ctx->hx);
+  F.hy = ptr<float>(ctx->hy);
+  F.hz = ptr<float>(ctx->hz);
+  F.hlayer = ptr<int>(ctx->hlayer);
+  F.hit_off = ptr<int>(ctx->hit_off);
+  F.sp = ptr<float>(ctx->sp);
+  F.sc = ptr<float>(ctx->sc);
+  F.seed_event = ptr<int>(ctx->seed_event);
+  F.align = ptr<Align4>(ctx->align4);
+  F.ns = ctx->n_seeds;
+  F.fit_p = ptr<float>(ctx->fit_p);
+  F.fit_C = ptr<float>(ctx->fit_C);
+  F.fit_chi2 = ptr<float>(ctx->fit_chi2);
+  F.fit_status = ptr<int>(ctx->fit_status);
+  if (source == KF_FIT_FOUND) {
+    if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_fit_tracks: no found tracks");
+    F.lists = ptr<int>(ctx->out_hits);
+    F.n_list = ptr<int>(ctx->out_n);
+    F.max_len = ctx->g.n_layers;
+    F.keep = ctx->deduped ? ptr<unsigned char>(ctx->keep) : nullptr;
+  } else if (source == KF_FIT_GIVEN) {
+    if (!hit_lists || !n_hits || max_len < 1) return fail(ctx, KF_ERR_ARG, "kf_fit_tracks: missing hit lists");
+    const size_t n = (size_t)ctx->n_seeds;
+    if (!device_ptrs) {
+      for (size_t s = 0; s < n; ++s) {
+        if (n_hits[s] < 1 || n_hits[s] > max_len) return fail(ctx, KF_ERR_ARG, "kf_fit_tracks: bad hit count");
+        const int e = ctx->seed_event_h[s];
+        const int nh = ctx->hit_off_h[e + 1] - ctx->hit_off_h[e];
+        for (int k = 0; k < n_hits[s]; ++k) {
+          const int h = hit_lists[s * max_len + k];
+          if (h < 0 || h >= nh) return fail(ctx, KF_ERR_ARG, "kf_fit_tracks: hit index out of range");
+        }
+      }
+    }
+    CK(grow(ctx->given_lists, sizeof(int) * n * max_len));
+    CK(grow(ctx->given_n, sizeof(int) * n));
+    CK(put(ctx->given_lists.p, hit_lists, sizeof(int) * n * max_len, device_ptrs, st));
+    CK(put(ctx->given_n.p, n_hits, sizeof(int) * n, device_ptrs, st));
+    F.lists = ptr<int>(ctx->given_lists);
+    F.n_list = ptr<int>(ctx->given_n);
+    F.max_len = max_len;
+    F.keep = nullptr;
+    ctx->given_max_len = max_len;
+    if (!device_ptrs) CK(cudaStreamSynchronize(st));
+  } else {
+    return fail(ctx, KF_ERR_ARG, "kf_fit_tracks: unknown source");
+  }
+  stage_mark(ctx, 6, st);
+  CK(launch_fit(F, st));
+  stage_mark(ctx, 7, st);
+  ctx->fitted = true;
+  ctx->fit_source = source;
+  return KF_OK;
+}
+
+int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs, void* stream) {
+  (void)g_align; (void)g_hits; (void)g_seed; (void)device_ptrs; (void)stream;
+  if (!ctx) return KF_ERR_ARG;
+  return fail(ctx, KF_ERR_STATE, "kf_fit_adjoint: not available in this build");
+}
+
+static int check_status(kf_ctx* ctx, cudaStream_t st) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h == ST_OK) return KF_OK;
+  CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  switch (h) {
+    case ST_DEDUP_PARTNERS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: partner table overflow");
+    case ST_DEDUP_CONFLICTS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: conflict table overflow");
+    case ST_DEDUP_ROUNDS: return fail(ctx, KF_ERR_TIMEOUT, "duplicate removal: resolution did not settle");
+    default: return fail(ctx, KF_ERR_CUDA, "unknown device status");
+  }
+}
+
+int kf_sync(kf_ctx* ctx, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  cudaStream_t st = S(stream);
+  CK(cudaStreamSynchronize(st));
+  return check_status(ctx, st);
+}
+
+int kf_get_tracks(kf_ctx* ctx, int* hits, int* n_found, float* chi2, float* params, float* cov,
+                  unsigned char* keep, int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_get_tracks: run kf_find_tracks first");
+  cudaStream_t st = S(stream);
+  const size_t n = (size_t)ctx->n_seeds, L = (size_t)ctx->g.n_layers;
+  if (hits) CK(get(hits, ctx->out_hits.p, sizeof(int) * n * L, device_ptrs, st));
+  if (n_found) CK(get(n_found, ctx->out_n.p, sizeof(int) * n, device_ptrs, st));
+  if (chi2) CK(get(chi2, ctx->out_chi2.p, sizeof(float) * n, device_ptrs, st));
+  if (params) CK(get(params, ctx->out_p.p, sizeof(float) * 6 * n, device_ptrs, st));
+  if (cov) CK(get(cov, ctx->out_C.p, sizeof(float) * 21 * n, device_ptrs, st));
+  if (keep) CK(get(keep, ctx->keep.p, n, device_ptrs, st));
+  if (!device_ptrs) return check_status(ctx, st);
+  return KF_OK;
+}
+
+int kf_get_fit(kf_ctx* ctx, float* params, float* cov, float* chi2, int* status, int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (!ctx->fitted) return fail(ctx, KF_ERR_STATE, "kf_get_fit: run kf_fit_tracks first");
+  cudaStream_t st = S(stream);
+  const size_t n = (size_t)ctx->n_seeds;
+  if (params) CK(get(params, ctx->fit_p.p, sizeof(float) * 6 * n, device_ptrs, st));
+  if (cov) CK(get(cov, ctx->fit_C.p, sizeof(float) * 21 * n, device_ptrs, st));
+  if (chi2) CK(get(chi2, ctx->fit_chi2.p, sizeof(float) * n, device_ptrs, st));
+  if (status) CK(get(status, ctx->fit_status.p, sizeof(int) * n, device_ptrs, st));
+  if (!device_ptrs) return check_status(ctx, st);
+  return KF_OK;
+}
+
+int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream) {
+  if (!ctx || !counters8) return KF_ERR_ARG;
+  cudaStream_t st = S(stream);
+  CK(cudaMemcpyAsync(counters8, ctx->counters.p, 8 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return KF_OK;
+}
+
+int kf_set_stage_timing(kf_ctx* ctx, int enable) {
+  if (!ctx) return KF_ERR_ARG;
+  if (enable)
+    for (cudaEvent_t& e : ctx->ev)
+      if (!e) CK(cudaEventCreate(&e));
+  ctx->stage_timing = enable ? 1 : 0;
+  return KF_OK;
+}
+
+int kf_get_stage_ms(kf_ctx* ctx, float* ms4, void* stream) {
+  if (!ctx || !ms4) return KF_ERR_ARG;
+  if (!ctx->stage_timing) return fail(ctx, KF_ERR_STATE, "kf_get_stage_ms: stage timing is off");
+  CK(cudaStreamSynchronize(S(stream)));
+  for (int k = 0; k < 4; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) != cudaSuccess) ms = -1.f;
+    ms4[k] = ms;
+  }
+  cudaGetLastError();  // an event that never ran leaves a benign error
+  return KF_OK;
+}
+
+int kf_graph_kernel_count(kf_ctx* ctx, int* n_kernels) {
+  if (!ctx || !n_kernels) return KF_ERR_ARG;
+  if (!ctx->graph) return fail(ctx, KF_ERR_STATE, "kf_graph_kernel_count: capture a graph first");
+  size_t n = 0;
+  CK(cudaGraphGetNodes(ctx->graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(ctx->graph, nodes.data(), &n));
+  int k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *n_kernels = k;
+  return KF_OK;
+}
+
+int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (with_adjoint) return fail(ctx, KF_ERR_STATE, "kf_capture_graph: adjoint not available in this build");
+  cudaStream_t st = S(stream);
+  if (!st) return fail(ctx, KF_ERR_ARG, "kf_capture_graph: capture needs a non-default stream");
+  if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = kf_find_tracks(ctx, stream);
+  if (rc == KF_OK) rc = kf_remove_duplicates(ctx, stream);
+  if (rc == KF_OK) rc = kf_fit_tracks(ctx, KF_FIT_FOUND, nullptr, nullptr, 0, 1, stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc != KF_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ctx, KF_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  ctx->graph = graph;
+  CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, 0));
+  return KF_OK;
+}
+
+int kf_launch_graph(kf_ctx* ctx, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (!ctx->exec) return fail(ctx, KF_ERR_STATE, "kf_launch_graph: capture a graph first");
+  CK(cudaGraphLaunch(ctx->exec, S(stream)));
+  ctx->found = ctx->deduped = ctx->fitted = true;
+  ctx->fit_source = KF_FIT_FOUND;
+  return KF_OK;
+}
+
+int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (ctx->n_seed_events != ctx->n_events || ctx->n_events < 1)
+    return fail(ctx, KF_ERR_STATE, "kf_autotune: load hits and seeds first");
+  cudaStream_t st = S(stream);
+  const int lane_opts[] = {4, 6, 8, 10, 12, 16};
+  const int thread_opts[] = {64, 128, 256};
+  const int saved_lanes = ctx->lanes, saved_threads = ctx->threads, saved_pers = ctx->persistent,
+            saved_bps = ctx->blocks_per_sm, saved_rc = ctx->regcap;
+  float best = 1e30f;
+  int best_l = saved_lanes, best_t = saved_threads, best_p = saved_pers, best_b = saved_bps,
+      best_rc = saved_rc;
+  int nr = 0;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  int rc = KF_OK;
+  for (int lanes : lane_opts) {
+    if (lanes < ctx->cfg.max_cands) continue;
+    for (int threads : thread_opts)
+    for (int regcap = 0; regcap < 2; ++regcap) {
+      int bps = 1;
+      if (find_prepare(lanes, regcap, threads, &bps) != cudaSuccess || bps < 1) continue;
+      for (int pers = 0; pers < 2 && rc == KF_OK; ++pers) {
+        ctx->lanes = lanes;
+        ctx->threads = threads;
+        ctx->persistent = pers;
+        ctx->blocks_per_sm = bps;
+        ctx->regcap = regcap;
+        rc = kf_find_tracks(ctx, stream);  // warm-up
+        if (rc != KF_OK) break;
+        float tot = 0.f;
+        for (int rep = 0; rep < 3 && rc == KF_OK; ++rep) {
+          cudaEventRecord(a, st);
+          rc = kf_find_tracks(ctx, stream);
+          cudaEventRecord(b, st);
+          cudaEventSynchronize(b);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, b);
+          tot += ms;
+        }
+        const float ms = tot / 3.f;
+        if (results && nr < max_results) {
+          results[5 * nr + 0] = (float)lanes;
+          results[5 * nr + 1] = (float)threads;
+          results[5 * nr + 2] = (float)pers;
+          results[5 * nr + 3] = (float)regcap;
+          results[5 * nr + 4] = ms;
+        }
+        ++nr;
+        if (ms < best) {
+          best = ms;
+          best_l = lanes;
+          best_t = threads;
+          best_p = pers;
+          best_b = bps;
+          best_rc = regcap;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ctx->lanes = best_l;
+  ctx->threads = best_t;
+  ctx->persistent = best_p;
+  ctx->blocks_per_sm = best_b;
+  ctx->regcap = best_rc;
+  CK(find_prepare(best_l, best_rc, best_t, &ctx->blocks_per_sm));
+  if (n_results) *n_results = nr;
+  if (rc != KF_OK) return rc;
+  return KF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,438 @@
+// Device-side Kalman-filter arithmetic shared by the finding, fitting and
+// adjoint kernels (registers only; templated on the scalar type so that the
+// fit can redo an ill-conditioned step in double precision).
+//
+// Track state p = (x, y, z, q/pT, phi, theta); covariance C as the 21-float
+// upper triangle.  The method follows the paper's Kalman-filter building and
+// fitting (Sec. 2) with the largest matrices being the symmetric 6x6
+// covariance (Sec. 2, Matriplex paragraph): every product below skips the
+// structural zeros and ones of the propagation Jacobian, the GPU counterpart of
+// the paper's known-element elimination.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kf.h"
+
+namespace kfg {
+
+constexpr float KCURV = 0.00299792458f;  // 1/rho [1/cm] = KCURV * B[T] / pT[GeV]
+constexpr double MPION = 0.13957;
+constexpr float PI_F = 3.14159265358979323846f;
+constexpr float TWO_PI_F = 6.28318530717958647692f;
+constexpr int MAX_ETA_BINS = 256;
+
+// Geometry and settings, passed by value as a kernel parameter.
+struct DevGeom {
+  int n_layers;
+  int max_cands;
+  int max_holes;
+  int n_eta;
+  int n_phi;
+  float z_max;
+  float kb;  // -KCURV * bz: signed curvature h = kb * (q/pT)
+  float vr;  // sigma_rphi^2
+  float vz;  // sigma_z^2
+  float chi2_cut;
+  float radius[KF_MAX_LAYERS];
+  float x0[KF_MAX_LAYERS];
+  float eta_max[KF_MAX_LAYERS];  // asinh(z_max / R): half-range of the eta grid
+};
+
+// Per-layer alignment: (cos a, sin a) of the correction rotation a = -a_rphi/R,
+// the raw-angle offset a_rphi/R and a_z.
+struct Align4 {
+  float ca, sa, dphi, az;
+};
+
+__host__ __device__ constexpr int S6(int i, int j) {
+  return i <= j ? i * 6 - i * (i - 1) / 2 + (j - i) : j * 6 - j * (j - 1) / 2 + (i - j);
+}
+
+// Structure of the propagation Jacobian: 0 = structural zero, 1 = one, 2 = value.
+// Rows q/pT and theta are identity; x', y', phi' depend on (x, y, q/pT, phi);
+// z' depends on all six with dz'/dz = 1.
+__host__ __device__ constexpr int JS(int i, int j) {
+  return (i == 3) ? (j == 3 ? 1 : 0)
+         : (i == 5) ? (j == 5 ? 1 : 0)
+         : (i == 2) ? (j == 2 ? 1 : 2)
+         : ((j == 2 || j == 5) ? 0 : 2);
+}
+__host__ __device__ constexpr int JNNZ(int i) {
+  return (i == 3 || i == 5) ? 1 : (i == 2 ? 6 : 4);
+}
+
+// Scalar-generic math (float -> single-precision intrinsics, double -> double).
+__device__ __forceinline__ float kfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double kfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ void ksincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void ksincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float ksqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double ksqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float krsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double krsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float katan(float x) { return atanf(x); }
+__device__ __forceinline__ double katan(double x) { return atan(x); }
+__device__ __forceinline__ float ksin(float x) { return sinf(x); }
+__device__ __forceinline__ double ksin(double x) { return sin(x); }
+__device__ __forceinline__ float klog(float x) { return logf(x); }
+__device__ __forceinline__ double klog(double x) { return log(x); }
+__device__ __forceinline__ float kabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double kabs(double x) { return fabs(x); }
+__device__ __forceinline__ float kmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double kmin(double a, double b) { return fmin(a, b); }
+
+// sinc(psi) = sin(psi)/psi, cosc(psi) = (1 - cos psi)/psi,
+// f1 = (psi cos psi - sin psi)/psi^2, f2 = (psi sin psi - 1 + cos psi)/psi^2.
+// Power series (derived from the Taylor series of sin and cos) below |psi| =
+// 0.5, which covers every layer-to-layer step above pT = 0.5 GeV; direct forms
+// without cancellation above.
+template <class T>
+__device__ __forceinline__ void helix_fns(T psi, T& sc, T& cc, T& f1, T& f2) {
+  if (kabs(psi) < T(0.5)) {
+    const T q = psi * psi;
+    sc = kfma(q, kfma(q, kfma(q, kfma(q, T(1.0 / 362880.0), T(-1.0 / 5040.0)), T(1.0 / 120.0)), T(-1.0 / 6.0)), T(1));
+    cc = psi * kfma(q, kfma(q, kfma(q, kfma(q, T(1.0 / 3628800.0), T(-1.0 / 40320.0)), T(1.0 / 720.0)),
+                            T(-1.0 / 24.0)), T(0.5));
+    f1 = psi * kfma(q, kfma(q, kfma(q, kfma(q, T(-1.0 / 3991680.0), T(1.0 / 45360.0)), T(-1.0 / 840.0)),
+                            T(1.0 / 30.0)), T(-1.0 / 3.0));
+    f2 = kfma(q, kfma(q, kfma(q, kfma(q, T(1.0 / 403200.0), T(-1.0 / 5760.0)), T(1.0 / 144.0)), T(-1.0 / 8.0)),
+              T(0.5));
+    if (sizeof(T) == 8) {  // double: extend each series by its next term
+      const T q5 = q * q * q * q * q;
+      sc += q5 * T(-1.0 / 39916800.0);
+      cc += psi * q5 * T(-1.0 / 479001600.0);
+      f1 += psi * q5 * T(12.0 / 6227020800.0);
+      f2 += q5 * T(-11.0 / 479001600.0);
+    }
+  } else {
+    T sn, cs;
+    ksincos(psi, &sn, &cs);
+    const T hs = ksin(T(0.5) * psi);
+    const T ip = T(1) / psi;
+    sc = sn * ip;
+    cc = T(2) * hs * hs * ip;
+    f1 = (cs - sc) * ip;
+    f2 = (sn - cc) * ip;
+  }
+}
+
+// Smallest s > 0 (transverse arc length) with x(s)^2 + y(s)^2 = R^2.
+// psi = h s solves A sin psi + B (1 - cos psi) = E with A = b h, B = a h + 1,
+// E = h^2 (R^2 - r0^2)/2; tau = tan(psi/2) solves (2B - E) tau^2 + 2A tau - E = 0,
+// each root taken in its cancellation-free form.
+template <class T>
+__device__ __forceinline__ bool path_length(T x, T y, T h, T cf, T sf, T R, T& s) {
+  const T b = kfma(x, cf, y * sf);
+  const T a = kfma(y, cf, -x * sf);
+  const T r0 = ksqrt(kfma(x, x, y * y));
+  const T dR2 = (R - r0) * (R + r0);
+  if (h == T(0)) {
+    const T disc = kfma(b, b, dR2);
+    if (disc < T(0)) return false;
+    const T sq = ksqrt(disc);
+    T lo, hi;
+    if (b > T(0)) {
+      lo = -(b + sq);
+      hi = dR2 / (b + sq);
+    } else {
+      hi = sq - b;
+      lo = (hi == T(0)) ? T(0) : -dR2 / hi;
+    }
+    if (lo > T(0)) { s = lo; return true; }
+    if (hi > T(0)) { s = hi; return true; }
+    return false;
+  }
+  const T A = b * h;
+  const T B = kfma(a, h, T(1));
+  const T E = T(0.5) * h * h * dR2;
+  const T den = T(2) * B - E;
+  const T D = kfma(A, A, E * den);
+  if (D < T(0)) return false;
+  const T sq = ksqrt(D);
+  T n0, d0, n1, d1;
+  if (A >= T(0)) {
+    n0 = E; d0 = A + sq; n1 = -(A + sq); d1 = den;
+  } else {
+    n0 = sq - A; d0 = den; n1 = E; d1 = A - sq;
+  }
+  const T turn = T(2.0 * 3.14159265358979323846) / kabs(h);
+  const T ih = T(1) / h;
+  T best = T(INFINITY);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T nn = k ? n1 : n0, dd = k ? d1 : d0;
+    T psi;
+    if (dd == T(0)) {
+      if (nn == T(0)) continue;
+      psi = T(3.14159265358979323846);
+    } else {
+      psi = T(2) * katan(nn / dd);
+    }
+    T sk = psi * ih;
+    if (sk <= T(0)) sk += turn;
+    best = kmin(best, sk);
+  }
+  if (!(best < T(INFINITY))) return false;
+  s = best;
+  return true;
+}
+
+// C <- J C J^T using only the structural non-zeros of J (JS).  J entries with
+// JS == 2 must be set; others are ignored.
+template <class T>
+__device__ __forceinline__ void transport(const T (&J)[6][6], T (&C)[21]) {
+  T Tm[6][6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      T acc = T(0);
+      bool first = true;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (JS(i, j) == 0) continue;
+        const T c = C[S6(j, k)];
+        if (JS(i, j) == 1) acc = first ? c : acc + c;
+        else acc = first ? J[i][j] * c : kfma(J[i][j], c, acc);
+        first = false;
+      }
+      Tm[i][k] = acc;
+    }
+  }
+  T out[21];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int j = i; j < 6; ++j) {
+      // (T J^T)_ij = T_i . J_j = T_j . J_i (symmetry): take the sparser J row.
+      const bool use_j = JNNZ(j) <= JNNZ(i);
+      const int tr = use_j ? i : j, jr = use_j ? j : i;
+      T acc = T(0);
+      bool first = true;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        if (JS(jr, k) == 0) continue;
+        const T t = Tm[tr][k];
+        if (JS(jr, k) == 1) acc = first ? t : acc + t;
+        else acc = first ? t * J[jr][k] : kfma(t, J[jr][k], acc);
+        first = false;
+      }
+      out[S6(i, j)] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = out[k];
+}
+
+// Path length and crossing geometry only: returns false without a crossing;
+// z_out is z at the crossing and cos_out = |cos| of the angle between the
+// direction and the radial direction there (1 = radial, 0 = tangent).
+__device__ __forceinline__ bool crossing(const float (&p)[6], float R, float kb, float& z_out,
+                                         float& cos_out) {
+  float sf, cf;
+  sincosf(p[4], &sf, &cf);
+  const float h = kb * p[3];
+  float s;
+  if (!path_length<float>(p[0], p[1], h, cf, sf, R, s)) return false;
+  float sth, cth;
+  sincosf(p[5], &sth, &cth);
+  z_out = fmaf(s, cth / sth, p[2]);
+  const float psi = h * s;
+  float sc, cc, f1, f2;
+  helix_fns<float>(psi, sc, cc, f1, f2);
+  const float Sx = s * sc, Cx = s * cc;
+  const float xn = p[0] + fmaf(cf, Sx, -sf * Cx);
+  const float yn = p[1] + fmaf(sf, Sx, cf * Cx);
+  const float cpsi = fmaf(-psi, cc, 1.f), spsi = psi * sc;
+  const float cp = fmaf(cf, cpsi, -sf * spsi), sp = fmaf(sf, cpsi, cf * spsi);
+  cos_out = fabsf(fmaf(xn, cp, yn * sp)) * rsqrtf(fmaf(xn, xn, yn * yn));
+  return true;
+}
+
+// Propagation to the cylinder of radius R (closed-form helix, exact
+// Jacobian, covariance transport).  Returns 1 on success (p, C updated),
+// 0 without a crossing, 2 when |z| at the crossing exceeds z_lim; p and C are
+// untouched unless 1 is returned.  cos_out (optional) receives |cos| of the
+// angle between the direction and the radial direction at the crossing.
+template <class T>
+__device__ __forceinline__ int propagate(T (&p)[6], T (&C)[21], T R, T kb, T z_lim, T* cos_out = nullptr) {
+  const T x = p[0], y = p[1], kap = p[3], phi = p[4], th = p[5];
+  T sf, cf;
+  ksincos(phi, &sf, &cf);
+  const T h = kb * kap;
+  T s;
+  if (!path_length<T>(x, y, h, cf, sf, R, s)) return 0;
+  T sth, cth;
+  ksincos(th, &sth, &cth);
+  const T cot = cth / sth;
+  const T zn = kfma(s, cot, p[2]);
+  if (kabs(zn) > z_lim) return 2;
+  const T psi = h * s;
+  T sc, cc, f1, f2;
+  helix_fns<T>(psi, sc, cc, f1, f2);
+  const T Sx = s * sc, Cx = s * cc;
+  const T dx = kfma(cf, Sx, -sf * Cx);
+  const T dy = kfma(sf, Sx, cf * Cx);
+  const T xn = x + dx, yn = y + dy;
+  // direction at the crossing: cos psi = 1 - psi*cc, sin psi = psi*sc
+  const T cpsi = kfma(-psi, cc, T(1)), spsi = psi * sc;
+  const T cp = kfma(cf, cpsi, -sf * spsi);
+  const T sp = kfma(sf, cpsi, cf * spsi);
+  const T s2 = s * s;
+  const T dSdh = s2 * f1, dCdh = s2 * f2;
+  const T Fx3 = kb * kfma(cf, dSdh, -sf * dCdh);
+  const T Fy3 = kb * kfma(sf, dSdh, cf * dCdh);
+  const T Fx4 = -dy, Fy4 = dx;
+  const T dgds = kfma(xn, cp, yn * sp);
+  if (cos_out) *cos_out = kabs(dgds) / R;
+  const T inv = T(-1) / dgds;
+  const T ds0 = xn * inv, ds1 = yn * inv;
+  const T ds3 = kfma(xn, Fx3, yn * Fy3) * inv;
+  const T ds4 = kfma(xn, Fx4, yn * Fy4) * inv;
+  T J[6][6];
+  J[0][0] = kfma(cp, ds0, T(1)); J[0][1] = cp * ds1; J[0][3] = kfma(cp, ds3, Fx3); J[0][4] = kfma(cp, ds4, Fx4);
+  J[1][0] = sp * ds0; J[1][1] = kfma(sp, ds1, T(1)); J[1][3] = kfma(sp, ds3, Fy3); J[1][4] = kfma(sp, ds4, Fy4);
+  J[2][0] = cot * ds0; J[2][1] = cot * ds1; J[2][3] = cot * ds3; J[2][4] = cot * ds4;
+  J[2][5] = -s / (sth * sth);
+  J[4][0] = h * ds0; J[4][1] = h * ds1; J[4][3] = kfma(h, ds3, kb * s); J[4][4] = kfma(h, ds4, T(1));
+  transport<T>(J, C);
+  p[0] = xn;
+  p[1] = yn;
+  p[2] = zn;
+  p[4] = phi + psi;
+  return 1;
+}
+
+// Tangent-frame measurement at the prediction: u = (-sin phi_p, cos phi_p)
+// with (cos, sin) phi_p = (x, y)/r; a0 = C H0^T, S = H C H^T + V, S^-1.
+template <class T>
+struct FrameT {
+  T su, cu;
+  T a0[6];
+  T s00, s11;
+  T si00, si01, si11;
+};
+using Frame = FrameT<float>;
+
+template <class T>
+__device__ __forceinline__ void make_frame(const T (&p)[6], const T (&C)[21], T vr, T vz, FrameT<T>& f) {
+  const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
+  f.cu = p[0] * ir;
+  f.su = p[1] * ir;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) f.a0[i] = kfma(-f.su, C[S6(i, 0)], f.cu * C[S6(i, 1)]);
+  const T s00 = kfma(-f.su, f.a0[0], kfma(f.cu, f.a0[1], vr));
+  const T s01 = f.a0[2];
+  const T s11 = C[S6(2, 2)] + vz;
+  const T idet = T(1) / kfma(s00, s11, -s01 * s01);
+  f.s00 = s00;
+  f.s11 = s11;
+  f.si00 = s11 * idet;
+  f.si01 = -s01 * idet;
+  f.si11 = s00 * idet;
+}
+
+// Residual of a corrected hit m against the prediction; false on the far half.
+template <class T>
+__device__ __forceinline__ bool residual(const T (&p)[6], const FrameT<T>& f, T mx, T my, T mz, T& r0,
+                                         T& r1) {
+  if (kfma(mx, p[0], my * p[1]) <= T(0)) return false;
+  r0 = kfma(-f.su, mx - p[0], f.cu * (my - p[1]));
+  r1 = mz - p[2];
+  return true;
+}
+
+template <class T>
+__device__ __forceinline__ T chi2_of(const FrameT<T>& f, T r0, T r1) {
+  return kfma(f.si00 * r0, r0, kfma(T(2) * f.si01 * r0, r1, f.si11 * r1 * r1));
+}
+
+// Gain K = C H^T S^-1, p += K r, C -= K H C (upper triangle).
+template <class T>
+__device__ __forceinline__ void kf_update(T (&p)[6], T (&C)[21], const FrameT<T>& f, T r0, T r1) {
+  T a1[6], k0[6], k1[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) a1[i] = C[S6(i, 2)];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    k0[i] = kfma(f.a0[i], f.si00, a1[i] * f.si01);
+    k1[i] = kfma(f.a0[i], f.si01, a1[i] * f.si11);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[i] = kfma(k0[i], r0, kfma(k1[i], r1, p[i]));
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i; j < 6; ++j) C[S6(i, j)] -= kfma(k0[i], f.a0[j], k1[i] * a1[j]);
+}
+
+// Thin-scatterer multiple scattering (Highland width, pion mass for beta):
+// Var(phi) += theta0^2 / sin^2(theta), Var(theta) += theta0^2.
+template <class T>
+__device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
+  if (p[3] == T(0) || x0 <= T(0)) return;
+  T sth, cth, sph, cph;
+  ksincos(p[5], &sth, &cth);
+  ksincos(p[4], &sph, &cph);
+  const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
+  const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;  // cos(phi - phi_p)
+  const T pm = T(1) / (kabs(p[3]) * sth);
+  const T beta = pm / ksqrt(kfma(pm, pm, T(MPION * MPION)));
+  const T t = x0 / kabs(sth * cdiff);
+  const T th0 = T(0.0136) / (beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
+  const T v = th0 * th0;
+  C[S6(4, 4)] += v / (sth * sth);
+  C[S6(5, 5)] += v;
+}
+
+// ---------------------------------------------------------------- hit grid
+// phi bins: floor((phi + pi) * n_phi / 2pi) (monotone in phi; wrapped mod
+// n_phi for hits).  eta bins: 64 equal steps of eta = asinh(z/R) over
+// [-asinh(z_max/R), asinh(z_max/R)], realised as a step function of z through
+// a per-layer table of bin edges in z (edge[k] = R sinh(eta_k)), so that the
+// map is monotone in z and identical for hits and search windows.
+__device__ __forceinline__ int phi_bin_raw(float phi, int n_phi) {
+  return (int)floorf((phi + PI_F) * ((float)n_phi / TWO_PI_F));
+}
+__device__ __forceinline__ int wrap_bin(int b, int n) {
+  b %= n;
+  return b < 0 ? b + n : b;
+}
+__device__ __forceinline__ int eta_bin(float z, float R, float eta_max, int n_eta, const float* edges) {
+  const float eta = asinhf(z / R);
+  int b = (int)floorf((eta + eta_max) * ((float)n_eta / (2.f * eta_max)));
+  b = min(max(b, 0), n_eta - 1);
+  while (b > 0 && z < __ldg(edges + b)) --b;
+  while (b < n_eta - 1 && z >= __ldg(edges + b + 1)) ++b;
+  return b;
+}
+
+// Ranking key of a candidate child (lower is better): 6 bits 63 - n_found,
+// 32 bits chi2 sum (non-negative float bits are monotone), 4 bits parent
+// slot, 1 bit non-hit, 21 bits hit index.
+constexpr unsigned long long KEY_EMPTY = ~0ull;
+__device__ __forceinline__ unsigned long long make_key(int n_found, float chi2, int parent,
+                                                       int nonhit, int hit) {
+  return ((unsigned long long)(63 - n_found) << 58) |
+         ((unsigned long long)__float_as_uint(fmaxf(chi2, 0.f)) << 26) |
+         ((unsigned long long)(parent & 15) << 22) | ((unsigned long long)(nonhit & 1) << 21) |
+         (unsigned long long)(hit & 0x1FFFFF);
+}
+__device__ __forceinline__ int key_nfound(unsigned long long k) { return 63 - (int)(k >> 58); }
+__device__ __forceinline__ float key_chi2(unsigned long long k) {
+  return __uint_as_float((unsigned)((k >> 26) & 0xFFFFFFFFull));
+}
+__device__ __forceinline__ int key_parent(unsigned long long k) { return (int)((k >> 22) & 15); }
+__device__ __forceinline__ int key_nonhit(unsigned long long k) { return (int)((k >> 21) & 1); }
+__device__ __forceinline__ int key_hit(unsigned long long k) { return (int)(k & 0x1FFFFF); }
+
+__device__ __forceinline__ void corrected_hit(const Align4& a, float x, float y, float z, float& mx,
+                                              float& my, float& mz) {
+  mx = fmaf(a.ca, x, -a.sa * y);
+  my = fmaf(a.sa, x, a.ca * y);
+  mz = z - a.az;
+}
+
+}  // namespace kfg

@@ -1,0 +1,181 @@
+// Duplicate removal after building (the paper's post-processing step, Sec. 4.2).
+//
+// Definition (sequential): visit the tracks of an event by (more hits, lower
+// chi2 sum, lower index); keep a track unless it shares more than
+// frac * min(nA, nB) hits with a track already kept.
+//
+// Parallel form, one thread block per event, identical result:
+//   1. hit -> owning tracks table (count, block scan, fill);
+//   2. for every track, the shared-hit counts with every other track through
+//      that table; a pair over the threshold is a conflict, recorded at the
+//      lower-priority track;
+//   3. resolution rounds: an undecided track is removed as soon as one of its
+//      higher-priority conflicts is kept, and kept as soon as all of them are
+//      removed.  The decisions equal the sequential walk's, because each one
+//      only depends on the final decisions of higher-priority tracks; every
+//      round settles at least the highest-priority undecided track.
+// Scratch (the owner table, the conflict lists and the decision states) lives
+// in global memory owned by the caller.
+#include "kf_internal.h"
+
+namespace kfg {
+
+namespace {
+
+constexpr int DEDUP_THREADS = 1024;
+
+__device__ __forceinline__ bool prio_less(int na, float ca, int ia, int nb, float cb, int ib) {
+  if (na != nb) return na > nb;
+  if (ca != cb) return ca < cb;
+  return ia < ib;
+}
+
+__global__ void __launch_bounds__(DEDUP_THREADS) k_dedup(const DedupParams P) {
+  __shared__ unsigned sh_scan[33];
+  __shared__ int sh_flag;
+  const int e = P.e_begin + blockIdx.x;
+  const int s0 = P.seed_off[e], s1 = P.seed_off[e + 1];
+  const int h0 = P.hit_off[e], h1 = P.hit_off[e + 1];
+  const int nh = h1 - h0;
+  const int L = P.L;
+  unsigned* cnt = P.hit_cnt + h0 + e;   // nh + 1 entries per event
+  int* owners = P.owners + (size_t)s0 * L;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int i = tid; i <= nh; i += nt) cnt[i] = 0u;
+  __syncthreads();
+  for (int t = s0 + tid; t < s1; t += nt) {
+    const int n = P.out_n[t];
+    const int* ht = P.out_hits + (size_t)t * L;
+    for (int j = 0; j < n; ++j) atomicAdd(&cnt[ht[j]], 1u);
+  }
+  __syncthreads();
+  // block exclusive scan of cnt[0..nh)
+  {
+    const int per = (nh + nt - 1) / nt;
+    const int b = tid * per;
+    unsigned s = 0;
+    for (int k = 0; k < per; ++k)
+      if (b + k < nh) s += cnt[b + k];
+    // inline block scan
+    const int lane = tid & 31, warp = tid >> 5;
+    unsigned incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) sh_scan[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = nt >> 5;
+      unsigned w = lane < nw ? sh_scan[lane] : 0u, wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += v;
+      }
+      if (lane < nw) sh_scan[lane] = wi - w;
+    }
+    __syncthreads();
+    unsigned run = sh_scan[warp] + incl - s;
+    for (int k = 0; k < per; ++k)
+      if (b + k < nh) {
+        const unsigned v = cnt[b + k];
+        cnt[b + k] = run;
+        run += v;
+      }
+  }
+  __syncthreads();
+  // fill: afterwards cnt[h] is the end of hit h's owner range, cnt[h-1] its start
+  for (int t = s0 + tid; t < s1; t += nt) {
+    const int n = P.out_n[t];
+    const int* ht = P.out_hits + (size_t)t * L;
+    for (int j = 0; j < n; ++j) owners[atomicAdd(&cnt[ht[j]], 1u)] = t;
+  }
+  __syncthreads();
+  // conflicts
+  for (int t = s0 + tid; t < s1; t += nt) {
+    const int n = P.out_n[t];
+    const float c = P.out_chi2[t];
+    const int* ht = P.out_hits + (size_t)t * L;
+    int pid[DEDUP_PARTNER_CAP];
+    int pcnt[DEDUP_PARTNER_CAP];
+    int np = 0;
+    bool overflow = false;
+    for (int j = 0; j < n; ++j) {
+      const int h = ht[j];
+      const unsigned a = h == 0 ? 0u : cnt[h - 1], b = cnt[h];
+      for (unsigned q = a; q < b; ++q) {
+        const int u = owners[q];
+        if (u == t) continue;
+        int k = 0;
+        while (k < np && pid[k] != u) ++k;
+        if (k < np) {
+          pcnt[k]++;
+        } else if (np < DEDUP_PARTNER_CAP) {
+          pid[np] = u;
+          pcnt[np] = 1;
+          ++np;
+        } else {
+          overflow = true;
+        }
+      }
+    }
+    if (overflow) atomicCAS(P.status, ST_OK, ST_DEDUP_PARTNERS);
+    int nc = 0;
+    for (int k = 0; k < np; ++k) {
+      const int u = pid[k];
+      const int nu = P.out_n[u];
+      if ((float)pcnt[k] > P.frac * (float)min(n, nu) && prio_less(nu, P.out_chi2[u], u, n, c, t)) {
+        if (nc < DEDUP_CONF_CAP) P.conf[(size_t)t * DEDUP_CONF_CAP + nc] = u;
+        else atomicCAS(P.status, ST_OK, ST_DEDUP_CONFLICTS);
+        ++nc;
+      }
+    }
+    P.n_conf[t] = min(nc, DEDUP_CONF_CAP);
+    P.state[t] = 0;  // undecided
+  }
+  __syncthreads();
+  // resolution rounds (bounded by the number of tracks)
+  const int max_rounds = (s1 - s0) + 2;
+  int round = 0;
+  for (;;) {
+    if (tid == 0) sh_flag = 0;
+    __syncthreads();
+    int undecided = 0;
+    for (int t = s0 + tid; t < s1; t += nt) {
+      if (P.state[t] != 0) continue;
+      const int nc = P.n_conf[t];
+      bool any_kept = false, all_removed = true;
+      for (int k = 0; k < nc; ++k) {
+        const unsigned char s = ((volatile unsigned char*)P.state)[P.conf[(size_t)t * DEDUP_CONF_CAP + k]];
+        if (s == 1) any_kept = true;
+        if (s != 2) all_removed = false;
+      }
+      if (any_kept) P.state[t] = 2;
+      else if (all_removed) P.state[t] = 1;
+      else undecided = 1;
+    }
+    if (undecided) sh_flag = 1;
+    __syncthreads();
+    const int more = sh_flag;
+    __syncthreads();
+    if (!more) break;
+    if (++round > max_rounds) {
+      if (tid == 0) atomicCAS(P.status, ST_OK, ST_DEDUP_ROUNDS);
+      break;
+    }
+  }
+  for (int t = s0 + tid; t < s1; t += nt) P.keep[t] = P.state[t] == 1 ? 1 : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_dedup(const DedupParams& P, int n_events, cudaStream_t st) {
+  if (n_events <= 0) return cudaSuccess;
+  k_dedup<<<n_events, DEDUP_THREADS, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace kfg

@@ -1,0 +1,427 @@
+// Combinatorial Kalman-filter track finding (the paper's "build" step, Sec. 2).
+//
+// Mapping: one seed per group of G lanes, one lane per candidate slot (G >=
+// N = max_cands), 32/G seeds per warp processed in lockstep.  A candidate's
+// state (6 parameters + 21 covariance terms) stays in its lane's registers
+// across all layers.  One loop covers the seed fit (three forced hits) and the
+// layers after the seed.  Per layer:
+//   1. every live candidate propagates to the layer (closed-form helix, exact
+//      Jacobian, sparse J C J^T) and builds its measurement frame;
+//   2. it walks the eta x phi bins of a window that contains the whole
+//      chi2 < cut ellipse (bounds padded by the FP32 error of the window
+//      arithmetic), tests every hit there and keeps its own best N
+//      hit-children in a sorted list in shared memory;
+//   3. the group selects the N best children of all its candidates by their
+//      64-bit ranking keys (more hits, lower chi2 sum, parent slot, hit
+//      before hole, hit index): each child's rank is its position in its own
+//      list plus the number of smaller keys in the other lanes' lists, and
+//      the children of rank < N land in the slots of their rank;
+//   4. each lane pulls its chosen parent's predicted state with warp shuffles,
+//      applies the Kalman update for a hit-child and the scattering of the layer.
+// Parent pointers and hit indices go to a per-group history in shared memory;
+// the best candidate's hit list is rebuilt from it at the end.
+#include "kf_internal.h"
+
+namespace kfg {
+
+namespace {
+
+constexpr int HIST_LAYERS = KF_MAX_LAYERS;
+constexpr int BACKUP_STRIDE = 28;  // 27 state floats, padded
+// Shared memory per warp: history [32 lanes][32 layers] int, child lists
+// [32 lanes][KF_MAX_CANDS + 1] u64, selected children [32] u64, list lengths
+// [32] int, state backup [32 lanes][28] float.
+constexpr int LIST_STRIDE = KF_MAX_CANDS + 1;
+constexpr int SMEM_HIST = 32 * HIST_LAYERS * 4;
+constexpr int SMEM_LIST = 32 * LIST_STRIDE * 8;
+constexpr int SMEM_SLOT = 32 * 8;
+constexpr int SMEM_CNT = 32 * 4;
+constexpr int SMEM_BACKUP = 32 * BACKUP_STRIDE * 4;
+constexpr int SMEM_PER_WARP = SMEM_HIST + SMEM_LIST + SMEM_SLOT + SMEM_CNT + SMEM_BACKUP;
+// Window padding: relative and absolute slack on the chi2-ellipse bounds that
+// covers the FP32 rounding of the window arithmetic and of the hit's own
+// angle and eta-bin computation.
+constexpr float WIN_REL = 1e-3f;
+constexpr float WIN_PHI_ABS = 1e-5f;  // rad
+constexpr float WIN_Z_ABS = 1e-4f;    // cm
+
+template <int G, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
+  constexpr int W = 32 / G;  // seeds per warp
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int grp = lane / G;
+  const int gl = lane - grp * G;
+  const int base = grp * G;
+  const bool lane_used = grp < W;
+  unsigned char* ws = smem + (size_t)warp * SMEM_PER_WARP;
+  int* hist = reinterpret_cast<int*>(ws);
+  unsigned long long* lists = reinterpret_cast<unsigned long long*>(ws + SMEM_HIST);
+  unsigned long long* lst = lists + lane * LIST_STRIDE;
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(ws + SMEM_HIST + SMEM_LIST);
+  int* cnts = reinterpret_cast<int*>(ws + SMEM_HIST + SMEM_LIST + SMEM_SLOT);
+  float* bak = reinterpret_cast<float*>(ws + SMEM_HIST + SMEM_LIST + SMEM_SLOT + SMEM_CNT) + lane * BACKUP_STRIDE;
+
+  const DevGeom& g = P.g;
+  const int L = g.n_layers;
+  const int N = g.max_cands;
+  const int n_seed_range = P.s_end - P.s_begin;
+  const int n_tasks = (n_seed_range + W - 1) / W;
+  const int warps_per_block = blockDim.x >> 5;
+
+  unsigned long long c_steps = 0, c_updates = 0, c_chi2 = 0, c_seeds = 0, c_holes = 0;
+
+  int task;
+  if (P.persistent) {
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(P.queue, 1u);
+    task = (int)__shfl_sync(0xffffffffu, t, 0);
+  } else {
+    task = blockIdx.x * warps_per_block + warp;
+  }
+
+  while (task < n_tasks) {
+    const int seed = P.s_begin + task * W + grp;
+    const bool has_seed = lane_used && (seed < P.s_end);
+    int ev = 0, hoff = 0;
+    float p[6], C[21];
+    float chi2 = 0.f;
+    int nfound = 3, nholes = 0;
+    bool finished = false;
+    bool occ = has_seed && gl == 0;
+    int sh0 = 0, sh1 = 0, sh2 = 0, sl0 = 0, sl1 = 0, sl2 = 0;
+    if (has_seed) {
+      ev = P.seed_event[seed];
+      hoff = P.hit_off[ev];
+      sh0 = P.sh[seed];
+      sh1 = P.sh[(size_t)P.ns + seed];
+      sh2 = P.sh[2 * (size_t)P.ns + seed];
+      sl0 = P.hlayer[hoff + sh0];
+      sl1 = P.hlayer[hoff + sh1];
+      sl2 = P.hlayer[hoff + sh2];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + seed];
+#pragma unroll
+      for (int k = 0; k < 21; ++k) C[k] = P.sc[(size_t)k * P.ns + seed];
+      if (gl == 0) c_seeds++;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) p[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) C[k] = 0.f;
+    }
+    const int start = has_seed ? sl2 + 1 : L;           // first layer searched
+    const int n_iter = has_seed ? 3 + (L - start) : 0;  // seed hits + layers
+    const int it_end = __reduce_max_sync(0xffffffffu, n_iter);
+
+#pragma unroll 1
+    for (int it = 0; it < it_end; ++it) {
+      const bool in_seed = it < 3;
+      const bool active = it < n_iter;
+      const int l = in_seed ? (it == 0 ? sl0 : (it == 1 ? sl1 : sl2)) : start + (it - 3);
+      int cls = 0;  // 1 = carried unchanged, 2 = propagated with hit/hole children
+      int cnt = 0;
+      unsigned long long tail = KEY_EMPTY;
+      if (active && occ) {
+        if (finished) {
+          cls = 1;
+          tail = make_key(nfound, chi2, gl, 1, 0);
+        } else {
+          if (!in_seed) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) bak[k] = p[k];
+#pragma unroll
+            for (int k = 0; k < 21; ++k) bak[6 + k] = C[k];
+          }
+          const float R = g.radius[l];
+          const int pr = (it == 0) ? 1 : propagate<float>(p, C, R, g.kb, in_seed ? INFINITY : g.z_max);
+          if (pr != 1) {
+            cls = 1;
+            finished = true;
+            tail = make_key(nfound, chi2, gl, 1, 0);
+          } else {
+            cls = 2;
+            if (!in_seed) {
+              c_steps++;
+              Frame f;
+              make_frame<float>(p, C, g.vr, g.vz, f);
+              const Align4 al = P.align[l];
+              // Window containing the ellipse chi2 < cut: |r_rphi| < sqrt(cut S00)
+              // with r_rphi = R_hit sin(dphi) on the near half, |r_z| < sqrt(cut S11).
+              const float w1 = sqrtf(g.chi2_cut * f.s00);
+              const float w2 = sqrtf(g.chi2_cut * f.s11);
+              float dphi = (w1 >= R) ? 0.5f * PI_F : asinf(w1 / R);
+              dphi = fminf(dphi, 0.5f * PI_F) * (1.f + WIN_REL) + WIN_PHI_ABS;
+              const float phic = atan2f(p[1], p[0]) + al.dphi;
+              const int nphi = g.n_phi, neta = g.n_eta;
+              const int u0 = phi_bin_raw(phic - dphi, nphi);
+              const int u1 = phi_bin_raw(phic + dphi, nphi);
+              int span = u1 - u0 + 1, b0;
+              if (span >= nphi) { span = nphi; b0 = 0; } else { b0 = wrap_bin(u0, nphi); }
+              const float zc = p[2] + al.az;
+              const float wz = w2 * (1.f + WIN_REL) + WIN_Z_ABS;
+              const float* edges = P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1);
+              const int e0 = eta_bin(zc - wz, R, g.eta_max[l], neta, edges);
+              const int e1 = eta_bin(zc + wz, R, g.eta_max[l], neta, edges);
+              const unsigned* off = P.bin_off + ((size_t)ev * L + l) * ((size_t)neta * nphi);
+              const int nf1 = nfound + 1;
+              const int b1 = min(b0 + span, nphi);
+              const int b2 = b0 + span - nphi;  // > 0 when the window wraps
+#pragma unroll 1
+              for (int e = e0; e <= e1; ++e) {
+                const unsigned* row = off + (size_t)e * nphi;
+#pragma unroll 1
+                for (int part = 0; part < 2; ++part) {
+                  if (part == 1 && b2 <= 0) break;
+                  const unsigned i0 = part ? row[0] : row[b0];
+                  const unsigned i1 = part ? row[b2] : row[b1];
+#pragma unroll 1
+                  for (unsigned i = i0; i < i1; ++i) {
+                    const float4 h = P.hb[i];
+                    float mx, my, mz;
+                    corrected_hit(al, h.x, h.y, h.z, mx, my, mz);
+                    float r0, r1;
+                    c_chi2++;
+                    if (!residual<float>(p, f, mx, my, mz, r0, r1)) continue;
+                    const float c2 = chi2_of<float>(f, r0, r1);
+                    if (!(c2 < g.chi2_cut)) continue;
+                    const unsigned long long key = make_key(nf1, chi2 + c2, gl, 0, __float_as_int(h.w));
+                    int pos;
+                    if (cnt < N) pos = cnt++;
+                    else if (key < lst[N - 1]) pos = N - 1;
+                    else continue;
+                    while (pos > 0 && lst[pos - 1] > key) { lst[pos] = lst[pos - 1]; --pos; }
+                    lst[pos] = key;
+                  }
+                }
+              }
+              if (nholes < g.max_holes) {
+                tail = make_key(nfound, chi2, gl, 1, 0);
+              } else if (cnt == 0) {
+                // no compatible hit and no hole left: the candidate stops unchanged
+                cls = 1;
+                finished = true;
+                tail = make_key(nfound, chi2, gl, 1, 0);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) p[k] = bak[k];
+#pragma unroll
+                for (int k = 0; k < 21; ++k) C[k] = bak[6 + k];
+              }
+            }
+          }
+        }
+      }
+
+      // Top-N of all children of each group (layers only; a group in its seed
+      // fit keeps its single candidate).
+      unsigned long long mine = KEY_EMPTY;
+      int par = gl, p_holes = nholes, p_cls = cls;
+      if (__any_sync(0xffffffffu, active && !in_seed)) {
+        // Rank of each child = its position in its own sorted list + the
+        // number of smaller keys in the other lists of the group (keys are
+        // unique); the children of rank < N go to the slots of their rank.
+        if (tail != KEY_EMPTY) lst[cnt++] = tail;
+        cnts[lane] = cnt;
+        slot[lane] = KEY_EMPTY;
+        __syncwarp();
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) {
+          const unsigned long long key = lst[j];
+          int rank = j;
+#pragma unroll 1
+          for (int k = 0; k < G && rank < N; ++k) {
+            if (k == gl) continue;
+            const int ck = cnts[base + k];
+            const unsigned long long* lk = lists + (base + k) * LIST_STRIDE;
+            int q = 0;
+            while (q < ck && lk[q] < key) ++q;
+            rank += q;
+          }
+          if (rank >= N) break;  // later children of this lane rank lower still
+          slot[base + rank] = key;
+        }
+        __syncwarp();
+        if (lane_used && gl < N) mine = slot[lane];
+        // Pull the parent's exported state (the prediction, or the unchanged
+        // state of a carried candidate).
+        par = (mine != KEY_EMPTY) ? key_parent(mine) : gl;
+        const int src = lane_used ? base + par : lane;
+        float np[6], nC[21];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) np[k] = __shfl_sync(0xffffffffu, p[k], src);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) nC[k] = __shfl_sync(0xffffffffu, C[k], src);
+        p_holes = __shfl_sync(0xffffffffu, nholes, src);
+        p_cls = __shfl_sync(0xffffffffu, cls, src);
+        if (active && !in_seed) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) p[k] = np[k];
+#pragma unroll
+          for (int k = 0; k < 21; ++k) C[k] = nC[k];
+        }
+      }
+
+      if (active) {
+        // What the lane does with its (new) candidate on this layer.
+        bool do_update = false, do_ms = false;
+        int hit = 0;
+        if (in_seed) {
+          do_update = occ && cls == 2;
+          hit = it == 0 ? sh0 : (it == 1 ? sh1 : sh2);
+        } else if (mine == KEY_EMPTY) {
+          occ = false;
+        } else {
+          occ = true;
+          nfound = key_nfound(mine);
+          chi2 = key_chi2(mine);
+          nholes = p_holes;
+          if (!key_nonhit(mine)) {
+            do_update = true;
+            hit = key_hit(mine);
+            finished = false;
+          } else if (p_cls == 2) {
+            nholes += 1;
+            do_ms = true;
+            finished = false;
+            c_holes++;
+          } else {
+            finished = true;
+          }
+          hist[(grp * HIST_LAYERS + l) * G + gl] = (par << 24) | (do_update ? hit + 1 : 0);
+        }
+        if (do_update) {
+          const int hi = hoff + hit;
+          float mx, my, mz;
+          corrected_hit(P.align[l], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+          Frame f;
+          make_frame<float>(p, C, g.vr, g.vz, f);
+          float r0, r1;
+          if (residual<float>(p, f, mx, my, mz, r0, r1)) {
+            if (in_seed) chi2 += chi2_of<float>(f, r0, r1);
+            kf_update<float>(p, C, f, r0, r1);
+            do_ms = true;
+            if (!in_seed) c_updates++;
+          } else {
+            finished = true;  // far-side seed hit: the seed fit stops here
+          }
+        }
+        if (do_ms) add_ms<float>(p, C, g.x0[l]);
+      }
+      __syncwarp();
+    }
+
+    // The best candidate sits in slot 0: rebuild its hit list.
+    if (has_seed && gl == 0) {
+      int* oh = P.out_hits + (size_t)seed * L;
+      int k = nfound - 1;
+      int slot = 0;
+      for (int l = L - 1; l >= start; --l) {
+        const int e = hist[(grp * HIST_LAYERS + l) * G + slot];
+        if (e & 0xFFFFFF) oh[k--] = (e & 0xFFFFFF) - 1;
+        slot = e >> 24;
+      }
+      oh[0] = sh0;
+      oh[1] = sh1;
+      oh[2] = sh2;
+      for (int j = nfound; j < L; ++j) oh[j] = -1;
+      P.out_n[seed] = nfound;
+      P.out_chi2[seed] = chi2;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) P.out_p[(size_t)q * P.ns + seed] = p[q];
+#pragma unroll
+      for (int q = 0; q < 21; ++q) P.out_C[(size_t)q * P.ns + seed] = C[q];
+    }
+    __syncwarp();
+
+    if (P.persistent) {
+      unsigned t = 0;
+      if (lane == 0) t = atomicAdd(P.queue, 1u);
+      task = (int)__shfl_sync(0xffffffffu, t, 0);
+    } else {
+      break;
+    }
+  }
+
+  // Counters: one atomic per warp.
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    c_steps += __shfl_xor_sync(0xffffffffu, c_steps, off);
+    c_updates += __shfl_xor_sync(0xffffffffu, c_updates, off);
+    c_chi2 += __shfl_xor_sync(0xffffffffu, c_chi2, off);
+    c_seeds += __shfl_xor_sync(0xffffffffu, c_seeds, off);
+    c_holes += __shfl_xor_sync(0xffffffffu, c_holes, off);
+  }
+  if (lane == 0 && P.counters) {
+    atomicAdd(&P.counters[0], c_steps);
+    atomicAdd(&P.counters[1], c_updates);
+    atomicAdd(&P.counters[2], c_chi2);
+    atomicAdd(&P.counters[3], c_seeds);
+    atomicAdd(&P.counters[4], c_holes);
+  }
+}
+
+template <int G, int MINB>
+cudaError_t prepare_g(int threads, int* blocks_per_sm) {
+  const size_t smem = (size_t)(threads / 32) * SMEM_PER_WARP;
+  cudaError_t err = cudaFuncSetAttribute(k_find<G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  if (blocks_per_sm)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_find<G, MINB>, threads, smem);
+  return err;
+}
+
+template <int G, int MINB>
+cudaError_t launch_g(const FindParams& P, int threads, int grid_cap, cudaStream_t st) {
+  const size_t smem = (size_t)(threads / 32) * SMEM_PER_WARP;
+  constexpr int W = 32 / G;
+  const int n = P.s_end - P.s_begin;
+  const int n_tasks = (n + W - 1) / W;
+  const int wpb = threads / 32;
+  int grid = (n_tasks + wpb - 1) / wpb;
+  if (P.persistent && grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+  if (grid < 1) grid = 1;
+  k_find<G, MINB><<<grid, threads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+// Kernel variants: lanes per seed G x register budget (MINB = 1: the
+// compiler's choice; MINB = 3: at most 85 registers for three 256-thread
+// blocks per SM).
+#define KF_FIND_DISPATCH(FN, ...)                                   \
+  switch (lanes * 4 + (regcap ? 1 : 0)) {                          \
+    case 4 * 4: return FN<4, 1>(__VA_ARGS__);                      \
+    case 4 * 4 + 1: return FN<4, 3>(__VA_ARGS__);                  \
+    case 6 * 4: return FN<6, 1>(__VA_ARGS__);                      \
+    case 6 * 4 + 1: return FN<6, 3>(__VA_ARGS__);                  \
+    case 8 * 4: return FN<8, 1>(__VA_ARGS__);                      \
+    case 8 * 4 + 1: return FN<8, 3>(__VA_ARGS__);                  \
+    case 10 * 4: return FN<10, 1>(__VA_ARGS__);                    \
+    case 10 * 4 + 1: return FN<10, 3>(__VA_ARGS__);                \
+    case 12 * 4: return FN<12, 1>(__VA_ARGS__);                    \
+    case 12 * 4 + 1: return FN<12, 3>(__VA_ARGS__);                \
+    case 16 * 4: return FN<16, 1>(__VA_ARGS__);                    \
+    case 16 * 4 + 1: return FN<16, 3>(__VA_ARGS__);                \
+    default: return cudaErrorInvalidValue;                         \
+  }
+
+}  // namespace
+
+size_t find_smem_bytes(int threads) { return (size_t)(threads / 32) * SMEM_PER_WARP; }
+
+bool find_lanes_supported(int lanes) {
+  return lanes == 4 || lanes == 6 || lanes == 8 || lanes == 10 || lanes == 12 || lanes == 16;
+}
+
+cudaError_t find_prepare(int lanes, int regcap, int threads, int* blocks_per_sm) {
+  KF_FIND_DISPATCH(prepare_g, threads, blocks_per_sm)
+}
+
+cudaError_t launch_find(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
+                        cudaStream_t st) {
+  if (P.s_end <= P.s_begin) return cudaSuccess;
+  KF_FIND_DISPATCH(launch_g, P, threads, grid_cap, st)
+}
+
+}  // namespace kfg

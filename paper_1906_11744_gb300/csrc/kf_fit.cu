@@ -1,0 +1,129 @@
+// Kalman re-fit of tracks (the paper's "fitting" step, Sec. 5): one thread
+// per track, state and covariance in registers, from the seed prior placed at
+// the first hit over the track's hits layer by layer.  The result is the
+// state after the last hit, before its scattering, and the summed chi2 of the
+// predicted residuals.
+//
+// Conditioning: where a track crosses a layer close to tangentially (the
+// looper at the end of its reach), the propagation Jacobian grows like
+// 1/cos(alpha) and the predicted covariance gains a large, nearly rank-one
+// term that the update then removes again; FP32 loses the posterior there.
+// A first FP32 pass fits every track and flags a track as soon as one of its
+// crossings has cos(alpha) below CAREFUL_COS; a second pass refits only the
+// flagged tracks, running those steps' propagation and update in double
+// precision (a small fraction of tracks: loopers near their maximum radius).
+#include "kf_internal.h"
+
+namespace kfg {
+
+namespace {
+
+constexpr float CAREFUL_COS = 0.5f;
+
+// One Kalman step in scalar type T: propagate (unless first), update with the
+// corrected hit, scatter unless last.  Returns a KF_FIT_* status.
+template <class T>
+__device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float (&Cf)[21], bool first,
+                                        bool last, int L, float mx, float my, float mz, float& chi2) {
+  T p[6], C[21];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = (T)pf[k];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = (T)Cf[k];
+  if (!first && propagate<T>(p, C, (T)g.radius[L], (T)g.kb, T(INFINITY)) != 1) return KF_FIT_NO_CROSS;
+  FrameT<T> f;
+  make_frame<T>(p, C, (T)g.vr, (T)g.vz, f);
+  T r0, r1;
+  if (!residual<T>(p, f, (T)mx, (T)my, (T)mz, r0, r1)) return KF_FIT_FAR_SIDE;
+  chi2 += (float)chi2_of<T>(f, r0, r1);
+  kf_update<T>(p, C, f, r0, r1);
+  if (!last) add_ms<T>(p, C, (T)g.x0[L]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) pf[k] = (float)p[k];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) Cf[k] = (float)C[k];
+  return KF_FIT_OK;
+}
+
+// Status of a track whose FP32 pass met a near-tangent crossing; the
+// careful pass refits it from the start.
+constexpr int FIT_NEEDS_CAREFUL = 2;
+
+template <bool CAREFUL>
+__global__ void __launch_bounds__(128) k_fit(const FitParams P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P.ns) return;
+  if (CAREFUL && P.fit_status[t] != FIT_NEEDS_CAREFUL) return;
+  if (!CAREFUL && P.keep && !P.keep[t]) {  // removed as a duplicate: zero outputs
+#pragma unroll
+    for (int k = 0; k < 6; ++k) P.fit_p[(size_t)k * P.ns + t] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P.fit_C[(size_t)k * P.ns + t] = 0.f;
+    P.fit_chi2[t] = 0.f;
+    P.fit_status[t] = KF_FIT_SKIPPED;
+    return;
+  }
+  const DevGeom& g = P.g;
+  float p[6], C[21];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + t];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = P.sc[(size_t)k * P.ns + t];
+  const int hoff = P.hit_off[P.seed_event[t]];
+  const int n = P.n_list[t];
+  const int* lst = P.lists + (size_t)t * P.max_len;
+  float chi2 = 0.f;
+  int status = KF_FIT_OK;
+#pragma unroll 1
+  for (int k = 0; k < n && status == KF_FIT_OK; ++k) {
+    const int hi = hoff + lst[k];
+    const int L = P.hlayer[hi];
+    float mx, my, mz;
+    corrected_hit(P.align[L], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+    if (!CAREFUL) {
+      if (k > 0) {
+        float cosa = 1.f;
+        if (propagate<float>(p, C, g.radius[L], g.kb, INFINITY, &cosa) != 1) { status = KF_FIT_NO_CROSS; break; }
+        if (cosa < CAREFUL_COS) {
+          P.fit_status[t] = FIT_NEEDS_CAREFUL;
+          return;
+        }
+      }
+      Frame f;
+      make_frame<float>(p, C, g.vr, g.vz, f);
+      float r0, r1;
+      if (!residual<float>(p, f, mx, my, mz, r0, r1)) { status = KF_FIT_FAR_SIDE; break; }
+      chi2 += chi2_of<float>(f, r0, r1);
+      kf_update<float>(p, C, f, r0, r1);
+      if (k + 1 < n) add_ms<float>(p, C, g.x0[L]);
+    } else {
+      bool careful = false;
+      if (k > 0) {
+        float zc, cosa;
+        if (!crossing(p, g.radius[L], g.kb, zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
+        careful = cosa < CAREFUL_COS;
+      }
+      status = careful ? fit_step<double>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
+                       : fit_step<float>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) P.fit_p[(size_t)k * P.ns + t] = p[k];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) P.fit_C[(size_t)k * P.ns + t] = C[k];
+  P.fit_chi2[t] = chi2;
+  P.fit_status[t] = status;
+}
+
+}  // namespace
+
+cudaError_t launch_fit(const FitParams& P, cudaStream_t st) {
+  if (P.ns <= 0) return cudaSuccess;
+  const int threads = 128;
+  const int blocks = (P.ns + threads - 1) / threads;
+  k_fit<false><<<blocks, threads, 0, st>>>(P);
+  k_fit<true><<<blocks, threads, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace kfg

@@ -1,0 +1,123 @@
+// Internal launch interface between the C ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kf_common.cuh"
+
+namespace kfg {
+
+// Device-side status word values (sticky; read by kf_sync / kf_get_*).
+enum : int {
+  ST_OK = 0,
+  ST_DEDUP_PARTNERS = 1,   // a track shares hits with more tracks than the partner table holds
+  ST_DEDUP_CONFLICTS = 2,  // more higher-priority conflicts than the conflict table holds
+  ST_DEDUP_ROUNDS = 3,     // the resolution loop hit its iteration bound
+};
+
+struct FindParams {
+  DevGeom g;
+  const float* hx;
+  const float* hy;
+  const float* hz;
+  const int* hlayer;
+  const int* hit_off;        // [n_events + 1]
+  const float4* hb;          // binned hits (x, y, z, event-local index as int bits)
+  const unsigned* bin_off;   // [n_events * n_layers * n_bins + 1] global offsets into hb
+  const float* eta_edges;    // [KF_MAX_LAYERS][MAX_ETA_BINS + 1] z edges of the eta bins
+  const float* sp;           // seed params [6][ns]
+  const float* sc;           // seed cov [21][ns]
+  const int* sh;             // seed hits [3][ns]
+  const int* seed_event;     // [ns]
+  const Align4* align;       // [n_layers]
+  int ns;                    // seed stride
+  int s_begin, s_end;        // seed range of this launch
+  int* out_hits;             // [ns][n_layers]
+  int* out_n;                // [ns]
+  float* out_chi2;           // [ns]
+  float* out_p;              // [6][ns]
+  float* out_C;              // [21][ns]
+  unsigned* queue;           // persistent work counter (zeroed before the launch)
+  unsigned long long* counters;  // [4]
+  int persistent;
+};
+
+struct BinParams {
+  DevGeom g;
+  const float* hx;
+  const float* hy;
+  const float* hz;
+  const int* hlayer;
+  const int* hit_off;
+  int n_events;
+  int h_begin, h_end;     // hit range of this launch
+  const float* eta_edges; // [KF_MAX_LAYERS][MAX_ETA_BINS + 1]
+  unsigned* cnt;          // [n_bins_total + 1] counts, then offsets
+  unsigned* key;          // [n_hits]
+  unsigned* rank;         // [n_hits]
+  float4* hb;             // [n_hits]
+};
+
+struct DedupParams {
+  const int* out_hits;   // [ns][L]
+  const int* out_n;
+  const float* out_chi2;
+  const int* hit_off;
+  const int* seed_off;   // [n_events + 1]
+  int L;
+  int ns;
+  float frac;
+  int e_begin;           // first event of this launch (one block per event)
+  unsigned* hit_cnt;     // [n_hits + n_events]
+  int* owners;           // [ns * L]
+  int* conf;             // [ns * DEDUP_CONF_CAP]
+  int* n_conf;           // [ns]
+  unsigned char* state;  // [ns]
+  unsigned char* keep;   // [ns]
+  int* status;
+};
+
+constexpr int DEDUP_PARTNER_CAP = 32;
+constexpr int DEDUP_CONF_CAP = 16;
+
+struct FitParams {
+  DevGeom g;
+  const float* hx;
+  const float* hy;
+  const float* hz;
+  const int* hlayer;
+  const int* hit_off;
+  const float* sp;
+  const float* sc;
+  const int* seed_event;
+  const Align4* align;
+  int ns;
+  const int* lists;       // [ns][max_len]
+  const int* n_list;      // [ns]
+  int max_len;
+  const unsigned char* keep;  // may be null
+  float* fit_p;           // [6][ns]
+  float* fit_C;           // [21][ns]
+  float* fit_chi2;        // [ns]
+  int* fit_status;        // [ns]
+};
+
+// kf_find.cu
+cudaError_t launch_find(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
+                        cudaStream_t st);
+size_t find_smem_bytes(int threads);
+bool find_lanes_supported(int lanes);
+// Sets the dynamic shared-memory limit of the kernel variant (must run
+// outside stream capture) and reports resident blocks per SM.
+cudaError_t find_prepare(int lanes, int regcap, int threads, int* blocks_per_sm);
+// kf_bin.cu
+cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsigned first_pos,
+                       unsigned* scan_tmp, size_t scan_tmp_elems, cudaStream_t st);
+size_t scan_tmp_elems(size_t n);
+// kf_dedup.cu
+cudaError_t launch_dedup(const DedupParams& P, int n_events, cudaStream_t st);
+// kf_fit.cu
+cudaError_t launch_fit(const FitParams& P, cudaStream_t st);
+
+}  // namespace kfg

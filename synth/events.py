@@ -30,10 +30,13 @@ K_FIELD = 0.00299792458
 M_PION = 0.13957
 
 #: Variances of the seed prior placed at the first seed hit, in the order
-#: (x, y, z, q/pT, phi, theta).  Loose with respect to the circle estimate yet
-#: tight enough that no single Kalman update shrinks a variance by more than
-#: about three orders of magnitude.
-SEED_PRIOR_VAR = (1.0e-2, 1.0e-2, 1.0e-1, 4.0e-2, 1.0e-3, 1.0e-2)
+#: (x, y, z, q/pT, phi, theta).  The position is the first hit itself; the
+#: direction and curvature widths are about two to three times the RMS error
+#: of the three-hit circle estimate (q/pT 0.05 GeV^-1, phi 0.004 rad, theta
+#: 0.007 rad in the 17-layer geometry), loose against the estimate while
+#: keeping the information gain of each Kalman update within the range a
+#: single-precision covariance resolves.
+SEED_PRIOR_VAR = (1.0e-2, 1.0e-2, 1.0e-1, 1.0e-2, 1.0e-4, 4.0e-4)
 
 
 @dataclasses.dataclass(frozen=True)

@@ -1,0 +1,61 @@
+"""C ABI checks that need no GPU: the library builds, loads and exports
+every entry point that include/kf.h declares; the binding has the same names."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "kf.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(kf_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["kf_create", "kf_destroy", "kf_load_hits", "kf_load_seeds", "kf_set_alignment",
+              "kf_find_tracks", "kf_remove_duplicates", "kf_fit_tracks", "kf_fit_adjoint",
+              "kf_get_tracks", "kf_get_fit", "kf_capture_graph", "kf_launch_graph", "kf_autotune",
+              "kf_get_counters", "kf_sync", "kf_last_error"]:
+        assert n in names, n
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+
+    from paper_1906_11744_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_header():
+    from paper_1906_11744_gb300 import _lib
+    assert sorted(_lib.exported_symbols()) == _declared()
+
+
+def test_host_argument_errors_without_gpu():
+    """kf_create rejects bad geometry and settings before touching the device."""
+    import ctypes
+
+    from paper_1906_11744_gb300 import _lib, make_config, make_detector
+    lib = _lib.load()
+    ctx = ctypes.c_void_p()
+    bad_det = make_detector([10.0, 5.0], [0.02, 0.02])  # radii must increase
+    assert lib.kf_create(ctypes.byref(bad_det), ctypes.byref(make_config()), ctypes.byref(ctx)) == _lib.KF_ERR_ARG
+    det = make_detector([5.0, 10.0], [0.02, 0.02])
+    for cfg in (make_config(max_cands=0), make_config(max_cands=17), make_config(lanes_per_seed=5),
+                make_config(lanes_per_seed=4, max_cands=6), make_config(block_threads=48),
+                make_config(chi2_cut=-1.0)):
+        assert lib.kf_create(ctypes.byref(det), ctypes.byref(cfg), ctypes.byref(ctx)) == _lib.KF_ERR_ARG
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1906_11744_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(_lib.KFError):
+        _lib.load()
