@@ -40,7 +40,7 @@ struct kf_ctx {
   // duplicate removal scratch
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state;
   // fit
-  DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status;
+  DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count;
   int given_max_len = 0;
   bool found = false, deduped = false, fitted = false;
   int fit_source = KF_FIT_FOUND;
@@ -175,7 +175,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = find_prepare(ctx->lanes, ctx->regcap, ctx->threads, &ctx->blocks_per_sm);
+  if (e == cudaSuccess) e = find_prepare(ctx->lanes, ctx->regcap, ctx->threads, ctx->g.n_layers, &ctx->blocks_per_sm);
   if (e == cudaSuccess) e = grow(ctx->align4, sizeof(Align4) * KF_MAX_LAYERS);
   if (e == cudaSuccess) {
     // z edges of the eta bins per layer: edge_k = R sinh(-eta_max + k * 2 eta_max / n_eta)
@@ -220,7 +220,8 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue,
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
-                    &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status};
+                    &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
+                    &ctx->careful_count};
   for (DevBuf* b : bufs) release(*b);
   delete ctx;
   return KF_OK;
@@ -317,6 +318,8 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->fit_C, sizeof(float) * 21 * (size_t)n));
   CK(grow(ctx->fit_chi2, sizeof(float) * (size_t)n));
   CK(grow(ctx->fit_status, sizeof(int) * (size_t)n));
+  CK(grow(ctx->careful_list, sizeof(int) * (size_t)n));
+  CK(grow(ctx->careful_count, 64));
   CK(put(ctx->sp.p, params, sizeof(float) * 6 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sc.p, cov, sizeof(float) * 21 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sh.p, seed_hits, sizeof(int) * 3 * (size_t)n, device_ptrs, st));
@@ -496,6 +499,8 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   F.fit_C = ptr<float>(ctx->fit_C);
   F.fit_chi2 = ptr<float>(ctx->fit_chi2);
   F.fit_status = ptr<int>(ctx->fit_status);
+  F.careful_list = ptr<int>(ctx->careful_list);
+  F.careful_count = ptr<unsigned>(ctx->careful_count);
   if (source == KF_FIT_FOUND) {
     if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_fit_tracks: no found tracks");
     F.lists = ptr<int>(ctx->out_hits);
@@ -695,7 +700,7 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
     for (int threads : thread_opts)
     for (int regcap = 0; regcap < 2; ++regcap) {
       int bps = 1;
-      if (find_prepare(lanes, regcap, threads, &bps) != cudaSuccess || bps < 1) continue;
+      if (find_prepare(lanes, regcap, threads, ctx->g.n_layers, &bps) != cudaSuccess || bps < 1) continue;
       for (int pers = 0; pers < 2 && rc == KF_OK; ++pers) {
         ctx->lanes = lanes;
         ctx->threads = threads;
@@ -741,7 +746,7 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
   ctx->persistent = best_p;
   ctx->blocks_per_sm = best_b;
   ctx->regcap = best_rc;
-  CK(find_prepare(best_l, best_rc, best_t, &ctx->blocks_per_sm));
+  CK(find_prepare(best_l, best_rc, best_t, ctx->g.n_layers, &ctx->blocks_per_sm));
   if (n_results) *n_results = nr;
   if (rc != KF_OK) return rc;
   return KF_OK;

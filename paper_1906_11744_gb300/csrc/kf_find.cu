@@ -13,9 +13,9 @@
 //      hit-children in a sorted list in shared memory;
 //   3. the group selects the N best children of all its candidates by their
 //      64-bit ranking keys (more hits, lower chi2 sum, parent slot, hit
-//      before hole, hit index): each child's rank is its position in its own
-//      list plus the number of smaller keys in the other lanes' lists, and
-//      the children of rank < N land in the slots of their rank;
+//      before hole, hit index): the children are packed into one shared
+//      array, each lane ranks a few of them by counting smaller keys, and the
+//      children of rank < N land in the slots of their rank;
 //   4. each lane pulls its chosen parent's predicted state with warp shuffles,
 //      applies the Kalman update for a hit-child and the scattering of the layer.
 // Parent pointers and hit indices go to a per-group history in shared memory;
@@ -26,18 +26,19 @@ namespace kfg {
 
 namespace {
 
-constexpr int HIST_LAYERS = KF_MAX_LAYERS;
 constexpr int BACKUP_STRIDE = 28;  // 27 state floats, padded
-// Shared memory per warp: history [32 lanes][32 layers] int, child lists
-// [32 lanes][KF_MAX_CANDS + 1] u64, selected children [32] u64, list lengths
-// [32] int, state backup [32 lanes][28] float.
+// Shared memory per warp: child lists [32 lanes][KF_MAX_CANDS + 1] u64; the
+// packed children of each group [32][KF_MAX_CANDS + 1] u64, which between the
+// propagation and the selection holds the state backup [32 lanes][28] float;
+// selected children [32] u64; history [32 lanes][n_layers] int.
 constexpr int LIST_STRIDE = KF_MAX_CANDS + 1;
-constexpr int SMEM_HIST = 32 * HIST_LAYERS * 4;
 constexpr int SMEM_LIST = 32 * LIST_STRIDE * 8;
+constexpr int SMEM_GATHER = 32 * LIST_STRIDE * 8;
 constexpr int SMEM_SLOT = 32 * 8;
-constexpr int SMEM_CNT = 32 * 4;
-constexpr int SMEM_BACKUP = 32 * BACKUP_STRIDE * 4;
-constexpr int SMEM_PER_WARP = SMEM_HIST + SMEM_LIST + SMEM_SLOT + SMEM_CNT + SMEM_BACKUP;
+static_assert(32 * BACKUP_STRIDE * 4 <= SMEM_GATHER, "backup must fit the gather area");
+__host__ __device__ constexpr int smem_per_warp(int n_layers) {
+  return SMEM_LIST + SMEM_GATHER + SMEM_SLOT + ((32 * n_layers * 4 + 15) / 16) * 16;
+}
 // Window padding: relative and absolute slack on the chi2-ellipse bounds that
 // covers the FP32 rounding of the window arithmetic and of the hit's own
 // angle and eta-bin computation.
@@ -55,16 +56,14 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
   const int gl = lane - grp * G;
   const int base = grp * G;
   const bool lane_used = grp < W;
-  unsigned char* ws = smem + (size_t)warp * SMEM_PER_WARP;
-  int* hist = reinterpret_cast<int*>(ws);
-  unsigned long long* lists = reinterpret_cast<unsigned long long*>(ws + SMEM_HIST);
-  unsigned long long* lst = lists + lane * LIST_STRIDE;
-  unsigned long long* slot = reinterpret_cast<unsigned long long*>(ws + SMEM_HIST + SMEM_LIST);
-  int* cnts = reinterpret_cast<int*>(ws + SMEM_HIST + SMEM_LIST + SMEM_SLOT);
-  float* bak = reinterpret_cast<float*>(ws + SMEM_HIST + SMEM_LIST + SMEM_SLOT + SMEM_CNT) + lane * BACKUP_STRIDE;
-
   const DevGeom& g = P.g;
   const int L = g.n_layers;
+  unsigned char* ws = smem + (size_t)warp * smem_per_warp(L);
+  unsigned long long* lst = reinterpret_cast<unsigned long long*>(ws) + lane * LIST_STRIDE;
+  unsigned long long* gather = reinterpret_cast<unsigned long long*>(ws + SMEM_LIST);
+  float* bak = reinterpret_cast<float*>(gather) + lane * BACKUP_STRIDE;
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(ws + SMEM_LIST + SMEM_GATHER);
+  int* hist = reinterpret_cast<int*>(ws + SMEM_LIST + SMEM_GATHER + SMEM_SLOT);
   const int N = g.max_cands;
   const int n_seed_range = P.s_end - P.s_begin;
   const int n_tasks = (n_seed_range + W - 1) / W;
@@ -128,7 +127,7 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
           cls = 1;
           tail = make_key(nfound, chi2, gl, 1, 0);
         } else {
-          if (!in_seed) {
+          if (!in_seed && nholes >= g.max_holes) {  // only such a candidate can stop
 #pragma unroll
             for (int k = 0; k < 6; ++k) bak[k] = p[k];
 #pragma unroll
@@ -168,14 +167,22 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
               const int nf1 = nfound + 1;
               const int b1 = min(b0 + span, nphi);
               const int b2 = b0 + span - nphi;  // > 0 when the window wraps
+              const bool wrap = b2 > 0;
 #pragma unroll 1
-              for (int e = e0; e <= e1; ++e) {
-                const unsigned* row = off + (size_t)e * nphi;
+              for (int e = e0; e <= e1; e += 2) {
+                // Offsets of up to two eta rows (each one or two phi ranges),
+                // all loaded before any is used.
+                const bool two = e + 1 <= e1;
+                const unsigned* rA = off + (size_t)e * nphi;
+                const unsigned* rB = rA + nphi;
+                unsigned o0 = rA[b0], o1 = rA[b1];
+                unsigned o2 = wrap ? rA[0] : 0u, o3 = wrap ? rA[b2] : 0u;
+                unsigned o4 = two ? rB[b0] : 0u, o5 = two ? rB[b1] : 0u;
+                unsigned o6 = (two && wrap) ? rB[0] : 0u, o7 = (two && wrap) ? rB[b2] : 0u;
 #pragma unroll 1
-                for (int part = 0; part < 2; ++part) {
-                  if (part == 1 && b2 <= 0) break;
-                  const unsigned i0 = part ? row[0] : row[b0];
-                  const unsigned i1 = part ? row[b2] : row[b1];
+                for (int part = 0; part < 4; ++part) {
+                  const unsigned i0 = o0, i1 = o1;
+                  o0 = o2; o1 = o3; o2 = o4; o3 = o5; o4 = o6; o5 = o7;
 #pragma unroll 1
                   for (unsigned i = i0; i < i1; ++i) {
                     const float4 h = P.hb[i];
@@ -222,24 +229,27 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
         // number of smaller keys in the other lists of the group (keys are
         // unique); the children of rank < N go to the slots of their rank.
         if (tail != KEY_EMPTY) lst[cnt++] = tail;
-        cnts[lane] = cnt;
+        // Pack the group's children into one array: exclusive prefix of the
+        // list lengths over the group's lanes.
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, off);
+          if (gl >= off) incl += v;
+        }
+        const int M = __shfl_sync(0xffffffffu, incl, min(base + G - 1, 31));
+        unsigned long long* A = gather + base * LIST_STRIDE;
+        for (int j = 0, o = incl - cnt; j < cnt; ++j) A[o + j] = lst[j];
         slot[lane] = KEY_EMPTY;
         __syncwarp();
+        // rank = number of smaller keys in the group (keys are unique)
 #pragma unroll 1
-        for (int j = 0; j < cnt; ++j) {
-          const unsigned long long key = lst[j];
-          int rank = j;
-#pragma unroll 1
-          for (int k = 0; k < G && rank < N; ++k) {
-            if (k == gl) continue;
-            const int ck = cnts[base + k];
-            const unsigned long long* lk = lists + (base + k) * LIST_STRIDE;
-            int q = 0;
-            while (q < ck && lk[q] < key) ++q;
-            rank += q;
-          }
-          if (rank >= N) break;  // later children of this lane rank lower still
-          slot[base + rank] = key;
+        for (int m = gl; m < M && lane_used; m += G) {
+          const unsigned long long key = A[m];
+          int rank = 0;
+#pragma unroll 4
+          for (int q = 0; q < M; ++q) rank += A[q] < key ? 1 : 0;
+          if (rank < N) slot[base + rank] = key;
         }
         __syncwarp();
         if (lane_used && gl < N) mine = slot[lane];
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
           } else {
             finished = true;
           }
-          hist[(grp * HIST_LAYERS + l) * G + gl] = (par << 24) | (do_update ? hit + 1 : 0);
+          hist[(grp * L + l) * G + gl] = (par << 24) | (do_update ? hit + 1 : 0);
         }
         if (do_update) {
           const int hi = hoff + hit;
@@ -315,11 +325,11 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
     if (has_seed && gl == 0) {
       int* oh = P.out_hits + (size_t)seed * L;
       int k = nfound - 1;
-      int slot = 0;
+      int cur = 0;
       for (int l = L - 1; l >= start; --l) {
-        const int e = hist[(grp * HIST_LAYERS + l) * G + slot];
+        const int e = hist[(grp * L + l) * G + cur];
         if (e & 0xFFFFFF) oh[k--] = (e & 0xFFFFFF) - 1;
-        slot = e >> 24;
+        cur = e >> 24;
       }
       oh[0] = sh0;
       oh[1] = sh1;
@@ -362,8 +372,8 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
 }
 
 template <int G, int MINB>
-cudaError_t prepare_g(int threads, int* blocks_per_sm) {
-  const size_t smem = (size_t)(threads / 32) * SMEM_PER_WARP;
+cudaError_t prepare_g(int threads, int n_layers, int* blocks_per_sm) {
+  const size_t smem = (size_t)(threads / 32) * smem_per_warp(n_layers);
   cudaError_t err = cudaFuncSetAttribute(k_find<G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
@@ -374,7 +384,7 @@ cudaError_t prepare_g(int threads, int* blocks_per_sm) {
 
 template <int G, int MINB>
 cudaError_t launch_g(const FindParams& P, int threads, int grid_cap, cudaStream_t st) {
-  const size_t smem = (size_t)(threads / 32) * SMEM_PER_WARP;
+  const size_t smem = (size_t)(threads / 32) * smem_per_warp(P.g.n_layers);
   constexpr int W = 32 / G;
   const int n = P.s_end - P.s_begin;
   const int n_tasks = (n + W - 1) / W;
@@ -408,14 +418,14 @@ cudaError_t launch_g(const FindParams& P, int threads, int grid_cap, cudaStream_
 
 }  // namespace
 
-size_t find_smem_bytes(int threads) { return (size_t)(threads / 32) * SMEM_PER_WARP; }
+size_t find_smem_bytes(int threads, int n_layers) { return (size_t)(threads / 32) * smem_per_warp(n_layers); }
 
 bool find_lanes_supported(int lanes) {
   return lanes == 4 || lanes == 6 || lanes == 8 || lanes == 10 || lanes == 12 || lanes == 16;
 }
 
-cudaError_t find_prepare(int lanes, int regcap, int threads, int* blocks_per_sm) {
-  KF_FIND_DISPATCH(prepare_g, threads, blocks_per_sm)
+cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* blocks_per_sm) {
+  KF_FIND_DISPATCH(prepare_g, threads, n_layers, blocks_per_sm)
 }
 
 cudaError_t launch_find(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,

@@ -45,15 +45,8 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   return KF_FIT_OK;
 }
 
-// Status of a track whose FP32 pass met a near-tangent crossing; the
-// careful pass refits it from the start.
-constexpr int FIT_NEEDS_CAREFUL = 2;
-
 template <bool CAREFUL>
-__global__ void __launch_bounds__(128) k_fit(const FitParams P) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= P.ns) return;
-  if (CAREFUL && P.fit_status[t] != FIT_NEEDS_CAREFUL) return;
+__device__ __forceinline__ void fit_track(const FitParams& P, int t) {
   if (!CAREFUL && P.keep && !P.keep[t]) {  // removed as a duplicate: zero outputs
 #pragma unroll
     for (int k = 0; k < 6; ++k) P.fit_p[(size_t)k * P.ns + t] = 0.f;
@@ -84,8 +77,8 @@ __global__ void __launch_bounds__(128) k_fit(const FitParams P) {
       if (k > 0) {
         float cosa = 1.f;
         if (propagate<float>(p, C, g.radius[L], g.kb, INFINITY, &cosa) != 1) { status = KF_FIT_NO_CROSS; break; }
-        if (cosa < CAREFUL_COS) {
-          P.fit_status[t] = FIT_NEEDS_CAREFUL;
+        if (cosa < CAREFUL_COS) {  // leave the track to the careful pass
+          P.careful_list[atomicAdd(P.careful_count, 1u)] = t;
           return;
         }
       }
@@ -115,14 +108,31 @@ __global__ void __launch_bounds__(128) k_fit(const FitParams P) {
   P.fit_status[t] = status;
 }
 
+__global__ void __launch_bounds__(128) k_fit(const FitParams P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < P.ns) fit_track<false>(P, t);
+}
+
+// Second pass over the flagged tracks (grid-stride over their list).
+__global__ void __launch_bounds__(128) k_fit_careful(const FitParams P) {
+  const unsigned n = *P.careful_count;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    fit_track<true>(P, P.careful_list[i]);
+}
+
 }  // namespace
 
 cudaError_t launch_fit(const FitParams& P, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
   const int threads = 128;
   const int blocks = (P.ns + threads - 1) / threads;
-  k_fit<false><<<blocks, threads, 0, st>>>(P);
-  k_fit<true><<<blocks, threads, 0, st>>>(P);
+  cudaError_t e = cudaMemsetAsync(P.careful_count, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  k_fit<<<blocks, threads, 0, st>>>(P);
+  // flagged tracks are a few percent of all: a grid sized for a twentieth of
+  // them, striding over however many there are
+  const int careful_blocks = (P.ns / 20 + threads - 1) / threads + 1;
+  k_fit_careful<<<careful_blocks, threads, 0, st>>>(P);
   return cudaGetLastError();
 }
 

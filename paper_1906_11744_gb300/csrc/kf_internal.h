@@ -101,16 +101,18 @@ struct FitParams {
   float* fit_C;           // [21][ns]
   float* fit_chi2;        // [ns]
   int* fit_status;        // [ns]
+  int* careful_list;      // [ns] tracks refitted with double-precision steps
+  unsigned* careful_count;  // zeroed before the launch
 };
 
 // kf_find.cu
 cudaError_t launch_find(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
                         cudaStream_t st);
-size_t find_smem_bytes(int threads);
+size_t find_smem_bytes(int threads, int n_layers);
 bool find_lanes_supported(int lanes);
 // Sets the dynamic shared-memory limit of the kernel variant (must run
 // outside stream capture) and reports resident blocks per SM.
-cudaError_t find_prepare(int lanes, int regcap, int threads, int* blocks_per_sm);
+cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* blocks_per_sm);
 // kf_bin.cu
 cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsigned first_pos,
                        unsigned* scan_tmp, size_t scan_tmp_elems, cudaStream_t st);
