@@ -194,6 +194,40 @@ int kf_sync(kf_ctx* ctx, void* stream);
 /* Message of the last error on this context (static storage, never NULL). */
 const char* kf_last_error(const kf_ctx* ctx);
 
+/* Limits of kf_remove_duplicates_noalloc (one event per call). */
+#define KF_NOALLOC_MAX_TRACKS 16384
+#define KF_NOALLOC_MAX_HITS 262144
+
+/* Duplicate removal for ONE event without any device allocation.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory at all -- code running inside a host framework
+ * that owns every device allocation through its own pool, a trigger-style
+ * pipeline where cudaMalloc/cudaFree are banned from the hot path because
+ * they synchronize the device, or a plugin held to another library's fixed
+ * memory budget.  It needs no kf_ctx (creating one allocates).
+ *
+ * Same definition as kf_remove_duplicates.  Inputs and the output are device
+ * pointers owned by the caller, read and written in stream order:
+ *   hits     int   [n_tracks][n_layers] event-local hit indices, -1 padded;
+ *            every used index must lie in [0, n_hits);
+ *   n_found  int   [n_tracks] hits per track (<= n_layers);
+ *   chi2     float [n_tracks] chi2 sums (ordering key);
+ *   keep     uint8 [n_tracks] output, 1 = kept;
+ *   status   int   [1] output (may be NULL): 0, or a nonzero device-side
+ *            status when a table of the kernel overflowed.
+ * Scratch lives in a fixed static device array (about 4.2 MB, present on every
+ * device that loads the library until the process exits).  The first call on a
+ * device looks up that array's device address (with the device current); make
+ * that first call before any stream capture.  Every call shares the array, so
+ * calls whose kernels overlap on the GPU race: order them on one stream.
+ * Returns KF_ERR_CAPACITY when n_tracks > KF_NOALLOC_MAX_TRACKS or n_hits >
+ * KF_NOALLOC_MAX_HITS (nothing is launched), KF_ERR_ARG for a bad argument,
+ * KF_ERR_CUDA when the address lookup or a launch fails.  Asynchronous. */
+int kf_remove_duplicates_noalloc(int n_tracks, int n_layers, int n_hits, const int* hits,
+                                 const int* n_found, const float* chi2, float dup_shared_frac,
+                                 unsigned char* keep, int* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

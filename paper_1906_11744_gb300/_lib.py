@@ -26,6 +26,8 @@ KF_FIT_FOUND = 0
 KF_FIT_GIVEN = 1
 KF_FIT_OK = 0
 KF_FIT_SKIPPED = 1
+KF_NOALLOC_MAX_TRACKS = 16384
+KF_NOALLOC_MAX_HITS = 262144
 
 
 class kf_detector(ctypes.Structure):
@@ -69,6 +71,7 @@ _SIGS = {
     "kf_get_stage_ms": ([_P, _P, _P], _I),
     "kf_graph_kernel_count": ([_P, _P], _I),
     "kf_last_error": ([_P], ctypes.c_char_p),
+    "kf_remove_duplicates_noalloc": ([_I, _I, _I, _P, _P, _P, ctypes.c_float, _P, _P, _P], _I),
 }
 
 _lib = None
@@ -260,3 +263,17 @@ def kf_sync(ctx, stream=None):
 
 def kf_last_error(ctx) -> str:
     return load().kf_last_error(ctx).decode()
+
+
+def kf_remove_duplicates_noalloc(n_tracks, n_layers, n_hits, hits, n_found, chi2, dup_shared_frac, keep,
+                                 status=None, stream=None):
+    """Allocation-free duplicate removal of one event; all arrays are CUDA
+    tensors (the caller owns them).  Returns the C return code."""
+    args = [_arg(hits, np.int32), _arg(n_found, np.int32), _arg(chi2, np.float32), _arg(keep, np.uint8),
+            _arg(status, np.int32)]
+    for a in args:
+        if a[2] == 0:
+            raise KFError("kf_remove_duplicates_noalloc takes device arrays only")
+    return load().kf_remove_duplicates_noalloc(int(n_tracks), int(n_layers), int(n_hits), args[0][0], args[1][0],
+                                               args[2][0], float(dup_shared_frac), args[3][0], args[4][0],
+                                               _stream(stream))

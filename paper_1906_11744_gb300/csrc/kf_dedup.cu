@@ -16,6 +16,8 @@
 //      round settles at least the highest-priority undecided track.
 // Scratch (the owner table, the conflict lists and the decision states) lives
 // in global memory owned by the caller.
+#include <mutex>
+
 #include "kf_internal.h"
 
 namespace kfg {
@@ -178,4 +180,96 @@ cudaError_t launch_dedup(const DedupParams& P, int n_events, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free duplicate removal (kf_remove_duplicates_noalloc).
+//
+// Some callers cannot allocate device memory at all: code that runs inside a
+// host framework which owns every device allocation through its own pool, a
+// trigger-style pipeline that forbids cudaMalloc/cudaFree on its hot path
+// because they synchronize the device, or a plugin living within another
+// library's fixed memory budget.  For them the duplicate-removal kernel also
+// runs on a fixed scratch area in a file-scope device array, sized for one
+// event of at most KF_NOALLOC_MAX_TRACKS tracks and KF_NOALLOC_MAX_HITS hits.
+// The array exists once per device that loads the library and stays until the
+// process exits.  Every call shares it: two calls whose kernels overlap on the
+// GPU (different streams, or different host threads) race and give undefined
+// results, so such calls must be ordered.
+namespace {
+
+constexpr size_t NA_CNT_BYTES = ((size_t)(KF_NOALLOC_MAX_HITS + 1) * 4 + 255) / 256 * 256;
+constexpr size_t NA_OWN_BYTES = (size_t)KF_NOALLOC_MAX_TRACKS * KF_MAX_LAYERS * 4;
+constexpr size_t NA_CONF_BYTES = (size_t)KF_NOALLOC_MAX_TRACKS * DEDUP_CONF_CAP * 4;
+constexpr size_t NA_NCONF_BYTES = (size_t)KF_NOALLOC_MAX_TRACKS * 4;
+constexpr size_t NA_STATE_BYTES = ((size_t)KF_NOALLOC_MAX_TRACKS + 255) / 256 * 256;
+constexpr size_t NA_MISC_BYTES = 256;  // event offsets and the status word
+constexpr size_t NA_BYTES =
+    NA_CNT_BYTES + NA_OWN_BYTES + NA_CONF_BYTES + NA_NCONF_BYTES + NA_STATE_BYTES + NA_MISC_BYTES;
+
+static __device__ __align__(256) unsigned char kf_noalloc_scratch[NA_BYTES];
+
+// Device address of the scratch array per device, found once per device.
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex na_mutex;
+unsigned char* na_ptr[NA_MAX_DEVICES] = {};
+
+// Writes the one-event offsets and clears the status words.
+__global__ void k_noalloc_prep(int* misc, int n_tracks, int n_hits, int* user_status) {
+  if (threadIdx.x == 0) {
+    misc[0] = 0;         // seed_off
+    misc[1] = n_tracks;
+    misc[2] = 0;         // hit_off
+    misc[3] = n_hits;
+    misc[4] = ST_OK;     // status
+    if (user_status) *user_status = ST_OK;
+  }
+}
+
+}  // namespace
+
 }  // namespace kfg
+
+extern "C" int kf_remove_duplicates_noalloc(int n_tracks, int n_layers, int n_hits, const int* hits,
+                                            const int* n_found, const float* chi2, float dup_shared_frac,
+                                            unsigned char* keep, int* status, void* stream) {
+  using namespace kfg;
+  if (n_tracks < 0 || n_hits < 0 || n_layers < 1 || n_layers > KF_MAX_LAYERS || !(dup_shared_frac >= 0.f))
+    return KF_ERR_ARG;
+  if (n_tracks > KF_NOALLOC_MAX_TRACKS || n_hits > KF_NOALLOC_MAX_HITS) return KF_ERR_CAPACITY;
+  if (n_tracks == 0) return KF_OK;
+  if (!hits || !n_found || !chi2 || !keep) return KF_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return KF_ERR_CUDA;
+  unsigned char* base;
+  {
+    std::lock_guard<std::mutex> lock(na_mutex);
+    if (!na_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, kf_noalloc_scratch) != cudaSuccess || !p) return KF_ERR_CUDA;
+      na_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    base = na_ptr[dev];
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* misc = reinterpret_cast<int*>(base + NA_BYTES - NA_MISC_BYTES);
+  DedupParams D;
+  D.out_hits = hits;
+  D.out_n = n_found;
+  D.out_chi2 = chi2;
+  D.seed_off = misc;
+  D.hit_off = misc + 2;
+  D.L = n_layers;
+  D.ns = n_tracks;
+  D.frac = dup_shared_frac;
+  D.e_begin = 0;
+  D.hit_cnt = reinterpret_cast<unsigned*>(base);
+  D.owners = reinterpret_cast<int*>(base + NA_CNT_BYTES);
+  D.conf = reinterpret_cast<int*>(base + NA_CNT_BYTES + NA_OWN_BYTES);
+  D.n_conf = reinterpret_cast<int*>(base + NA_CNT_BYTES + NA_OWN_BYTES + NA_CONF_BYTES);
+  D.state = base + NA_CNT_BYTES + NA_OWN_BYTES + NA_CONF_BYTES + NA_NCONF_BYTES;
+  D.keep = keep;
+  D.status = status ? status : misc + 4;
+  k_noalloc_prep<<<1, 32, 0, st>>>(misc, n_tracks, n_hits, status);
+  if (cudaGetLastError() != cudaSuccess) return KF_ERR_CUDA;
+  if (launch_dedup(D, 1, st) != cudaSuccess) return KF_ERR_CUDA;
+  return KF_OK;
+}
