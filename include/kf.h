@@ -139,11 +139,13 @@ int kf_remove_duplicates(kf_ctx* ctx, void* stream);
 int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hits, int max_len,
                   int device_ptrs, void* stream);
 
-/* Gradient of the summed chi2 of the last kf_fit_tracks with respect to the
- * alignment offsets (g_align float [n_layers][2]), hit positions (g_hits
- * float [n_hits][3], global hit order, may be NULL) and seed parameters
- * (g_seed float [6][n_seeds], may be NULL).  Forward states are recomputed
- * from checkpoints every ckpt_stride layers. */
+/* Gradient of the summed chi2 of the last kf_fit_tracks (tracks with status
+ * KF_FIT_OK) with respect to the alignment offsets (g_align float
+ * [n_layers][2]), hit positions (g_hits float [n_hits][3], global hit order,
+ * may be NULL) and seed parameters (g_seed float [6][n_seeds], may be NULL):
+ * the adjoint of the fit, one thread per track.  Forward states are kept
+ * every ckpt_stride hits and recomputed in between; ckpt_stride (1..8) must
+ * satisfy hits per track <= 9 * ckpt_stride (KF_ERR_CAPACITY otherwise). */
 int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs,
                    void* stream);
 
@@ -159,11 +161,18 @@ int kf_get_tracks(kf_ctx* ctx, int* hits, int* n_found, float* chi2, float* para
 int kf_get_fit(kf_ctx* ctx, float* params, float* cov, float* chi2, int* status, int device_ptrs,
                void* stream);
 
-/* Capture find + duplicate removal + fit (+ adjoint if with_adjoint) on the
- * stream into a CUDA graph owned by the context; kf_launch_graph replays it.
- * Loads between launches must not grow any buffer. */
+/* Capture find + duplicate removal + fit (+ the adjoint of the fit if
+ * with_adjoint, its gradients kept in the context for kf_get_gradient) on
+ * the stream into a CUDA graph owned by the context; kf_launch_graph replays
+ * it.  stream must not be the legacy default stream.  Loads between launches
+ * must not grow any buffer. */
 int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream);
 int kf_launch_graph(kf_ctx* ctx, void* stream);
+
+/* Copy out the gradients kept by a graph with the adjoint (or by the last
+ * kf_fit_adjoint called with host pointers): g_align float [n_layers][2],
+ * g_hits float [n_hits][3], g_seed float [6][n_seeds]; any may be NULL. */
+int kf_get_gradient(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs, void* stream);
 
 /* Time every lanes-per-seed / block-size / register-budget / launch-form
  * choice of the finding kernel on the loaded inputs and keep the fastest in

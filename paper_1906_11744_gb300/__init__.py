@@ -27,6 +27,7 @@ from ._lib import (  # noqa: F401
     kf_fit_tracks,
     kf_get_counters,
     kf_get_fit,
+    kf_get_gradient,
     kf_get_stage_ms,
     kf_get_tracks,
     kf_graph_kernel_count,

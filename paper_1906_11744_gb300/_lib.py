@@ -71,6 +71,7 @@ _SIGS = {
     "kf_get_stage_ms": ([_P, _P, _P], _I),
     "kf_graph_kernel_count": ([_P, _P], _I),
     "kf_last_error": ([_P], ctypes.c_char_p),
+    "kf_get_gradient": ([_P, _P, _P, _P, _I, _P], _I),
     "kf_remove_duplicates_noalloc": ([_I, _I, _I, _P, _P, _P, ctypes.c_float, _P, _P, _P], _I),
 }
 
@@ -202,6 +203,12 @@ def kf_fit_adjoint(ctx, g_align, g_hits=None, g_seed=None, stream=None):
     ps, ks, fs = _arg(g_seed, np.float32)
     rc = load().kf_fit_adjoint(ctx, pa, ph, ps, _flag(fa, fh, fs), _stream(stream))
     _check(ctx, rc, "kf_fit_adjoint")
+
+
+def kf_get_gradient(ctx, g_align=None, g_hits=None, g_seed=None, stream=None):
+    args = [_arg(g_align, np.float32), _arg(g_hits, np.float32), _arg(g_seed, np.float32)]
+    rc = load().kf_get_gradient(ctx, *[a[0] for a in args], _flag(*[a[2] for a in args]), _stream(stream))
+    _check(ctx, rc, "kf_get_gradient")
 
 
 def kf_get_tracks(ctx, hits=None, n_found=None, chi2=None, params=None, cov=None, keep=None, stream=None):

@@ -44,6 +44,8 @@ struct kf_ctx {
   int given_max_len = 0;
   bool found = false, deduped = false, fitted = false;
   int fit_source = KF_FIT_FOUND;
+  FitParams last_fit;
+  DevBuf adj_align_acc, adj_align, adj_hits, adj_seed;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int stage_timing = 0;
@@ -120,6 +122,22 @@ int auto_lanes(int n) {
 }
 
 }  // namespace
+
+static int check_status(kf_ctx* ctx, cudaStream_t st) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h == ST_OK) return KF_OK;
+  CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  switch (h) {
+    case ST_DEDUP_PARTNERS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: partner table overflow");
+    case ST_DEDUP_CONFLICTS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: conflict table overflow");
+    case ST_DEDUP_ROUNDS: return fail(ctx, KF_ERR_TIMEOUT, "duplicate removal: resolution did not settle");
+    default: return fail(ctx, KF_ERR_CUDA, "unknown device status");
+  }
+}
+static int check_status_sync(kf_ctx* ctx, cudaStream_t st) { return check_status(ctx, st); }
 
 extern "C" {
 
@@ -221,7 +239,8 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
-                    &ctx->careful_count};
+                    &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
+                    &ctx->adj_seed};
   for (DevBuf* b : bufs) release(*b);
   delete ctx;
   return KF_OK;
@@ -537,31 +556,63 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   stage_mark(ctx, 6, st);
   CK(launch_fit(F, st));
   stage_mark(ctx, 7, st);
+  ctx->last_fit = F;
   ctx->fitted = true;
   ctx->fit_source = source;
   return KF_OK;
 }
 
 int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs, void* stream) {
-  (void)g_align; (void)g_hits; (void)g_seed; (void)device_ptrs; (void)stream;
   if (!ctx) return KF_ERR_ARG;
-  return fail(ctx, KF_ERR_STATE, "kf_fit_adjoint: not available in this build");
+  if (!ctx->fitted) return fail(ctx, KF_ERR_STATE, "kf_fit_adjoint: run kf_fit_tracks first");
+  if (!g_align) return fail(ctx, KF_ERR_ARG, "kf_fit_adjoint: g_align is required");
+  const FitParams& F = ctx->last_fit;
+  const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : 4;
+  if (!adjoint_stride_ok(stride, F.max_len))
+    return fail(ctx, KF_ERR_CAPACITY, "kf_fit_adjoint: ckpt_stride must be 1..8 with hits per track <= 9 * stride");
+  cudaStream_t st = S(stream);
+  const size_t ns = (size_t)ctx->n_seeds, nh = (size_t)ctx->n_hits;
+  CK(grow(ctx->adj_align_acc, sizeof(double) * 2 * KF_MAX_LAYERS));
+  CK(grow(ctx->adj_align, sizeof(float) * 2 * KF_MAX_LAYERS));
+  if (!device_ptrs) {
+    if (g_hits) CK(grow(ctx->adj_hits, sizeof(float) * 3 * nh));
+    if (g_seed) CK(grow(ctx->adj_seed, sizeof(float) * 6 * ns));
+  }
+  AdjParams A;
+  A.g = ctx->g;
+  A.hx = F.hx;
+  A.hy = F.hy;
+  A.hz = F.hz;
+  A.hlayer = F.hlayer;
+  A.hit_off = F.hit_off;
+  A.sp = F.sp;
+  A.sc = F.sc;
+  A.seed_event = F.seed_event;
+  A.align = F.align;
+  A.ns = F.ns;
+  A.n_hits = ctx->n_hits;
+  A.lists = F.lists;
+  A.n_list = F.n_list;
+  A.max_len = F.max_len;
+  A.keep = F.keep;
+  A.fit_status = F.fit_status;
+  A.stride = stride;
+  A.g_hits = g_hits ? (device_ptrs ? g_hits : ptr<float>(ctx->adj_hits)) : nullptr;
+  A.g_seed = g_seed ? (device_ptrs ? g_seed : ptr<float>(ctx->adj_seed)) : nullptr;
+  A.g_align = device_ptrs ? g_align : ptr<float>(ctx->adj_align);
+  A.g_align_acc = ptr<double>(ctx->adj_align_acc);
+  A.careful_list = F.careful_list;
+  A.careful_count = F.careful_count;
+  CK(launch_adjoint(A, st));
+  if (!device_ptrs) {
+    CK(cudaMemcpyAsync(g_align, A.g_align, sizeof(float) * 2 * ctx->g.n_layers, cudaMemcpyDeviceToHost, st));
+    if (g_hits) CK(cudaMemcpyAsync(g_hits, A.g_hits, sizeof(float) * 3 * nh, cudaMemcpyDeviceToHost, st));
+    if (g_seed) CK(cudaMemcpyAsync(g_seed, A.g_seed, sizeof(float) * 6 * ns, cudaMemcpyDeviceToHost, st));
+    return check_status_sync(ctx, st);
+  }
+  return KF_OK;
 }
 
-static int check_status(kf_ctx* ctx, cudaStream_t st) {
-  int h = 0;
-  CK(cudaMemcpyAsync(&h, ctx->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (h == ST_OK) return KF_OK;
-  CK(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), st));
-  CK(cudaStreamSynchronize(st));
-  switch (h) {
-    case ST_DEDUP_PARTNERS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: partner table overflow");
-    case ST_DEDUP_CONFLICTS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: conflict table overflow");
-    case ST_DEDUP_ROUNDS: return fail(ctx, KF_ERR_TIMEOUT, "duplicate removal: resolution did not settle");
-    default: return fail(ctx, KF_ERR_CUDA, "unknown device status");
-  }
-}
 
 int kf_sync(kf_ctx* ctx, void* stream) {
   if (!ctx) return KF_ERR_ARG;
@@ -648,15 +699,23 @@ int kf_graph_kernel_count(kf_ctx* ctx, int* n_kernels) {
 
 int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   if (!ctx) return KF_ERR_ARG;
-  if (with_adjoint) return fail(ctx, KF_ERR_STATE, "kf_capture_graph: adjoint not available in this build");
   cudaStream_t st = S(stream);
   if (!st) return fail(ctx, KF_ERR_ARG, "kf_capture_graph: capture needs a non-default stream");
   if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
   if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  if (with_adjoint) {  // every buffer the captured work uses exists before capture starts
+    CK(grow(ctx->adj_align_acc, sizeof(double) * 2 * KF_MAX_LAYERS));
+    CK(grow(ctx->adj_align, sizeof(float) * 2 * KF_MAX_LAYERS));
+    CK(grow(ctx->adj_hits, sizeof(float) * 3 * (size_t)ctx->n_hits));
+    CK(grow(ctx->adj_seed, sizeof(float) * 6 * (size_t)ctx->n_seeds));
+  }
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = kf_find_tracks(ctx, stream);
   if (rc == KF_OK) rc = kf_remove_duplicates(ctx, stream);
   if (rc == KF_OK) rc = kf_fit_tracks(ctx, KF_FIT_FOUND, nullptr, nullptr, 0, 1, stream);
+  if (rc == KF_OK && with_adjoint)  // gradient into context buffers; kf_get_gradient reads them
+    rc = kf_fit_adjoint(ctx, ptr<float>(ctx->adj_align), ptr<float>(ctx->adj_hits), ptr<float>(ctx->adj_seed), 1,
+                        stream);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(st, &graph);
   if (rc != KF_OK) {
@@ -666,6 +725,25 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   if (e != cudaSuccess) return fail(ctx, KF_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
   ctx->graph = graph;
   CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, 0));
+  return KF_OK;
+}
+
+int kf_get_gradient(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (!ctx->adj_align.p) return fail(ctx, KF_ERR_STATE, "kf_get_gradient: no gradient computed");
+  cudaStream_t st = S(stream);
+  if (g_align) CK(get(g_align, ctx->adj_align.p, sizeof(float) * 2 * ctx->g.n_layers, device_ptrs, st));
+  if (g_hits) {
+    if (ctx->adj_hits.bytes < sizeof(float) * 3 * (size_t)ctx->n_hits)
+      return fail(ctx, KF_ERR_STATE, "kf_get_gradient: no hit gradient kept");
+    CK(get(g_hits, ctx->adj_hits.p, sizeof(float) * 3 * (size_t)ctx->n_hits, device_ptrs, st));
+  }
+  if (g_seed) {
+    if (ctx->adj_seed.bytes < sizeof(float) * 6 * (size_t)ctx->n_seeds)
+      return fail(ctx, KF_ERR_STATE, "kf_get_gradient: no seed gradient kept");
+    CK(get(g_seed, ctx->adj_seed.p, sizeof(float) * 6 * (size_t)ctx->n_seeds, device_ptrs, st));
+  }
+  if (!device_ptrs) return check_status(ctx, st);
   return KF_OK;
 }
 

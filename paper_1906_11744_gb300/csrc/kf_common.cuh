@@ -257,7 +257,8 @@ __device__ __forceinline__ bool crossing(const float (&p)[6], float R, float kb,
 // untouched unless 1 is returned.  cos_out (optional) receives |cos| of the
 // angle between the direction and the radial direction at the crossing.
 template <class T>
-__device__ __forceinline__ int propagate(T (&p)[6], T (&C)[21], T R, T kb, T z_lim, T* cos_out = nullptr) {
+__device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim, T (&q)[6], T (&J)[6][6],
+                                             T* cos_out = nullptr) {
   const T x = p[0], y = p[1], kap = p[3], phi = p[4], th = p[5];
   T sf, cf;
   ksincos(phi, &sf, &cf);
@@ -291,17 +292,28 @@ __device__ __forceinline__ int propagate(T (&p)[6], T (&C)[21], T R, T kb, T z_l
   const T ds0 = xn * inv, ds1 = yn * inv;
   const T ds3 = kfma(xn, Fx3, yn * Fy3) * inv;
   const T ds4 = kfma(xn, Fx4, yn * Fy4) * inv;
-  T J[6][6];
   J[0][0] = kfma(cp, ds0, T(1)); J[0][1] = cp * ds1; J[0][3] = kfma(cp, ds3, Fx3); J[0][4] = kfma(cp, ds4, Fx4);
   J[1][0] = sp * ds0; J[1][1] = kfma(sp, ds1, T(1)); J[1][3] = kfma(sp, ds3, Fy3); J[1][4] = kfma(sp, ds4, Fy4);
   J[2][0] = cot * ds0; J[2][1] = cot * ds1; J[2][3] = cot * ds3; J[2][4] = cot * ds4;
   J[2][5] = -s / (sth * sth);
   J[4][0] = h * ds0; J[4][1] = h * ds1; J[4][3] = kfma(h, ds3, kb * s); J[4][4] = kfma(h, ds4, T(1));
+  q[0] = xn;
+  q[1] = yn;
+  q[2] = zn;
+  q[3] = kap;
+  q[4] = phi + psi;
+  q[5] = th;
+  return 1;
+}
+
+template <class T>
+__device__ __forceinline__ int propagate(T (&p)[6], T (&C)[21], T R, T kb, T z_lim, T* cos_out = nullptr) {
+  T q[6], J[6][6];
+  const int rc = prop_jacobian<T>(p, R, kb, z_lim, q, J, cos_out);
+  if (rc != 1) return rc;
   transport<T>(J, C);
-  p[0] = xn;
-  p[1] = yn;
-  p[2] = zn;
-  p[4] = phi + psi;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = q[k];
   return 1;
 }
 
@@ -370,6 +382,27 @@ __device__ __forceinline__ void kf_update(T (&p)[6], T (&C)[21], const FrameT<T>
 
 // Thin-scatterer multiple scattering (Highland width, pion mass for beta):
 // Var(phi) += theta0^2 / sin^2(theta), Var(theta) += theta0^2.
+// The two variance terms (phi-phi, theta-theta) the scattering adds.
+template <class T>
+__device__ __forceinline__ void ms_terms(const T (&p)[6], T x0, T& q44, T& q55) {
+  if (p[3] == T(0) || x0 <= T(0)) {
+    q44 = T(0);
+    q55 = T(0);
+    return;
+  }
+  T sth, cth, sph, cph;
+  ksincos(p[5], &sth, &cth);
+  ksincos(p[4], &sph, &cph);
+  const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
+  const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;  // cos(phi - phi_p)
+  const T pm = T(1) / (kabs(p[3]) * sth);
+  const T beta = pm / ksqrt(kfma(pm, pm, T(MPION * MPION)));
+  const T t = x0 / kabs(sth * cdiff);
+  const T th0 = T(0.0136) / (beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
+  q55 = th0 * th0;
+  q44 = q55 / (sth * sth);
+}
+
 template <class T>
 __device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
   if (p[3] == T(0) || x0 <= T(0)) return;

@@ -105,6 +105,36 @@ struct FitParams {
   unsigned* careful_count;  // zeroed before the launch
 };
 
+struct AdjParams {
+  DevGeom g;
+  const float* hx;
+  const float* hy;
+  const float* hz;
+  const int* hlayer;
+  const int* hit_off;
+  const float* sp;
+  const float* sc;
+  const int* seed_event;
+  const Align4* align;
+  int ns;
+  int n_hits;
+  const int* lists;
+  const int* n_list;
+  int max_len;
+  const unsigned char* keep;   // may be null
+  const int* fit_status;       // tracks with a status other than KF_FIT_OK are skipped
+  int stride;                  // checkpoint stride
+  float* g_hits;               // [n_hits][3] or null
+  float* g_seed;               // [6][ns] or null
+  float* g_align;              // [n_layers][2]
+  double* g_align_acc;         // [2 * KF_MAX_LAYERS] accumulator
+  int* careful_list;
+  unsigned* careful_count;
+};
+
+// kf_adjoint.cu
+cudaError_t launch_adjoint(const AdjParams& P, cudaStream_t st);
+bool adjoint_stride_ok(int stride, int max_len);
 // kf_find.cu
 cudaError_t launch_find(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
                         cudaStream_t st);
