@@ -3,7 +3,9 @@
 Workload: PU-200-like batch, 100 events x 8,000 generated tracks, 17 barrel
 layers, 20% noise hits, up to 10 candidates per seed (synthetic, seeded).
 One step = bin hits, find tracks for every seed, remove duplicates, re-fit the
-kept tracks, replayed as one captured CUDA graph over the whole batch.
+kept tracks and take the gradient of their summed chi2 with respect to the
+layer alignment offsets (adjoint of the fit), replayed as one captured CUDA
+graph over the whole batch.
 
 Prints one JSON line: seeds/s (whole job), candidate-layer steps/s, the plain
 per-event launch form for comparison, the end-to-end rate through the C ABI
@@ -128,8 +130,9 @@ def tracker_for(b, **cfg):
 
 
 def oracle_sample(b, budget_s=15.0):
-    """The FP64 oracle (find + duplicate removal + re-fit, one host core) on
-    whole events of the batch until about budget_s seconds of work."""
+    """The FP64 oracle (find + duplicate removal + re-fit with the gradient of
+    the summed chi2, one host core) on whole events of the batch until about
+    budget_s seconds of work."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
@@ -142,7 +145,7 @@ def oracle_sample(b, budget_s=15.0):
         x, y, z, lay = b.event_hits(e)
         prm, cov, sh = b.event_seeds(e)
         k = np.nonzero(keep)[0]
-        oracle.fit(b.det, prm[:, k], cov[:, k], r["hits"][k], r["n_found"][k], x, y, z, lay, align=b.align)
+        oracle.fit_grad(b.det, prm[:, k], cov[:, k], r["hits"][k], r["n_found"][k], x, y, z, lay, b.align)
         seeds += prm.shape[1]
         steps += r["counters"]["steps"]
         events += 1
@@ -150,7 +153,7 @@ def oracle_sample(b, budget_s=15.0):
             break
     dt = time.perf_counter() - t0
     return dict(value=seeds / dt, unit=UNIT, cores=1, kind="oracle", seconds=dt,
-                sample=f"{events} of {b.n_events} events ({seeds} seeds), find + dedup + fit, FP64, 1 thread",
+                sample=f"{events} of {b.n_events} events ({seeds} seeds), find + dedup + fit + chi2 gradient, FP64, 1 thread",
                 steps_per_s=steps / dt)
 
 
@@ -231,7 +234,7 @@ def main():
     if not args.no_autotune:
         tune = t.autotune(stream)
     t.set_stage_timing(True)
-    t.capture_graph(stream=stream)
+    t.capture_graph(with_adjoint=True, stream=stream)
     n_kernels = t.graph_kernel_count()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -246,7 +249,7 @@ def main():
 
     ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage = {"bin": 0.0, "find": 0.0, "dedup": 0.0, "fit": 0.0}
+    stage = {"bin": 0.0, "find": 0.0, "dedup": 0.0, "fit": 0.0, "adjoint": 0.0}
     clocks = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
@@ -293,10 +296,13 @@ def main():
         tp.load_seeds(b.seed_off, d_in["params"], d_in["cov"], d_in["seed_hits"], stream)
         tp.set_alignment(b.align, stream)
 
+        g_plain = torch.empty((b.det.n_layers, 2), dtype=torch.float32, device=dev)
+
         def plain_step():
             tp.find_tracks(stream)
             tp.remove_duplicates(stream)
             tp.fit_tracks(KF_FIT_FOUND, stream=stream)
+            tp.fit_adjoint(g_plain, stream=stream)
 
         for _ in range(args.warmup):
             plain_step()
@@ -311,7 +317,8 @@ def main():
         stream.synchronize()
         pms = sum(a.elapsed_time(bb) for a, bb in zip(pa, pb))
         plain = {"value": seeds_all * args.steps / (pms / 1e3), "unit": UNIT,
-                 "ms_per_step": pms / args.steps, "form": "per-event launches of bin/find/dedup, one fit, no graph"}
+                 "ms_per_step": pms / args.steps,
+                 "form": "per-event launches of bin/find/dedup, one fit and one adjoint launch, no graph"}
         tp.close()
 
     # end to end through the C ABI with host buffers (pinned), host<->device copies inside
@@ -328,7 +335,8 @@ def main():
         fouts = dict(params=torch.empty((6, n_seeds), dtype=torch.float32).pin_memory(),
                      chi2=torch.empty(n_seeds, dtype=torch.float32).pin_memory(),
                      status=torch.empty(n_seeds, dtype=torch.int32).pin_memory())
-        from paper_1906_11744_gb300 import kf_get_fit, kf_get_tracks
+        g_host = torch.empty((b.det.n_layers, 2), dtype=torch.float32).pin_memory()
+        from paper_1906_11744_gb300 import kf_get_fit, kf_get_gradient, kf_get_tracks
 
         def e2e_step():
             t.load_hits(b.hit_off, h["x"], h["y"], h["z"], h["layer"], stream)
@@ -336,6 +344,7 @@ def main():
             t.launch_graph(stream)
             kf_get_tracks(t.ctx, **outs, stream=stream)
             kf_get_fit(t.ctx, **fouts, stream=stream)
+            kf_get_gradient(t.ctx, g_align=g_host, stream=stream)
 
         for _ in range(2):
             e2e_step()
@@ -351,7 +360,7 @@ def main():
             e2e_s = float(tm.item())
         bi = sum(v.numel() * v.element_size() for v in h.values())
         bo = sum(v.numel() * v.element_size() for v in outs.values()) + \
-            sum(v.numel() * v.element_size() for v in fouts.values())
+            sum(v.numel() * v.element_size() for v in fouts.values()) + g_host.numel() * 4
         e2e = {"value": seeds_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * e2e_s / args.steps}
 
@@ -366,7 +375,7 @@ def main():
                "config": {"workload": workload_desc(args.config) + (f" (events={args.events})" if args.events else ""),
                           "seeds_per_gpu": n_seeds, "hits_per_gpu": b.n_hits,
                           "l2": "flushed (2x L2 write) before every timed step",
-                          "launch": "one CUDA graph per step: bin(5 kernels) + find + dedup + fit",
+                          "launch": "one CUDA graph per step: bin (5 kernels) + find + dedup + fit (2) + alignment-gradient adjoint (3)",
                           "autotuned": None if tune is None else {
                               "lanes_per_seed": int(tune[np.argmin(tune[:, 4])][0]),
                               "block_threads": int(tune[np.argmin(tune[:, 4])][1]),

@@ -188,11 +188,12 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
 int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream);
 
 /* Stage timing: with enable = 1, CUDA events are recorded around the
- * binning, finding, duplicate removal and fit launches (also inside a
- * captured graph).  kf_get_stage_ms (synchronous) returns the durations of
- * the last completed run: ms4 = {bin, find, dedup, fit}. */
+ * binning, finding, duplicate removal, fit and adjoint launches (also inside
+ * a captured graph).  kf_get_stage_ms (synchronous) returns the durations of
+ * the last completed run: ms5 = {bin, find, dedup, fit, adjoint}; a stage
+ * that did not run reads -1. */
 int kf_set_stage_timing(kf_ctx* ctx, int enable);
-int kf_get_stage_ms(kf_ctx* ctx, float* ms4, void* stream);
+int kf_get_stage_ms(kf_ctx* ctx, float* ms5, void* stream);
 
 /* Number of kernel nodes in the captured graph (launches per replay). */
 int kf_graph_kernel_count(kf_ctx* ctx, int* n_kernels);

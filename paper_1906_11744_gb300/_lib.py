@@ -253,9 +253,9 @@ def kf_set_stage_timing(ctx, enable=True):
 
 
 def kf_get_stage_ms(ctx, stream=None):
-    ms = np.zeros(4, np.float32)
+    ms = np.zeros(5, np.float32)
     _check(ctx, load().kf_get_stage_ms(ctx, ms.ctypes.data_as(_P), _stream(stream)), "kf_get_stage_ms")
-    return dict(bin=float(ms[0]), find=float(ms[1]), dedup=float(ms[2]), fit=float(ms[3]))
+    return dict(bin=float(ms[0]), find=float(ms[1]), dedup=float(ms[2]), fit=float(ms[3]), adjoint=float(ms[4]))
 
 
 def kf_graph_kernel_count(ctx):

@@ -49,7 +49,7 @@ struct kf_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int stage_timing = 0;
-  cudaEvent_t ev[8] = {};  // bin start/end, find start/end, dedup start/end, fit start/end
+  cudaEvent_t ev[10] = {};  // start/end of bin, find, dedup, fit, adjoint
   std::string err = "";
 };
 
@@ -603,7 +603,9 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   A.g_align_acc = ptr<double>(ctx->adj_align_acc);
   A.careful_list = F.careful_list;
   A.careful_count = F.careful_count;
+  stage_mark(ctx, 8, st);
   CK(launch_adjoint(A, st));
+  stage_mark(ctx, 9, st);
   if (!device_ptrs) {
     CK(cudaMemcpyAsync(g_align, A.g_align, sizeof(float) * 2 * ctx->g.n_layers, cudaMemcpyDeviceToHost, st));
     if (g_hits) CK(cudaMemcpyAsync(g_hits, A.g_hits, sizeof(float) * 3 * nh, cudaMemcpyDeviceToHost, st));
@@ -667,14 +669,14 @@ int kf_set_stage_timing(kf_ctx* ctx, int enable) {
   return KF_OK;
 }
 
-int kf_get_stage_ms(kf_ctx* ctx, float* ms4, void* stream) {
-  if (!ctx || !ms4) return KF_ERR_ARG;
+int kf_get_stage_ms(kf_ctx* ctx, float* ms5, void* stream) {
+  if (!ctx || !ms5) return KF_ERR_ARG;
   if (!ctx->stage_timing) return fail(ctx, KF_ERR_STATE, "kf_get_stage_ms: stage timing is off");
   CK(cudaStreamSynchronize(S(stream)));
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) != cudaSuccess) ms = -1.f;
-    ms4[k] = ms;
+    ms5[k] = ms;
   }
   cudaGetLastError();  // an event that never ran leaves a benign error
   return KF_OK;
