@@ -2,10 +2,11 @@
 // positions, seed parameters), one thread per track.
 //
 // Forward: the fit of kf_fit.cu (prior at the first hit; per hit: propagate,
-// tangent-frame measurement, chi2, update, scattering except after the last),
-// keeping the state (p, C) every `stride` hits as a checkpoint.  Reverse: for
-// each segment from the last, the states before each step are recomputed from
-// the segment's checkpoint, then the steps are reversed one by one:
+// tangent-frame measurement, chi2, update, scattering except after the last)
+// writes the state (p, C) before every `stride`-th hit as a checkpoint.
+// Reverse: for each segment from the last, the states before each step are
+// recomputed from the segment's checkpoint, then the steps are reversed one
+// by one:
 //   * scattering C += Q(p): dQ/dp by forward-mode dual numbers (5 directions);
 //   * update and chi2 with U = C H^T, S = H U + V, K = U S^-1,
 //       p' = p + U S^-1 r,  C' = C - U S^-1 U^T,  chi2 = r^T S^-1 r,
@@ -16,8 +17,10 @@
 //     pbar <- J^T pbar' + sum_ij Jbar_ij dJ_ij/dp with Jbar = 2 Cbar' J C and
 //     dJ/dp from the same propagation code run on dual numbers.
 // The adjoint of the final state is zero: the objective is the chi2 sum.
-// Tracks with a near-tangent crossing are left to a second pass in double
-// precision, as in the fit.
+// Tracks the fit flagged for a near-tangent crossing go to a second pass that
+// keeps their adjoints in double and runs the near-tangent steps in double.
+#include <type_traits>
+
 #include "kf_dual.cuh"
 #include "kf_internal.h"
 
@@ -306,14 +309,62 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   for (int i = 0; i < 6; ++i) pb[i] = pin[i];
 }
 
-constexpr int MAX_CK = 9;   // checkpoints per track
-constexpr int MAX_SEG = 8;  // stride limit
+// Whether step k of a track (from the state before it) crosses its layer
+// close to tangentially; the careful pass runs such steps in double.
+__device__ __forceinline__ bool near_tangent(const DevGeom& g, const float (&p)[6], float R) {
+  float zc, cosa;
+  if (!crossing(p, R, g.kb, zc, cosa)) return false;
+  return cosa < ADJ_CAREFUL_COS;
+}
 
-template <class S, bool CAREFUL>
+// Forward step in precision S on float storage.
+template <class S>
+__device__ __noinline__ void fwd_step_store(const DevGeom& g, float* st, const Hit<S>& h, bool first, bool last) {
+  S p[6], C[21];
+  for (int q = 0; q < 6; ++q) p[q] = (S)st[q];
+  for (int q = 0; q < 21; ++q) C[q] = (S)st[6 + q];
+  fwd_step<S>(g, p, C, h, first, last);
+  for (int q = 0; q < 6; ++q) st[27 + q] = (float)p[q];
+  for (int q = 0; q < 21; ++q) st[27 + 6 + q] = (float)C[q];
+}
+
+// Reverse step in precision S with the adjoints kept in A (double in the
+// careful pass, float otherwise).
+template <class S, class A>
+__device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, const Hit<S>& h, bool first,
+                                            bool last, A (&pbA)[6], A (&CbA)[6][6], A (&hbA)[3], A (&abA)[2]) {
+  S p[6], C[21], pb[6], Cb[6][6], hb[3], ab[2];
+  for (int q = 0; q < 6; ++q) p[q] = (S)st[q];
+  for (int q = 0; q < 21; ++q) C[q] = (S)st[6 + q];
+  for (int i = 0; i < 6; ++i) {
+    pb[i] = (S)pbA[i];
+    for (int j = 0; j < 6; ++j) Cb[i][j] = (S)CbA[i][j];
+  }
+  rev_step<S>(g, p, C, h, first, last, pb, Cb, hb, ab);
+  for (int i = 0; i < 6; ++i) {
+    pbA[i] = (A)pb[i];
+    for (int j = 0; j < 6; ++j) CbA[i][j] = (A)Cb[i][j];
+  }
+  for (int i = 0; i < 3; ++i) hbA[i] = (A)hb[i];
+  for (int i = 0; i < 2; ++i) abA[i] = (A)ab[i];
+}
+
+// Reverse sweep of one fitted track from the fit's checkpoints.  CAREFUL:
+// the track the fit flagged as near-tangent; its near-tangent steps run in
+// double precision and its adjoints are kept in double.
+template <bool CAREFUL>
 __device__ void adjoint_track(const AdjParams& P, int t, double* sh_align) {
+  using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
-  if (!CAREFUL && ((P.keep && !P.keep[t]) || P.fit_status[t] != KF_FIT_OK)) {
-    if (P.g_seed)  // not fitted: no contribution
+  if (!CAREFUL) {
+    if ((P.keep && !P.keep[t]) || P.fit_status[t] != KF_FIT_OK) {
+      if (P.g_seed)  // not fitted: no contribution
+        for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
+      return;
+    }
+    if (P.careful_flag[t]) return;  // left to the careful pass
+  } else if (P.fit_status[t] != KF_FIT_OK) {
+    if (P.g_seed)
       for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
     return;
   }
@@ -321,84 +372,70 @@ __device__ void adjoint_track(const AdjParams& P, int t, double* sh_align) {
   const int* lst = P.lists + (size_t)t * P.max_len;
   const int hoff = P.hit_off[P.seed_event[t]];
   const int stride = P.stride;
-  S p[6], C[21];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) p[k] = (S)P.sp[(size_t)k * P.ns + t];
-#pragma unroll
-  for (int k = 0; k < 21; ++k) C[k] = (S)P.sc[(size_t)k * P.ns + t];
-  S ck[MAX_CK][27];
-  for (int k = 0; k < n; ++k) {
-    if (k % stride == 0) {
-      const int c = k / stride;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) ck[c][q] = p[q];
-#pragma unroll
-      for (int q = 0; q < 21; ++q) ck[c][6 + q] = C[q];
-    }
-    const Hit<S> h = load_hit<S>(P, hoff + lst[k]);
-    const int st = fwd_step<S>(g, p, C, h, k == 0, k + 1 == n);
-    if (st == 99) {  // near-tangent: redo this track in double precision
-      P.careful_list[atomicAdd(P.careful_count, 1u)] = t;
-      return;
-    }
-    if (st != KF_FIT_OK) return;
-  }
-  S pb[6], Cb[6][6];
-#pragma unroll
+  A pb[6], Cb[6][6];
   for (int i = 0; i < 6; ++i) {
-    pb[i] = S(0);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) Cb[i][j] = S(0);
+    pb[i] = A(0);
+    for (int j = 0; j < 6; ++j) Cb[i][j] = A(0);
   }
-  S seg[MAX_SEG][27];
+  float seg[(MAX_CKPT_STRIDE + 1) * 27];  // states before each step of a segment
   for (int c = (n - 1) / stride; c >= 0; --c) {
     const int k0 = c * stride, k1 = min(n, k0 + stride);
-    for (int q = 0; q < 27; ++q) seg[0][q] = ck[c][q];
-    for (int k = k0; k + 1 < k1; ++k) {  // states before each step of the segment
-      S ps[6], Cs[21];
-      for (int q = 0; q < 6; ++q) ps[q] = seg[k - k0][q];
-      for (int q = 0; q < 21; ++q) Cs[q] = seg[k - k0][6 + q];
-      const Hit<S> h = load_hit<S>(P, hoff + lst[k]);
-      fwd_step<S>(g, ps, Cs, h, k == 0, k + 1 == n);
-      for (int q = 0; q < 6; ++q) seg[k - k0 + 1][q] = ps[q];
-      for (int q = 0; q < 21; ++q) seg[k - k0 + 1][6 + q] = Cs[q];
+    const float* ck = P.ckpt + (size_t)c * 27 * P.ns + t;
+    for (int q = 0; q < 27; ++q) seg[q] = ck[(size_t)q * P.ns];
+    for (int k = k0; k + 1 < k1; ++k) {
+      float* st = seg + (k - k0) * 27;
+      const int hi = hoff + lst[k];
+      if (CAREFUL && k > 0) {
+        float pf[6];
+        for (int q = 0; q < 6; ++q) pf[q] = st[q];
+        if (near_tangent(g, pf, g.radius[P.hlayer[hi]])) {
+          fwd_step_store<double>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n);
+          continue;
+        }
+      }
+      fwd_step_store<float>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      S ps[6], Cs[21];
-      for (int q = 0; q < 6; ++q) ps[q] = seg[k - k0][q];
-      for (int q = 0; q < 21; ++q) Cs[q] = seg[k - k0][6 + q];
+      const float* st = seg + (k - k0) * 27;
       const int hl = lst[k];
-      const Hit<S> h = load_hit<S>(P, hoff + hl);
-      S hb[3], ab[2];
-      rev_step<S>(g, ps, Cs, h, k == 0, k + 1 == n, pb, Cb, hb, ab);
+      const int hi = hoff + hl;
+      A hb[3], ab[2];
+      bool dbl = false;
+      if (CAREFUL && k > 0) {
+        float pf[6];
+        for (int q = 0; q < 6; ++q) pf[q] = st[q];
+        dbl = near_tangent(g, pf, g.radius[P.hlayer[hi]]);
+      }
+      if (dbl) rev_step_store<double, A>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb, ab);
+      else rev_step_store<float, A>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb, ab);
       if (P.g_hits) {
-        float* gh = P.g_hits + 3 * ((size_t)hoff + hl);
+        float* gh = P.g_hits + 3 * (size_t)hi;
         atomicAdd(gh + 0, (float)hb[0]);
         atomicAdd(gh + 1, (float)hb[1]);
         atomicAdd(gh + 2, (float)hb[2]);
       }
-      atomicAdd(sh_align + 2 * h.L, (double)ab[0]);
-      atomicAdd(sh_align + 2 * h.L + 1, (double)ab[1]);
+      const int L = P.hlayer[hi];
+      atomicAdd(sh_align + 2 * L, (double)ab[0]);
+      atomicAdd(sh_align + 2 * L + 1, (double)ab[1]);
     }
   }
   if (P.g_seed) {
-#pragma unroll
     for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = (float)pb[k];
   }
 }
 
-template <class S, bool CAREFUL>
+template <bool CAREFUL>
 __global__ void __launch_bounds__(128) k_adjoint(const AdjParams P) {
   __shared__ double sh_align[2 * KF_MAX_LAYERS];
   for (int i = threadIdx.x; i < 2 * KF_MAX_LAYERS; i += blockDim.x) sh_align[i] = 0.0;
   __syncthreads();
   if (!CAREFUL) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.ns) adjoint_track<S, false>(P, t, sh_align);
+    if (t < P.ns) adjoint_track<false>(P, t, sh_align);
   } else {
     const unsigned n = *P.careful_count;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      adjoint_track<S, true>(P, P.careful_list[i], sh_align);
+      adjoint_track<true>(P, P.careful_list[i], sh_align);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 2 * P.g.n_layers; i += blockDim.x)
@@ -413,18 +450,17 @@ __global__ void k_adjoint_finish(const AdjParams P) {
 }  // namespace
 
 bool adjoint_stride_ok(int stride, int max_len) {
-  return stride >= 1 && stride <= MAX_SEG && max_len <= MAX_CK * stride;
+  return stride >= 1 && stride <= MAX_CKPT_STRIDE && max_len <= MAX_CKPT * stride;
 }
 
 cudaError_t launch_adjoint(const AdjParams& P, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(P.careful_count, 0, sizeof(unsigned), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.g_align_acc, 0, sizeof(double) * 2 * KF_MAX_LAYERS, st);
+  cudaError_t e = cudaMemsetAsync(P.g_align_acc, 0, sizeof(double) * 2 * KF_MAX_LAYERS, st);
   if (e == cudaSuccess && P.g_hits) e = cudaMemsetAsync(P.g_hits, 0, sizeof(float) * 3 * (size_t)P.n_hits, st);
   if (e != cudaSuccess) return e;
   const int threads = 128;
   if (P.ns > 0) {
-    k_adjoint<float, false><<<(P.ns + threads - 1) / threads, threads, 0, st>>>(P);
-    k_adjoint<double, true><<<(P.ns / 20 + threads - 1) / threads + 1, threads, 0, st>>>(P);
+    k_adjoint<false><<<(P.ns + threads - 1) / threads, threads, 0, st>>>(P);
+    k_adjoint<true><<<(P.ns / 20 + threads - 1) / threads + 1, threads, 0, st>>>(P);
   }
   k_adjoint_finish<<<1, 2 * KF_MAX_LAYERS, 0, st>>>(P);
   return cudaGetLastError();

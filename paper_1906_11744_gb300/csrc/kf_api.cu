@@ -40,7 +40,8 @@ struct kf_ctx {
   // duplicate removal scratch
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state;
   // fit
-  DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count;
+  DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count, careful_flag, ckpt;
+  bool want_ckpt = false;
   int given_max_len = 0;
   bool found = false, deduped = false, fitted = false;
   int fit_source = KF_FIT_FOUND;
@@ -240,7 +241,7 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
-                    &ctx->adj_seed};
+                    &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt};
   for (DevBuf* b : bufs) release(*b);
   delete ctx;
   return KF_OK;
@@ -339,6 +340,7 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->fit_status, sizeof(int) * (size_t)n));
   CK(grow(ctx->careful_list, sizeof(int) * (size_t)n));
   CK(grow(ctx->careful_count, 64));
+  CK(grow(ctx->careful_flag, (size_t)n));
   CK(put(ctx->sp.p, params, sizeof(float) * 6 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sc.p, cov, sizeof(float) * 21 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sh.p, seed_hits, sizeof(int) * 3 * (size_t)n, device_ptrs, st));
@@ -369,8 +371,13 @@ int kf_set_alignment(kf_ctx* ctx, const float* offsets, int device_ptrs, void* s
 }
 
 static void stage_mark(kf_ctx* ctx, int i, cudaStream_t st) {
-  // External record: inside stream capture this becomes an event-record node.
-  if (ctx->stage_timing && ctx->ev[i]) cudaEventRecordWithFlags(ctx->ev[i], st, cudaEventRecordExternal);
+  if (!ctx->stage_timing || !ctx->ev[i]) return;
+  // Inside stream capture an external record becomes an event-record node;
+  // outside capture it is a plain record.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ctx->ev[i], st, cudaEventRecordExternal);
+  else cudaEventRecord(ctx->ev[i], st);
 }
 
 static FindParams find_params(kf_ctx* ctx) {
@@ -520,6 +527,13 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   F.fit_status = ptr<int>(ctx->fit_status);
   F.careful_list = ptr<int>(ctx->careful_list);
   F.careful_count = ptr<unsigned>(ctx->careful_count);
+  F.careful_flag = ptr<unsigned char>(ctx->careful_flag);
+  F.ckpt_stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : 4;
+  F.ckpt = nullptr;
+  if (ctx->want_ckpt) {  // checkpoints for the adjoint
+    CK(grow(ctx->ckpt, sizeof(float) * (size_t)MAX_CKPT * 27 * (size_t)ctx->n_seeds));
+    F.ckpt = ptr<float>(ctx->ckpt);
+  }
   if (source == KF_FIT_FOUND) {
     if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_fit_tracks: no found tracks");
     F.lists = ptr<int>(ctx->out_hits);
@@ -566,11 +580,18 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   if (!ctx) return KF_ERR_ARG;
   if (!ctx->fitted) return fail(ctx, KF_ERR_STATE, "kf_fit_adjoint: run kf_fit_tracks first");
   if (!g_align) return fail(ctx, KF_ERR_ARG, "kf_fit_adjoint: g_align is required");
-  const FitParams& F = ctx->last_fit;
   const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : 4;
-  if (!adjoint_stride_ok(stride, F.max_len))
+  if (!adjoint_stride_ok(stride, ctx->last_fit.max_len))
     return fail(ctx, KF_ERR_CAPACITY, "kf_fit_adjoint: ckpt_stride must be 1..8 with hits per track <= 9 * stride");
   cudaStream_t st = S(stream);
+  if (!ctx->last_fit.ckpt) {  // the last fit kept no checkpoints: refit with them (same lists)
+    ctx->want_ckpt = true;
+    CK(grow(ctx->ckpt, sizeof(float) * (size_t)MAX_CKPT * 27 * (size_t)ctx->n_seeds));
+    ctx->last_fit.ckpt = ptr<float>(ctx->ckpt);
+    ctx->last_fit.ckpt_stride = stride;
+    CK(launch_fit(ctx->last_fit, st));
+  }
+  const FitParams& F = ctx->last_fit;
   const size_t ns = (size_t)ctx->n_seeds, nh = (size_t)ctx->n_hits;
   CK(grow(ctx->adj_align_acc, sizeof(double) * 2 * KF_MAX_LAYERS));
   CK(grow(ctx->adj_align, sizeof(float) * 2 * KF_MAX_LAYERS));
@@ -603,6 +624,8 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   A.g_align_acc = ptr<double>(ctx->adj_align_acc);
   A.careful_list = F.careful_list;
   A.careful_count = F.careful_count;
+  A.careful_flag = F.careful_flag;
+  A.ckpt = F.ckpt;
   stage_mark(ctx, 8, st);
   CK(launch_adjoint(A, st));
   stage_mark(ctx, 9, st);
@@ -706,6 +729,8 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
   if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
   if (with_adjoint) {  // every buffer the captured work uses exists before capture starts
+    ctx->want_ckpt = true;
+    CK(grow(ctx->ckpt, sizeof(float) * (size_t)MAX_CKPT * 27 * (size_t)ctx->n_seeds));
     CK(grow(ctx->adj_align_acc, sizeof(double) * 2 * KF_MAX_LAYERS));
     CK(grow(ctx->adj_align, sizeof(float) * 2 * KF_MAX_LAYERS));
     CK(grow(ctx->adj_hits, sizeof(float) * 3 * (size_t)ctx->n_hits));

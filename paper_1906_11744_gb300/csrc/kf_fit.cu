@@ -57,6 +57,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
     return;
   }
   const DevGeom& g = P.g;
+  if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;
   float p[6], C[21];
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + t];
@@ -69,6 +70,13 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
   int status = KF_FIT_OK;
 #pragma unroll 1
   for (int k = 0; k < n && status == KF_FIT_OK; ++k) {
+    if (P.ckpt && k % P.ckpt_stride == 0 && k / P.ckpt_stride < MAX_CKPT) {  // state before hit k
+      float* c = P.ckpt + (size_t)(k / P.ckpt_stride) * 27 * P.ns + t;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) c[(size_t)q * P.ns] = p[q];
+#pragma unroll
+      for (int q = 0; q < 21; ++q) c[(size_t)(6 + q) * P.ns] = C[q];
+    }
     const int hi = hoff + lst[k];
     const int L = P.hlayer[hi];
     float mx, my, mz;
@@ -79,6 +87,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
         if (propagate<float>(p, C, g.radius[L], g.kb, INFINITY, &cosa) != 1) { status = KF_FIT_NO_CROSS; break; }
         if (cosa < CAREFUL_COS) {  // leave the track to the careful pass
           P.careful_list[atomicAdd(P.careful_count, 1u)] = t;
+          if (P.careful_flag) P.careful_flag[t] = 1;
           return;
         }
       }

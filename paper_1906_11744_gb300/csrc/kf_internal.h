@@ -103,7 +103,13 @@ struct FitParams {
   int* fit_status;        // [ns]
   int* careful_list;      // [ns] tracks refitted with double-precision steps
   unsigned* careful_count;  // zeroed before the launch
+  unsigned char* careful_flag;  // [ns] 1 for the tracks of careful_list
+  float* ckpt;            // [MAX_CKPT][27][ns] states before every ckpt_stride-th hit, or null
+  int ckpt_stride;
 };
+
+constexpr int MAX_CKPT = 9;       // checkpoints per track
+constexpr int MAX_CKPT_STRIDE = 8;
 
 struct AdjParams {
   DevGeom g;
@@ -128,8 +134,10 @@ struct AdjParams {
   float* g_seed;               // [6][ns] or null
   float* g_align;              // [n_layers][2]
   double* g_align_acc;         // [2 * KF_MAX_LAYERS] accumulator
-  int* careful_list;
-  unsigned* careful_count;
+  const int* careful_list;     // tracks the fit flagged as near-tangent ...
+  const unsigned* careful_count;
+  const unsigned char* careful_flag;  // ... and their per-track flag
+  const float* ckpt;           // the fit's checkpoints [MAX_CKPT][27][ns]
 };
 
 // kf_adjoint.cu
