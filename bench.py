@@ -42,6 +42,12 @@ F_MS = 25         # multiple-scattering term
 F_SEED = 1436     # seed fit over three hits
 F_FIT_HIT = 608   # re-fit: propagation + transport + update + scattering per hit
 
+# DRAM traffic (read + write) of one k_find launch on the 100-event batch,
+# scaled by events from the ncu capture summarized in
+# profiles/k_find_pu200_20events.md (192.8 MB for 20 events).  Set to None
+# whenever k_find changes until it is captured again.
+FIND_TRAFFIC_BYTES = 192.76e6 * 5
+
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -110,6 +116,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(value, device):
+    """Largest value over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def make_inputs(name, rank, n_events=None):
@@ -268,10 +285,7 @@ def main():
     clocks.stop()
     step_ms = [a.elapsed_time(bb) for a, bb in zip(ev_a, ev_b)]
     total_ms = sum(step_ms)
-    if world > 1:
-        tm = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tm.item())
+    total_ms = max_over_ranks(total_ms, dev)
     seeds_all = n_seeds * world
     value = seeds_all * args.steps / (total_ms / 1e3)
     steps_per_s = counters["steps"] * world * args.steps / (total_ms / 1e3)
@@ -282,8 +296,11 @@ def main():
                   + (counters["updates"] + counters["holes"]) * F_MS + counters["seeds"] * F_SEED)
     achieved = find_flops / (find_ms / 1e3) / 1e12
     peak = fp32_peak_tflops()
+    traffic = None
+    if FIND_TRAFFIC_BYTES is not None and args.config == "c4" and not args.events:
+        traffic = FIND_TRAFFIC_BYTES
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_find",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_find",
                 "flops_per_launch": find_flops, "find_ms": find_ms,
                 "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts x max clock)"}
 
@@ -354,10 +371,7 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            tm = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(tm.item())
+        e2e_s = max_over_ranks(e2e_s, dev)
         bi = sum(v.numel() * v.element_size() for v in h.values())
         bo = sum(v.numel() * v.element_size() for v in outs.values()) + \
             sum(v.numel() * v.element_size() for v in fouts.values()) + g_host.numel() * 4
