@@ -91,10 +91,10 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   if (!first) {
     D pd[6], qd[6], Jd[6][6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) pd[k] = D(0.0), pd[k].v = p_in[k];
+    for (int k = 0; k < 6; ++k) pd[k] = D::of(p_in[k]);
 #pragma unroll
     for (int d = 0; d < NDIR; ++d) pd[dir_param(d)].d[d] = S(1);
-    prop_jacobian<D>(pd, D((double)h.R), D((double)g.kb), D(INFINITY), qd, Jd);
+    prop_jacobian<D>(pd, D::of(h.R), D::of((S)g.kb), D::of(S(INFINITY)), qd, Jd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       q[i] = qd[i].v;
@@ -139,10 +139,10 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   if (!last) {
     D pd[6], q44, q55;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) pd[k] = D(0.0), pd[k].v = pu[k];
+    for (int k = 0; k < 6; ++k) pd[k] = D::of(pu[k]);
 #pragma unroll
     for (int d = 0; d < NDIR; ++d) pd[dir_param(d)].d[d] = S(1);
-    ms_terms<D>(pd, D((double)g.x0[h.L]), q44, q55);
+    ms_terms<D>(pd, D::of((S)g.x0[h.L]), q44, q55);
 #pragma unroll
     for (int d = 0; d < NDIR; ++d)
       pbu[dir_param(d)] = kfma(Cb[4][4], q44.d[d], kfma(Cb[5][5], q55.d[d], pbu[dir_param(d)]));

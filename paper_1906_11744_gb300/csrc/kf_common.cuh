@@ -434,7 +434,10 @@ __device__ __forceinline__ int wrap_bin(int b, int n) {
   return b < 0 ? b + n : b;
 }
 __device__ __forceinline__ int eta_bin(float z, float R, float eta_max, int n_eta, const float* edges) {
-  const float eta = asinhf(z / R);
+  // First guess from a fast asinh(z/R) = sign * log(|u| + sqrt(u^2 + 1)); the
+  // edge comparisons below make the result exact whatever the guess.
+  const float u = fabsf(z / R);
+  const float eta = copysignf(__logf(u + sqrtf(fmaf(u, u, 1.f))), z);
   int b = (int)floorf((eta + eta_max) * ((float)n_eta / (2.f * eta_max)));
   b = min(max(b, 0), n_eta - 1);
   while (b > 0 && z < __ldg(edges + b)) --b;

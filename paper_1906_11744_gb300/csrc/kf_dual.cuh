@@ -18,6 +18,14 @@ struct Dual {
 #pragma unroll
     for (int i = 0; i < N; ++i) d[i] = S(0);
   }
+  // From a value already in S (no round trip through double for S = float).
+  __device__ __forceinline__ static Dual of(S c) {
+    Dual r;
+    r.v = c;
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = S(0);
+    return r;
+  }
 };
 
 template <class S, int N>

@@ -150,7 +150,11 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
               // with r_rphi = R_hit sin(dphi) on the near half, |r_z| < sqrt(cut S11).
               const float w1 = sqrtf(g.chi2_cut * f.s00);
               const float w2 = sqrtf(g.chi2_cut * f.s11);
-              float dphi = (w1 >= R) ? 0.5f * PI_F : asinf(w1 / R);
+              // asin(x) for the usual small x by x + x^3/6 + 3x^5/40 (truncation
+              // below 3e-9 relative for x < 0.05, far inside the padding)
+              const float xr = w1 / R;
+              float dphi = (xr >= 1.f) ? 0.5f * PI_F
+                           : (xr < 0.05f ? xr * fmaf(xr * xr, fmaf(xr * xr, 0.075f, 1.f / 6.f), 1.f) : asinf(xr));
               dphi = fminf(dphi, 0.5f * PI_F) * (1.f + WIN_REL) + WIN_PHI_ABS;
               const float phic = atan2f(p[1], p[0]) + al.dphi;
               const int nphi = g.n_phi, neta = g.n_eta;

@@ -1,0 +1,88 @@
+"""Parity at the benchmark's full size and launch configuration.
+
+The PU-200-like batch (100 events x 8,000 tracks, 20% noise, N = 10) runs as
+the benchmark runs it: 10 lanes per seed, 256-thread blocks, persistent
+launch, one captured graph with binning, finding, duplicate removal, fit and
+adjoint.  The oracle checks sampled outputs it can compute one by one:
+found hit lists of 600 seeds from three events, duplicate flags of one whole
+event, fits and seed gradients of sampled kept tracks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from kfhelp import TOL, audit_mismatch, cov_close, param_close, tracker_for
+from synth import make_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pu200():
+    import torch
+    from paper_1906_11744_gb300 import kf_get_gradient
+    b = make_batch("c4")
+    dev = torch.device("cuda:0")
+    t = tracker_for(b, device=dev, lanes_per_seed=10, block_threads=256, persistent=1)
+    s = torch.cuda.Stream()
+    t.capture_graph(with_adjoint=True, stream=s)
+    t.launch_graph(stream=s)
+    s.synchronize()
+    trk = t.get_tracks()
+    fit = t.get_fit()
+    g_seed = np.zeros((6, b.n_seeds), np.float32)
+    kf_get_gradient(t.ctx, g_seed=g_seed)
+    counters = t.counters()
+    t.close()
+    return b, trk, fit, g_seed, counters
+
+
+def test_sampled_found_tracks(pu200):
+    b, trk, fit, g_seed, counters = pu200
+    assert counters["seeds"] == b.n_seeds
+    n_cmp = 0
+    mism = []
+    for e in (0, 37, 99):
+        a = b.seed_off[e]
+        ns = b.seed_off[e + 1] - a
+        for lo in (0, ns // 2, ns - 100):
+            ref = oracle.find_event(b, e, seeds=(lo, lo + 100))
+            for i in range(100):
+                n_cmp += 1
+                if not np.array_equal(trk["hits"][a + lo + i], ref["hits"][i]):
+                    mism.append((e, lo + i, trk["hits"][a + lo + i], ref["hits"][i]))
+    assert n_cmp == 900
+    assert len(mism) <= 0.005 * n_cmp, len(mism)
+    for e, s, g, r in mism:
+        ok, kind, rel = audit_mismatch(b, e, s, g, r)
+        assert ok, (e, s, kind, rel)
+
+
+def test_whole_event_duplicate_flags(pu200):
+    b, trk, fit, g_seed, counters = pu200
+    e = 57
+    a, c = b.seed_off[e], b.seed_off[e + 1]
+    keep = oracle.dedup(trk["hits"][a:c], trk["n_found"][a:c], trk["chi2"][a:c].astype(np.float64), 0.5)
+    assert np.array_equal(keep, trk["keep"][a:c])
+
+
+def test_sampled_fits_and_seed_gradients(pu200):
+    b, trk, fit, g_seed, counters = pu200
+    for e in (3, 71):
+        a = b.seed_off[e]
+        x, y, z, lay = b.event_hits(e)
+        idx = np.arange(a, a + 400, 2)
+        kept = idx[(trk["keep"][idx] == 1) & (fit["status"][idx] == 0)]
+        p, C, c2, st = oracle.fit(b.det, b.params[:, kept], b.cov[:, kept], trk["hits"][kept],
+                                  trk["n_found"][kept], x, y, z, lay, align=b.align)
+        ok = st == 0
+        okp, ep = param_close(fit["params"][:, kept].T[ok], p[ok])
+        okc, ec = cov_close(fit["cov"][:, kept].T[ok], C[ok], p[ok])
+        assert okp.all(), ep
+        assert okc.all(), ec
+        sel = kept[ok][:60]
+        tot, ga, gh, gs, each = oracle.fit_grad(b.det, b.params[:, sel], b.cov[:, sel], trk["hits"][sel],
+                                                trk["n_found"][sel], x, y, z, lay, b.align)
+        err = np.abs(g_seed[:, sel].T - gs).max() / np.abs(gs).max()
+        assert err < 1e-3, err
+    assert TOL == 1e-4
