@@ -43,10 +43,9 @@ F_SEED = 1436     # seed fit over three hits
 F_FIT_HIT = 608   # re-fit: propagation + transport + update + scattering per hit
 
 # DRAM traffic (read + write) of one k_find launch on the 100-event batch,
-# scaled by events from the ncu capture summarized in
-# profiles/k_find_pu200_20events.md (192.8 MB for 20 events).  Set to None
-# whenever k_find changes until it is captured again.
-FIND_TRAFFIC_BYTES = 192.76e6 * 5
+# scaled by events from an ncu capture of the same kernel on 20 of its events
+# (192.2 MB).  Set to None whenever k_find changes until it is captured again.
+FIND_TRAFFIC_BYTES = 192.21e6 * 5
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -216,6 +215,8 @@ def main():
     ap.add_argument("--config", default="c4")
     ap.add_argument("--events", type=int, default=None, help="override the number of events")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--find-shape", default=None,
+                    help="lanes,threads,persistent,regcap of the finding kernel (skips the autotuner)")
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -243,7 +244,12 @@ def main():
                 cov=tt(b.cov), seed_hits=tt(b.seed_hits))
     torch.cuda.synchronize()
 
-    t = tracker_for(b, persistent=1, per_event=0)
+    shape = {}
+    if args.find_shape:
+        lanes, threads, pers, regcap = (int(v) for v in args.find_shape.split(","))
+        shape = dict(lanes_per_seed=lanes, block_threads=threads, persistent=pers, find_regcap=regcap)
+        args.no_autotune = True
+    t = tracker_for(b, **{"persistent": 1, "per_event": 0, **shape})
     t.load_hits(b.hit_off, d_in["x"], d_in["y"], d_in["z"], d_in["layer"], stream)
     t.load_seeds(b.seed_off, d_in["params"], d_in["cov"], d_in["seed_hits"], stream)
     t.set_alignment(b.align, stream)
@@ -390,6 +396,7 @@ def main():
                           "seeds_per_gpu": n_seeds, "hits_per_gpu": b.n_hits,
                           "l2": "flushed (2x L2 write) before every timed step",
                           "launch": "one CUDA graph per step: bin (5 kernels) + find + dedup + fit (2) + alignment-gradient adjoint (3)",
+                          "find_shape": shape or None,
                           "autotuned": None if tune is None else {
                               "lanes_per_seed": int(tune[np.argmin(tune[:, 4])][0]),
                               "block_threads": int(tune[np.argmin(tune[:, 4])][1]),

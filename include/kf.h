@@ -90,6 +90,9 @@ typedef struct {
   int per_event;          /* 1 = bin, find and remove duplicates with one launch per event
                              (the plain form); 0 = one launch per step over the whole batch */
   int ckpt_stride;        /* layers between forward checkpoints of the adjoint (>= 1) */
+  int find_regcap;        /* 0 = finding kernel at the compiler's register count (blocks <= 256
+                             threads); 1 = at most 102 registers, five blocks per SM (blocks
+                             <= 128 threads).  The results are identical. */
 } kf_config;
 
 /* Create a context for a detector and configuration.  Allocates nothing on

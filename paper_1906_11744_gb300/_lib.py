@@ -41,7 +41,7 @@ class kf_config(ctypes.Structure):
                 ("dup_shared_frac", ctypes.c_float), ("n_eta_bins", ctypes.c_int),
                 ("n_phi_bins", ctypes.c_int), ("lanes_per_seed", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("per_event", ctypes.c_int), ("ckpt_stride", ctypes.c_int)]
+                ("per_event", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("find_regcap", ctypes.c_int)]
 
 
 class KFError(RuntimeError):

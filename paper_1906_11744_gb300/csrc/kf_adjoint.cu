@@ -7,21 +7,25 @@
 // Reverse: for each segment from the last, the states before each step are
 // recomputed from the segment's checkpoint, then the steps are reversed one
 // by one:
-//   * scattering C += Q(p): dQ/dp by forward-mode dual numbers (5 directions);
+//   * scattering C += Q(p): the Highland variances differentiated by hand
+//     through log(theta0) (q/pT, theta, and phi relative to the position angle);
 //   * update and chi2 with U = C H^T, S = H U + V, K = U S^-1,
 //       p' = p + U S^-1 r,  C' = C - U S^-1 U^T,  chi2 = r^T S^-1 r,
 //     reversed with the matrix identities dS^-1 = -S^-1 dS S^-1 (adjoints of
 //     U, S^-1, r, H and C by hand);
 //   * the measurement frame H(p) and residual r(p, m), m = R(-a_rphi/R_L) h - a_z e_z;
 //   * propagation q = F(p), C' = J C J^T: Cbar <- J^T Cbar' J,
-//     pbar <- J^T pbar' + sum_ij Jbar_ij dJ_ij/dp with Jbar = 2 Cbar' J C and
-//     dJ/dp from the same propagation code run on dual numbers.
+//     pbar <- J^T pbar' + sum_ij Jbar_ij dJ_ij/dp with Jbar = 2 Cbar' J C; the
+//     contraction is one reverse sweep through the Jacobian's intermediates,
+//     with the path length's dependence on p from the implicit function
+//     theorem (ds/dp = -(dg/dp)/(dg/ds) for g = x(s)^2 + y(s)^2 - R^2) and
+//     d sinc/dpsi = f1, d cosc/dpsi = f2.
 // The adjoint of the final state is zero: the objective is the chi2 sum.
 // Tracks the fit flagged for a near-tangent crossing go to a second pass that
 // keeps their adjoints in double and runs the near-tangent steps in double.
 #include <type_traits>
 
-#include "kf_dual.cuh"
+#include "kf_common.cuh"
 #include "kf_internal.h"
 
 namespace kfg {
@@ -29,8 +33,145 @@ namespace kfg {
 namespace {
 
 constexpr float ADJ_CAREFUL_COS = 0.5f;
-constexpr int NDIR = 5;  // dual directions: x, y, q/pT, phi, theta
-__device__ __forceinline__ int dir_param(int d) { return d < 2 ? d : d + 1; }
+
+// Derivatives of f1 and f2 (the helix functions of kf_common.cuh) in psi:
+// f1' = -(sin psi + 2 f1)/psi, f2' = (cos psi - 2 f2)/psi, by the term-wise
+// derivatives of the same power series below |psi| = 0.5.
+template <class T>
+__device__ __forceinline__ void helix_dfns(T psi, T f1, T f2, T& df1, T& df2) {
+  if (kabs(psi) < T(0.5)) {
+    const T q = psi * psi;
+    df1 = kfma(q, kfma(q, kfma(q, kfma(q, T(-1.0 / 443520.0), T(1.0 / 6480.0)), T(-1.0 / 168.0)), T(0.1)),
+               T(-1.0 / 3.0));
+    df2 = psi * kfma(q, kfma(q, kfma(q, T(1.0 / 50400.0), T(-1.0 / 960.0)), T(1.0 / 36.0)), T(-0.25));
+    if (sizeof(T) == 8) {  // the extra term of the double series
+      const T q4 = q * q * q * q;
+      df1 += q4 * q * T(1.0 / 47174400.0);
+      df2 += psi * q4 * T(-1.0 / 4354560.0);
+    }
+  } else {
+    T sn, cs;
+    ksincos(psi, &sn, &cs);
+    const T ip = T(1) / psi;
+    df1 = -(sn + T(2) * f1) * ip;
+    df2 = (cs - T(2) * f2) * ip;
+  }
+}
+
+// v += sum_il Jb_il dJ_il/dp for the propagation Jacobian J(p) of
+// prop_jacobian (to the layer it crossed at transverse path length s).  Jb
+// is read at the structural non-zeros (JS == 2) only.  Reverse sweep through
+// the Jacobian's intermediates in the opposite order of their computation.
+template <class T>
+__device__ __forceinline__ void jac_vjp(const T (&p)[6], T s, T kb, const T (&Jb)[6][6], T (&v)[6]) {
+  const T x = p[0], y = p[1], h = kb * p[3];
+  T sf, cf, sth, cth;
+  ksincos(p[4], &sf, &cf);
+  ksincos(p[5], &sth, &cth);
+  const T ist = T(1) / sth;
+  const T cot = cth * ist;
+  const T psi = h * s;
+  T sc, cc, f1, f2, df1, df2;
+  helix_fns<T>(psi, sc, cc, f1, f2);
+  helix_dfns<T>(psi, f1, f2, df1, df2);
+  const T Sx = s * sc, Cx = s * cc;
+  const T dx = kfma(cf, Sx, -sf * Cx), dy = kfma(sf, Sx, cf * Cx);
+  const T xn = x + dx, yn = y + dy;
+  const T cpsi = kfma(-psi, cc, T(1)), spsi = psi * sc;
+  const T cp = kfma(cf, cpsi, -sf * spsi), sp = kfma(sf, cpsi, cf * spsi);
+  const T s2 = s * s, dSdh = s2 * f1, dCdh = s2 * f2;
+  const T Fx3 = kb * kfma(cf, dSdh, -sf * dCdh), Fy3 = kb * kfma(sf, dSdh, cf * dCdh);
+  const T Fx4 = -dy, Fy4 = dx;
+  const T inv = T(-1) / kfma(xn, cp, yn * sp);
+  const T g3 = kfma(xn, Fx3, yn * Fy3), g4 = kfma(xn, Fx4, yn * Fy4);
+  const T ds[4] = {xn * inv, yn * inv, g3 * inv, g4 * inv};  // ds/d(x, y, q/pT, phi)
+  // J rows 0, 1, 2, 4 over columns (x, y, q/pT, phi) are (cp, sp, cot, h) ds_c
+  // plus terms free of ds; row 2 column theta is -s / sin^2 theta.
+  T cpb = T(0), spb = T(0), cotb = T(0), hb = T(0), dsb[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int col = c < 2 ? c : c + 1;
+    cpb = kfma(Jb[0][col], ds[c], cpb);
+    spb = kfma(Jb[1][col], ds[c], spb);
+    cotb = kfma(Jb[2][col], ds[c], cotb);
+    hb = kfma(Jb[4][col], ds[c], hb);
+    dsb[c] = kfma(Jb[0][col], cp, kfma(Jb[1][col], sp, kfma(Jb[2][col], cot, Jb[4][col] * h)));
+  }
+  T sb = kfma(Jb[4][3], kb, -Jb[2][5] * ist * ist);
+  T sthb = T(2) * Jb[2][5] * s * ist * ist * ist;
+  // ds_c = g_c inv with g = (xn, yn, g3, g4), inv = -1/(xn cp + yn sp)
+  const T invb = kfma(dsb[0], xn, kfma(dsb[1], yn, kfma(dsb[2], g3, dsb[3] * g4)));
+  T xnb = kfma(dsb[2], Fx3, kfma(dsb[3], Fx4, dsb[0])) * inv;
+  T ynb = kfma(dsb[2], Fy3, kfma(dsb[3], Fy4, dsb[1])) * inv;
+  const T Fx3b = kfma(dsb[2] * xn, inv, Jb[0][3]), Fy3b = kfma(dsb[2] * yn, inv, Jb[1][3]);
+  const T Fx4b = kfma(dsb[3] * xn, inv, Jb[0][4]), Fy4b = kfma(dsb[3] * yn, inv, Jb[1][4]);
+  const T dgdsb = invb * inv * inv;
+  xnb = kfma(dgdsb, cp, xnb);
+  ynb = kfma(dgdsb, sp, ynb);
+  cpb = kfma(dgdsb, xn, cpb);
+  spb = kfma(dgdsb, yn, spb);
+  // F4 = (-dy, dx); F3 = kb R(phi) (dS/dh, dC/dh)
+  T dxb = Fy4b + xnb, dyb = ynb - Fx4b;
+  const T dSdhb = kb * kfma(Fx3b, cf, Fy3b * sf), dCdhb = kb * kfma(-Fx3b, sf, Fy3b * cf);
+  T cfb = kb * kfma(Fx3b, dSdh, Fy3b * dCdh), sfb = kb * kfma(-Fx3b, dCdh, Fy3b * dSdh);
+  sb = kfma(T(2) * s, kfma(dSdhb, f1, dCdhb * f2), sb);
+  const T f1b = dSdhb * s2, f2b = dCdhb * s2;
+  // (cp, sp) = R(phi) (cos psi, sin psi)
+  cfb = kfma(cpb, cpsi, kfma(spb, spsi, cfb));
+  sfb = kfma(-cpb, spsi, kfma(spb, cpsi, sfb));
+  const T cpsib = kfma(cpb, cf, spb * sf), spsib = kfma(-cpb, sf, spb * cf);
+  T psib = kfma(-cpsib, cc, spsib * sc);
+  T ccb = -cpsib * psi, scb = spsib * psi;
+  // (dx, dy) = R(phi) (S, C) with S = s sinc, C = s cosc
+  cfb = kfma(dxb, Sx, kfma(dyb, Cx, cfb));
+  sfb = kfma(-dxb, Cx, kfma(dyb, Sx, sfb));
+  const T Sxb = kfma(dxb, cf, dyb * sf), Cxb = kfma(-dxb, sf, dyb * cf);
+  sb = kfma(Sxb, sc, kfma(Cxb, cc, sb));
+  scb = kfma(Sxb, s, scb);
+  ccb = kfma(Cxb, s, ccb);
+  psib = kfma(scb, f1, kfma(ccb, f2, kfma(f1b, df1, kfma(f2b, df2, psib))));
+  hb = kfma(psib, s, hb);
+  sb = kfma(psib, h, sb);
+  // cot = cos theta / sin theta
+  sthb = kfma(-cotb * cot, ist, sthb);
+  v[0] += kfma(sb, ds[0], xnb);
+  v[1] += kfma(sb, ds[1], ynb);
+  v[3] += kfma(kb, hb, sb * ds[2]);
+  v[4] += kfma(sfb, cf, kfma(-cfb, sf, sb * ds[3]));
+  v[5] += kfma(sthb, cth, -cotb);
+}
+
+// v += b44 dq44/dp + b55 dq55/dp for the scattering variances of ms_terms:
+// with L = log theta0, dL = (beta^2 - 2)(d|q/pT|/|q/pT| + dsin/sin)
+//   + (1/2 + 0.038/(1 + 0.038 log t)) dlog t,  t = x0/|sin theta cos(phi - phi_p)|,
+// phi_p the position angle; dq55 = 2 q55 dL, dq44 = q44 (2 dL - 2 dsin/sin).
+template <class T>
+__device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T b44, T b55, T (&v)[6]) {
+  if (p[3] == T(0) || x0 <= T(0)) return;
+  T sth, cth, sph, cph;
+  ksincos(p[5], &sth, &cth);
+  ksincos(p[4], &sph, &cph);
+  const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
+  const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;   // cos(phi - phi_p)
+  const T sdiff = kfma(sph, p[0], -cph * p[1]) * ir;  // sin(phi - phi_p)
+  const T pm = T(1) / (kabs(p[3]) * sth);
+  const T e2 = kfma(pm, pm, T(MPION * MPION));
+  const T beta = pm / ksqrt(e2);
+  const T t = x0 / kabs(sth * cdiff);
+  const T lt = klog(t);
+  const T th0 = T(0.0136) / (beta * pm) * ksqrt(t) * kfma(T(0.038), lt, T(1));
+  const T q55 = th0 * th0;
+  const T q44 = q55 / (sth * sth);
+  const T W = T(2) * kfma(b55, q55, b44 * q44);
+  const T a = pm * pm / e2 - T(2);
+  const T bt = T(0.5) + T(0.038) / kfma(T(0.038), lt, T(1));
+  v[3] += -W * a / p[3];
+  v[5] += kfma(-W, a + bt, T(-2) * b44 * q44) * cth / sth;
+  const T wc = W * bt * sdiff / cdiff;  // adjoint of phi - phi_p
+  v[4] += wc;
+  v[0] = kfma(wc * p[1], ir * ir, v[0]);
+  v[1] = kfma(-wc * p[0], ir * ir, v[1]);
+}
 
 template <class S>
 struct Hit {
@@ -82,30 +223,12 @@ template <class S>
 __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], const S (&C_in)[21],
                                          const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
                                          S (&hb)[3], S (&ab)[2]) {
-  using D = Dual<S, NDIR>;
   // ---- forward recompute of the step
-  S q[6], J[6][6], Cp[21];
-  S dJ[6][6][NDIR];  // dJ_ij / d(direction)
+  S q[6], J[6][6], Cp[21], s_len = S(0);
 #pragma unroll
   for (int k = 0; k < 21; ++k) Cp[k] = C_in[k];
   if (!first) {
-    D pd[6], qd[6], Jd[6][6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) pd[k] = D::of(p_in[k]);
-#pragma unroll
-    for (int d = 0; d < NDIR; ++d) pd[dir_param(d)].d[d] = S(1);
-    prop_jacobian<D>(pd, D::of(h.R), D::of((S)g.kb), D::of(S(INFINITY)), qd, Jd);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      q[i] = qd[i].v;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (JS(i, j) != 2) continue;
-        J[i][j] = Jd[i][j].v;
-#pragma unroll
-        for (int d = 0; d < NDIR; ++d) dJ[i][j][d] = Jd[i][j].d[d];
-      }
-    }
+    prop_jacobian<S>(p_in, h.R, (S)g.kb, S(INFINITY), q, J, nullptr, &s_len);
     transport<S>(J, Cp);
   } else {
 #pragma unroll
@@ -136,17 +259,7 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   S pbu[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) pbu[i] = pb[i];
-  if (!last) {
-    D pd[6], q44, q55;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) pd[k] = D::of(pu[k]);
-#pragma unroll
-    for (int d = 0; d < NDIR; ++d) pd[dir_param(d)].d[d] = S(1);
-    ms_terms<D>(pd, D::of((S)g.x0[h.L]), q44, q55);
-#pragma unroll
-    for (int d = 0; d < NDIR; ++d)
-      pbu[dir_param(d)] = kfma(Cb[4][4], q44.d[d], kfma(Cb[5][5], q55.d[d], pbu[dir_param(d)]));
-  }
+  if (!last) ms_vjp<S>(pu, (S)g.x0[h.L], Cb[4][4], Cb[5][5], pbu);
   // ---- reverse: update and chi2 (chi2 adjoint 1)
   const S w0 = [&] { S a = S(0); for (int i = 0; i < 6; ++i) a = kfma(U[i][0], pbu[i], a); return a; }();
   const S w1 = [&] { S a = S(0); for (int i = 0; i < 6; ++i) a = kfma(U[i][1], pbu[i], a); return a; }();
@@ -265,19 +378,18 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
     }
     pin[k] = a;
   }
+  S Jb[6][6];  // Jbar_il = 2 sum_j Cbp_ij (J C_in)_jl at the structural non-zeros
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
       if (JS(i, l) != 2) continue;
-      // Jbar_il = 2 sum_j Cbp_ij (J C_in)_jl
       S jb = S(0);
 #pragma unroll
       for (int j = 0; j < 6; ++j) jb = kfma(Cbp[i][j], CJ[j][l], jb);
-      jb *= S(2);
-#pragma unroll
-      for (int d = 0; d < NDIR; ++d) pin[dir_param(d)] = kfma(jb, dJ[i][l][d], pin[dir_param(d)]);
+      Jb[i][l] = S(2) * jb;
     }
+  jac_vjp<S>(p_in, s_len, (S)g.kb, Jb, pin);
   // Cbar_in = J^T Cbar' J
   S T1[6][6];  // Cbp J
 #pragma unroll

@@ -167,6 +167,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   if (!supported_lanes(lanes) || lanes < cfg->max_cands) return KF_ERR_ARG;
   int threads = cfg->block_threads ? cfg->block_threads : 128;
   if (threads < 32 || threads > 256 || threads % 32) return KF_ERR_ARG;
+  if (cfg->find_regcap < 0 || cfg->find_regcap > 1 || (cfg->find_regcap && threads > 128)) return KF_ERR_ARG;
   ctx = new kf_ctx();
   ctx->det = *det;
   ctx->cfg = *cfg;
@@ -174,6 +175,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   ctx->threads = threads;
   ctx->persistent = cfg->persistent ? 1 : 0;
   ctx->per_event = cfg->per_event ? 1 : 0;
+  ctx->regcap = cfg->find_regcap;
   DevGeom& g = ctx->g;
   std::memset(&g, 0, sizeof(g));
   g.n_layers = det->n_layers;

@@ -255,10 +255,11 @@ __device__ __forceinline__ bool crossing(const float (&p)[6], float R, float kb,
 // Jacobian, covariance transport).  Returns 1 on success (p, C updated),
 // 0 without a crossing, 2 when |z| at the crossing exceeds z_lim; p and C are
 // untouched unless 1 is returned.  cos_out (optional) receives |cos| of the
-// angle between the direction and the radial direction at the crossing.
+// angle between the direction and the radial direction at the crossing,
+// s_out (optional) the transverse path length.
 template <class T>
 __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim, T (&q)[6], T (&J)[6][6],
-                                             T* cos_out = nullptr) {
+                                             T* cos_out = nullptr, T* s_out = nullptr) {
   const T x = p[0], y = p[1], kap = p[3], phi = p[4], th = p[5];
   T sf, cf;
   ksincos(phi, &sf, &cf);
@@ -288,6 +289,7 @@ __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim
   const T Fx4 = -dy, Fy4 = dx;
   const T dgds = kfma(xn, cp, yn * sp);
   if (cos_out) *cos_out = kabs(dgds) / R;
+  if (s_out) *s_out = s;
   const T inv = T(-1) / dgds;
   const T ds0 = xn * inv, ds1 = yn * inv;
   const T ds3 = kfma(xn, Fx3, yn * Fy3) * inv;

@@ -46,8 +46,10 @@ constexpr float WIN_REL = 1e-3f;
 constexpr float WIN_PHI_ABS = 1e-5f;  // rad
 constexpr float WIN_Z_ABS = 1e-4f;    // cm
 
-template <int G, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
+// CAP = 0: blocks of up to 256 threads, registers at the compiler's choice;
+// CAP = 1: blocks of up to 128 threads, five per SM (at most 102 registers).
+template <int G, int CAP>
+__global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const FindParams P) {
   constexpr int W = 32 / G;  // seeds per warp
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -375,18 +377,25 @@ __global__ void __launch_bounds__(256, MINB) k_find(const FindParams P) {
   }
 }
 
-template <int G, int MINB>
+template <int G, int CAP>
 cudaError_t prepare_g(int threads, int n_layers, int* blocks_per_sm) {
   const size_t smem = (size_t)(threads / 32) * smem_per_warp(n_layers);
-  cudaError_t err = cudaFuncSetAttribute(k_find<G, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t err = cudaFuncSetAttribute(k_find<G, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
+  cudaFuncAttributes fa;
+  err = cudaFuncGetAttributes(&fa, k_find<G, CAP>);
+  if (err != cudaSuccess) return err;
+  if (threads > fa.maxThreadsPerBlock) {  // the launch bounds forbid this block size
+    if (blocks_per_sm) *blocks_per_sm = 0;
+    return cudaSuccess;
+  }
   if (blocks_per_sm)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_find<G, MINB>, threads, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_find<G, CAP>, threads, smem);
   return err;
 }
 
-template <int G, int MINB>
+template <int G, int CAP>
 cudaError_t launch_g(const FindParams& P, int threads, int grid_cap, cudaStream_t st) {
   const size_t smem = (size_t)(threads / 32) * smem_per_warp(P.g.n_layers);
   constexpr int W = 32 / G;
@@ -396,27 +405,25 @@ cudaError_t launch_g(const FindParams& P, int threads, int grid_cap, cudaStream_
   int grid = (n_tasks + wpb - 1) / wpb;
   if (P.persistent && grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
-  k_find<G, MINB><<<grid, threads, smem, st>>>(P);
+  k_find<G, CAP><<<grid, threads, smem, st>>>(P);
   return cudaGetLastError();
 }
 
-// Kernel variants: lanes per seed G x register budget (MINB = 1: the
-// compiler's choice; MINB = 3: at most 85 registers for three 256-thread
-// blocks per SM).
+// Kernel variants: lanes per seed G x register budget CAP (regcap).
 #define KF_FIND_DISPATCH(FN, ...)                                   \
   switch (lanes * 4 + (regcap ? 1 : 0)) {                          \
-    case 4 * 4: return FN<4, 1>(__VA_ARGS__);                      \
-    case 4 * 4 + 1: return FN<4, 3>(__VA_ARGS__);                  \
-    case 6 * 4: return FN<6, 1>(__VA_ARGS__);                      \
-    case 6 * 4 + 1: return FN<6, 3>(__VA_ARGS__);                  \
-    case 8 * 4: return FN<8, 1>(__VA_ARGS__);                      \
-    case 8 * 4 + 1: return FN<8, 3>(__VA_ARGS__);                  \
-    case 10 * 4: return FN<10, 1>(__VA_ARGS__);                    \
-    case 10 * 4 + 1: return FN<10, 3>(__VA_ARGS__);                \
-    case 12 * 4: return FN<12, 1>(__VA_ARGS__);                    \
-    case 12 * 4 + 1: return FN<12, 3>(__VA_ARGS__);                \
-    case 16 * 4: return FN<16, 1>(__VA_ARGS__);                    \
-    case 16 * 4 + 1: return FN<16, 3>(__VA_ARGS__);                \
+    case 4 * 4: return FN<4, 0>(__VA_ARGS__);                      \
+    case 4 * 4 + 1: return FN<4, 1>(__VA_ARGS__);                  \
+    case 6 * 4: return FN<6, 0>(__VA_ARGS__);                      \
+    case 6 * 4 + 1: return FN<6, 1>(__VA_ARGS__);                  \
+    case 8 * 4: return FN<8, 0>(__VA_ARGS__);                      \
+    case 8 * 4 + 1: return FN<8, 1>(__VA_ARGS__);                  \
+    case 10 * 4: return FN<10, 0>(__VA_ARGS__);                    \
+    case 10 * 4 + 1: return FN<10, 1>(__VA_ARGS__);                \
+    case 12 * 4: return FN<12, 0>(__VA_ARGS__);                    \
+    case 12 * 4 + 1: return FN<12, 1>(__VA_ARGS__);                \
+    case 16 * 4: return FN<16, 0>(__VA_ARGS__);                    \
+    case 16 * 4 + 1: return FN<16, 1>(__VA_ARGS__);                \
     default: return cudaErrorInvalidValue;                         \
   }
 

@@ -49,6 +49,7 @@ def test_host_argument_errors_without_gpu():
     det = make_detector([5.0, 10.0], [0.02, 0.02])
     for cfg in (make_config(max_cands=0), make_config(max_cands=17), make_config(lanes_per_seed=5),
                 make_config(lanes_per_seed=4, max_cands=6), make_config(block_threads=48),
+                make_config(find_regcap=1, block_threads=256), make_config(find_regcap=2),
                 make_config(chi2_cut=-1.0)):
         assert lib.kf_create(ctypes.byref(det), ctypes.byref(cfg), ctypes.byref(ctx)) == _lib.KF_ERR_ARG
 

@@ -1,9 +1,9 @@
 """Parity at the benchmark's full size and launch configuration.
 
 The PU-200-like batch (100 events x 8,000 tracks, 20% noise, N = 10) runs as
-the benchmark runs it: 10 lanes per seed, 256-thread blocks, persistent
-launch, one captured graph with binning, finding, duplicate removal, fit and
-adjoint.  The oracle checks sampled outputs it can compute one by one:
+the benchmark runs it: the finding kernel's launch shape chosen by the
+autotuner, then one captured graph with binning, finding, duplicate removal,
+fit and adjoint.  The oracle checks sampled outputs it can compute one by one:
 found hit lists of 600 seeds from three events, duplicate flags of one whole
 event, fits and seed gradients of sampled kept tracks.
 """
@@ -23,8 +23,9 @@ def pu200():
     from paper_1906_11744_gb300 import kf_get_gradient
     b = make_batch("c4")
     dev = torch.device("cuda:0")
-    t = tracker_for(b, device=dev, lanes_per_seed=10, block_threads=256, persistent=1)
+    t = tracker_for(b, device=dev)
     s = torch.cuda.Stream()
+    t.autotune(s)
     t.capture_graph(with_adjoint=True, stream=s)
     t.launch_graph(stream=s)
     s.synchronize()

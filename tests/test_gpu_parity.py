@@ -97,14 +97,16 @@ def test_find_candidate_counts(cands):
     assert not unexplained, unexplained
 
 
-@pytest.mark.parametrize("lanes,threads,persistent", [(8, 64, 0), (16, 256, 1), (6, 128, 1), (12, 96, 0)])
-def test_launch_shapes_give_identical_results(lanes, threads, persistent):
-    """Lanes per seed, block size and launch form change nothing in the result."""
+@pytest.mark.parametrize("lanes,threads,persistent,regcap", [
+    (8, 64, 0, 0), (16, 256, 1, 0), (6, 128, 1, 0), (12, 96, 0, 0),
+    (10, 128, 1, 1), (8, 64, 0, 1), (16, 96, 1, 1)])
+def test_launch_shapes_give_identical_results(lanes, threads, persistent, regcap):
+    """Lanes per seed, block size, register cap and launch form change nothing in the result."""
     b = make_batch("c1", tracks=600)
     base = tracker_for(b)
     base.find_tracks()
     r0 = base.get_tracks()
-    t = tracker_for(b, lanes_per_seed=lanes, block_threads=threads, persistent=persistent)
+    t = tracker_for(b, lanes_per_seed=lanes, block_threads=threads, persistent=persistent, find_regcap=regcap)
     t.find_tracks()
     r1 = t.get_tracks()
     for k in ("hits", "n_found", "chi2", "params", "cov"):
