@@ -21,6 +21,11 @@
 //     theorem (ds/dp = -(dg/dp)/(dg/ds) for g = x(s)^2 + y(s)^2 - R^2) and
 //     d sinc/dpsi = f1, d cosc/dpsi = f2.
 // The adjoint of the final state is zero: the objective is the chi2 sum.
+// Alignment: the corrected position depends on the layer's offsets only, and
+// a rotation keeps cross products, so the alignment gradient of layer L is
+// the sum over its hits of (-(x g_y - y g_x)/R_L, -g_z), g the gradient with
+// respect to the raw position (x, y, z) of the hit; one pass over the hits
+// forms it from the hit gradients after the sweep.
 // Tracks the fit flagged for a near-tangent crossing go to a second pass that
 // keeps their adjoints in double and runs the near-tangent steps in double.
 #include <type_traits>
@@ -33,6 +38,10 @@ namespace kfg {
 namespace {
 
 constexpr float ADJ_CAREFUL_COS = 0.5f;
+// Threads per block of the adjoint kernels; also the row stride (in floats)
+// of the segment buffer in shared memory.
+constexpr int ADJ_THREADS = 128;
+constexpr int LD = ADJ_THREADS;
 
 // Derivatives of f1 and f2 (the helix functions of kf_common.cuh) in psi:
 // f1' = -(sin psi + 2 f1)/psi, f2' = (cos psi - 2 f2)/psi, by the term-wise
@@ -217,12 +226,12 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
 
 // Reverse of one step.  In: the state before the step (p_in, C_in), the
 // adjoints of the state after it (pb, Cb: Cb a full symmetric 6x6).  Out: pb,
-// Cb replaced by the adjoints of the state before it; the hit and alignment
-// gradients of this step in hb[3], ab[2].
+// Cb replaced by the adjoints of the state before it; the gradient of this
+// step with respect to the raw hit position in hb[3].
 template <class S>
 __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], const S (&C_in)[21],
                                          const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
-                                         S (&hb)[3], S (&ab)[2]) {
+                                         S (&hb)[3]) {
   // ---- forward recompute of the step
   S q[6], J[6][6], Cp[21], s_len = S(0);
 #pragma unroll
@@ -339,14 +348,11 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   pbp[2] -= rb1;
   pbp[0] = kfma(Hb00, q[0] * q[1] * irho3, kfma(Hb01, q[1] * q[1] * irho3, pbp[0]));
   pbp[1] = kfma(-Hb00, q[0] * q[0] * irho3, kfma(-Hb01, q[0] * q[1] * irho3, pbp[1]));
-  // hit and alignment
-  const S mbx = -su * rb0, mby = cu * rb0, mbz = rb1;
+  // hit: mbar = (-su, cu) rb0 + e_z rb1, rotated back to the raw position
+  const S mbx = -su * rb0, mby = cu * rb0;
   hb[0] = kfma(h.ca, mbx, h.sa * mby);
   hb[1] = kfma(-h.sa, mbx, h.ca * mby);
-  hb[2] = mbz;
-  const S alpha_b = kfma(-h.my, mbx, h.mx * mby);  // d/d(rotation angle)
-  ab[0] = -alpha_b / h.R;                           // angle = -a_rphi / R
-  ab[1] = -mbz;
+  hb[2] = rb1;
   // ---- reverse: propagation
   if (first) {
 #pragma unroll
@@ -429,43 +435,45 @@ __device__ __forceinline__ bool near_tangent(const DevGeom& g, const float (&p)[
   return cosa < ADJ_CAREFUL_COS;
 }
 
-// Forward step in precision S on float storage.
+// Forward step in precision S on float storage: the state before the step at
+// st[q * LD], q < 27; the state after it goes to st[(27 + q) * LD].
 template <class S>
 __device__ __noinline__ void fwd_step_store(const DevGeom& g, float* st, const Hit<S>& h, bool first, bool last) {
   S p[6], C[21];
-  for (int q = 0; q < 6; ++q) p[q] = (S)st[q];
-  for (int q = 0; q < 21; ++q) C[q] = (S)st[6 + q];
+  for (int q = 0; q < 6; ++q) p[q] = (S)st[q * LD];
+  for (int q = 0; q < 21; ++q) C[q] = (S)st[(6 + q) * LD];
   fwd_step<S>(g, p, C, h, first, last);
-  for (int q = 0; q < 6; ++q) st[27 + q] = (float)p[q];
-  for (int q = 0; q < 21; ++q) st[27 + 6 + q] = (float)C[q];
+  for (int q = 0; q < 6; ++q) st[(27 + q) * LD] = (float)p[q];
+  for (int q = 0; q < 21; ++q) st[(27 + 6 + q) * LD] = (float)C[q];
 }
 
 // Reverse step in precision S with the adjoints kept in A (double in the
-// careful pass, float otherwise).
+// careful pass, float otherwise); the state before the step at st[q * LD].
 template <class S, class A>
 __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, const Hit<S>& h, bool first,
-                                            bool last, A (&pbA)[6], A (&CbA)[6][6], A (&hbA)[3], A (&abA)[2]) {
-  S p[6], C[21], pb[6], Cb[6][6], hb[3], ab[2];
-  for (int q = 0; q < 6; ++q) p[q] = (S)st[q];
-  for (int q = 0; q < 21; ++q) C[q] = (S)st[6 + q];
+                                            bool last, A (&pbA)[6], A (&CbA)[6][6], A (&hbA)[3]) {
+  S p[6], C[21], pb[6], Cb[6][6], hb[3];
+  for (int q = 0; q < 6; ++q) p[q] = (S)st[q * LD];
+  for (int q = 0; q < 21; ++q) C[q] = (S)st[(6 + q) * LD];
   for (int i = 0; i < 6; ++i) {
     pb[i] = (S)pbA[i];
     for (int j = 0; j < 6; ++j) Cb[i][j] = (S)CbA[i][j];
   }
-  rev_step<S>(g, p, C, h, first, last, pb, Cb, hb, ab);
+  rev_step<S>(g, p, C, h, first, last, pb, Cb, hb);
   for (int i = 0; i < 6; ++i) {
     pbA[i] = (A)pb[i];
     for (int j = 0; j < 6; ++j) CbA[i][j] = (A)Cb[i][j];
   }
   for (int i = 0; i < 3; ++i) hbA[i] = (A)hb[i];
-  for (int i = 0; i < 2; ++i) abA[i] = (A)ab[i];
 }
 
 // Reverse sweep of one fitted track from the fit's checkpoints.  CAREFUL:
 // the track the fit flagged as near-tangent; its near-tangent steps run in
-// double precision and its adjoints are kept in double.
+// double precision and its adjoints are kept in double.  seg: this thread's
+// column of the block's segment buffer in shared memory (states before each
+// step of a segment, [slot][27][LD]).
 template <bool CAREFUL>
-__device__ void adjoint_track(const AdjParams& P, int t, double* sh_align) {
+__device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
   using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
   if (!CAREFUL) {
@@ -489,17 +497,16 @@ __device__ void adjoint_track(const AdjParams& P, int t, double* sh_align) {
     pb[i] = A(0);
     for (int j = 0; j < 6; ++j) Cb[i][j] = A(0);
   }
-  float seg[(MAX_CKPT_STRIDE + 1) * 27];  // states before each step of a segment
   for (int c = (n - 1) / stride; c >= 0; --c) {
     const int k0 = c * stride, k1 = min(n, k0 + stride);
     const float* ck = P.ckpt + (size_t)c * 27 * P.ns + t;
-    for (int q = 0; q < 27; ++q) seg[q] = ck[(size_t)q * P.ns];
+    for (int q = 0; q < 27; ++q) seg[q * LD] = ck[(size_t)q * P.ns];
     for (int k = k0; k + 1 < k1; ++k) {
-      float* st = seg + (k - k0) * 27;
+      float* st = seg + (k - k0) * 27 * LD;
       const int hi = hoff + lst[k];
       if (CAREFUL && k > 0) {
         float pf[6];
-        for (int q = 0; q < 6; ++q) pf[q] = st[q];
+        for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
         if (near_tangent(g, pf, g.radius[P.hlayer[hi]])) {
           fwd_step_store<double>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n);
           continue;
@@ -508,27 +515,22 @@ __device__ void adjoint_track(const AdjParams& P, int t, double* sh_align) {
       fwd_step_store<float>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      const float* st = seg + (k - k0) * 27;
+      const float* st = seg + (k - k0) * 27 * LD;
       const int hl = lst[k];
       const int hi = hoff + hl;
-      A hb[3], ab[2];
+      A hb[3];
       bool dbl = false;
       if (CAREFUL && k > 0) {
         float pf[6];
-        for (int q = 0; q < 6; ++q) pf[q] = st[q];
+        for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
         dbl = near_tangent(g, pf, g.radius[P.hlayer[hi]]);
       }
-      if (dbl) rev_step_store<double, A>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb, ab);
-      else rev_step_store<float, A>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb, ab);
-      if (P.g_hits) {
-        float* gh = P.g_hits + 3 * (size_t)hi;
-        atomicAdd(gh + 0, (float)hb[0]);
-        atomicAdd(gh + 1, (float)hb[1]);
-        atomicAdd(gh + 2, (float)hb[2]);
-      }
-      const int L = P.hlayer[hi];
-      atomicAdd(sh_align + 2 * L, (double)ab[0]);
-      atomicAdd(sh_align + 2 * L + 1, (double)ab[1]);
+      if (dbl) rev_step_store<double, A>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      else rev_step_store<float, A>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
+      atomicAdd(gh + 0, (float)hb[0]);
+      atomicAdd(gh + 1, (float)hb[1]);
+      atomicAdd(gh + 2, (float)hb[2]);
     }
   }
   if (P.g_seed) {
@@ -537,21 +539,44 @@ __device__ void adjoint_track(const AdjParams& P, int t, double* sh_align) {
 }
 
 template <bool CAREFUL>
-__global__ void __launch_bounds__(128) k_adjoint(const AdjParams P) {
-  __shared__ double sh_align[2 * KF_MAX_LAYERS];
-  for (int i = threadIdx.x; i < 2 * KF_MAX_LAYERS; i += blockDim.x) sh_align[i] = 0.0;
-  __syncthreads();
-  if (!CAREFUL) {
+__global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
+  extern __shared__ float seg_all[];  // [stride][27][LD]
+  float* seg = seg_all + threadIdx.x;
+  if constexpr (!CAREFUL) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.ns) adjoint_track<false>(P, t, sh_align);
+    if (t < P.ns) adjoint_track<false>(P, t, seg);
   } else {
     const unsigned n = *P.careful_count;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      adjoint_track<true>(P, P.careful_list[i], sh_align);
+      adjoint_track<true>(P, P.careful_list[i], seg);
+  }
+}
+
+// Alignment gradient from the hit gradients: per warp, per-layer sums in
+// shared memory (atomics only between lanes on the same layer), then one
+// double-precision add per block and layer.
+constexpr int ALIGN_THREADS = 256;
+__global__ void __launch_bounds__(ALIGN_THREADS) k_align_grad(const AdjParams P) {
+  constexpr int NW = ALIGN_THREADS / 32;
+  __shared__ float acc[NW][2 * KF_MAX_LAYERS];
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < NW * 2 * KF_MAX_LAYERS; i += blockDim.x) (&acc[0][0])[i] = 0.f;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n_hits; i += gridDim.x * blockDim.x) {
+    const int L = P.hlayer[i];
+    const float gx = P.g_hits[3 * (size_t)i], gy = P.g_hits[3 * (size_t)i + 1], gz = P.g_hits[3 * (size_t)i + 2];
+    if (gx == 0.f && gy == 0.f && gz == 0.f) continue;  // hit on no fitted track
+    const float cr = fmaf(P.hx[i], gy, -P.hy[i] * gx);
+    atomicAdd(&acc[warp][2 * L], -cr / P.g.radius[L]);
+    atomicAdd(&acc[warp][2 * L + 1], -gz);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * P.g.n_layers; i += blockDim.x)
-    if (sh_align[i] != 0.0) atomicAdd(P.g_align_acc + i, sh_align[i]);
+  for (int i = threadIdx.x; i < 2 * P.g.n_layers; i += blockDim.x) {
+    double a = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) a += (double)acc[w][i];
+    if (a != 0.0) atomicAdd(P.g_align_acc + i, a);
+  }
 }
 
 __global__ void k_adjoint_finish(const AdjParams P) {
@@ -566,13 +591,26 @@ bool adjoint_stride_ok(int stride, int max_len) {
 }
 
 cudaError_t launch_adjoint(const AdjParams& P, cudaStream_t st) {
+  if (!P.g_hits) return cudaErrorInvalidValue;  // the alignment gradient is formed from it
   cudaError_t e = cudaMemsetAsync(P.g_align_acc, 0, sizeof(double) * 2 * KF_MAX_LAYERS, st);
-  if (e == cudaSuccess && P.g_hits) e = cudaMemsetAsync(P.g_hits, 0, sizeof(float) * 3 * (size_t)P.n_hits, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.g_hits, 0, sizeof(float) * 3 * (size_t)P.n_hits, st);
   if (e != cudaSuccess) return e;
-  const int threads = 128;
+  const size_t smem = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
+  e = cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   if (P.ns > 0) {
-    k_adjoint<false><<<(P.ns + threads - 1) / threads, threads, 0, st>>>(P);
-    k_adjoint<true><<<(P.ns / 20 + threads - 1) / threads + 1, threads, 0, st>>>(P);
+    k_adjoint<false><<<(P.ns + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, smem, st>>>(P);
+    k_adjoint<true><<<(P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1, ADJ_THREADS, smem, st>>>(P);
+  }
+  if (P.n_hits > 0) {
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = min((P.n_hits + ALIGN_THREADS - 1) / ALIGN_THREADS, 8 * sms);
+    k_align_grad<<<blocks, ALIGN_THREADS, 0, st>>>(P);
   }
   k_adjoint_finish<<<1, 2 * KF_MAX_LAYERS, 0, st>>>(P);
   return cudaGetLastError();

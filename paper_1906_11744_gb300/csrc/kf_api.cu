@@ -597,10 +597,11 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   const size_t ns = (size_t)ctx->n_seeds, nh = (size_t)ctx->n_hits;
   CK(grow(ctx->adj_align_acc, sizeof(double) * 2 * KF_MAX_LAYERS));
   CK(grow(ctx->adj_align, sizeof(float) * 2 * KF_MAX_LAYERS));
-  if (!device_ptrs) {
-    if (g_hits) CK(grow(ctx->adj_hits, sizeof(float) * 3 * nh));
-    if (g_seed) CK(grow(ctx->adj_seed, sizeof(float) * 6 * ns));
-  }
+  // The hit gradient is always formed (the alignment gradient is summed from
+  // it); without a device array from the caller it goes to the context.
+  const bool own_hits = !(device_ptrs && g_hits);
+  if (own_hits) CK(grow(ctx->adj_hits, sizeof(float) * 3 * nh));
+  if (!device_ptrs && g_seed) CK(grow(ctx->adj_seed, sizeof(float) * 6 * ns));
   AdjParams A;
   A.g = ctx->g;
   A.hx = F.hx;
@@ -620,7 +621,7 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   A.keep = F.keep;
   A.fit_status = F.fit_status;
   A.stride = stride;
-  A.g_hits = g_hits ? (device_ptrs ? g_hits : ptr<float>(ctx->adj_hits)) : nullptr;
+  A.g_hits = own_hits ? ptr<float>(ctx->adj_hits) : g_hits;
   A.g_seed = g_seed ? (device_ptrs ? g_seed : ptr<float>(ctx->adj_seed)) : nullptr;
   A.g_align = device_ptrs ? g_align : ptr<float>(ctx->adj_align);
   A.g_align_acc = ptr<double>(ctx->adj_align_acc);

@@ -130,7 +130,7 @@ struct AdjParams {
   const unsigned char* keep;   // may be null
   const int* fit_status;       // tracks with a status other than KF_FIT_OK are skipped
   int stride;                  // checkpoint stride
-  float* g_hits;               // [n_hits][3] or null
+  float* g_hits;               // [n_hits][3] (required: the alignment gradient is summed from it)
   float* g_seed;               // [6][ns] or null
   float* g_align;              // [n_layers][2]
   double* g_align_acc;         // [2 * KF_MAX_LAYERS] accumulator
