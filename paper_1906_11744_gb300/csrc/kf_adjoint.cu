@@ -590,7 +590,7 @@ bool adjoint_stride_ok(int stride, int max_len) {
   return stride >= 1 && stride <= MAX_CKPT_STRIDE && max_len <= MAX_CKPT * stride;
 }
 
-cudaError_t launch_adjoint(const AdjParams& P, cudaStream_t st) {
+cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
   if (!P.g_hits) return cudaErrorInvalidValue;  // the alignment gradient is formed from it
   cudaError_t e = cudaMemsetAsync(P.g_align_acc, 0, sizeof(double) * 2 * KF_MAX_LAYERS, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.g_hits, 0, sizeof(float) * 3 * (size_t)P.n_hits, st);
@@ -599,14 +599,26 @@ cudaError_t launch_adjoint(const AdjParams& P, cudaStream_t st) {
   e = cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (P.ns > 0) {
+  return e;
+}
+
+cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t st) {
+  if (P.ns <= 0) return cudaSuccess;
+  const size_t smem = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
+  if (!careful) {
     k_adjoint<false><<<(P.ns + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, smem, st>>>(P);
+  } else {
+    // flagged tracks are a few percent: a grid for a twentieth of all,
+    // striding over however many there are
     k_adjoint<true><<<(P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1, ADJ_THREADS, smem, st>>>(P);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_end(const AdjParams& P, cudaStream_t st) {
   if (P.n_hits > 0) {
     int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
+    cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int blocks = min((P.n_hits + ALIGN_THREADS - 1) / ALIGN_THREADS, 8 * sms);

@@ -2,6 +2,7 @@
 // autotuner.  The calls follow the paper's problem statement: load hits and
 // seeds (Sec. 3), find tracks (Sec. 2), remove duplicates (Sec. 4.2), fit
 // tracks (Sec. 5).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,7 +37,7 @@ struct kf_ctx {
   // binning
   DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp;
   // finding
-  DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status;
+  DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent;
   // duplicate removal scratch
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state;
   // fit
@@ -51,6 +52,10 @@ struct kf_ctx {
   cudaGraphExec_t exec = nullptr;
   int stage_timing = 0;
   cudaEvent_t ev[10] = {};  // start/end of bin, find, dedup, fit, adjoint
+  // Side stream (highest priority) for the careful passes that run beside
+  // the main passes; fork/join events.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err = "";
 };
 
@@ -212,6 +217,13 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
       e = cudaMemcpy(ctx->eta_edges.p, edges.data(), sizeof(float) * edges.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = grow(ctx->queue, 64);
+  if (e == cudaSuccess) {
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = grow(ctx->counters, 64);
   if (e == cudaSuccess) e = grow(ctx->status, 64);
   if (e == cudaSuccess) {
@@ -233,12 +245,15 @@ int kf_destroy(kf_ctx* ctx) {
   if (!ctx) return KF_ERR_ARG;
   for (cudaEvent_t& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   DevBuf* bufs[] = {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
                     &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->hb,
                     &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->out_hits,
-                    &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue,
+                    &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent,
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
@@ -328,6 +343,7 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->seed_off, sizeof(int) * (n_events + 1)));
   CK(grow(ctx->out_hits, sizeof(int) * (size_t)n * L));
   CK(grow(ctx->out_n, sizeof(int) * (size_t)n));
+  CK(grow(ctx->tangent, sizeof(int) * (size_t)n));
   CK(grow(ctx->out_chi2, sizeof(float) * (size_t)n));
   CK(grow(ctx->out_p, sizeof(float) * 6 * (size_t)n));
   CK(grow(ctx->out_C, sizeof(float) * 21 * (size_t)n));
@@ -382,6 +398,20 @@ static void stage_mark(kf_ctx* ctx, int i, cudaStream_t st) {
   else cudaEventRecord(ctx->ev[i], st);
 }
 
+// Work on ctx->side after everything enqueued so far on st (fork), and st
+// after everything enqueued on ctx->side (join).  Inside a stream capture the
+// side stream joins the capture and becomes a parallel branch of the graph.
+static cudaError_t fork_side(kf_ctx* ctx, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  return e;
+}
+static cudaError_t join_side(kf_ctx* ctx, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(ctx->ev_join, ctx->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_join, 0);
+  return e;
+}
+
 static FindParams find_params(kf_ctx* ctx) {
   FindParams P;
   P.g = ctx->g;
@@ -407,6 +437,7 @@ static FindParams find_params(kf_ctx* ctx) {
   P.out_p = ptr<float>(ctx->out_p);
   P.out_C = ptr<float>(ctx->out_C);
   P.queue = ptr<unsigned>(ctx->queue);
+  P.tangent_list = ptr<int>(ctx->tangent);
   P.counters = ptr<unsigned long long>(ctx->counters);
   P.persistent = ctx->persistent;
   return P;
@@ -431,6 +462,13 @@ static BinParams bin_params(kf_ctx* ctx) {
   return B;
 }
 
+// Blocks of the careful pass over the seeds the main pass gave up (a few
+// percent, 12 per block and round; two blocks fit an SM): enough for all of
+// them in about one round, at most two blocks per SM.
+static int careful_grid(const kf_ctx* ctx, int n_seeds) {
+  return std::max(1, std::min(2 * ctx->num_sms, (n_seeds / 50 + 11) / 12));
+}
+
 int kf_find_tracks(kf_ctx* ctx, void* stream) {
   if (!ctx) return KF_ERR_ARG;
   if (ctx->n_hits < 0 || ctx->n_seed_events != ctx->n_events || ctx->n_events < 1)
@@ -447,9 +485,10 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
                   ctx->scan_tmp.bytes / sizeof(unsigned), st));
     stage_mark(ctx, 1, st);
     FindParams P = find_params(ctx);
-    if (P.persistent) CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
+    CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
     stage_mark(ctx, 2, st);
-    CK(launch_find(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
+    CK(launch_find_main(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
+    CK(launch_find_careful(P, ctx->lanes, careful_grid(ctx, P.s_end - P.s_begin), st));
     stage_mark(ctx, 3, st);
   } else {
     for (int e = 0; e < ctx->n_events; ++e) {
@@ -461,8 +500,9 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
       FindParams P = find_params(ctx);
       P.s_begin = ctx->seed_off_h[e];
       P.s_end = ctx->seed_off_h[e + 1];
-      if (P.persistent) CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
-      CK(launch_find(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
+      CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
+      CK(launch_find_main(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
+      CK(launch_find_careful(P, ctx->lanes, careful_grid(ctx, P.s_end - P.s_begin), st));
     }
   }
   ctx->found = true;
@@ -630,7 +670,12 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   A.careful_flag = F.careful_flag;
   A.ckpt = F.ckpt;
   stage_mark(ctx, 8, st);
-  CK(launch_adjoint(A, st));
+  CK(launch_adjoint_begin(A, st));
+  CK(fork_side(ctx, st));
+  CK(launch_adjoint_pass(A, true, ctx->side));  // near-tangent tracks beside the FP32 pass
+  CK(launch_adjoint_pass(A, false, st));
+  CK(join_side(ctx, st));
+  CK(launch_adjoint_end(A, st));
   stage_mark(ctx, 9, st);
   if (!device_ptrs) {
     CK(cudaMemcpyAsync(g_align, A.g_align, sizeof(float) * 2 * ctx->g.n_layers, cudaMemcpyDeviceToHost, st));
@@ -754,7 +799,7 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   }
   if (e != cudaSuccess) return fail(ctx, KF_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
   ctx->graph = graph;
-  CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, 0));
+  CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, cudaGraphInstantiateFlagUseNodePriority));
   return KF_OK;
 }
 

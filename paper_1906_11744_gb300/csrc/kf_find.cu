@@ -45,10 +45,38 @@ __host__ __device__ constexpr int smem_per_warp(int n_layers) {
 constexpr float WIN_REL = 1e-3f;
 constexpr float WIN_PHI_ABS = 1e-5f;  // rad
 constexpr float WIN_Z_ABS = 1e-4f;    // cm
+// Crossings closer to tangent than this (cos of the angle between direction
+// and radial direction) are propagated in double: the FP32 error of the
+// transported covariance grows as 1/cos^4 and near the turning radius of a
+// looper it can leave the prediction without a positive definite S.  The
+// main pass gives up a seed whose candidates meet such a crossing (after that
+// layer its lanes go idle) and lists it; a careful pass after it (the same
+// kernel with CAREFUL) redoes the listed seeds with those propagations in
+// double, so that the double code and its registers stay out of the main
+// pass.  About 1.4% of the seeds of a PU-200 batch (low-pT loopers).
+constexpr float FIND_CAREFUL_COS = 0.5f;
+constexpr int CAREFUL_THREADS = 128;
+
+// Double-precision propagation of the state st[0..26] (p, then C) in place;
+// st is the lane's child list in shared memory, unused at this point.
+__device__ __noinline__ int careful_propagate(float* st, float R, float kb, float z_lim) {
+  double p[6], C[21];
+  for (int k = 0; k < 6; ++k) p[k] = st[k];
+  for (int k = 0; k < 21; ++k) C[k] = st[6 + k];
+  const int rc = propagate<double>(p, C, (double)R, (double)kb, (double)z_lim);
+  if (rc == 1) {
+    for (int k = 0; k < 6; ++k) st[k] = (float)p[k];
+    for (int k = 0; k < 21; ++k) st[6 + k] = (float)C[k];
+  }
+  return rc;
+}
 
 // CAP = 0: blocks of up to 256 threads, registers at the compiler's choice;
 // CAP = 1: blocks of up to 128 threads, five per SM (at most 102 registers).
-template <int G, int CAP>
+// CAREFUL: the pass over the seeds the main pass listed (always persistent).
+// Counters in P.queue: [0] main-pass work, [1] careful-pass work, [2] number
+// of listed seeds.
+template <int G, int CAP, bool CAREFUL>
 __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const FindParams P) {
   constexpr int W = 32 / G;  // seeds per warp
   extern __shared__ __align__(16) unsigned char smem[];
@@ -67,24 +95,40 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   unsigned long long* slot = reinterpret_cast<unsigned long long*>(ws + SMEM_LIST + SMEM_GATHER);
   int* hist = reinterpret_cast<int*>(ws + SMEM_LIST + SMEM_GATHER + SMEM_SLOT);
   const int N = g.max_cands;
-  const int n_seed_range = P.s_end - P.s_begin;
+  const int n_seed_range = CAREFUL ? (int)P.queue[2] : P.s_end - P.s_begin;
   const int n_tasks = (n_seed_range + W - 1) / W;
   const int warps_per_block = blockDim.x >> 5;
+  unsigned* const queue = P.queue + (CAREFUL ? 1 : 0);
+  // Counters: per-warp sums in shared memory (lane 0 of the warp owns its
+  // row), added to the global counters once when the warp ends.
+  __shared__ unsigned long long s_cnt[8][8];
+  if (lane < 8) s_cnt[warp][lane] = 0ull;
+  __syncwarp();
 
-  unsigned long long c_steps = 0, c_updates = 0, c_chi2 = 0, c_seeds = 0, c_holes = 0;
 
   int task;
-  if (P.persistent) {
+  if (CAREFUL || P.persistent) {
     unsigned t = 0;
-    if (lane == 0) t = atomicAdd(P.queue, 1u);
+    if (lane == 0) t = atomicAdd(queue, 1u);
     task = (int)__shfl_sync(0xffffffffu, t, 0);
   } else {
     task = blockIdx.x * warps_per_block + warp;
   }
 
   while (task < n_tasks) {
-    const int seed = P.s_begin + task * W + grp;
-    const bool has_seed = lane_used && (seed < P.s_end);
+    int seed;
+    bool has_seed;
+    if constexpr (CAREFUL) {
+      const int j = task * W + grp;
+      has_seed = lane_used && j < n_seed_range;
+      seed = has_seed ? P.tangent_list[j] : 0;
+    } else {
+      seed = P.s_begin + task * W + grp;
+      has_seed = lane_used && (seed < P.s_end);
+    }
+    // counters of this task (dropped for a seed given up)
+    unsigned c_steps = 0, c_updates = 0, c_chi2 = 0, c_seeds = 0, c_holes = 0, c_careful = 0, c_npd = 0;
+    bool near = false, given_up = false;
     int ev = 0, hoff = 0;
     float p[6], C[21];
     float chi2 = 0.f;
@@ -113,7 +157,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       for (int k = 0; k < 21; ++k) C[k] = 0.f;
     }
     const int start = has_seed ? sl2 + 1 : L;           // first layer searched
-    const int n_iter = has_seed ? 3 + (L - start) : 0;  // seed hits + layers
+    int n_iter = has_seed ? 3 + (L - start) : 0;        // seed hits + layers
     const int it_end = __reduce_max_sync(0xffffffffu, n_iter);
 
 #pragma unroll 1
@@ -136,7 +180,32 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             for (int k = 0; k < 21; ++k) bak[6 + k] = C[k];
           }
           const float R = g.radius[l];
-          const int pr = (it == 0) ? 1 : propagate<float>(p, C, R, g.kb, in_seed ? INFINITY : g.z_max);
+          int pr = 1;
+          if (it != 0) {
+            const float z_lim = in_seed ? INFINITY : g.z_max;
+            float q[6], J[6][6], cosa = 1.f;
+            pr = prop_jacobian<float>(p, R, g.kb, z_lim, q, J, &cosa);
+            if (CAREFUL && pr == 1 && cosa < FIND_CAREFUL_COS) {
+              float* st = reinterpret_cast<float*>(lst);
+#pragma unroll
+              for (int k = 0; k < 6; ++k) st[k] = p[k];
+#pragma unroll
+              for (int k = 0; k < 21; ++k) st[6 + k] = C[k];
+              pr = careful_propagate(st, R, g.kb, z_lim);
+              if (pr == 1) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) p[k] = st[k];
+#pragma unroll
+                for (int k = 0; k < 21; ++k) C[k] = st[6 + k];
+              }
+              c_careful++;
+            } else if (pr == 1) {
+              if (!CAREFUL && cosa < FIND_CAREFUL_COS) near = true;
+              transport<float>(J, C);
+#pragma unroll
+              for (int k = 0; k < 6; ++k) p[k] = q[k];
+            }
+          }
           if (pr != 1) {
             cls = 1;
             finished = true;
@@ -147,6 +216,10 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
               c_steps++;
               Frame f;
               make_frame<float>(p, C, g.vr, g.vz, f);
+              // A prediction without a positive definite S searches no hits
+              // (the careful propagation should leave none; counted).
+              const bool spd = f.s00 > 0.f && f.si00 > 0.f && f.si11 > 0.f;
+              if (!spd) c_npd++;
               const Align4 al = P.align[l];
               // Window containing the ellipse chi2 < cut: |r_rphi| < sqrt(cut S00)
               // with r_rphi = R_hit sin(dphi) on the near half, |r_z| < sqrt(cut S11).
@@ -168,7 +241,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
               const float wz = w2 * (1.f + WIN_REL) + WIN_Z_ABS;
               const float* edges = P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1);
               const int e0 = eta_bin(zc - wz, R, g.eta_max[l], neta, edges);
-              const int e1 = eta_bin(zc + wz, R, g.eta_max[l], neta, edges);
+              const int e1 = spd ? eta_bin(zc + wz, R, g.eta_max[l], neta, edges) : e0 - 1;
               const unsigned* off = P.bin_off + ((size_t)ev * L + l) * ((size_t)neta * nphi);
               const int nf1 = nfound + 1;
               const int b1 = min(b0 + span, nphi);
@@ -230,6 +303,15 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       // fit keeps its single candidate).
       unsigned long long mine = KEY_EMPTY;
       int par = gl, p_holes = nholes, p_cls = cls;
+      if constexpr (!CAREFUL) {
+        // A group with a near-tangent crossing gives its seed up after this
+        // layer (its lanes go idle) and lists it for the careful pass.
+        const unsigned nb = __ballot_sync(0xffffffffu, near);
+        if (lane_used && ((nb >> base) & ((1u << G) - 1u)) && !given_up) {
+          given_up = true;
+          n_iter = min(n_iter, it + 1);
+        }
+      }
       if (__any_sync(0xffffffffu, active && !in_seed)) {
         // Rank of each child = its position in its own sorted list + the
         // number of smaller keys in the other lists of the group (keys are
@@ -327,8 +409,32 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       __syncwarp();
     }
 
+    if (given_up) {
+      if (has_seed && gl == 0) P.tangent_list[atomicAdd(P.queue + 2, 1u)] = seed;
+      c_steps = c_updates = c_chi2 = c_seeds = c_holes = c_npd = 0;
+    }
+    // Counters of the task: summed over the warp into its shared row.
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      c_steps += __shfl_xor_sync(0xffffffffu, c_steps, off);
+      c_updates += __shfl_xor_sync(0xffffffffu, c_updates, off);
+      c_chi2 += __shfl_xor_sync(0xffffffffu, c_chi2, off);
+      c_seeds += __shfl_xor_sync(0xffffffffu, c_seeds, off);
+      c_holes += __shfl_xor_sync(0xffffffffu, c_holes, off);
+      c_careful += __shfl_xor_sync(0xffffffffu, c_careful, off);
+      c_npd += __shfl_xor_sync(0xffffffffu, c_npd, off);
+    }
+    if (lane == 0) {
+      s_cnt[warp][0] += c_steps;
+      s_cnt[warp][1] += c_updates;
+      s_cnt[warp][2] += c_chi2;
+      s_cnt[warp][3] += c_seeds;
+      s_cnt[warp][4] += c_holes;
+      s_cnt[warp][5] += c_careful;
+      s_cnt[warp][6] += c_npd;
+    }
     // The best candidate sits in slot 0: rebuild its hit list.
-    if (has_seed && gl == 0) {
+    if (has_seed && gl == 0 && !given_up) {
       int* oh = P.out_hits + (size_t)seed * L;
       int k = nfound - 1;
       int cur = 0;
@@ -350,53 +456,41 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     }
     __syncwarp();
 
-    if (P.persistent) {
+    if (CAREFUL || P.persistent) {
       unsigned t = 0;
-      if (lane == 0) t = atomicAdd(P.queue, 1u);
+      if (lane == 0) t = atomicAdd(queue, 1u);
       task = (int)__shfl_sync(0xffffffffu, t, 0);
     } else {
       break;
     }
   }
-
-  // Counters: one atomic per warp.
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    c_steps += __shfl_xor_sync(0xffffffffu, c_steps, off);
-    c_updates += __shfl_xor_sync(0xffffffffu, c_updates, off);
-    c_chi2 += __shfl_xor_sync(0xffffffffu, c_chi2, off);
-    c_seeds += __shfl_xor_sync(0xffffffffu, c_seeds, off);
-    c_holes += __shfl_xor_sync(0xffffffffu, c_holes, off);
-  }
-  if (lane == 0 && P.counters) {
-    atomicAdd(&P.counters[0], c_steps);
-    atomicAdd(&P.counters[1], c_updates);
-    atomicAdd(&P.counters[2], c_chi2);
-    atomicAdd(&P.counters[3], c_seeds);
-    atomicAdd(&P.counters[4], c_holes);
-  }
+  __syncwarp();
+  if (lane < 7 && P.counters && s_cnt[warp][lane]) atomicAdd(&P.counters[lane], s_cnt[warp][lane]);
 }
 
 template <int G, int CAP>
 cudaError_t prepare_g(int threads, int n_layers, int* blocks_per_sm) {
   const size_t smem = (size_t)(threads / 32) * smem_per_warp(n_layers);
-  cudaError_t err = cudaFuncSetAttribute(k_find<G, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t err = cudaFuncSetAttribute(k_find<G, CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_find<G, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((CAREFUL_THREADS / 32) * smem_per_warp(n_layers)));
   if (err != cudaSuccess) return err;
   cudaFuncAttributes fa;
-  err = cudaFuncGetAttributes(&fa, k_find<G, CAP>);
+  err = cudaFuncGetAttributes(&fa, k_find<G, CAP, false>);
   if (err != cudaSuccess) return err;
   if (threads > fa.maxThreadsPerBlock) {  // the launch bounds forbid this block size
     if (blocks_per_sm) *blocks_per_sm = 0;
     return cudaSuccess;
   }
   if (blocks_per_sm)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_find<G, CAP>, threads, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_find<G, CAP, false>, threads, smem);
   return err;
 }
 
 template <int G, int CAP>
-cudaError_t launch_g(const FindParams& P, int threads, int grid_cap, cudaStream_t st) {
+cudaError_t launch_main_g(const FindParams& P, int threads, int grid_cap, cudaStream_t st) {
   const size_t smem = (size_t)(threads / 32) * smem_per_warp(P.g.n_layers);
   constexpr int W = 32 / G;
   const int n = P.s_end - P.s_begin;
@@ -405,7 +499,14 @@ cudaError_t launch_g(const FindParams& P, int threads, int grid_cap, cudaStream_
   int grid = (n_tasks + wpb - 1) / wpb;
   if (P.persistent && grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
-  k_find<G, CAP><<<grid, threads, smem, st>>>(P);
+  k_find<G, CAP, false><<<grid, threads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int G, int CAP>
+cudaError_t launch_careful_g(const FindParams& P, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)(CAREFUL_THREADS / 32) * smem_per_warp(P.g.n_layers);
+  k_find<G, 0, true><<<grid, CAREFUL_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -439,10 +540,16 @@ cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* 
   KF_FIND_DISPATCH(prepare_g, threads, n_layers, blocks_per_sm)
 }
 
-cudaError_t launch_find(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
-                        cudaStream_t st) {
+cudaError_t launch_find_main(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
+                             cudaStream_t st) {
   if (P.s_end <= P.s_begin) return cudaSuccess;
-  KF_FIND_DISPATCH(launch_g, P, threads, grid_cap, st)
+  KF_FIND_DISPATCH(launch_main_g, P, threads, grid_cap, st)
+}
+
+cudaError_t launch_find_careful(const FindParams& P, int lanes, int grid, cudaStream_t st) {
+  if (P.s_end <= P.s_begin) return cudaSuccess;
+  const int regcap = 0;
+  KF_FIND_DISPATCH(launch_careful_g, P, grid, st)
 }
 
 }  // namespace kfg

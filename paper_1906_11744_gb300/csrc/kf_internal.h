@@ -38,8 +38,10 @@ struct FindParams {
   float* out_chi2;           // [ns]
   float* out_p;              // [6][ns]
   float* out_C;              // [21][ns]
-  unsigned* queue;           // persistent work counter (zeroed before the launch)
-  unsigned long long* counters;  // [4]
+  unsigned* queue;           // [3] work counters of the main and careful passes and the
+                             // number of listed seeds (zeroed before the launch)
+  int* tangent_list;         // [ns] seeds the main pass left to the careful pass
+  unsigned long long* counters;  // [8], see kf_get_counters
   int persistent;
 };
 
@@ -141,11 +143,19 @@ struct AdjParams {
 };
 
 // kf_adjoint.cu
-cudaError_t launch_adjoint(const AdjParams& P, cudaStream_t st);
+// Adjoint: zero the accumulators, the FP32 pass and the near-tangent pass
+// (independent: either order or concurrently), then the alignment sum.
+cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st);
+cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t st);
+cudaError_t launch_adjoint_end(const AdjParams& P, cudaStream_t st);
 bool adjoint_stride_ok(int stride, int max_len);
 // kf_find.cu
-cudaError_t launch_find(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
-                        cudaStream_t st);
+// Finding: the main pass (gives up and lists seeds that meet a near-tangent
+// crossing), then the careful pass over the listed seeds (persistent, any
+// grid; the count is read on the device).
+cudaError_t launch_find_main(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
+                             cudaStream_t st);
+cudaError_t launch_find_careful(const FindParams& P, int lanes, int grid, cudaStream_t st);
 size_t find_smem_bytes(int threads, int n_layers);
 bool find_lanes_supported(int lanes);
 // Sets the dynamic shared-memory limit of the kernel variant (must run
