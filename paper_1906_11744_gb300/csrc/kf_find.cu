@@ -39,6 +39,11 @@ static_assert(32 * BACKUP_STRIDE * 4 <= SMEM_GATHER, "backup must fit the gather
 __host__ __device__ constexpr int smem_per_warp(int n_layers) {
   return SMEM_LIST + SMEM_GATHER + SMEM_SLOT + ((32 * n_layers * 4 + 15) / 16) * 16;
 }
+// The careful pass adds each lane's double-precision prediction [32][27].
+constexpr int SMEM_DSTATE = 32 * 27 * 8;
+__host__ __device__ constexpr int smem_per_warp_k(int n_layers, bool careful) {
+  return smem_per_warp(n_layers) + (careful ? SMEM_DSTATE : 0);
+}
 // Window padding: relative and absolute slack on the chi2-ellipse bounds that
 // covers the FP32 rounding of the window arithmetic and of the hit's own
 // angle and eta-bin computation.
@@ -53,22 +58,83 @@ constexpr float WIN_Z_ABS = 1e-4f;    // cm
 // layer its lanes go idle) and lists it; a careful pass after it (the same
 // kernel with CAREFUL) redoes the listed seeds with those propagations in
 // double, so that the double code and its registers stay out of the main
-// pass.  About 1.4% of the seeds of a PU-200 batch (low-pT loopers).
+// pass.  About 1.4% of the seeds of a PU-200 batch (low-pT loopers).  On such
+// a layer the careful pass keeps the prediction in double (shared memory):
+// the measurement frame (S, S^-1) is formed from it in double and only then
+// rounded for the window search, and the children of that prediction are
+// updated (and scattered) in double from it, as the re-fit's careful pass
+// does, because the prediction carries a large nearly rank-one term that
+// FP32 rounding of the covariance would turn indefinite.
 constexpr float FIND_CAREFUL_COS = 0.5f;
 constexpr int CAREFUL_THREADS = 128;
 
 // Double-precision propagation of the state st[0..26] (p, then C) in place;
-// st is the lane's child list in shared memory, unused at this point.
-__device__ __noinline__ int careful_propagate(float* st, float R, float kb, float z_lim) {
+// st is the lane's child list in shared memory, unused at this point.  The
+// double result also goes to dst[0..26].
+__device__ __noinline__ int careful_propagate(float* st, double* dst, float R, float kb, float z_lim) {
   double p[6], C[21];
   for (int k = 0; k < 6; ++k) p[k] = st[k];
   for (int k = 0; k < 21; ++k) C[k] = st[6 + k];
   const int rc = propagate<double>(p, C, (double)R, (double)kb, (double)z_lim);
   if (rc == 1) {
-    for (int k = 0; k < 6; ++k) st[k] = (float)p[k];
-    for (int k = 0; k < 21; ++k) st[6 + k] = (float)C[k];
+    for (int k = 0; k < 6; ++k) {
+      st[k] = (float)p[k];
+      dst[k] = p[k];
+    }
+    for (int k = 0; k < 21; ++k) {
+      st[6 + k] = (float)C[k];
+      dst[6 + k] = C[k];
+    }
   }
   return rc;
+}
+
+// Measurement frame of a double-precision prediction, rounded.
+__device__ __noinline__ Frame careful_frame(const double* dst, float vr, float vz) {
+  double p[6], C[21];
+  for (int k = 0; k < 6; ++k) p[k] = dst[k];
+  for (int k = 0; k < 21; ++k) C[k] = dst[6 + k];
+  FrameT<double> fd;
+  make_frame<double>(p, C, (double)vr, (double)vz, fd);
+  Frame f;
+  f.su = (float)fd.su;
+  f.cu = (float)fd.cu;
+  for (int k = 0; k < 6; ++k) f.a0[k] = (float)fd.a0[k];
+  f.s00 = (float)fd.s00;
+  f.s11 = (float)fd.s11;
+  f.si00 = (float)fd.si00;
+  f.si01 = (float)fd.si01;
+  f.si11 = (float)fd.si11;
+  return f;
+}
+
+// A child of a double-precision prediction in[0..26]: the update with the
+// corrected hit m (upd) and the scattering of the layer (ms; always after an
+// update), in double; the result rounded to out[0..26].  Returns false for a
+// hit on the far half (no update, no scattering); *dchi2 = the hit's chi2.
+__device__ __noinline__ bool careful_child(const double* in, float* out, float mx, float my, float mz, bool upd,
+                                           bool ms, float x0, float vr, float vz, float* dchi2) {
+  double p[6], C[21];
+  for (int k = 0; k < 6; ++k) p[k] = in[k];
+  for (int k = 0; k < 21; ++k) C[k] = in[6 + k];
+  bool ok = true;
+  if (upd) {
+    FrameT<double> f;
+    make_frame<double>(p, C, (double)vr, (double)vz, f);
+    double r0, r1;
+    ok = residual<double>(p, f, (double)mx, (double)my, (double)mz, r0, r1);
+    if (ok) {
+      *dchi2 = (float)chi2_of<double>(f, r0, r1);
+      kf_update<double>(p, C, f, r0, r1);
+      ms = true;
+    } else {
+      ms = false;
+    }
+  }
+  if (ms) add_ms<double>(p, C, (double)x0);
+  for (int k = 0; k < 6; ++k) out[k] = (float)p[k];
+  for (int k = 0; k < 21; ++k) out[6 + k] = (float)C[k];
+  return ok;
 }
 
 // CAP = 0: blocks of up to 256 threads, registers at the compiler's choice;
@@ -88,7 +154,8 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   const bool lane_used = grp < W;
   const DevGeom& g = P.g;
   const int L = g.n_layers;
-  unsigned char* ws = smem + (size_t)warp * smem_per_warp(L);
+  unsigned char* ws = smem + (size_t)warp * smem_per_warp_k(L, CAREFUL);
+  double* const dst_warp = reinterpret_cast<double*>(ws + smem_per_warp(L));  // careful pass only
   unsigned long long* lst = reinterpret_cast<unsigned long long*>(ws) + lane * LIST_STRIDE;
   unsigned long long* gather = reinterpret_cast<unsigned long long*>(ws + SMEM_LIST);
   float* bak = reinterpret_cast<float*>(gather) + lane * BACKUP_STRIDE;
@@ -167,6 +234,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       const int l = in_seed ? (it == 0 ? sl0 : (it == 1 ? sl1 : sl2)) : start + (it - 3);
       int cls = 0;  // 1 = carried unchanged, 2 = propagated with hit/hole children
       int cnt = 0;
+      bool dbl = false;  // careful pass: the prediction of this layer is kept in double
       unsigned long long tail = KEY_EMPTY;
       if (active && occ) {
         if (finished) {
@@ -191,7 +259,8 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
               for (int k = 0; k < 6; ++k) st[k] = p[k];
 #pragma unroll
               for (int k = 0; k < 21; ++k) st[6 + k] = C[k];
-              pr = careful_propagate(st, R, g.kb, z_lim);
+              pr = careful_propagate(st, dst_warp + lane * 27, R, g.kb, z_lim);
+              dbl = pr == 1;
               if (pr == 1) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) p[k] = st[k];
@@ -215,7 +284,8 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             if (!in_seed) {
               c_steps++;
               Frame f;
-              make_frame<float>(p, C, g.vr, g.vz, f);
+              if (CAREFUL && dbl) f = careful_frame(dst_warp + lane * 27, g.vr, g.vz);
+              else make_frame<float>(p, C, g.vr, g.vz, f);
               // A prediction without a positive definite S searches no hits
               // (the careful propagation should leave none; counted).
               const bool spd = f.s00 > 0.f && f.si00 > 0.f && f.si11 > 0.f;
@@ -303,6 +373,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       // fit keeps its single candidate).
       unsigned long long mine = KEY_EMPTY;
       int par = gl, p_holes = nholes, p_cls = cls;
+      bool p_dbl = dbl;
       if constexpr (!CAREFUL) {
         // A group with a near-tangent crossing gives its seed up after this
         // layer (its lanes go idle) and lists it for the careful pass.
@@ -352,6 +423,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         for (int k = 0; k < 21; ++k) nC[k] = __shfl_sync(0xffffffffu, C[k], src);
         p_holes = __shfl_sync(0xffffffffu, nholes, src);
         p_cls = __shfl_sync(0xffffffffu, cls, src);
+        if constexpr (CAREFUL) p_dbl = __shfl_sync(0xffffffffu, (int)dbl, src) != 0;
         if (active && !in_seed) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) p[k] = np[k];
@@ -387,6 +459,31 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             finished = true;
           }
           hist[(grp * L + l) * G + gl] = (par << 24) | (do_update ? hit + 1 : 0);
+        }
+        if (CAREFUL && p_dbl && (do_update || do_ms)) {
+          // child of a double-precision prediction (the parent's, or the
+          // lane's own in the seed fit)
+          float mx = 0.f, my = 0.f, mz = 0.f;
+          if (do_update) {
+            const int hi = hoff + hit;
+            corrected_hit(P.align[l], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+          }
+          float* st = reinterpret_cast<float*>(lst);
+          float dchi2 = 0.f;
+          const double* in = dst_warp + (in_seed ? lane : base + par) * 27;
+          if (careful_child(in, st, mx, my, mz, do_update, do_ms, g.x0[l], g.vr, g.vz, &dchi2)) {
+            if (do_update) {
+              if (in_seed) chi2 += dchi2;
+              if (!in_seed) c_updates++;
+            }
+          } else {
+            finished = true;  // far-side seed hit: the seed fit stops here
+          }
+#pragma unroll
+          for (int k = 0; k < 6; ++k) p[k] = st[k];
+#pragma unroll
+          for (int k = 0; k < 21; ++k) C[k] = st[6 + k];
+          do_update = do_ms = false;
         }
         if (do_update) {
           const int hi = hoff + hit;
@@ -475,7 +572,7 @@ cudaError_t prepare_g(int threads, int n_layers, int* blocks_per_sm) {
                                          (int)smem);
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_find<G, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)((CAREFUL_THREADS / 32) * smem_per_warp(n_layers)));
+                               (int)((CAREFUL_THREADS / 32) * smem_per_warp_k(n_layers, true)));
   if (err != cudaSuccess) return err;
   cudaFuncAttributes fa;
   err = cudaFuncGetAttributes(&fa, k_find<G, CAP, false>);
@@ -505,7 +602,7 @@ cudaError_t launch_main_g(const FindParams& P, int threads, int grid_cap, cudaSt
 
 template <int G, int CAP>
 cudaError_t launch_careful_g(const FindParams& P, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)(CAREFUL_THREADS / 32) * smem_per_warp(P.g.n_layers);
+  const size_t smem = (size_t)(CAREFUL_THREADS / 32) * smem_per_warp_k(P.g.n_layers, true);
   k_find<G, 0, true><<<grid, CAREFUL_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }

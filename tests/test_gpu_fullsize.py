@@ -59,6 +59,45 @@ def test_sampled_found_tracks(pu200):
         assert ok, (e, s, kind, rel)
 
 
+def _most_tangent_seeds(b, events, per_event):
+    """Seeds whose circle (from the seed parameters, centred at distance d with
+    radius rho) crosses a searched layer R at the smallest cos(angle to the
+    radial direction) = d sin(gamma) / R, cos(gamma) = (d^2 + rho^2 - R^2) / (2 d rho)."""
+    K = 0.00299792458
+    R = np.asarray(b.det.radius, np.float64)
+    out = []
+    for e in events:
+        a, c = b.seed_off[e], b.seed_off[e + 1]
+        p = b.params[:, a:c].astype(np.float64)
+        h = -K * b.det.bz * p[3]
+        cx = p[0] - np.sin(p[4]) / h
+        cy = p[1] + np.cos(p[4]) / h
+        d, rho = np.hypot(cx, cy), 1 / np.abs(h)
+        cg = (d[:, None] ** 2 + rho[:, None] ** 2 - R[None, 3:] ** 2) / (2 * d[:, None] * rho[:, None])
+        cos = np.where(np.abs(cg) <= 1, d[:, None] * np.sqrt(np.clip(1 - cg * cg, 0, 1)) / R[None, 3:], np.inf)
+        order = np.argsort(cos.min(axis=1))[:per_event]
+        out += [(e, int(s)) for s in order]
+    return out
+
+
+def test_near_tangent_loopers(pu200):
+    """Low-pT loopers crossing outer layers close to tangentially: the finding
+    redoes them with double-precision prediction, frame and update on those
+    layers; their hit lists must equal the oracle's.  Seeds 391026, 581377 and
+    741665 of this batch once accepted hits with FP64 chi2 above 1000."""
+    b, trk, fit, g_seed, counters = pu200
+    assert counters["not_pd"] == 0
+    assert counters["careful"] > 0
+    cases = [(int(np.searchsorted(b.seed_off, s, side="right") - 1), None, s) for s in (391026, 581377, 741665)]
+    cases = [(e, s - b.seed_off[e]) for e, _, s in cases] + _most_tangent_seeds(b, (5, 50), 15)
+    for e, ls in cases:
+        ref = oracle.find_event(b, e, seeds=(ls, ls + 1))
+        g = trk["hits"][b.seed_off[e] + ls]
+        if not np.array_equal(g, ref["hits"][0]):
+            ok, kind, rel = audit_mismatch(b, e, ls, g, ref["hits"][0])
+            assert ok, (e, ls, kind, rel)
+
+
 def test_whole_event_duplicate_flags(pu200):
     b, trk, fit, g_seed, counters = pu200
     e = 57
