@@ -29,13 +29,13 @@ struct kf_ctx {
   int lanes = 0, threads = 0, persistent = 1, per_event = 0, regcap = 0;
   int num_sms = 0;
   int blocks_per_sm = 1;
-  int n_events = 0, n_hits = 0, n_seeds = 0, n_seed_events = -1;
+  int n_events = 0, n_hits = 0, n_seeds = 0, n_seed_events = -1, max_event_hits = 0;
   std::vector<int> hit_off_h, seed_off_h, seed_event_h;
   size_t n_bins_total = 0;
   // inputs
   DevBuf hx, hy, hz, hlayer, hit_off, seed_off, sp, sc, sh, seed_event, align_raw, align4, eta_edges;
   // binning
-  DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp;
+  DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp, bin_grouped, bin_gtab;
   // finding
   DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent;
   // duplicate removal scratch
@@ -252,7 +252,7 @@ int kf_destroy(kf_ctx* ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   DevBuf* bufs[] = {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
                     &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->hb,
-                    &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->out_hits,
+                    &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->bin_grouped, &ctx->bin_gtab, &ctx->out_hits,
                     &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent,
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
@@ -294,6 +294,8 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   CK(grow(ctx->bin_rank, sizeof(unsigned) * n));
   CK(grow(ctx->bin_cnt, sizeof(unsigned) * (n_bins + 1)));
   CK(grow(ctx->scan_tmp, sizeof(unsigned) * scan_tmp_elems(n_bins)));
+  CK(grow(ctx->bin_grouped, sizeof(float4) * n));
+  CK(grow(ctx->bin_gtab, sizeof(unsigned) * bin_group_elems(n_events, ctx->g.n_layers, ctx->g.n_eta, ctx->g.n_phi)));
   CK(grow(ctx->dd_hit_cnt, sizeof(unsigned) * ((size_t)n + n_events)));
   CK(put(ctx->hx.p, x, sizeof(float) * n, device_ptrs, st));
   CK(put(ctx->hy.p, y, sizeof(float) * n, device_ptrs, st));
@@ -305,6 +307,9 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   ctx->n_events = n_events;
   ctx->n_hits = n;
   ctx->n_bins_total = n_bins;
+  ctx->max_event_hits = 0;
+  for (int e = 0; e < n_events; ++e)
+    ctx->max_event_hits = std::max(ctx->max_event_hits, ev_offsets[e + 1] - ev_offsets[e]);
   ctx->found = ctx->deduped = ctx->fitted = false;
   if (!device_ptrs) CK(cudaStreamSynchronize(st));  // host staging vector stays valid until here
   else CK(cudaStreamSynchronize(st));
@@ -458,6 +463,8 @@ static BinParams bin_params(kf_ctx* ctx) {
   B.key = ptr<unsigned>(ctx->bin_key);
   B.rank = ptr<unsigned>(ctx->bin_rank);
   B.hb = ptr<float4>(ctx->hb);
+  B.grouped = ptr<float4>(ctx->bin_grouped);
+  B.gtab = ptr<unsigned>(ctx->bin_gtab);
   B.eta_edges = ptr<float>(ctx->eta_edges);
   return B;
 }
@@ -481,7 +488,7 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
   if (!ctx->per_event) {
     BinParams B = bin_params(ctx);
     stage_mark(ctx, 0, st);
-    CK(launch_bin(B, 0, ctx->n_bins_total, 0u, ptr<unsigned>(ctx->scan_tmp),
+    CK(launch_bin(B, 0, ctx->n_bins_total, 0u, ctx->max_event_hits, ptr<unsigned>(ctx->scan_tmp),
                   ctx->scan_tmp.bytes / sizeof(unsigned), st));
     stage_mark(ctx, 1, st);
     FindParams P = find_params(ctx);
@@ -495,7 +502,8 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
       BinParams B = bin_params(ctx);
       B.h_begin = ctx->hit_off_h[e];
       B.h_end = ctx->hit_off_h[e + 1];
-      CK(launch_bin(B, (size_t)e * cells, cells, (unsigned)ctx->hit_off_h[e], ptr<unsigned>(ctx->scan_tmp),
+      CK(launch_bin(B, (size_t)e * cells, cells, (unsigned)ctx->hit_off_h[e],
+                    ctx->hit_off_h[e + 1] - ctx->hit_off_h[e], ptr<unsigned>(ctx->scan_tmp),
                     ctx->scan_tmp.bytes / sizeof(unsigned), st));
       FindParams P = find_params(ctx);
       P.s_begin = ctx->seed_off_h[e];

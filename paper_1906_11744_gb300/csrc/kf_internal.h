@@ -59,6 +59,9 @@ struct BinParams {
   unsigned* key;          // [n_hits]
   unsigned* rank;         // [n_hits]
   float4* hb;             // [n_hits]
+  float4* grouped;        // [n_hits] hits grouped by (event, layer) (layer-grouped form)
+  unsigned* gtab;         // bin_group_elems(): bucket counts, bases (+ total), cursors of the
+                          // (event, layer, chunk of eta rows) buckets
 };
 
 struct DedupParams {
@@ -162,9 +165,10 @@ bool find_lanes_supported(int lanes);
 // outside stream capture) and reports resident blocks per SM.
 cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* blocks_per_sm);
 // kf_bin.cu
-cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsigned first_pos,
+cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsigned first_pos, int max_event_hits,
                        unsigned* scan_tmp, size_t scan_tmp_elems, cudaStream_t st);
 size_t scan_tmp_elems(size_t n);
+size_t bin_group_elems(int n_events, int n_layers, int n_eta, int n_phi);
 // kf_dedup.cu
 cudaError_t launch_dedup(const DedupParams& P, int n_events, cudaStream_t st);
 // kf_fit.cu
