@@ -39,7 +39,7 @@ struct kf_ctx {
   // finding
   DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent;
   // duplicate removal scratch
-  DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state;
+  DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state, dd_scan_tmp;
   // fit
   DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count, careful_flag, ckpt;
   bool want_ckpt = false;
@@ -255,7 +255,7 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->bin_grouped, &ctx->bin_gtab, &ctx->out_hits,
                     &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent,
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
-                    &ctx->dd_nconf, &ctx->dd_state, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
+                    &ctx->dd_nconf, &ctx->dd_state, &ctx->dd_scan_tmp, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt};
@@ -296,7 +296,8 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   CK(grow(ctx->scan_tmp, sizeof(unsigned) * scan_tmp_elems(n_bins)));
   CK(grow(ctx->bin_grouped, sizeof(float4) * n));
   CK(grow(ctx->bin_gtab, sizeof(unsigned) * bin_group_elems(n_events, ctx->g.n_layers, ctx->g.n_eta, ctx->g.n_phi)));
-  CK(grow(ctx->dd_hit_cnt, sizeof(unsigned) * ((size_t)n + n_events)));
+  CK(grow(ctx->dd_hit_cnt, sizeof(unsigned) * ((size_t)n + n_events + 1)));
+  CK(grow(ctx->dd_scan_tmp, sizeof(unsigned) * scan_tmp_elems((size_t)n + n_events)));
   CK(put(ctx->hx.p, x, sizeof(float) * n, device_ptrs, st));
   CK(put(ctx->hy.p, y, sizeof(float) * n, device_ptrs, st));
   CK(put(ctx->hz.p, z, sizeof(float) * n, device_ptrs, st));
@@ -528,6 +529,7 @@ int kf_remove_duplicates(kf_ctx* ctx, void* stream) {
   D.out_chi2 = ptr<float>(ctx->out_chi2);
   D.hit_off = ptr<int>(ctx->hit_off);
   D.seed_off = ptr<int>(ctx->seed_off);
+  D.seed_event = ptr<int>(ctx->seed_event);
   D.L = ctx->g.n_layers;
   D.ns = ctx->n_seeds;
   D.frac = ctx->cfg.dup_shared_frac;
@@ -541,7 +543,8 @@ int kf_remove_duplicates(kf_ctx* ctx, void* stream) {
   D.status = ptr<int>(ctx->status);
   if (!ctx->per_event) {
     stage_mark(ctx, 4, st);
-    CK(launch_dedup(D, ctx->n_events, st));
+    CK(launch_dedup_batched(D, ctx->n_events, ctx->n_hits, ptr<unsigned>(ctx->dd_scan_tmp),
+                            ctx->dd_scan_tmp.bytes / sizeof(unsigned), st));
     stage_mark(ctx, 5, st);
   } else {
     for (int e = 0; e < ctx->n_events; ++e) {

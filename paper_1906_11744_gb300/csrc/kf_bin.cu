@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_cells(const BinParams P, int e
 size_t scan_tmp_elems(size_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 // Exclusive scan of cnt[0..n) in place plus `add`; cnt[n] = total + add.
-static cudaError_t scan_inplace(unsigned* cnt, size_t n, unsigned add, unsigned* tmp, size_t tmp_elems,
-                                cudaStream_t st) {
+cudaError_t scan_exclusive_inplace(unsigned* cnt, size_t n, unsigned add, unsigned* tmp, size_t tmp_elems,
+                                   cudaStream_t st) {
   const int n_tiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
   if ((size_t)n_tiles + 1 > tmp_elems) return cudaErrorInvalidValue;
   k_scan_reduce<<<n_tiles, SCAN_THREADS, 0, st>>>(cnt, n, tmp);
@@ -386,7 +386,7 @@ cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsi
   const int threads = 256;
   const int blocks = (n_hits + threads - 1) / threads;
   if (n_hits > 0) k_bin_count<<<blocks, threads, 0, st>>>(P);
-  err = scan_inplace(P.cnt + bin_begin, n_bins, first_pos, scan_tmp, scan_tmp_elems_, st);
+  err = scan_exclusive_inplace(P.cnt + bin_begin, n_bins, first_pos, scan_tmp, scan_tmp_elems_, st);
   if (err != cudaSuccess) return err;
   if (n_hits > 0) k_bin_scatter<<<blocks, threads, 0, st>>>(P);
   return cudaGetLastError();

@@ -70,6 +70,7 @@ struct DedupParams {
   const float* out_chi2;
   const int* hit_off;
   const int* seed_off;   // [n_events + 1]
+  const int* seed_event; // [ns] (batched launch)
   int L;
   int ns;
   float frac;
@@ -168,9 +169,17 @@ cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* 
 cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsigned first_pos, int max_event_hits,
                        unsigned* scan_tmp, size_t scan_tmp_elems, cudaStream_t st);
 size_t scan_tmp_elems(size_t n);
+// Exclusive scan of cnt[0..n) in place plus add; cnt[n] = total + add.
+// tmp: scan_tmp_elems(n) entries.
+cudaError_t scan_exclusive_inplace(unsigned* cnt, size_t n, unsigned add, unsigned* tmp, size_t tmp_elems,
+                                   cudaStream_t st);
 size_t bin_group_elems(int n_events, int n_layers, int n_eta, int n_phi);
 // kf_dedup.cu
 cudaError_t launch_dedup(const DedupParams& P, int n_events, cudaStream_t st);
+// Whole batch: hit_cnt holds n_hits + n_events + 1 entries; scan_tmp
+// scan_tmp_elems(n_hits + n_events) entries.
+cudaError_t launch_dedup_batched(const DedupParams& P, int n_events, int n_hits, unsigned* scan_tmp,
+                                 size_t scan_tmp_elems, cudaStream_t st);
 // kf_fit.cu
 cudaError_t launch_fit(const FitParams& P, cudaStream_t st);
 
