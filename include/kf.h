@@ -188,8 +188,9 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
  * window-searched on one layer), [1] hit-children updated, [2] hits whose
  * chi2 was evaluated, [3] seeds, [4] hole-children (scattering only),
  * [5] propagations run in double (crossings with cos(angle to the radial
- * direction) < 0.5), [6] predictions without a positive definite measurement
- * covariance (no hit searched; expected 0), [7] reserved (0). */
+ * direction) < 0.2), [6] predictions without a positive definite measurement
+ * covariance (no hit searched; expected 0), [7] seeds redone by the careful
+ * pass (their candidates met such a crossing). */
 int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream);
 
 /* Stage timing: with enable = 1, CUDA events are recorded around the

@@ -245,7 +245,7 @@ def kf_get_counters(ctx, stream=None):
     c = np.zeros(8, np.int64)
     _check(ctx, load().kf_get_counters(ctx, c.ctypes.data_as(_P), _stream(stream)), "kf_get_counters")
     return dict(steps=int(c[0]), updates=int(c[1]), chi2_evals=int(c[2]), seeds=int(c[3]),
-                holes=int(c[4]), careful=int(c[5]), not_pd=int(c[6]))
+                holes=int(c[4]), careful=int(c[5]), not_pd=int(c[6]), redone=int(c[7]))
 
 
 def kf_set_stage_timing(ctx, enable=True):

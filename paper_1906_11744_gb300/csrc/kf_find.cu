@@ -58,14 +58,18 @@ constexpr float WIN_Z_ABS = 1e-4f;    // cm
 // layer its lanes go idle) and lists it; a careful pass after it (the same
 // kernel with CAREFUL) redoes the listed seeds with those propagations in
 // double, so that the double code and its registers stay out of the main
-// pass.  About 1.4% of the seeds of a PU-200 batch (low-pT loopers).  On such
+// pass.  The threshold for the finding is 0.2: on the PU-200 batch every
+// threshold from 0.1 to 0.5 gives the oracle's hit lists for the most tangent
+// loopers, and no prediction without a positive definite S, while the double
+// work (FP64 runs at a small fraction of the FP32 rate) grows tenfold from 0.2
+// to 0.5.  The number of seeds redone is counted (counter 7).  On such
 // a layer the careful pass keeps the prediction in double (shared memory):
 // the measurement frame (S, S^-1) is formed from it in double and only then
 // rounded for the window search, and the children of that prediction are
 // updated (and scattered) in double from it, as the re-fit's careful pass
 // does, because the prediction carries a large nearly rank-one term that
 // FP32 rounding of the covariance would turn indefinite.
-constexpr float FIND_CAREFUL_COS = 0.5f;
+constexpr float FIND_CAREFUL_COS = 0.2f;
 constexpr int CAREFUL_THREADS = 128;
 
 // Double-precision propagation of the state st[0..26] (p, then C) in place;
@@ -170,6 +174,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   // row), added to the global counters once when the warp ends.
   __shared__ unsigned long long s_cnt[8][8];
   if (lane < 8) s_cnt[warp][lane] = 0ull;
+  unsigned c_redo = 0;  // seeds given up (kept across tasks: not a per-task count)
   __syncwarp();
 
 
@@ -332,23 +337,40 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
                 for (int part = 0; part < 4; ++part) {
                   const unsigned i0 = o0, i1 = o1;
                   o0 = o2; o1 = o3; o2 = o4; o3 = o5; o4 = o6; o5 = o7;
-#pragma unroll 1
-                  for (unsigned i = i0; i < i1; ++i) {
-                    const float4 h = P.hb[i];
+                  // chi2 of one hit; the compatible ones enter the sorted list
+                  auto consider = [&](const float4& h) {
                     float mx, my, mz;
                     corrected_hit(al, h.x, h.y, h.z, mx, my, mz);
                     float r0, r1;
                     c_chi2++;
-                    if (!residual<float>(p, f, mx, my, mz, r0, r1)) continue;
+                    if (!residual<float>(p, f, mx, my, mz, r0, r1)) return;
                     const float c2 = chi2_of<float>(f, r0, r1);
-                    if (!(c2 < g.chi2_cut)) continue;
+                    if (!(c2 < g.chi2_cut)) return;
                     const unsigned long long key = make_key(nf1, chi2 + c2, gl, 0, __float_as_int(h.w));
                     int pos;
                     if (cnt < N) pos = cnt++;
                     else if (key < lst[N - 1]) pos = N - 1;
-                    else continue;
+                    else return;
                     while (pos > 0 && lst[pos - 1] > key) { lst[pos] = lst[pos - 1]; --pos; }
                     lst[pos] = key;
+                  };
+                  if constexpr (CAREFUL) {
+                    // near-tangent windows can hold thousands of hits: loads in
+                    // batches of 8, so that their latencies overlap
+                    constexpr int B = 8;
+#pragma unroll 1
+                    for (unsigned i = i0; i < i1; i += B) {
+                      float4 hh[B];
+#pragma unroll
+                      for (int k = 0; k < B; ++k)
+                        if (i + k < i1) hh[k] = P.hb[i + k];
+#pragma unroll
+                      for (int k = 0; k < B; ++k)
+                        if (i + k < i1) consider(hh[k]);
+                    }
+                  } else {
+#pragma unroll 1
+                    for (unsigned i = i0; i < i1; ++i) consider(P.hb[i]);
                   }
                 }
               }
@@ -507,7 +529,10 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     }
 
     if (given_up) {
-      if (has_seed && gl == 0) P.tangent_list[atomicAdd(P.queue + 2, 1u)] = seed;
+      if (has_seed && gl == 0) {
+        P.tangent_list[atomicAdd(P.queue + 2, 1u)] = seed;
+        ++c_redo;
+      }
       c_steps = c_updates = c_chi2 = c_seeds = c_holes = c_npd = 0;
     }
     // Counters of the task: summed over the warp into its shared row.
@@ -563,6 +588,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   }
   __syncwarp();
   if (lane < 7 && P.counters && s_cnt[warp][lane]) atomicAdd(&P.counters[lane], s_cnt[warp][lane]);
+  if (c_redo && P.counters) atomicAdd(&P.counters[7], (unsigned long long)c_redo);
 }
 
 template <int G, int CAP>
