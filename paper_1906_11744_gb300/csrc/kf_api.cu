@@ -30,7 +30,7 @@ struct kf_ctx {
   int num_sms = 0;
   int blocks_per_sm = 1;
   int n_events = 0, n_hits = 0, n_seeds = 0, n_seed_events = -1, max_event_hits = 0;
-  std::vector<int> hit_off_h, seed_off_h, seed_event_h;
+  std::vector<int> hit_off_h, seed_off_h;
   size_t n_bins_total = 0;
   // inputs
   DevBuf hx, hy, hz, hlayer, hit_off, seed_off, sp, sc, sh, seed_event, align_raw, align4, eta_edges;
@@ -106,6 +106,18 @@ cudaError_t put(void* dst, const void* src, size_t n, int device_ptrs, cudaStrea
 cudaError_t get(void* dst, const void* src, size_t n, int device_ptrs, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return cudaMemcpyAsync(dst, src, n, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+// Event of every seed from the seed offsets (binary search).
+__global__ void k_seed_event(const int* seed_off, int n_events, int n, int* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int lo = 0, hi = n_events - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seed_off[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  out[s] = lo;
 }
 
 __global__ void k_align(const float* off, const DevGeom g, Align4* out) {
@@ -279,10 +291,6 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   const size_t nb = (size_t)ctx->g.n_eta * ctx->g.n_phi;
   const size_t n_bins = (size_t)n_events * ctx->g.n_layers * nb;
   if (n_bins >= 0xFFFFFFFFull) return fail(ctx, KF_ERR_CAPACITY, "kf_load_hits: too many hit-grid cells");
-  if (!device_ptrs)
-    for (int i = 0; i < n; ++i)
-      if (layer[i] < 0 || layer[i] >= ctx->g.n_layers)
-        return fail(ctx, KF_ERR_ARG, "kf_load_hits: layer index out of range");
   cudaStream_t st = S(stream);
   CK(grow(ctx->hx, sizeof(float) * n));
   CK(grow(ctx->hy, sizeof(float) * n));
@@ -305,15 +313,33 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   ctx->hit_off_h.assign(ev_offsets, ev_offsets + n_events + 1);
   CK(cudaMemcpyAsync(ctx->hit_off.p, ctx->hit_off_h.data(), sizeof(int) * (n_events + 1),
                      cudaMemcpyHostToDevice, st));
+  ctx->found = ctx->deduped = ctx->fitted = false;
+  // Host arrays: layer indices checked while the copies run (the caller's
+  // buffers are in use until the synchronization below).
+  bool bad = false;
+  if (!device_ptrs) {
+    int lo = 0, hi = 0;
+    if (n > 0) {
+      lo = hi = layer[0];
+      for (int i = 1; i < n; ++i) {
+        lo = std::min(lo, layer[i]);
+        hi = std::max(hi, layer[i]);
+      }
+    }
+    bad = lo < 0 || hi >= ctx->g.n_layers;
+  }
+  CK(cudaStreamSynchronize(st));
+  if (bad) {
+    ctx->n_events = 0;
+    ctx->n_hits = -1;
+    return fail(ctx, KF_ERR_ARG, "kf_load_hits: layer index out of range");
+  }
   ctx->n_events = n_events;
   ctx->n_hits = n;
   ctx->n_bins_total = n_bins;
   ctx->max_event_hits = 0;
   for (int e = 0; e < n_events; ++e)
     ctx->max_event_hits = std::max(ctx->max_event_hits, ev_offsets[e + 1] - ev_offsets[e]);
-  ctx->found = ctx->deduped = ctx->fitted = false;
-  if (!device_ptrs) CK(cudaStreamSynchronize(st));  // host staging vector stays valid until here
-  else CK(cudaStreamSynchronize(st));
   return KF_OK;
 }
 
@@ -324,22 +350,9 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
     return fail(ctx, KF_ERR_ARG, "kf_load_seeds: null argument");
   if (n_events != ctx->n_events) return fail(ctx, KF_ERR_STATE, "kf_load_seeds: load hits of the same events first");
   if (ev_offsets[0] != 0) return fail(ctx, KF_ERR_ARG, "kf_load_seeds: ev_offsets[0] must be 0");
-  std::vector<int> sev;
-  for (int e = 0; e < n_events; ++e) {
+  for (int e = 0; e < n_events; ++e)
     if (ev_offsets[e + 1] < ev_offsets[e]) return fail(ctx, KF_ERR_ARG, "kf_load_seeds: decreasing ev_offsets");
-    for (int s = ev_offsets[e]; s < ev_offsets[e + 1]; ++s) sev.push_back(e);
-  }
   const int n = ev_offsets[n_events];
-  if (!device_ptrs) {
-    for (int s = 0; s < n; ++s) {
-      const int e = sev[s];
-      const int nh = ctx->hit_off_h[e + 1] - ctx->hit_off_h[e];
-      for (int k = 0; k < 3; ++k) {
-        const int h = seed_hits[(size_t)k * n + s];
-        if (h < 0 || h >= nh) return fail(ctx, KF_ERR_ARG, "kf_load_seeds: seed hit index out of range");
-      }
-    }
-  }
   cudaStream_t st = S(stream);
   const int L = ctx->g.n_layers;
   CK(grow(ctx->sp, sizeof(float) * 6 * (size_t)n));
@@ -369,15 +382,38 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(put(ctx->sc.p, cov, sizeof(float) * 21 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sh.p, seed_hits, sizeof(int) * 3 * (size_t)n, device_ptrs, st));
   ctx->seed_off_h.assign(ev_offsets, ev_offsets + n_events + 1);
-  ctx->seed_event_h = sev;
   CK(cudaMemcpyAsync(ctx->seed_off.p, ctx->seed_off_h.data(), sizeof(int) * (n_events + 1),
                      cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->seed_event.p, sev.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+  if (n > 0) {
+    k_seed_event<<<(n + 255) / 256, 256, 0, st>>>(ptr<int>(ctx->seed_off), n_events, n, ptr<int>(ctx->seed_event));
+    CK(cudaGetLastError());
+  }
   CK(cudaMemsetAsync(ctx->keep.p, 1, (size_t)n, st));
+  ctx->found = ctx->deduped = ctx->fitted = false;
+  // Host arrays: seed hit indices checked per event while the copies run.
+  bool bad = false;
+  if (!device_ptrs) {
+    for (int e = 0; e < n_events && !bad; ++e) {
+      const int nh = ctx->hit_off_h[e + 1] - ctx->hit_off_h[e];
+      for (int k = 0; k < 3 && !bad; ++k) {
+        const int* sh = seed_hits + (size_t)k * n;
+        int lo = 0, hi = -1;
+        if (ev_offsets[e + 1] > ev_offsets[e]) lo = hi = sh[ev_offsets[e]];
+        for (int s = ev_offsets[e] + 1; s < ev_offsets[e + 1]; ++s) {
+          lo = std::min(lo, sh[s]);
+          hi = std::max(hi, sh[s]);
+        }
+        bad = lo < 0 || hi >= nh;
+      }
+    }
+  }
   CK(cudaStreamSynchronize(st));
+  if (bad) {
+    ctx->n_seed_events = -1;
+    return fail(ctx, KF_ERR_ARG, "kf_load_seeds: seed hit index out of range");
+  }
   ctx->n_seeds = n;
   ctx->n_seed_events = n_events;
-  ctx->found = ctx->deduped = ctx->fitted = false;
   return KF_OK;
 }
 
@@ -599,7 +635,8 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
     if (!device_ptrs) {
       for (size_t s = 0; s < n; ++s) {
         if (n_hits[s] < 1 || n_hits[s] > max_len) return fail(ctx, KF_ERR_ARG, "kf_fit_tracks: bad hit count");
-        const int e = ctx->seed_event_h[s];
+        const int e = (int)(std::upper_bound(ctx->seed_off_h.begin(), ctx->seed_off_h.end(), (int)s) -
+                            ctx->seed_off_h.begin()) - 1;
         const int nh = ctx->hit_off_h[e + 1] - ctx->hit_off_h[e];
         for (int k = 0; k < n_hits[s]; ++k) {
           const int h = hit_lists[s * max_len + k];

@@ -226,8 +226,15 @@ def test_capacity_and_argument_errors():
     bad[0] = 99
     with pytest.raises(KFError):
         t.load_hits(b.hit_off, b.x, b.y, b.z, bad)
+    with pytest.raises(KFError):  # the rejected load leaves no usable hits
+        t.find_tracks()
     t.load_hits(b.hit_off, b.x, b.y, b.z, b.layer)
     sh = b.seed_hits.copy()
     sh[0, 0] = b.x.size + 5
     with pytest.raises(KFError):
         t.load_seeds(b.seed_off, b.params, b.cov, sh)
+    with pytest.raises(KFError):
+        t.find_tracks()
+    t.load_seeds(b.seed_off, b.params, b.cov, b.seed_hits)
+    t.find_tracks()
+    assert t.counters()["seeds"] == b.n_seeds
