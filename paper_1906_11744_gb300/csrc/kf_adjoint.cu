@@ -477,12 +477,14 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
   using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
   if (!CAREFUL) {
+    // Tracks the fit left to its careful pass are the careful adjoint's, whose
+    // pass runs at the same time as this one.
+    if (P.careful_flag[t]) return;
     if ((P.keep && !P.keep[t]) || P.fit_status[t] != KF_FIT_OK) {
       if (P.g_seed)  // not fitted: no contribution
         for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
       return;
     }
-    if (P.careful_flag[t]) return;  // left to the careful pass
   } else if (P.fit_status[t] != KF_FIT_OK) {
     if (P.g_seed)
       for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;

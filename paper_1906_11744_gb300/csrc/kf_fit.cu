@@ -47,6 +47,7 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
 
 template <bool CAREFUL>
 __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
+  if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;  // set below if the track is left to the careful pass
   if (!CAREFUL && P.keep && !P.keep[t]) {  // removed as a duplicate: zero outputs
 #pragma unroll
     for (int k = 0; k < 6; ++k) P.fit_p[(size_t)k * P.ns + t] = 0.f;
@@ -57,7 +58,6 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
     return;
   }
   const DevGeom& g = P.g;
-  if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;
   float p[6], C[21];
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + t];
@@ -131,18 +131,30 @@ __global__ void __launch_bounds__(128) k_fit_careful(const FitParams P) {
 
 }  // namespace
 
-cudaError_t launch_fit(const FitParams& P, cudaStream_t st) {
+cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
   const int threads = 128;
   const int blocks = (P.ns + threads - 1) / threads;
   cudaError_t e = cudaMemsetAsync(P.careful_count, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   k_fit<<<blocks, threads, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit_careful(const FitParams& P, cudaStream_t st) {
+  if (P.ns <= 0) return cudaSuccess;
   // flagged tracks are a few percent of all: a grid sized for a twentieth of
   // them, striding over however many there are
+  const int threads = 128;
   const int careful_blocks = (P.ns / 20 + threads - 1) / threads + 1;
   k_fit_careful<<<careful_blocks, threads, 0, st>>>(P);
   return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const FitParams& P, cudaStream_t st) {
+  cudaError_t e = launch_fit_main(P, st);
+  if (e == cudaSuccess) e = launch_fit_careful(P, st);
+  return e;
 }
 
 }  // namespace kfg

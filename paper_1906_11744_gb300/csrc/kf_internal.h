@@ -180,7 +180,10 @@ cudaError_t launch_dedup(const DedupParams& P, int n_events, cudaStream_t st);
 // scan_tmp_elems(n_hits + n_events) entries.
 cudaError_t launch_dedup_batched(const DedupParams& P, int n_events, int n_hits, unsigned* scan_tmp,
                                  size_t scan_tmp_elems, cudaStream_t st);
-// kf_fit.cu
+// kf_fit.cu: the FP32 pass (flags and lists near-tangent tracks) and the
+// careful pass over the list; launch_fit runs both.
+cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st);
+cudaError_t launch_fit_careful(const FitParams& P, cudaStream_t st);
 cudaError_t launch_fit(const FitParams& P, cudaStream_t st);
 
 }  // namespace kfg
