@@ -26,8 +26,10 @@
 // the sum over its hits of (-(x g_y - y g_x)/R_L, -g_z), g the gradient with
 // respect to the raw position (x, y, z) of the hit; one pass over the hits
 // forms it from the hit gradients after the sweep.
-// Tracks the fit flagged for a near-tangent crossing go to a second pass that
-// keeps their adjoints in double and runs the near-tangent steps in double.
+// Tracks with a crossing closer to tangent than cos(alpha) = 0.2 (the fit
+// marks them) go to a second pass that keeps their adjoints in double and runs
+// those steps in double; the rest, including tracks whose fit ran steps
+// between 0.2 and 0.5 in double, are reversed in FP32 from the checkpoints.
 #include <type_traits>
 
 #include "kf_common.cuh"
@@ -37,7 +39,7 @@ namespace kfg {
 
 namespace {
 
-constexpr float ADJ_CAREFUL_COS = 0.5f;
+constexpr float ADJ_CAREFUL_COS = ADJOINT_CAREFUL_COS;
 // Threads per block of the adjoint kernels; also the row stride (in floats)
 // of the segment buffer in shared memory.
 constexpr int ADJ_THREADS = 128;
@@ -477,14 +479,16 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
   using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
   if (!CAREFUL) {
-    // Tracks the fit left to its careful pass are the careful adjoint's, whose
-    // pass runs at the same time as this one.
-    if (P.careful_flag[t]) return;
+    // Tracks with a crossing below ADJ_CAREFUL_COS are the careful adjoint's,
+    // whose pass runs at the same time as this one.
+    if (P.careful_flag[t] == 2) return;
     if ((P.keep && !P.keep[t]) || P.fit_status[t] != KF_FIT_OK) {
       if (P.g_seed)  // not fitted: no contribution
         for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
       return;
     }
+  } else if (P.careful_flag[t] != 2) {
+    return;  // no crossing below ADJ_CAREFUL_COS: the FP32 pass's
   } else if (P.fit_status[t] != KF_FIT_OK) {
     if (P.g_seed)
       for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;

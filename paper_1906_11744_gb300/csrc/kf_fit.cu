@@ -67,6 +67,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
   const int n = P.n_list[t];
   const int* lst = P.lists + (size_t)t * P.max_len;
   float chi2 = 0.f;
+  float min_cos = 1.f;
   int status = KF_FIT_OK;
 #pragma unroll 1
   for (int k = 0; k < n && status == KF_FIT_OK; ++k) {
@@ -104,6 +105,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
         float zc, cosa;
         if (!crossing(p, g.radius[L], g.kb, zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
         careful = cosa < CAREFUL_COS;
+        min_cos = fminf(min_cos, cosa);
       }
       status = careful ? fit_step<double>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
                        : fit_step<float>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2);
@@ -115,6 +117,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
   for (int k = 0; k < 21; ++k) P.fit_C[(size_t)k * P.ns + t] = C[k];
   P.fit_chi2[t] = chi2;
   P.fit_status[t] = status;
+  if (CAREFUL && P.careful_flag) P.careful_flag[t] = min_cos < ADJOINT_CAREFUL_COS ? 2 : 1;
 }
 
 __global__ void __launch_bounds__(128) k_fit(const FitParams P) {

@@ -84,6 +84,10 @@ struct DedupParams {
   int* status;
 };
 
+// The adjoint redoes in double only the steps closer to tangent than this
+// (its tolerance is looser than the fit's; the fit's threshold is 0.5).
+constexpr float ADJOINT_CAREFUL_COS = 0.2f;
+
 constexpr int DEDUP_PARTNER_CAP = 32;
 constexpr int DEDUP_CONF_CAP = 16;
 
@@ -109,7 +113,8 @@ struct FitParams {
   int* fit_status;        // [ns]
   int* careful_list;      // [ns] tracks refitted with double-precision steps
   unsigned* careful_count;  // zeroed before the launch
-  unsigned char* careful_flag;  // [ns] 1 for the tracks of careful_list
+  unsigned char* careful_flag;  // [ns] 0, or for the tracks of careful_list 1, or 2 when one
+                                // of their crossings has cos(alpha) < ADJOINT_CAREFUL_COS
   float* ckpt;            // [MAX_CKPT][27][ns] states before every ckpt_stride-th hit, or null
   int ckpt_stride;
 };
