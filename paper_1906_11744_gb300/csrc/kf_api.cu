@@ -33,7 +33,7 @@ struct kf_ctx {
   std::vector<int> hit_off_h, seed_off_h;
   size_t n_bins_total = 0;
   // inputs
-  DevBuf hx, hy, hz, hlayer, hit_off, seed_off, sp, sc, sh, seed_event, align_raw, align4, eta_edges;
+  DevBuf hx, hy, hz, hlayer, hit_off, seed_off, sp, sc, sh, seed_event, align_raw, align4, eta_edges, eta_lut;
   // binning
   DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp, bin_grouped, bin_gtab;
   // finding
@@ -205,6 +205,8 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   g.vr = det->sigma_rphi * det->sigma_rphi;
   g.vz = det->sigma_z * det->sigma_z;
   g.chi2_cut = cfg->chi2_cut;
+  g.phi_scale = (float)cfg->n_phi_bins / TWO_PI_F;
+  g.eta_lut_scale = (float)ETA_LUT / (2.f * det->z_max);
   for (int l = 0; l < det->n_layers; ++l) {
     g.radius[l] = det->radius[l];
     g.x0[l] = det->x0[l];
@@ -227,6 +229,19 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
     e = grow(ctx->eta_edges, sizeof(float) * edges.size());
     if (e == cudaSuccess)
       e = cudaMemcpy(ctx->eta_edges.p, edges.data(), sizeof(float) * edges.size(), cudaMemcpyHostToDevice);
+    // first guess of the bin per uniform z cell: the bin of the cell's lower end
+    std::vector<unsigned char> lut((size_t)KF_MAX_LAYERS * ETA_LUT, 0);
+    for (int l = 0; l < det->n_layers; ++l) {
+      const float* ed = edges.data() + (size_t)l * (MAX_ETA_BINS + 1);
+      int b = 0;
+      for (int c = 0; c < ETA_LUT; ++c) {
+        const float z = -det->z_max + (float)c / g.eta_lut_scale;
+        while (b < cfg->n_eta_bins - 1 && z >= ed[b + 1]) ++b;
+        lut[(size_t)l * ETA_LUT + c] = (unsigned char)b;
+      }
+    }
+    if (e == cudaSuccess) e = grow(ctx->eta_lut, lut.size());
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->eta_lut.p, lut.data(), lut.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = grow(ctx->queue, 64);
   if (e == cudaSuccess) {
@@ -263,7 +278,7 @@ int kf_destroy(kf_ctx* ctx) {
   if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   DevBuf* bufs[] = {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
-                    &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->hb,
+                    &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->eta_lut, &ctx->hb,
                     &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->bin_grouped, &ctx->bin_gtab, &ctx->out_hits,
                     &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent,
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
@@ -465,6 +480,7 @@ static FindParams find_params(kf_ctx* ctx) {
   P.hb = ptr<float4>(ctx->hb);
   P.bin_off = ptr<unsigned>(ctx->bin_cnt);
   P.eta_edges = ptr<float>(ctx->eta_edges);
+  P.eta_lut = ptr<unsigned char>(ctx->eta_lut);
   P.sp = ptr<float>(ctx->sp);
   P.sc = ptr<float>(ctx->sc);
   P.sh = ptr<int>(ctx->sh);
@@ -503,6 +519,7 @@ static BinParams bin_params(kf_ctx* ctx) {
   B.grouped = ptr<float4>(ctx->bin_grouped);
   B.gtab = ptr<unsigned>(ctx->bin_gtab);
   B.eta_edges = ptr<float>(ctx->eta_edges);
+  B.eta_lut = ptr<unsigned char>(ctx->eta_lut);
   return B;
 }
 

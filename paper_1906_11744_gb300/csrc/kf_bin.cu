@@ -38,8 +38,9 @@ __device__ __forceinline__ int event_of(const int* hit_off, int n_events, int i)
 // Cell of a hit within its layer's grid.
 __device__ __forceinline__ int cell_of(const BinParams& P, int l, float x, float y, float z) {
   const DevGeom& g = P.g;
-  const int pb = wrap_bin(phi_bin_raw(atan2f(y, x), g.n_phi), g.n_phi);
-  const int eb = eta_bin(z, g.radius[l], g.eta_max[l], g.n_eta, P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1));
+  const int pb = wrap_bin(phi_bin_raw(atan2f(y, x), g.phi_scale), g.n_phi);
+  const int eb = eta_bin(z, g.n_eta, g.z_max, g.eta_lut_scale, P.eta_lut + (size_t)l * ETA_LUT,
+                         P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1));
   return eb * g.n_phi + pb;
 }
 
@@ -171,7 +172,8 @@ __host__ __device__ inline Chunks chunks_of(int n_eta, int n_phi) {
 
 __device__ __forceinline__ int eta_bin_of(const BinParams& P, int l, float z) {
   const DevGeom& g = P.g;
-  return eta_bin(z, g.radius[l], g.eta_max[l], g.n_eta, P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1));
+  return eta_bin(z, g.n_eta, g.z_max, g.eta_lut_scale, P.eta_lut + (size_t)l * ETA_LUT,
+                 P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1));
 }
 
 // Bucket of hit i of event ev within the event (layer, chunk).
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(CELL_THREADS) k_cells(const BinParams P, int e
                   (size_t)row0 * n_phi;
   const int tid = threadIdx.x;
   auto cell = [&](const float4& h) {
-    return (eta_bin_of(P, l, h.z) - row0) * n_phi + wrap_bin(phi_bin_raw(atan2f(h.y, h.x), n_phi), n_phi);
+    return (eta_bin_of(P, l, h.z) - row0) * n_phi + wrap_bin(phi_bin_raw(atan2f(h.y, h.x), P.g.phi_scale), n_phi);
   };
   if (n > 65535) {
     for (int c = tid; c < C; c += CELL_THREADS) off[c] = 0u;

@@ -22,6 +22,7 @@ constexpr double MPION = 0.13957;
 constexpr float PI_F = 3.14159265358979323846f;
 constexpr float TWO_PI_F = 6.28318530717958647692f;
 constexpr int MAX_ETA_BINS = 256;
+constexpr int ETA_LUT = 4096;  // uniform z cells per layer of the eta-bin first guess
 
 // Geometry and settings, passed by value as a kernel parameter.
 struct DevGeom {
@@ -35,6 +36,8 @@ struct DevGeom {
   float vr;  // sigma_rphi^2
   float vz;  // sigma_z^2
   float chi2_cut;
+  float phi_scale;      // n_phi / 2 pi
+  float eta_lut_scale;  // ETA_LUT / (2 z_max)
   float radius[KF_MAX_LAYERS];
   float x0[KF_MAX_LAYERS];
   float eta_max[KF_MAX_LAYERS];  // asinh(z_max / R): half-range of the eta grid
@@ -157,23 +160,35 @@ __device__ __forceinline__ bool path_length(T x, T y, T h, T cf, T sf, T R, T& s
   } else {
     n0 = sq - A; d0 = den; n1 = E; d1 = A - sq;
   }
+  // s_k = psi_k / h with psi_k = 2 atan(tau_k), tau_k = n_k / d_k (psi = pi for
+  // d_k = 0), plus a full turn when not positive; the smaller s is taken.
+  // psi is increasing in tau, so the root is chosen on tau and one atan is
+  // evaluated: for h > 0 positive tau (smallest first) before negative (most
+  // negative first); for h < 0 negative tau (closest to 0 first) before
+  // positive (largest first, d = 0 first of all); tau = 0 (s = a full turn)
+  // and n = d = 0 (no root) last.
   const T turn = T(2.0 * 3.14159265358979323846) / kabs(h);
   const T ih = T(1) / h;
-  T best = T(INFINITY);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const T nn = k ? n1 : n0, dd = k ? d1 : d0;
-    T psi;
+  const bool pos_h = h > T(0);
+  // rank: 0 preferred class, 1 other sign, 2 tau = 0, 3 no root
+  auto rank_of = [&](T nn, T dd, T& tau) {
     if (dd == T(0)) {
-      if (nn == T(0)) continue;
-      psi = T(3.14159265358979323846);
-    } else {
-      psi = T(2) * katan(nn / dd);
+      tau = T(INFINITY);
+      return nn == T(0) ? 3 : (pos_h ? 0 : 1);
     }
-    T sk = psi * ih;
-    if (sk <= T(0)) sk += turn;
-    best = kmin(best, sk);
-  }
+    tau = nn / dd;
+    if (tau == T(0)) return 2;
+    return (tau > T(0)) == pos_h ? 0 : 1;
+  };
+  T t0, t1;
+  const int k0 = rank_of(n0, d0, t0), k1 = rank_of(n1, d1, t1);
+  if (k0 == 3 && k1 == 3) return false;
+  // same rank: ascending tau for h > 0, descending for h < 0
+  const bool first = k0 != k1 ? k0 < k1 : (pos_h ? t0 <= t1 : t0 >= t1);
+  const T dd = first ? d0 : d1, tc = first ? t0 : t1;
+  const T psi = dd == T(0) ? T(3.14159265358979323846) : T(2) * katan(tc);
+  T best = psi * ih;
+  if (best <= T(0)) best += turn;
   if (!(best < T(INFINITY))) return false;
   s = best;
   return true;
@@ -428,20 +443,22 @@ __device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
 // [-asinh(z_max/R), asinh(z_max/R)], realised as a step function of z through
 // a per-layer table of bin edges in z (edge[k] = R sinh(eta_k)), so that the
 // map is monotone in z and identical for hits and search windows.
-__device__ __forceinline__ int phi_bin_raw(float phi, int n_phi) {
-  return (int)floorf((phi + PI_F) * ((float)n_phi / TWO_PI_F));
+__device__ __forceinline__ int phi_bin_raw(float phi, float phi_scale) {
+  return (int)floorf((phi + PI_F) * phi_scale);
 }
 __device__ __forceinline__ int wrap_bin(int b, int n) {
+  if (b >= 0 && b < n) return b;
+  if (b < 0 && b >= -n) return b + n;
+  if (b >= n && b < 2 * n) return b - n;
   b %= n;
   return b < 0 ? b + n : b;
 }
-__device__ __forceinline__ int eta_bin(float z, float R, float eta_max, int n_eta, const float* edges) {
-  // First guess from a fast asinh(z/R) = sign * log(|u| + sqrt(u^2 + 1)); the
-  // edge comparisons below make the result exact whatever the guess.
-  const float u = fabsf(z / R);
-  const float eta = copysignf(__logf(u + sqrtf(fmaf(u, u, 1.f))), z);
-  int b = (int)floorf((eta + eta_max) * ((float)n_eta / (2.f * eta_max)));
-  b = min(max(b, 0), n_eta - 1);
+__device__ __forceinline__ int eta_bin(float z, int n_eta, float z_max, float lut_scale, const unsigned char* lut,
+                                       const float* edges) {
+  // First guess: the bin of the lower end of z's cell in a uniform z grid;
+  // the edge comparisons below make the result exact whatever the guess.
+  const int c = min(max((int)floorf((z + z_max) * lut_scale), 0), ETA_LUT - 1);
+  int b = lut[c];
   while (b > 0 && z < __ldg(edges + b)) --b;
   while (b < n_eta - 1 && z >= __ldg(edges + b + 1)) ++b;
   return b;

@@ -308,15 +308,16 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
               dphi = fminf(dphi, 0.5f * PI_F) * (1.f + WIN_REL) + WIN_PHI_ABS;
               const float phic = atan2f(p[1], p[0]) + al.dphi;
               const int nphi = g.n_phi, neta = g.n_eta;
-              const int u0 = phi_bin_raw(phic - dphi, nphi);
-              const int u1 = phi_bin_raw(phic + dphi, nphi);
+              const int u0 = phi_bin_raw(phic - dphi, g.phi_scale);
+              const int u1 = phi_bin_raw(phic + dphi, g.phi_scale);
               int span = u1 - u0 + 1, b0;
               if (span >= nphi) { span = nphi; b0 = 0; } else { b0 = wrap_bin(u0, nphi); }
               const float zc = p[2] + al.az;
               const float wz = w2 * (1.f + WIN_REL) + WIN_Z_ABS;
               const float* edges = P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1);
-              const int e0 = eta_bin(zc - wz, R, g.eta_max[l], neta, edges);
-              const int e1 = spd ? eta_bin(zc + wz, R, g.eta_max[l], neta, edges) : e0 - 1;
+              const unsigned char* lut = P.eta_lut + (size_t)l * ETA_LUT;
+              const int e0 = eta_bin(zc - wz, neta, g.z_max, g.eta_lut_scale, lut, edges);
+              const int e1 = spd ? eta_bin(zc + wz, neta, g.z_max, g.eta_lut_scale, lut, edges) : e0 - 1;
               const unsigned* off = P.bin_off + ((size_t)ev * L + l) * ((size_t)neta * nphi);
               const int nf1 = nfound + 1;
               const int b1 = min(b0 + span, nphi);

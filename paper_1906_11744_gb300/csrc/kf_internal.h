@@ -26,6 +26,7 @@ struct FindParams {
   const float4* hb;          // binned hits (x, y, z, event-local index as int bits)
   const unsigned* bin_off;   // [n_events * n_layers * n_bins + 1] global offsets into hb
   const float* eta_edges;    // [KF_MAX_LAYERS][MAX_ETA_BINS + 1] z edges of the eta bins
+  const unsigned char* eta_lut;  // [KF_MAX_LAYERS][ETA_LUT] first guess of the eta bin
   const float* sp;           // seed params [6][ns]
   const float* sc;           // seed cov [21][ns]
   const int* sh;             // seed hits [3][ns]
@@ -55,6 +56,7 @@ struct BinParams {
   int n_events;
   int h_begin, h_end;     // hit range of this launch
   const float* eta_edges; // [KF_MAX_LAYERS][MAX_ETA_BINS + 1]
+  const unsigned char* eta_lut;  // [KF_MAX_LAYERS][ETA_LUT]
   unsigned* cnt;          // [n_bins_total + 1] counts, then offsets
   unsigned* key;          // [n_hits]
   unsigned* rank;         // [n_hits]
