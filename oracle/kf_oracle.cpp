@@ -41,9 +41,10 @@ constexpr double PI = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- dual numbers
 // Forward-mode derivatives: value v plus derivatives d[0..g_nd) with respect to
-// g_nd independent inputs.  Branches compare values only.
+// g_nd independent inputs.  Branches compare values only.  g_nd is per host
+// thread, so that calls on different threads do not interfere.
 constexpr int DMAX = 112;
-int g_nd = 0;
+thread_local int g_nd = 0;
 
 struct Dual {
   double v;

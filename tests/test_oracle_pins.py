@@ -395,3 +395,25 @@ def test_golden_closed_forms():
             assert int(ok) == int(expected), line
         n += 1
     assert n == 4
+
+
+def test_oracle_threads_give_sequential_results():
+    """The oracle's calls run on several host threads at once (the timed CPU
+    baseline does so); the dual-number width is per thread, so concurrent
+    gradients equal sequential ones."""
+    from concurrent.futures import ThreadPoolExecutor
+    b = make_batch("c1", tracks=200)
+    x, y, z, lay = b.event_hits(0)
+    prm, cov, sh = b.event_seeds(0)
+    r = oracle.find_event(b, 0)
+    ks = [np.arange(i, prm.shape[1], 4) for i in range(4)]
+
+    def run(k):
+        return oracle.fit_grad(b.det, prm[:, k], cov[:, k], r["hits"][k], r["n_found"][k], x, y, z, lay, b.align)
+
+    seq = [run(k) for k in ks]
+    with ThreadPoolExecutor(4) as ex:
+        par = list(ex.map(run, ks))
+    for s_, p_ in zip(seq, par):
+        for a, c in zip(s_, p_):
+            assert np.array_equal(np.asarray(a), np.asarray(c))
