@@ -37,7 +37,7 @@ struct kf_ctx {
   // binning
   DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp, bin_grouped, bin_gtab;
   // finding
-  DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent;
+  DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent, seed_order;
   // duplicate removal scratch
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state, dd_scan_tmp;
   // fit
@@ -280,7 +280,7 @@ int kf_destroy(kf_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
                     &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->eta_lut, &ctx->hb,
                     &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->bin_grouped, &ctx->bin_gtab, &ctx->out_hits,
-                    &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent,
+                    &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent, &ctx->seed_order,
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->dd_scan_tmp, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
@@ -378,6 +378,7 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->out_hits, sizeof(int) * (size_t)n * L));
   CK(grow(ctx->out_n, sizeof(int) * (size_t)n));
   CK(grow(ctx->tangent, sizeof(int) * (size_t)n));
+  CK(grow(ctx->seed_order, sizeof(int) * (size_t)n));
   CK(grow(ctx->out_chi2, sizeof(float) * (size_t)n));
   CK(grow(ctx->out_p, sizeof(float) * 6 * (size_t)n));
   CK(grow(ctx->out_C, sizeof(float) * 21 * (size_t)n));
@@ -402,6 +403,8 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   if (n > 0) {
     k_seed_event<<<(n + 255) / 256, 256, 0, st>>>(ptr<int>(ctx->seed_off), n_events, n, ptr<int>(ctx->seed_event));
     CK(cudaGetLastError());
+    CK(launch_seed_order(ptr<float>(ctx->sp) + 5 * (size_t)n, ptr<int>(ctx->seed_off), n_events,
+                         ptr<int>(ctx->seed_order), st));
   }
   CK(cudaMemsetAsync(ctx->keep.p, 1, (size_t)n, st));
   ctx->found = ctx->deduped = ctx->fitted = false;
@@ -496,6 +499,7 @@ static FindParams find_params(kf_ctx* ctx) {
   P.out_C = ptr<float>(ctx->out_C);
   P.queue = ptr<unsigned>(ctx->queue);
   P.tangent_list = ptr<int>(ctx->tangent);
+  P.order = ptr<int>(ctx->seed_order);
   P.counters = ptr<unsigned long long>(ctx->counters);
   P.persistent = ctx->persistent;
   return P;

@@ -195,8 +195,9 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       has_seed = lane_used && j < n_seed_range;
       seed = has_seed ? P.tangent_list[j] : 0;
     } else {
-      seed = P.s_begin + task * W + grp;
-      has_seed = lane_used && (seed < P.s_end);
+      const int j = P.s_begin + task * W + grp;
+      has_seed = lane_used && (j < P.s_end);
+      seed = has_seed && P.order ? P.order[j] : j;
     }
     // counters of this task (dropped for a seed given up)
     unsigned c_steps = 0, c_updates = 0, c_chi2 = 0, c_seeds = 0, c_holes = 0, c_careful = 0, c_npd = 0;
@@ -652,7 +653,58 @@ cudaError_t launch_careful_g(const FindParams& P, int grid, cudaStream_t st) {
     default: return cudaErrorInvalidValue;                         \
   }
 
+// Order in which the finding takes the seeds of each event: by polar angle
+// theta (counting sort into THETA_BINS bins, one block per event).  The seeds
+// of a warp then cross about as many layers before they leave the barrel,
+// which keeps its groups busy for the same number of iterations; the result
+// of a seed does not depend on the order.
+constexpr int THETA_BINS = 1024;
+__global__ void __launch_bounds__(1024) k_seed_order(const float* theta, const int* seed_off, int* order) {
+  __shared__ unsigned cnt[THETA_BINS];
+  __shared__ unsigned sh[33];
+  const int s0 = seed_off[blockIdx.x], s1 = seed_off[blockIdx.x + 1];
+  for (int k = threadIdx.x; k < THETA_BINS; k += blockDim.x) cnt[k] = 0u;
+  __syncthreads();
+  auto bin_of = [&](int s) {
+    return min(max((int)(theta[s] * (THETA_BINS / PI_F)), 0), THETA_BINS - 1);
+  };
+  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) atomicAdd(&cnt[bin_of(s)], 1u);
+  __syncthreads();
+  // exclusive scan of the THETA_BINS counts (one per thread)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned v = threadIdx.x < THETA_BINS ? cnt[threadIdx.x] : 0u;
+  unsigned incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    const unsigned w = lane < nw ? sh[lane] : 0u;
+    unsigned wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) sh[lane] = wi - w;
+  }
+  __syncthreads();
+  if (threadIdx.x < THETA_BINS) cnt[threadIdx.x] = sh[warp] + incl - v;
+  __syncthreads();
+  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) order[s0 + atomicAdd(&cnt[bin_of(s)], 1u)] = s;
+}
+
 }  // namespace
+
+cudaError_t launch_seed_order(const float* theta, const int* seed_off, int n_events, int* order, cudaStream_t st) {
+  if (n_events <= 0) return cudaSuccess;
+  k_seed_order<<<n_events, 1024, 0, st>>>(theta, seed_off, order);
+  return cudaGetLastError();
+}
 
 size_t find_smem_bytes(int threads, int n_layers) { return (size_t)(threads / 32) * smem_per_warp(n_layers); }
 

@@ -34,6 +34,7 @@ struct FindParams {
   const Align4* align;       // [n_layers]
   int ns;                    // seed stride
   int s_begin, s_end;        // seed range of this launch
+  const int* order;          // [ns] order of the seeds within each event (or null)
   int* out_hits;             // [ns][n_layers]
   int* out_n;                // [ns]
   float* out_chi2;           // [ns]
@@ -167,6 +168,8 @@ bool adjoint_stride_ok(int stride, int max_len);
 cudaError_t launch_find_main(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
                              cudaStream_t st);
 cudaError_t launch_find_careful(const FindParams& P, int lanes, int grid, cudaStream_t st);
+// Per event, the seeds sorted by theta (params row 5) into order[].
+cudaError_t launch_seed_order(const float* theta, const int* seed_off, int n_events, int* order, cudaStream_t st);
 size_t find_smem_bytes(int threads, int n_layers);
 bool find_lanes_supported(int lanes);
 // Sets the dynamic shared-memory limit of the kernel variant (must run
