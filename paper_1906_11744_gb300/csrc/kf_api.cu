@@ -37,7 +37,7 @@ struct kf_ctx {
   // binning
   DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp, bin_grouped, bin_gtab;
   // finding
-  DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent, seed_order;
+  DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent, seed_order, check;
   // duplicate removal scratch
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state, dd_scan_tmp;
   // fit
@@ -106,6 +106,24 @@ cudaError_t put(void* dst, const void* src, size_t n, int device_ptrs, cudaStrea
 cudaError_t get(void* dst, const void* src, size_t n, int device_ptrs, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return cudaMemcpyAsync(dst, src, n, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+// Input checks on the device (after the copies; works for host and device
+// arrays alike): any value outside [0, hi) sets *bad.
+__global__ void k_check_range(const int* v, int n, int hi, int* bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (v[i] < 0 || v[i] >= hi) *bad = 1;
+}
+// Seed hit indices (three per seed, [3][n]) against their event's hit count.
+__global__ void k_check_seed_hits(const int* sh, const int* seed_event, const int* hit_off, int n, int* bad) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int e = seed_event[s];
+    const int nh = hit_off[e + 1] - hit_off[e];
+    for (int k = 0; k < 3; ++k) {
+      const int h = sh[(size_t)k * n + s];
+      if (h < 0 || h >= nh) *bad = 1;
+    }
+  }
 }
 
 // Event of every seed from the seed offsets (binary search).
@@ -280,7 +298,7 @@ int kf_destroy(kf_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
                     &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->eta_lut, &ctx->hb,
                     &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->bin_grouped, &ctx->bin_gtab, &ctx->out_hits,
-                    &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent, &ctx->seed_order,
+                    &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent, &ctx->seed_order, &ctx->check,
                     &ctx->counters, &ctx->status, &ctx->dd_hit_cnt, &ctx->dd_owners, &ctx->dd_conf,
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->dd_scan_tmp, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
@@ -329,20 +347,17 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   CK(cudaMemcpyAsync(ctx->hit_off.p, ctx->hit_off_h.data(), sizeof(int) * (n_events + 1),
                      cudaMemcpyHostToDevice, st));
   ctx->found = ctx->deduped = ctx->fitted = false;
-  // Host arrays: layer indices checked while the copies run (the caller's
-  // buffers are in use until the synchronization below).
-  bool bad = false;
-  if (!device_ptrs) {
-    int lo = 0, hi = 0;
-    if (n > 0) {
-      lo = hi = layer[0];
-      for (int i = 1; i < n; ++i) {
-        lo = std::min(lo, layer[i]);
-        hi = std::max(hi, layer[i]);
-      }
-    }
-    bad = lo < 0 || hi >= ctx->g.n_layers;
+  // Layer indices checked on the device (the caller's buffers are in use until
+  // the synchronization below).
+  int bad = 0;
+  CK(grow(ctx->check, 64));
+  CK(cudaMemsetAsync(ctx->check.p, 0, sizeof(int), st));
+  if (n > 0) {
+    k_check_range<<<std::min((n + 255) / 256, 4 * ctx->num_sms), 256, 0, st>>>(ptr<int>(ctx->hlayer), n,
+                                                                               ctx->g.n_layers, ptr<int>(ctx->check));
+    CK(cudaGetLastError());
   }
+  CK(cudaMemcpyAsync(&bad, ctx->check.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (bad) {
     ctx->n_events = 0;
@@ -408,23 +423,16 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   }
   CK(cudaMemsetAsync(ctx->keep.p, 1, (size_t)n, st));
   ctx->found = ctx->deduped = ctx->fitted = false;
-  // Host arrays: seed hit indices checked per event while the copies run.
-  bool bad = false;
-  if (!device_ptrs) {
-    for (int e = 0; e < n_events && !bad; ++e) {
-      const int nh = ctx->hit_off_h[e + 1] - ctx->hit_off_h[e];
-      for (int k = 0; k < 3 && !bad; ++k) {
-        const int* sh = seed_hits + (size_t)k * n;
-        int lo = 0, hi = -1;
-        if (ev_offsets[e + 1] > ev_offsets[e]) lo = hi = sh[ev_offsets[e]];
-        for (int s = ev_offsets[e] + 1; s < ev_offsets[e + 1]; ++s) {
-          lo = std::min(lo, sh[s]);
-          hi = std::max(hi, sh[s]);
-        }
-        bad = lo < 0 || hi >= nh;
-      }
-    }
+  // Seed hit indices checked on the device against their event's hits.
+  int bad = 0;
+  CK(grow(ctx->check, 64));
+  CK(cudaMemsetAsync(ctx->check.p, 0, sizeof(int), st));
+  if (n > 0) {
+    k_check_seed_hits<<<std::min((n + 255) / 256, 4 * ctx->num_sms), 256, 0, st>>>(
+        ptr<int>(ctx->sh), ptr<int>(ctx->seed_event), ptr<int>(ctx->hit_off), n, ptr<int>(ctx->check));
+    CK(cudaGetLastError());
   }
+  CK(cudaMemcpyAsync(&bad, ctx->check.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (bad) {
     ctx->n_seed_events = -1;

@@ -238,3 +238,15 @@ def test_capacity_and_argument_errors():
     t.load_seeds(b.seed_off, b.params, b.cov, b.seed_hits)
     t.find_tracks()
     assert t.counters()["seeds"] == b.n_seeds
+    # the same checks on device arrays
+    import torch
+    dev = torch.device("cuda:0")
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    with pytest.raises(KFError):
+        t.load_hits(b.hit_off, tt(b.x), tt(b.y), tt(b.z), tt(bad))
+    t.load_hits(b.hit_off, tt(b.x), tt(b.y), tt(b.z), tt(b.layer))
+    with pytest.raises(KFError):
+        t.load_seeds(b.seed_off, tt(b.params), tt(b.cov), tt(sh))
+    t.load_seeds(b.seed_off, tt(b.params), tt(b.cov), tt(b.seed_hits))
+    t.find_tracks()
+    assert t.counters()["seeds"] == b.n_seeds
