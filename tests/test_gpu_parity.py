@@ -250,3 +250,48 @@ def test_capacity_and_argument_errors():
     t.load_seeds(b.seed_off, tt(b.params), tt(b.cov), tt(b.seed_hits))
     t.find_tracks()
     assert t.counters()["seeds"] == b.n_seeds
+
+
+def test_straight_tracks_at_zero_field():
+    """B = 0: the straight-line propagation (no curvature) in finding and fit."""
+    b = make_batch("c0", bz=0.0)
+    trk, ref, mism, kinds, unexplained = _find_and_compare(b)
+    assert len(mism) <= max(1, 0.005 * b.n_seeds)
+    assert not unexplained, unexplained
+    t = tracker_for(b)
+    t.find_tracks()
+    t.remove_duplicates()
+    from paper_1906_11744_gb300 import KF_FIT_FOUND
+    t.fit_tracks(KF_FIT_FOUND)
+    fit = t.get_fit()
+    x, y, z, lay = b.event_hits(0)
+    ok = fit["status"] == 0
+    p, C, c2, st = oracle.fit(b.det, b.params[:, ok], b.cov[:, ok], trk["hits"][ok], trk["n_found"][ok],
+                              x, y, z, lay, align=b.align)
+    okp, ep = param_close(fit["params"][:, ok].T[st == 0], p[st == 0])
+    assert okp.all(), ep
+
+
+def test_thirty_two_layers():
+    """The largest detector the library takes (KF_MAX_LAYERS = 32 layers)."""
+    b = make_batch("c1", tracks=300, n_layers=32)
+    assert b.det.n_layers == 32
+    trk, ref, mism, kinds, unexplained = _find_and_compare(b)
+    assert len(mism) <= max(1, 0.005 * b.n_seeds)
+    assert not unexplained, unexplained
+
+
+def test_batch_without_seeds():
+    """Hits but no seeds at all: every stage runs on empty work."""
+    from paper_1906_11744_gb300 import KF_FIT_FOUND, Tracker, make_config, make_detector
+    b = make_batch("c1", tracks=50)
+    det = b.det
+    t = Tracker(make_detector(det.radius, det.x0, det.z_max, det.bz, det.sigma_rphi, det.sigma_z),
+                make_config(max_cands=6))
+    t.load_hits(b.hit_off, b.x, b.y, b.z, b.layer)
+    t.load_seeds([0, 0], np.zeros((6, 0), np.float32), np.zeros((21, 0), np.float32), np.zeros((3, 0), np.int32))
+    t.find_tracks()
+    t.remove_duplicates()
+    t.fit_tracks(KF_FIT_FOUND)
+    assert t.counters()["seeds"] == 0
+    assert t.get_tracks()["hits"].shape[0] == 0
