@@ -44,8 +44,8 @@ F_FIT_HIT = 608   # re-fit: propagation + transport + update + scattering per hi
 
 # DRAM traffic (read + write) of one k_find launch on the 100-event batch,
 # scaled by events from an ncu capture of the same kernel on 20 of its events
-# (193.7 MB).  Set to None whenever k_find changes until it is captured again.
-FIND_TRAFFIC_BYTES = None
+# (193.6 MB).  Set to None whenever k_find changes until it is captured again.
+FIND_TRAFFIC_BYTES = 193.58e6 * 5
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
