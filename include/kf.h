@@ -89,7 +89,7 @@ typedef struct {
   int persistent;         /* 1 = persistent work-queue launch, 0 = one warp per seed tile */
   int per_event;          /* 1 = bin, find and remove duplicates with one launch per event
                              (the plain form); 0 = one launch per step over the whole batch */
-  int ckpt_stride;        /* layers between forward checkpoints of the adjoint (>= 1) */
+  int ckpt_stride;        /* hits between forward checkpoints of the adjoint (0 = 2; 1..8) */
   int find_regcap;        /* 0 = finding kernel at the compiler's register count (blocks <= 256
                              threads); 1 = at most 102 registers, five blocks per SM (blocks
                              <= 128 threads).  The results are identical. */
@@ -148,7 +148,7 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
  * may be NULL) and seed parameters (g_seed float [6][n_seeds], may be NULL):
  * the adjoint of the fit, one thread per track.  Forward states are kept
  * every ckpt_stride hits and recomputed in between; ckpt_stride (1..8) must
- * satisfy hits per track <= 9 * ckpt_stride (KF_ERR_CAPACITY otherwise). */
+ * satisfy hits per track <= 32 * ckpt_stride (KF_ERR_CAPACITY otherwise). */
 int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs,
                    void* stream);
 

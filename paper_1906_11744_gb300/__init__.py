@@ -54,7 +54,7 @@ def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1)
 
 def make_config(max_cands=6, max_holes=3, chi2_cut=30.0, dup_shared_frac=0.5, n_eta_bins=64,
                 n_phi_bins=1024, lanes_per_seed=0, block_threads=0, persistent=1, per_event=0,
-                ckpt_stride=4, find_regcap=0) -> kf_config:
+                ckpt_stride=2, find_regcap=0) -> kf_config:
     return kf_config(max_cands, max_holes, chi2_cut, dup_shared_frac, n_eta_bins, n_phi_bins,
                      lanes_per_seed, block_threads, persistent, per_event, ckpt_stride, find_regcap)
 

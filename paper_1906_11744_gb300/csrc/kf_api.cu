@@ -646,12 +646,9 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   F.careful_list = ptr<int>(ctx->careful_list);
   F.careful_count = ptr<unsigned>(ctx->careful_count);
   F.careful_flag = ptr<unsigned char>(ctx->careful_flag);
-  F.ckpt_stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : 4;
+  F.ckpt_stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
   F.ckpt = nullptr;
-  if (ctx->want_ckpt) {  // checkpoints for the adjoint
-    CK(grow(ctx->ckpt, sizeof(float) * (size_t)MAX_CKPT * 27 * (size_t)ctx->n_seeds));
-    F.ckpt = ptr<float>(ctx->ckpt);
-  }
+  F.ckpt_slices = 0;
   if (source == KF_FIT_FOUND) {
     if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_fit_tracks: no found tracks");
     F.lists = ptr<int>(ctx->out_hits);
@@ -686,6 +683,11 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   } else {
     return fail(ctx, KF_ERR_ARG, "kf_fit_tracks: unknown source");
   }
+  if (ctx->want_ckpt) {  // checkpoints for the adjoint
+    F.ckpt_slices = ckpt_slices_for(F.max_len, F.ckpt_stride);
+    CK(grow(ctx->ckpt, sizeof(float) * (size_t)F.ckpt_slices * 27 * (size_t)ctx->n_seeds));
+    F.ckpt = ptr<float>(ctx->ckpt);
+  }
   stage_mark(ctx, 6, st);
   CK(launch_fit(F, st));
   stage_mark(ctx, 7, st);
@@ -699,15 +701,16 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   if (!ctx) return KF_ERR_ARG;
   if (!ctx->fitted) return fail(ctx, KF_ERR_STATE, "kf_fit_adjoint: run kf_fit_tracks first");
   if (!g_align) return fail(ctx, KF_ERR_ARG, "kf_fit_adjoint: g_align is required");
-  const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : 4;
+  const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
   if (!adjoint_stride_ok(stride, ctx->last_fit.max_len))
-    return fail(ctx, KF_ERR_CAPACITY, "kf_fit_adjoint: ckpt_stride must be 1..8 with hits per track <= 9 * stride");
+    return fail(ctx, KF_ERR_CAPACITY, "kf_fit_adjoint: ckpt_stride must be 1..8 with hits per track <= 32 * stride");
   cudaStream_t st = S(stream);
   if (!ctx->last_fit.ckpt) {  // the last fit kept no checkpoints: refit with them (same lists)
     ctx->want_ckpt = true;
-    CK(grow(ctx->ckpt, sizeof(float) * (size_t)MAX_CKPT * 27 * (size_t)ctx->n_seeds));
-    ctx->last_fit.ckpt = ptr<float>(ctx->ckpt);
     ctx->last_fit.ckpt_stride = stride;
+    ctx->last_fit.ckpt_slices = ckpt_slices_for(ctx->last_fit.max_len, stride);
+    CK(grow(ctx->ckpt, sizeof(float) * (size_t)ctx->last_fit.ckpt_slices * 27 * (size_t)ctx->n_seeds));
+    ctx->last_fit.ckpt = ptr<float>(ctx->ckpt);
     CK(launch_fit(ctx->last_fit, st));
   }
   const FitParams& F = ctx->last_fit;
@@ -855,7 +858,8 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
   if (with_adjoint) {  // every buffer the captured work uses exists before capture starts
     ctx->want_ckpt = true;
-    CK(grow(ctx->ckpt, sizeof(float) * (size_t)MAX_CKPT * 27 * (size_t)ctx->n_seeds));
+    const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
+    CK(grow(ctx->ckpt, sizeof(float) * (size_t)ckpt_slices_for(ctx->g.n_layers, stride) * 27 * (size_t)ctx->n_seeds));
     CK(grow(ctx->adj_align_acc, sizeof(double) * 2 * KF_MAX_LAYERS));
     CK(grow(ctx->adj_align, sizeof(float) * 2 * KF_MAX_LAYERS));
     CK(grow(ctx->adj_hits, sizeof(float) * 3 * (size_t)ctx->n_hits));

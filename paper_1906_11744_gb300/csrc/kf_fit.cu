@@ -71,7 +71,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
   int status = KF_FIT_OK;
 #pragma unroll 1
   for (int k = 0; k < n && status == KF_FIT_OK; ++k) {
-    if (P.ckpt && k % P.ckpt_stride == 0 && k / P.ckpt_stride < MAX_CKPT) {  // state before hit k
+    if (P.ckpt && k % P.ckpt_stride == 0 && k / P.ckpt_stride < P.ckpt_slices) {  // state before hit k
       float* c = P.ckpt + (size_t)(k / P.ckpt_stride) * 27 * P.ns + t;
 #pragma unroll
       for (int q = 0; q < 6; ++q) c[(size_t)q * P.ns] = p[q];

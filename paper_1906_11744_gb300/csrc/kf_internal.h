@@ -118,11 +118,18 @@ struct FitParams {
   unsigned* careful_count;  // zeroed before the launch
   unsigned char* careful_flag;  // [ns] 0, or for the tracks of careful_list 1, or 2 when one
                                 // of their crossings has cos(alpha) < ADJOINT_CAREFUL_COS
-  float* ckpt;            // [MAX_CKPT][27][ns] states before every ckpt_stride-th hit, or null
+  float* ckpt;            // [ckpt_slices][27][ns] states before every ckpt_stride-th hit, or null
   int ckpt_stride;
+  int ckpt_slices;        // checkpoints per track the buffer holds
 };
 
-constexpr int MAX_CKPT = 9;       // checkpoints per track
+constexpr int MAX_CKPT = KF_MAX_LAYERS;  // checkpoints per track at most
+// Checkpoints per track for tracks of up to max_len hits.
+inline int ckpt_slices_for(int max_len, int stride) {
+  const int n = (max_len + stride - 1) / stride;
+  return n < MAX_CKPT ? n : MAX_CKPT;
+}
+constexpr int DEFAULT_CKPT_STRIDE = 2;
 constexpr int MAX_CKPT_STRIDE = 8;
 
 struct AdjParams {
@@ -151,7 +158,7 @@ struct AdjParams {
   const int* careful_list;     // tracks the fit flagged as near-tangent ...
   const unsigned* careful_count;
   const unsigned char* careful_flag;  // ... and their per-track flag
-  const float* ckpt;           // the fit's checkpoints [MAX_CKPT][27][ns]
+  const float* ckpt;           // the fit's checkpoints [slices][27][ns]
 };
 
 // kf_adjoint.cu

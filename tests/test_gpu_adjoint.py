@@ -48,7 +48,7 @@ def _setup(n_tracks=300, stride=4, seed=1003):
     return b, t, lists, n
 
 
-@pytest.mark.parametrize("stride", [4, 2, 8])
+@pytest.mark.parametrize("stride", [4, 2, 8, 1])
 def test_adjoint_matches_oracle_dual_gradient(stride):
     b, t, lists, n = _setup(stride=stride)
     fit = t.get_fit()
