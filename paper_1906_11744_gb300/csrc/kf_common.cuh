@@ -86,11 +86,15 @@ __device__ __forceinline__ float katan(float x) { return atanf(x); }
 __device__ __forceinline__ double katan(double x) { return atan(x); }
 __device__ __forceinline__ float ksin(float x) { return sinf(x); }
 __device__ __forceinline__ double ksin(double x) { return sin(x); }
-__device__ __forceinline__ float klog(float x) { return logf(x); }
+__device__ __forceinline__ float klog(float x) { return __logf(x); }  // hardware approximation
 __device__ __forceinline__ double klog(double x) { return log(x); }
 __device__ __forceinline__ float kabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double kabs(double x) { return fabs(x); }
 __device__ __forceinline__ float kmin(float a, float b) { return fminf(a, b); }
+// Quotient and reciprocal: FP32 by the hardware reciprocal (about 2 ulp, far
+// below what the state's FP32 rounding already costs a track), double exact.
+__device__ __forceinline__ float kdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double kdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ double kmin(double a, double b) { return fmin(a, b); }
 
 // sinc(psi) = sin(psi)/psi, cosc(psi) = (1 - cos psi)/psi,
@@ -174,8 +178,8 @@ __device__ __forceinline__ bool path_length(T x, T y, T h, T cf, T sf, T R, T& s
   // negative first); for h < 0 negative tau (closest to 0 first) before
   // positive (largest first, d = 0 first of all); tau = 0 (s = a full turn)
   // and n = d = 0 (no root) last.
-  const T turn = T(2.0 * 3.14159265358979323846) / kabs(h);
-  const T ih = T(1) / h;
+  const T turn = kdiv(T(2.0 * 3.14159265358979323846), kabs(h));
+  const T ih = kdiv(T(1), h);
   const bool pos_h = h > T(0);
   // rank: 0 preferred class, 1 other sign, 2 tau = 0, 3 no root
   auto rank_of = [&](T nn, T dd, T& tau) {
@@ -183,7 +187,7 @@ __device__ __forceinline__ bool path_length(T x, T y, T h, T cf, T sf, T R, T& s
       tau = T(INFINITY);
       return nn == T(0) ? 3 : (pos_h ? 0 : 1);
     }
-    tau = nn / dd;
+    tau = kdiv(nn, dd);
     if (tau == T(0)) return 2;
     return (tau > T(0)) == pos_h ? 0 : 1;
   };
@@ -290,7 +294,7 @@ __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim
   if (!path_length<T>(x, y, h, cf, sf, R, s)) return 0;
   T sth, cth;
   ksincos(th, &sth, &cth);
-  const T cot = cth / sth;
+  const T cot = kdiv(cth, sth);
   const T zn = kfma(s, cot, p[2]);
   if (kabs(zn) > z_lim) return 2;
   const T psi = h * s;
@@ -312,14 +316,14 @@ __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim
   const T dgds = kfma(xn, cp, yn * sp);
   if (cos_out) *cos_out = kabs(dgds) / R;
   if (s_out) *s_out = s;
-  const T inv = T(-1) / dgds;
+  const T inv = kdiv(T(-1), dgds);
   const T ds0 = xn * inv, ds1 = yn * inv;
   const T ds3 = kfma(xn, Fx3, yn * Fy3) * inv;
   const T ds4 = kfma(xn, Fx4, yn * Fy4) * inv;
   J[0][0] = kfma(cp, ds0, T(1)); J[0][1] = cp * ds1; J[0][3] = kfma(cp, ds3, Fx3); J[0][4] = kfma(cp, ds4, Fx4);
   J[1][0] = sp * ds0; J[1][1] = kfma(sp, ds1, T(1)); J[1][3] = kfma(sp, ds3, Fy3); J[1][4] = kfma(sp, ds4, Fy4);
   J[2][0] = cot * ds0; J[2][1] = cot * ds1; J[2][3] = cot * ds3; J[2][4] = cot * ds4;
-  J[2][5] = -s / (sth * sth);
+  J[2][5] = -kdiv(s, sth * sth);
   J[4][0] = h * ds0; J[4][1] = h * ds1; J[4][3] = kfma(h, ds3, kb * s); J[4][4] = kfma(h, ds4, T(1));
   q[0] = xn;
   q[1] = yn;
@@ -362,7 +366,7 @@ __device__ __forceinline__ void make_frame(const T (&p)[6], const T (&C)[21], T 
   const T s00 = kfma(-f.su, f.a0[0], kfma(f.cu, f.a0[1], vr));
   const T s01 = f.a0[2];
   const T s11 = C[S6(2, 2)] + vz;
-  const T idet = T(1) / kfma(s00, s11, -s01 * s01);
+  const T idet = kdiv(T(1), kfma(s00, s11, -s01 * s01));
   f.s00 = s00;
   f.s11 = s11;
   f.si00 = s11 * idet;
@@ -419,12 +423,12 @@ __device__ __forceinline__ void ms_terms(const T (&p)[6], T x0, T& q44, T& q55) 
   ksincos(p[4], &sph, &cph);
   const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
   const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;  // cos(phi - phi_p)
-  const T pm = T(1) / (kabs(p[3]) * sth);
-  const T beta = pm / ksqrt(kfma(pm, pm, T(MPION * MPION)));
-  const T t = x0 / kabs(sth * cdiff);
-  const T th0 = T(0.0136) / (beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
+  const T pm = kdiv(T(1), kabs(p[3]) * sth);
+  const T beta = kdiv(pm, ksqrt(kfma(pm, pm, T(MPION * MPION))));
+  const T t = kdiv(x0, kabs(sth * cdiff));
+  const T th0 = kdiv(T(0.0136), beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
   q55 = th0 * th0;
-  q44 = q55 / (sth * sth);
+  q44 = kdiv(q55, sth * sth);
 }
 
 template <class T>
@@ -435,12 +439,12 @@ __device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
   ksincos(p[4], &sph, &cph);
   const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
   const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;  // cos(phi - phi_p)
-  const T pm = T(1) / (kabs(p[3]) * sth);
-  const T beta = pm / ksqrt(kfma(pm, pm, T(MPION * MPION)));
-  const T t = x0 / kabs(sth * cdiff);
-  const T th0 = T(0.0136) / (beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
+  const T pm = kdiv(T(1), kabs(p[3]) * sth);
+  const T beta = kdiv(pm, ksqrt(kfma(pm, pm, T(MPION * MPION))));
+  const T t = kdiv(x0, kabs(sth * cdiff));
+  const T th0 = kdiv(T(0.0136), beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
   const T v = th0 * th0;
-  C[S6(4, 4)] += v / (sth * sth);
+  C[S6(4, 4)] += kdiv(v, sth * sth);
   C[S6(5, 5)] += v;
 }
 
