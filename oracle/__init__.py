@@ -67,7 +67,11 @@ def lib():
                                          _P, _P, _P, _P, _P, _P]
             L.orc_replay.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
             L.orc_dedup.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_double,
-                                    ctypes.c_int, _P]
+                                    ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double]
+            L.orc_kinematics.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P]
+            L.orc_seed_clean.argtypes = [ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _P]
         return _lib
 
 
@@ -241,13 +245,37 @@ def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=
                               children=int(cnt[6])))
 
 
-def dedup(hits, n_hits, chi2, frac=0.5, brute=False):
-    """Greedy duplicate removal over one event's tracks; returns keep flags (uint8)."""
+def dedup(hits, n_hits, chi2, frac=0.5, brute=False, params=None, bz=0.0, deta=0.0, dphi=0.0, dpt=0.0):
+    """Greedy duplicate removal over one event's tracks; returns keep flags (uint8).
+    With params ([n][6] track states) a pair must also pass the pT, eta and phi
+    pre-cuts (deta, dphi, dpt; a cut <= 0 is off)."""
     hits = _c(hits, np.int32); n_hits = _c(n_hits, np.int32); chi2 = _c(chi2, np.float64)
     n = n_hits.size
     keep = np.zeros(n, np.uint8)
+    pp = None if params is None else _c(np.asarray(params, np.float64).reshape(n, 6), np.float64)
     lib().orc_dedup(n, _ptr(hits), _ptr(n_hits), _ptr(chi2), hits.shape[1] if n else 1,
-                    float(frac), int(brute), _ptr(keep))
+                    float(frac), int(brute), _ptr(keep), None if pp is None else _ptr(pp), float(bz),
+                    float(deta), float(dphi), float(dpt))
+    return keep
+
+
+def kinematics(bz, params):
+    """(eta, |q/pT|, phi0) of track states params [n][6]; phi0 is the direction
+    of motion at the point of the helix closest to the z axis."""
+    pp = _c(np.asarray(params, np.float64).reshape(-1, 6), np.float64)
+    out = np.zeros((pp.shape[0], 3))
+    lib().orc_kinematics(pp.shape[0], float(bz), _ptr(pp), _ptr(out))
+    return out
+
+
+def seed_clean(params, hits, bz, deta, dphi=0.0, dpt=0.0, min_shared=0):
+    """Seed cleaning of one event's seeds (params [n][6], hits [n][3]): keep
+    flags (uint8) of the greedy walk in seed order."""
+    pp = _c(np.asarray(params, np.float64).reshape(-1, 6), np.float64)
+    hh = _c(np.asarray(hits).reshape(-1, 3), np.int32)
+    keep = np.zeros(pp.shape[0], np.uint8)
+    lib().orc_seed_clean(pp.shape[0], _ptr(pp), _ptr(hh), float(bz), float(deta), float(dphi), float(dpt),
+                         int(min_shared), _ptr(keep))
     return keep
 
 

@@ -16,7 +16,8 @@
 //   * gain K = C H^T S^-1, p <- p + K r, C <- C - K H C;
 //   * thin-scatterer multiple scattering after each layer (Highland width);
 //   * combinatorial finding with per-seed top-N candidates (Sec. 2);
-//   * greedy duplicate removal on shared-hit fraction (Sec. 4.2);
+//   * greedy duplicate removal on shared-hit fraction with optional pT, eta
+//     and phi pre-cuts, and seed cleaning before building (both Sec. 4.2);
 //   * the full re-fit and the summed chi2, with forward-mode dual numbers for
 //     d(chi2)/d(alignment, hits, seed parameters).
 // Matrices are full 6x6 arrays and products are plain triple loops: no
@@ -621,6 +622,45 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
 }  // namespace
 
 // ====================================================================== C API
+// Kinematic quantities of a track state (Sec. 4.2 names pT, eta and phi as
+// the criteria of seed cleaning and duplicate removal):
+//   k[0] = eta = -ln tan(theta/2);
+//   k[1] = |q/pT|;
+//   k[2] = phi0, the transverse direction of motion at the point of the helix
+//          closest to the z axis.  The track circle has centre
+//          c = (x - sin(phi)/h, y + cos(phi)/h) and radius 1/|h|; its point
+//          closest to the axis is c - c/(|c| |h|), where the direction of
+//          motion is perpendicular to c: sign(h) (c_y, -c_x)/|c|.  A straight
+//          track (h = 0) keeps its direction.
+void kinematics_of(double bz, const double* p, double* k) {
+  const double h = -KCURV * bz * p[3];
+  k[0] = -std::log(std::tan(0.5 * p[5]));
+  k[1] = std::fabs(p[3]);
+  if (h == 0.0) {
+    k[2] = std::atan2(std::sin(p[4]), std::cos(p[4]));
+    return;
+  }
+  const double cx = p[0] - std::sin(p[4]) / h;
+  const double cy = p[1] + std::cos(p[4]) / h;
+  const double n = std::sqrt(cx * cx + cy * cy);
+  const double sg = h > 0.0 ? 1.0 : -1.0;
+  k[2] = std::atan2(-sg * cx / n, sg * cy / n);
+}
+
+// Kinematic closeness of two tracks: |d eta| < deta, |d phi0| < dphi (the
+// difference taken on the circle) and ||k_a| - |k_b|| <= dpt max(|k_a|, |k_b|)
+// (the relative pT difference); a cut <= 0 is not applied.
+bool kin_close(const double* a, const double* b, double deta, double dphi, double dpt) {
+  if (deta > 0.0 && !(std::fabs(a[0] - b[0]) < deta)) return false;
+  if (dphi > 0.0) {
+    double d = std::fabs(a[2] - b[2]);
+    if (d > PI) d = 2.0 * PI - d;
+    if (!(d < dphi)) return false;
+  }
+  if (dpt > 0.0 && !(std::fabs(a[1] - b[1]) <= dpt * std::max(a[1], b[1]))) return false;
+  return true;
+}
+
 extern "C" {
 
 struct orc_detector {
@@ -897,10 +937,19 @@ int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, con
 
 // Duplicate removal for one event's tracks: walk tracks by (more hits, lower
 // chi2, lower index); keep a track unless it shares more than frac*min(nA, nB)
-// hits with a track already kept.  hits [n][max_len] event-local indices.
-// brute != 0 compares against every kept track directly.
+// hits with a track already kept and, when params is given, is also
+// kinematically close to it (kin_close with deta, dphi, dpt; pT, eta and phi
+// of the track states params [n][6]).  A track without hits is never kept.
+// hits [n][max_len] event-local indices.  brute != 0 compares against every
+// kept track directly.
 int orc_dedup(int n_tracks, const int* hits, const int* n_hits, const double* chi2, int max_len,
-              double frac, int brute, unsigned char* keep) {
+              double frac, int brute, unsigned char* keep, const double* params, double bz, double deta,
+              double dphi, double dpt) {
+  std::vector<double> kin(params ? 3 * (size_t)n_tracks : 0);
+  for (int t = 0; params && t < n_tracks; ++t) kinematics_of(bz, params + 6 * (size_t)t, &kin[3 * (size_t)t]);
+  auto close = [&](int a, int b) {
+    return !params || kin_close(&kin[3 * (size_t)a], &kin[3 * (size_t)b], deta, dphi, dpt);
+  };
   std::vector<int> order(n_tracks);
   std::iota(order.begin(), order.end(), 0);
   std::sort(order.begin(), order.end(), [&](int a, int b) {
@@ -922,7 +971,7 @@ int orc_dedup(int n_tracks, const int* hits, const int* n_hits, const double* ch
         int nsh = 0;
         for (int a = 0; a < n_hits[t]; ++a)
           for (int b = 0; b < n_hits[k]; ++b) nsh += ht[a] == hk[b];
-        if (nsh > frac * std::min(n_hits[t], n_hits[k])) { dup = true; break; }
+        if (nsh > frac * std::min(n_hits[t], n_hits[k]) && close(t, k)) { dup = true; break; }
       }
     } else {
       std::vector<int> touched;
@@ -933,11 +982,11 @@ int orc_dedup(int n_tracks, const int* hits, const int* n_hits, const double* ch
         }
       }
       for (int k : touched) {
-        if (shared[k] > frac * std::min(n_hits[t], n_hits[k])) dup = true;
+        if (shared[k] > frac * std::min(n_hits[t], n_hits[k]) && close(t, k)) dup = true;
         shared[k] = 0;
       }
     }
-    if (!dup) {
+    if (!dup && n_hits[t] > 0) {
       keep[t] = 1;
       kept.push_back(t);
       if (!brute) {
@@ -947,6 +996,38 @@ int orc_dedup(int n_tracks, const int* hits, const int* n_hits, const double* ch
         }
       }
     }
+  }
+  return 0;
+}
+
+// Kinematic quantities of n states params [n][6] into out [n][3]
+// (eta, |q/pT|, phi0; see kinematics_of).
+void orc_kinematics(int n, double bz, const double* params, double* out) {
+  for (int i = 0; i < n; ++i) kinematics_of(bz, params + 6 * (size_t)i, out + 3 * (size_t)i);
+}
+
+// Seed cleaning before building (Sec. 4.2, first step), one event: visit the
+// seeds by index and drop a seed when a seed already kept is kinematically
+// close to it (kin_close with deta, dphi, dpt on the seed states params
+// [n][6]) and shares at least min_shared of its three hits (hits [n][3]).
+int orc_seed_clean(int n, const double* params, const int* hits, double bz, double deta, double dphi,
+                   double dpt, int min_shared, unsigned char* keep) {
+  std::vector<double> kin(3 * (size_t)n);
+  for (int i = 0; i < n; ++i) kinematics_of(bz, params + 6 * (size_t)i, &kin[3 * (size_t)i]);
+  std::vector<int> kept;
+  for (int j = 0; j < n; ++j) {
+    bool dup = false;
+    for (int i : kept) {
+      int shared = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) shared += hits[3 * (size_t)j + a] == hits[3 * (size_t)i + b];
+      if (shared >= min_shared && kin_close(&kin[3 * (size_t)j], &kin[3 * (size_t)i], deta, dphi, dpt)) {
+        dup = true;
+        break;
+      }
+    }
+    keep[j] = dup ? 0 : 1;
+    if (!dup) kept.push_back(j);
   }
   return 0;
 }

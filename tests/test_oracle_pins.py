@@ -417,3 +417,169 @@ def test_oracle_threads_give_sequential_results():
     for s_, p_ in zip(seq, par):
         for a, c in zip(s_, p_):
             assert np.array_equal(np.asarray(a), np.asarray(c))
+
+
+# ------------------------------------------------- kinematic duplicate criteria
+
+def _state(eta, phi, kappa, x=0.0, y=0.0, z=0.0):
+    return [x, y, z, kappa, phi, 2.0 * math.atan(math.exp(-eta))]
+
+
+def test_phi0_is_the_direction_at_closest_approach_brute_force():
+    """phi0 against a brute-force search for the point of the helix closest to
+    the z axis (dense sampling of one turn, then a bounded 1D minimisation),
+    the helix written out from its parametric form."""
+    from scipy.optimize import minimize_scalar
+    rng = np.random.default_rng(7)
+    for bz in (3.8, -2.0):
+        for _ in range(40):
+            x, y = rng.uniform(-60, 60, 2)
+            kap = rng.choice([-1, 1]) * rng.uniform(0.05, 2.0)
+            phi = rng.uniform(-math.pi, math.pi)
+            p = [x, y, rng.uniform(-50, 50), kap, phi, rng.uniform(0.3, 2.8)]
+            h = -C_LIGHT * bz * kap
+            turn = 2 * math.pi / abs(h)
+
+            def r2(s):
+                xs = x + (math.sin(phi + h * s) - math.sin(phi)) / h
+                ys = y - (math.cos(phi + h * s) - math.cos(phi)) / h
+                return xs * xs + ys * ys
+
+            grid = np.linspace(0.0, turn, 20001)
+            xs = x + (np.sin(phi + h * grid) - math.sin(phi)) / h
+            ys = y - (np.cos(phi + h * grid) - math.cos(phi)) / h
+            i = int(np.argmin(xs * xs + ys * ys))
+            d = turn / 20000
+            res = minimize_scalar(r2, bounds=(grid[i] - d, grid[i] + d), method="bounded",
+                                  options={"xatol": 1e-12 * turn})
+            want = math.atan2(math.sin(phi + h * res.x), math.cos(phi + h * res.x))
+            got = oracle.kinematics(bz, [p])[0, 2]
+            diff = abs(got - want)
+            assert min(diff, 2 * math.pi - diff) < 1e-6
+
+
+def test_phi0_straight_line_and_invariance_along_the_helix():
+    # zero field: the direction does not change along the line
+    p = [30.0, -4.0, 1.0, 0.7, 2.5, 1.1]
+    assert abs(oracle.kinematics(0.0, [p])[0, 2] - 2.5) < 1e-15
+    # a track from the origin: phi0 is its initial direction at every radius
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        phi = rng.uniform(-math.pi, math.pi)
+        eta = rng.uniform(-1.5, 1.5)
+        kap = rng.choice([-1, 1]) * rng.uniform(0.1, 2.0)
+        p0 = _state(eta, phi, kap)
+        for R in (4.0, 30.0, 80.0):
+            ok, q, _ = oracle.propagate(3.8, p0, R)
+            if not ok:
+                continue
+            k = oracle.kinematics(3.8, [q])[0]
+            d = abs(k[2] - phi)
+            assert min(d, 2 * math.pi - d) < 1e-12
+            assert abs(k[0] - eta) < 1e-12          # theta is constant along the helix
+            assert abs(k[1] - abs(kap)) < 1e-15
+    # eta = asinh(cot theta)
+    for th in (0.3, 1.0, math.pi / 2, 2.0, 2.9):
+        k = oracle.kinematics(3.8, [[0, 0, 0, 0.5, 0.0, th]])[0]
+        assert abs(k[0] - math.asinh(math.cos(th) / math.sin(th))) < 1e-14
+
+
+def test_seed_clean_small_cases():
+    hits = np.array([[1, 2, 3], [4, 5, 6], [7, 8, 9]], np.int32)
+    # A~B and B~C in eta, A and C not: greedy keeps A, drops B, keeps C
+    p = [_state(0.0, 0.1, 0.5), _state(0.03, 0.1, 0.5), _state(0.06, 0.1, 0.5)]
+    assert list(oracle.seed_clean(p, hits, 3.8, 0.05)) == [1, 0, 1]
+    # shared hits required: none shared -> nothing dropped; one shared -> dropped
+    assert list(oracle.seed_clean(p, hits, 3.8, 0.05, min_shared=1)) == [1, 1, 1]
+    h2 = hits.copy(); h2[1, 2] = 1
+    assert list(oracle.seed_clean(p, h2, 3.8, 0.05, min_shared=1)) == [1, 0, 1]
+    assert list(oracle.seed_clean(p, h2, 3.8, 0.05, min_shared=2)) == [1, 1, 1]
+    # phi difference taken on the circle
+    q = [_state(0.0, math.pi - 0.01, 0.5), _state(0.0, -math.pi + 0.01, 0.5)]
+    assert list(oracle.seed_clean(q, hits[:2], 3.8, 0.05, dphi=0.05)) == [1, 0]
+    assert list(oracle.seed_clean(q, hits[:2], 3.8, 0.05, dphi=0.015)) == [1, 1]
+    # relative pT: |0.5 - 0.55| / 0.55 = 0.0909
+    r = [_state(0.0, 0.0, 0.5), _state(0.0, 0.0, -0.55)]
+    assert list(oracle.seed_clean(r, hits[:2], 3.8, 0.05, dpt=0.1)) == [1, 0]
+    assert list(oracle.seed_clean(r, hits[:2], 3.8, 0.05, dpt=0.09)) == [1, 1]
+
+
+def _np_kin(bz, p):
+    """eta, |q/pT| and phi0 by other formulas: asinh(cot theta), and phi0 from
+    h times the circle centre, which needs no division by h."""
+    p = np.asarray(p, np.float64)
+    h = -C_LIGHT * bz * p[:, 3]
+    vx = h * p[:, 0] - np.sin(p[:, 4])
+    vy = h * p[:, 1] + np.cos(p[:, 4])
+    return np.stack([np.arcsinh(np.cos(p[:, 5]) / np.sin(p[:, 5])), np.abs(p[:, 3]),
+                     np.arctan2(-vx, vy)], axis=1)
+
+
+def _np_close(ka, kb, deta, dphi, dpt):
+    ok = np.ones(np.broadcast(ka[..., 0], kb[..., 0]).shape, bool)
+    if deta > 0:
+        ok &= np.abs(ka[..., 0] - kb[..., 0]) < deta
+    if dphi > 0:
+        d = np.abs(ka[..., 2] - kb[..., 2])
+        ok &= np.minimum(d, 2 * np.pi - d) < dphi
+    if dpt > 0:
+        ok &= np.abs(ka[..., 1] - kb[..., 1]) <= dpt * np.maximum(ka[..., 1], kb[..., 1])
+    return ok
+
+
+@pytest.mark.parametrize("cuts", [(0.05, 0.05, 0.0, 1), (0.02, 0.02, 0.5, 0)])
+def test_seed_clean_c1b_fixed_point(cuts):
+    """On the duplicate-seed workload: the kept set is the fixed point of the
+    greedy rule (a seed is kept iff no kept lower-index seed is its duplicate),
+    checked with an independently written pair predicate; the injected
+    duplicates (two shared hits) are removed."""
+    deta, dphi, dpt, ms = cuts
+    b = make_batch("c1b")
+    p = b.params.T.astype(np.float64)
+    sh = b.seed_hits.T
+    keep = oracle.seed_clean(p, sh, b.det.bz, deta, dphi, dpt, ms)
+    k = _np_kin(b.det.bz, p)
+    n = p.shape[0]
+    close = _np_close(k[:, None, :], k[None, :, :], deta, dphi, dpt)
+    shared = (sh[:, None, :, None] == sh[None, :, None, :]).sum(axis=(2, 3))
+    dup = close & (shared >= ms)
+    kept = keep.astype(bool)
+    for j in range(n):
+        assert kept[j] == (not np.any(kept[:j] & dup[:j, j])), j
+    n_orig = np.unique(b.seed_sim).size
+    if ms == 1:  # exactly the injected duplicates go
+        assert kept[:n_orig].all() and (~kept[n_orig:]).sum() >= 0.98 * (n - n_orig)
+
+
+def test_dedup_kinematic_precuts():
+    hits = np.full((2, 5), -1, np.int32)
+    hits[0] = [1, 2, 3, 4, 5]
+    hits[1] = [1, 2, 3, 4, 6]
+    n = np.array([5, 5], np.int32)
+    chi2 = np.array([1.0, 2.0])
+    p = [_state(0.0, 0.2, 0.5), _state(0.3, 0.2, 0.5)]
+    assert list(oracle.dedup(hits, n, chi2)) == [1, 0]
+    assert list(oracle.dedup(hits, n, chi2, params=p, bz=3.8, deta=0.1)) == [1, 1]
+    assert list(oracle.dedup(hits, n, chi2, params=p, bz=3.8, deta=0.5)) == [1, 0]
+    assert list(oracle.dedup(hits, n, chi2, brute=True, params=p, bz=3.8, deta=0.1)) == [1, 1]
+    # a track without hits is never kept
+    assert list(oracle.dedup(hits, np.array([5, 0], np.int32), chi2)) == [1, 0]
+
+
+def test_dedup_kinematic_index_equals_brute_force():
+    b = make_batch("c1b", tracks=600)
+    r = oracle.find_event(b, 0)
+    for cuts in [(0.01, 0.01, 0.2), (0.002, 0.0, 0.0), (0.0, 0.003, 0.05)]:
+        k1 = oracle.dedup(r["hits"], r["n_found"], r["chi2"], 0.5, params=r["p"], bz=b.det.bz,
+                          deta=cuts[0], dphi=cuts[1], dpt=cuts[2])
+        k2 = oracle.dedup(r["hits"], r["n_found"], r["chi2"], 0.5, brute=True, params=r["p"],
+                          bz=b.det.bz, deta=cuts[0], dphi=cuts[1], dpt=cuts[2])
+        assert np.array_equal(k1, k2)
+        # no kept pair is a duplicate under both criteria
+        kin = _np_kin(b.det.bz, np.asarray(r["p"]).reshape(-1, 6))
+        kept = np.nonzero(k1)[0]
+        sets = [set(r["hits"][i, :r["n_found"][i]]) for i in kept]
+        for a in range(len(kept)):
+            for c in range(a + 1, len(kept)):
+                over = len(sets[a] & sets[c]) > 0.5 * min(len(sets[a]), len(sets[c]))
+                assert not (over and _np_close(kin[kept[a]], kin[kept[c]], *cuts))
