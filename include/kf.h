@@ -8,7 +8,8 @@
  *   - load hits and seeds (Sec. 3: the input conversion step of the build);
  *   - find tracks: combinatorial Kalman-filter building with per-seed
  *     candidate ranking (Sec. 2; candidate scores, Sec. 4.3);
- *   - remove duplicates: the post-processing step on shared hits (Sec. 4.2);
+ *   - seed cleaning before finding and duplicate removal after it: the two
+ *     steps of duplicate handling on pT, eta, phi and shared hits (Sec. 4.2);
  *   - fit tracks: the Kalman re-fit of the built tracks (Sec. 5, "fitting");
  *   - the gradient of the summed fit chi2 with respect to layer alignment
  *     offsets, hit positions and seed parameters (adjoint of the fit).
@@ -52,6 +53,7 @@ extern "C" {
 #define KF_MAX_LAYERS 32       /* barrel layers */
 #define KF_MAX_CANDS 16        /* candidates kept per seed */
 #define KF_MAX_EVENT_HITS (1 << 21) /* hits per event (21-bit hit index in ranking keys) */
+#define KF_SEED_MAX_DETA 1.0f       /* largest eta window of seed cleaning */
 
 /* Fit sources for kf_fit_tracks. */
 #define KF_FIT_FOUND 0 /* hit lists produced by kf_find_tracks (kept tracks only after dedup) */
@@ -93,6 +95,23 @@ typedef struct {
   int find_regcap;        /* 0 = finding kernel at the compiler's register count (blocks <= 256
                              threads); 1 = at most 102 registers, five blocks per SM (blocks
                              <= 128 threads).  The results are identical. */
+  /* Kinematic criteria (Sec. 4.2 names pT, eta and phi).  For two states A, B:
+   * eta = -ln tan(theta/2); phi0 = the direction of motion at the point of the
+   * helix closest to the z axis (the same for every state along a helix);
+   * k = q/pT.  A and B are close when |eta_A - eta_B| < deta,
+   * |phi0_A - phi0_B| (on the circle) < dphi and
+   * ||k_A| - |k_B|| <= dpt * max(|k_A|, |k_B|); a cut of 0 is not applied. */
+  float dup_deta;         /* duplicate removal: a pair over the shared-hit fraction is a */
+  float dup_dphi;         /* duplicate only if its found states are also close (all 0: the */
+  float dup_dpt;          /* shared fraction alone); each >= 0 */
+  int seed_clean;         /* 1 = seed cleaning before finding: visit each event's seeds by index
+                             and drop a seed that is close to a kept one and shares at least
+                             seed_min_shared of its three hits with it.  A dropped seed gives an
+                             empty track (n_found 0, keep 0). */
+  float seed_deta;        /* seed cleaning cuts: 0 < seed_deta <= KF_SEED_MAX_DETA, */
+  float seed_dphi;        /* seed_dphi >= 0, */
+  float seed_dpt;         /* seed_dpt >= 0 */
+  int seed_min_shared;    /* 0..3 */
 } kf_config;
 
 /* Create a context for a detector and configuration.  Allocates nothing on
@@ -123,14 +142,19 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
  * z by -a_z.  Zero after kf_create. */
 int kf_set_alignment(kf_ctx* ctx, const float* offsets, int device_ptrs, void* stream);
 
-/* Bin hits and run the combinatorial Kalman-filter finding for every seed
- * (Sec. 2): seed fit over the three seed hits, then per layer propagation,
- * covariance transport, chi2 of every compatible hit, per-seed top-N
- * ranking, update and multiple scattering.  Asynchronous. */
+/* Bin hits, clean the seeds (with seed_clean) and run the combinatorial
+ * Kalman-filter finding for every (kept) seed (Sec. 2): seed fit over the
+ * three seed hits, then per layer propagation, covariance transport, chi2 of
+ * every compatible hit, per-seed top-N ranking, update and multiple
+ * scattering.  Asynchronous.  Errors of seed cleaning (more than 16
+ * lower-index duplicates of one seed: KF_ERR_CAPACITY) surface at the next
+ * synchronizing call. */
 int kf_find_tracks(kf_ctx* ctx, void* stream);
 
-/* Duplicate removal over the found tracks of each event (Sec. 4.2).
- * Asynchronous.  Requires kf_find_tracks. */
+/* Duplicate removal over the found tracks of each event (Sec. 4.2): shared
+ * hits over dup_shared_frac and the kinematic pre-cuts dup_deta, dup_dphi,
+ * dup_dpt; an empty track (a cleaned seed) is never kept.  Asynchronous.
+ * Requires kf_find_tracks. */
 int kf_remove_duplicates(kf_ctx* ctx, void* stream);
 
 /* Kalman re-fit from each seed's prior over a hit list.
@@ -186,7 +210,8 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
 /* Counters of the last kf_find_tracks, synchronous (8 values):
  * [0] candidate-layer steps (a live candidate propagated, transported and
  * window-searched on one layer), [1] hit-children updated, [2] hits whose
- * chi2 was evaluated, [3] seeds, [4] hole-children (scattering only),
+ * chi2 was evaluated, [3] seeds built (those kept by seed cleaning), [4]
+ * hole-children (scattering only),
  * [5] propagations run in double (crossings with cos(angle to the radial
  * direction) < 0.2), [6] predictions without a positive definite measurement
  * covariance (no hit searched; expected 0), [7] seeds redone by the careful
@@ -194,12 +219,13 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
 int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream);
 
 /* Stage timing: with enable = 1, CUDA events are recorded around the
- * binning, finding, duplicate removal, fit and adjoint launches (also inside
- * a captured graph).  kf_get_stage_ms (synchronous) returns the durations of
- * the last completed run: ms5 = {bin, find, dedup, fit, adjoint}; a stage
- * that did not run reads -1. */
+ * binning, finding, duplicate removal, fit, adjoint and seed-cleaning
+ * launches of the batched form (also inside a captured graph).
+ * kf_get_stage_ms (synchronous) returns the durations of the last completed
+ * run: ms6 = {bin, find, dedup, fit, adjoint, seed clean} (find excludes seed
+ * cleaning); a stage that did not run reads -1. */
 int kf_set_stage_timing(kf_ctx* ctx, int enable);
-int kf_get_stage_ms(kf_ctx* ctx, float* ms5, void* stream);
+int kf_get_stage_ms(kf_ctx* ctx, float* ms6, void* stream);
 
 /* Number of kernel nodes in the captured graph (launches per replay). */
 int kf_graph_kernel_count(kf_ctx* ctx, int* n_kernels);

@@ -28,6 +28,7 @@ KF_FIT_OK = 0
 KF_FIT_SKIPPED = 1
 KF_NOALLOC_MAX_TRACKS = 16384
 KF_NOALLOC_MAX_HITS = 262144
+KF_SEED_MAX_DETA = 1.0
 
 
 class kf_detector(ctypes.Structure):
@@ -41,7 +42,10 @@ class kf_config(ctypes.Structure):
                 ("dup_shared_frac", ctypes.c_float), ("n_eta_bins", ctypes.c_int),
                 ("n_phi_bins", ctypes.c_int), ("lanes_per_seed", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("per_event", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("find_regcap", ctypes.c_int)]
+                ("per_event", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("find_regcap", ctypes.c_int),
+                ("dup_deta", ctypes.c_float), ("dup_dphi", ctypes.c_float), ("dup_dpt", ctypes.c_float),
+                ("seed_clean", ctypes.c_int), ("seed_deta", ctypes.c_float), ("seed_dphi", ctypes.c_float),
+                ("seed_dpt", ctypes.c_float), ("seed_min_shared", ctypes.c_int)]
 
 
 class KFError(RuntimeError):
@@ -253,9 +257,11 @@ def kf_set_stage_timing(ctx, enable=True):
 
 
 def kf_get_stage_ms(ctx, stream=None):
-    ms = np.zeros(5, np.float32)
+    """Stage durations of the last run (ms); stages that did not run are left out."""
+    ms = np.zeros(6, np.float32)
     _check(ctx, load().kf_get_stage_ms(ctx, ms.ctypes.data_as(_P), _stream(stream)), "kf_get_stage_ms")
-    return dict(bin=float(ms[0]), find=float(ms[1]), dedup=float(ms[2]), fit=float(ms[3]), adjoint=float(ms[4]))
+    names = ("bin", "find", "dedup", "fit", "adjoint", "seed_clean")
+    return {k: float(v) for k, v in zip(names, ms) if v >= 0}
 
 
 def kf_graph_kernel_count(ctx):

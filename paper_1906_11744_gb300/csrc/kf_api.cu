@@ -38,8 +38,10 @@ struct kf_ctx {
   DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp, bin_grouped, bin_gtab;
   // finding
   DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent, seed_order, check;
-  // duplicate removal scratch
+  // duplicate removal scratch (the conflict lists also serve seed cleaning)
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state, dd_scan_tmp;
+  // seed cleaning
+  DevBuf sc_kin, sc_seed, clean_order, kept_cnt;
   // fit
   DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count, careful_flag, ckpt;
   bool want_ckpt = false;
@@ -51,7 +53,7 @@ struct kf_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int stage_timing = 0;
-  cudaEvent_t ev[10] = {};  // start/end of bin, find, dedup, fit, adjoint
+  cudaEvent_t ev[12] = {};  // start/end of bin, find, dedup, fit, adjoint, seed cleaning
   // Side stream (highest priority) for the careful passes that run beside
   // the main passes; fork/join events.
   cudaStream_t side = nullptr;
@@ -170,6 +172,8 @@ static int check_status(kf_ctx* ctx, cudaStream_t st) {
     case ST_DEDUP_PARTNERS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: partner table overflow");
     case ST_DEDUP_CONFLICTS: return fail(ctx, KF_ERR_CAPACITY, "duplicate removal: conflict table overflow");
     case ST_DEDUP_ROUNDS: return fail(ctx, KF_ERR_TIMEOUT, "duplicate removal: resolution did not settle");
+    case ST_SEED_CONFLICTS: return fail(ctx, KF_ERR_CAPACITY, "seed cleaning: conflict table overflow");
+    case ST_SEED_ROUNDS: return fail(ctx, KF_ERR_TIMEOUT, "seed cleaning: resolution did not settle");
     default: return fail(ctx, KF_ERR_CUDA, "unknown device status");
   }
 }
@@ -203,6 +207,13 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   int threads = cfg->block_threads ? cfg->block_threads : 128;
   if (threads < 32 || threads > 256 || threads % 32) return KF_ERR_ARG;
   if (cfg->find_regcap < 0 || cfg->find_regcap > 1 || (cfg->find_regcap && threads > 128)) return KF_ERR_ARG;
+  auto cut_ok = [](float c) { return c >= 0.f && std::isfinite(c); };
+  if (!cut_ok(cfg->dup_deta) || !cut_ok(cfg->dup_dphi) || !cut_ok(cfg->dup_dpt)) return KF_ERR_ARG;
+  if (cfg->seed_clean < 0 || cfg->seed_clean > 1) return KF_ERR_ARG;
+  if (cfg->seed_clean && (!(cfg->seed_deta > 0.f) || !(cfg->seed_deta <= KF_SEED_MAX_DETA) ||
+                          !cut_ok(cfg->seed_dphi) || !cut_ok(cfg->seed_dpt) || cfg->seed_min_shared < 0 ||
+                          cfg->seed_min_shared > 3))
+    return KF_ERR_ARG;
   ctx = new kf_ctx();
   ctx->det = *det;
   ctx->cfg = *cfg;
@@ -303,7 +314,8 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->dd_nconf, &ctx->dd_state, &ctx->dd_scan_tmp, &ctx->given_lists, &ctx->given_n, &ctx->fit_p,
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
-                    &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt};
+                    &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
+                    &ctx->clean_order, &ctx->kept_cnt};
   for (DevBuf* b : bufs) release(*b);
   delete ctx;
   return KF_OK;
@@ -409,6 +421,12 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->careful_list, sizeof(int) * (size_t)n));
   CK(grow(ctx->careful_count, 64));
   CK(grow(ctx->careful_flag, (size_t)n));
+  if (ctx->cfg.seed_clean) {
+    CK(grow(ctx->sc_kin, sizeof(float4) * (size_t)n));
+    CK(grow(ctx->sc_seed, sizeof(int4) * (size_t)n));
+    CK(grow(ctx->clean_order, sizeof(int) * (size_t)n));
+    CK(grow(ctx->kept_cnt, sizeof(int) * (size_t)n_events));
+  }
   CK(put(ctx->sp.p, params, sizeof(float) * 6 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sc.p, cov, sizeof(float) * 21 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sh.p, seed_hits, sizeof(int) * 3 * (size_t)n, device_ptrs, st));
@@ -508,9 +526,43 @@ static FindParams find_params(kf_ctx* ctx) {
   P.queue = ptr<unsigned>(ctx->queue);
   P.tangent_list = ptr<int>(ctx->tangent);
   P.order = ptr<int>(ctx->seed_order);
+  P.seed_off = ptr<int>(ctx->seed_off);
+  P.kept_cnt = nullptr;
   P.counters = ptr<unsigned long long>(ctx->counters);
   P.persistent = ctx->persistent;
   return P;
+}
+
+static SeedCleanParams clean_params(kf_ctx* ctx) {
+  SeedCleanParams C;
+  C.kb = ctx->g.kb;
+  C.sp = ptr<float>(ctx->sp);
+  C.sc = ptr<float>(ctx->sc);
+  C.sh = ptr<int>(ctx->sh);
+  C.seed_off = ptr<int>(ctx->seed_off);
+  C.seed_event = ptr<int>(ctx->seed_event);
+  C.order = ptr<int>(ctx->seed_order);
+  C.ns = ctx->n_seeds;
+  C.L = ctx->g.n_layers;
+  C.deta = ctx->cfg.seed_deta;
+  C.dphi = ctx->cfg.seed_dphi;
+  C.dpt = ctx->cfg.seed_dpt;
+  C.min_shared = ctx->cfg.seed_min_shared;
+  C.kin = ptr<float4>(ctx->sc_kin);
+  C.kseed = ptr<int4>(ctx->sc_seed);
+  C.conf = ptr<int>(ctx->dd_conf);
+  C.n_conf = ptr<int>(ctx->dd_nconf);
+  C.state = ptr<unsigned char>(ctx->dd_state);
+  C.clean_order = ptr<int>(ctx->clean_order);
+  C.kept_cnt = ptr<int>(ctx->kept_cnt);
+  C.out_hits = ptr<int>(ctx->out_hits);
+  C.out_n = ptr<int>(ctx->out_n);
+  C.out_chi2 = ptr<float>(ctx->out_chi2);
+  C.out_p = ptr<float>(ctx->out_p);
+  C.out_C = ptr<float>(ctx->out_C);
+  C.keep = ptr<unsigned char>(ctx->keep);
+  C.status = ptr<int>(ctx->status);
+  return C;
 }
 
 static BinParams bin_params(kf_ctx* ctx) {
@@ -558,6 +610,13 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
                   ctx->scan_tmp.bytes / sizeof(unsigned), st));
     stage_mark(ctx, 1, st);
     FindParams P = find_params(ctx);
+    if (ctx->cfg.seed_clean) {
+      stage_mark(ctx, 10, st);
+      CK(launch_seed_clean(clean_params(ctx), 0, ctx->n_seeds, 0, ctx->n_events, st));
+      stage_mark(ctx, 11, st);
+      P.order = ptr<int>(ctx->clean_order);
+      P.kept_cnt = ptr<int>(ctx->kept_cnt);
+    }
     CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
     stage_mark(ctx, 2, st);
     CK(launch_find_main(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
@@ -574,6 +633,11 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
       FindParams P = find_params(ctx);
       P.s_begin = ctx->seed_off_h[e];
       P.s_end = ctx->seed_off_h[e + 1];
+      if (ctx->cfg.seed_clean) {
+        CK(launch_seed_clean(clean_params(ctx), P.s_begin, P.s_end, e, 1, st));
+        P.order = ptr<int>(ctx->clean_order);
+        P.kept_cnt = ptr<int>(ctx->kept_cnt);
+      }
       CK(cudaMemsetAsync(ctx->queue.p, 0, 64, st));
       CK(launch_find_main(P, ctx->lanes, ctx->regcap, ctx->threads, grid_cap, st));
       CK(launch_find_careful(P, ctx->lanes, careful_grid(ctx, P.s_end - P.s_begin), st));
@@ -606,6 +670,13 @@ int kf_remove_duplicates(kf_ctx* ctx, void* stream) {
   D.state = ptr<unsigned char>(ctx->dd_state);
   D.keep = ptr<unsigned char>(ctx->keep);
   D.status = ptr<int>(ctx->status);
+  if (ctx->cfg.dup_deta > 0.f || ctx->cfg.dup_dphi > 0.f || ctx->cfg.dup_dpt > 0.f) {
+    D.trk_p = ptr<float>(ctx->out_p);
+    D.kb = ctx->g.kb;
+    D.deta = ctx->cfg.dup_deta;
+    D.dphi = ctx->cfg.dup_dphi;
+    D.dpt = ctx->cfg.dup_dpt;
+  }
   if (!ctx->per_event) {
     stage_mark(ctx, 4, st);
     CK(launch_dedup_batched(D, ctx->n_events, ctx->n_hits, ptr<unsigned>(ctx->dd_scan_tmp),
@@ -820,14 +891,14 @@ int kf_set_stage_timing(kf_ctx* ctx, int enable) {
   return KF_OK;
 }
 
-int kf_get_stage_ms(kf_ctx* ctx, float* ms5, void* stream) {
-  if (!ctx || !ms5) return KF_ERR_ARG;
+int kf_get_stage_ms(kf_ctx* ctx, float* ms6, void* stream) {
+  if (!ctx || !ms6) return KF_ERR_ARG;
   if (!ctx->stage_timing) return fail(ctx, KF_ERR_STATE, "kf_get_stage_ms: stage timing is off");
   CK(cudaStreamSynchronize(S(stream)));
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) != cudaSuccess) ms = -1.f;
-    ms5[k] = ms;
+    ms6[k] = ms;
   }
   cudaGetLastError();  // an event that never ran leaves a benign error
   return KF_OK;

@@ -1,8 +1,24 @@
-// Duplicate removal after building (the paper's post-processing step, Sec. 4.2).
+// Duplicate handling (Sec. 4.2): seed cleaning before building and duplicate
+// removal after it.
 //
-// Definition (sequential): visit the tracks of an event by (more hits, lower
-// chi2 sum, lower index); keep a track unless it shares more than
-// frac * min(nA, nB) hits with a track already kept.
+// Kinematic closeness of two tracks or seeds (the paper names pT, eta and phi
+// as criteria of both steps): |d eta| < deta, |d phi0| < dphi (difference on
+// the circle), ||k_A| - |k_B|| <= dpt max(|k_A|, |k_B|) with k = q/pT; a cut
+// <= 0 is not applied.  eta = -ln tan(theta/2); phi0 is the direction of
+// motion at the point of the helix closest to the z axis, which every state
+// along the helix shares.
+//
+// Duplicate removal, definition (sequential): visit the tracks of an event by
+// (more hits, lower chi2 sum, lower index); keep a track unless it shares more
+// than frac * min(nA, nB) hits with a track already kept and (with the
+// kinematic pre-cuts) is kinematically close to it.  A track without hits (a
+// cleaned seed's) is never kept.
+//
+// Seed cleaning, definition (sequential): visit the seeds of an event by
+// index; drop a seed when a seed already kept is kinematically close to it and
+// shares at least min_shared of its three hits.  Parallel form: the same
+// conflict lists and resolution rounds as below, the pairs found by scanning
+// each seed's neighbours in the theta order of the event.
 //
 // Parallel form, identical result:
 //   1. hit -> owning tracks table (count, exclusive scan, fill);
@@ -30,6 +46,42 @@ namespace {
 
 constexpr int DEDUP_THREADS = 1024;
 
+// (eta, phi0, |q/pT|) of a state.  phi0 = atan2(-v_x, v_y) with
+// v = h c = (h x - sin phi, h y + cos phi), h times the centre c of the track
+// circle: the closest point to the axis lies along c, where the direction of
+// motion is sign(h) (c_y, -c_x)/|c|.  For h = 0, v = (-sin phi, cos phi) and
+// phi0 = phi.  Accurate library functions: these values decide which tracks
+// are kept.
+struct Kin {
+  float eta, phi0, ak;
+};
+__device__ __forceinline__ Kin kin_of(float x, float y, float kappa, float phi, float theta, float kb) {
+  const float h = kb * kappa;
+  float s, c;
+  sincosf(phi, &s, &c);
+  Kin k;
+  k.eta = -logf(tanf(0.5f * theta));
+  k.phi0 = atan2f(-fmaf(h, x, -s), fmaf(h, y, c));
+  k.ak = fabsf(kappa);
+  return k;
+}
+__device__ __forceinline__ bool kin_close(const Kin& a, const Kin& b, float deta, float dphi, float dpt) {
+  if (deta > 0.f && !(fabsf(a.eta - b.eta) < deta)) return false;
+  if (dphi > 0.f) {
+    float d = fabsf(a.phi0 - b.phi0);
+    if (d > PI_F) d = TWO_PI_F - d;
+    if (!(d < dphi)) return false;
+  }
+  if (dpt > 0.f && !(fabsf(a.ak - b.ak) <= dpt * fmaxf(a.ak, b.ak))) return false;
+  return true;
+}
+// Kinematics of track t from its state [6][ns].
+__device__ __forceinline__ Kin track_kin(const DedupParams& P, int t) {
+  const float* q = P.trk_p + t;
+  const size_t n = (size_t)P.ns;
+  return kin_of(q[0], q[n], q[3 * n], q[4 * n], q[5 * n], P.kb);
+}
+
 __device__ __forceinline__ bool prio_less(int na, float ca, int ia, int nb, float cb, int ib) {
   if (na != nb) return na > nb;
   if (ca != cb) return ca < cb;
@@ -54,6 +106,11 @@ __device__ __forceinline__ void dd_fill(const DedupParams& P, int t, unsigned* c
 __device__ __forceinline__ void dd_conflicts(const DedupParams& P, int t, const unsigned* cnt, unsigned start0,
                                              const int* owners) {
   const int n = P.out_n[t];
+  if (n == 0) {  // no track (a cleaned seed): removed, nothing to compare
+    P.n_conf[t] = 0;
+    P.state[t] = 2;
+    return;
+  }
   const float c = P.out_chi2[t];
   const int* ht = P.out_hits + (size_t)t * P.L;
   int pid[DEDUP_PARTNER_CAP];
@@ -80,11 +137,15 @@ __device__ __forceinline__ void dd_conflicts(const DedupParams& P, int t, const 
     }
   }
   if (overflow) atomicCAS(P.status, ST_OK, ST_DEDUP_PARTNERS);
+  const bool kin = P.trk_p != nullptr;
+  Kin kt;
+  if (kin) kt = track_kin(P, t);
   int nc = 0;
   for (int k = 0; k < np; ++k) {
     const int u = pid[k];
     const int nu = P.out_n[u];
-    if ((float)pcnt[k] > P.frac * (float)min(n, nu) && prio_less(nu, P.out_chi2[u], u, n, c, t)) {
+    if ((float)pcnt[k] > P.frac * (float)min(n, nu) && prio_less(nu, P.out_chi2[u], u, n, c, t) &&
+        (!kin || kin_close(kt, track_kin(P, u), P.deta, P.dphi, P.dpt))) {
       if (nc < DEDUP_CONF_CAP) P.conf[(size_t)t * DEDUP_CONF_CAP + nc] = u;
       else atomicCAS(P.status, ST_OK, ST_DEDUP_CONFLICTS);
       ++nc;
@@ -94,9 +155,18 @@ __device__ __forceinline__ void dd_conflicts(const DedupParams& P, int t, const 
   P.state[t] = 0;  // undecided
 }
 
-// Resolution rounds of event e's tracks [s0, s1) by the whole block, then the
-// keep flags.
-__device__ void dd_rounds(const DedupParams& P, int s0, int s1) {
+// Resolution rounds of items [s0, s1) (an event's tracks or seeds) by the
+// whole block, then the keep flags.  Each item's conflicts are the
+// higher-priority items that remove it if kept.
+struct Rounds {
+  const int* n_conf;
+  const int* conf;
+  unsigned char* state;
+  unsigned char* keep;
+  int* status;
+  int err;  // status value when the rounds do not settle
+};
+__device__ void dd_rounds(const Rounds& P, int s0, int s1) {
   __shared__ int sh_flag;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int max_rounds = (s1 - s0) + 2;  // bounded by the number of tracks
@@ -124,7 +194,7 @@ __device__ void dd_rounds(const DedupParams& P, int s0, int s1) {
     __syncthreads();
     if (!more) break;
     if (++round > max_rounds) {
-      if (tid == 0) atomicCAS(P.status, ST_OK, ST_DEDUP_ROUNDS);
+      if (tid == 0) atomicCAS(P.status, ST_OK, P.err);
       break;
     }
   }
@@ -188,7 +258,7 @@ __global__ void __launch_bounds__(DEDUP_THREADS) k_dedup(const DedupParams P) {
   __syncthreads();
   for (int t = s0 + tid; t < s1; t += nt) dd_conflicts(P, t, cnt, 0u, owners);
   __syncthreads();
-  dd_rounds(P, s0, s1);
+  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_DEDUP_ROUNDS}, s0, s1);
 }
 
 // Batched steps, one thread per track of the whole batch.  Event e's table
@@ -221,7 +291,113 @@ __global__ void k_dd_conflicts(const DedupParams P) {
 }
 __global__ void __launch_bounds__(DEDUP_THREADS) k_dd_rounds(const DedupParams P) {
   const int e = blockIdx.x;
-  dd_rounds(P, P.seed_off[e], P.seed_off[e + 1]);
+  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_DEDUP_ROUNDS}, P.seed_off[e], P.seed_off[e + 1]);
+}
+
+// ------------------------------------------------------------ seed cleaning
+// Kinematics and hits of the seed at each position of the theta order.
+__global__ void k_sc_kin(const SeedCleanParams P, int pos_begin, int pos_end) {
+  const int j = pos_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= pos_end) return;
+  const int s = P.order[j];
+  const size_t n = (size_t)P.ns;
+  const float th = P.sp[5 * n + s];
+  const Kin k = kin_of(P.sp[s], P.sp[n + s], P.sp[3 * n + s], P.sp[4 * n + s], th, P.kb);
+  P.kin[j] = make_float4(k.eta, k.phi0, k.ak, __int_as_float(seed_theta_bin(th)));
+  P.kseed[j] = make_int4(s, P.sh[s], P.sh[n + s], P.sh[2 * n + s]);
+}
+
+// Conflicts of the seed at position j: the lower-index seeds of its event
+// that are its duplicates.  The theta order is sorted by theta bin, so the
+// seeds within deta in eta lie in the bins of the theta range
+// [theta(eta + deta), theta(eta - deta)], theta(eta) = 2 atan(exp(-eta)); one
+// bin more on each side absorbs rounding.  Every seed in those bins is tested
+// with the exact cuts.
+__global__ void k_sc_conflicts(const SeedCleanParams P, int pos_begin, int pos_end) {
+  const int j = pos_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= pos_end) return;
+  const int e = P.seed_event[j];  // positions and seed indices share the event ranges
+  const int lo = P.seed_off[e], hi = P.seed_off[e + 1];
+  const float4 a4 = P.kin[j];
+  const int4 me = P.kseed[j];
+  const Kin a{a4.x, a4.y, a4.z};
+  const int b_lo = seed_theta_bin(2.f * atanf(expf(-(a.eta + P.deta)))) - 1;
+  const int b_hi = seed_theta_bin(2.f * atanf(expf(-(a.eta - P.deta)))) + 1;
+  int nc = 0;
+  auto test = [&](int q) {
+    const int4 o = P.kseed[q];
+    if (o.x >= me.x) return;  // only lower-index seeds remove this one
+    const float4 b4 = P.kin[q];
+    if (!kin_close(a, Kin{b4.x, b4.y, b4.z}, P.deta, P.dphi, P.dpt)) return;
+    const int shared = (me.y == o.y) + (me.y == o.z) + (me.y == o.w) + (me.z == o.y) + (me.z == o.z) +
+                       (me.z == o.w) + (me.w == o.y) + (me.w == o.z) + (me.w == o.w);
+    if (shared < P.min_shared) return;
+    if (nc < DEDUP_CONF_CAP) P.conf[(size_t)me.x * DEDUP_CONF_CAP + nc] = o.x;
+    else atomicCAS(P.status, ST_OK, ST_SEED_CONFLICTS);
+    ++nc;
+  };
+  for (int q = j - 1; q >= lo && __float_as_int(P.kin[q].w) >= b_lo; --q) test(q);
+  for (int q = j + 1; q < hi && __float_as_int(P.kin[q].w) <= b_hi; ++q) test(q);
+  P.n_conf[me.x] = min(nc, DEDUP_CONF_CAP);
+  P.state[me.x] = 0;
+}
+
+// Per event (one block): the resolution rounds, then the new order of its
+// positions (kept seeds first, each part in theta order) and the empty
+// outputs of the dropped seeds.
+__global__ void __launch_bounds__(DEDUP_THREADS) k_sc_resolve(const SeedCleanParams P, int e_begin) {
+  __shared__ int s_warp[DEDUP_THREADS / 32];
+  __shared__ int s_tot;
+  const int e = e_begin + blockIdx.x;
+  const int s0 = P.seed_off[e], s1 = P.seed_off[e + 1];
+  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_SEED_ROUNDS}, s0, s1);
+  __syncthreads();
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  // kept seeds of the event
+  int c = 0;
+  for (int j = s0 + tid; j < s1; j += nt) c += P.state[P.order[j]] == 1;
+  if (tid == 0) s_tot = 0;
+  __syncthreads();
+  c = __reduce_add_sync(0xffffffffu, c);
+  if (lane == 0) atomicAdd(&s_tot, c);
+  __syncthreads();
+  const int n_kept = s_tot;
+  if (tid == 0) P.kept_cnt[e] = n_kept;
+  // stable split of the positions, one chunk of nt at a time
+  int base_k = 0, base_d = 0;
+  for (int c0 = s0; c0 < s1; c0 += nt) {
+    const int j = c0 + tid;
+    const bool valid = j < s1;
+    const int s = valid ? P.order[j] : 0;
+    const bool kept = valid && P.state[s] == 1;
+    const unsigned bal = __ballot_sync(0xffffffffu, kept);
+    __syncthreads();  // s_warp of the previous chunk is read
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int v = s_warp[w];
+      if (w < warp) before += v;
+      total += v;
+    }
+    const int kr = before + __popc(bal & ((1u << lane) - 1u));  // kept positions before j in the chunk
+    if (valid) {
+      if (kept) {
+        P.clean_order[s0 + base_k + kr] = s;
+      } else {
+        P.clean_order[s0 + n_kept + base_d + (tid - kr)] = s;
+        const size_t n = (size_t)P.ns;
+        P.out_n[s] = 0;
+        P.out_chi2[s] = 0.f;
+        for (int l = 0; l < P.L; ++l) P.out_hits[(size_t)s * P.L + l] = -1;
+        for (int k = 0; k < 6; ++k) P.out_p[k * n + s] = P.sp[k * n + s];
+        for (int k = 0; k < 21; ++k) P.out_C[k * n + s] = P.sc[k * n + s];
+      }
+    }
+    const int n_valid = min(nt, s1 - c0);
+    base_k += total;
+    base_d += n_valid - total;
+  }
 }
 
 }  // namespace
@@ -247,6 +423,19 @@ cudaError_t launch_dedup_batched(const DedupParams& P, int n_events, int n_hits,
     k_dd_conflicts<<<blocks, threads, 0, st>>>(P);
   }
   k_dd_rounds<<<n_events, DEDUP_THREADS, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_clean(const SeedCleanParams& P, int pos_begin, int pos_end, int e_begin, int n_events,
+                              cudaStream_t st) {
+  if (n_events <= 0) return cudaSuccess;
+  const int n = pos_end - pos_begin;
+  if (n > 0) {
+    const int threads = 256, blocks = (n + threads - 1) / threads;
+    k_sc_kin<<<blocks, threads, 0, st>>>(P, pos_begin, pos_end);
+    k_sc_conflicts<<<blocks, threads, 0, st>>>(P, pos_begin, pos_end);
+  }
+  k_sc_resolve<<<n_events, DEDUP_THREADS, 0, st>>>(P, e_begin);
   return cudaGetLastError();
 }
 

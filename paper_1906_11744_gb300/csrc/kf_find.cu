@@ -197,6 +197,10 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     } else {
       const int j = P.s_begin + task * W + grp;
       has_seed = lane_used && (j < P.s_end);
+      if (has_seed && P.kept_cnt) {  // after seed cleaning: the event's first kept_cnt positions
+        const int e = P.seed_event[j];  // positions and seed indices share the event ranges
+        has_seed = j - P.seed_off[e] < P.kept_cnt[e];
+      }
       seed = has_seed && P.order ? P.order[j] : j;
     }
     // counters of this task (dropped for a seed given up)
@@ -654,20 +658,18 @@ cudaError_t launch_careful_g(const FindParams& P, int grid, cudaStream_t st) {
   }
 
 // Order in which the finding takes the seeds of each event: by polar angle
-// theta (counting sort into THETA_BINS bins, one block per event).  The seeds
-// of a warp then cross about as many layers before they leave the barrel,
-// which keeps its groups busy for the same number of iterations; the result
-// of a seed does not depend on the order.
-constexpr int THETA_BINS = 1024;
+// theta (counting sort into SEED_THETA_BINS bins, one block per event).  The
+// seeds of a warp then cross about as many layers before they leave the
+// barrel, which keeps its groups busy for the same number of iterations; the
+// result of a seed does not depend on the order.
+constexpr int THETA_BINS = SEED_THETA_BINS;
 __global__ void __launch_bounds__(1024) k_seed_order(const float* theta, const int* seed_off, int* order) {
   __shared__ unsigned cnt[THETA_BINS];
   __shared__ unsigned sh[33];
   const int s0 = seed_off[blockIdx.x], s1 = seed_off[blockIdx.x + 1];
   for (int k = threadIdx.x; k < THETA_BINS; k += blockDim.x) cnt[k] = 0u;
   __syncthreads();
-  auto bin_of = [&](int s) {
-    return min(max((int)(theta[s] * (THETA_BINS / PI_F)), 0), THETA_BINS - 1);
-  };
+  auto bin_of = [&](int s) { return seed_theta_bin(theta[s]); };
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) atomicAdd(&cnt[bin_of(s)], 1u);
   __syncthreads();
   // exclusive scan of the THETA_BINS counts (one per thread)

@@ -14,7 +14,17 @@ enum : int {
   ST_DEDUP_PARTNERS = 1,   // a track shares hits with more tracks than the partner table holds
   ST_DEDUP_CONFLICTS = 2,  // more higher-priority conflicts than the conflict table holds
   ST_DEDUP_ROUNDS = 3,     // the resolution loop hit its iteration bound
+  ST_SEED_CONFLICTS = 4,   // seed cleaning: more lower-index duplicates than the conflict table holds
+  ST_SEED_ROUNDS = 5,      // seed cleaning: the resolution loop hit its iteration bound
 };
+
+// Seeds of an event are taken in order of their polar angle, counting-sorted
+// into SEED_THETA_BINS equal bins of [0, pi] (the order within a bin is
+// arbitrary).
+constexpr int SEED_THETA_BINS = 1024;
+__device__ __forceinline__ int seed_theta_bin(float theta) {
+  return min(max((int)(theta * ((float)SEED_THETA_BINS / PI_F)), 0), SEED_THETA_BINS - 1);
+}
 
 struct FindParams {
   DevGeom g;
@@ -35,6 +45,9 @@ struct FindParams {
   int ns;                    // seed stride
   int s_begin, s_end;        // seed range of this launch
   const int* order;          // [ns] order of the seeds within each event (or null)
+  const int* seed_off;       // [n_events + 1]
+  const int* kept_cnt;       // [n_events] seeds left by seed cleaning (or null: every seed);
+                             // with it, order lists each event's kept seeds first
   int* out_hits;             // [ns][n_layers]
   int* out_n;                // [ns]
   float* out_chi2;           // [ns]
@@ -83,6 +96,40 @@ struct DedupParams {
   int* conf;             // [ns * DEDUP_CONF_CAP]
   int* n_conf;           // [ns]
   unsigned char* state;  // [ns]
+  unsigned char* keep;   // [ns]
+  int* status;
+  // Kinematic pre-cuts (null trk_p: none): a pair is a duplicate only if its
+  // states trk_p [6][ns] are also close in eta, phi0 and pT (a cut <= 0 is off).
+  const float* trk_p = nullptr;
+  float kb = 0.f;        // h = kb * q/pT
+  float deta = 0.f, dphi = 0.f, dpt = 0.f;
+};
+
+struct SeedCleanParams {
+  float kb;              // h = kb * q/pT
+  const float* sp;       // seed params [6][ns]
+  const float* sc;       // seed cov [21][ns]
+  const int* sh;         // seed hits [3][ns]
+  const int* seed_off;   // [n_events + 1]
+  const int* seed_event; // [ns]
+  const int* order;      // [ns] the theta order of each event's seeds
+  int ns;
+  int L;
+  float deta, dphi, dpt; // cuts (deta > 0; dphi, dpt <= 0: not applied)
+  int min_shared;        // seed hits shared, at least
+  float4* kin;           // [ns] by position in order: (eta, phi0, |q/pT|, theta bin as int bits)
+  int4* kseed;           // [ns] by position: (seed, its three hits)
+  int* conf;             // [ns * DEDUP_CONF_CAP] lower-index duplicates of each seed
+  int* n_conf;           // [ns]
+  unsigned char* state;  // [ns]
+  int* clean_order;      // [ns] per event: the kept seeds in theta order, then the dropped ones
+  int* kept_cnt;         // [n_events]
+  // outputs written for a dropped seed: an empty track, not kept
+  int* out_hits;         // [ns][L]
+  int* out_n;
+  float* out_chi2;
+  float* out_p;          // [6][ns]
+  float* out_C;          // [21][ns]
   unsigned char* keep;   // [ns]
   int* status;
 };
@@ -197,6 +244,10 @@ cudaError_t launch_dedup(const DedupParams& P, int n_events, cudaStream_t st);
 // scan_tmp_elems(n_hits + n_events) entries.
 cudaError_t launch_dedup_batched(const DedupParams& P, int n_events, int n_hits, unsigned* scan_tmp,
                                  size_t scan_tmp_elems, cudaStream_t st);
+// Seed cleaning of the seeds at positions [pos_begin, pos_end) of the theta
+// order, which are those of events [e_begin, e_begin + n_events).
+cudaError_t launch_seed_clean(const SeedCleanParams& P, int pos_begin, int pos_end, int e_begin, int n_events,
+                              cudaStream_t st);
 // kf_fit.cu: the FP32 pass (flags and lists near-tangent tracks) and the
 // careful pass over the list; launch_fit runs both.
 cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st);
