@@ -9,8 +9,10 @@ graph over the whole batch.
 
 Prints one JSON line: seeds/s (whole job), candidate-layer steps/s, the plain
 per-event launch form for comparison, the end-to-end rate through the C ABI
-with host buffers, the FP32 roofline of the find kernel and the FP64 oracle's
-rate on the host cores (bounded sample).
+with host buffers, the FP32 roofline of the find kernel, the same step with
+seed cleaning and the kinematic pre-cuts of duplicate removal switched on
+(timed separately, with the cleaning stage's memory roofline) and the FP64
+oracle's rate on the host cores (bounded sample).
 """
 from __future__ import annotations
 
@@ -45,11 +47,32 @@ F_FIT_HIT = 608   # re-fit: propagation + transport + update + scattering per hi
 # DRAM traffic (read + write) of one k_find launch on the 100-event batch,
 # scaled by events from an ncu capture of the same kernel on 20 of its events
 # (193.6 MB).  Set to None whenever k_find changes until it is captured again.
-FIND_TRAFFIC_BYTES = 193.58e6 * 5
+FIND_TRAFFIC_BYTES = None
+
+# Duplicate handling measured beside the headline step (Sec. 4.2): seed
+# cleaning on kinematics alone (eta, phi0 within 0.01, pT within 20%) and
+# duplicate removal with pre-cuts (eta, phi0 within 0.02, pT within 30%).
+DUP_CFG = dict(seed_clean=1, seed_deta=0.01, seed_dphi=0.01, seed_dpt=0.2, seed_min_shared=0,
+               dup_deta=0.02, dup_dphi=0.02, dup_dpt=0.3)
+# Algorithmic HBM bytes of seed cleaning per seed: k_sc_kin reads the order
+# entry, five state values and three hit indices and writes 32 B of
+# kinematics and hits (68 B); k_sc_conflicts reads its own 32 B and writes a
+# conflict count and state (37 B; neighbours come from L2); k_sc_resolve reads
+# order and state twice, writes the new order entry and keep flag (15 B).
+CLEAN_BYTES_PER_SEED = 68 + 37 + 15
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+
+
+def _measured_peak(key, fallback):
+    """(value, source) of a measured peak of this GPU model, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
 
 
 def fp32_peak_tflops(mhz=SM_MAX_MHZ):
@@ -240,6 +263,7 @@ def main():
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-dup", action="store_true", help="skip the duplicate-handling step")
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--ref-events", type=int, default=20)
@@ -364,6 +388,50 @@ def main():
                  "form": "per-event launches of bin/find/dedup, one fit and one adjoint launch, no graph"}
         tp.close()
 
+    # the same step with seed cleaning and the kinematic pre-cuts of duplicate removal
+    dup = None
+    if not args.no_dup:
+        best = {} if tune is None else dict(
+            lanes_per_seed=int(tune[np.argmin(tune[:, 4])][0]), block_threads=int(tune[np.argmin(tune[:, 4])][1]),
+            persistent=int(tune[np.argmin(tune[:, 4])][2]), find_regcap=int(tune[np.argmin(tune[:, 4])][3]))
+        td = tracker_for(b, **{"persistent": 1, "per_event": 0, **(shape or best), **DUP_CFG})
+        td.load_hits(b.hit_off, d_in["x"], d_in["y"], d_in["z"], d_in["layer"], stream)
+        td.load_seeds(b.seed_off, d_in["params"], d_in["cov"], d_in["seed_hits"], stream)
+        td.set_alignment(b.align, stream)
+        td.set_stage_timing(True)
+        td.capture_graph(with_adjoint=True, stream=stream)
+        for _ in range(args.warmup):
+            td.launch_graph(stream)
+        stream.synchronize()
+        dc = td.counters(stream)
+        da = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        db = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        dstage = {}
+        for k in range(args.steps):
+            flush_l2()
+            da[k].record(stream)
+            td.launch_graph(stream)
+            db[k].record(stream)
+            for key, v in td.stage_ms(stream).items():
+                dstage[key] = dstage.get(key, 0.0) + v
+        stream.synchronize()
+        dms = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in zip(da, db)), dev)
+        trk = td.get_tracks(stream=stream)
+        clean_ms = dstage["seed_clean"] / args.steps
+        clean_gbs = n_seeds * CLEAN_BYTES_PER_SEED / (clean_ms / 1e3) / 1e9
+        hbm_peak = _measured_peak("hbm_gbs", 6800.0)
+        dup = {"value": seeds_all * args.steps / (dms / 1e3), "unit": UNIT, "ms_per_step": dms / args.steps,
+               "cuts": DUP_CFG, "stage_ms": {k: v / args.steps for k, v in dstage.items()},
+               "seeds_dropped_per_step": int(n_seeds - dc["seeds"]),
+               "tracks_kept_per_step": int(trk["keep"].sum()),
+               "tracks_kept_without": None,
+               "gpu_launches": td.graph_kernel_count() * args.steps,
+               "roofline_seed_clean": {"bound": "hbm", "achieved": clean_gbs, "peak": hbm_peak[0],
+                                       "unit": "GB/s", "frac": clean_gbs / hbm_peak[0], "peak_source": hbm_peak[1],
+                                       "bytes_per_seed": CLEAN_BYTES_PER_SEED, "traffic": None}}
+        td.close()
+        dup["tracks_kept_without"] = int(t.get_tracks(stream=stream)["keep"].sum())
+
     # end to end through the C ABI with host buffers (pinned), host<->device copies inside
     e2e = None
     if not args.no_e2e:
@@ -433,6 +501,7 @@ def main():
                "e2e": e2e,
                "gpu_launches": n_kernels * args.steps,
                "roofline": roofline,
+               "dup_handling": dup,
                "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample",
                                                                             "single_core_value", "single_core_sample")},
                "clocks": clocks.summary()}

@@ -41,7 +41,7 @@ struct kf_ctx {
   // duplicate removal scratch (the conflict lists also serve seed cleaning)
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state, dd_scan_tmp;
   // seed cleaning
-  DevBuf sc_kin, sc_seed, clean_order, kept_cnt;
+  DevBuf sc_kin, sc_seed, clean_order, kept_cnt, sc_list, sc_list_cnt;
   // fit
   DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count, careful_flag, ckpt;
   bool want_ckpt = false;
@@ -315,7 +315,7 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->fit_C, &ctx->fit_chi2, &ctx->fit_status, &ctx->careful_list,
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
-                    &ctx->clean_order, &ctx->kept_cnt};
+                    &ctx->clean_order, &ctx->kept_cnt, &ctx->sc_list, &ctx->sc_list_cnt};
   for (DevBuf* b : bufs) release(*b);
   delete ctx;
   return KF_OK;
@@ -426,6 +426,8 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
     CK(grow(ctx->sc_seed, sizeof(int4) * (size_t)n));
     CK(grow(ctx->clean_order, sizeof(int) * (size_t)n));
     CK(grow(ctx->kept_cnt, sizeof(int) * (size_t)n_events));
+    CK(grow(ctx->sc_list, sizeof(int) * (size_t)n));
+    CK(grow(ctx->sc_list_cnt, sizeof(int) * (size_t)n_events));
   }
   CK(put(ctx->sp.p, params, sizeof(float) * 6 * (size_t)n, device_ptrs, st));
   CK(put(ctx->sc.p, cov, sizeof(float) * 21 * (size_t)n, device_ptrs, st));
@@ -553,6 +555,8 @@ static SeedCleanParams clean_params(kf_ctx* ctx) {
   C.conf = ptr<int>(ctx->dd_conf);
   C.n_conf = ptr<int>(ctx->dd_nconf);
   C.state = ptr<unsigned char>(ctx->dd_state);
+  C.list = ptr<int>(ctx->sc_list);
+  C.list_cnt = ptr<int>(ctx->sc_list_cnt);
   C.clean_order = ptr<int>(ctx->clean_order);
   C.kept_cnt = ptr<int>(ctx->kept_cnt);
   C.out_hits = ptr<int>(ctx->out_hits);

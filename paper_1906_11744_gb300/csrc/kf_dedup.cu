@@ -166,39 +166,49 @@ struct Rounds {
   int* status;
   int err;  // status value when the rounds do not settle
 };
-__device__ void dd_rounds(const Rounds& P, int s0, int s1) {
+// One step of item t: removed as soon as one of its conflicts is kept, kept
+// as soon as all of them are removed.  Returns false while undecided.
+__device__ __forceinline__ bool dd_decide(const Rounds& P, int t) {
+  if (P.state[t] != 0) return true;
+  const int nc = min(P.n_conf[t], DEDUP_CONF_CAP);
+  bool any_kept = false, all_removed = true;
+  for (int k = 0; k < nc; ++k) {
+    const unsigned char s = ((volatile unsigned char*)P.state)[P.conf[(size_t)t * DEDUP_CONF_CAP + k]];
+    if (s == 1) any_kept = true;
+    if (s != 2) all_removed = false;
+  }
+  if (any_kept) P.state[t] = 2;
+  else if (all_removed) P.state[t] = 1;
+  else return false;
+  return true;
+}
+// Rounds by the whole block over items item(0..n) until every one is decided
+// (at most n + 2 rounds: each settles the highest-priority undecided item).
+template <class Item>
+__device__ void dd_rounds_over(const Rounds& P, int n, Item item) {
   __shared__ int sh_flag;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int max_rounds = (s1 - s0) + 2;  // bounded by the number of tracks
-  int round = 0;
-  for (;;) {
+  for (int round = 0;; ++round) {
     if (tid == 0) sh_flag = 0;
     __syncthreads();
-    int undecided = 0;
-    for (int t = s0 + tid; t < s1; t += nt) {
-      if (P.state[t] != 0) continue;
-      const int nc = P.n_conf[t];
-      bool any_kept = false, all_removed = true;
-      for (int k = 0; k < nc; ++k) {
-        const unsigned char s = ((volatile unsigned char*)P.state)[P.conf[(size_t)t * DEDUP_CONF_CAP + k]];
-        if (s == 1) any_kept = true;
-        if (s != 2) all_removed = false;
-      }
-      if (any_kept) P.state[t] = 2;
-      else if (all_removed) P.state[t] = 1;
-      else undecided = 1;
-    }
+    bool undecided = false;
+    for (int i = tid; i < n; i += nt)
+      if (!dd_decide(P, item(i))) undecided = true;
     if (undecided) sh_flag = 1;
     __syncthreads();
     const int more = sh_flag;
     __syncthreads();
     if (!more) break;
-    if (++round > max_rounds) {
+    if (round > n + 2) {
       if (tid == 0) atomicCAS(P.status, ST_OK, P.err);
       break;
     }
   }
-  for (int t = s0 + tid; t < s1; t += nt) P.keep[t] = P.state[t] == 1 ? 1 : 0;
+}
+__device__ void dd_rounds(const Rounds& P, int s0, int s1) {
+  dd_rounds_over(P, s1 - s0, [&](int i) { return s0 + i; });
+  if (P.keep)
+    for (int t = s0 + threadIdx.x; t < s1; t += blockDim.x) P.keep[t] = P.state[t] == 1 ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(DEDUP_THREADS) k_dedup(const DedupParams P) {
@@ -295,109 +305,126 @@ __global__ void __launch_bounds__(DEDUP_THREADS) k_dd_rounds(const DedupParams P
 }
 
 // ------------------------------------------------------------ seed cleaning
-// Kinematics and hits of the seed at each position of the theta order.
+// Kinematics and hits of the seed at each position of the theta order; its
+// conflict count cleared and its state preset to kept (a seed without
+// conflicts is kept); the event's list of seeds with conflicts emptied.
 __global__ void k_sc_kin(const SeedCleanParams P, int pos_begin, int pos_end) {
   const int j = pos_begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= pos_end) return;
+  const int e = P.seed_event[j];
+  if (j == P.seed_off[e]) P.list_cnt[e] = 0;
   const int s = P.order[j];
   const size_t n = (size_t)P.ns;
   const float th = P.sp[5 * n + s];
   const Kin k = kin_of(P.sp[s], P.sp[n + s], P.sp[3 * n + s], P.sp[4 * n + s], th, P.kb);
   P.kin[j] = make_float4(k.eta, k.phi0, k.ak, __int_as_float(seed_theta_bin(th)));
   P.kseed[j] = make_int4(s, P.sh[s], P.sh[n + s], P.sh[2 * n + s]);
+  P.n_conf[j] = 0;
+  P.state[j] = 1;
 }
 
-// Conflicts of the seed at position j: the lower-index seeds of its event
-// that are its duplicates.  The theta order is sorted by theta bin, so the
-// seeds within deta in eta lie in the bins of the theta range
-// [theta(eta + deta), theta(eta - deta)], theta(eta) = 2 atan(exp(-eta)); one
-// bin more on each side absorbs rounding.  Every seed in those bins is tested
-// with the exact cuts.
+// Duplicate pairs, each tested once: the seed at position j against the
+// later positions of its event within its theta-bin window.  A pair found is
+// a conflict of its higher-index seed (conflict lists and decision states are
+// kept by position, so that the resolution reads them in order); a seed's
+// first conflict makes it undecided and enters it in its event's list (at
+// most one entry per position of the event).  The theta
+// order is sorted by theta bin, and every seed within deta in eta of seed j
+// has theta below theta(eta_j - deta), theta(eta) = 2 atan(exp(-eta)): the
+// scan stops past that bin (one bin more absorbs rounding).  A later position
+// in the same or a later bin can also lie below eta_j; both halves of the
+// window are covered because the lower member of every pair scans upward.
 __global__ void k_sc_conflicts(const SeedCleanParams P, int pos_begin, int pos_end) {
   const int j = pos_begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= pos_end) return;
   const int e = P.seed_event[j];  // positions and seed indices share the event ranges
   const int lo = P.seed_off[e], hi = P.seed_off[e + 1];
   const float4 a4 = P.kin[j];
-  const int4 me = P.kseed[j];
   const Kin a{a4.x, a4.y, a4.z};
-  const int b_lo = seed_theta_bin(2.f * atanf(expf(-(a.eta + P.deta)))) - 1;
   const int b_hi = seed_theta_bin(2.f * atanf(expf(-(a.eta - P.deta)))) + 1;
-  int nc = 0;
-  auto test = [&](int q) {
-    const int4 o = P.kseed[q];
-    if (o.x >= me.x) return;  // only lower-index seeds remove this one
+  int4 me = make_int4(-1, 0, 0, 0);
+  for (int q = j + 1; q < hi; ++q) {
     const float4 b4 = P.kin[q];
-    if (!kin_close(a, Kin{b4.x, b4.y, b4.z}, P.deta, P.dphi, P.dpt)) return;
+    if (__float_as_int(b4.w) > b_hi) break;
+    if (!kin_close(a, Kin{b4.x, b4.y, b4.z}, P.deta, P.dphi, P.dpt)) continue;
+    if (me.x < 0) me = P.kseed[j];
+    const int4 o = P.kseed[q];
     const int shared = (me.y == o.y) + (me.y == o.z) + (me.y == o.w) + (me.z == o.y) + (me.z == o.z) +
                        (me.z == o.w) + (me.w == o.y) + (me.w == o.z) + (me.w == o.w);
-    if (shared < P.min_shared) return;
-    if (nc < DEDUP_CONF_CAP) P.conf[(size_t)me.x * DEDUP_CONF_CAP + nc] = o.x;
+    if (shared < P.min_shared) continue;
+    const int t = o.x > me.x ? q : j, u = o.x > me.x ? j : q;  // t is removed by u if u is kept
+    const int slot = atomicAdd(&P.n_conf[t], 1);
+    if (slot < DEDUP_CONF_CAP) P.conf[(size_t)t * DEDUP_CONF_CAP + slot] = u;
     else atomicCAS(P.status, ST_OK, ST_SEED_CONFLICTS);
-    ++nc;
-  };
-  for (int q = j - 1; q >= lo && __float_as_int(P.kin[q].w) >= b_lo; --q) test(q);
-  for (int q = j + 1; q < hi && __float_as_int(P.kin[q].w) <= b_hi; ++q) test(q);
-  P.n_conf[me.x] = min(nc, DEDUP_CONF_CAP);
-  P.state[me.x] = 0;
+    if (slot == 0) {
+      P.state[t] = 0;
+      P.list[lo + atomicAdd(&P.list_cnt[e], 1)] = t;
+    }
+  }
 }
 
-// Per event (one block): the resolution rounds, then the new order of its
-// positions (kept seeds first, each part in theta order) and the empty
-// outputs of the dropped seeds.
+// Per event (one block): the resolution rounds over the event's seeds with
+// conflicts; then the new order of its positions (kept seeds first in theta
+// order, the dropped ones from the end) and the empty outputs of the dropped
+// seeds.  Each thread splits a contiguous segment of positions; one block
+// scan of the segments' kept counts places them.
 __global__ void __launch_bounds__(DEDUP_THREADS) k_sc_resolve(const SeedCleanParams P, int e_begin) {
   __shared__ int s_warp[DEDUP_THREADS / 32];
   __shared__ int s_tot;
   const int e = e_begin + blockIdx.x;
   const int s0 = P.seed_off[e], s1 = P.seed_off[e + 1];
-  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_SEED_ROUNDS}, s0, s1);
-  __syncthreads();
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  // kept seeds of the event
-  int c = 0;
-  for (int j = s0 + tid; j < s1; j += nt) c += P.state[P.order[j]] == 1;
-  if (tid == 0) s_tot = 0;
-  __syncthreads();
-  c = __reduce_add_sync(0xffffffffu, c);
-  if (lane == 0) atomicAdd(&s_tot, c);
-  __syncthreads();
-  const int n_kept = s_tot;
-  if (tid == 0) P.kept_cnt[e] = n_kept;
-  // stable split of the positions, one chunk of nt at a time
-  int base_k = 0, base_d = 0;
-  for (int c0 = s0; c0 < s1; c0 += nt) {
-    const int j = c0 + tid;
-    const bool valid = j < s1;
-    const int s = valid ? P.order[j] : 0;
-    const bool kept = valid && P.state[s] == 1;
-    const unsigned bal = __ballot_sync(0xffffffffu, kept);
-    __syncthreads();  // s_warp of the previous chunk is read
-    if (lane == 0) s_warp[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < nw; ++w) {
-      const int v = s_warp[w];
-      if (w < warp) before += v;
-      total += v;
-    }
-    const int kr = before + __popc(bal & ((1u << lane) - 1u));  // kept positions before j in the chunk
-    if (valid) {
-      if (kept) {
-        P.clean_order[s0 + base_k + kr] = s;
-      } else {
-        P.clean_order[s0 + n_kept + base_d + (tid - kr)] = s;
-        const size_t n = (size_t)P.ns;
-        P.out_n[s] = 0;
-        P.out_chi2[s] = 0.f;
-        for (int l = 0; l < P.L; ++l) P.out_hits[(size_t)s * P.L + l] = -1;
-        for (int k = 0; k < 6; ++k) P.out_p[k * n + s] = P.sp[k * n + s];
-        for (int k = 0; k < 21; ++k) P.out_C[k * n + s] = P.sc[k * n + s];
-      }
-    }
-    const int n_valid = min(nt, s1 - c0);
-    base_k += total;
-    base_d += n_valid - total;
+  if (s1 <= s0) {
+    if (threadIdx.x == 0) P.kept_cnt[e] = 0;
+    return;
   }
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int* list = P.list + s0;
+  dd_rounds_over(Rounds{P.n_conf, P.conf, P.state, nullptr, P.status, ST_SEED_ROUNDS}, P.list_cnt[e],
+                 [&](int i) { return list[i]; });
+  __syncthreads();
+  const int per = (s1 - s0 + nt - 1) / nt;
+  const int a = min(s0 + tid * per, s1), b = min(a + per, s1);
+  int mine = 0;
+  for (int j = a; j < b; ++j) mine += P.state[j] == 1;
+  // exclusive scan of the kept counts over the block
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = lane < nw ? s_warp[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += v;
+    }
+    if (lane < nw) s_warp[lane] = wi - w;
+    if (lane == nw - 1) s_tot = wi;
+  }
+  __syncthreads();
+  int kr = s_warp[warp] + incl - mine;   // kept positions before this segment
+  int dr = (a - s0) - kr;                // dropped positions before it
+  const size_t n = (size_t)P.ns;
+  for (int j = a; j < b; ++j) {
+    const int s = P.order[j];
+    if (P.state[j] == 1) {
+      P.clean_order[s0 + kr++] = s;
+    } else {
+      P.clean_order[s1 - 1 - dr++] = s;
+      P.keep[s] = 0;
+      P.out_n[s] = 0;
+      P.out_chi2[s] = 0.f;
+      for (int l = 0; l < P.L; ++l) P.out_hits[(size_t)s * P.L + l] = -1;
+      for (int k = 0; k < 6; ++k) P.out_p[k * n + s] = P.sp[k * n + s];
+      for (int k = 0; k < 21; ++k) P.out_C[k * n + s] = P.sc[k * n + s];
+    }
+  }
+  if (tid == 0) P.kept_cnt[e] = s_tot;
 }
 
 }  // namespace

@@ -119,9 +119,11 @@ struct SeedCleanParams {
   int min_shared;        // seed hits shared, at least
   float4* kin;           // [ns] by position in order: (eta, phi0, |q/pT|, theta bin as int bits)
   int4* kseed;           // [ns] by position: (seed, its three hits)
-  int* conf;             // [ns * DEDUP_CONF_CAP] lower-index duplicates of each seed
-  int* n_conf;           // [ns]
-  unsigned char* state;  // [ns]
+  int* conf;             // [ns * DEDUP_CONF_CAP] by position: positions of the lower-index duplicates
+  int* n_conf;           // [ns] by position
+  unsigned char* state;  // [ns] by position
+  int* list;             // [ns] per event (at its positions): the positions with conflicts
+  int* list_cnt;         // [n_events]
   int* clean_order;      // [ns] per event: the kept seeds in theta order, then the dropped ones
   int* kept_cnt;         // [n_events]
   // outputs written for a dropped seed: an empty track, not kept
