@@ -3,8 +3,10 @@
 // Mapping: one seed per group of G lanes, one lane per candidate slot (G >=
 // N = max_cands), 32/G seeds per warp processed in lockstep.  A candidate's
 // state (6 parameters + 21 covariance terms) stays in its lane's registers
-// across all layers.  One loop covers the seed fit (three forced hits) and the
-// layers after the seed.  Per layer:
+// across all layers.  The seed fit (three forced hits) runs before, one
+// thread per seed (k_seed_fit): inside the group loop only one lane of each
+// group would work on it.  The careful pass keeps the seed fit in its loop
+// (with double-precision steps where needed).  Per layer:
 //   1. every live candidate propagates to the layer (closed-form helix, exact
 //      Jacobian, sparse J C J^T) and builds its measurement frame;
 //   2. it walks the eta x phi bins of a window that contains the whole
@@ -146,6 +148,66 @@ __device__ __noinline__ bool careful_child(const double* in, float* out, float m
 // CAREFUL: the pass over the seeds the main pass listed (always persistent).
 // Counters in P.queue: [0] main-pass work, [1] careful-pass work, [2] number
 // of listed seeds.
+// Seed fit, one thread per seed of [s_begin, s_end): at the first seed hit
+// the update of the prior, then for the second and third hit propagation,
+// transport and update, with the scattering of each layer after its update.
+// sfit [28][ns] gets (p, C, chi2 sum); sflag bit 0: finished (no crossing or
+// a far-side seed hit: later layers carry the state unchanged), bit 1: a
+// crossing closer to tangent than FIND_CAREFUL_COS (the main pass lists the
+// seed for the careful pass without searching it).
+__global__ void k_seed_fit(const FindParams P) {
+  const int seed = P.s_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (seed >= P.s_end) return;
+  const DevGeom& g = P.g;
+  const size_t ns = (size_t)P.ns;
+  const int hoff = P.hit_off[P.seed_event[seed]];
+  float p[6], C[21];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = P.sp[k * ns + seed];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = P.sc[k * ns + seed];
+  float chi2 = 0.f;
+  unsigned flag = 0;
+#pragma unroll 1
+  for (int it = 0; it < 3; ++it) {
+    const int hi = hoff + P.sh[it * ns + seed];
+    const int l = P.hlayer[hi];
+    if (it != 0) {
+      float q[6], J[6][6], cosa = 1.f;
+      const int pr = prop_jacobian<float>(p, g.radius[l], g.kb, INFINITY, q, J, &cosa);
+      if (pr != 1) {
+        flag |= 1u;
+        break;
+      }
+      if (cosa < FIND_CAREFUL_COS) {
+        flag |= 2u;
+        break;
+      }
+      transport<float>(J, C);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) p[k] = q[k];
+    }
+    float mx, my, mz;
+    corrected_hit(P.align[l], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+    Frame f;
+    make_frame<float>(p, C, g.vr, g.vz, f);
+    float r0, r1;
+    if (!residual<float>(p, f, mx, my, mz, r0, r1)) {
+      flag |= 1u;
+      break;
+    }
+    chi2 += chi2_of<float>(f, r0, r1);
+    kf_update<float>(p, C, f, r0, r1);
+    add_ms<float>(p, C, g.x0[l]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) P.sfit[k * ns + seed] = p[k];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) P.sfit[(6 + k) * ns + seed] = C[k];
+  P.sfit[27 * ns + seed] = chi2;
+  P.sflag[seed] = (unsigned char)flag;
+}
+
 template <int G, int CAP, bool CAREFUL>
 __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const FindParams P) {
   constexpr int W = 32 / G;  // seeds per warp
@@ -219,13 +281,24 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       sh0 = P.sh[seed];
       sh1 = P.sh[(size_t)P.ns + seed];
       sh2 = P.sh[2 * (size_t)P.ns + seed];
-      sl0 = P.hlayer[hoff + sh0];
-      sl1 = P.hlayer[hoff + sh1];
       sl2 = P.hlayer[hoff + sh2];
+      if constexpr (CAREFUL) {
+        sl0 = P.hlayer[hoff + sh0];
+        sl1 = P.hlayer[hoff + sh1];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + seed];
+        for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + seed];
 #pragma unroll
-      for (int k = 0; k < 21; ++k) C[k] = P.sc[(size_t)k * P.ns + seed];
+        for (int k = 0; k < 21; ++k) C[k] = P.sc[(size_t)k * P.ns + seed];
+      } else {  // the fitted seed
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] = P.sfit[(size_t)k * P.ns + seed];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) C[k] = P.sfit[(size_t)(6 + k) * P.ns + seed];
+        chi2 = P.sfit[(size_t)27 * P.ns + seed];
+        const unsigned flag = P.sflag[seed];
+        finished = (flag & 1u) != 0;
+        if (flag & 2u) given_up = true;
+      }
       if (gl == 0) c_seeds++;
     } else {
 #pragma unroll
@@ -234,12 +307,14 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       for (int k = 0; k < 21; ++k) C[k] = 0.f;
     }
     const int start = has_seed ? sl2 + 1 : L;           // first layer searched
-    int n_iter = has_seed ? 3 + (L - start) : 0;        // seed hits + layers
+    // iterations: the three seed hits (careful pass only; the main pass starts
+    // from the fitted seed), then the layers
+    int n_iter = has_seed && !given_up ? 3 + (L - start) : 0;
     const int it_end = __reduce_max_sync(0xffffffffu, n_iter);
 
 #pragma unroll 1
-    for (int it = 0; it < it_end; ++it) {
-      const bool in_seed = it < 3;
+    for (int it = CAREFUL ? 0 : 3; it < it_end; ++it) {
+      const bool in_seed = CAREFUL && it < 3;
       const bool active = it < n_iter;
       const int l = in_seed ? (it == 0 ? sl0 : (it == 1 ? sl1 : sl2)) : start + (it - 3);
       int cls = 0;  // 1 = carried unchanged, 2 = propagated with hit/hole children
@@ -721,6 +796,10 @@ cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* 
 cudaError_t launch_find_main(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
                              cudaStream_t st) {
   if (P.s_end <= P.s_begin) return cudaSuccess;
+  const int n = P.s_end - P.s_begin;
+  k_seed_fit<<<(n + 127) / 128, 128, 0, st>>>(P);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   KF_FIND_DISPATCH(launch_main_g, P, threads, grid_cap, st)
 }
 

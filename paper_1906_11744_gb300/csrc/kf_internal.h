@@ -56,6 +56,8 @@ struct FindParams {
   unsigned* queue;           // [3] work counters of the main and careful passes and the
                              // number of listed seeds (zeroed before the launch)
   int* tangent_list;         // [ns] seeds the main pass left to the careful pass
+  float* sfit;               // [28][ns] fitted seeds (p, C, chi2 sum), written by the seed fit
+  unsigned char* sflag;      // [ns] seed-fit flags (bit 0 finished, bit 1 near-tangent crossing)
   unsigned long long* counters;  // [8], see kf_get_counters
   int persistent;
 };
