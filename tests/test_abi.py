@@ -54,6 +54,35 @@ def test_host_argument_errors_without_gpu():
         assert lib.kf_create(ctypes.byref(det), ctypes.byref(cfg), ctypes.byref(ctx)) == _lib.KF_ERR_ARG
 
 
+def test_duplicate_cut_argument_errors_without_gpu():
+    """Seed-cleaning and duplicate pre-cut settings are checked before the device:
+    negative or non-finite cuts, an eta window of seed cleaning outside
+    (0, KF_SEED_MAX_DETA], more than three shared seed hits.  Valid settings get
+    past the checks (and fail only at the device, absent here)."""
+    import ctypes
+    import math
+
+    from paper_1906_11744_gb300 import _lib, make_config, make_detector
+    lib = _lib.load()
+    ctx = ctypes.c_void_p()
+    det = make_detector([5.0, 10.0], [0.02, 0.02])
+    bad = (make_config(dup_deta=-0.1), make_config(dup_dphi=math.inf), make_config(dup_dpt=math.nan),
+           make_config(seed_clean=2), make_config(seed_clean=1, seed_deta=0.0),
+           make_config(seed_clean=1, seed_deta=1.5), make_config(seed_clean=1, seed_dphi=-1.0),
+           make_config(seed_clean=1, seed_dpt=math.inf), make_config(seed_clean=1, seed_min_shared=4),
+           make_config(seed_clean=1, seed_min_shared=-1))
+    for cfg in bad:
+        assert lib.kf_create(ctypes.byref(det), ctypes.byref(cfg), ctypes.byref(ctx)) == _lib.KF_ERR_ARG
+    ok = (make_config(dup_deta=0.02, dup_dphi=0.02, dup_dpt=0.3),
+          make_config(seed_clean=1, seed_deta=_lib.KF_SEED_MAX_DETA, seed_min_shared=3),
+          make_config(seed_clean=0, seed_deta=0.0))  # cuts of a disabled cleaning are not checked
+    for cfg in ok:
+        rc = lib.kf_create(ctypes.byref(det), ctypes.byref(cfg), ctypes.byref(ctx))
+        assert rc != _lib.KF_ERR_ARG
+        if rc == _lib.KF_OK:
+            lib.kf_destroy(ctx)
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     from paper_1906_11744_gb300 import _lib
     monkeypatch.setattr(_lib, "_lib", None)
