@@ -38,7 +38,7 @@ struct kf_ctx {
   DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp, bin_grouped, bin_gtab;
   // finding
   DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent, seed_order, check;
-  DevBuf sfit, sflag;
+  DevBuf sfit, sflag, skeys;
   // duplicate removal scratch (the conflict lists also serve seed cleaning)
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state, dd_scan_tmp;
   // seed cleaning
@@ -317,7 +317,7 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
                     &ctx->clean_order, &ctx->kept_cnt, &ctx->sc_list, &ctx->sc_list_cnt, &ctx->sfit,
-                    &ctx->sflag};
+                    &ctx->sflag, &ctx->skeys};
   for (DevBuf* b : bufs) release(*b);
   delete ctx;
   return KF_OK;
@@ -408,8 +408,9 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->out_n, sizeof(int) * (size_t)n));
   CK(grow(ctx->tangent, sizeof(int) * (size_t)n));
   CK(grow(ctx->seed_order, sizeof(int) * (size_t)n));
-  CK(grow(ctx->sfit, sizeof(float) * 28 * (size_t)n));
+  CK(grow(ctx->sfit, sizeof(float) * 29 * (size_t)n));
   CK(grow(ctx->sflag, (size_t)n));
+  CK(grow(ctx->skeys, sizeof(unsigned long long) * ctx->g.max_cands * (size_t)n));
   CK(grow(ctx->out_chi2, sizeof(float) * (size_t)n));
   CK(grow(ctx->out_p, sizeof(float) * 6 * (size_t)n));
   CK(grow(ctx->out_C, sizeof(float) * 21 * (size_t)n));
@@ -533,6 +534,7 @@ static FindParams find_params(kf_ctx* ctx) {
   P.tangent_list = ptr<int>(ctx->tangent);
   P.sfit = ptr<float>(ctx->sfit);
   P.sflag = ptr<unsigned char>(ctx->sflag);
+  P.skeys = ptr<unsigned long long>(ctx->skeys);
   P.order = ptr<int>(ctx->seed_order);
   P.seed_off = ptr<int>(ctx->seed_off);
   P.kept_cnt = nullptr;

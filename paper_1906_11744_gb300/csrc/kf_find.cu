@@ -3,10 +3,11 @@
 // Mapping: one seed per group of G lanes, one lane per candidate slot (G >=
 // N = max_cands), 32/G seeds per warp processed in lockstep.  A candidate's
 // state (6 parameters + 21 covariance terms) stays in its lane's registers
-// across all layers.  The seed fit (three forced hits) runs before, one
-// thread per seed (k_seed_fit): inside the group loop only one lane of each
-// group would work on it.  The careful pass keeps the seed fit in its loop
-// (with double-precision steps where needed).  Per layer:
+// across all layers.  The seed fit (three forced hits) and the first layer
+// after it, where each seed has a single candidate, run before, one thread
+// per seed (k_seed_fit): inside the group loop only one lane of each group
+// would work on them.  The careful pass keeps the seed fit and the first
+// layer in its loop (with double-precision steps where needed).  Per layer:
 //   1. every live candidate propagates to the layer (closed-form helix, exact
 //      Jacobian, sparse J C J^T) and builds its measurement frame;
 //   2. it walks the eta x phi bins of a window that contains the whole
@@ -148,64 +149,250 @@ __device__ __noinline__ bool careful_child(const double* in, float* out, float m
 // CAREFUL: the pass over the seeds the main pass listed (always persistent).
 // Counters in P.queue: [0] main-pass work, [1] careful-pass work, [2] number
 // of listed seeds.
-// Seed fit, one thread per seed of [s_begin, s_end): at the first seed hit
-// the update of the prior, then for the second and third hit propagation,
-// transport and update, with the scattering of each layer after its update.
-// sfit [28][ns] gets (p, C, chi2 sum); sflag bit 0: finished (no crossing or
-// a far-side seed hit: later layers carry the state unchanged), bit 1: a
-// crossing closer to tangent than FIND_CAREFUL_COS (the main pass lists the
-// seed for the careful pass without searching it).
-__global__ void k_seed_fit(const FindParams P) {
-  const int seed = P.s_begin + blockIdx.x * blockDim.x + threadIdx.x;
-  if (seed >= P.s_end) return;
+// The eta-phi bins of the window that contains the chi2 < cut ellipse of the
+// prediction p (frame f) on layer l: |r_rphi| < sqrt(cut S00) with
+// r_rphi = R_hit sin(dphi) on the near half, |r_z| < sqrt(cut S11); rows
+// [e0, e1] (none when S is not positive definite), columns [b0, b1) and, when
+// the window wraps around phi = pi, [0, b2) as well.
+struct Window {
+  int e0, e1, b0, b1, b2;
+};
+__device__ __forceinline__ Window window_of(const FindParams& P, int l, float R, const float (&p)[6],
+                                            const Frame& f, bool spd, const Align4& al) {
   const DevGeom& g = P.g;
-  const size_t ns = (size_t)P.ns;
-  const int hoff = P.hit_off[P.seed_event[seed]];
-  float p[6], C[21];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) p[k] = P.sp[k * ns + seed];
-#pragma unroll
-  for (int k = 0; k < 21; ++k) C[k] = P.sc[k * ns + seed];
-  float chi2 = 0.f;
-  unsigned flag = 0;
+  const float w1 = sqrtf(g.chi2_cut * f.s00);
+  const float w2 = sqrtf(g.chi2_cut * f.s11);
+  // asin(x) for the usual small x by x + x^3/6 + 3x^5/40 (truncation below
+  // 3e-9 relative for x < 0.05, far inside the padding)
+  const float xr = w1 / R;
+  float dphi = (xr >= 1.f) ? 0.5f * PI_F
+               : (xr < 0.05f ? xr * fmaf(xr * xr, fmaf(xr * xr, 0.075f, 1.f / 6.f), 1.f) : asinf(xr));
+  dphi = fminf(dphi, 0.5f * PI_F) * (1.f + WIN_REL) + WIN_PHI_ABS;
+  const float phic = atan2f(p[1], p[0]) + al.dphi;
+  const int nphi = g.n_phi, neta = g.n_eta;
+  const int u0 = phi_bin_raw(phic - dphi, g.phi_scale);
+  const int u1 = phi_bin_raw(phic + dphi, g.phi_scale);
+  int span = u1 - u0 + 1, b0;
+  if (span >= nphi) { span = nphi; b0 = 0; } else { b0 = wrap_bin(u0, nphi); }
+  const float zc = p[2] + al.az;
+  const float wz = w2 * (1.f + WIN_REL) + WIN_Z_ABS;
+  const float* edges = P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1);
+  const unsigned char* lut = P.eta_lut + (size_t)l * ETA_LUT;
+  Window w;
+  w.e0 = eta_bin(zc - wz, neta, g.z_max, g.eta_lut_scale, lut, edges);
+  w.e1 = spd ? eta_bin(zc + wz, neta, g.z_max, g.eta_lut_scale, lut, edges) : w.e0 - 1;
+  w.b0 = b0;
+  w.b1 = min(b0 + span, nphi);
+  w.b2 = b0 + span - nphi;  // > 0 when the window wraps
+  return w;
+}
+
+// Tests every hit of the window (cell offsets off of the event and layer)
+// against the prediction; the hits with chi2 < cut become children (ranking
+// key: nf1 hits, chi2 sum + chi2, parent slot) in the candidate's ascending
+// child list lst[0..cnt) of at most max_cands.  BATCH: hits loaded in batches
+// of 8, so that their latencies overlap (near-tangent windows can hold
+// thousands of hits).
+template <bool BATCH>
+__device__ __forceinline__ void scan_window(const FindParams& P, const unsigned* off, const Window& w,
+                                            const Align4& al, const float (&p)[6], const Frame& f, int nf1,
+                                            float chi2, int slot, unsigned long long* lst, int& cnt,
+                                            unsigned& c_chi2) {
+  const int nphi = P.g.n_phi, N = P.g.max_cands;
+  const float cut = P.g.chi2_cut;
+  const bool wrap = w.b2 > 0;
 #pragma unroll 1
-  for (int it = 0; it < 3; ++it) {
-    const int hi = hoff + P.sh[it * ns + seed];
-    const int l = P.hlayer[hi];
-    if (it != 0) {
-      float q[6], J[6][6], cosa = 1.f;
-      const int pr = prop_jacobian<float>(p, g.radius[l], g.kb, INFINITY, q, J, &cosa);
-      if (pr != 1) {
-        flag |= 1u;
-        break;
-      }
-      if (cosa < FIND_CAREFUL_COS) {
-        flag |= 2u;
-        break;
-      }
-      transport<float>(J, C);
+  for (int e = w.e0; e <= w.e1; e += 2) {
+    // Offsets of up to two eta rows (each one or two phi ranges), all loaded
+    // before any is used.
+    const bool two = e + 1 <= w.e1;
+    const unsigned* rA = off + (size_t)e * nphi;
+    const unsigned* rB = rA + nphi;
+    unsigned o0 = rA[w.b0], o1 = rA[w.b1];
+    unsigned o2 = wrap ? rA[0] : 0u, o3 = wrap ? rA[w.b2] : 0u;
+    unsigned o4 = two ? rB[w.b0] : 0u, o5 = two ? rB[w.b1] : 0u;
+    unsigned o6 = (two && wrap) ? rB[0] : 0u, o7 = (two && wrap) ? rB[w.b2] : 0u;
+#pragma unroll 1
+    for (int part = 0; part < 4; ++part) {
+      const unsigned i0 = o0, i1 = o1;
+      o0 = o2; o1 = o3; o2 = o4; o3 = o5; o4 = o6; o5 = o7;
+      // chi2 of one hit; the compatible ones enter the sorted list
+      auto consider = [&](const float4& h) {
+        float mx, my, mz;
+        corrected_hit(al, h.x, h.y, h.z, mx, my, mz);
+        float r0, r1;
+        c_chi2++;
+        if (!residual<float>(p, f, mx, my, mz, r0, r1)) return;
+        const float c2 = chi2_of<float>(f, r0, r1);
+        if (!(c2 < cut)) return;
+        const unsigned long long key = make_key(nf1, chi2 + c2, slot, 0, __float_as_int(h.w));
+        int pos;
+        if (cnt < N) pos = cnt++;
+        else if (key < lst[N - 1]) pos = N - 1;
+        else return;
+        while (pos > 0 && lst[pos - 1] > key) { lst[pos] = lst[pos - 1]; --pos; }
+        lst[pos] = key;
+      };
+      if constexpr (BATCH) {
+        constexpr int B = 8;
+#pragma unroll 1
+        for (unsigned i = i0; i < i1; i += B) {
+          float4 hh[B];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) p[k] = q[k];
+          for (int k = 0; k < B; ++k)
+            if (i + k < i1) hh[k] = P.hb[i + k];
+#pragma unroll
+          for (int k = 0; k < B; ++k)
+            if (i + k < i1) consider(hh[k]);
+        }
+      } else {
+#pragma unroll 1
+        for (unsigned i = i0; i < i1; ++i) consider(P.hb[i]);
+      }
     }
-    float mx, my, mz;
-    corrected_hit(P.align[l], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
-    Frame f;
-    make_frame<float>(p, C, g.vr, g.vz, f);
-    float r0, r1;
-    if (!residual<float>(p, f, mx, my, mz, r0, r1)) {
-      flag |= 1u;
-      break;
-    }
-    chi2 += chi2_of<float>(f, r0, r1);
-    kf_update<float>(p, C, f, r0, r1);
-    add_ms<float>(p, C, g.x0[l]);
   }
+}
+
+// Seed fit and first layer, one thread per seed of [s_begin, s_end).
+// Seed fit: at the first seed hit the update of the prior, then for the
+// second and third hit propagation, transport and update, with the
+// scattering of each layer after its update.  First layer after the seed
+// (the seed's single candidate): what the group loop does on a layer for one
+// live candidate — propagation, window search and its children (hit children
+// and the hole child, top max_cands by ranking key).  Outputs: sfit [28][ns]
+// the state the children are taken from (the prediction on the first layer,
+// or the unchanged state of a carried candidate) and the seed's chi2 sum;
+// skeys [max_cands][ns] the children in ascending key order; sflag bit 1 a
+// crossing closer to tangent than FIND_CAREFUL_COS (the main pass lists the
+// seed for the careful pass without searching it), bit 2 the candidate is
+// carried unchanged (no crossing, a far-side seed hit, or a stop), bits 3-7
+// the number of children; sfit row 28 the first layer's counts (bits 0-29
+// chi2 evaluations, bit 30 a candidate-layer step, bit 31 a prediction
+// without positive definite S), which the main pass adds to its counters
+// (so that they are dropped with the rest if it gives the seed up later).
+constexpr int SEED_THREADS = 128;
+__global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
+  __shared__ unsigned long long s_lst[SEED_THREADS][KF_MAX_CANDS];
+  const int seed = P.s_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned c_steps = 0, c_chi2 = 0, c_npd = 0;
+  if (seed < P.s_end) {
+    const DevGeom& g = P.g;
+    const size_t ns = (size_t)P.ns;
+    const int N = g.max_cands;
+    const int ev = P.seed_event[seed];
+    const int hoff = P.hit_off[ev];
+    float p[6], C[21];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) P.sfit[k * ns + seed] = p[k];
+    for (int k = 0; k < 6; ++k) p[k] = P.sp[k * ns + seed];
 #pragma unroll
-  for (int k = 0; k < 21; ++k) P.sfit[(6 + k) * ns + seed] = C[k];
-  P.sfit[27 * ns + seed] = chi2;
-  P.sflag[seed] = (unsigned char)flag;
+    for (int k = 0; k < 21; ++k) C[k] = P.sc[k * ns + seed];
+    float chi2 = 0.f;
+    bool finished = false, near = false;
+    int l = 0;
+#pragma unroll 1
+    for (int it = 0; it < 3; ++it) {
+      const int hi = hoff + P.sh[it * ns + seed];
+      l = P.hlayer[hi];
+      if (finished || near) continue;  // (l still walks to the third seed hit's layer)
+      if (it != 0) {
+        float q[6], J[6][6], cosa = 1.f;
+        const int pr = prop_jacobian<float>(p, g.radius[l], g.kb, INFINITY, q, J, &cosa);
+        if (pr != 1) {
+          finished = true;
+          continue;
+        }
+        if (cosa < FIND_CAREFUL_COS) {
+          near = true;
+          continue;
+        }
+        transport<float>(J, C);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] = q[k];
+      }
+      float mx, my, mz;
+      corrected_hit(P.align[l], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+      Frame f;
+      make_frame<float>(p, C, g.vr, g.vz, f);
+      float r0, r1;
+      if (!residual<float>(p, f, mx, my, mz, r0, r1)) {
+        finished = true;
+        continue;
+      }
+      chi2 += chi2_of<float>(f, r0, r1);
+      kf_update<float>(p, C, f, r0, r1);
+      add_ms<float>(p, C, g.x0[l]);
+    }
+    // first layer after the seed
+    unsigned long long* lst = s_lst[threadIdx.x];
+    int cnt = 0;
+    bool carried = true;
+    const int L = g.n_layers, l1 = l + 1;
+    if (!near && l1 < L) {
+      unsigned long long tail = make_key(3, chi2, 0, 1, 0);
+      if (!finished) {
+        float bp[6], bC[21];  // state before the layer, kept for a stop
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bp[k] = p[k];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) bC[k] = C[k];
+        const float R = g.radius[l1];
+        float q[6], J[6][6], cosa = 1.f;
+        const int pr = prop_jacobian<float>(p, R, g.kb, g.z_max, q, J, &cosa);
+        if (pr == 1 && cosa < FIND_CAREFUL_COS) {
+          near = true;
+        } else if (pr == 1) {
+          transport<float>(J, C);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) p[k] = q[k];
+          carried = false;
+          c_steps++;
+          Frame f;
+          make_frame<float>(p, C, g.vr, g.vz, f);
+          const bool spd = f.s00 > 0.f && f.si00 > 0.f && f.si11 > 0.f;
+          if (!spd) c_npd++;
+          const Align4 al = P.align[l1];
+          const Window w = window_of(P, l1, R, p, f, spd, al);
+          const unsigned* off = P.bin_off + ((size_t)ev * L + l1) * ((size_t)g.n_eta * g.n_phi);
+          scan_window<false>(P, off, w, al, p, f, 4, chi2, 0, lst, cnt, c_chi2);
+          if (g.max_holes > 0) {
+            // hole child
+          } else if (cnt == 0) {  // no compatible hit and no hole allowed: stops unchanged
+            tail = make_key(3, chi2, 0, 1, 0);
+            carried = true;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) p[k] = bp[k];
+#pragma unroll
+            for (int k = 0; k < 21; ++k) C[k] = bC[k];
+          } else {
+            tail = KEY_EMPTY;
+          }
+        }
+      }
+      if (!near && tail != KEY_EMPTY) {
+        // the hole (or carried) child joins the hit children; the best N stay
+        int pos;
+        if (cnt < N) pos = cnt++;
+        else if (tail < lst[N - 1]) pos = N - 1;
+        else pos = -1;
+        if (pos >= 0) {
+          while (pos > 0 && lst[pos - 1] > tail) { lst[pos] = lst[pos - 1]; --pos; }
+          lst[pos] = tail;
+        }
+      }
+    }
+    if (near) {
+      cnt = 0;
+      c_steps = c_chi2 = c_npd = 0;  // the careful pass redoes and counts the seed
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) P.sfit[k * ns + seed] = p[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P.sfit[(6 + k) * ns + seed] = C[k];
+    P.sfit[27 * ns + seed] = chi2;
+    P.sfit[28 * ns + seed] = __uint_as_float(min(c_chi2, (1u << 30) - 1u) | (c_steps << 30) | (c_npd << 31));
+    for (int k = 0; k < cnt; ++k) P.skeys[k * ns + seed] = lst[k];
+    P.sflag[seed] = (unsigned char)((near ? 2u : 0u) | (carried ? 4u : 0u) | ((unsigned)cnt << 3));
+  }
 }
 
 template <int G, int CAP, bool CAREFUL>
@@ -268,6 +455,10 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     // counters of this task (dropped for a seed given up)
     unsigned c_steps = 0, c_updates = 0, c_chi2 = 0, c_seeds = 0, c_holes = 0, c_careful = 0, c_npd = 0;
     bool near = false, given_up = false;
+    // main pass: the first layer's children, found by the seed kernel (this
+    // lane's child and whether their parent was carried or propagated)
+    unsigned long long first_key = KEY_EMPTY;
+    int first_cls = 0;
     int ev = 0, hoff = 0;
     float p[6], C[21];
     float chi2 = 0.f;
@@ -289,15 +480,16 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + seed];
 #pragma unroll
         for (int k = 0; k < 21; ++k) C[k] = P.sc[(size_t)k * P.ns + seed];
-      } else {  // the fitted seed
+      } else {  // the fitted seed and its first layer
 #pragma unroll
         for (int k = 0; k < 6; ++k) p[k] = P.sfit[(size_t)k * P.ns + seed];
 #pragma unroll
         for (int k = 0; k < 21; ++k) C[k] = P.sfit[(size_t)(6 + k) * P.ns + seed];
         chi2 = P.sfit[(size_t)27 * P.ns + seed];
         const unsigned flag = P.sflag[seed];
-        finished = (flag & 1u) != 0;
         if (flag & 2u) given_up = true;
+        first_cls = (flag & 4u) ? 1 : 2;
+        if (gl < (int)(flag >> 3)) first_key = P.skeys[(size_t)gl * P.ns + seed];
       }
       if (gl == 0) c_seeds++;
     } else {
@@ -321,7 +513,9 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       int cnt = 0;
       bool dbl = false;  // careful pass: the prediction of this layer is kept in double
       unsigned long long tail = KEY_EMPTY;
-      if (active && occ) {
+      // main pass: the first layer after the seed was searched by the seed kernel
+      const bool pre = !CAREFUL && it == 3;
+      if (active && occ && !pre) {
         if (finished) {
           cls = 1;
           tail = make_key(nfound, chi2, gl, 1, 0);
@@ -376,85 +570,9 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
               const bool spd = f.s00 > 0.f && f.si00 > 0.f && f.si11 > 0.f;
               if (!spd) c_npd++;
               const Align4 al = P.align[l];
-              // Window containing the ellipse chi2 < cut: |r_rphi| < sqrt(cut S00)
-              // with r_rphi = R_hit sin(dphi) on the near half, |r_z| < sqrt(cut S11).
-              const float w1 = sqrtf(g.chi2_cut * f.s00);
-              const float w2 = sqrtf(g.chi2_cut * f.s11);
-              // asin(x) for the usual small x by x + x^3/6 + 3x^5/40 (truncation
-              // below 3e-9 relative for x < 0.05, far inside the padding)
-              const float xr = w1 / R;
-              float dphi = (xr >= 1.f) ? 0.5f * PI_F
-                           : (xr < 0.05f ? xr * fmaf(xr * xr, fmaf(xr * xr, 0.075f, 1.f / 6.f), 1.f) : asinf(xr));
-              dphi = fminf(dphi, 0.5f * PI_F) * (1.f + WIN_REL) + WIN_PHI_ABS;
-              const float phic = atan2f(p[1], p[0]) + al.dphi;
-              const int nphi = g.n_phi, neta = g.n_eta;
-              const int u0 = phi_bin_raw(phic - dphi, g.phi_scale);
-              const int u1 = phi_bin_raw(phic + dphi, g.phi_scale);
-              int span = u1 - u0 + 1, b0;
-              if (span >= nphi) { span = nphi; b0 = 0; } else { b0 = wrap_bin(u0, nphi); }
-              const float zc = p[2] + al.az;
-              const float wz = w2 * (1.f + WIN_REL) + WIN_Z_ABS;
-              const float* edges = P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1);
-              const unsigned char* lut = P.eta_lut + (size_t)l * ETA_LUT;
-              const int e0 = eta_bin(zc - wz, neta, g.z_max, g.eta_lut_scale, lut, edges);
-              const int e1 = spd ? eta_bin(zc + wz, neta, g.z_max, g.eta_lut_scale, lut, edges) : e0 - 1;
-              const unsigned* off = P.bin_off + ((size_t)ev * L + l) * ((size_t)neta * nphi);
-              const int nf1 = nfound + 1;
-              const int b1 = min(b0 + span, nphi);
-              const int b2 = b0 + span - nphi;  // > 0 when the window wraps
-              const bool wrap = b2 > 0;
-#pragma unroll 1
-              for (int e = e0; e <= e1; e += 2) {
-                // Offsets of up to two eta rows (each one or two phi ranges),
-                // all loaded before any is used.
-                const bool two = e + 1 <= e1;
-                const unsigned* rA = off + (size_t)e * nphi;
-                const unsigned* rB = rA + nphi;
-                unsigned o0 = rA[b0], o1 = rA[b1];
-                unsigned o2 = wrap ? rA[0] : 0u, o3 = wrap ? rA[b2] : 0u;
-                unsigned o4 = two ? rB[b0] : 0u, o5 = two ? rB[b1] : 0u;
-                unsigned o6 = (two && wrap) ? rB[0] : 0u, o7 = (two && wrap) ? rB[b2] : 0u;
-#pragma unroll 1
-                for (int part = 0; part < 4; ++part) {
-                  const unsigned i0 = o0, i1 = o1;
-                  o0 = o2; o1 = o3; o2 = o4; o3 = o5; o4 = o6; o5 = o7;
-                  // chi2 of one hit; the compatible ones enter the sorted list
-                  auto consider = [&](const float4& h) {
-                    float mx, my, mz;
-                    corrected_hit(al, h.x, h.y, h.z, mx, my, mz);
-                    float r0, r1;
-                    c_chi2++;
-                    if (!residual<float>(p, f, mx, my, mz, r0, r1)) return;
-                    const float c2 = chi2_of<float>(f, r0, r1);
-                    if (!(c2 < g.chi2_cut)) return;
-                    const unsigned long long key = make_key(nf1, chi2 + c2, gl, 0, __float_as_int(h.w));
-                    int pos;
-                    if (cnt < N) pos = cnt++;
-                    else if (key < lst[N - 1]) pos = N - 1;
-                    else return;
-                    while (pos > 0 && lst[pos - 1] > key) { lst[pos] = lst[pos - 1]; --pos; }
-                    lst[pos] = key;
-                  };
-                  if constexpr (CAREFUL) {
-                    // near-tangent windows can hold thousands of hits: loads in
-                    // batches of 8, so that their latencies overlap
-                    constexpr int B = 8;
-#pragma unroll 1
-                    for (unsigned i = i0; i < i1; i += B) {
-                      float4 hh[B];
-#pragma unroll
-                      for (int k = 0; k < B; ++k)
-                        if (i + k < i1) hh[k] = P.hb[i + k];
-#pragma unroll
-                      for (int k = 0; k < B; ++k)
-                        if (i + k < i1) consider(hh[k]);
-                    }
-                  } else {
-#pragma unroll 1
-                    for (unsigned i = i0; i < i1; ++i) consider(P.hb[i]);
-                  }
-                }
-              }
+              const Window w = window_of(P, l, R, p, f, spd, al);
+              const unsigned* off = P.bin_off + ((size_t)ev * L + l) * ((size_t)g.n_eta * g.n_phi);
+              scan_window<CAREFUL>(P, off, w, al, p, f, nfound + 1, chi2, gl, lst, cnt, c_chi2);
               if (nholes < g.max_holes) {
                 tail = make_key(nfound, chi2, gl, 1, 0);
               } else if (cnt == 0) {
@@ -486,7 +604,14 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
           n_iter = min(n_iter, it + 1);
         }
       }
-      if (__any_sync(0xffffffffu, active && !in_seed)) {
+      if (pre) {
+        // the children of the seed's candidate, in rank order, one per lane;
+        // every lane holds their parent's state already
+        mine = lane_used ? first_key : KEY_EMPTY;
+        par = 0;
+        p_holes = 0;
+        p_cls = first_cls;
+      } else if (__any_sync(0xffffffffu, active && !in_seed)) {
         // Rank of each child = its position in its own sorted list + the
         // number of smaller keys in the other lists of the group (keys are
         // unique); the children of rank < N go to the slots of their rank.
@@ -609,6 +734,14 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       __syncwarp();
     }
 
+    if constexpr (!CAREFUL) {
+      if (has_seed && gl == 0) {  // the first layer's counts, from the seed kernel
+        const unsigned c = __float_as_uint(P.sfit[(size_t)28 * P.ns + seed]);
+        c_chi2 += c & ((1u << 30) - 1u);
+        c_steps += (c >> 30) & 1u;
+        c_npd += c >> 31;
+      }
+    }
     if (given_up) {
       if (has_seed && gl == 0) {
         P.tangent_list[atomicAdd(P.queue + 2, 1u)] = seed;
@@ -797,7 +930,7 @@ cudaError_t launch_find_main(const FindParams& P, int lanes, int regcap, int thr
                              cudaStream_t st) {
   if (P.s_end <= P.s_begin) return cudaSuccess;
   const int n = P.s_end - P.s_begin;
-  k_seed_fit<<<(n + 127) / 128, 128, 0, st>>>(P);
+  k_seed_fit<<<(n + SEED_THREADS - 1) / SEED_THREADS, SEED_THREADS, 0, st>>>(P);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   KF_FIND_DISPATCH(launch_main_g, P, threads, grid_cap, st)

@@ -56,8 +56,11 @@ struct FindParams {
   unsigned* queue;           // [3] work counters of the main and careful passes and the
                              // number of listed seeds (zeroed before the launch)
   int* tangent_list;         // [ns] seeds the main pass left to the careful pass
-  float* sfit;               // [28][ns] fitted seeds (p, C, chi2 sum), written by the seed fit
-  unsigned char* sflag;      // [ns] seed-fit flags (bit 0 finished, bit 1 near-tangent crossing)
+  float* sfit;               // [29][ns] seed kernel: the state the first layer's children come
+                             // from (p, C), the seed's chi2 sum, the first layer's counts
+  unsigned long long* skeys; // [max_cands][ns] seed kernel: the first layer's children (keys)
+  unsigned char* sflag;      // [ns] seed kernel: bit 1 near-tangent crossing, bit 2 carried,
+                             // bits 3-7 number of children
   unsigned long long* counters;  // [8], see kf_get_counters
   int persistent;
 };
