@@ -60,6 +60,11 @@ DUP_CFG = dict(seed_clean=1, seed_deta=0.01, seed_dphi=0.01, seed_dpt=0.2, seed_
 # conflict count and state (37 B; neighbours come from L2); k_sc_resolve reads
 # order and state twice, writes the new order entry and keep flag (15 B).
 CLEAN_BYTES_PER_SEED = 68 + 37 + 15
+# DRAM traffic (read + write) of the three seed-cleaning kernels per 100-event
+# batch, scaled by events from an ncu capture on 20 of its events (17.57 MB;
+# ncu flushes the caches before each kernel, so this is the cold-cache figure).
+# Set to None whenever those kernels change until they are captured again.
+CLEAN_TRAFFIC_BYTES = 17.57e6 * 5
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -428,7 +433,9 @@ def main():
                "gpu_launches": td.graph_kernel_count() * args.steps,
                "roofline_seed_clean": {"bound": "hbm", "achieved": clean_gbs, "peak": hbm_peak[0],
                                        "unit": "GB/s", "frac": clean_gbs / hbm_peak[0], "peak_source": hbm_peak[1],
-                                       "bytes_per_seed": CLEAN_BYTES_PER_SEED, "traffic": None}}
+                                       "bytes_per_seed": CLEAN_BYTES_PER_SEED,
+                                       "traffic": (CLEAN_TRAFFIC_BYTES if CLEAN_TRAFFIC_BYTES is not None
+                                                   and args.config == "c4" and not args.events else None)}}
         td.close()
         dup["tracks_kept_without"] = int(t.get_tracks(stream=stream)["keep"].sum())
 
