@@ -52,7 +52,8 @@ def _find_and_compare(b, e=0, tracker=None, seeds=None, **cfg):
     trk = t.get_tracks()
     a, bnd = b.seed_off[e], b.seed_off[e + 1]
     lo, hi = (0, bnd - a) if seeds is None else seeds
-    ref = oracle.find_event(b, e, seeds=(lo, hi), max_cands=cfg.get("max_cands"))
+    ref = oracle.find_event(b, e, seeds=(lo, hi), max_cands=cfg.get("max_cands"),
+                            max_holes=cfg.get("max_holes", 3))
     gh = trk["hits"][a + lo:a + hi]
     mism = [i for i in range(hi - lo) if not np.array_equal(gh[i], ref["hits"][i])]
     kinds = {}
@@ -95,6 +96,25 @@ def test_find_candidate_counts(cands):
     trk, ref, mism, kinds, unexplained = _find_and_compare(b, max_cands=cands)
     assert len(mism) <= max(1, 0.005 * b.n_seeds)
     assert not unexplained, unexplained
+
+
+@pytest.mark.parametrize("holes", [0, 1])
+def test_find_hole_limits(holes):
+    """Fewer holes allowed: with none, a candidate without a compatible hit
+    stops unchanged — also on the first layer after the seed, which the
+    one-thread-per-seed kernel searches."""
+    b = make_batch("c1", tracks=400)
+    # every fifth track's hit on the first layer after its seed moved 5 cm
+    # along z (out of its window): those candidates find no compatible hit there
+    th = b.track_hits[0]
+    moved = th[::5, 3]
+    b.z[b.hit_off[0] + moved[moved >= 0]] += 5.0
+    trk, ref, mism, kinds, unexplained = _find_and_compare(b, max_holes=holes)
+    assert len(mism) <= max(1, 0.005 * b.n_seeds)
+    assert not unexplained, unexplained
+    if holes == 0:  # some tracks stop at the first layer after the seed
+        assert (ref["n_found"] == 3).sum() > 10
+        assert np.array_equal(trk["n_found"] == 3, ref["n_found"] == 3)
 
 
 @pytest.mark.parametrize("lanes,threads,persistent,regcap", [
