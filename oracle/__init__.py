@@ -34,7 +34,8 @@ def build(force: bool = False) -> str:
 class Detector(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int), ("radius", ctypes.c_double * 64),
                 ("x0", ctypes.c_double * 64), ("z_max", ctypes.c_double), ("bz", ctypes.c_double),
-                ("sigma_rphi", ctypes.c_double), ("sigma_z", ctypes.c_double)]
+                ("sigma_rphi", ctypes.c_double), ("sigma_z", ctypes.c_double),
+                ("n_z", ctypes.c_int), ("x0_map", ctypes.c_void_p)]
 
 
 class Config(ctypes.Structure):
@@ -56,6 +57,8 @@ def lib():
             L.orc_transport.argtypes = [_P, _P, _P]
             L.orc_update.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P]
             L.orc_highland.argtypes = [_P, ctypes.c_double]
+            L.orc_x0_at.argtypes = [_P, ctypes.c_int, ctypes.c_double]
+            L.orc_x0_at.restype = ctypes.c_double
             L.orc_highland.restype = ctypes.c_double
             L.orc_add_ms.argtypes = [_P, _P, ctypes.c_double]
             L.orc_fit.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_long, _P, _P, ctypes.c_int,
@@ -95,6 +98,11 @@ def make_detector(det) -> Detector:
     d.bz = float(np.float32(det.bz))
     d.sigma_rphi = float(np.float32(det.sigma_rphi))
     d.sigma_z = float(np.float32(det.sigma_z))
+    m = getattr(det, "x0_map", None)
+    if m is not None:  # float32-rounded like every other input; kept alive by the structure
+        d._map = np.ascontiguousarray(np.asarray(m, np.float32).astype(np.float64).reshape(det.n_layers, -1))
+        d.n_z = d._map.shape[1]
+        d.x0_map = d._map.ctypes.data
     return d
 
 
@@ -143,6 +151,12 @@ def update(p, C, m, vr, vz):
 def highland(p, x0):
     p = _c(p, np.float64)
     return lib().orc_highland(_ptr(p), x0)
+
+
+def x0_at(det, layer: int, z: float) -> float:
+    """Thickness of a layer at z: the detector's material map, else its x0."""
+    d = make_detector(det)
+    return lib().orc_x0_at(ctypes.byref(d), int(layer), float(z))
 
 
 def add_ms(p, C, x0):

@@ -137,6 +137,8 @@ struct Det {
   double bz;
   double sigma_rphi;
   double sigma_z;
+  int n_z;               // material map nodes per layer (0: the per-layer x0)
+  const double* x0_map;  // [n_layers][n_z] thickness at z_k = -z_max + k 2 z_max/(n_z - 1)
 };
 
 struct Cfg {
@@ -377,7 +379,7 @@ void kf_update(T p[6], T C[6][6], const Meas<T>& m) {
 // position: Highland width theta0 = 0.0136/(beta p) sqrt(t) (1 + 0.038 ln t),
 // t = x0 / |sin(theta) cos(phi - phi_p)|, p = pT/sin(theta), pion mass for beta.
 template <class T>
-T highland(const T p[6], double x0) {
+T highland(const T p[6], T x0) {
   T st = sin(p[5]);
   T pm = 1.0 / (fabs(p[3]) * st);
   T beta = pm / sqrt(pm * pm + MPION * MPION);
@@ -387,13 +389,33 @@ T highland(const T p[6], double x0) {
 }
 
 template <class T>
-void add_ms(const T p[6], T C[6][6], double x0) {
-  if (val(p[3]) == 0.0 || x0 <= 0.0) return;
+void add_ms(const T p[6], T C[6][6], T x0) {
+  if (val(p[3]) == 0.0 || val(x0) <= 0.0) return;
   T th0 = highland(p, x0);
   T st = sin(p[5]);
   T v = th0 * th0;
   C[4][4] += v / (st * st);
   C[5][5] += v;
+}
+
+// Thickness of layer L (radiation lengths at normal incidence) at z: the
+// per-layer value, or with a material map (the detector's two-dimensional
+// material description, Sec. 3: radiation lengths indexed in r and z, here
+// per barrel layer and z node) linear between the nodes and constant beyond
+// the ends.  The node is chosen from the value of z; the interpolation
+// weight carries its derivative.
+template <class T>
+T x0_at(const Det& det, int L, const T& z) {
+  if (det.n_z < 2) return T(det.x0[L]);
+  const double h = 2.0 * det.z_max / (det.n_z - 1);
+  const double* m = det.x0_map + (size_t)L * det.n_z;
+  const double u = (val(z) + det.z_max) / h;
+  if (u <= 0.0) return T(m[0]);
+  if (u >= det.n_z - 1) return T(m[det.n_z - 1]);
+  int k = (int)std::floor(u);
+  if (k > det.n_z - 2) k = det.n_z - 2;
+  const T f = (z + det.z_max) / h - (double)k;
+  return m[k] + f * (m[k + 1] - m[k]);
 }
 
 // Alignment correction of a raw hit on layer L: rotate by -a_rphi/R_L about z,
@@ -436,7 +458,7 @@ int fit_track(const Det& det, const T p0[6], const double C0[6][6], int n, const
     chi2 += ms.chi2;
     if (chi2_each) chi2_each[k] = ms.chi2;
     kf_update(p, C, ms);
-    if (k + 1 < n || ms_after_last) add_ms(p, C, det.x0[L]);
+    if (k + 1 < n || ms_after_last) add_ms(p, C, x0_at(det, L, p[2]));
   }
   return 0;
 }
@@ -602,7 +624,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
       } else {
         c.n_holes += 1;
       }
-      add_ms(c.p, c.C, det.x0[Lyr]);
+      add_ms(c.p, c.C, x0_at(det, Lyr, c.p[2]));
       ++cnt.ms;
       next.push_back(c);
     }
@@ -671,6 +693,8 @@ struct orc_detector {
   double bz;
   double sigma_rphi;
   double sigma_z;
+  int n_z;               // material map nodes per layer (0: none)
+  const double* x0_map;  // [n_layers][n_z]
 };
 
 struct orc_config {
@@ -687,6 +711,8 @@ static Det to_det(const orc_detector* d) {
   o.bz = d->bz;
   o.sigma_rphi = d->sigma_rphi;
   o.sigma_z = d->sigma_z;
+  o.n_z = d->x0_map ? d->n_z : 0;
+  o.x0_map = d->x0_map;
   return o;
 }
 
@@ -745,6 +771,9 @@ int orc_update(const double* p, const double* C, const double* m, double vr, dou
 }
 
 double orc_highland(const double* p, double x0) { return highland<double>(p, x0); }
+
+// Thickness of layer L at z (see x0_at).
+double orc_x0_at(const orc_detector* dptr, int L, double z) { return x0_at(to_det(dptr), L, z); }
 
 void orc_add_ms(const double* p, double* C, double x0) {
   double Cm[6][6];
@@ -929,7 +958,7 @@ int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, con
       kf_update(p, C, ms);
       *n_found += 1;
     }
-    add_ms(p, C, det.x0[l]);
+    add_ms(p, C, x0_at(det, l, p[2]));
   }
   *chi2sum = chi2;
   return 0;

@@ -47,6 +47,9 @@ class Detector:
     bz: float = 3.8
     sigma_rphi: float = 0.01
     sigma_z: float = 0.1
+    # optional material map [n_layers][n_z]: thickness at z nodes spread evenly
+    # over [-z_max, z_max] (the simulation itself uses x0)
+    x0_map: object = None
 
     @property
     def n_layers(self) -> int:

@@ -7,6 +7,7 @@ differences, forward-mode automatic differentiation, the normal equations of
 least squares, positive semi-definiteness, pull widths against generator truth,
 brute-force search and brute-force duplicate removal.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -332,10 +333,20 @@ def test_dedup_greedy_order_small_case():
     assert list(oracle.dedup(hits, n, chi2, brute=True)) == [1, 0, 0, 1]
 
 
-def test_dual_gradient_against_finite_differences():
+def _material_map(det, n_z=9, seed=11):
+    """A strongly varying map: thickness 0.005-0.06 X0 at n_z z nodes per layer."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.005, 0.06, size=(det.n_layers, n_z)).astype(np.float32)
+
+
+@pytest.mark.parametrize("with_map", [False, True])
+def test_dual_gradient_against_finite_differences(with_map):
     """d(sum chi2)/d(alignment, hits, seed parameters) by dual numbers ==
-    central finite differences of the fit (FP64)."""
+    central finite differences of the fit (FP64); with a material map the
+    scattering thickness also depends on the state's z."""
     b = make_batch("c3", tracks=40)
+    if with_map:
+        b.det = dataclasses.replace(b.det, x0_map=_material_map(b.det))
     L = b.det.n_layers
     x, y, z, lay = b.event_hits(0)
     prm, cov, sh = b.event_seeds(0)
@@ -583,3 +594,32 @@ def test_dedup_kinematic_index_equals_brute_force():
             for c in range(a + 1, len(kept)):
                 over = len(sets[a] & sets[c]) > 0.5 * min(len(sets[a]), len(sets[c]))
                 assert not (over and _np_close(kin[kept[a]], kin[kept[c]], *cuts))
+
+
+# ------------------------------------------------------------- material map
+
+def test_material_map_interpolation():
+    """Thickness at z: linear between the nodes, constant beyond the ends
+    (against numpy's interpolation); without a map, the per-layer value."""
+    b = make_batch("c1", tracks=10)
+    det = dataclasses.replace(b.det, x0_map=_material_map(b.det))
+    nodes = np.linspace(-det.z_max, det.z_max, 9)
+    rng = np.random.default_rng(5)
+    for layer in (0, 7, 16):
+        for z in np.concatenate([rng.uniform(-1.3 * det.z_max, 1.3 * det.z_max, 50), nodes]):
+            want = np.interp(z, nodes, det.x0_map[layer].astype(np.float64))
+            assert abs(oracle.x0_at(det, layer, z) - want) < 1e-12
+        assert oracle.x0_at(b.det, layer, 33.0) == float(np.float32(b.det.x0[layer]))
+
+
+def test_material_map_constant_equals_per_layer():
+    """A map holding each layer's x0 at every node gives the per-layer fit and
+    finding (the interpolation of equal nodes is that value)."""
+    b = make_batch("c1", tracks=300)
+    flat = np.repeat(np.asarray(b.det.x0, np.float32)[:, None], 5, axis=1)
+    r0 = oracle.find_event(b, 0)
+    b.det = dataclasses.replace(b.det, x0_map=flat)
+    r1 = oracle.find_event(b, 0)
+    assert np.array_equal(r0["hits"], r1["hits"])
+    assert np.allclose(r0["chi2"], r1["chi2"], rtol=1e-12, atol=0)
+    assert np.allclose(r0["p"], r1["p"], rtol=1e-12, atol=1e-14)
