@@ -137,6 +137,18 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
 int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* params,
                   const float* cov, const int* seed_hits, int device_ptrs, void* stream);
 
+/* Material map (the r-z material description of Sec. 3, per barrel layer):
+ * x0_map float [n_layers][n_z], the thickness in radiation lengths at normal
+ * incidence at n_z z nodes spread evenly over [-z_max, z_max]; between nodes
+ * the thickness is linear in z, beyond the ends constant, and the scattering
+ * of a layer uses it at the state's z.  n_z = 0 (x0_map may be NULL) returns
+ * to the per-layer x0 of the detector.  2 <= n_z <= KF_MAX_MATERIAL_NODES;
+ * host values must be finite and >= 0 (device arrays are not checked).  A
+ * captured graph keeps the material it was captured with: this call drops the
+ * graph (capture again).  Errors: KF_ERR_ARG. */
+#define KF_MAX_MATERIAL_NODES 4096
+int kf_set_material(kf_ctx* ctx, int n_z, const float* x0_map, int device_ptrs, void* stream);
+
 /* Layer alignment offsets float [n_layers][2] = (a_rphi, a_z) in cm.  A hit
  * on layer L is used after rotating it by -a_rphi/R_L about z and shifting
  * z by -a_z.  Zero after kf_create. */

@@ -37,6 +37,7 @@ from ._lib import (  # noqa: F401
     kf_load_seeds,
     kf_remove_duplicates,
     kf_set_alignment,
+    kf_set_material,
     kf_set_stage_timing,
     kf_sync,
 )
@@ -101,6 +102,10 @@ class Tracker:
 
     def set_alignment(self, offsets, stream=None):
         kf_set_alignment(self.ctx, offsets, stream)
+
+    def set_material(self, x0_map=None, stream=None):
+        """Thickness per layer at z nodes [n_layers][n_z] (None: per-layer x0)."""
+        kf_set_material(self.ctx, x0_map, stream)
 
     def find_tracks(self, stream=None):
         kf_find_tracks(self.ctx, stream)

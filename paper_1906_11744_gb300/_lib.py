@@ -29,6 +29,7 @@ KF_FIT_SKIPPED = 1
 KF_NOALLOC_MAX_TRACKS = 16384
 KF_NOALLOC_MAX_HITS = 262144
 KF_SEED_MAX_DETA = 1.0
+KF_MAX_MATERIAL_NODES = 4096
 
 
 class kf_detector(ctypes.Structure):
@@ -60,6 +61,7 @@ _SIGS = {
     "kf_load_hits": ([_P, _I, _P, _P, _P, _P, _P, _I, _P], _I),
     "kf_load_seeds": ([_P, _I, _P, _P, _P, _P, _I, _P], _I),
     "kf_set_alignment": ([_P, _P, _I, _P], _I),
+    "kf_set_material": ([_P, _I, _P, _I, _P], _I),
     "kf_find_tracks": ([_P, _P], _I),
     "kf_remove_duplicates": ([_P, _P], _I),
     "kf_fit_tracks": ([_P, _I, _P, _P, _I, _I, _P], _I),
@@ -183,6 +185,16 @@ def kf_load_seeds(ctx, ev_offsets, params, cov, seed_hits, stream=None):
 def kf_set_alignment(ctx, offsets, stream=None):
     po, ko, fo = _arg(offsets, np.float32)
     _check(ctx, load().kf_set_alignment(ctx, po, _flag(fo), _stream(stream)), "kf_set_alignment")
+
+
+def kf_set_material(ctx, x0_map=None, stream=None):
+    """x0_map [n_layers][n_z] (None: back to the per-layer x0)."""
+    if x0_map is None:
+        _check(ctx, load().kf_set_material(ctx, 0, None, 0, _stream(stream)), "kf_set_material")
+        return
+    n_z = int(x0_map.shape[1])
+    pm, km, fm = _arg(x0_map, np.float32)
+    _check(ctx, load().kf_set_material(ctx, n_z, pm, _flag(fm), _stream(stream)), "kf_set_material")
 
 
 def kf_find_tracks(ctx, stream=None):

@@ -152,12 +152,14 @@ __device__ __forceinline__ void jac_vjp(const T (&p)[6], T s, T kb, const T (&Jb
   v[5] += kfma(sthb, cth, -cotb);
 }
 
-// v += b44 dq44/dp + b55 dq55/dp for the scattering variances of ms_terms:
+// v += b44 dq44/dp + b55 dq55/dp for the scattering variances of add_ms:
 // with L = log theta0, dL = (beta^2 - 2)(d|q/pT|/|q/pT| + dsin/sin)
 //   + (1/2 + 0.038/(1 + 0.038 log t)) dlog t,  t = x0/|sin theta cos(phi - phi_p)|,
 // phi_p the position angle; dq55 = 2 q55 dL, dq44 = q44 (2 dL - 2 dsin/sin).
+// The thickness x0 may depend on z (material map): dlog t gains
+// (dx0/dz)/x0 dz.
 template <class T>
-__device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T b44, T b55, T (&v)[6]) {
+__device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T dx0dz, T b44, T b55, T (&v)[6]) {
   if (p[3] == T(0) || x0 <= T(0)) return;
   T sth, cth, sph, cph;
   ksincos(p[5], &sth, &cth);
@@ -182,6 +184,8 @@ __device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T b44, T b55, T (&
   v[4] += wc;
   v[0] = kfma(wc * p[1], ir * ir, v[0]);
   v[1] = kfma(-wc * p[0], ir * ir, v[1]);
+  // a material map: the thickness depends on z, d(log t)/dz = (dx0/dz)/x0
+  v[2] = kfma(W * bt, dx0dz / x0, v[2]);
 }
 
 template <class S>
@@ -222,7 +226,7 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
   S r0, r1;
   if (!residual<S>(p, f, h.mx, h.my, h.mz, r0, r1)) return KF_FIT_FAR_SIDE;
   kf_update<S>(p, C, f, r0, r1);
-  if (!last) add_ms<S>(p, C, (S)g.x0[h.L]);
+  if (!last) add_ms<S>(p, C, x0_at<S>(g, h.L, p[2]));
   return KF_FIT_OK;
 }
 
@@ -270,7 +274,11 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   S pbu[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) pbu[i] = pb[i];
-  if (!last) ms_vjp<S>(pu, (S)g.x0[h.L], Cb[4][4], Cb[5][5], pbu);
+  if (!last) {
+    S dx0dz;
+    const S x0 = x0_at<S>(g, h.L, pu[2], &dx0dz);
+    ms_vjp<S>(pu, x0, dx0dz, Cb[4][4], Cb[5][5], pbu);
+  }
   // ---- reverse: update and chi2 (chi2 adjoint 1)
   const S w0 = [&] { S a = S(0); for (int i = 0; i < 6; ++i) a = kfma(U[i][0], pbu[i], a); return a; }();
   const S w1 = [&] { S a = S(0); for (int i = 0; i < 6; ++i) a = kfma(U[i][1], pbu[i], a); return a; }();

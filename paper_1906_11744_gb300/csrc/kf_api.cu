@@ -38,7 +38,7 @@ struct kf_ctx {
   DevBuf hb, bin_cnt, bin_key, bin_rank, scan_tmp, bin_grouped, bin_gtab;
   // finding
   DevBuf out_hits, out_n, out_chi2, out_p, out_C, keep, queue, counters, status, tangent, seed_order, check;
-  DevBuf sfit, sflag, skeys;
+  DevBuf sfit, sflag, skeys, x0map;
   // duplicate removal scratch (the conflict lists also serve seed cleaning)
   DevBuf dd_hit_cnt, dd_owners, dd_conf, dd_nconf, dd_state, dd_scan_tmp;
   // seed cleaning
@@ -317,7 +317,7 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
                     &ctx->clean_order, &ctx->kept_cnt, &ctx->sc_list, &ctx->sc_list_cnt, &ctx->sfit,
-                    &ctx->sflag, &ctx->skeys};
+                    &ctx->sflag, &ctx->skeys, &ctx->x0map};
   for (DevBuf* b : bufs) release(*b);
   delete ctx;
   return KF_OK;
@@ -465,6 +465,34 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   }
   ctx->n_seeds = n;
   ctx->n_seed_events = n_events;
+  return KF_OK;
+}
+
+int kf_set_material(kf_ctx* ctx, int n_z, const float* x0_map, int device_ptrs, void* stream) {
+  if (!ctx) return KF_ERR_ARG;
+  if (n_z == 0) {
+    ctx->g.x0map = nullptr;
+    ctx->g.n_z = 0;
+    ctx->g.z_node_inv = 0.f;
+  } else {
+    if (n_z < 2 || n_z > KF_MAX_MATERIAL_NODES || !x0_map)
+      return fail(ctx, KF_ERR_ARG, "kf_set_material: 2 <= n_z <= KF_MAX_MATERIAL_NODES and a map are required");
+    const size_t n = (size_t)ctx->g.n_layers * n_z;
+    if (!device_ptrs)
+      for (size_t i = 0; i < n; ++i)
+        if (!(x0_map[i] >= 0.f) || !std::isfinite(x0_map[i]))
+          return fail(ctx, KF_ERR_ARG, "kf_set_material: thickness must be finite and >= 0");
+    cudaStream_t st = S(stream);
+    CK(grow(ctx->x0map, sizeof(float) * n));
+    CK(put(ctx->x0map.p, x0_map, sizeof(float) * n, device_ptrs, st));
+    if (!device_ptrs) CK(cudaStreamSynchronize(st));
+    ctx->g.x0map = ptr<float>(ctx->x0map);
+    ctx->g.n_z = n_z;
+    ctx->g.z_node_inv = (float)(n_z - 1) / (2.f * ctx->g.z_max);
+  }
+  // the graph's kernels hold the old geometry
+  if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
+  if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
   return KF_OK;
 }
 

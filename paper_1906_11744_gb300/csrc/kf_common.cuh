@@ -41,6 +41,11 @@ struct DevGeom {
   float radius[KF_MAX_LAYERS];
   float x0[KF_MAX_LAYERS];
   float eta_max[KF_MAX_LAYERS];  // asinh(z_max / R): half-range of the eta grid
+  // Material map (null: the per-layer x0): thickness [n_layers][n_z] at z
+  // nodes spread evenly over [-z_max, z_max]; z_node_inv = (n_z - 1)/(2 z_max).
+  const float* x0map;
+  int n_z;
+  float z_node_inv;
 };
 
 // Per-layer alignment: (cos a, sin a) of the correction rotation a = -a_rphi/R,
@@ -429,6 +434,28 @@ __device__ __forceinline__ void ms_terms(const T (&p)[6], T x0, T& q44, T& q55) 
   const T th0 = kdiv(T(0.0136), beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
   q55 = th0 * th0;
   q44 = kdiv(q55, sth * sth);
+}
+
+// Thickness of layer l (radiation lengths at normal incidence) at z: the
+// per-layer value, or linear between the material-map nodes and constant
+// beyond the ends (the detector's r-z material description, Sec. 3).  slope,
+// if given, receives d(thickness)/dz.
+template <class T>
+__device__ __forceinline__ T x0_at(const DevGeom& g, int l, T z, T* slope = nullptr) {
+  if (!g.x0map) {
+    if (slope) *slope = T(0);
+    return (T)g.x0[l];
+  }
+  const float* m = g.x0map + (size_t)l * g.n_z;
+  const T u = (z + (T)g.z_max) * (T)g.z_node_inv;
+  if (!(u > T(0)) || u >= T(g.n_z - 1)) {  // beyond an end (or not a number): the end node
+    if (slope) *slope = T(0);
+    return (T)m[u >= T(g.n_z - 1) ? g.n_z - 1 : 0];
+  }
+  const int k = min((int)u, g.n_z - 2);
+  const T d = (T)m[k + 1] - (T)m[k];
+  if (slope) *slope = d * (T)g.z_node_inv;
+  return kfma(u - T(k), d, (T)m[k]);
 }
 
 template <class T>

@@ -120,7 +120,8 @@ __device__ __noinline__ Frame careful_frame(const double* dst, float vr, float v
 // update), in double; the result rounded to out[0..26].  Returns false for a
 // hit on the far half (no update, no scattering); *dchi2 = the hit's chi2.
 __device__ __noinline__ bool careful_child(const double* in, float* out, float mx, float my, float mz, bool upd,
-                                           bool ms, float x0, float vr, float vz, float* dchi2) {
+                                           bool ms, const DevGeom& g, int l, float* dchi2) {
+  const float vr = g.vr, vz = g.vz;
   double p[6], C[21];
   for (int k = 0; k < 6; ++k) p[k] = in[k];
   for (int k = 0; k < 21; ++k) C[k] = in[6 + k];
@@ -138,7 +139,7 @@ __device__ __noinline__ bool careful_child(const double* in, float* out, float m
       ms = false;
     }
   }
-  if (ms) add_ms<double>(p, C, (double)x0);
+  if (ms) add_ms<double>(p, C, x0_at<double>(g, l, p[2]));
   for (int k = 0; k < 6; ++k) out[k] = (float)p[k];
   for (int k = 0; k < 21; ++k) out[6 + k] = (float)C[k];
   return ok;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
       }
       chi2 += chi2_of<float>(f, r0, r1);
       kf_update<float>(p, C, f, r0, r1);
-      add_ms<float>(p, C, g.x0[l]);
+      add_ms<float>(p, C, x0_at<float>(g, l, p[2]));
     }
     // first layer after the seed
     unsigned long long* lst = s_lst[threadIdx.x];
@@ -699,7 +700,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
           float* st = reinterpret_cast<float*>(lst);
           float dchi2 = 0.f;
           const double* in = dst_warp + (in_seed ? lane : base + par) * 27;
-          if (careful_child(in, st, mx, my, mz, do_update, do_ms, g.x0[l], g.vr, g.vz, &dchi2)) {
+          if (careful_child(in, st, mx, my, mz, do_update, do_ms, g, l, &dchi2)) {
             if (do_update) {
               if (in_seed) chi2 += dchi2;
               if (!in_seed) c_updates++;
@@ -729,7 +730,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             finished = true;  // far-side seed hit: the seed fit stops here
           }
         }
-        if (do_ms) add_ms<float>(p, C, g.x0[l]);
+        if (do_ms) add_ms<float>(p, C, x0_at<float>(g, l, p[2]));
       }
       __syncwarp();
     }

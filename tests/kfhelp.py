@@ -30,6 +30,8 @@ def tracker_for(batch, device=None, **cfg):
         t.load_hits(batch.hit_off, tt(batch.x), tt(batch.y), tt(batch.z), tt(batch.layer))
         t.load_seeds(batch.seed_off, tt(batch.params), tt(batch.cov), tt(batch.seed_hits))
     t.set_alignment(batch.align)
+    if getattr(d, "x0_map", None) is not None:
+        t.set_material(np.asarray(d.x0_map, np.float32))
     return t
 
 
