@@ -440,8 +440,9 @@ def main():
         dup["tracks_kept_without"] = int(t.get_tracks(stream=stream)["keep"].sum())
 
     # end to end through the C ABI with host buffers (pinned), host<->device copies inside.
-    # Two contexts in flight: while one step's graph runs, the next step's inputs are
-    # uploaded (and checked) through the other context; every step's uploads and result
+    # Two contexts: while one step's graph runs, the next step's inputs are uploaded (and
+    # checked) through the other context; its graph starts once this step's results are
+    # downloaded, so graphs never run at the same time.  Every step's uploads and result
     # downloads stay inside the timed region.  The serial form (one context) is kept beside.
     e2e = None
     if not args.no_e2e:
@@ -472,10 +473,13 @@ def main():
         t2.capture_graph(with_adjoint=True, stream=stream2)
         lanes = [(t, stream, host_outs()), (t2, stream2, host_outs())]
 
-        def issue(i):  # upload (synchronizes this context's stream only) and launch
+        def upload(i):  # synchronizes this context's stream only
             c, st, _ = lanes[i]
             c.load_hits(b.hit_off, h["x"], h["y"], h["z"], h["layer"], st)
             c.load_seeds(b.seed_off, h["params"], h["cov"], h["seed_hits"], st)
+
+        def launch(i):
+            c, st, _ = lanes[i]
             c.launch_graph(st)
 
         def collect(i):  # downloads into pinned host buffers (each call synchronizes)
@@ -486,14 +490,16 @@ def main():
 
         def run_serial(n):
             for _ in range(n):
-                issue(0)
+                upload(0)
+                launch(0)
                 collect(0)
 
         def run_pipelined(n):
-            issue(0)
+            upload(0)
             for k in range(n):
+                launch(k % 2)
                 if k + 1 < n:
-                    issue((k + 1) % 2)
+                    upload((k + 1) % 2)  # beside the graph just launched
                 collect(k % 2)
 
         run_serial(2)
@@ -514,7 +520,7 @@ def main():
             sum(v.numel() * v.element_size() for v in fouts.values()) + g_host.numel() * 4
         e2e = {"value": seeds_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * e2e_s / args.steps,
-               "form": "two contexts in flight: uploads of step k+1 overlap the graph of step k",
+               "form": "two contexts: uploads of step k+1 overlap the graph of step k; graphs run one at a time",
                "serial": {"value": seeds_all * args.steps / serial_s, "ms_per_step": 1e3 * serial_s / args.steps,
                           "form": "one context: upload, graph, download in sequence"}}
 
