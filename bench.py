@@ -269,6 +269,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dup", action="store_true", help="skip the duplicate-handling step")
+    ap.add_argument("--no-material", action="store_true", help="skip the material-map step")
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--ref-events", type=int, default=20)
@@ -439,6 +440,41 @@ def main():
         td.close()
         dup["tracks_kept_without"] = int(t.get_tracks(stream=stream)["keep"].sum())
 
+    # the same step with a material map (thickness per layer at 9 z nodes, 0.01-0.03 X0)
+    mat = None
+    if not args.no_material:
+        best = shape or ({} if tune is None else dict(
+            lanes_per_seed=int(tune[np.argmin(tune[:, 4])][0]), block_threads=int(tune[np.argmin(tune[:, 4])][1]),
+            persistent=int(tune[np.argmin(tune[:, 4])][2]), find_regcap=int(tune[np.argmin(tune[:, 4])][3])))
+        tm = tracker_for(b, **{"persistent": 1, "per_event": 0, **best})
+        tm.load_hits(b.hit_off, d_in["x"], d_in["y"], d_in["z"], d_in["layer"], stream)
+        tm.load_seeds(b.seed_off, d_in["params"], d_in["cov"], d_in["seed_hits"], stream)
+        tm.set_alignment(b.align, stream)
+        x0_map = np.random.default_rng(17).uniform(0.01, 0.03, size=(b.det.n_layers, 9)).astype(np.float32)
+        tm.set_material(x0_map, stream)
+        tm.set_stage_timing(True)
+        tm.capture_graph(with_adjoint=True, stream=stream)
+        for _ in range(args.warmup):
+            tm.launch_graph(stream)
+        stream.synchronize()
+        ma = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        mb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        mstage = {}
+        for k in range(args.steps):
+            flush_l2()
+            ma[k].record(stream)
+            tm.launch_graph(stream)
+            mb[k].record(stream)
+            for key, v in tm.stage_ms(stream).items():
+                mstage[key] = mstage.get(key, 0.0) + v
+        stream.synchronize()
+        mms = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in zip(ma, mb)), dev)
+        mat = {"value": seeds_all * args.steps / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / args.steps,
+               "map": "thickness per layer at 9 z nodes over [-z_max, z_max], uniform 0.01-0.03 X0, linear between",
+               "stage_ms": {k: v / args.steps for k, v in mstage.items()},
+               "gpu_launches": tm.graph_kernel_count() * args.steps}
+        tm.close()
+
     # end to end through the C ABI with host buffers (pinned), host<->device copies inside.
     # Two contexts: while one step's graph runs, the next step's inputs are uploaded (and
     # checked) through the other context; its graph starts once this step's results are
@@ -554,6 +590,7 @@ def main():
                "gpu_launches": n_kernels * args.steps,
                "roofline": roofline,
                "dup_handling": dup,
+               "material_map": mat,
                "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample",
                                                                             "single_core_value", "single_core_sample")},
                "clocks": clocks.summary()}
