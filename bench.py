@@ -46,8 +46,8 @@ F_FIT_HIT = 608   # re-fit: propagation + transport + update + scattering per hi
 
 # DRAM traffic (read + write) of one k_find launch on the 100-event batch,
 # scaled by events from an ncu capture of the same kernel on 20 of its events
-# (192.5 MB).  Set to None whenever k_find changes until it is captured again.
-FIND_TRAFFIC_BYTES = 192.52e6 * 5
+# (191.9 MB).  Set to None whenever k_find changes until it is captured again.
+FIND_TRAFFIC_BYTES = 191.92e6 * 5
 
 # Duplicate handling measured beside the headline step (Sec. 4.2): seed
 # cleaning on kinematics alone (eta, phi0 within 0.01, pT within 20%) and
