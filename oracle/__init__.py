@@ -35,7 +35,7 @@ class Detector(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int), ("radius", ctypes.c_double * 64),
                 ("x0", ctypes.c_double * 64), ("z_max", ctypes.c_double), ("bz", ctypes.c_double),
                 ("sigma_rphi", ctypes.c_double), ("sigma_z", ctypes.c_double),
-                ("n_z", ctypes.c_int), ("x0_map", ctypes.c_void_p)]
+                ("n_z", ctypes.c_int), ("x0_map", ctypes.c_void_p), ("eloss", ctypes.c_double * 64)]
 
 
 class Config(ctypes.Structure):
@@ -58,6 +58,7 @@ def lib():
             L.orc_update.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P]
             L.orc_highland.argtypes = [_P, ctypes.c_double]
             L.orc_x0_at.argtypes = [_P, ctypes.c_int, ctypes.c_double]
+            L.orc_eloss.argtypes = [_P, _P, ctypes.c_double]
             L.orc_x0_at.restype = ctypes.c_double
             L.orc_highland.restype = ctypes.c_double
             L.orc_add_ms.argtypes = [_P, _P, ctypes.c_double]
@@ -98,6 +99,8 @@ def make_detector(det) -> Detector:
     d.bz = float(np.float32(det.bz))
     d.sigma_rphi = float(np.float32(det.sigma_rphi))
     d.sigma_z = float(np.float32(det.sigma_z))
+    for i, e in enumerate(getattr(det, "eloss", ()) or ()):
+        d.eloss[i] = float(np.float32(e))
     m = getattr(det, "x0_map", None)
     if m is not None:  # float32-rounded like every other input; kept alive by the structure
         d._map = np.ascontiguousarray(np.asarray(m, np.float32).astype(np.float64).reshape(det.n_layers, -1))
@@ -151,6 +154,15 @@ def update(p, C, m, vr, vz):
 def highland(p, x0):
     p = _c(p, np.float64)
     return lib().orc_highland(_ptr(p), x0)
+
+
+def eloss(p, C, e):
+    """Mean ionization energy loss step of one state (e: the layer's loss at
+    normal incidence for beta -> 1, GeV): returns (p', C' [6][6])."""
+    p = _c(p, np.float64).copy()
+    C = _c(np.asarray(C, np.float64).reshape(36), np.float64).copy()
+    lib().orc_eloss(_ptr(p), _ptr(C), float(e))
+    return p, C.reshape(6, 6)
 
 
 def x0_at(det, layer: int, z: float) -> float:

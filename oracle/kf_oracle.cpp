@@ -139,6 +139,7 @@ struct Det {
   double sigma_z;
   int n_z;               // material map nodes per layer (0: the per-layer x0)
   const double* x0_map;  // [n_layers][n_z] thickness at z_k = -z_max + k 2 z_max/(n_z - 1)
+  double eloss[64];      // mean ionization loss per layer at normal incidence, beta -> 1 (GeV; 0: none)
 };
 
 struct Cfg {
@@ -418,6 +419,60 @@ T x0_at(const Det& det, int L, const T& z) {
   return m[k] + f * (m[k + 1] - m[k]);
 }
 
+// Mean ionization energy loss in a thin layer (the paper's material arrays
+// serve scattering and energy loss, Sec. 3), outward motion:
+//   dE = e f / beta^2,  f = 1/|sin(theta) cos(phi - phi_p)| (the scattering's path
+//   factor), e = the layer's loss at normal incidence for beta -> 1 (leading
+//   Bethe-Bloch dependence; logarithmic rise and density effect left out);
+//   E' = E - dE (dE at most (E - m)/2),  p' = sqrt(E'^2 - m^2),  q/pT' = q/pT p/p'.
+// The covariance follows the map: C' = F C F^T, F the identity but for the
+// q/pT row dk'/dp (written out below; pinned against finite differences).
+// Straggling is not modelled.
+template <class T>
+void add_eloss(T p[6], T C[6][6], double e) {
+  if (e <= 0.0 || val(p[3]) == 0.0) return;
+  const T st = sin(p[5]), ct = cos(p[5]);
+  const T pm = 1.0 / (fabs(p[3]) * st);
+  const T E = sqrt(pm * pm + MPION * MPION);
+  const T b2 = pm * pm / (E * E);
+  const T phip = atan2(p[1], p[0]);
+  const T cd = cos(p[4] - phip), sd = sin(p[4] - phip);
+  const T f = 1.0 / fabs(st * cd);
+  T dE = e * f / b2;
+  if (val(dE) > 0.5 * (val(E) - MPION)) dE = 0.5 * (E - MPION);
+  const T E1 = E - dE;
+  const T pm1 = sqrt(E1 * E1 - MPION * MPION);
+  const T k1 = p[3] * pm / pm1;
+  // d log p' = A d log p + B d log f (dE from the formula; a capped dE is
+  // treated the same way, a limit no test reaches)
+  const T A = E1 / (pm1 * pm1) * (E * b2 - 2.0 * dE * (b2 - 1.0));
+  const T B = -(E1 / (pm1 * pm1)) * dE;
+  const T r2 = p[0] * p[0] + p[1] * p[1];
+  const T tn = sd / cd;
+  T F3[6];
+  F3[0] = k1 * B * tn * (-p[1] / r2);
+  F3[1] = k1 * B * tn * (p[0] / r2);
+  F3[2] = T(0.0);
+  F3[3] = k1 * A / p[3];
+  F3[4] = -k1 * B * tn;
+  F3[5] = k1 * (ct / st) * (A + B - 1.0);
+  // C' = F C F^T with F = I except row 3
+  T c3[6];  // row 3 of F C
+  for (int j = 0; j < 6; ++j) {
+    T a = T(0.0);
+    for (int k = 0; k < 6; ++k) a = a + F3[k] * C[k][j];
+    c3[j] = a;
+  }
+  T c33 = T(0.0);
+  for (int k = 0; k < 6; ++k) c33 = c33 + c3[k] * F3[k];
+  for (int j = 0; j < 6; ++j) {
+    C[3][j] = c3[j];
+    C[j][3] = c3[j];
+  }
+  C[3][3] = c33;
+  p[3] = k1;
+}
+
 // Alignment correction of a raw hit on layer L: rotate by -a_rphi/R_L about z,
 // then z -= a_z.
 template <class T>
@@ -458,7 +513,10 @@ int fit_track(const Det& det, const T p0[6], const double C0[6][6], int n, const
     chi2 += ms.chi2;
     if (chi2_each) chi2_each[k] = ms.chi2;
     kf_update(p, C, ms);
-    if (k + 1 < n || ms_after_last) add_ms(p, C, x0_at(det, L, p[2]));
+    if (k + 1 < n || ms_after_last) {
+      add_ms(p, C, x0_at(det, L, p[2]));
+      add_eloss(p, C, det.eloss[L]);
+    }
   }
   return 0;
 }
@@ -625,6 +683,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
         c.n_holes += 1;
       }
       add_ms(c.p, c.C, x0_at(det, Lyr, c.p[2]));
+      add_eloss(c.p, c.C, det.eloss[Lyr]);
       ++cnt.ms;
       next.push_back(c);
     }
@@ -695,6 +754,7 @@ struct orc_detector {
   double sigma_z;
   int n_z;               // material map nodes per layer (0: none)
   const double* x0_map;  // [n_layers][n_z]
+  double eloss[64];      // mean ionization loss per layer (GeV; 0: none)
 };
 
 struct orc_config {
@@ -713,6 +773,7 @@ static Det to_det(const orc_detector* d) {
   o.sigma_z = d->sigma_z;
   o.n_z = d->x0_map ? d->n_z : 0;
   o.x0_map = d->x0_map;
+  for (int i = 0; i < 64; ++i) o.eloss[i] = d->eloss[i];
   return o;
 }
 
@@ -771,6 +832,14 @@ int orc_update(const double* p, const double* C, const double* m, double vr, dou
 }
 
 double orc_highland(const double* p, double x0) { return highland<double>(p, x0); }
+
+// Energy loss step on one state (see add_eloss): p [6] and C [36] in place.
+void orc_eloss(double* p, double* C, double e) {
+  double Cm[6][6];
+  for (int i = 0; i < 36; ++i) Cm[i / 6][i % 6] = C[i];
+  add_eloss(p, Cm, e);
+  for (int i = 0; i < 36; ++i) C[i] = Cm[i / 6][i % 6];
+}
 
 // Thickness of layer L at z (see x0_at).
 double orc_x0_at(const orc_detector* dptr, int L, double z) { return x0_at(to_det(dptr), L, z); }
@@ -959,6 +1028,7 @@ int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, con
       *n_found += 1;
     }
     add_ms(p, C, x0_at(det, l, p[2]));
+    add_eloss(p, C, det.eloss[l]);
   }
   *chi2sum = chi2;
   return 0;

@@ -50,6 +50,9 @@ class Detector:
     # optional material map [n_layers][n_z]: thickness at z nodes spread evenly
     # over [-z_max, z_max] (the simulation itself uses x0)
     x0_map: object = None
+    # optional mean ionization loss per layer at normal incidence for beta -> 1
+    # (GeV); the simulation itself has none
+    eloss: tuple = ()
 
     @property
     def n_layers(self) -> int:

@@ -339,14 +339,17 @@ def _material_map(det, n_z=9, seed=11):
     return rng.uniform(0.005, 0.06, size=(det.n_layers, n_z)).astype(np.float32)
 
 
-@pytest.mark.parametrize("with_map", [False, True])
-def test_dual_gradient_against_finite_differences(with_map):
+@pytest.mark.parametrize("with_map,with_eloss", [(False, False), (True, False), (True, True)])
+def test_dual_gradient_against_finite_differences(with_map, with_eloss):
     """d(sum chi2)/d(alignment, hits, seed parameters) by dual numbers ==
     central finite differences of the fit (FP64); with a material map the
-    scattering thickness also depends on the state's z."""
+    scattering thickness also depends on the state's z; with energy loss q/pT
+    changes after every layer."""
     b = make_batch("c3", tracks=40)
     if with_map:
         b.det = dataclasses.replace(b.det, x0_map=_material_map(b.det))
+    if with_eloss:
+        b.det = dataclasses.replace(b.det, eloss=(2e-4,) * b.det.n_layers)
     L = b.det.n_layers
     x, y, z, lay = b.event_hits(0)
     prm, cov, sh = b.event_seeds(0)
@@ -623,3 +626,62 @@ def test_material_map_constant_equals_per_layer():
     assert np.array_equal(r0["hits"], r1["hits"])
     assert np.allclose(r0["chi2"], r1["chi2"], rtol=1e-12, atol=0)
     assert np.allclose(r0["p"], r1["p"], rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------ energy loss
+
+MPI = 0.13957
+
+
+def _pmag(p):
+    return 1.0 / (abs(p[3]) * math.sin(p[5]))
+
+
+def test_eloss_momentum_change_and_path_factor():
+    """dE = beta dp to first order; the loss doubles at half the normal
+    component of the direction (cos(phi - phi_p) = 0.5) and grows as 1/beta^2
+    at low momentum; the charge is kept."""
+    e = 1e-6
+    for kap in (0.5, -2.0, 5.0):
+        p = np.array([40.0, 0.0, 3.0, kap, 0.0, math.pi / 2])
+        q, _ = oracle.eloss(p, np.eye(6), e)
+        pm, pm1 = _pmag(p), _pmag(q)
+        beta = pm / math.hypot(pm, MPI)
+        de = e / beta ** 2
+        assert abs((pm - pm1) - de / beta) < 1e-5 * de  # second order: m^2 beta dE / (2 p^3)
+        assert np.sign(q[3]) == np.sign(kap)
+        # oblique: cos(phi - phi_p) = 0.5 -> twice the path
+        p2 = p.copy(); p2[4] = math.pi / 3
+        q2, _ = oracle.eloss(p2, np.eye(6), e)
+        assert abs((pm - _pmag(q2)) / (pm - pm1) - 2.0) < 1e-5
+    # 1/beta^2: at p = 0.2 GeV the loss is (1 + m^2/p^2) times the beta -> 1 value
+    p = np.array([40.0, 0.0, 3.0, 5.0, 0.0, math.pi / 2])
+    q, _ = oracle.eloss(p, np.eye(6), e)
+    pm = _pmag(p)
+    dE = (math.hypot(pm, MPI) - math.hypot(_pmag(q), MPI))
+    assert abs(dE / e - (1 + MPI ** 2 / pm ** 2)) < 1e-5
+
+
+def test_eloss_jacobian_against_finite_differences():
+    """The covariance map C' = F C F^T with F = d p'/d p: the hand-written q/pT
+    row against central differences of the state map."""
+    rng = np.random.default_rng(4)
+    e = 3e-4
+    for _ in range(20):
+        p = np.array([rng.uniform(-50, 50), rng.uniform(-50, 50), rng.uniform(-30, 30),
+                      rng.choice([-1, 1]) * rng.uniform(0.1, 3.0), rng.uniform(-3, 3), rng.uniform(0.5, 2.6)])
+        phip = math.atan2(p[1], p[0])
+        if abs(math.cos(p[4] - phip)) < 0.2:
+            continue
+        F = np.zeros((6, 6))
+        for j in range(6):
+            h = 1e-6 * max(1.0, abs(p[j]))
+            a, b = p.copy(), p.copy()
+            a[j] += h
+            b[j] -= h
+            F[:, j] = (oracle.eloss(a, np.eye(6), e)[0] - oracle.eloss(b, np.eye(6), e)[0]) / (2 * h)
+        A = rng.normal(size=(6, 6))
+        C = A @ A.T
+        q, C1 = oracle.eloss(p, C, e)
+        want = F @ C @ F.T
+        assert np.abs(C1 - want).max() < 1e-6 * np.abs(want).max()
