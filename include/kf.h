@@ -126,6 +126,9 @@ int kf_destroy(kf_ctx* ctx);
  * x, y, z: float [n_hits] global positions (cm); layer: int [n_hits] in
  * [0, n_layers).  A hit is referred to by its index within its event
  * (0 .. ev_offsets[e+1]-ev_offsets[e]-1), in the order given here.
+ * Loading hits unloads the seeds (their hit indices refer to the previous
+ * hits): call kf_load_seeds again before finding, fitting, tuning or a graph
+ * replay, which return KF_ERR_STATE until then.
  * Errors: KF_ERR_ARG, KF_ERR_CAPACITY (an event above KF_MAX_EVENT_HITS). */
 int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* x,
                  const float* y, const float* z, const int* layer, int device_ptrs, void* stream);
@@ -203,8 +206,12 @@ int kf_get_fit(kf_ctx* ctx, float* params, float* cov, float* chi2, int* status,
 /* Capture find + duplicate removal + fit (+ the adjoint of the fit if
  * with_adjoint, its gradients kept in the context for kf_get_gradient) on
  * the stream into a CUDA graph owned by the context; kf_launch_graph replays
- * it.  stream must not be the legacy default stream.  Loads between launches
- * must not grow any buffer. */
+ * it.  stream must not be the legacy default stream.  The graph holds the
+ * buffer addresses, sizes and event offsets of the capture: loads between
+ * replays may change the values of hits and seeds, but kf_launch_graph
+ * returns KF_ERR_STATE (capture again) when a load since the capture changed
+ * a size or an event offset or moved a buffer, or when the seeds were not
+ * loaded again after the hits. */
 int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream);
 int kf_launch_graph(kf_ctx* ctx, void* stream);
 
@@ -261,15 +268,18 @@ const char* kf_last_error(const kf_ctx* ctx);
  * they synchronize the device, or a plugin held to another library's fixed
  * memory budget.  It needs no kf_ctx (creating one allocates).
  *
- * Same definition as kf_remove_duplicates.  Inputs and the output are device
- * pointers owned by the caller, read and written in stream order:
+ * Same definition as kf_remove_duplicates with the shared-hit criterion
+ * alone: the kinematic pre-cuts (dup_deta, dup_dphi, dup_dpt of kf_config)
+ * are not applied here.  Inputs and the output are device pointers owned by
+ * the caller, read and written in stream order:
  *   hits     int   [n_tracks][n_layers] event-local hit indices, -1 padded;
  *            every used index must lie in [0, n_hits);
  *   n_found  int   [n_tracks] hits per track (<= n_layers);
  *   chi2     float [n_tracks] chi2 sums (ordering key);
  *   keep     uint8 [n_tracks] output, 1 = kept;
  *   status   int   [1] output (may be NULL): 0, or a nonzero device-side
- *            status when a table of the kernel overflowed.
+ *            status when a table of the kernel overflowed; written by every
+ *            call that returns KF_OK, n_tracks = 0 included.
  * Scratch lives in a fixed static device array (about 4.2 MB, present on every
  * device that loads the library until the process exits).  The first call on a
  * device looks up that array's device address (with the device current); make

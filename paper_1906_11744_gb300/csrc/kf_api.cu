@@ -53,6 +53,12 @@ struct kf_ctx {
   DevBuf adj_align_acc, adj_align, adj_hits, adj_seed;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // What the captured graph baked in: the device address of every buffer and
+  // the loaded sizes and event offsets.  A replay after a load that moved a
+  // buffer or changed a size is refused.
+  std::vector<void*> graph_bufs;
+  std::vector<int> graph_hit_off, graph_seed_off;
+  int graph_n_seeds = -1;
   int stage_timing = 0;
   cudaEvent_t ev[12] = {};  // start/end of bin, find, dedup, fit, adjoint, seed cleaning
   // Side stream (highest priority) for the careful passes that run beside
@@ -298,16 +304,9 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   return KF_OK;
 }
 
-int kf_destroy(kf_ctx* ctx) {
-  if (!ctx) return KF_ERR_ARG;
-  for (cudaEvent_t& e : ctx->ev)
-    if (e) cudaEventDestroy(e);
-  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-  if (ctx->side) cudaStreamDestroy(ctx->side);
-  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
-  if (ctx->graph) cudaGraphDestroy(ctx->graph);
-  DevBuf* bufs[] = {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
+// Every device buffer of a context.
+static std::vector<DevBuf*> all_bufs(kf_ctx* ctx) {
+  return {&ctx->hx, &ctx->hy, &ctx->hz, &ctx->hlayer, &ctx->hit_off, &ctx->seed_off, &ctx->sp,
                     &ctx->sc, &ctx->sh, &ctx->seed_event, &ctx->align_raw, &ctx->align4, &ctx->eta_edges, &ctx->eta_lut, &ctx->hb,
                     &ctx->bin_cnt, &ctx->bin_key, &ctx->bin_rank, &ctx->scan_tmp, &ctx->bin_grouped, &ctx->bin_gtab, &ctx->out_hits,
                     &ctx->out_n, &ctx->out_chi2, &ctx->out_p, &ctx->out_C, &ctx->keep, &ctx->queue, &ctx->tangent, &ctx->seed_order, &ctx->check,
@@ -318,7 +317,18 @@ int kf_destroy(kf_ctx* ctx) {
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
                     &ctx->clean_order, &ctx->kept_cnt, &ctx->sc_list, &ctx->sc_list_cnt, &ctx->sfit,
                     &ctx->sflag, &ctx->skeys, &ctx->x0map};
-  for (DevBuf* b : bufs) release(*b);
+}
+
+int kf_destroy(kf_ctx* ctx) {
+  if (!ctx) return KF_ERR_ARG;
+  for (cudaEvent_t& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  for (DevBuf* b : all_bufs(ctx)) release(*b);
   delete ctx;
   return KF_OK;
 }
@@ -361,6 +371,9 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   CK(cudaMemcpyAsync(ctx->hit_off.p, ctx->hit_off_h.data(), sizeof(int) * (n_events + 1),
                      cudaMemcpyHostToDevice, st));
   ctx->found = ctx->deduped = ctx->fitted = false;
+  // Seed hit indices were checked against the previous hit offsets: the seeds
+  // must be loaded again before finding, fitting or tuning.
+  ctx->n_seed_events = -1;
   // Layer indices checked on the device (the caller's buffers are in use until
   // the synchronization below).
   int bad = 0;
@@ -992,6 +1005,11 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   if (e != cudaSuccess) return fail(ctx, KF_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
   ctx->graph = graph;
   CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, cudaGraphInstantiateFlagUseNodePriority));
+  ctx->graph_bufs.clear();
+  for (DevBuf* b : all_bufs(ctx)) ctx->graph_bufs.push_back(b->p);
+  ctx->graph_hit_off = ctx->hit_off_h;
+  ctx->graph_seed_off = ctx->seed_off_h;
+  ctx->graph_n_seeds = ctx->n_seeds;
   return KF_OK;
 }
 
@@ -1017,6 +1035,19 @@ int kf_get_gradient(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, i
 int kf_launch_graph(kf_ctx* ctx, void* stream) {
   if (!ctx) return KF_ERR_ARG;
   if (!ctx->exec) return fail(ctx, KF_ERR_STATE, "kf_launch_graph: capture a graph first");
+  if (ctx->n_seed_events != ctx->n_events || ctx->n_hits < 0)
+    return fail(ctx, KF_ERR_STATE, "kf_launch_graph: load hits and seeds first");
+  // The graph's kernels hold the buffer addresses, sizes and event offsets of
+  // the capture: a load that reallocated a buffer or changed a size would make
+  // them read freed memory or stale extents.
+  bool same = ctx->hit_off_h == ctx->graph_hit_off && ctx->seed_off_h == ctx->graph_seed_off &&
+              ctx->n_seeds == ctx->graph_n_seeds;
+  const std::vector<DevBuf*> bufs = all_bufs(ctx);
+  same = same && bufs.size() == ctx->graph_bufs.size();
+  for (size_t i = 0; same && i < bufs.size(); ++i) same = bufs[i]->p == ctx->graph_bufs[i];
+  if (!same)
+    return fail(ctx, KF_ERR_STATE,
+                "kf_launch_graph: a load since the capture changed the sizes or moved a buffer; capture again");
   CK(cudaGraphLaunch(ctx->exec, S(stream)));
   ctx->found = ctx->deduped = ctx->fitted = true;
   ctx->fit_source = KF_FIT_FOUND;

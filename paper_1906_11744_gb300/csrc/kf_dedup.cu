@@ -521,7 +521,11 @@ extern "C" int kf_remove_duplicates_noalloc(int n_tracks, int n_layers, int n_hi
   if (n_tracks < 0 || n_hits < 0 || n_layers < 1 || n_layers > KF_MAX_LAYERS || !(dup_shared_frac >= 0.f))
     return KF_ERR_ARG;
   if (n_tracks > KF_NOALLOC_MAX_TRACKS || n_hits > KF_NOALLOC_MAX_HITS) return KF_ERR_CAPACITY;
-  if (n_tracks == 0) return KF_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n_tracks == 0) {  // nothing to remove; the status still reads "no error"
+    if (status && cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return KF_ERR_CUDA;
+    return KF_OK;
+  }
   if (!hits || !n_found || !chi2 || !keep) return KF_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return KF_ERR_CUDA;
@@ -535,7 +539,6 @@ extern "C" int kf_remove_duplicates_noalloc(int n_tracks, int n_layers, int n_hi
     }
     base = na_ptr[dev];
   }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int* misc = reinterpret_cast<int*>(base + NA_BYTES - NA_MISC_BYTES);
   DedupParams D;
   D.out_hits = hits;

@@ -18,6 +18,8 @@ def tracker_for(batch, device=None, **cfg):
     from paper_1906_11744_gb300 import Tracker, make_config, make_detector
 
     d = batch.det
+    if any(getattr(d, "eloss", ()) or ()):
+        raise ValueError("the CUDA path does not apply energy loss; this detector sets it")
     det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z)
     c = dict(max_cands=batch.cfg["max_cands"])
     c.update(cfg)

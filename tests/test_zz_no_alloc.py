@@ -52,6 +52,22 @@ def test_noalloc_matches_context_entry_point_twice():
         assert trk["keep"].sum() < n  # the duplicate seeds were removed
 
 
+def test_noalloc_zero_tracks_clears_status():
+    """An event without tracks launches no kernel but still writes 0 to the
+    status word, so a caller never reads what an earlier call left there."""
+    import torch
+
+    from paper_1906_11744_gb300 import _lib
+    dev = torch.device("cuda:0")
+    status = torch.full((1,), -9, dtype=torch.int32, device=dev)
+    empty_i = torch.zeros((1,), dtype=torch.int32, device=dev)
+    rc = _lib.kf_remove_duplicates_noalloc(0, 17, 0, empty_i, empty_i, torch.zeros(1, device=dev), 0.5,
+                                           torch.zeros(1, dtype=torch.uint8, device=dev), status)
+    assert rc == _lib.KF_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+
 def test_noalloc_rejects_events_beyond_its_limits():
     from paper_1906_11744_gb300 import _lib
     lib = _lib.load()
