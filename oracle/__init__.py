@@ -69,7 +69,8 @@ def lib():
             L.orc_find_event.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                          ctypes.c_long, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
                                          _P, _P, _P, _P, _P, _P]
-            L.orc_replay.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_replay.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_select_children.argtypes = [ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int, _P]
             L.orc_dedup.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double]
@@ -333,5 +334,41 @@ def replay_path(batch, e: int, seed: int, hits_row, align=None):
     nf = np.zeros(1, np.int32)
     d = make_detector(det)
     st = lib().orc_replay(ctypes.byref(d), _ptr(x), _ptr(y), _ptr(z), _ptr(lay), _ptr(p0), _ptr(c0),
-                          _ptr(s3), _ptr(dec), _ptr(al), _ptr(chi2l), _ptr(tot), _ptr(nf))
+                          _ptr(s3), _ptr(dec), _ptr(al), _ptr(chi2l), _ptr(tot), _ptr(nf), None, None)
     return int(st), float(tot[0]), int(nf[0]), chi2l
+
+
+def replay_decisions(batch, e: int, seed: int, decisions, align=None):
+    """Replay a finding path given per layer: a hit index (update), -1 (hole)
+    or -2 (stop; the path ends).  Returns (status, chi2 sum, n_found,
+    per-layer chi2, final p [6], final C [21])."""
+    det = batch.det
+    x, y, z, lay = batch.event_hits(e)
+    prm, cov, sh = batch.event_seeds(e)
+    x, y, z = _c(x, np.float64), _c(y, np.float64), _c(z, np.float64)
+    lay = _c(lay, np.int32)
+    dec = _c(decisions, np.int32)
+    p0 = _c(prm[:, seed], np.float64)
+    c0 = _c(cov[:, seed], np.float64)
+    s3 = _c(sh[:, seed], np.int32)
+    al = _c(batch.align if align is None else align, np.float64)
+    chi2l = np.zeros(det.n_layers)
+    tot = np.zeros(1)
+    nf = np.zeros(1, np.int32)
+    pf = np.zeros(6)
+    cf = np.zeros(21)
+    d = make_detector(det)
+    st = lib().orc_replay(ctypes.byref(d), _ptr(x), _ptr(y), _ptr(z), _ptr(lay), _ptr(p0), _ptr(c0),
+                          _ptr(s3), _ptr(dec), _ptr(al), _ptr(chi2l), _ptr(tot), _ptr(nf), _ptr(pf), _ptr(cf))
+    return int(st), float(tot[0]), int(nf[0]), chi2l, pf, cf
+
+
+def select_children(n_found, chi2, parent, kind, hit, max_cands):
+    """The finding's selection step on hand-made children (kind 0 hit, 1 hole,
+    2 carried): indices of the kept children in rank order."""
+    n = len(n_found)
+    nf = _c(n_found, np.int32); c2 = _c(chi2, np.float64); pa = _c(parent, np.int32)
+    kd = _c(kind, np.int32); ht = _c(hit, np.int32)
+    out = np.zeros(max(n, 1), np.int32)
+    k = lib().orc_select_children(n, _ptr(nf), _ptr(c2), _ptr(pa), _ptr(kd), _ptr(ht), int(max_cands), _ptr(out))
+    return out[:k].tolist()

@@ -25,7 +25,10 @@
 //
 // Parity status: every function here is pinned by tests under tests/ (closed
 // forms, Runge-Kutta integration, finite differences, brute force, least
-// squares, pull widths).
+// squares, pull widths).  The finding's candidate selection (ranking key,
+// truncation to N, hole limit, stop and carry rules, chi2 cut) is pinned by
+// hand-made child lists and by a brute-force beam on tiny events that
+// recomputes every path through orc_replay.
 
 #include <algorithm>
 #include <cmath>
@@ -540,7 +543,7 @@ struct Child {
   int parent;
   int kind;
   int hit;
-  double hit_chi2;
+  int tag;  // not part of the key: carried through the selection unchanged
 };
 
 // Ranking key of the candidate score: more hits first, then lower chi2 sum,
@@ -551,6 +554,16 @@ bool child_less(const Child& a, const Child& b) {
   if (a.parent != b.parent) return a.parent < b.parent;
   if (a.kind != b.kind) return a.kind < b.kind;
   return a.hit < b.hit;
+}
+
+// The selection step of the finding: the children of all candidates of a
+// seed on one layer ranked by child_less, the best max_cands kept in rank
+// order (the new candidate slots).  Keys are unique: children of one parent
+// differ in kind or hit, children of different parents in parent rank.
+std::vector<Child> select_children(std::vector<Child> children, int max_cands) {
+  std::sort(children.begin(), children.end(), child_less);
+  if (children.size() > (size_t)max_cands) children.resize((size_t)max_cands);
+  return children;
 }
 
 struct LayerIndex {  // hits of one layer sorted by z (exact chi2 pre-selection)
@@ -609,7 +622,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
     for (size_t r = 0; r < cands.size(); ++r) {
       const Cand& c = cands[r];
       if (c.finished) {
-        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0.0});
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0});
         continue;
       }
       Cand& pc = predicted[r];
@@ -617,7 +630,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
       double J[6][6];
       ++cnt.prop_calls;
       if (!propagate(det.bz, c.p, R, pc.p, J) || std::fabs(pc.p[2]) > det.z_max) {
-        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0.0});
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0});
         continue;
       }
       transport(J, pc.C);
@@ -643,21 +656,21 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
         ++cnt.chi2_evals;
         if (!measure(pc.p, pc.C, m, vr, vz, ms)) continue;
         if (ms.chi2 < cfg.chi2_cut) {
-          children.push_back({c.n_found + 1, c.chi2 + ms.chi2, (int)r, KIND_HIT, hidx, ms.chi2});
+          children.push_back({c.n_found + 1, c.chi2 + ms.chi2, (int)r, KIND_HIT, hidx, 0});
           ++n_children;
         }
       }
       if (c.n_holes < cfg.max_holes) {
-        children.push_back({c.n_found, c.chi2, (int)r, KIND_HOLE, -1, 0.0});
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_HOLE, -1, 0});
         ++n_children;
       }
       if (n_children == 0) {  // no compatible hit and no hole left: the candidate stops
-        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0.0});
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0});
       }
     }
     cnt.children += (long long)children.size();
-    std::sort(children.begin(), children.end(), child_less);
-    const size_t keep = std::min(children.size(), (size_t)cfg.max_cands);
+    children = select_children(std::move(children), cfg.max_cands);
+    const size_t keep = children.size();
     std::vector<Cand> next;
     next.reserve(keep);
     for (size_t k = 0; k < keep; ++k) {
@@ -981,16 +994,31 @@ int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits,
   return 0;
 }
 
+// The selection step alone, for hand-made children (n of them, fields as in
+// Child; kind 0 hit, 1 hole, 2 carried): writes the indices of the kept
+// children in rank order to out_idx and returns how many were kept.
+int orc_select_children(int n, const int* n_found, const double* chi2, const int* parent, const int* kind,
+                        const int* hit, int max_cands, int* out_idx) {
+  std::vector<Child> ch(n);
+  for (int i = 0; i < n; ++i) {
+    ch[i] = Child{n_found[i], chi2[i], parent[i], kind[i], hit[i], i};
+  }
+  const std::vector<Child> kept = select_children(ch, max_cands);
+  for (size_t k = 0; k < kept.size(); ++k) out_idx[k] = kept[k].tag;
+  return (int)kept.size();
+}
+
 // Replay one candidate path of the finding: seed fit over the three seed
 // hits (scattering after the last), then for each layer from the one after
 // the third seed hit: decisions[l] = hit index (update), -1 (hole) or -2
 // (stop).  Scattering follows every update and every hole, as in finding.
-// chi2_layer[l] receives each hit's chi2.  Returns 0, or -1 when the
+// chi2_layer[l] receives each hit's chi2; p_out [6] and C_out [21] (may be
+// NULL) the state at the end of the path.  Returns 0, or -1 when the
 // propagation finds no crossing, -2 for a far-side hit.
 int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, const double* hz,
                const int* hlayer, const double* p0v, const double* C0v, const int* sh,
                const int* decisions, const double* align, double* chi2_layer, double* chi2sum,
-               int* n_found) {
+               int* n_found, double* p_out, double* C_out) {
   const Det det = to_det(dptr);
   const int L = det.n_layers;
   double al[64][2];
@@ -1031,6 +1059,11 @@ int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, con
     add_eloss(p, C, det.eloss[l]);
   }
   *chi2sum = chi2;
+  if (p_out)
+    for (int k = 0; k < 6; ++k) p_out[k] = p[k];
+  if (C_out)
+    for (int a = 0; a < 6; ++a)
+      for (int b = a; b < 6; ++b) C_out[sym_index(a, b)] = C[a][b];
   return 0;
 }
 
