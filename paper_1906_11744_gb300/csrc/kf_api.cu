@@ -247,11 +247,14 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
     g.radius[l] = det->radius[l];
     g.x0[l] = det->x0[l];
     g.eta_max[l] = asinhf(det->z_max / det->radius[l]);
+    g.eta_scale[l] = (float)cfg->n_eta_bins / (2.f * g.eta_max[l]);
+    g.r_inv[l] = 1.f / det->radius[l];
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = find_prepare(ctx->lanes, ctx->regcap, ctx->threads, ctx->g.n_layers, &ctx->blocks_per_sm);
+  if (e == cudaSuccess)
+    e = find_prepare(ctx->lanes, ctx->regcap, ctx->threads, ctx->g.n_layers, ctx->g.n_eta, &ctx->blocks_per_sm);
   if (e == cudaSuccess) e = grow(ctx->align4, sizeof(Align4) * KF_MAX_LAYERS);
   if (e == cudaSuccess) {
     // z edges of the eta bins per layer: edge_k = R sinh(-eta_max + k * 2 eta_max / n_eta)
@@ -1076,7 +1079,8 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
     for (int threads : thread_opts)
     for (int regcap = 0; regcap < 2; ++regcap) {
       int bps = 1;
-      if (find_prepare(lanes, regcap, threads, ctx->g.n_layers, &bps) != cudaSuccess || bps < 1) continue;
+      if (find_prepare(lanes, regcap, threads, ctx->g.n_layers, ctx->g.n_eta, &bps) != cudaSuccess || bps < 1)
+        continue;
       for (int pers = 0; pers < 2 && rc == KF_OK; ++pers) {
         ctx->lanes = lanes;
         ctx->threads = threads;
@@ -1122,7 +1126,7 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
   ctx->persistent = best_p;
   ctx->blocks_per_sm = best_b;
   ctx->regcap = best_rc;
-  CK(find_prepare(best_l, best_rc, best_t, ctx->g.n_layers, &ctx->blocks_per_sm));
+  CK(find_prepare(best_l, best_rc, best_t, ctx->g.n_layers, ctx->g.n_eta, &ctx->blocks_per_sm));
   if (n_results) *n_results = nr;
   if (rc != KF_OK) return rc;
   return KF_OK;

@@ -41,6 +41,8 @@ struct DevGeom {
   float radius[KF_MAX_LAYERS];
   float x0[KF_MAX_LAYERS];
   float eta_max[KF_MAX_LAYERS];  // asinh(z_max / R): half-range of the eta grid
+  float eta_scale[KF_MAX_LAYERS];  // n_eta / (2 eta_max): eta bins per unit of eta
+  float r_inv[KF_MAX_LAYERS];      // 1 / R
   // Material map (null: the per-layer x0): thickness [n_layers][n_z] at z
   // nodes spread evenly over [-z_max, z_max]; z_node_inv = (n_z - 1)/(2 z_max).
   const float* x0map;
@@ -170,6 +172,18 @@ __device__ __forceinline__ bool path_length(T x, T y, T h, T cf, T sf, T R, T& s
   const T D = kfma(A, A, E * den);
   if (D < T(0)) return false;
   const T sq = ksqrt(D);
+  // Outward crossing (the usual step to the next layer): inside the cylinder
+  // (E > 0), moving outward (b > 0, A = b h not zero) with den > 0, the root of
+  // the sign of h is
+  // tau = E / (A + sq) for h > 0 and E / (A - sq) for h < 0, and the other
+  // root has the opposite sign, so the general selection below would take
+  // exactly this one; its quotient, arctangent and arc length are the same
+  // operations as there.
+  if (E > T(0) && b > T(0) && den > T(0) && A != T(0)) {
+    const T psi = T(2) * katan(kdiv(E, h > T(0) ? A + sq : A - sq));
+    s = psi * kdiv(T(1), h);
+    return true;
+  }
   T n0, d0, n1, d1;
   if (A >= T(0)) {
     n0 = E; d0 = A + sq; n1 = -(A + sq); d1 = den;
@@ -211,12 +225,23 @@ __device__ __forceinline__ bool path_length(T x, T y, T h, T cf, T sf, T R, T& s
 }
 
 // C <- J C J^T using only the structural non-zeros of J (JS).  J entries with
-// JS == 2 must be set; others are ignored.
+// JS == 2 must be set; others are ignored.  Rows 3 and 5 of J are unit rows,
+// so (J C) has C's rows there and C' keeps C's (3,3), (3,5), (5,5).  The
+// other rows i are taken one at a time in the order 2, 0, 1, 4: T_i = J_i C,
+// then C'_ik = T_i . J_k for the rows k not yet done (k = i included) and
+// C'_i3 = T_i[3], C'_i5 = T_i[5] (the unit rows of J).  Only one row of J C is
+// live at a time, which keeps the register demand of the step low.
 template <class T>
 __device__ __forceinline__ void transport(const T (&J)[6][6], T (&C)[21]) {
-  T Tm[6][6];
+  constexpr int ORD[4] = {2, 0, 1, 4};
+  T out[21];
+  out[S6(3, 3)] = C[S6(3, 3)];
+  out[S6(3, 5)] = C[S6(3, 5)];
+  out[S6(5, 5)] = C[S6(5, 5)];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
+  for (int a = 0; a < 4; ++a) {
+    const int i = ORD[a];
+    T t[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       T acc = T(0);
@@ -229,28 +254,23 @@ __device__ __forceinline__ void transport(const T (&J)[6][6], T (&C)[21]) {
         else acc = first ? J[i][j] * c : kfma(J[i][j], c, acc);
         first = false;
       }
-      Tm[i][k] = acc;
+      t[k] = acc;
     }
-  }
-  T out[21];
+    out[S6(i, 3)] = t[3];
+    out[S6(i, 5)] = t[5];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-#pragma unroll
-    for (int j = i; j < 6; ++j) {
-      // (T J^T)_ij = T_i . J_j = T_j . J_i (symmetry): take the sparser J row.
-      const bool use_j = JNNZ(j) <= JNNZ(i);
-      const int tr = use_j ? i : j, jr = use_j ? j : i;
+    for (int b = a; b < 4; ++b) {
+      const int kr = ORD[b];
       T acc = T(0);
       bool first = true;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        if (JS(jr, k) == 0) continue;
-        const T t = Tm[tr][k];
-        if (JS(jr, k) == 1) acc = first ? t : acc + t;
-        else acc = first ? t * J[jr][k] : kfma(t, J[jr][k], acc);
+      for (int m = 0; m < 6; ++m) {
+        if (JS(kr, m) == 0) continue;
+        if (JS(kr, m) == 1) acc = first ? t[m] : acc + t[m];
+        else acc = first ? t[m] * J[kr][m] : kfma(t[m], J[kr][m], acc);
         first = false;
       }
-      out[S6(i, j)] = acc;
+      out[S6(i, kr)] = acc;
     }
   }
 #pragma unroll
@@ -499,6 +519,48 @@ __device__ __forceinline__ int eta_bin(float z, int n_eta, float z_max, float lu
   int b = lut[c];
   while (b > 0 && z < __ldg(edges + b)) --b;
   while (b < n_eta - 1 && z >= __ldg(edges + b + 1)) ++b;
+  return b;
+}
+
+// Square root of a non-negative x through the hardware reciprocal square
+// root (a few ulp; 0 for x <= 0): for window bounds, which are padded.
+__device__ __forceinline__ float sqrt_bound(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// atan2(y, x) for the centre of a search window: the quotient of the smaller
+// by the larger of |x|, |y| through the hardware reciprocal, atan(t) = t P(t^2)
+// on [0, 1] with a degree-6 polynomial in t^2 fitted to atan (weighted least
+// squares on Chebyshev nodes), then the octant.  Largest error about 1e-6 rad
+// (3.3e-7 from the polynomial in FP32, the rest from the quotient and the
+// octant offsets); window bounds carry an absolute padding well above it.
+__device__ __forceinline__ float atan2_window(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+  const float q = t * t;
+  float r = fmaf(q, 0.006811764f, -0.03360415f);
+  r = fmaf(q, r, 0.07962362f);
+  r = fmaf(q, r, -0.13233341f);
+  r = fmaf(q, r, 0.19807817f);
+  r = fmaf(q, r, -0.3331737f);
+  r = fmaf(q, r, 0.99999613f);
+  r *= t;
+  if (ay > ax) r = 1.57079633f - r;
+  if (x < 0.f) r = 3.14159265f - r;
+  return copysignf(r, y);
+}
+
+// The same eta bin with the layer's edges in shared memory and an arithmetic
+// first guess (eta = asinh(z/R) through the hardware logarithm; only a guess:
+// the edge comparisons make the result exact), so that a window costs no
+// global-memory lookup.
+__device__ __forceinline__ int eta_bin_smem(float z, float r_inv, float eta_max, float eta_scale, int n_eta,
+                                            const float* edges) {
+  const float x = z * r_inv, ax = fabsf(x);
+  const float eta = copysignf(__logf(ax + sqrt_bound(fmaf(ax, ax, 1.f))), x);
+  int b = (int)floorf((eta + eta_max) * eta_scale);
+  b = min(max(b, 0), n_eta - 1);
+  while (b > 0 && z < edges[b]) --b;
+  while (b < n_eta - 1 && z >= edges[b + 1]) ++b;
   return b;
 }
 

@@ -30,28 +30,38 @@ namespace kfg {
 namespace {
 
 constexpr int BACKUP_STRIDE = 28;  // 27 state floats, padded
-// Shared memory per warp: child lists [32 lanes][KF_MAX_CANDS + 1] u64; the
-// packed children of each group [32][KF_MAX_CANDS + 1] u64, which between the
-// propagation and the selection holds the state backup [32 lanes][28] float;
-// selected children [32] u64; history [32 lanes][n_layers] int.
-constexpr int LIST_STRIDE = KF_MAX_CANDS + 1;
-constexpr int SMEM_LIST = 32 * LIST_STRIDE * 8;
-constexpr int SMEM_GATHER = 32 * LIST_STRIDE * 8;
+// Shared memory per warp, for G lanes per seed: child lists [32 lanes][G + 1]
+// u64 (at most N <= G hit children and the hole or carried child; the careful
+// pass also keeps 27 floats of scratch there, so at least 14 entries); the
+// packed children of each group [32][G + 1] u64, which between the propagation
+// and the selection holds the state backup [32 lanes][28] float; selected
+// children [32] u64; history [32 lanes][n_layers] int.
+__host__ __device__ constexpr int list_stride(int G, bool careful) {
+  return (careful && G + 1 < 14) ? 14 : G + 1;
+}
+__host__ __device__ constexpr int smem_list(int G, bool careful) { return 32 * list_stride(G, careful) * 8; }
+__host__ __device__ constexpr int smem_gather(int G, bool careful) {
+  return smem_list(G, careful) > 32 * BACKUP_STRIDE * 4 ? smem_list(G, careful) : 32 * BACKUP_STRIDE * 4;
+}
 constexpr int SMEM_SLOT = 32 * 8;
-static_assert(32 * BACKUP_STRIDE * 4 <= SMEM_GATHER, "backup must fit the gather area");
-__host__ __device__ constexpr int smem_per_warp(int n_layers) {
-  return SMEM_LIST + SMEM_GATHER + SMEM_SLOT + ((32 * n_layers * 4 + 15) / 16) * 16;
+__host__ __device__ constexpr int smem_per_warp(int G, bool careful, int n_layers) {
+  return smem_list(G, careful) + smem_gather(G, careful) + SMEM_SLOT + ((32 * n_layers * 4 + 15) / 16) * 16;
 }
 // The careful pass adds each lane's double-precision prediction [32][27].
 constexpr int SMEM_DSTATE = 32 * 27 * 8;
-__host__ __device__ constexpr int smem_per_warp_k(int n_layers, bool careful) {
-  return smem_per_warp(n_layers) + (careful ? SMEM_DSTATE : 0);
+__host__ __device__ constexpr int smem_per_warp_k(int G, int n_layers, bool careful) {
+  return smem_per_warp(G, careful, n_layers) + (careful ? SMEM_DSTATE : 0);
+}
+// Shared memory per block ahead of the warps' areas: the z edges of the eta
+// bins of every layer [n_layers][n_eta + 1].
+__host__ __device__ constexpr int smem_edges(int n_layers, int n_eta) {
+  return ((n_layers * (n_eta + 1) * 4 + 15) / 16) * 16;
 }
 // Window padding: relative and absolute slack on the chi2-ellipse bounds that
 // covers the FP32 rounding of the window arithmetic and of the hit's own
 // angle and eta-bin computation.
 constexpr float WIN_REL = 1e-3f;
-constexpr float WIN_PHI_ABS = 1e-5f;  // rad
+constexpr float WIN_PHI_ABS = 1.5e-5f;  // rad (includes the error of atan2_window, about 1e-6)
 constexpr float WIN_Z_ABS = 1e-4f;    // cm
 // Crossings closer to tangent than this (cos of the angle between direction
 // and radial direction) are propagated in double: the FP32 error of the
@@ -158,18 +168,23 @@ __device__ __noinline__ bool careful_child(const double* in, float* out, float m
 struct Window {
   int e0, e1, b0, b1, b2;
 };
+// s_edges: the eta-bin edges of every layer in shared memory ([n_layers][n_eta
+// + 1]), or null for the global table and its first-guess lookup.
 __device__ __forceinline__ Window window_of(const FindParams& P, int l, float R, const float (&p)[6],
-                                            const Frame& f, bool spd, const Align4& al) {
+                                            const Frame& f, bool spd, const Align4& al,
+                                            const float* s_edges = nullptr) {
   const DevGeom& g = P.g;
-  const float w1 = sqrtf(g.chi2_cut * f.s00);
-  const float w2 = sqrtf(g.chi2_cut * f.s11);
+  // Bounds through hardware approximations (square root, quotient, window
+  // centre angle): their errors are a few ulp, far inside the padding.
+  const float w1 = sqrt_bound(g.chi2_cut * f.s00);
+  const float w2 = sqrt_bound(g.chi2_cut * f.s11);
   // asin(x) for the usual small x by x + x^3/6 + 3x^5/40 (truncation below
   // 3e-9 relative for x < 0.05, far inside the padding)
-  const float xr = w1 / R;
+  const float xr = w1 * g.r_inv[l];
   float dphi = (xr >= 1.f) ? 0.5f * PI_F
                : (xr < 0.05f ? xr * fmaf(xr * xr, fmaf(xr * xr, 0.075f, 1.f / 6.f), 1.f) : asinf(xr));
   dphi = fminf(dphi, 0.5f * PI_F) * (1.f + WIN_REL) + WIN_PHI_ABS;
-  const float phic = atan2f(p[1], p[0]) + al.dphi;
+  const float phic = atan2_window(p[1], p[0]) + al.dphi;
   const int nphi = g.n_phi, neta = g.n_eta;
   const int u0 = phi_bin_raw(phic - dphi, g.phi_scale);
   const int u1 = phi_bin_raw(phic + dphi, g.phi_scale);
@@ -177,11 +192,18 @@ __device__ __forceinline__ Window window_of(const FindParams& P, int l, float R,
   if (span >= nphi) { span = nphi; b0 = 0; } else { b0 = wrap_bin(u0, nphi); }
   const float zc = p[2] + al.az;
   const float wz = w2 * (1.f + WIN_REL) + WIN_Z_ABS;
-  const float* edges = P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1);
-  const unsigned char* lut = P.eta_lut + (size_t)l * ETA_LUT;
   Window w;
-  w.e0 = eta_bin(zc - wz, neta, g.z_max, g.eta_lut_scale, lut, edges);
-  w.e1 = spd ? eta_bin(zc + wz, neta, g.z_max, g.eta_lut_scale, lut, edges) : w.e0 - 1;
+  if (s_edges) {
+    const float* edges = s_edges + l * (neta + 1);
+    const float ri = g.r_inv[l], em = g.eta_max[l], es = g.eta_scale[l];
+    w.e0 = eta_bin_smem(zc - wz, ri, em, es, neta, edges);
+    w.e1 = spd ? eta_bin_smem(zc + wz, ri, em, es, neta, edges) : w.e0 - 1;
+  } else {
+    const float* edges = P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1);
+    const unsigned char* lut = P.eta_lut + (size_t)l * ETA_LUT;
+    w.e0 = eta_bin(zc - wz, neta, g.z_max, g.eta_lut_scale, lut, edges);
+    w.e1 = spd ? eta_bin(zc + wz, neta, g.z_max, g.eta_lut_scale, lut, edges) : w.e0 - 1;
+  }
   w.b0 = b0;
   w.b1 = min(b0 + span, nphi);
   w.b2 = b0 + span - nphi;  // > 0 when the window wraps
@@ -213,29 +235,29 @@ __device__ __forceinline__ void scan_window(const FindParams& P, const unsigned*
     unsigned o2 = wrap ? rA[0] : 0u, o3 = wrap ? rA[w.b2] : 0u;
     unsigned o4 = two ? rB[w.b0] : 0u, o5 = two ? rB[w.b1] : 0u;
     unsigned o6 = (two && wrap) ? rB[0] : 0u, o7 = (two && wrap) ? rB[w.b2] : 0u;
+    // chi2 of one hit; the compatible ones enter the sorted list
+    auto consider = [&](const float4& h) {
+      float mx, my, mz;
+      corrected_hit(al, h.x, h.y, h.z, mx, my, mz);
+      float r0, r1;
+      c_chi2++;
+      if (!residual<float>(p, f, mx, my, mz, r0, r1)) return;
+      const float c2 = chi2_of<float>(f, r0, r1);
+      if (!(c2 < cut)) return;
+      const unsigned long long key = make_key(nf1, chi2 + c2, slot, 0, __float_as_int(h.w));
+      int pos;
+      if (cnt < N) pos = cnt++;
+      else if (key < lst[N - 1]) pos = N - 1;
+      else return;
+      while (pos > 0 && lst[pos - 1] > key) { lst[pos] = lst[pos - 1]; --pos; }
+      lst[pos] = key;
+    };
+    if constexpr (BATCH) {
+      constexpr int B = 8;
 #pragma unroll 1
-    for (int part = 0; part < 4; ++part) {
-      const unsigned i0 = o0, i1 = o1;
-      o0 = o2; o1 = o3; o2 = o4; o3 = o5; o4 = o6; o5 = o7;
-      // chi2 of one hit; the compatible ones enter the sorted list
-      auto consider = [&](const float4& h) {
-        float mx, my, mz;
-        corrected_hit(al, h.x, h.y, h.z, mx, my, mz);
-        float r0, r1;
-        c_chi2++;
-        if (!residual<float>(p, f, mx, my, mz, r0, r1)) return;
-        const float c2 = chi2_of<float>(f, r0, r1);
-        if (!(c2 < cut)) return;
-        const unsigned long long key = make_key(nf1, chi2 + c2, slot, 0, __float_as_int(h.w));
-        int pos;
-        if (cnt < N) pos = cnt++;
-        else if (key < lst[N - 1]) pos = N - 1;
-        else return;
-        while (pos > 0 && lst[pos - 1] > key) { lst[pos] = lst[pos - 1]; --pos; }
-        lst[pos] = key;
-      };
-      if constexpr (BATCH) {
-        constexpr int B = 8;
+      for (int part = 0; part < 4; ++part) {
+        const unsigned i0 = o0, i1 = o1;
+        o0 = o2; o1 = o3; o2 = o4; o3 = o5; o4 = o6; o5 = o7;
 #pragma unroll 1
         for (unsigned i = i0; i < i1; i += B) {
           float4 hh[B];
@@ -246,9 +268,14 @@ __device__ __forceinline__ void scan_window(const FindParams& P, const unsigned*
           for (int k = 0; k < B; ++k)
             if (i + k < i1) consider(hh[k]);
         }
-      } else {
+      }
+    } else {
+      // one loop over the (up to four) ranges of the two rows
+      const unsigned n0 = o1 - o0, n01 = n0 + (o3 - o2), n012 = n01 + (o5 - o4), tot = n012 + (o7 - o6);
 #pragma unroll 1
-        for (unsigned i = i0; i < i1; ++i) consider(P.hb[i]);
+      for (unsigned t = 0; t < tot; ++t) {
+        const unsigned i = t < n0 ? o0 + t : t < n01 ? o2 + (t - n0) : t < n012 ? o4 + (t - n01) : o6 + (t - n012);
+        consider(P.hb[i]);
       }
     }
   }
@@ -408,13 +435,22 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   const bool lane_used = grp < W;
   const DevGeom& g = P.g;
   const int L = g.n_layers;
-  unsigned char* ws = smem + (size_t)warp * smem_per_warp_k(L, CAREFUL);
-  double* const dst_warp = reinterpret_cast<double*>(ws + smem_per_warp(L));  // careful pass only
-  unsigned long long* lst = reinterpret_cast<unsigned long long*>(ws) + lane * LIST_STRIDE;
-  unsigned long long* gather = reinterpret_cast<unsigned long long*>(ws + SMEM_LIST);
+  // the eta-bin edges of every layer, copied once per block
+  float* const s_edges = reinterpret_cast<float*>(smem);
+  for (int i = threadIdx.x; i < L * (g.n_eta + 1); i += blockDim.x) {
+    const int l = i / (g.n_eta + 1);
+    s_edges[i] = P.eta_edges[(size_t)l * (MAX_ETA_BINS + 1) + (i - l * (g.n_eta + 1))];
+  }
+  __syncthreads();
+  constexpr int LS = list_stride(G, CAREFUL);
+  constexpr int SL = smem_list(G, CAREFUL), SG = smem_gather(G, CAREFUL);
+  unsigned char* ws = smem + smem_edges(L, g.n_eta) + (size_t)warp * smem_per_warp_k(G, L, CAREFUL);
+  double* const dst_warp = reinterpret_cast<double*>(ws + smem_per_warp(G, CAREFUL, L));  // careful pass only
+  unsigned long long* lst = reinterpret_cast<unsigned long long*>(ws) + lane * LS;
+  unsigned long long* gather = reinterpret_cast<unsigned long long*>(ws + SL);
   float* bak = reinterpret_cast<float*>(gather) + lane * BACKUP_STRIDE;
-  unsigned long long* slot = reinterpret_cast<unsigned long long*>(ws + SMEM_LIST + SMEM_GATHER);
-  int* hist = reinterpret_cast<int*>(ws + SMEM_LIST + SMEM_GATHER + SMEM_SLOT);
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(ws + SL + SG);
+  int* hist = reinterpret_cast<int*>(ws + SL + SG + SMEM_SLOT);
   const int N = g.max_cands;
   const int n_seed_range = CAREFUL ? (int)P.queue[2] : P.s_end - P.s_begin;
   const int n_tasks = (n_seed_range + W - 1) / W;
@@ -571,7 +607,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
               const bool spd = f.s00 > 0.f && f.si00 > 0.f && f.si11 > 0.f;
               if (!spd) c_npd++;
               const Align4 al = P.align[l];
-              const Window w = window_of(P, l, R, p, f, spd, al);
+              const Window w = window_of(P, l, R, p, f, spd, al, s_edges);
               const unsigned* off = P.bin_off + ((size_t)ev * L + l) * ((size_t)g.n_eta * g.n_phi);
               scan_window<CAREFUL>(P, off, w, al, p, f, nfound + 1, chi2, gl, lst, cnt, c_chi2);
               if (nholes < g.max_holes) {
@@ -596,6 +632,17 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       unsigned long long mine = KEY_EMPTY;
       int par = gl, p_holes = nholes, p_cls = cls;
       bool p_dbl = dbl;
+      // The chosen hit's coordinates are loaded as soon as the child is known,
+      // so that the load overlaps the state exchange.
+      float hit_x = 0.f, hit_y = 0.f, hit_z = 0.f;
+      auto fetch_hit = [&]() {
+        if (active && mine != KEY_EMPTY && !key_nonhit(mine)) {
+          const int hi = hoff + key_hit(mine);
+          hit_x = __ldg(P.hx + hi);
+          hit_y = __ldg(P.hy + hi);
+          hit_z = __ldg(P.hz + hi);
+        }
+      };
       if constexpr (!CAREFUL) {
         // A group with a near-tangent crossing gives its seed up after this
         // layer (its lanes go idle) and lists it for the careful pass.
@@ -609,6 +656,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         // the children of the seed's candidate, in rank order, one per lane;
         // every lane holds their parent's state already
         mine = lane_used ? first_key : KEY_EMPTY;
+        fetch_hit();
         par = 0;
         p_holes = 0;
         p_cls = first_cls;
@@ -626,39 +674,54 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
           if (gl >= off) incl += v;
         }
         const int M = __shfl_sync(0xffffffffu, incl, min(base + G - 1, 31));
-        unsigned long long* A = gather + base * LIST_STRIDE;
+        unsigned long long* A = gather + base * LS;
         for (int j = 0, o = incl - cnt; j < cnt; ++j) A[o + j] = lst[j];
+        // An odd count is padded with an empty key (never smaller), so that
+        // the ranking reads two keys per 16-byte load.  The group's area holds
+        // G (G + 1) keys, an even number, so an odd count leaves room for the
+        // pad; it starts on a 16-byte boundary for the same reason.
+        if (gl == G - 1 && (M & 1)) A[M] = KEY_EMPTY;
         slot[lane] = KEY_EMPTY;
         __syncwarp();
         // rank = number of smaller keys in the group (keys are unique)
+        const ulonglong2* A2 = reinterpret_cast<const ulonglong2*>(A);
 #pragma unroll 1
         for (int m = gl; m < M && lane_used; m += G) {
           const unsigned long long key = A[m];
           int rank = 0;
 #pragma unroll 4
-          for (int q = 0; q < M; ++q) rank += A[q] < key ? 1 : 0;
+          for (int q = 0; q < (M + 1) / 2; ++q) {
+            const ulonglong2 v = A2[q];
+            rank += (v.x < key ? 1 : 0) + (v.y < key ? 1 : 0);
+          }
           if (rank < N) slot[base + rank] = key;
         }
         __syncwarp();
         if (lane_used && gl < N) mine = slot[lane];
+        fetch_hit();
         // Pull the parent's exported state (the prediction, or the unchanged
-        // state of a carried candidate).
+        // state of a carried candidate) through shared memory: every lane
+        // writes its 27 values to the packed-children area (no longer read
+        // after the selection; rows of 27 floats, so that the 32 lanes fall in
+        // distinct banks), then reads its parent's row.
         par = (mine != KEY_EMPTY) ? key_parent(mine) : gl;
         const int src = lane_used ? base + par : lane;
-        float np[6], nC[21];
+        float* xs = reinterpret_cast<float*>(gather);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) np[k] = __shfl_sync(0xffffffffu, p[k], src);
+        for (int k = 0; k < 6; ++k) xs[lane * 27 + k] = p[k];
 #pragma unroll
-        for (int k = 0; k < 21; ++k) nC[k] = __shfl_sync(0xffffffffu, C[k], src);
+        for (int k = 0; k < 21; ++k) xs[lane * 27 + 6 + k] = C[k];
         p_holes = __shfl_sync(0xffffffffu, nholes, src);
         p_cls = __shfl_sync(0xffffffffu, cls, src);
         if constexpr (CAREFUL) p_dbl = __shfl_sync(0xffffffffu, (int)dbl, src) != 0;
+        __syncwarp();
         if (active && !in_seed) {
 #pragma unroll
-          for (int k = 0; k < 6; ++k) p[k] = np[k];
+          for (int k = 0; k < 6; ++k) p[k] = xs[src * 27 + k];
 #pragma unroll
-          for (int k = 0; k < 21; ++k) C[k] = nC[k];
+          for (int k = 0; k < 21; ++k) C[k] = xs[src * 27 + 6 + k];
         }
+        __syncwarp();
       }
 
       if (active) {
@@ -715,9 +778,14 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
           do_update = do_ms = false;
         }
         if (do_update) {
-          const int hi = hoff + hit;
           float mx, my, mz;
-          corrected_hit(P.align[l], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+          if (in_seed) {
+            const int hi = hoff + hit;
+            hit_x = P.hx[hi];
+            hit_y = P.hy[hi];
+            hit_z = P.hz[hi];
+          }
+          corrected_hit(P.align[l], hit_x, hit_y, hit_z, mx, my, mz);
           Frame f;
           make_frame<float>(p, C, g.vr, g.vz, f);
           float r0, r1;
@@ -807,13 +875,14 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
 }
 
 template <int G, int CAP>
-cudaError_t prepare_g(int threads, int n_layers, int* blocks_per_sm) {
-  const size_t smem = (size_t)(threads / 32) * smem_per_warp(n_layers);
+cudaError_t prepare_g(int threads, int n_layers, int n_eta, int* blocks_per_sm) {
+  const size_t smem = smem_edges(n_layers, n_eta) + (size_t)(threads / 32) * smem_per_warp(G, false, n_layers);
   cudaError_t err = cudaFuncSetAttribute(k_find<G, CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_find<G, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)((CAREFUL_THREADS / 32) * smem_per_warp_k(n_layers, true)));
+                               (int)(smem_edges(n_layers, n_eta) +
+                                     (CAREFUL_THREADS / 32) * smem_per_warp_k(G, n_layers, true)));
   if (err != cudaSuccess) return err;
   cudaFuncAttributes fa;
   err = cudaFuncGetAttributes(&fa, k_find<G, CAP, false>);
@@ -829,7 +898,8 @@ cudaError_t prepare_g(int threads, int n_layers, int* blocks_per_sm) {
 
 template <int G, int CAP>
 cudaError_t launch_main_g(const FindParams& P, int threads, int grid_cap, cudaStream_t st) {
-  const size_t smem = (size_t)(threads / 32) * smem_per_warp(P.g.n_layers);
+  const size_t smem =
+      smem_edges(P.g.n_layers, P.g.n_eta) + (size_t)(threads / 32) * smem_per_warp(G, false, P.g.n_layers);
   constexpr int W = 32 / G;
   const int n = P.s_end - P.s_begin;
   const int n_tasks = (n + W - 1) / W;
@@ -843,7 +913,8 @@ cudaError_t launch_main_g(const FindParams& P, int threads, int grid_cap, cudaSt
 
 template <int G, int CAP>
 cudaError_t launch_careful_g(const FindParams& P, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)(CAREFUL_THREADS / 32) * smem_per_warp_k(P.g.n_layers, true);
+  const size_t smem =
+      smem_edges(P.g.n_layers, P.g.n_eta) + (size_t)(CAREFUL_THREADS / 32) * smem_per_warp_k(G, P.g.n_layers, true);
   k_find<G, 0, true><<<grid, CAREFUL_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
@@ -917,14 +988,16 @@ cudaError_t launch_seed_order(const float* theta, const int* seed_off, int n_eve
   return cudaGetLastError();
 }
 
-size_t find_smem_bytes(int threads, int n_layers) { return (size_t)(threads / 32) * smem_per_warp(n_layers); }
+size_t find_smem_bytes(int threads, int n_layers, int n_eta) {
+  return smem_edges(n_layers, n_eta) + (size_t)(threads / 32) * smem_per_warp(KF_MAX_CANDS, false, n_layers);
+}
 
 bool find_lanes_supported(int lanes) {
   return lanes == 4 || lanes == 6 || lanes == 8 || lanes == 10 || lanes == 12 || lanes == 16;
 }
 
-cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* blocks_per_sm) {
-  KF_FIND_DISPATCH(prepare_g, threads, n_layers, blocks_per_sm)
+cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int n_eta, int* blocks_per_sm) {
+  KF_FIND_DISPATCH(prepare_g, threads, n_layers, n_eta, blocks_per_sm)
 }
 
 cudaError_t launch_find_main(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,

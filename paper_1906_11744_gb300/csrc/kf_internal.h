@@ -231,11 +231,11 @@ cudaError_t launch_find_main(const FindParams& P, int lanes, int regcap, int thr
 cudaError_t launch_find_careful(const FindParams& P, int lanes, int grid, cudaStream_t st);
 // Per event, the seeds sorted by theta (params row 5) into order[].
 cudaError_t launch_seed_order(const float* theta, const int* seed_off, int n_events, int* order, cudaStream_t st);
-size_t find_smem_bytes(int threads, int n_layers);
+size_t find_smem_bytes(int threads, int n_layers, int n_eta);
 bool find_lanes_supported(int lanes);
 // Sets the dynamic shared-memory limit of the kernel variant (must run
 // outside stream capture) and reports resident blocks per SM.
-cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int* blocks_per_sm);
+cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int n_eta, int* blocks_per_sm);
 // kf_bin.cu
 cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsigned first_pos, int max_event_hits,
                        unsigned* scan_tmp, size_t scan_tmp_elems, cudaStream_t st);
