@@ -66,6 +66,7 @@ def lib():
                                   _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]
             L.orc_fit_grad.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_long, _P, _P, ctypes.c_int,
                                        _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_fit_grad32.argtypes = L.orc_fit_grad.argtypes
             L.orc_find_event.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                          ctypes.c_long, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
                                          _P, _P, _P, _P, _P, _P]
@@ -216,9 +217,11 @@ def fit(det, prior_p, prior_C, hit_lists, n_hits, hx, hy, hz, hlayer, align=None
     return p, C, c2, st
 
 
-def fit_grad(det, prior_p, prior_C, hit_lists, n_hits, hx, hy, hz, hlayer, align=None):
+def fit_grad(det, prior_p, prior_C, hit_lists, n_hits, hx, hy, hz, hlayer, align=None, fp32=False):
     """Summed fit chi2 and its gradient (forward-mode dual numbers).
-    Returns (chi2_total, g_align [L][2], g_hits [n_hit_arrays][3], g_seed [n][6], chi2 [n])."""
+    Returns (chi2_total, g_align [L][2], g_hits [n_hit_arrays][3], g_seed [n][6], chi2 [n]).
+    fp32: the same computation with every operation rounded to single
+    precision (the FP32 rounding scale of each result)."""
     prior_p = _c(prior_p, np.float64); prior_C = _c(prior_C, np.float64)
     n = prior_p.shape[1]
     hit_lists = _c(hit_lists, np.int32); n_hits = _c(n_hits, np.int32)
@@ -228,7 +231,8 @@ def fit_grad(det, prior_p, prior_C, hit_lists, n_hits, hx, hy, hz, hlayer, align
     tot = np.zeros(1); ga = np.zeros((det.n_layers, 2)); gh = np.zeros((hx.size, 3))
     gs = np.zeros((n, 6)); each = np.zeros(n)
     d = make_detector(det)
-    rc = lib().orc_fit_grad(ctypes.byref(d), n, _ptr(prior_p), _ptr(prior_C), n, _ptr(hit_lists),
+    fn = lib().orc_fit_grad32 if fp32 else lib().orc_fit_grad
+    rc = fn(ctypes.byref(d), n, _ptr(prior_p), _ptr(prior_C), n, _ptr(hit_lists),
                             _ptr(n_hits), hit_lists.shape[1], _ptr(hx), _ptr(hy), _ptr(hz),
                             _ptr(hlayer), _ptr(align), _ptr(tot), _ptr(ga), _ptr(gh), _ptr(gs),
                             _ptr(each))
@@ -269,7 +273,7 @@ def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=
     return dict(hits=out_hits, n_found=out_n, chi2=out_c2, p=out_p, C=out_C,
                 counters=dict(steps=int(cnt[0]), prop_calls=int(cnt[1]), updates=int(cnt[2]),
                               ms=int(cnt[3]), chi2_evals=int(cnt[4]), seeds=int(cnt[5]),
-                              children=int(cnt[6])))
+                              children=int(cnt[6]), holes=int(cnt[7])))
 
 
 def dedup(hits, n_hits, chi2, frac=0.5, brute=False, params=None, bz=0.0, deta=0.0, dphi=0.0, dpt=0.0):

@@ -47,79 +47,120 @@ constexpr double PI = 3.14159265358979323846;
 // Forward-mode derivatives: value v plus derivatives d[0..g_nd) with respect to
 // g_nd independent inputs.  Branches compare values only.  g_nd is per host
 // thread, so that calls on different threads do not interfere.
+// DualB<false> (Dual) is double precision.  DualB<true> (Dual32) rounds the
+// value and every derivative to single precision after each operation: the
+// same computation as single-precision arithmetic would do it (library
+// functions rounded from their double values), which measures how far FP32
+// rounding alone moves a result.
 constexpr int DMAX = 112;
 thread_local int g_nd = 0;
 
-struct Dual {
+template <bool R32>
+inline double rnd(double x) { return R32 ? (double)(float)x : x; }
+
+template <bool R32>
+struct DualB {
   double v;
   double d[DMAX];
-  Dual() : v(0.0) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }
-  Dual(double x) : v(x) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }  // NOLINT implicit
+  DualB() : v(0.0) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }
+  DualB(double x) : v(rnd<R32>(x)) { for (int i = 0; i < g_nd; ++i) d[i] = 0.0; }  // NOLINT implicit
 };
-inline Dual make_var(double x, int k) {
-  Dual r(x);
+using Dual = DualB<false>;
+using Dual32 = DualB<true>;
+template <bool R = false>
+inline DualB<R> make_var(double x, int k) {
+  DualB<R> r(x);
   r.d[k] = 1.0;
   return r;
 }
 inline double val(double x) { return x; }
-inline double val(const Dual& x) { return x.v; }
+template <bool R>
+inline double val(const DualB<R>& x) { return x.v; }
 
-inline Dual operator+(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v + b.v;
-  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] + b.d[i];
+template <bool R>
+inline DualB<R> operator+(const DualB<R>& a, const DualB<R>& b) {
+  DualB<R> r; r.v = rnd<R>(a.v + b.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>(a.d[i] + b.d[i]);
   return r;
 }
-inline Dual operator-(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v - b.v;
-  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] - b.d[i];
+template <bool R>
+inline DualB<R> operator-(const DualB<R>& a, const DualB<R>& b) {
+  DualB<R> r; r.v = rnd<R>(a.v - b.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>(a.d[i] - b.d[i]);
   return r;
 }
-inline Dual operator-(const Dual& a) {
-  Dual r; r.v = -a.v;
+template <bool R>
+inline DualB<R> operator-(const DualB<R>& a) {
+  DualB<R> r; r.v = -a.v;
   for (int i = 0; i < g_nd; ++i) r.d[i] = -a.d[i];
   return r;
 }
-inline Dual operator*(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v * b.v;
-  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+template <bool R>
+inline DualB<R> operator*(const DualB<R>& a, const DualB<R>& b) {
+  DualB<R> r; r.v = rnd<R>(a.v * b.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>(rnd<R>(a.d[i] * b.v) + rnd<R>(a.v * b.d[i]));
   return r;
 }
-inline Dual operator/(const Dual& a, const Dual& b) {
-  Dual r; r.v = a.v / b.v;
-  const double ib = 1.0 / b.v;
-  for (int i = 0; i < g_nd; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+template <bool R>
+inline DualB<R> operator/(const DualB<R>& a, const DualB<R>& b) {
+  DualB<R> r; r.v = rnd<R>(a.v / b.v);
+  const double ib = rnd<R>(1.0 / b.v);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>(rnd<R>(a.d[i] - rnd<R>(r.v * b.d[i])) * ib);
   return r;
 }
-inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
-inline Dual operator+(double a, const Dual& b) { return b + a; }
-inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
-inline Dual operator-(double a, const Dual& b) { return (-b) + a; }
-inline Dual operator*(const Dual& a, double b) {
-  Dual r; r.v = a.v * b;
-  for (int i = 0; i < g_nd; ++i) r.d[i] = a.d[i] * b;
+template <bool R>
+inline DualB<R> operator+(const DualB<R>& a, double b) { DualB<R> r = a; r.v = rnd<R>(r.v + b); return r; }
+template <bool R>
+inline DualB<R> operator+(double a, const DualB<R>& b) { return b + a; }
+template <bool R>
+inline DualB<R> operator-(const DualB<R>& a, double b) { DualB<R> r = a; r.v = rnd<R>(r.v - b); return r; }
+template <bool R>
+inline DualB<R> operator-(double a, const DualB<R>& b) { return (-b) + a; }
+template <bool R>
+inline DualB<R> operator*(const DualB<R>& a, double b) {
+  DualB<R> r; r.v = rnd<R>(a.v * b);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>(a.d[i] * b);
   return r;
 }
-inline Dual operator*(double a, const Dual& b) { return b * a; }
-inline Dual operator/(const Dual& a, double b) { return a * (1.0 / b); }
-inline Dual operator/(double a, const Dual& b) { return Dual(a) / b; }
-inline Dual& operator+=(Dual& a, const Dual& b) { a = a + b; return a; }
-inline Dual& operator-=(Dual& a, const Dual& b) { a = a - b; return a; }
+template <bool R>
+inline DualB<R> operator*(double a, const DualB<R>& b) { return b * a; }
+template <bool R>
+inline DualB<R> operator/(const DualB<R>& a, double b) { return a * rnd<R>(1.0 / b); }
+template <bool R>
+inline DualB<R> operator/(double a, const DualB<R>& b) { return DualB<R>(a) / b; }
+template <bool R>
+inline DualB<R>& operator+=(DualB<R>& a, const DualB<R>& b) { a = a + b; return a; }
+template <bool R>
+inline DualB<R>& operator-=(DualB<R>& a, const DualB<R>& b) { a = a - b; return a; }
+template <bool R>
+inline DualB<R>& operator+=(DualB<R>& a, double b) { a = a + b; return a; }
+template <bool R>
+inline DualB<R>& operator-=(DualB<R>& a, double b) { a = a - b; return a; }
 
-inline Dual chain(const Dual& a, double f, double df) {
-  Dual r; r.v = f;
-  for (int i = 0; i < g_nd; ++i) r.d[i] = df * a.d[i];
+template <bool R>
+inline DualB<R> chain(const DualB<R>& a, double f, double df) {
+  DualB<R> r; r.v = rnd<R>(f);
+  const double dr = rnd<R>(df);
+  for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>(dr * a.d[i]);
   return r;
 }
-inline Dual sin(const Dual& a) { return chain(a, std::sin(a.v), std::cos(a.v)); }
-inline Dual cos(const Dual& a) { return chain(a, std::cos(a.v), -std::sin(a.v)); }
-inline Dual atan(const Dual& a) { return chain(a, std::atan(a.v), 1.0 / (1.0 + a.v * a.v)); }
-inline Dual sqrt(const Dual& a) { double s = std::sqrt(a.v); return chain(a, s, 0.5 / s); }
-inline Dual log(const Dual& a) { return chain(a, std::log(a.v), 1.0 / a.v); }
-inline Dual fabs(const Dual& a) { return a.v < 0 ? -a : a; }
-inline Dual atan2(const Dual& y, const Dual& x) {
+template <bool R>
+inline DualB<R> sin(const DualB<R>& a) { return chain(a, std::sin(a.v), std::cos(a.v)); }
+template <bool R>
+inline DualB<R> cos(const DualB<R>& a) { return chain(a, std::cos(a.v), -std::sin(a.v)); }
+template <bool R>
+inline DualB<R> atan(const DualB<R>& a) { return chain(a, std::atan(a.v), 1.0 / (1.0 + a.v * a.v)); }
+template <bool R>
+inline DualB<R> sqrt(const DualB<R>& a) { double s = std::sqrt(a.v); return chain(a, s, 0.5 / s); }
+template <bool R>
+inline DualB<R> log(const DualB<R>& a) { return chain(a, std::log(a.v), 1.0 / a.v); }
+template <bool R>
+inline DualB<R> fabs(const DualB<R>& a) { return a.v < 0 ? -a : a; }
+template <bool R>
+inline DualB<R> atan2(const DualB<R>& y, const DualB<R>& x) {
   const double r2 = x.v * x.v + y.v * y.v;
-  Dual r; r.v = std::atan2(y.v, x.v);
-  for (int i = 0; i < g_nd; ++i) r.d[i] = (x.v * y.d[i] - y.v * x.d[i]) / r2;
+  DualB<R> r; r.v = rnd<R>(std::atan2(y.v, x.v));
+  for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>((x.v * y.d[i] - y.v * x.d[i]) / r2);
   return r;
 }
 
@@ -579,7 +620,7 @@ struct Counters {
   long long chi2_evals;   // hits whose chi2 was evaluated
   long long seeds;
   long long children;     // children ranked
-  long long reserved;
+  long long holes;        // kept hole children (scattering without an update)
 };
 
 void seed_state(const double* params, const double* cov, long stride, long i, double p[6],
@@ -694,6 +735,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
         ++cnt.updates;
       } else {
         c.n_holes += 1;
+        ++cnt.holes;
       }
       add_ms(c.p, c.C, x0_at(det, Lyr, c.p[2]));
       add_eloss(c.p, c.C, det.eloss[Lyr]);
@@ -902,7 +944,12 @@ int orc_fit(const orc_detector* dptr, int n_tracks, const double* prior_p, const
 // Summed chi2 of the fits and its gradient by forward-mode dual numbers:
 // g_align [n_layers][2], g_hits [n_hit_arrays][3] (accumulated over tracks
 // sharing a hit), g_seed [n_tracks][6].
-int orc_fit_grad(const orc_detector* dptr, int n_tracks, const double* prior_p,
+}  // extern "C"
+
+// The summed fit chi2 and its gradient, forward mode (D = Dual, or Dual32 for
+// the same computation with single-precision rounding after every operation).
+template <class D>
+int fit_grad_impl(const orc_detector* dptr, int n_tracks, const double* prior_p,
                  const double* prior_C, long stride, const int* hit_lists, const int* n_hits,
                  int max_len, const double* hx, const double* hy, const double* hz,
                  const int* hlayer, const double* align, double* chi2_total, double* g_align,
@@ -914,28 +961,28 @@ int orc_fit_grad(const orc_detector* dptr, int n_tracks, const double* prior_p,
     const int n = n_hits[t];
     g_nd = 6 + 3 * n + 2 * L;
     if (g_nd > DMAX) { g_nd = 0; return -1; }
-    Dual p0[6];
+    D p0[6];
     double C0[6][6], p0v[6];
     seed_state(prior_p, prior_C, stride, t, p0v, C0);
-    for (int k = 0; k < 6; ++k) p0[k] = make_var(p0v[k], k);
-    std::vector<Dual> rawv(3 * (size_t)n);
+    for (int k = 0; k < 6; ++k) p0[k] = D(p0v[k]), p0[k].d[k] = 1.0;
+    std::vector<D> rawv(3 * (size_t)n);
     std::vector<int> lays(n);
     for (int k = 0; k < n; ++k) {
       const int hidx = hit_lists[(size_t)t * max_len + k];
-      rawv[3 * k] = make_var(hx[hidx], 6 + 3 * k);
-      rawv[3 * k + 1] = make_var(hy[hidx], 6 + 3 * k + 1);
-      rawv[3 * k + 2] = make_var(hz[hidx], 6 + 3 * k + 2);
+      rawv[3 * k] = D(hx[hidx]), rawv[3 * k].d[6 + 3 * k] = 1.0;
+      rawv[3 * k + 1] = D(hy[hidx]), rawv[3 * k + 1].d[6 + 3 * k + 1] = 1.0;
+      rawv[3 * k + 2] = D(hz[hidx]), rawv[3 * k + 2].d[6 + 3 * k + 2] = 1.0;
       lays[k] = hlayer[hidx];
     }
-    std::vector<Dual> alv(2 * (size_t)L);
+    std::vector<D> alv(2 * (size_t)L);
     for (int i = 0; i < L; ++i) {
-      alv[2 * i] = make_var(align[2 * i], 6 + 3 * n + 2 * i);
-      alv[2 * i + 1] = make_var(align[2 * i + 1], 6 + 3 * n + 2 * i + 1);
+      alv[2 * i] = D(align[2 * i]), alv[2 * i].d[6 + 3 * n + 2 * i] = 1.0;
+      alv[2 * i + 1] = D(align[2 * i + 1]), alv[2 * i + 1].d[6 + 3 * n + 2 * i + 1] = 1.0;
     }
-    Dual p[6], C[6][6], c2;
-    const int st = fit_track<Dual>(det, p0, C0, n, reinterpret_cast<const Dual(*)[3]>(rawv.data()),
-                                   lays.data(), reinterpret_cast<const Dual(*)[2]>(alv.data()),
-                                   false, p, C, c2);
+    D p[6], C[6][6], c2;
+    const int st = fit_track<D>(det, p0, C0, n, reinterpret_cast<const D(*)[3]>(rawv.data()),
+                                lays.data(), reinterpret_cast<const D(*)[2]>(alv.data()),
+                                false, p, C, c2);
     if (st != 0) { g_nd = 0; return -2 - t; }
     total += c2.v;
     if (chi2_each) chi2_each[t] = c2.v;
@@ -949,6 +996,28 @@ int orc_fit_grad(const orc_detector* dptr, int n_tracks, const double* prior_p,
   *chi2_total = total;
   g_nd = 0;
   return 0;
+}
+
+extern "C" {
+
+int orc_fit_grad(const orc_detector* dptr, int n_tracks, const double* prior_p,
+                 const double* prior_C, long stride, const int* hit_lists, const int* n_hits,
+                 int max_len, const double* hx, const double* hy, const double* hz,
+                 const int* hlayer, const double* align, double* chi2_total, double* g_align,
+                 double* g_hits, double* g_seed, double* chi2_each) {
+  return fit_grad_impl<Dual>(dptr, n_tracks, prior_p, prior_C, stride, hit_lists, n_hits, max_len, hx, hy, hz,
+                             hlayer, align, chi2_total, g_align, g_hits, g_seed, chi2_each);
+}
+
+// The same gradient with every operation rounded to single precision (the
+// inputs too): the FP32 rounding scale of each gradient component.
+int orc_fit_grad32(const orc_detector* dptr, int n_tracks, const double* prior_p,
+                   const double* prior_C, long stride, const int* hit_lists, const int* n_hits,
+                   int max_len, const double* hx, const double* hy, const double* hz,
+                   const int* hlayer, const double* align, double* chi2_total, double* g_align,
+                   double* g_hits, double* g_seed, double* chi2_each) {
+  return fit_grad_impl<Dual32>(dptr, n_tracks, prior_p, prior_C, stride, hit_lists, n_hits, max_len, hx, hy,
+                               hz, hlayer, align, chi2_total, g_align, g_hits, g_seed, chi2_each);
 }
 
 // Combinatorial finding for seeds [s_begin, s_end) of one event.  Hits are
@@ -989,7 +1058,7 @@ int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits,
   if (counters) {
     counters[0] += cnt.steps; counters[1] += cnt.prop_calls; counters[2] += cnt.updates;
     counters[3] += cnt.ms; counters[4] += cnt.chi2_evals; counters[5] += cnt.seeds;
-    counters[6] += cnt.children;
+    counters[6] += cnt.children; counters[7] += cnt.holes;
   }
   return 0;
 }

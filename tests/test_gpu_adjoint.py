@@ -6,13 +6,21 @@ here the GPU adjoint (FP32, checkpointed reverse sweep) must match it within
 1e-3 relative, and the alignment gradient must also match FP64 central finite
 differences of the oracle's summed chi2.
 
-"1e-3 relative" is read per gradient array, against its largest component:
-max|g - g_ref| <= 1e-3 max|g_ref|.  Components far below the array's scale
-come out of sums of much larger terms of both signs (residual times inverse
-covariance, ~1/sigma^2), whose FP32 rounding bounds their absolute error, so
-a per-component relative bound would test FP32 cancellation rather than the
-adjoint; the same reverse sweep written in float32 numpy shows the same
-per-component spread (see the design notes).
+"1e-3 relative" is read two ways, both asserted:
+  * per gradient array, against its largest component:
+    max|g - g_ref| <= 1e-3 max|g_ref|;
+  * per component: |g - g_ref| <= 1e-3 |g_ref| + 8 sigma, where sigma is that
+    component's FP32 rounding scale: the RMS change when the oracle runs the
+    same gradient with every operation rounded to single precision, on
+    inputs jittered by up to one FP32 ulp (four trials).  The emulation
+    rounds correctly (0.5 ulp per operation); the CUDA path takes its
+    reciprocals, sines and logarithms from the hardware approximations (up to
+    about 2 ulp), so its rounding scale is up to 4 sigma: the bound is two of
+    those.  Components far
+    below their array's scale are sums of much larger terms of both signs
+    (residual times inverse covariance, ~1/sigma^2), so their FP32 error is
+    set by those terms, not by their own size.  The fraction of components
+    inside the plain 1e-3 relative bound is printed beside it.
 """
 import numpy as np
 import pytest
@@ -37,6 +45,36 @@ def _close(g, ref):
     return float(np.abs(g - ref).max() / scale), comp
 
 
+def _fp32_sigma(b, sel, lists, n, trials=4, seed=7):
+    """The oracle's gradients (align, hits, seed) and, per component, the RMS
+    over `trials` of their change when the same computation runs with every
+    operation rounded to single precision, on inputs (hit coordinates, seed
+    parameters) jittered by up to one FP32 ulp: the FP32 rounding scale of
+    each component."""
+    from kfhelp import JITTER_REL
+    x, y, z, lay = b.event_hits(0)
+    rng = np.random.default_rng(seed)
+    base = oracle.fit_grad(b.det, b.params[:, sel], b.cov[:, sel], lists[sel], n[sel], x, y, z, lay, b.align)
+    acc = [np.zeros_like(base[1]), np.zeros_like(base[2]), np.zeros_like(base[3])]
+    for _ in range(trials):
+        j = lambda a: a.astype(np.float64) * (1.0 + JITTER_REL * rng.uniform(-1, 1, a.shape))  # noqa: E731
+        g = oracle.fit_grad(b.det, j(b.params[:, sel]), b.cov[:, sel], lists[sel], n[sel], j(x), j(y), j(z), lay,
+                            b.align, fp32=True)
+        for k in range(3):
+            acc[k] += (g[k + 1] - base[k + 1]) ** 2
+    return base, [np.sqrt(a / trials) for a in acc]
+
+
+def _component_ok(g, ref, sigma):
+    """Per-component bound |g - ref| <= 1e-3 |ref| + 8 sigma; returns (all
+    inside, fraction inside the plain 1e-3 relative bound, largest ratio)."""
+    g, ref = np.asarray(g, np.float64), np.asarray(ref, np.float64)
+    d = np.abs(g - ref)
+    bound = REL * np.abs(ref) + 8.0 * sigma
+    plain = d <= REL * np.abs(ref)
+    return bool(np.all(d <= bound)), float(plain.mean()), float((d / np.maximum(bound, 1e-300)).max())
+
+
 def _setup(n_tracks=300, stride=4, seed=1003):
     from paper_1906_11744_gb300 import KF_FIT_GIVEN
     b = make_batch("c3", tracks=n_tracks, seed=seed)
@@ -58,17 +96,19 @@ def test_adjoint_matches_oracle_dual_gradient(stride):
     g_hits = np.zeros((b.n_hits, 3), np.float32)
     g_seed = np.zeros((6, b.n_seeds), np.float32)
     t.fit_adjoint(g_align, g_hits, g_seed)
-    x, y, z, lay = b.event_hits(0)
     sel = np.nonzero(ok)[0]
-    tot, ga, gh, gs, each = oracle.fit_grad(b.det, b.params[:, sel], b.cov[:, sel], lists[sel], n[sel],
-                                            x, y, z, lay, b.align)
+    (tot, ga, gh, gs, each), sig = _fp32_sigma(b, sel, lists, n)
     ea, ca = _close(g_align, ga)
     eh, ch = _close(g_hits, gh)
     es, cs = _close(g_seed[:, sel].T, gs)
+    comp = [_component_ok(g_align, ga, sig[0]), _component_ok(g_hits, gh, sig[1]),
+            _component_ok(g_seed[:, sel].T, gs, sig[2])]
     print(f"stride {stride}: norm-wise align {ea:.2e} hits {eh:.2e} seed {es:.2e}; "
-          f"components above 1% of scale: {ca:.2e} {ch:.2e} {cs:.2e}")
+          f"components above 1% of scale: {ca:.2e} {ch:.2e} {cs:.2e}; "
+          f"inside plain 1e-3: {comp[0][1]:.4f} {comp[1][1]:.4f} {comp[2][1]:.4f}; "
+          f"largest |dg| / (1e-3 |g| + 8 sigma): {comp[0][2]:.2f} {comp[1][2]:.2f} {comp[2][2]:.2f}")
     assert ea < REL and eh < REL and es < REL
-    assert ca < 1e-2 and ch < 1e-2 and cs < 1e-2
+    assert all(c[0] for c in comp), comp
     assert np.all(g_seed[:, ~ok] == 0)
 
 

@@ -3,15 +3,15 @@
 The PU-200-like batch (100 events x 8,000 tracks, 20% noise, N = 10) runs as
 the benchmark runs it: the finding kernel's launch shape chosen by the
 autotuner, then one captured graph with binning, finding, duplicate removal,
-fit and adjoint.  The oracle checks sampled outputs it can compute one by one:
-found hit lists of 600 seeds from three events, duplicate flags of one whole
-event, fits and seed gradients of sampled kept tracks.
+fit and adjoint.  The oracle checks every seed of ten whole events (80,000 seeds, on all host
+cores), duplicate flags of one whole event, fits and seed gradients of sampled
+kept tracks, and the work counters of one whole event.
 """
 import numpy as np
 import pytest
 
 import oracle
-from kfhelp import TOL, audit_mismatch, cov_close, param_close, tracker_for
+from kfhelp import TOL, audit_mismatch, cov_close, found_cov_close, jitter_audit, oracle_find_events, param_close, tracker_for
 from synth import make_batch
 
 pytestmark = pytest.mark.gpu
@@ -126,3 +126,59 @@ def test_sampled_fits_and_seed_gradients(pu200):
         err = np.abs(g_seed[:, sel].T - gs).max() / np.abs(gs).max()
         assert err < 1e-3, err
     assert TOL == 1e-4
+
+
+def test_ten_whole_events_against_oracle(pu200):
+    """Every seed of ten whole PU-200 events: hit lists identical for at least
+    99.5% of seeds; parameters and covariances of the identical ones within
+    the fit tolerances.  Each mismatch is classified: a chi2-sum tie within
+    1e-5 relative (the stated near-tie bound), or else a tie or a hit at the
+    cut that one-ulp jitter of the hit coordinates shows to be unresolved at
+    FP32 resolution (jitter_audit); none may be left unexplained."""
+    b, trk, fit, g_seed, counters = pu200
+    events = list(range(0, 100, 10))
+    ref, _ = oracle_find_events(b, events)
+    n_all = n_same = 0
+    classes = {"tie<=1e-5": 0, "fp32-tie": 0}
+    worst = 0.0
+    for e in events:
+        a = b.seed_off[e]
+        r = ref[e]
+        ns = r["hits"].shape[0]
+        gh = trk["hits"][a:a + ns]
+        same = np.all(gh == r["hits"], axis=1)
+        n_all += ns
+        n_same += int(same.sum())
+        okp, ep = param_close(trk["params"][:, a:a + ns].T[same], r["p"][same])
+        okc, ec = found_cov_close(trk["cov"][:, a:a + ns].T[same], r["C"][same], r["p"][same])
+        assert okp.all(), (e, ep)
+        assert okc.all(), (e, ec)
+        for i in np.nonzero(~same)[0]:
+            ok, kind, rel = audit_mismatch(b, e, i, gh[i], r["hits"][i])
+            if kind == "tie" and rel <= 1e-5:
+                classes["tie<=1e-5"] += 1
+                continue
+            ok2, rel2, spread = jitter_audit(b, e, i, gh[i], r["hits"][i])
+            assert ok2, (e, i, kind, rel, spread)
+            classes["fp32-tie"] += 1
+            worst = max(worst, rel)
+    rate = n_same / n_all
+    print(f"ten PU-200 events: {n_same}/{n_all} seeds identical ({rate:.5f}); mismatches {classes}, "
+          f"largest relative chi2-sum difference among the FP32 ties {worst:.2e}")
+    assert n_all == 80000
+    assert rate >= 0.995
+
+
+def test_counters_equal_oracle_whole_event():
+    """The kernels' work counters on one whole PU-200 event equal the oracle's
+    (where a near-tie sends a candidate along another path the counts may
+    differ by that path's steps; bounded at 1e-4 relative)."""
+    b = make_batch("c4", n_events=1)
+    t = tracker_for(b)
+    t.find_tracks()
+    g = t.counters()
+    t.close()
+    _, c = oracle_find_events(b, [0])
+    for k in ("steps", "updates", "holes", "seeds"):
+        assert abs(g[k] - c[k]) <= 1e-4 * c[k], (k, g[k], c[k])
+    print("PU-200 event 0 counters (GPU, oracle):", {k: (g[k], c[k]) for k in ("steps", "updates", "holes", "seeds")})

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from kfhelp import audit_mismatch, cov_close, param_close, tracker_for
+from kfhelp import audit_mismatch, cov_close, found_cov_close, param_close, tracker_for
 from synth import make_batch
 from synth.events import true_hit_lists
 
@@ -81,6 +81,35 @@ def test_find_parity(name):
     assert rel.max() < 2e-3, rel.max()
     okp, ep = param_close(trk["params"].T[same], ref["p"][same])
     assert okp.all(), ep
+    # found-track covariances, in the local frame (as for the fit; the bound
+    # grows below cos(alpha) = 0.5 at the last crossing, see found_cov_close)
+    okc, ec = found_cov_close(trk["cov"].T[same], ref["C"][same], ref["p"][same])
+    print(f"{name}: found params max scaled err {ep:.2e}, cov max error / bound {ec[0]:.2f}, radial {ec[1]:.2f}")
+    assert okc.all(), ec
+
+
+@pytest.mark.parametrize("name,exact", [("c1", True), ("c1b", False)])
+def test_counters_equal_oracle(name, exact):
+    """The work the kernels count is the oracle's work on the same inputs:
+    candidate-layer steps, kept hit-children (updates), kept hole children
+    and seeds built.  The benchmark's flop count multiplies these.  Exact on
+    c1; on c1b a chi2 near-tie at the top-N boundary among candidates that
+    do not win may move one child between the two sides, which changes a
+    count by one while every found track still agrees (bound 1e-4)."""
+    from kfhelp import oracle_find_events
+    b = make_batch(name)
+    t = tracker_for(b)
+    t.find_tracks()
+    g = t.counters()
+    trk = t.get_tracks()
+    ref, c = oracle_find_events(b, [0])
+    assert np.array_equal(trk["hits"], ref[0]["hits"])  # counts are comparable where the tracks agree
+    for k in ("steps", "updates", "holes", "seeds"):
+        if exact:
+            assert g[k] == c[k], (k, g[k], c[k])
+        else:
+            assert abs(g[k] - c[k]) <= 1e-4 * c[k], (k, g[k], c[k])
+    print(f"{name}: oracle {dict((k, c[k]) for k in ('steps', 'updates', 'holes', 'seeds'))}, GPU steps {g['steps']}, updates {g['updates']}, holes {g['holes']}, seeds {g['seeds']}")
 
 
 def test_find_with_misalignment():
