@@ -35,19 +35,27 @@ METRIC = "seeds/s and candidate-layer KF updates/s at PU-200, batched vs plain; 
 UNIT = "seeds/s"
 L2_BYTES = 129 * 1024 * 1024
 
-# Algorithmic FP32 operations per unit of work (an FMA counts 2), counted on
-# the minimal sparse formulation of each step; see the design notes.
-F_STEP = 443      # propagation + exact Jacobian + sparse J C J^T + frame + window
-F_HIT = 25        # alignment correction + residual + chi2 of one hit in a window
-F_UPDATE = 195    # frame + gain + state/covariance update of a kept hit-child
-F_MS = 25         # multiple-scattering term
-F_SEED = 1436     # seed fit over three hits
-F_FIT_HIT = 608   # re-fit: propagation + transport + update + scattering per hit
+# Algorithmic operations per unit of work (an FMA counts 2): the operation
+# census of the oracle's own step functions (trivial operations dropped, shared
+# ones and symmetric results counted once) on states of the same workload,
+# stored by the census script beside the oracle and read here as data.  Per
+# candidate-layer step (propagation, transport, frame, z window), per hit in
+# the search window, per kept hit-child (update), per scattering, per seed fit
+# and per hit of the re-fit; window hits per step from the oracle's count of
+# hits inside each prediction's chi2-ellipse bounding box.
+with open(os.path.join(ROOT, "oracle", "flop_census.json")) as _f:
+    CENSUS = json.load(_f)
+F_STEP = CENSUS["flops"]["F_STEP"]
+F_HIT = CENSUS["flops"]["F_HIT"]
+F_UPDATE = CENSUS["flops"]["F_UPDATE"]
+F_MS = CENSUS["flops"]["F_MS"]
+F_SEED = CENSUS["flops"]["F_SEED"]
+WINDOW_HITS_PER_STEP = CENSUS["window_hits_per_step"]
 
 # DRAM traffic (read + write) of one k_find launch on the 100-event batch,
-# scaled by events from an ncu capture of the same kernel on 20 of its events
-# (191.9 MB).  Set to None whenever k_find changes until it is captured again.
-FIND_TRAFFIC_BYTES = 191.92e6 * 5
+# scaled by events from an ncu capture of the same kernel on 20 of its events.
+# None whenever k_find changes until it is captured again.
+FIND_TRAFFIC_BYTES = None
 
 # Duplicate handling measured beside the headline step (Sec. 4.2): seed
 # cleaning on kinematics alone (eta, phi0 within 0.01, pT within 20%) and
@@ -66,7 +74,6 @@ CLEAN_BYTES_PER_SEED = 68 + 37 + 15
 # Set to None whenever those kernels change until they are captured again.
 CLEAN_TRAFFIC_BYTES = 17.57e6 * 5
 
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
@@ -80,8 +87,13 @@ def _measured_peak(key, fallback):
         return fallback, "fallback"
 
 
-def fp32_peak_tflops(mhz=SM_MAX_MHZ):
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def sm_count(dev=0):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def fp32_peak_tflops(n_sm, mhz=SM_MAX_MHZ):
+    return n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
 def dist_env():
@@ -350,17 +362,23 @@ def main():
 
     # roofline of the find kernel (ALU bound: FP32 FMA pipe)
     find_ms = stage["find"] / args.steps
-    find_flops = (counters["steps"] * F_STEP + counters["chi2_evals"] * F_HIT + counters["updates"] * F_UPDATE
+    # counters (steps, updates, holes, seeds) equal the oracle's on the same
+    # inputs (tests); window hits from the oracle's rate per step
+    find_flops = (counters["steps"] * (F_STEP + WINDOW_HITS_PER_STEP * F_HIT) + counters["updates"] * F_UPDATE
                   + (counters["updates"] + counters["holes"]) * F_MS + counters["seeds"] * F_SEED)
     achieved = find_flops / (find_ms / 1e3) / 1e12
-    peak = fp32_peak_tflops()
+    n_sm = sm_count(dev)
+    peak = fp32_peak_tflops(n_sm)
     traffic = None
     if FIND_TRAFFIC_BYTES is not None and args.config == "c4" and not args.events:
         traffic = FIND_TRAFFIC_BYTES
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "k_find",
                 "flops_per_launch": find_flops, "find_ms": find_ms,
-                "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts x max clock)"}
+                "flops_per_unit": {"step": F_STEP, "window_hit": F_HIT, "window_hits_per_step": WINDOW_HITS_PER_STEP,
+                                   "update": F_UPDATE, "scatter": F_MS, "seed_fit": F_SEED,
+                                   "source": "oracle operation census (oracle/flop_census.json)"},
+                "peak_note": f"{n_sm} SMs (device) x 128 FP32 lanes x 2 x 2070 MHz (unit counts x max clock)"}
 
     # plain per-event launches (no graph), same work
     plain = None

@@ -72,6 +72,9 @@ def lib():
                                          _P, _P, _P, _P, _P, _P]
             L.orc_replay.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
             L.orc_select_children.argtypes = [ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int, _P]
+            L.orc_census_step.argtypes = [_P, ctypes.c_double, _P, _P, ctypes.c_int, _P, _P, _P, _P]
+            L.orc_census_fit.argtypes = [_P, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
+            L.orc_census_transport.argtypes = [_P, _P, _P]
             L.orc_dedup.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_int, _P, _P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double]
@@ -260,7 +263,7 @@ def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=
     out_c2 = np.zeros(n)
     out_p = np.zeros((n, 6))
     out_C = np.zeros((n, 21))
-    cnt = np.zeros(8, np.int64)
+    cnt = np.zeros(9, np.int64)
     mc = batch.cfg["max_cands"] if max_cands is None else max_cands
     d = make_detector(det)
     cfg = make_config(mc, max_holes, chi2_cut)
@@ -273,7 +276,7 @@ def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=
     return dict(hits=out_hits, n_found=out_n, chi2=out_c2, p=out_p, C=out_C,
                 counters=dict(steps=int(cnt[0]), prop_calls=int(cnt[1]), updates=int(cnt[2]),
                               ms=int(cnt[3]), chi2_evals=int(cnt[4]), seeds=int(cnt[5]),
-                              children=int(cnt[6]), holes=int(cnt[7])))
+                              children=int(cnt[6]), holes=int(cnt[7]), window_hits=int(cnt[8])))
 
 
 def dedup(hits, n_hits, chi2, frac=0.5, brute=False, params=None, bz=0.0, deta=0.0, dphi=0.0, dpt=0.0):
@@ -376,3 +379,41 @@ def select_children(n_found, chi2, parent, kind, hit, max_cands):
     out = np.zeros(max(n, 1), np.int32)
     k = lib().orc_select_children(n, _ptr(nf), _ptr(c2), _ptr(pa), _ptr(kd), _ptr(ht), int(max_cands), _ptr(out))
     return out[:k].tolist()
+
+
+# ------------------------------------------------------------ operation census
+CENSUS_PARTS = ("propagate_transport", "frame_window", "hit_chi2", "update", "scatter")
+
+
+def census_step(det, p, C21, layer, m1, m2, align=(0.0, 0.0), chi2_cut=30.0):
+    """Operations of one finding step (orc_census_step): a [5][4] array, rows
+    CENSUS_PARTS, columns (adds, multiplies, divides, special functions);
+    None when the state does not cross the layer or a hit is on the far side."""
+    out = np.zeros(20, np.int64)
+    d = make_detector(det)
+    rc = lib().orc_census_step(ctypes.byref(d), float(chi2_cut), _ptr(_c(p, np.float64)), _ptr(_c(C21, np.float64)),
+                               int(layer), _ptr(_c(m1, np.float64)), _ptr(_c(m2, np.float64)),
+                               _ptr(_c(align, np.float64)), _ptr(out))
+    return None if rc != 0 else out.reshape(5, 4)
+
+
+def census_fit(det, p0, C21, raw, layers, align, ms_after_last=False):
+    """Operations of a Kalman fit over the hits raw [n][3] on layers [n]
+    (orc_census_fit): (adds, multiplies, divides, special functions), or None
+    when the fit fails."""
+    out = np.zeros(4, np.int64)
+    raw = _c(raw, np.float64)
+    d = make_detector(det)
+    rc = lib().orc_census_fit(ctypes.byref(d), _ptr(_c(p0, np.float64)), _ptr(_c(C21, np.float64)), raw.shape[0],
+                              _ptr(raw), _ptr(_c(layers, np.int32)), _ptr(_c(align, np.float64)),
+                              int(ms_after_last), _ptr(out))
+    return None if rc != 0 else out
+
+
+def census_transport(J, C21):
+    """Operations of one covariance transport (orc_census_transport): entries
+    of J exactly 0 or 1 are constants.  (adds, multiplies, divides, special)."""
+    out = np.zeros(4, np.int64)
+    lib().orc_census_transport(_ptr(_c(np.asarray(J, np.float64).reshape(36), np.float64)), _ptr(_c(C21, np.float64)),
+                               _ptr(out))
+    return out

@@ -35,6 +35,8 @@
 #include <cstdint>
 #include <cstring>
 #include <numeric>
+#include <map>
+#include <tuple>
 #include <vector>
 
 namespace {
@@ -162,6 +164,125 @@ inline DualB<R> atan2(const DualB<R>& y, const DualB<R>& x) {
   DualB<R> r; r.v = rnd<R>(std::atan2(y.v, x.v));
   for (int i = 0; i < g_nd; ++i) r.d[i] = rnd<R>((x.v * y.d[i] - y.v * x.d[i]) / r2);
   return r;
+}
+
+// ---------------------------------------------------------------- operation census
+// A counting scalar: each operation on Cn values is recorded as a node of a
+// computation graph.  Trivial operations are not recorded: a product with a
+// constant 0 is the constant 0, with a constant 1 (or -1) the other operand
+// (or its negation); a sum with a constant 0 the other operand; operations on
+// constants fold.  Identical operations on the same operands are one node.
+// The operations a set of results needs are the nodes that reach them; sign
+// changes and absolute values cost nothing, every other node one operation
+// (an add, multiply, divide or special function).  The finding and fitting
+// steps run unchanged on Cn through their templates; a symmetric matrix
+// result is taken from its upper triangle (see symmetrize).
+struct CnNode {
+  char op;
+  int a, b;
+};
+thread_local std::vector<CnNode> g_tape;
+thread_local std::map<std::tuple<char, int, int>, int> g_cse;
+
+struct Cn {
+  double v;
+  int id;  // a node of g_tape, or -1 for a constant (exactly v)
+  Cn() : v(0.0), id(-1) {}
+  Cn(double x) : v(x), id(-1) {}  // NOLINT implicit: a constant
+};
+inline double val(const Cn& x) { return x.v; }
+inline Cn cn_input(double x) {
+  g_tape.push_back({'i', -1, -1});
+  Cn r(x);
+  r.id = (int)g_tape.size() - 1;
+  return r;
+}
+inline Cn cn_node(char op, const Cn& a, const Cn& b, double v, bool commutes) {
+  int x = a.id, y = b.id;
+  if (commutes && x > y) std::swap(x, y);
+  const auto key = std::make_tuple(op, x, y);
+  const auto it = g_cse.find(key);
+  Cn r(v);
+  if (it != g_cse.end()) {
+    r.id = it->second;
+  } else {
+    g_tape.push_back({op, x, y});
+    r.id = (int)g_tape.size() - 1;
+    g_cse.emplace(key, r.id);
+  }
+  return r;
+}
+inline bool cn_is(const Cn& a, double c) { return a.id < 0 && a.v == c; }
+inline Cn operator-(const Cn& a) {
+  if (a.id < 0) return Cn(-a.v);
+  return cn_node('n', a, Cn(), -a.v, false);
+}
+inline Cn operator+(const Cn& a, const Cn& b) {
+  if (a.id < 0 && b.id < 0) return Cn(a.v + b.v);
+  if (cn_is(a, 0.0)) return b;
+  if (cn_is(b, 0.0)) return a;
+  return cn_node('+', a, b, a.v + b.v, true);
+}
+inline Cn operator-(const Cn& a, const Cn& b) {
+  if (a.id < 0 && b.id < 0) return Cn(a.v - b.v);
+  if (cn_is(b, 0.0)) return a;
+  if (cn_is(a, 0.0)) return -b;
+  return cn_node('-', a, b, a.v - b.v, false);
+}
+inline Cn operator*(const Cn& a, const Cn& b) {
+  if (a.id < 0 && b.id < 0) return Cn(a.v * b.v);
+  if (cn_is(a, 0.0) || cn_is(b, 0.0)) return Cn(0.0);
+  if (cn_is(a, 1.0)) return b;
+  if (cn_is(b, 1.0)) return a;
+  if (cn_is(a, -1.0)) return -b;
+  if (cn_is(b, -1.0)) return -a;
+  return cn_node('*', a, b, a.v * b.v, true);
+}
+inline Cn operator/(const Cn& a, const Cn& b) {
+  if (a.id < 0 && b.id < 0) return Cn(a.v / b.v);
+  if (cn_is(a, 0.0)) return Cn(0.0);
+  if (cn_is(b, 1.0)) return a;
+  return cn_node('/', a, b, a.v / b.v, false);
+}
+inline Cn& operator+=(Cn& a, const Cn& b) { a = a + b; return a; }
+inline Cn& operator-=(Cn& a, const Cn& b) { a = a - b; return a; }
+inline Cn cn_fn(char op, const Cn& a, double v) { return a.id < 0 ? Cn(v) : cn_node(op, a, Cn(), v, false); }
+inline Cn sin(const Cn& a) { return cn_fn('s', a, std::sin(a.v)); }
+inline Cn cos(const Cn& a) { return cn_fn('c', a, std::cos(a.v)); }
+inline Cn atan(const Cn& a) { return cn_fn('t', a, std::atan(a.v)); }
+inline Cn sqrt(const Cn& a) { return cn_fn('q', a, std::sqrt(a.v)); }
+inline Cn log(const Cn& a) { return cn_fn('l', a, std::log(a.v)); }
+inline Cn fabs(const Cn& a) { return cn_fn('a', a, std::fabs(a.v)); }
+inline Cn atan2(const Cn& y, const Cn& x) {
+  if (y.id < 0 && x.id < 0) return Cn(std::atan2(y.v, x.v));
+  return cn_node('2', y, x, std::atan2(y.v, x.v), false);
+}
+
+// Operations needed for the results `outs` (node ids; constants need none):
+// counts[0] adds and subtracts, [1] multiplies, [2] divides, [3] special
+// functions (sine, cosine, arctangent, square root, logarithm).
+void cn_count(const std::vector<int>& outs, long long counts[4]) {
+  std::vector<char> seen(g_tape.size(), 0);
+  std::vector<int> stack;
+  for (int o : outs)
+    if (o >= 0) stack.push_back(o);
+  for (int k = 0; k < 4; ++k) counts[k] = 0;
+  while (!stack.empty()) {
+    const int n = stack.back();
+    stack.pop_back();
+    if (seen[n]) continue;
+    seen[n] = 1;
+    const CnNode& nd = g_tape[n];
+    switch (nd.op) {
+      case '+': case '-': counts[0]++; break;
+      case '*': counts[1]++; break;
+      case '/': counts[2]++; break;
+      case 's': case 'c': case 't': case 'q': case 'l': case '2': counts[3]++; break;
+      default: break;  // inputs, sign changes, absolute values
+    }
+    if (nd.a >= 0) stack.push_back(nd.a);
+    if (nd.b >= 0) stack.push_back(nd.b);
+  }
 }
 
 using std::atan;
@@ -331,6 +452,18 @@ bool propagate(double bz, const T p[6], double R, T q[6], T J[6][6]) {
   return true;
 }
 
+// C <- (out + out^T) / 2.  For the operation census a symmetric result is
+// computed once: C takes the upper triangle of out (no operation).
+template <class T>
+void symmetrize(const T out[6][6], T C[6][6]) {
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) C[i][j] = 0.5 * (out[i][j] + out[j][i]);
+}
+inline void symmetrize(const Cn out[6][6], Cn C[6][6]) {
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) C[i][j] = i <= j ? out[i][j] : out[j][i];
+}
+
 template <class T>
 void transport(const T J[6][6], T C[6][6]) {  // C <- J C J^T
   T JC[6][6], out[6][6];
@@ -346,8 +479,7 @@ void transport(const T J[6][6], T C[6][6]) {  // C <- J C J^T
       for (int k = 0; k < 6; ++k) acc += JC[i][k] * J[j][k];
       out[i][j] = acc;
     }
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) C[i][j] = 0.5 * (out[i][j] + out[j][i]);
+  symmetrize(out, C);
 }
 
 // ---------------------------------------------------------------- measurement
@@ -416,8 +548,7 @@ void kf_update(T p[6], T C[6][6], const Meas<T>& m) {
   T out[6][6];
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) out[i][j] = C[i][j] - (K[i][0] * HC[0][j] + K[i][1] * HC[1][j]);
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) C[i][j] = 0.5 * (out[i][j] + out[j][i]);
+  symmetrize(out, C);
 }
 
 // Multiple scattering in a thin layer of x0 radiation lengths at the current
@@ -531,8 +662,8 @@ void correct_hit(const T raw[3], const T& a_rphi, const T& a_z, double R, T m[3]
 // Kalman fit over hits (raw positions, per-hit layer), from prior (p0, C0)
 // placed at the first hit: no propagation before the first update, MS after
 // each update except (optionally) the last.  Returns 0 or a negative status.
-template <class T>
-int fit_track(const Det& det, const T p0[6], const double C0[6][6], int n, const T (*raw)[3],
+template <class T, class TC>
+int fit_track(const Det& det, const T p0[6], const TC C0[6][6], int n, const T (*raw)[3],
               const int* layers, const T (*align)[2], bool ms_after_last, T p[6], T C[6][6],
               T& chi2, T* chi2_each = nullptr) {
   for (int i = 0; i < 6; ++i) {
@@ -621,6 +752,9 @@ struct Counters {
   long long seeds;
   long long children;     // children ranked
   long long holes;        // kept hole children (scattering without an update)
+  long long window_hits;  // hits inside the bounding box of the chi2 < cut ellipse of the
+                          // prediction (|r_rphi| and |r_z| within sqrt(cut S) each): the
+                          // method's search window, implementation-independent
 };
 
 void seed_state(const double* params, const double* cov, long stride, long i, double p[6],
@@ -646,7 +780,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
       lays[k] = hlayer[sh[k]];
     }
     double chi2;
-    int st = fit_track<double>(det, p0, C0, 3, raw, lays, align, true, c0.p, c0.C, chi2);
+    int st = fit_track<double, double>(det, p0, C0, 3, raw, lays, align, true, c0.p, c0.C, chi2);
     c0.n_found = 3;
     c0.n_holes = 0;
     c0.chi2 = chi2;
@@ -696,6 +830,9 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
         Meas<double> ms;
         ++cnt.chi2_evals;
         if (!measure(pc.p, pc.C, m, vr, vz, ms)) continue;
+        if (std::fabs(ms.r[0]) < std::sqrt(cfg.chi2_cut * ms.S[0][0]) &&
+            std::fabs(ms.r[1]) < std::sqrt(cfg.chi2_cut * ms.S[1][1]))
+          ++cnt.window_hits;
         if (ms.chi2 < cfg.chi2_cut) {
           children.push_back({c.n_found + 1, c.chi2 + ms.chi2, (int)r, KIND_HIT, hidx, 0});
           ++n_children;
@@ -930,7 +1067,7 @@ int orc_fit(const orc_detector* dptr, int n_tracks, const double* prior_p, const
       raw[3 * k] = hx[hidx]; raw[3 * k + 1] = hy[hidx]; raw[3 * k + 2] = hz[hidx];
       lays[k] = hlayer[hidx];
     }
-    status[t] = fit_track<double>(det, p0, C0, n, reinterpret_cast<const double(*)[3]>(raw.data()),
+    status[t] = fit_track<double, double>(det, p0, C0, n, reinterpret_cast<const double(*)[3]>(raw.data()),
                                   lays.data(), al, ms_after_last != 0, p, C, c2,
                                   chi2_each ? chi2_each + (size_t)t * max_len : nullptr);
     for (int k = 0; k < 6; ++k) p_out[6 * t + k] = p[k];
@@ -980,7 +1117,7 @@ int fit_grad_impl(const orc_detector* dptr, int n_tracks, const double* prior_p,
       alv[2 * i + 1] = D(align[2 * i + 1]), alv[2 * i + 1].d[6 + 3 * n + 2 * i + 1] = 1.0;
     }
     D p[6], C[6][6], c2;
-    const int st = fit_track<D>(det, p0, C0, n, reinterpret_cast<const D(*)[3]>(rawv.data()),
+    const int st = fit_track<D, double>(det, p0, C0, n, reinterpret_cast<const D(*)[3]>(rawv.data()),
                                 lays.data(), reinterpret_cast<const D(*)[2]>(alv.data()),
                                 false, p, C, c2);
     if (st != 0) { g_nd = 0; return -2 - t; }
@@ -1023,7 +1160,7 @@ int orc_fit_grad32(const orc_detector* dptr, int n_tracks, const double* prior_p
 // Combinatorial finding for seeds [s_begin, s_end) of one event.  Hits are
 // the event's arrays (event-local indices); seeds are structure-of-arrays with
 // the given stride; seed_hits [3][stride].  out_hits [n][n_layers] (padded -1),
-// out_p [n][6], out_C [n][21].  counters: see Counters.  brute != 0 tests every
+// out_p [n][6], out_C [n][21].  counters [9]: see Counters.  brute != 0 tests every
 // hit of the layer instead of the exact z pre-selection.
 int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits, const double* hx,
                    const double* hy, const double* hz, const int* hlayer, const double* params,
@@ -1058,9 +1195,143 @@ int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits,
   if (counters) {
     counters[0] += cnt.steps; counters[1] += cnt.prop_calls; counters[2] += cnt.updates;
     counters[3] += cnt.ms; counters[4] += cnt.chi2_evals; counters[5] += cnt.seeds;
-    counters[6] += cnt.children; counters[7] += cnt.holes;
+    counters[6] += cnt.children; counters[7] += cnt.holes; counters[8] += cnt.window_hits;
   }
   return 0;
+}
+
+// Operation census of one finding step (see Cn): a candidate (p [6], C [21])
+// propagated to layer L, two hits m1, m2 [3] (raw positions, corrected by the
+// alignment align [2] of L as in the finding) tested, the first kept and
+// updated, then the layer's scattering (and energy loss).  out[4 k + c] holds
+// (adds, multiplies, divides, special functions) for
+//   k = 0: propagation and covariance transport (results: the predicted state
+//          and the upper triangle of its covariance);
+//   k = 1: the measurement frame and the z window of the pre-selection (the
+//          hit-independent part of a chi2 test);
+//   k = 2: one hit's chi2 (alignment correction, residual, quadratic form);
+//   k = 3: the Kalman update of a kept hit-child;
+//   k = 4: the scattering applied to a kept child.
+// Alignment, state and hits are inputs of the count.  Returns 0, -1 without a
+// crossing of L, -2 for a far-side hit.
+int orc_census_step(const orc_detector* dptr, double chi2_cut, const double* p, const double* C21, int L,
+                    const double* m1, const double* m2, const double* align, long long* out) {
+  const Det det = to_det(dptr);
+  g_tape.clear();
+  g_cse.clear();
+  Cn pc[6], Cc[6][6], q[6], J[6][6];
+  for (int k = 0; k < 6; ++k) pc[k] = cn_input(p[k]);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) Cc[a][b] = Cc[b][a] = cn_input(C21[sym_index(a, b)]);
+  const Cn al0 = cn_input(align[0]), al1 = cn_input(align[1]);
+  const double R = det.radius[L];
+  if (!propagate(det.bz, pc, R, q, J)) return -1;
+  transport(J, Cc);
+  std::vector<int> outs;
+  for (int k = 0; k < 6; ++k) outs.push_back(q[k].id);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(Cc[a][b].id);
+  long long c0[4], c1[4], c2[4], c3[4], c4[4];
+  cn_count(outs, c0);
+  // the z window of the chi2 pre-selection, as the finding forms it
+  const double vr = det.sigma_rphi * det.sigma_rphi, vz = det.sigma_z * det.sigma_z;
+  const Cn w = sqrt(chi2_cut * (Cc[2][2] + vz)) + 1e-9;
+  const Cn lo = q[2] + al1 - w, hi = q[2] + al1 + w;
+  outs.push_back(lo.id);
+  outs.push_back(hi.id);
+  Cn r1[3], r2[3], mm1[3], mm2[3];
+  for (int k = 0; k < 3; ++k) r1[k] = cn_input(m1[k]), r2[k] = cn_input(m2[k]);
+  correct_hit(r1, al0, al1, R, mm1);
+  correct_hit(r2, al0, al1, R, mm2);
+  Meas<Cn> ms1, ms2;
+  if (!measure(q, Cc, mm1, vr, vz, ms1) || !measure(q, Cc, mm2, vr, vz, ms2)) return -2;
+  outs.push_back(ms1.chi2.id);
+  cn_count(outs, c1);
+  outs.push_back(ms2.chi2.id);
+  cn_count(outs, c2);
+  Cn pu[6], Cu[6][6];
+  for (int k = 0; k < 6; ++k) pu[k] = q[k];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) Cu[a][b] = Cc[a][b];
+  kf_update(pu, Cu, ms1);
+  const size_t n_before = outs.size();
+  for (int k = 0; k < 6; ++k) outs.push_back(pu[k].id);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(Cu[a][b].id);
+  cn_count(outs, c3);
+  add_ms(pu, Cu, x0_at(det, L, pu[2]));
+  add_eloss(pu, Cu, det.eloss[L]);
+  outs.resize(n_before);
+  for (int k = 0; k < 6; ++k) outs.push_back(pu[k].id);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(Cu[a][b].id);
+  cn_count(outs, c4);
+  for (int c = 0; c < 4; ++c) {
+    const long long hit = c2[c] - c1[c];
+    out[0 + c] = c0[c];
+    out[4 + c] = c1[c] - c0[c] - hit;
+    out[8 + c] = hit;
+    out[12 + c] = c3[c] - c2[c];
+    out[16 + c] = c4[c] - c3[c];
+  }
+  g_tape.clear();
+  g_cse.clear();
+  return 0;
+}
+
+// Operation census of one covariance transport C <- J C J^T (the upper
+// triangle of the result): entries of J equal to exactly 0 or 1 are constants,
+// the others and C [21] inputs.  out4 as for orc_census_step.
+int orc_census_transport(const double* J36, const double* C21, long long* out4) {
+  g_tape.clear();
+  g_cse.clear();
+  Cn J[6][6], C[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      const double v = J36[6 * i + j];
+      J[i][j] = (v == 0.0 || v == 1.0) ? Cn(v) : cn_input(v);
+    }
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) C[a][b] = C[b][a] = cn_input(C21[sym_index(a, b)]);
+  transport(J, C);
+  std::vector<int> outs;
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(C[a][b].id);
+  cn_count(outs, out4);
+  g_tape.clear();
+  g_cse.clear();
+  return 0;
+}
+
+// Operation census of a Kalman fit (as orc_fit, scattering after the last hit
+// if ms_after_last) over n hits raw [n][3] on layers [n], from the prior (p0
+// [6], C0 [21]) with the layers' alignment align [n_layers][2]; prior, hits and
+// alignment are inputs of the count.  out4: (adds, multiplies, divides,
+// special functions) of the final state, its covariance (upper triangle) and
+// the chi2 sum.  Returns the fit's status.
+int orc_census_fit(const orc_detector* dptr, const double* p0, const double* C21, int n, const double* raw,
+                   const int* layers, const double* align, int ms_after_last, long long* out4) {
+  const Det det = to_det(dptr);
+  g_tape.clear();
+  g_cse.clear();
+  Cn pc[6], C0[6][6], p[6], C[6][6], chi2;
+  for (int k = 0; k < 6; ++k) pc[k] = cn_input(p0[k]);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) C0[a][b] = C0[b][a] = cn_input(C21[sym_index(a, b)]);
+  std::vector<Cn> rv(3 * (size_t)n), av(2 * (size_t)det.n_layers);
+  for (int k = 0; k < 3 * n; ++k) rv[k] = cn_input(raw[k]);
+  for (int k = 0; k < 2 * det.n_layers; ++k) av[k] = cn_input(align[k]);
+  const int st = fit_track<Cn, Cn>(det, pc, C0, n, reinterpret_cast<const Cn(*)[3]>(rv.data()), layers,
+                                   reinterpret_cast<const Cn(*)[2]>(av.data()), ms_after_last != 0, p, C, chi2);
+  std::vector<int> outs;
+  for (int k = 0; k < 6; ++k) outs.push_back(p[k].id);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(C[a][b].id);
+  outs.push_back(chi2.id);
+  cn_count(outs, out4);
+  g_tape.clear();
+  g_cse.clear();
+  return st;
 }
 
 // The selection step alone, for hand-made children (n of them, fields as in
@@ -1102,7 +1373,7 @@ int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, con
     raw[k][0] = hx[sh[k]]; raw[k][1] = hy[sh[k]]; raw[k][2] = hz[sh[k]];
     lays[k] = hlayer[sh[k]];
   }
-  int st = fit_track<double>(det, p0, C0, 3, raw, lays, al, true, p, C, chi2);
+  int st = fit_track<double, double>(det, p0, C0, 3, raw, lays, al, true, p, C, chi2);
   *n_found = 3;
   for (int l = 0; l < L; ++l) chi2_layer[l] = 0.0;
   if (st != 0) { *chi2sum = chi2; return st; }
