@@ -168,6 +168,21 @@ def max_over_ranks(value, device):
     return float(t.item())
 
 
+def sum_alignment_over_ranks(g_align, chi2_total, device):
+    """The one exchange of the multi-GPU path: every rank fits its own events,
+    and the alignment gradient [n_layers][2] and the summed chi2 are added
+    over ranks (one all-reduce of 2 n_layers + 1 values).  Returns the sums;
+    the identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    v = np.concatenate([np.asarray(g_align, np.float64).ravel(), [float(chi2_total)]])
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.from_numpy(v).to(device)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        v = t.cpu().numpy()
+    return v[:-1].reshape(np.shape(g_align)), float(v[-1])
+
+
 def make_inputs(name, rank, n_events=None):
     from synth import make_batch
     # per-rank distinct events: shift the configuration seed by the rank
@@ -358,6 +373,17 @@ def main():
     total_ms = max_over_ranks(total_ms, dev)
     seeds_all = n_seeds * world
     value = seeds_all * args.steps / (total_ms / 1e3)
+
+    # the one exchange of the multi-GPU path, after the timed steps: the
+    # alignment gradient and the fit chi2 summed over ranks
+    from paper_1906_11744_gb300 import kf_get_gradient
+    g_rank = np.zeros((b.det.n_layers, 2), np.float32)
+    kf_get_gradient(t.ctx, g_align=g_rank, stream=stream)
+    fit_last = t.get_fit(stream=stream)
+    chi2_rank = float(fit_last["chi2"][fit_last["status"] == 0].astype(np.float64).sum())
+    g_sum, chi2_sum = sum_alignment_over_ranks(g_rank, chi2_rank, dev)
+    exchange = {"values": int(g_sum.size + 1), "chi2_total": chi2_sum, "g_align_abs_max": float(np.abs(g_sum).max()),
+                "form": "all-reduce (sum) of the alignment gradient and the fit chi2 over ranks, after the timed steps"}
     steps_per_s = counters["steps"] * world * args.steps / (total_ms / 1e3)
 
     # roofline of the find kernel (ALU bound: FP32 FMA pipe)
@@ -609,6 +635,7 @@ def main():
                "e2e": e2e,
                "gpu_launches": n_kernels * args.steps,
                "roofline": roofline,
+               "alignment_exchange": exchange,
                "dup_handling": dup,
                "material_map": mat,
                "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample",
