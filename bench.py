@@ -275,6 +275,73 @@ def run_reference(args):
     return 0
 
 
+def mixed_pileup(args, rank, dev, stream, flush_l2):
+    """The batching comparison on 64 events of uneven pileup (20-200, 1,000 to
+    10,000 seeds each, N = 6): one captured graph over the batch (launch shape
+    from the autotuner, whose full table is returned) against plain
+    per-event launches without a graph, the same step (bin, find, duplicate
+    removal, fit, adjoint) and L2 flush as the headline."""
+    import torch
+    from paper_1906_11744_gb300 import KF_FIT_FOUND
+    b = make_inputs("c2", rank)
+    d_in = {k: torch.from_numpy(np.ascontiguousarray(getattr(b, k))).to(dev)
+            for k in ("x", "y", "z", "layer", "params", "cov", "seed_hits")}
+
+    def loaded(**cfg):
+        t = tracker_for(b, **cfg)
+        t.load_hits(b.hit_off, d_in["x"], d_in["y"], d_in["z"], d_in["layer"], stream)
+        t.load_seeds(b.seed_off, d_in["params"], d_in["cov"], d_in["seed_hits"], stream)
+        t.set_alignment(b.align, stream)
+        return t
+
+    def timed(step):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        ea = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        eb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush_l2()
+            ea[k].record(stream)
+            step()
+            eb[k].record(stream)
+        stream.synchronize()
+        return max_over_ranks(sum(a.elapsed_time(c) for a, c in zip(ea, eb)), dev) / args.steps
+
+    tb = loaded(persistent=1, per_event=0)
+    tune = tb.autotune(stream)
+    best = tune[np.argmin(tune[:, 4])]
+    tb.close()
+    tb = loaded(persistent=1, per_event=0, lanes_per_seed=int(best[0]), block_threads=int(best[1]),
+                find_regcap=int(best[3]))
+    tb.capture_graph(with_adjoint=True, stream=stream)
+    ms_b = timed(lambda: tb.launch_graph(stream))
+    tb.close()
+    tp = loaded(persistent=0, per_event=1, lanes_per_seed=int(best[0]))
+    g_plain = torch.empty((b.det.n_layers, 2), dtype=torch.float32, device=dev)
+
+    def plain_step():
+        tp.find_tracks(stream)
+        tp.remove_duplicates(stream)
+        tp.fit_tracks(KF_FIT_FOUND, stream=stream)
+        tp.fit_adjoint(g_plain, stream=stream)
+
+    ms_p = timed(plain_step)
+    tp.close()
+    n = b.n_seeds * (int(os.environ.get("WORLD_SIZE", "1")))
+    per_ev = np.diff(b.seed_off)
+    return {"workload": workload_desc("c2"), "seeds_per_step": int(b.n_seeds),
+            "seeds_per_event_min_max": [int(per_ev.min()), int(per_ev.max())],
+            "batched": {"value": n / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b,
+                        "form": "one CUDA graph per step over the 64 events, persistent finding kernel"},
+            "plain": {"value": n / (ms_p / 1e3), "unit": UNIT, "ms_per_step": ms_p,
+                      "form": "per-event launches of bin/find/dedup, one fit and one adjoint launch, no graph"},
+            "batched_over_plain": ms_p / ms_b,
+            "autotune": {"columns": ["lanes_per_seed", "block_threads", "persistent", "register_cap", "find_ms"],
+                         "rows": [[float(v) for v in r] for r in tune],
+                         "pick": [float(v) for v in best]}}
+
+
 def workload_desc(name):
     from synth.events import CONFIGS
     c = CONFIGS[name]
@@ -299,6 +366,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dup", action="store_true", help="skip the duplicate-handling step")
     ap.add_argument("--no-material", action="store_true", help="skip the material-map step")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-pileup (64 events, PU 20-200) step")
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--ref-events", type=int, default=20)
@@ -439,6 +507,11 @@ def main():
                  "ms_per_step": pms / args.steps,
                  "form": "per-event launches of bin/find/dedup, one fit and one adjoint launch, no graph"}
         tp.close()
+
+    # mixed pileup: 64 events of pileup 20-200, batched graph against plain per-event launches
+    mixed = None
+    if not args.no_mixed and args.config == "c4":
+        mixed = mixed_pileup(args, rank, dev, stream, flush_l2)
 
     # the same step with seed cleaning and the kinematic pre-cuts of duplicate removal
     dup = None
@@ -636,6 +709,7 @@ def main():
                "gpu_launches": n_kernels * args.steps,
                "roofline": roofline,
                "alignment_exchange": exchange,
+               "mixed_pileup": mixed,
                "dup_handling": dup,
                "material_map": mat,
                "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample",

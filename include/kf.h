@@ -220,9 +220,10 @@ int kf_launch_graph(kf_ctx* ctx, void* stream);
  * g_hits float [n_hits][3], g_seed float [6][n_seeds]; any may be NULL. */
 int kf_get_gradient(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs, void* stream);
 
-/* Time every lanes-per-seed / block-size / register-budget / launch-form
- * choice of the finding kernel on the loaded inputs and keep the fastest in
- * the context.  Synchronous.  results (may be NULL) receives up to
+/* Time every lanes-per-seed (4..16, >= max_cands) / block-size (32, 64, 128,
+ * 256 threads: candidate tiles of that many lanes) / register-budget /
+ * launch-form choice of the finding kernel on the loaded inputs and keep the
+ * fastest in the context.  Synchronous.  results (may be NULL) receives up to
  * max_results rows of 5 floats (lanes, threads, persistent, register cap, ms). */
 int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, void* stream);
 

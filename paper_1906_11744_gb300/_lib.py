@@ -249,7 +249,7 @@ def kf_launch_graph(ctx, stream=None):
     _check(ctx, load().kf_launch_graph(ctx, _stream(stream)), "kf_launch_graph")
 
 
-def kf_autotune(ctx, stream=None, max_results=64):
+def kf_autotune(ctx, stream=None, max_results=128):
     res = np.zeros((max_results, 5), np.float32)
     n = ctypes.c_int(0)
     rc = load().kf_autotune(ctx, res.ctypes.data_as(_P), max_results, ctypes.byref(n), _stream(stream))

@@ -1063,7 +1063,8 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
     return fail(ctx, KF_ERR_STATE, "kf_autotune: load hits and seeds first");
   cudaStream_t st = S(stream);
   const int lane_opts[] = {4, 6, 8, 10, 12, 16};
-  const int thread_opts[] = {64, 128, 256};
+  // candidate tiles of 32 to 256 threads (one lane per candidate slot)
+  const int thread_opts[] = {32, 64, 128, 256};
   const int saved_lanes = ctx->lanes, saved_threads = ctx->threads, saved_pers = ctx->persistent,
             saved_bps = ctx->blocks_per_sm, saved_rc = ctx->regcap;
   float best = 1e30f;
