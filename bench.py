@@ -194,9 +194,7 @@ def make_inputs(name, rank, n_events=None):
 def tracker_for(b, **cfg):
     from paper_1906_11744_gb300 import Tracker, make_config, make_detector
     d = b.det
-    if any(getattr(d, "eloss", ()) or ()):
-        raise ValueError("the CUDA path does not apply energy loss; this detector sets it")
-    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z)
+    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None))
     c = dict(max_cands=b.cfg["max_cands"])
     c.update(cfg)
     return Tracker(det, make_config(**c))

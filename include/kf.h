@@ -76,6 +76,14 @@ typedef struct {
   float bz;                     /* field, tesla (0 = straight tracks) */
   float sigma_rphi;             /* hit resolution along r-phi, cm */
   float sigma_z;                /* hit resolution along z, cm */
+  /* Mean ionization energy loss of each layer at normal incidence for
+   * beta -> 1, GeV (>= 0; 0 = none).  Sec. 3: the material description also
+   * serves energy loss.  Applied after each layer's scattering: dE = e f /
+   * beta^2 with f = 1/|sin(theta) cos(phi - phi_p)| the scattering's path
+   * factor (phi_p the position angle) and beta from the pion mass; dE is at
+   * most (E - m)/2; q/pT is scaled by p/p' and the covariance carried through
+   * the Jacobian of that map.  Straggling is not modelled. */
+  float eloss[KF_MAX_LAYERS];
 } kf_detector;
 
 /* Algorithm settings (Sec. 2 and Sec. 4.3: windows, scores, duplicate cuts). */

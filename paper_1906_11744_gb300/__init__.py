@@ -43,12 +43,15 @@ from ._lib import (  # noqa: F401
 )
 
 
-def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1) -> kf_detector:
+def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1, eloss=None) -> kf_detector:
+    """Detector geometry (include/kf.h, kf_detector); eloss: mean ionization
+    loss per layer at normal incidence for beta -> 1 (GeV; None: none)."""
     d = kf_detector()
     d.n_layers = len(radius)
     for i, r in enumerate(radius):
         d.radius[i] = float(r)
         d.x0[i] = float(x0[i])
+        d.eloss[i] = float(eloss[i]) if eloss is not None and len(eloss) else 0.0
     d.z_max, d.bz, d.sigma_rphi, d.sigma_z = float(z_max), float(bz), float(sigma_rphi), float(sigma_z)
     return d
 

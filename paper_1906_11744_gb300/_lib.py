@@ -35,7 +35,8 @@ KF_MAX_MATERIAL_NODES = 4096
 class kf_detector(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int), ("radius", ctypes.c_float * KF_MAX_LAYERS),
                 ("x0", ctypes.c_float * KF_MAX_LAYERS), ("z_max", ctypes.c_float),
-                ("bz", ctypes.c_float), ("sigma_rphi", ctypes.c_float), ("sigma_z", ctypes.c_float)]
+                ("bz", ctypes.c_float), ("sigma_rphi", ctypes.c_float), ("sigma_z", ctypes.c_float),
+                ("eloss", ctypes.c_float * KF_MAX_LAYERS)]
 
 
 class kf_config(ctypes.Structure):

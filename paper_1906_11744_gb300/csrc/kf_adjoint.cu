@@ -37,6 +37,98 @@
 
 namespace kfg {
 
+// Forward-mode derivatives in six directions (the state's parameters): the
+// value v and d[k] = dv/dp_k.  The reverse of the energy-loss step takes the
+// derivatives of its Jacobian row through eloss_row on this scalar.
+template <class S>
+struct Dir6 {
+  S v, d[6];
+  __device__ Dir6() : v(S(0)) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[k] = S(0);
+  }
+  __device__ Dir6(S x) : v(x) {  // NOLINT implicit: a constant
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[k] = S(0);
+  }
+};
+template <class S>
+__device__ __forceinline__ Dir6<S> operator+(const Dir6<S>& a, const Dir6<S>& b) {
+  Dir6<S> r(a.v + b.v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> operator-(const Dir6<S>& a, const Dir6<S>& b) {
+  Dir6<S> r(a.v - b.v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> operator-(const Dir6<S>& a) {
+  Dir6<S> r(-a.v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> operator*(const Dir6<S>& a, const Dir6<S>& b) {
+  Dir6<S> r(a.v * b.v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = kfma(a.d[k], b.v, a.v * b.d[k]);
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> kfma(const Dir6<S>& a, const Dir6<S>& b, const Dir6<S>& c) {
+  Dir6<S> r(kfma(a.v, b.v, c.v));
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = kfma(a.d[k], b.v, kfma(a.v, b.d[k], c.d[k]));
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> kdiv(const Dir6<S>& a, const Dir6<S>& b) {
+  Dir6<S> r(kdiv(a.v, b.v));
+  const S ib = kdiv(S(1), b.v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> ksqrt(const Dir6<S>& a) {
+  Dir6<S> r(ksqrt(a.v));
+  const S h = kdiv(S(0.5), r.v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * h;
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> krsqrt(const Dir6<S>& a) {
+  Dir6<S> r(krsqrt(a.v));
+  const S h = S(-0.5) * r.v * r.v * r.v;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.d[k] = a.d[k] * h;
+  return r;
+}
+template <class S>
+__device__ __forceinline__ Dir6<S> kabs(const Dir6<S>& a) { return a.v < S(0) ? -a : a; }
+template <class S>
+__device__ __forceinline__ void ksincos(const Dir6<S>& a, Dir6<S>* s, Dir6<S>* c) {
+  S sv, cv;
+  ksincos(a.v, &sv, &cv);
+  s->v = sv;
+  c->v = cv;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    s->d[k] = cv * a.d[k];
+    c->d[k] = -sv * a.d[k];
+  }
+}
+template <class S>
+__device__ __forceinline__ S kval(const Dir6<S>& a) { return a.v; }
+
+
 namespace {
 
 constexpr float ADJ_CAREFUL_COS = ADJOINT_CAREFUL_COS;
@@ -188,6 +280,63 @@ __device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T dx0dz, T b44, T 
   v[2] = kfma(W * bt, dx0dz / x0, v[2]);
 }
 
+// Reverse of add_eloss at the state (p, C) it acted on.  In: pb, Cb (full
+// symmetric) the adjoints after it; out: the adjoints before it.  With F the
+// identity but for row 3 = u(p) (eloss_row) and L = pb . p' + <Cb, F C F^T>:
+//   Cbar = F^T Cb F;
+//   pbar_k = pb_k (k != 3) + pb_3 u_k + sum_j ubar_j du_j/dp_k,
+//   ubar_j = 2 sum_(b != 3) Cb_3b C_jb + 2 Cb_33 (C u)_j,
+// du/dp in forward mode (Dir6).
+template <class S>
+__device__ __noinline__ void eloss_vjp(const S (&p)[6], const S (&C)[21], S e, S (&pb)[6], S (&Cb)[6][6]) {
+  Dir6<S> pd[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    pd[k] = Dir6<S>(p[k]);
+    pd[k].d[k] = S(1);
+  }
+  Dir6<S> k1, u[6];
+  eloss_row<Dir6<S>>(pd, Dir6<S>(e), k1, u);
+  S uv[6], Cu[6], ub[6], pn[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) uv[j] = u[j].v;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    S a = S(0);
+#pragma unroll
+    for (int b = 0; b < 6; ++b) a = kfma(C[S6(j, b)], uv[b], a);
+    Cu[j] = a;
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    S a = Cb[3][3] * Cu[j];
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+      if (b != 3) a = kfma(Cb[3][b], C[S6(j, b)], a);
+    ub[j] = S(2) * a;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    S a = kfma(pb[3], uv[k], k == 3 ? S(0) : pb[k]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a = kfma(ub[j], u[j].d[k], a);
+    pn[k] = a;
+  }
+  // Cbar = F^T Cb F: X = Cb F (column k: Cb_:k for k != 3, plus Cb_:3 u_k),
+  // then F^T X (row k: X_k: for k != 3, plus u_k X_3:)
+  S X[6][6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) X[i][k] = kfma(Cb[i][3], uv[k], k == 3 ? S(0) : Cb[i][k]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int m = 0; m < 6; ++m) Cb[k][m] = kfma(uv[k], X[3][m], k == 3 ? S(0) : X[k][m]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) pb[k] = pn[k];
+}
+
 template <class S>
 struct Hit {
   S mx, my, mz;   // corrected position
@@ -226,7 +375,10 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
   S r0, r1;
   if (!residual<S>(p, f, h.mx, h.my, h.mz, r0, r1)) return KF_FIT_FAR_SIDE;
   kf_update<S>(p, C, f, r0, r1);
-  if (!last) add_ms<S>(p, C, x0_at<S>(g, h.L, p[2]));
+  if (!last) {
+    add_ms<S>(p, C, x0_at<S>(g, h.L, p[2]));
+    add_eloss<S>(p, C, (S)g.eloss[h.L]);
+  }
   return KF_FIT_OK;
 }
 
@@ -270,11 +422,24 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
 #pragma unroll
   for (int i = 0; i < 6; ++i) pu[i] = q[i] + kfma(U[i][0], sir0, U[i][1] * sir1);
 
-  // ---- reverse: scattering, C_out = C_upd + Q(p_upd)
+  // ---- reverse: energy loss and scattering, C_out = F (C_upd + Q(p_upd)) F^T
   S pbu[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) pbu[i] = pb[i];
   if (!last) {
+    const S e = (S)g.eloss[h.L];
+    if (e > S(0) && pu[3] != S(0)) {
+      // the state the loss acted on: the update's covariance plus the scattering
+      S Cm[21];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const S k0 = kfma(U[i][0], si00, U[i][1] * si01), k1 = kfma(U[i][0], si01, U[i][1] * si11);
+#pragma unroll
+        for (int j = i; j < 6; ++j) Cm[S6(i, j)] = Cp[S6(i, j)] - kfma(k0, U[j][0], k1 * U[j][1]);
+      }
+      add_ms<S>(pu, Cm, x0_at<S>(g, h.L, pu[2]));
+      eloss_vjp<S>(pu, Cm, e, pbu, Cb);
+    }
     S dx0dz;
     const S x0 = x0_at<S>(g, h.L, pu[2], &dx0dz);
     ms_vjp<S>(pu, x0, dx0dz, Cb[4][4], Cb[5][5], pbu);

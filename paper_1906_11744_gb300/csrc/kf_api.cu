@@ -201,6 +201,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   for (int l = 0; l < det->n_layers; ++l) {
     if (!(det->radius[l] > 0.f) || (l > 0 && !(det->radius[l] > det->radius[l - 1]))) return KF_ERR_ARG;
     if (!(det->x0[l] >= 0.f)) return KF_ERR_ARG;
+    if (!(det->eloss[l] >= 0.f) || !std::isfinite(det->eloss[l])) return KF_ERR_ARG;
   }
   if (!(det->z_max > 0.f) || !(det->sigma_rphi > 0.f) || !(det->sigma_z > 0.f) || !std::isfinite(det->bz))
     return KF_ERR_ARG;
@@ -246,6 +247,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   for (int l = 0; l < det->n_layers; ++l) {
     g.radius[l] = det->radius[l];
     g.x0[l] = det->x0[l];
+    g.eloss[l] = det->eloss[l];
     g.eta_max[l] = asinhf(det->z_max / det->radius[l]);
     g.eta_scale[l] = (float)cfg->n_eta_bins / (2.f * g.eta_max[l]);
     g.r_inv[l] = 1.f / det->radius[l];

@@ -41,6 +41,7 @@ struct DevGeom {
   float radius[KF_MAX_LAYERS];
   float x0[KF_MAX_LAYERS];
   float eta_max[KF_MAX_LAYERS];  // asinh(z_max / R): half-range of the eta grid
+  float eloss[KF_MAX_LAYERS];  // mean ionization loss per layer (GeV, 0: none)
   float eta_scale[KF_MAX_LAYERS];  // n_eta / (2 eta_max): eta bins per unit of eta
   float r_inv[KF_MAX_LAYERS];      // 1 / R
   // Material map (null: the per-layer x0): thickness [n_layers][n_z] at z
@@ -476,6 +477,93 @@ __device__ __forceinline__ T x0_at(const DevGeom& g, int l, T z, T* slope = null
   const T d = (T)m[k + 1] - (T)m[k];
   if (slope) *slope = d * (T)g.z_node_inv;
   return kfma(u - T(k), d, (T)m[k]);
+}
+
+// ---------------------------------------------------------------- energy loss
+// Mean ionization loss of a thin layer, applied after its scattering (Sec. 3:
+// the material description also serves energy loss), for outward motion:
+//   dE = e f / beta^2,  f = 1/|sin(theta) cos(D)|,  D = phi - phi_p (phi_p the
+//   position angle: f is the scattering's path factor),  beta = p/E for the
+//   pion mass m;  E' = E - min(dE, (E - m)/2),  p' = sqrt(E'^2 - m^2),
+//   k' = k p/p' for k = q/pT.
+// The covariance follows the map: C' = F C F^T with F the identity but for
+// its q/pT row u = dk'/d(x, y, z, k, phi, theta).  From log p = -log|k| -
+// log sin(theta), log f = -log sin(theta) - log|cos D| and
+//   d log p' = (E'/p'^2) dE' = A d log p + B d log f,
+//   A = (E'/p'^2)(E beta^2 + 2 dE (1 - beta^2)),  B = -(E'/p'^2) dE,
+// d log k' = A dk/k + (A + B - 1) cot(theta) dtheta - B tan(D) dD with
+// dD = dphi - (x dy - y dx)/r^2, so
+//   u = k' (-B tan(D) y/r^2, B tan(D) x/r^2, 0, A/k, -B tan(D), (A + B - 1) cot(theta)).
+// kval gives the value of a scalar (the cap is a branch on values); the
+// function is written for any scalar with the k* functions, so that the
+// adjoint can take its derivatives in forward mode (Dir6 below).
+__device__ __forceinline__ float kval(float x) { return x; }
+__device__ __forceinline__ double kval(double x) { return x; }
+template <class T>
+__device__ __forceinline__ void eloss_row(const T (&p)[6], T e, T& k1, T (&u)[6]) {
+  T sth, cth, sph, cph;
+  ksincos(p[5], &sth, &cth);
+  ksincos(p[4], &sph, &cph);
+  const T r2 = kfma(p[0], p[0], p[1] * p[1]);
+  const T ir = krsqrt(r2);
+  const T cd = kfma(cph, p[0], sph * p[1]) * ir;     // cos(phi - phi_p)
+  const T sd = kfma(sph, p[0], -(cph * p[1])) * ir;  // sin(phi - phi_p)
+  const T pm = kdiv(T(1), kabs(p[3]) * sth);
+  const T m2 = T(MPION * MPION);
+  const T p2 = pm * pm;
+  const T E2 = p2 + m2;
+  const T E = ksqrt(E2);
+  T dE = kdiv(e * E2, p2 * kabs(sth * cd));  // e f / beta^2
+  const T cap = T(0.5) * (E - T(MPION));
+  if (kval(dE) > kval(cap)) dE = cap;
+  // The terms near 1 and 0 are formed without cancellation (at high momentum
+  // dE/E is tiny): with x = dE (2E - dE)/p^2, p'^2 = p^2 (1 - x) and
+  //   p/p' = (1 - x)^(-1/2),
+  //   A - 1 = dE ((p^2 + 4 m^2)/E - dE (1 + 2 m^2/E^2)) / p'^2,
+  //   A + B - 1 = dE m^2 (3E - 2 dE) / (E^2 p'^2),
+  //   B = -(E - dE) dE / p'^2
+  // (identities of the definitions above).
+  const T x = kdiv(dE * (T(2) * E - dE), p2);
+  const T ratio = krsqrt(T(1) - x);  // p/p'
+  k1 = p[3] * ratio;
+  const T p1sq = p2 * (T(1) - x);
+  const T Am1 = kdiv(dE * (kdiv(p2 + T(4) * m2, E) - dE * (T(1) + kdiv(T(2) * m2, E2))), p1sq);
+  const T ApBm1 = kdiv(dE * m2 * (T(3) * E - T(2) * dE), E2 * p1sq);
+  const T B = -kdiv((E - dE) * dE, p1sq);
+  const T kbt = k1 * B * kdiv(sd, cd);
+  const T ir2 = ir * ir;
+  u[0] = -(kbt * p[1]) * ir2;
+  u[1] = kbt * p[0] * ir2;
+  u[2] = T(0);
+  u[3] = (T(1) + Am1) * ratio;  // k' A / k
+  u[4] = -kbt;
+  u[5] = k1 * kdiv(cth, sth) * ApBm1;
+}
+
+// Energy loss of a layer with loss e (GeV; 0: none) on the state (p, C).
+template <class T>
+__device__ __forceinline__ void add_eloss(T (&p)[6], T (&C)[21], T e) {
+  if (!(e > T(0)) || p[3] == T(0)) return;
+  T k1, u[6];
+  eloss_row<T>(p, e, k1, u);
+  T cu[6];  // (F C) row 3 = u^T C
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    T a = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k != 2) a = kfma(u[k], C[S6(k, j)], a);
+    cu[j] = a;
+  }
+  T c33 = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    if (k != 2) c33 = kfma(cu[k], u[k], c33);
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    if (j != 3) C[S6(3, j)] = cu[j];
+  C[S6(3, 3)] = c33;
+  p[3] = k1;
 }
 
 template <class T>

@@ -149,7 +149,10 @@ __device__ __noinline__ bool careful_child(const double* in, float* out, float m
       ms = false;
     }
   }
-  if (ms) add_ms<double>(p, C, x0_at<double>(g, l, p[2]));
+  if (ms) {
+    add_ms<double>(p, C, x0_at<double>(g, l, p[2]));
+    add_eloss<double>(p, C, (double)g.eloss[l]);
+  }
   for (int k = 0; k < 6; ++k) out[k] = (float)p[k];
   for (int k = 0; k < 21; ++k) out[6 + k] = (float)C[k];
   return ok;
@@ -349,6 +352,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
       chi2 += chi2_of<float>(f, r0, r1);
       kf_update<float>(p, C, f, r0, r1);
       add_ms<float>(p, C, x0_at<float>(g, l, p[2]));
+      add_eloss<float>(p, C, g.eloss[l]);
     }
     // first layer after the seed
     unsigned long long* lst = s_lst[threadIdx.x];
@@ -798,7 +802,10 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             finished = true;  // far-side seed hit: the seed fit stops here
           }
         }
-        if (do_ms) add_ms<float>(p, C, x0_at<float>(g, l, p[2]));
+        if (do_ms) {
+          add_ms<float>(p, C, x0_at<float>(g, l, p[2]));
+          add_eloss<float>(p, C, g.eloss[l]);
+        }
       }
       __syncwarp();
     }

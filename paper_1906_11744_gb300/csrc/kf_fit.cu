@@ -37,7 +37,10 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   if (!residual<T>(p, f, (T)mx, (T)my, (T)mz, r0, r1)) return KF_FIT_FAR_SIDE;
   chi2 += (float)chi2_of<T>(f, r0, r1);
   kf_update<T>(p, C, f, r0, r1);
-  if (!last) add_ms<T>(p, C, x0_at<T>(g, L, p[2]));
+  if (!last) {
+    add_ms<T>(p, C, x0_at<T>(g, L, p[2]));
+    add_eloss<T>(p, C, (T)g.eloss[L]);
+  }
 #pragma unroll
   for (int k = 0; k < 6; ++k) pf[k] = (float)p[k];
 #pragma unroll
@@ -98,7 +101,10 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
       if (!residual<float>(p, f, mx, my, mz, r0, r1)) { status = KF_FIT_FAR_SIDE; break; }
       chi2 += chi2_of<float>(f, r0, r1);
       kf_update<float>(p, C, f, r0, r1);
-      if (k + 1 < n) add_ms<float>(p, C, x0_at<float>(g, L, p[2]));
+      if (k + 1 < n) {
+        add_ms<float>(p, C, x0_at<float>(g, L, p[2]));
+        add_eloss<float>(p, C, g.eloss[L]);
+      }
     } else {
       bool careful = false;
       if (k > 0) {

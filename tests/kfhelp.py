@@ -18,9 +18,7 @@ def tracker_for(batch, device=None, **cfg):
     from paper_1906_11744_gb300 import Tracker, make_config, make_detector
 
     d = batch.det
-    if any(getattr(d, "eloss", ()) or ()):
-        raise ValueError("the CUDA path does not apply energy loss; this detector sets it")
-    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z)
+    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None))
     c = dict(max_cands=batch.cfg["max_cands"])
     c.update(cfg)
     t = Tracker(det, make_config(**c))
@@ -58,7 +56,6 @@ def local_frame(ref_p):
     return B, rad
 
 
-RADIAL_TOL = 1e-3
 
 
 def cov_close(gpu_c21, ref_c21, ref_p):
@@ -68,8 +65,9 @@ def cov_close(gpu_c21, ref_c21, ref_p):
     direction is structurally null, so correlation-scaling the global x/y
     block divides FP32 rounding by near-zero variances.  The comparison uses
     the 5x5 local block, correlation-scaled (|dC_ij| <= TOL sqrt(C_ii C_jj)),
-    and requires the radial variance of both to stay below RADIAL_TOL of the
-    tangential one."""
+    and the radial variance (zero on the cylinder, but for the update's
+    tangential step, which both sides share) within TOL of the oracle's
+    tangential variance."""
     import oracle
     g = oracle.sym_to_full(gpu_c21)
     r = oracle.sym_to_full(ref_c21)
@@ -81,9 +79,9 @@ def cov_close(gpu_c21, ref_c21, ref_p):
     err = np.abs(gl - rl) / np.maximum(norm, 1e-30)
     ok = np.all(err <= TOL, axis=(1, 2))
     tang = rl[:, 0, 0]
-    for c in (g, r):
-        radv = np.abs(np.einsum("ni,nij,nj->n", rad, c, rad))
-        ok &= radv <= RADIAL_TOL * tang
+    radg = np.einsum("ni,nij,nj->n", rad, g, rad)
+    radr = np.einsum("ni,nij,nj->n", rad, r, rad)
+    ok &= np.abs(radg - radr) <= TOL * tang
     return ok, float(err.max()) if err.size else 0.0
 
 
@@ -204,8 +202,8 @@ def found_cov_close(gpu_c21, ref_c21, ref_p):
     (0.5 / cos alpha)^4 below it.  The finder runs crossings down to
     cos(alpha) = 0.2 in FP32 (the re-fit only down to 0.5), and the FP32 error
     of the transported covariance grows as 1/cos^4 of that angle; the radial
-    variance (zero on the cylinder) is held to RADIAL_TOL of the tangential
-    one with the same factor.  Returns (ok mask, (largest error over its
+    variance is compared with the oracle's at the same bound, relative to the
+    tangential variance.  Returns (ok mask, (largest error over its
     bound, largest radial ratio over its bound))."""
     import oracle
     g = oracle.sym_to_full(gpu_c21)
@@ -219,10 +217,9 @@ def found_cov_close(gpu_c21, ref_c21, ref_p):
     tol = TOL * amp
     ok = err <= tol
     tang = rl[:, 0, 0]
-    rad_ratio = np.zeros(len(rl))
-    for c in (g, r):
-        radv = np.abs(np.einsum("ni,nij,nj->n", rad, c, rad))
-        rad_ratio = np.maximum(rad_ratio, radv / (RADIAL_TOL * amp * np.maximum(tang, 1e-300)))
+    radg = np.einsum("ni,nij,nj->n", rad, g, rad)
+    radr = np.einsum("ni,nij,nj->n", rad, r, rad)
+    rad_ratio = np.abs(radg - radr) / (tol * np.maximum(tang, 1e-300))
     ok &= rad_ratio <= 1.0
     if not err.size:
         return ok, (0.0, 0.0)
