@@ -120,6 +120,11 @@ typedef struct {
   float seed_dphi;        /* seed_dphi >= 0, */
   float seed_dpt;         /* seed_dpt >= 0 */
   int seed_min_shared;    /* 0..3 */
+  int resolve_max_rounds; /* 0 = the resolution rounds of seed cleaning and duplicate removal run
+                             until every decision is taken (at most items + 4 rounds, always
+                             enough); > 0 = give up after that many rounds: the next synchronizing
+                             call returns KF_ERR_TIMEOUT, and flags of undecided items are not
+                             valid (a latency bound on the device-side loop) */
 } kf_config;
 
 /* Create a context for a detector and configuration.  Allocates nothing on

@@ -47,7 +47,8 @@ class kf_config(ctypes.Structure):
                 ("per_event", ctypes.c_int), ("ckpt_stride", ctypes.c_int), ("find_regcap", ctypes.c_int),
                 ("dup_deta", ctypes.c_float), ("dup_dphi", ctypes.c_float), ("dup_dpt", ctypes.c_float),
                 ("seed_clean", ctypes.c_int), ("seed_deta", ctypes.c_float), ("seed_dphi", ctypes.c_float),
-                ("seed_dpt", ctypes.c_float), ("seed_min_shared", ctypes.c_int)]
+                ("seed_dpt", ctypes.c_float), ("seed_min_shared", ctypes.c_int),
+                ("resolve_max_rounds", ctypes.c_int)]
 
 
 class KFError(RuntimeError):

@@ -217,7 +217,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   if (cfg->find_regcap < 0 || cfg->find_regcap > 1 || (cfg->find_regcap && threads > 128)) return KF_ERR_ARG;
   auto cut_ok = [](float c) { return c >= 0.f && std::isfinite(c); };
   if (!cut_ok(cfg->dup_deta) || !cut_ok(cfg->dup_dphi) || !cut_ok(cfg->dup_dpt)) return KF_ERR_ARG;
-  if (cfg->seed_clean < 0 || cfg->seed_clean > 1) return KF_ERR_ARG;
+  if (cfg->seed_clean < 0 || cfg->seed_clean > 1 || cfg->resolve_max_rounds < 0) return KF_ERR_ARG;
   if (cfg->seed_clean && (!(cfg->seed_deta > 0.f) || !(cfg->seed_deta <= KF_SEED_MAX_DETA) ||
                           !cut_ok(cfg->seed_dphi) || !cut_ok(cfg->seed_dpt) || cfg->seed_min_shared < 0 ||
                           cfg->seed_min_shared > 3))
@@ -620,6 +620,7 @@ static SeedCleanParams clean_params(kf_ctx* ctx) {
   C.out_C = ptr<float>(ctx->out_C);
   C.keep = ptr<unsigned char>(ctx->keep);
   C.status = ptr<int>(ctx->status);
+  C.max_rounds = ctx->cfg.resolve_max_rounds;
   return C;
 }
 
@@ -728,6 +729,7 @@ int kf_remove_duplicates(kf_ctx* ctx, void* stream) {
   D.state = ptr<unsigned char>(ctx->dd_state);
   D.keep = ptr<unsigned char>(ctx->keep);
   D.status = ptr<int>(ctx->status);
+  D.max_rounds = ctx->cfg.resolve_max_rounds;
   if (ctx->cfg.dup_deta > 0.f || ctx->cfg.dup_dphi > 0.f || ctx->cfg.dup_dpt > 0.f) {
     D.trk_p = ptr<float>(ctx->out_p);
     D.kb = ctx->g.kb;

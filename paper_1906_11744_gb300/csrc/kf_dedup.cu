@@ -164,7 +164,8 @@ struct Rounds {
   unsigned char* state;
   unsigned char* keep;
   int* status;
-  int err;  // status value when the rounds do not settle
+  int err;         // status value when the rounds do not settle
+  int max_rounds;  // rounds before giving up; 0: n + 4, which always settles
 };
 // One step of item t: removed as soon as one of its conflicts is kept, kept
 // as soon as all of them are removed.  Returns false while undecided.
@@ -183,7 +184,8 @@ __device__ __forceinline__ bool dd_decide(const Rounds& P, int t) {
   return true;
 }
 // Rounds by the whole block over items item(0..n) until every one is decided
-// (at most n + 2 rounds: each settles the highest-priority undecided item).
+// (at most n + 2 rounds: each settles the highest-priority undecided item),
+// or, with a round cap, until the cap (the status then records the failure).
 template <class Item>
 __device__ void dd_rounds_over(const Rounds& P, int n, Item item) {
   __shared__ int sh_flag;
@@ -199,7 +201,7 @@ __device__ void dd_rounds_over(const Rounds& P, int n, Item item) {
     const int more = sh_flag;
     __syncthreads();
     if (!more) break;
-    if (round > n + 2) {
+    if (round + 1 >= (P.max_rounds > 0 ? P.max_rounds : n + 4)) {
       if (tid == 0) atomicCAS(P.status, ST_OK, P.err);
       break;
     }
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(DEDUP_THREADS) k_dedup(const DedupParams P) {
   __syncthreads();
   for (int t = s0 + tid; t < s1; t += nt) dd_conflicts(P, t, cnt, 0u, owners);
   __syncthreads();
-  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_DEDUP_ROUNDS}, s0, s1);
+  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_DEDUP_ROUNDS, P.max_rounds}, s0, s1);
 }
 
 // Batched steps, one thread per track of the whole batch.  Event e's table
@@ -301,7 +303,8 @@ __global__ void k_dd_conflicts(const DedupParams P) {
 }
 __global__ void __launch_bounds__(DEDUP_THREADS) k_dd_rounds(const DedupParams P) {
   const int e = blockIdx.x;
-  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_DEDUP_ROUNDS}, P.seed_off[e], P.seed_off[e + 1]);
+  dd_rounds(Rounds{P.n_conf, P.conf, P.state, P.keep, P.status, ST_DEDUP_ROUNDS, P.max_rounds}, P.seed_off[e],
+            P.seed_off[e + 1]);
 }
 
 // ------------------------------------------------------------ seed cleaning
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(DEDUP_THREADS) k_sc_resolve(const SeedCleanPar
   }
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int* list = P.list + s0;
-  dd_rounds_over(Rounds{P.n_conf, P.conf, P.state, nullptr, P.status, ST_SEED_ROUNDS}, P.list_cnt[e],
+  dd_rounds_over(Rounds{P.n_conf, P.conf, P.state, nullptr, P.status, ST_SEED_ROUNDS, P.max_rounds}, P.list_cnt[e],
                  [&](int i) { return list[i]; });
   __syncthreads();
   const int per = (s1 - s0 + nt - 1) / nt;

@@ -108,6 +108,7 @@ struct DedupParams {
   const float* trk_p = nullptr;
   float kb = 0.f;        // h = kb * q/pT
   float deta = 0.f, dphi = 0.f, dpt = 0.f;
+  int max_rounds = 0;    // resolution rounds before giving up (0: until settled)
 };
 
 struct SeedCleanParams {
@@ -139,6 +140,7 @@ struct SeedCleanParams {
   float* out_C;          // [21][ns]
   unsigned char* keep;   // [ns]
   int* status;
+  int max_rounds = 0;    // resolution rounds before giving up (0: until settled)
 };
 
 // The adjoint redoes in double only the steps closer to tangent than this

@@ -182,3 +182,50 @@ def test_seed_clean_capacity_error_and_empty_event():
     trk = t.get_tracks()
     t.close()
     assert (trk["n_found"] > 0).all()
+
+
+def _chain_of_seeds(n=400):
+    """One event whose seeds form a chain: seed k uses hits (k, k+1, k+2) and
+    all seeds have one state, so with two shared hits required seed k
+    conflicts only with seed k - 1; the greedy walk keeps every other seed."""
+    b = make_batch("c1", tracks=200)
+    x, y, z, lay = (a[: n + 2].copy() for a in b.event_hits(0))
+    prm = np.repeat(b.params[:, :1], n, axis=1)
+    cov = np.repeat(b.cov[:, :1], n, axis=1)
+    sh = np.stack([np.arange(n), np.arange(n) + 1, np.arange(n) + 2]).astype(np.int32)
+    return b.det, x, y, z, lay, prm, cov, sh
+
+
+def _clean_chain(resolve_max_rounds):
+    from paper_1906_11744_gb300 import Tracker, make_config, make_detector
+    d, x, y, z, lay, prm, cov, sh = _chain_of_seeds()
+    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z)
+    t = Tracker(det, make_config(max_cands=6, seed_clean=1, seed_deta=0.01, seed_dphi=0.01, seed_min_shared=2,
+                                 resolve_max_rounds=resolve_max_rounds))
+    t.load_hits(np.array([0, x.size], np.int32), x, y, z, lay)
+    t.load_seeds(np.array([0, prm.shape[1]], np.int32), prm, cov, sh)
+    t.find_tracks()
+    return t, d, prm, sh
+
+
+def test_resolution_round_cap_reports_a_timeout():
+    """The bounded device-side loop of seed cleaning (and duplicate removal)
+    gives up after resolve_max_rounds rounds: the next synchronizing call
+    returns KF_ERR_TIMEOUT, and the context stays usable.  Without a cap the
+    same chain settles to the oracle's greedy result (every other seed)."""
+    from paper_1906_11744_gb300 import KFError
+    from paper_1906_11744_gb300._lib import KF_ERR_TIMEOUT
+    t, d, prm, sh = _clean_chain(0)
+    dropped = t.get_tracks()["n_found"] == 0
+    t.close()
+    ref = oracle.seed_clean(prm.T.astype(np.float64), sh.T, float(np.float32(d.bz)), 0.01, 0.01, 0.0, 2)
+    assert np.array_equal(dropped, ref == 0)
+    assert np.array_equal(ref, (np.arange(prm.shape[1]) % 2 == 0).astype(np.uint8))
+    t, d, prm, sh = _clean_chain(1)
+    with pytest.raises(KFError, match=f"\\({KF_ERR_TIMEOUT}\\).*seed cleaning"):
+        t.get_tracks()
+    # the status was reported once and cleared: the context works again
+    t.find_tracks()
+    with pytest.raises(KFError, match="seed cleaning"):
+        t.get_tracks()
+    t.close()
