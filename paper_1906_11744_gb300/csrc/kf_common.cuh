@@ -583,6 +583,42 @@ __device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
   C[S6(5, 5)] += v;
 }
 
+// A seed prior much looser than the hit resolution (a position variance above
+// LOOSE_PRIOR times the measurement variance, in r-phi or in z): the first
+// updates then shrink the variances by more than the factor (position at the
+// first hit, direction and curvature at the next two), and C - K H C cancels
+// as many leading digits, which FP32 cannot spare.  The steps over the first
+// LOOSE_STEPS hits of such a track run in double (the careful passes of the
+// finding and the fit); the first update, at the prior point, through
+// first_update_double.
+constexpr int LOOSE_STEPS = 3;
+constexpr float LOOSE_PRIOR = 1000.f;
+__device__ __forceinline__ bool loose_prior(const float (&C)[21], const DevGeom& g) {
+  return C[S6(0, 0)] + C[S6(1, 1)] > LOOSE_PRIOR * g.vr || C[S6(2, 2)] > LOOSE_PRIOR * g.vz;
+}
+// The first update in double: frame, residual, chi2 (added to chi2), update,
+// then (if ms) the scattering and energy loss of layer l.  Returns false for a
+// hit on the far half (nothing changed).
+static __device__ __noinline__ bool first_update_double(float (&pf)[6], float (&Cf)[21], const DevGeom& g, int l,
+                                                        float mx, float my, float mz, bool ms, float& chi2) {
+  double p[6], C[21];
+  for (int k = 0; k < 6; ++k) p[k] = pf[k];
+  for (int k = 0; k < 21; ++k) C[k] = Cf[k];
+  FrameT<double> f;
+  make_frame<double>(p, C, (double)g.vr, (double)g.vz, f);
+  double r0, r1;
+  if (!residual<double>(p, f, (double)mx, (double)my, (double)mz, r0, r1)) return false;
+  chi2 += (float)chi2_of<double>(f, r0, r1);
+  kf_update<double>(p, C, f, r0, r1);
+  if (ms) {
+    add_ms<double>(p, C, x0_at<double>(g, l, p[2]));
+    add_eloss<double>(p, C, (double)g.eloss[l]);
+  }
+  for (int k = 0; k < 6; ++k) pf[k] = (float)p[k];
+  for (int k = 0; k < 21; ++k) Cf[k] = (float)C[k];
+  return true;
+}
+
 // ---------------------------------------------------------------- hit grid
 // phi bins: floor((phi + pi) * n_phi / 2pi) (monotone in phi; wrapped mod
 // n_phi for hits).  eta bins: 64 equal steps of eta = asinh(z/R) over

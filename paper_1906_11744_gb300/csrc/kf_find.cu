@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
 #pragma unroll
     for (int k = 0; k < 21; ++k) C[k] = P.sc[k * ns + seed];
     float chi2 = 0.f;
-    bool finished = false, near = false;
+    bool finished = false, near = loose_prior(C, g);  // a loose prior: the careful pass fits the seed
     int l = 0;
 #pragma unroll 1
     for (int it = 0; it < 3; ++it) {
@@ -503,6 +503,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     int ev = 0, hoff = 0;
     float p[6], C[21];
     float chi2 = 0.f;
+    bool loose = false;  // careful pass: the seed's prior is loose (its steps in double)
     int nfound = 3, nholes = 0;
     bool finished = false;
     bool occ = has_seed && gl == 0;
@@ -521,6 +522,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + seed];
 #pragma unroll
         for (int k = 0; k < 21; ++k) C[k] = P.sc[(size_t)k * P.ns + seed];
+        loose = loose_prior(C, g);
       } else {  // the fitted seed and its first layer
 #pragma unroll
         for (int k = 0; k < 6; ++k) p[k] = P.sfit[(size_t)k * P.ns + seed];
@@ -573,7 +575,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             const float z_lim = in_seed ? INFINITY : g.z_max;
             float q[6], J[6][6], cosa = 1.f;
             pr = prop_jacobian<float>(p, R, g.kb, z_lim, q, J, &cosa);
-            if (CAREFUL && pr == 1 && cosa < FIND_CAREFUL_COS) {
+            if (CAREFUL && pr == 1 && (cosa < FIND_CAREFUL_COS || (in_seed && loose))) {
               float* st = reinterpret_cast<float*>(lst);
 #pragma unroll
               for (int k = 0; k < 6; ++k) st[k] = p[k];
@@ -779,6 +781,14 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
           for (int k = 0; k < 6; ++k) p[k] = st[k];
 #pragma unroll
           for (int k = 0; k < 21; ++k) C[k] = st[6 + k];
+          do_update = do_ms = false;
+        }
+        if (do_update && CAREFUL && in_seed && it == 0 && loose) {
+          // the first update against a loose prior in double
+          const int hi = hoff + hit;
+          float mx, my, mz;
+          corrected_hit(P.align[l], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+          if (!first_update_double(p, C, g, l, mx, my, mz, true, chi2)) finished = true;
           do_update = do_ms = false;
         }
         if (do_update) {

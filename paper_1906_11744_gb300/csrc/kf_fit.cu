@@ -66,6 +66,13 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
   for (int k = 0; k < 6; ++k) p[k] = P.sp[(size_t)k * P.ns + t];
 #pragma unroll
   for (int k = 0; k < 21; ++k) C[k] = P.sc[(size_t)k * P.ns + t];
+  // a loose prior: the careful pass runs the first steps in double
+  const bool loose = loose_prior(C, g);
+  if (!CAREFUL && loose) {
+    P.careful_list[atomicAdd(P.careful_count, 1u)] = t;
+    if (P.careful_flag) P.careful_flag[t] = 1;
+    return;
+  }
   const int hoff = P.hit_off[P.seed_event[t]];
   const int n = P.n_list[t];
   const int* lst = P.lists + (size_t)t * P.max_len;
@@ -113,6 +120,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
         careful = cosa < CAREFUL_COS;
         min_cos = fminf(min_cos, cosa);
       }
+      if (loose && k < LOOSE_STEPS) careful = true;  // the first steps against a loose prior
       status = careful ? fit_step<double>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
                        : fit_step<float>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2);
     }
