@@ -280,61 +280,67 @@ __device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T dx0dz, T b44, T 
   v[2] = kfma(W * bt, dx0dz / x0, v[2]);
 }
 
-// Reverse of add_eloss at the state (p, C) it acted on.  In: pb, Cb (full
-// symmetric) the adjoints after it; out: the adjoints before it.  With F the
-// identity but for row 3 = u(p) (eloss_row) and L = pb . p' + <Cb, F C F^T>:
+// Reverse of add_eloss, out of line and through a record in local memory, so
+// that the reverse step keeps its registers for the path without loss.  In:
+// the step's prediction (p = the updated state, Cp the predicted covariance,
+// U = Cp H^T, S^-1), the layer's thickness x0 and loss e, and the adjoints pb,
+// Cb (upper triangle) of the state after the loss.  The state the loss acted
+// on is the update's covariance plus the scattering; with F the identity but
+// for row 3 = u(p) (eloss_row) and L = pb . p' + <Cb, F C F^T>:
 //   Cbar = F^T Cb F;
 //   pbar_k = pb_k (k != 3) + pb_3 u_k + sum_j ubar_j du_j/dp_k,
 //   ubar_j = 2 sum_(b != 3) Cb_3b C_jb + 2 Cb_33 (C u)_j,
-// du/dp in forward mode (Dir6).
+// du/dp in forward mode (Dir6).  pb, Cb are replaced by the adjoints before
+// the loss.
 template <class S>
-__device__ __noinline__ void eloss_vjp(const S (&p)[6], const S (&C)[21], S e, S (&pb)[6], S (&Cb)[6][6]) {
+struct ElossRev {
+  S p[6], Cp[21], U[6][2], si00, si01, si11, x0, e;
+  S pb[6], Cb[21];
+};
+template <class S>
+__device__ __noinline__ void eloss_vjp(ElossRev<S>* io) {
+  S C[21];
+  for (int i = 0; i < 6; ++i) {
+    const S k0 = kfma(io->U[i][0], io->si00, io->U[i][1] * io->si01);
+    const S k1 = kfma(io->U[i][0], io->si01, io->U[i][1] * io->si11);
+    for (int j = i; j < 6; ++j) C[S6(i, j)] = io->Cp[S6(i, j)] - kfma(k0, io->U[j][0], k1 * io->U[j][1]);
+  }
+  S p[6];
+  for (int k = 0; k < 6; ++k) p[k] = io->p[k];
+  add_ms<S>(p, C, io->x0);
   Dir6<S> pd[6];
-#pragma unroll
   for (int k = 0; k < 6; ++k) {
     pd[k] = Dir6<S>(p[k]);
     pd[k].d[k] = S(1);
   }
   Dir6<S> k1, u[6];
-  eloss_row<Dir6<S>>(pd, Dir6<S>(e), k1, u);
+  eloss_row<Dir6<S>>(pd, Dir6<S>(io->e), k1, u);
   S uv[6], Cu[6], ub[6], pn[6];
-#pragma unroll
   for (int j = 0; j < 6; ++j) uv[j] = u[j].v;
-#pragma unroll
   for (int j = 0; j < 6; ++j) {
     S a = S(0);
-#pragma unroll
     for (int b = 0; b < 6; ++b) a = kfma(C[S6(j, b)], uv[b], a);
     Cu[j] = a;
   }
-#pragma unroll
   for (int j = 0; j < 6; ++j) {
-    S a = Cb[3][3] * Cu[j];
-#pragma unroll
+    S a = io->Cb[S6(3, 3)] * Cu[j];
     for (int b = 0; b < 6; ++b)
-      if (b != 3) a = kfma(Cb[3][b], C[S6(j, b)], a);
+      if (b != 3) a = kfma(io->Cb[S6(3, b)], C[S6(j, b)], a);
     ub[j] = S(2) * a;
   }
-#pragma unroll
   for (int k = 0; k < 6; ++k) {
-    S a = kfma(pb[3], uv[k], k == 3 ? S(0) : pb[k]);
-#pragma unroll
+    S a = kfma(io->pb[3], uv[k], k == 3 ? S(0) : io->pb[k]);
     for (int j = 0; j < 6; ++j) a = kfma(ub[j], u[j].d[k], a);
     pn[k] = a;
   }
   // Cbar = F^T Cb F: X = Cb F (column k: Cb_:k for k != 3, plus Cb_:3 u_k),
   // then F^T X (row k: X_k: for k != 3, plus u_k X_3:)
   S X[6][6];
-#pragma unroll
   for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) X[i][k] = kfma(Cb[i][3], uv[k], k == 3 ? S(0) : Cb[i][k]);
-#pragma unroll
+    for (int k = 0; k < 6; ++k) X[i][k] = kfma(io->Cb[S6(i, 3)], uv[k], k == 3 ? S(0) : io->Cb[S6(i, k)]);
   for (int k = 0; k < 6; ++k)
-#pragma unroll
-    for (int m = 0; m < 6; ++m) Cb[k][m] = kfma(uv[k], X[3][m], k == 3 ? S(0) : X[k][m]);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) pb[k] = pn[k];
+    for (int m = k; m < 6; ++m) io->Cb[S6(k, m)] = kfma(uv[k], X[3][m], k == 3 ? S(0) : X[k][m]);
+  for (int k = 0; k < 6; ++k) io->pb[k] = pn[k];
 }
 
 template <class S>
@@ -362,7 +368,8 @@ __device__ __forceinline__ Hit<S> load_hit(const AdjParams& P, int hi) {
 // One forward fit step (as kf_fit.cu).  Returns false if the step fails or,
 // for float, when the crossing is near-tangent (the track then goes to the
 // double-precision pass).
-template <class S>
+// EL: the detector has energy loss (kernels without it carry none of its code).
+template <class S, bool EL>
 __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21], const Hit<S>& h, bool first,
                                         bool last) {
   if (!first) {
@@ -377,7 +384,7 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
   kf_update<S>(p, C, f, r0, r1);
   if (!last) {
     add_ms<S>(p, C, x0_at<S>(g, h.L, p[2]));
-    add_eloss<S>(p, C, (S)g.eloss[h.L]);
+    if constexpr (EL) add_eloss_ool<S>(p, C, (S)g.eloss[h.L]);
   }
   return KF_FIT_OK;
 }
@@ -386,7 +393,7 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
 // adjoints of the state after it (pb, Cb: Cb a full symmetric 6x6).  Out: pb,
 // Cb replaced by the adjoints of the state before it; the gradient of this
 // step with respect to the raw hit position in hb[3].
-template <class S>
+template <class S, bool EL>
 __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], const S (&C_in)[21],
                                          const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
                                          S (&hb)[3]) {
@@ -428,17 +435,33 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   for (int i = 0; i < 6; ++i) pbu[i] = pb[i];
   if (!last) {
     const S e = (S)g.eloss[h.L];
-    if (e > S(0) && pu[3] != S(0)) {
-      // the state the loss acted on: the update's covariance plus the scattering
-      S Cm[21];
+    if (EL && e > S(0) && pu[3] != S(0)) {
+      ElossRev<S> io;
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        const S k0 = kfma(U[i][0], si00, U[i][1] * si01), k1 = kfma(U[i][0], si01, U[i][1] * si11);
-#pragma unroll
-        for (int j = i; j < 6; ++j) Cm[S6(i, j)] = Cp[S6(i, j)] - kfma(k0, U[j][0], k1 * U[j][1]);
+        io.p[i] = pu[i];
+        io.pb[i] = pbu[i];
+        io.U[i][0] = U[i][0];
+        io.U[i][1] = U[i][1];
       }
-      add_ms<S>(pu, Cm, x0_at<S>(g, h.L, pu[2]));
-      eloss_vjp<S>(pu, Cm, e, pbu, Cb);
+#pragma unroll
+      for (int k = 0; k < 21; ++k) io.Cp[k] = Cp[k];
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) io.Cb[S6(i, j)] = Cb[i][j];
+      io.si00 = si00;
+      io.si01 = si01;
+      io.si11 = si11;
+      io.x0 = x0_at<S>(g, h.L, pu[2]);
+      io.e = e;
+      eloss_vjp<S>(&io);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) pbu[i] = io.pb[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) Cb[i][j] = Cb[j][i] = io.Cb[S6(i, j)];
     }
     S dx0dz;
     const S x0 = x0_at<S>(g, h.L, pu[2], &dx0dz);
@@ -612,19 +635,19 @@ __device__ __forceinline__ bool near_tangent(const DevGeom& g, const float (&p)[
 
 // Forward step in precision S on float storage: the state before the step at
 // st[q * LD], q < 27; the state after it goes to st[(27 + q) * LD].
-template <class S>
+template <class S, bool EL>
 __device__ __noinline__ void fwd_step_store(const DevGeom& g, float* st, const Hit<S>& h, bool first, bool last) {
   S p[6], C[21];
   for (int q = 0; q < 6; ++q) p[q] = (S)st[q * LD];
   for (int q = 0; q < 21; ++q) C[q] = (S)st[(6 + q) * LD];
-  fwd_step<S>(g, p, C, h, first, last);
+  fwd_step<S, EL>(g, p, C, h, first, last);
   for (int q = 0; q < 6; ++q) st[(27 + q) * LD] = (float)p[q];
   for (int q = 0; q < 21; ++q) st[(27 + 6 + q) * LD] = (float)C[q];
 }
 
 // Reverse step in precision S with the adjoints kept in A (double in the
 // careful pass, float otherwise); the state before the step at st[q * LD].
-template <class S, class A>
+template <class S, class A, bool EL>
 __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, const Hit<S>& h, bool first,
                                             bool last, A (&pbA)[6], A (&CbA)[6][6], A (&hbA)[3]) {
   S p[6], C[21], pb[6], Cb[6][6], hb[3];
@@ -634,7 +657,7 @@ __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, c
     pb[i] = (S)pbA[i];
     for (int j = 0; j < 6; ++j) Cb[i][j] = (S)CbA[i][j];
   }
-  rev_step<S>(g, p, C, h, first, last, pb, Cb, hb);
+  rev_step<S, EL>(g, p, C, h, first, last, pb, Cb, hb);
   for (int i = 0; i < 6; ++i) {
     pbA[i] = (A)pb[i];
     for (int j = 0; j < 6; ++j) CbA[i][j] = (A)Cb[i][j];
@@ -647,7 +670,7 @@ __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, c
 // double precision and its adjoints are kept in double.  seg: this thread's
 // column of the block's segment buffer in shared memory (states before each
 // step of a segment, [slot][27][LD]).
-template <bool CAREFUL>
+template <bool CAREFUL, bool EL>
 __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
   using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
@@ -687,11 +710,11 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
         float pf[6];
         for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
         if (near_tangent(g, pf, g.radius[P.hlayer[hi]])) {
-          fwd_step_store<double>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n);
+          fwd_step_store<double, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n);
           continue;
         }
       }
-      fwd_step_store<float>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
+      fwd_step_store<float, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
     }
     for (int k = k1 - 1; k >= k0; --k) {
       const float* st = seg + (k - k0) * 27 * LD;
@@ -704,8 +727,8 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
         for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
         dbl = near_tangent(g, pf, g.radius[P.hlayer[hi]]);
       }
-      if (dbl) rev_step_store<double, A>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
-      else rev_step_store<float, A>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      if (dbl) rev_step_store<double, A, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      else rev_step_store<float, A, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
       float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
       atomicAdd(gh + 0, (float)hb[0]);
       atomicAdd(gh + 1, (float)hb[1]);
@@ -717,17 +740,17 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
   }
 }
 
-template <bool CAREFUL>
+template <bool CAREFUL, bool EL>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
   extern __shared__ float seg_all[];  // [stride][27][LD]
   float* seg = seg_all + threadIdx.x;
   if constexpr (!CAREFUL) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.ns) adjoint_track<false>(P, t, seg);
+    if (t < P.ns) adjoint_track<false, EL>(P, t, seg);
   } else {
     const unsigned n = *P.careful_count;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      adjoint_track<true>(P, P.careful_list[i], seg);
+      adjoint_track<true, EL>(P, P.careful_list[i], seg);
   }
 }
 
@@ -775,21 +798,31 @@ cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(P.g_hits, 0, sizeof(float) * 3 * (size_t)P.n_hits, st);
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
-  e = cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k_adjoint<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_adjoint<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adjoint<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adjoint<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e;
 }
 
 cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
   const size_t smem = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
+  bool el = false;  // energy loss on any layer: the variant with its code
+  for (int l = 0; l < P.g.n_layers; ++l) el = el || P.g.eloss[l] > 0.f;
+  const int grid_all = (P.ns + ADJ_THREADS - 1) / ADJ_THREADS;
+  // flagged tracks are a few percent: a grid for a twentieth of all, striding
+  // over however many there are
+  const int grid_careful = (P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1;
   if (!careful) {
-    k_adjoint<false><<<(P.ns + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, smem, st>>>(P);
+    if (el) k_adjoint<false, true><<<grid_all, ADJ_THREADS, smem, st>>>(P);
+    else k_adjoint<false, false><<<grid_all, ADJ_THREADS, smem, st>>>(P);
   } else {
-    // flagged tracks are a few percent: a grid for a twentieth of all,
-    // striding over however many there are
-    k_adjoint<true><<<(P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1, ADJ_THREADS, smem, st>>>(P);
+    if (el) k_adjoint<true, true><<<grid_careful, ADJ_THREADS, smem, st>>>(P);
+    else k_adjoint<true, false><<<grid_careful, ADJ_THREADS, smem, st>>>(P);
   }
   return cudaGetLastError();
 }

@@ -566,6 +566,30 @@ __device__ __forceinline__ void add_eloss(T (&p)[6], T (&C)[21], T e) {
   p[3] = k1;
 }
 
+// The same, out of line: a layer without loss costs a comparison; with a loss
+// the state goes through a record in local memory, so that the register
+// allocation of the caller's usual path does not carry the loss's code.
+template <class T>
+struct State27 {
+  T p[6], C[21];
+};
+template <class T>
+static __device__ __noinline__ void eloss_record(State27<T>* s, T e) { add_eloss<T>(s->p, s->C, e); }
+template <class T>
+__device__ __forceinline__ void add_eloss_ool(T (&p)[6], T (&C)[21], T e) {
+  if (!(e > T(0))) return;
+  State27<T> s;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) s.p[k] = p[k];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) s.C[k] = C[k];
+  eloss_record<T>(&s, e);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = s.p[k];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = s.C[k];
+}
+
 template <class T>
 __device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
   if (p[3] == T(0) || x0 <= T(0)) return;

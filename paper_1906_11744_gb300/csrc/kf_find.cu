@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
       chi2 += chi2_of<float>(f, r0, r1);
       kf_update<float>(p, C, f, r0, r1);
       add_ms<float>(p, C, x0_at<float>(g, l, p[2]));
-      add_eloss<float>(p, C, g.eloss[l]);
+      add_eloss_ool<float>(p, C, g.eloss[l]);
     }
     // first layer after the seed
     unsigned long long* lst = s_lst[threadIdx.x];
@@ -427,7 +427,9 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
   }
 }
 
-template <int G, int CAP, bool CAREFUL>
+// EL: the detector has energy loss (the main pass without it carries none of
+// its code; the careful pass always does).
+template <int G, int CAP, bool CAREFUL, bool EL>
 __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const FindParams P) {
   constexpr int W = 32 / G;  // seeds per warp
   extern __shared__ __align__(16) unsigned char smem[];
@@ -814,7 +816,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         }
         if (do_ms) {
           add_ms<float>(p, C, x0_at<float>(g, l, p[2]));
-          add_eloss<float>(p, C, g.eloss[l]);
+          if constexpr (EL) add_eloss_ool<float>(p, C, g.eloss[l]);
         }
       }
       __syncwarp();
@@ -894,22 +896,24 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
 template <int G, int CAP>
 cudaError_t prepare_g(int threads, int n_layers, int n_eta, int* blocks_per_sm) {
   const size_t smem = smem_edges(n_layers, n_eta) + (size_t)(threads / 32) * smem_per_warp(G, false, n_layers);
-  cudaError_t err = cudaFuncSetAttribute(k_find<G, CAP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t err = cudaFuncSetAttribute(k_find<G, CAP, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_find<G, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    err = cudaFuncSetAttribute(k_find<G, CAP, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_find<G, 0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(smem_edges(n_layers, n_eta) +
                                      (CAREFUL_THREADS / 32) * smem_per_warp_k(G, n_layers, true)));
   if (err != cudaSuccess) return err;
   cudaFuncAttributes fa;
-  err = cudaFuncGetAttributes(&fa, k_find<G, CAP, false>);
+  err = cudaFuncGetAttributes(&fa, k_find<G, CAP, false, false>);
   if (err != cudaSuccess) return err;
   if (threads > fa.maxThreadsPerBlock) {  // the launch bounds forbid this block size
     if (blocks_per_sm) *blocks_per_sm = 0;
     return cudaSuccess;
   }
   if (blocks_per_sm)
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_find<G, CAP, false>, threads, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_find<G, CAP, false, false>, threads, smem);
   return err;
 }
 
@@ -924,7 +928,10 @@ cudaError_t launch_main_g(const FindParams& P, int threads, int grid_cap, cudaSt
   int grid = (n_tasks + wpb - 1) / wpb;
   if (P.persistent && grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid < 1) grid = 1;
-  k_find<G, CAP, false><<<grid, threads, smem, st>>>(P);
+  bool el = false;  // energy loss on any layer: the variant with its code
+  for (int l = 0; l < P.g.n_layers; ++l) el = el || P.g.eloss[l] > 0.f;
+  if (el) k_find<G, CAP, false, true><<<grid, threads, smem, st>>>(P);
+  else k_find<G, CAP, false, false><<<grid, threads, smem, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -932,7 +939,7 @@ template <int G, int CAP>
 cudaError_t launch_careful_g(const FindParams& P, int grid, cudaStream_t st) {
   const size_t smem =
       smem_edges(P.g.n_layers, P.g.n_eta) + (size_t)(CAREFUL_THREADS / 32) * smem_per_warp_k(G, P.g.n_layers, true);
-  k_find<G, 0, true><<<grid, CAREFUL_THREADS, smem, st>>>(P);
+  k_find<G, 0, true, true><<<grid, CAREFUL_THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   kf_update<T>(p, C, f, r0, r1);
   if (!last) {
     add_ms<T>(p, C, x0_at<T>(g, L, p[2]));
-    add_eloss<T>(p, C, (T)g.eloss[L]);
+    add_eloss_ool<T>(p, C, (T)g.eloss[L]);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) pf[k] = (float)p[k];
@@ -110,7 +110,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
       kf_update<float>(p, C, f, r0, r1);
       if (k + 1 < n) {
         add_ms<float>(p, C, x0_at<float>(g, L, p[2]));
-        add_eloss<float>(p, C, g.eloss[L]);
+        add_eloss_ool<float>(p, C, g.eloss[L]);
       }
     } else {
       bool careful = false;
