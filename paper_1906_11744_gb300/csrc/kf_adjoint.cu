@@ -665,15 +665,47 @@ __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, c
   for (int i = 0; i < 3; ++i) hbA[i] = (A)hb[i];
 }
 
-// Reverse sweep of one fitted track from the fit's checkpoints.  CAREFUL:
+// Forward step of the FP32 pass, inlined (as rev_step_regs).
+template <bool EL>
+__device__ __forceinline__ void fwd_step_regs(const DevGeom& g, float* st, const Hit<float>& h, bool first,
+                                              bool last) {
+  float p[6], C[21];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) p[q] = st[q * LD];
+#pragma unroll
+  for (int q = 0; q < 21; ++q) C[q] = st[(6 + q) * LD];
+  fwd_step<float, EL>(g, p, C, h, first, last);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) st[(27 + q) * LD] = p[q];
+#pragma unroll
+  for (int q = 0; q < 21; ++q) st[(27 + 6 + q) * LD] = C[q];
+}
+
+// The same reverse step inlined into the FP32 pass, so that the adjoints stay
+// in registers (an out-of-line call takes them by reference, through local
+// memory).
+template <bool EL>
+__device__ __forceinline__ void rev_step_regs(const DevGeom& g, const float* st, const Hit<float>& h, bool first,
+                                              bool last, float (&pb)[6], float (&Cb)[6][6], float (&hb)[3]) {
+  float p[6], C[21];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) p[q] = st[q * LD];
+#pragma unroll
+  for (int q = 0; q < 21; ++q) C[q] = st[(6 + q) * LD];
+  rev_step<float, EL>(g, p, C, h, first, last, pb, Cb, hb);
+}
+
+// Reverse sweep of the track at position i of the fit's order, from the
+// fit's checkpoints (column i).  CAREFUL:
 // the track the fit flagged as near-tangent; its near-tangent steps run in
 // double precision and its adjoints are kept in double.  seg: this thread's
 // column of the block's segment buffer in shared memory (states before each
 // step of a segment, [slot][27][LD]).
 template <bool CAREFUL, bool EL>
-__device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
+__device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
   using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
+  const int t = P.order[i];  // the track at position i of the fit's order (checkpoint column i)
   if (!CAREFUL) {
     // Tracks with a crossing below ADJ_CAREFUL_COS are the careful adjoint's,
     // whose pass runs at the same time as this one.
@@ -701,7 +733,7 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
   }
   for (int c = (n - 1) / stride; c >= 0; --c) {
     const int k0 = c * stride, k1 = min(n, k0 + stride);
-    const float* ck = P.ckpt + (size_t)c * 27 * P.ns + t;
+    const float* ck = P.ckpt + (size_t)c * 27 * P.ns + i;
     for (int q = 0; q < 27; ++q) seg[q * LD] = ck[(size_t)q * P.ns];
     for (int k = k0; k + 1 < k1; ++k) {
       float* st = seg + (k - k0) * 27 * LD;
@@ -714,7 +746,8 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
           continue;
         }
       }
-      fwd_step_store<float, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
+      if constexpr (!CAREFUL) fwd_step_regs<EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
+      else fwd_step_store<float, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
     }
     for (int k = k1 - 1; k >= k0; --k) {
       const float* st = seg + (k - k0) * 27 * LD;
@@ -727,7 +760,8 @@ __device__ void adjoint_track(const AdjParams& P, int t, float* seg) {
         for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
         dbl = near_tangent(g, pf, g.radius[P.hlayer[hi]]);
       }
-      if (dbl) rev_step_store<double, A, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      if constexpr (!CAREFUL) rev_step_regs<EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      else if (dbl) rev_step_store<double, A, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
       else rev_step_store<float, A, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
       float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
       atomicAdd(gh + 0, (float)hb[0]);
@@ -745,8 +779,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
   extern __shared__ float seg_all[];  // [stride][27][LD]
   float* seg = seg_all + threadIdx.x;
   if constexpr (!CAREFUL) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.ns) adjoint_track<false, EL>(P, t, seg);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.ns) adjoint_track<false, EL>(P, i, seg);
   } else {
     const unsigned n = *P.careful_count;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)

@@ -45,6 +45,7 @@ struct kf_ctx {
   DevBuf sc_kin, sc_seed, clean_order, kept_cnt, sc_list, sc_list_cnt;
   // fit
   DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count, careful_flag, ckpt;
+  DevBuf fit_order, fit_order_hist;
   bool want_ckpt = false;
   int given_max_len = 0;
   bool found = false, deduped = false, fitted = false;
@@ -321,7 +322,7 @@ static std::vector<DevBuf*> all_bufs(kf_ctx* ctx) {
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
                     &ctx->clean_order, &ctx->kept_cnt, &ctx->sc_list, &ctx->sc_list_cnt, &ctx->sfit,
-                    &ctx->sflag, &ctx->skeys, &ctx->x0map};
+                    &ctx->sflag, &ctx->skeys, &ctx->x0map, &ctx->fit_order, &ctx->fit_order_hist};
 }
 
 int kf_destroy(kf_ctx* ctx) {
@@ -444,6 +445,8 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->careful_list, sizeof(int) * (size_t)n));
   CK(grow(ctx->careful_count, 64));
   CK(grow(ctx->careful_flag, (size_t)n));
+  CK(grow(ctx->fit_order, sizeof(int) * (size_t)n));
+  CK(grow(ctx->fit_order_hist, sizeof(unsigned) * 2 * FIT_ORDER_BINS));
   if (ctx->cfg.seed_clean) {
     CK(grow(ctx->sc_kin, sizeof(float4) * (size_t)n));
     CK(grow(ctx->sc_seed, sizeof(int4) * (size_t)n));
@@ -777,6 +780,8 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   F.careful_list = ptr<int>(ctx->careful_list);
   F.careful_count = ptr<unsigned>(ctx->careful_count);
   F.careful_flag = ptr<unsigned char>(ctx->careful_flag);
+  F.order = ptr<int>(ctx->fit_order);
+  F.order_hist = ptr<unsigned>(ctx->fit_order_hist);
   F.ckpt_stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
   F.ckpt = nullptr;
   F.ckpt_slices = 0;
@@ -880,6 +885,7 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   A.careful_count = F.careful_count;
   A.careful_flag = F.careful_flag;
   A.ckpt = F.ckpt;
+  A.order = F.order;
   stage_mark(ctx, 8, st);
   CK(launch_adjoint_begin(A, st));
   CK(fork_side(ctx, st));

@@ -48,8 +48,10 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   return KF_FIT_OK;
 }
 
+// Track at position i of the fit's order; checkpoints go to column i.
 template <bool CAREFUL>
-__device__ __forceinline__ void fit_track(const FitParams& P, int t) {
+__device__ __forceinline__ void fit_track(const FitParams& P, int i) {
+  const int t = P.order[i];
   if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;  // set below if the track is left to the careful pass
   if (!CAREFUL && P.keep && !P.keep[t]) {  // removed as a duplicate: zero outputs
 #pragma unroll
@@ -69,7 +71,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
   // a loose prior: the careful pass runs the first steps in double
   const bool loose = loose_prior(C, g);
   if (!CAREFUL && loose) {
-    P.careful_list[atomicAdd(P.careful_count, 1u)] = t;
+    P.careful_list[atomicAdd(P.careful_count, 1u)] = i;
     if (P.careful_flag) P.careful_flag[t] = 1;
     return;
   }
@@ -82,7 +84,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
 #pragma unroll 1
   for (int k = 0; k < n && status == KF_FIT_OK; ++k) {
     if (P.ckpt && k % P.ckpt_stride == 0 && k / P.ckpt_stride < P.ckpt_slices) {  // state before hit k
-      float* c = P.ckpt + (size_t)(k / P.ckpt_stride) * 27 * P.ns + t;
+      float* c = P.ckpt + (size_t)(k / P.ckpt_stride) * 27 * P.ns + i;
 #pragma unroll
       for (int q = 0; q < 6; ++q) c[(size_t)q * P.ns] = p[q];
 #pragma unroll
@@ -97,7 +99,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
         float cosa = 1.f;
         if (propagate<float>(p, C, g.radius[L], g.kb, INFINITY, &cosa) != 1) { status = KF_FIT_NO_CROSS; break; }
         if (cosa < CAREFUL_COS) {  // leave the track to the careful pass
-          P.careful_list[atomicAdd(P.careful_count, 1u)] = t;
+          P.careful_list[atomicAdd(P.careful_count, 1u)] = i;
           if (P.careful_flag) P.careful_flag[t] = 1;
           return;
         }
@@ -135,8 +137,8 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int t) {
 }
 
 __global__ void __launch_bounds__(128) k_fit(const FitParams P) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < P.ns) fit_track<false>(P, t);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.ns) fit_track<false>(P, i);
 }
 
 // Second pass over the flagged tracks (grid-stride over their list).
@@ -146,14 +148,77 @@ __global__ void __launch_bounds__(128) k_fit_careful(const FitParams P) {
     fit_track<true>(P, P.careful_list[i]);
 }
 
+// The fit's track order: a counting sort by hit count, decreasing; tracks
+// removed as duplicates count as 0 hits and come last.  Positions within a
+// bin are taken by atomics (the order within a bin is not fixed; each track's
+// results do not depend on it).
+__device__ __forceinline__ int order_key(const FitParams& P, int t) {
+  if (P.keep && !P.keep[t]) return 0;
+  return min(max(P.n_list[t], 0), FIT_ORDER_BINS - 1);
+}
+
+constexpr int ORDER_THREADS = 256;
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_count(const FitParams P) {
+  __shared__ unsigned h[FIT_ORDER_BINS];
+  for (int b = threadIdx.x; b < FIT_ORDER_BINS; b += blockDim.x) h[b] = 0u;
+  __syncthreads();
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P.ns; t += gridDim.x * blockDim.x)
+    atomicAdd(&h[order_key(P, t)], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < FIT_ORDER_BINS; b += blockDim.x)
+    if (h[b]) atomicAdd(&P.order_hist[b], h[b]);
+}
+
+// One track per thread: position = (tracks in bins of more hits) + the
+// track's place among its bin's tracks (one atomic per bin and warp).
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_scatter(const FitParams P) {
+  static_assert(FIT_ORDER_BINS == 64, "two bins per lane");
+  __shared__ unsigned base[FIT_ORDER_BINS];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    // lane j holds bins 63 - 2j and 62 - 2j; exclusive prefix over lanes
+    const unsigned a = P.order_hist[63 - 2 * lane], b = P.order_hist[62 - 2 * lane];
+    unsigned incl = a + b;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const unsigned excl = incl - a - b;
+    base[63 - 2 * lane] = excl;
+    base[62 - 2 * lane] = excl + a;
+  }
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int key = t < P.ns ? order_key(P, t) : FIT_ORDER_BINS;  // FIT_ORDER_BINS: no track
+  const unsigned same = __match_any_sync(0xffffffffu, key);
+  if (key < FIT_ORDER_BINS) {
+    const int leader = __ffs(same) - 1;
+    unsigned off = 0;
+    if (lane == leader) off = atomicAdd(&P.order_hist[FIT_ORDER_BINS + key], (unsigned)__popc(same));
+    off = __shfl_sync(same, off, leader);
+    const unsigned rank = __popc(same & ((1u << lane) - 1u));
+    P.order[base[key] + off + rank] = t;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(P.order_hist, 0, sizeof(unsigned) * 2 * FIT_ORDER_BINS, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.careful_count, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int order_blocks = (P.ns + ORDER_THREADS - 1) / ORDER_THREADS;
+  k_order_count<<<min(order_blocks, 4 * sms), ORDER_THREADS, 0, st>>>(P);
+  k_order_scatter<<<order_blocks, ORDER_THREADS, 0, st>>>(P);
   const int threads = 128;
   const int blocks = (P.ns + threads - 1) / threads;
-  cudaError_t e = cudaMemsetAsync(P.careful_count, 0, sizeof(unsigned), st);
-  if (e != cudaSuccess) return e;
   k_fit<<<blocks, threads, 0, st>>>(P);
   return cudaGetLastError();
 }

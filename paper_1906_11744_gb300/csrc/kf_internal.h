@@ -170,14 +170,21 @@ struct FitParams {
   float* fit_C;           // [21][ns]
   float* fit_chi2;        // [ns]
   int* fit_status;        // [ns]
-  int* careful_list;      // [ns] tracks refitted with double-precision steps
+  int* careful_list;      // [ns] positions (in order) of the tracks refitted with double-precision steps
   unsigned* careful_count;  // zeroed before the launch
-  unsigned char* careful_flag;  // [ns] 0, or for the tracks of careful_list 1, or 2 when one
-                                // of their crossings has cos(alpha) < ADJOINT_CAREFUL_COS
-  float* ckpt;            // [ckpt_slices][27][ns] states before every ckpt_stride-th hit, or null
+  unsigned char* careful_flag;  // [ns] by track: 0, or for the tracks of careful_list 1, or 2 when
+                                // one of their crossings has cos(alpha) < ADJOINT_CAREFUL_COS
+  float* ckpt;            // [ckpt_slices][27][ns] by position: states before every ckpt_stride-th hit, or null
   int ckpt_stride;
   int ckpt_slices;        // checkpoints per track the buffer holds
+  // Tracks by decreasing hit count (duplicates last): thread i of the fit and
+  // of the adjoint takes track order[i], so that a warp's tracks run about the
+  // same number of steps and the checkpoints of a warp's step are adjacent.
+  int* order;             // [ns] written by launch_fit_main
+  unsigned* order_hist;   // [2 * FIT_ORDER_BINS] counts and cursors
 };
+
+constexpr int FIT_ORDER_BINS = 64;  // hit counts above 63 share the last bin
 
 constexpr int MAX_CKPT = KF_MAX_LAYERS;  // checkpoints per track at most
 // Checkpoints per track for tracks of up to max_len hits.
@@ -211,10 +218,11 @@ struct AdjParams {
   float* g_seed;               // [6][ns] or null
   float* g_align;              // [n_layers][2]
   double* g_align_acc;         // [2 * KF_MAX_LAYERS] accumulator
-  const int* careful_list;     // tracks the fit flagged as near-tangent ...
+  const int* careful_list;     // positions of the tracks the fit flagged as near-tangent ...
   const unsigned* careful_count;
   const unsigned char* careful_flag;  // ... and their per-track flag
-  const float* ckpt;           // the fit's checkpoints [slices][27][ns]
+  const float* ckpt;           // the fit's checkpoints [slices][27][ns] by position
+  const int* order;            // the fit's track order (position -> track)
 };
 
 // kf_adjoint.cu
