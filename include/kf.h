@@ -99,7 +99,7 @@ typedef struct {
   int persistent;         /* 1 = persistent work-queue launch, 0 = one warp per seed tile */
   int per_event;          /* 1 = bin, find and remove duplicates with one launch per event
                              (the plain form); 0 = one launch per step over the whole batch */
-  int ckpt_stride;        /* hits between forward checkpoints of the adjoint (0 = 2; 1..8) */
+  int ckpt_stride;        /* hits between forward checkpoints of the adjoint (0 = 1; 1..8) */
   int find_regcap;        /* 0 = finding kernel at the compiler's register count (blocks <= 256
                              threads); 1 = at most 102 registers, five blocks per SM (blocks
                              <= 128 threads).  The results are identical. */

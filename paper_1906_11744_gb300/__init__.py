@@ -58,7 +58,7 @@ def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1,
 
 def make_config(max_cands=6, max_holes=3, chi2_cut=30.0, dup_shared_frac=0.5, n_eta_bins=64,
                 n_phi_bins=1024, lanes_per_seed=0, block_threads=0, persistent=1, per_event=0,
-                ckpt_stride=2, find_regcap=0, dup_deta=0.0, dup_dphi=0.0, dup_dpt=0.0, seed_clean=0,
+                ckpt_stride=1, find_regcap=0, dup_deta=0.0, dup_dphi=0.0, dup_dpt=0.0, seed_clean=0,
                 seed_deta=0.05, seed_dphi=0.05, seed_dpt=0.0, seed_min_shared=1,
                 resolve_max_rounds=0) -> kf_config:
     """Algorithm settings (include/kf.h, kf_config).  The kinematic cuts of

@@ -26,10 +26,11 @@
 // the sum over its hits of (-(x g_y - y g_x)/R_L, -g_z), g the gradient with
 // respect to the raw position (x, y, z) of the hit; one pass over the hits
 // forms it from the hit gradients after the sweep.
-// Tracks with a crossing closer to tangent than cos(alpha) = 0.2 (the fit
-// marks them) go to a second pass that keeps their adjoints in double and runs
-// those steps in double; the rest, including tracks whose fit ran steps
-// between 0.2 and 0.5 in double, are reversed in FP32 from the checkpoints.
+// The tracks of the fit's careful list (a crossing with cos(alpha) < 0.5, or
+// a loose prior) go to a second pass that keeps their adjoints in double and
+// runs their steps with cos(alpha) < 0.2 in double; it can run beside the
+// FP32 pass, after the fit's own careful pass.  The rest are reversed in FP32
+// from the checkpoints.
 #include <type_traits>
 
 #include "kf_common.cuh"
@@ -665,20 +666,21 @@ __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, c
   for (int i = 0; i < 3; ++i) hbA[i] = (A)hb[i];
 }
 
-// Forward step of the FP32 pass, inlined (as rev_step_regs).
+// Forward step of the FP32 pass, inlined (as rev_step_regs): the state
+// before it at in[q * LD], the state after it to out[q * LD].
 template <bool EL>
-__device__ __forceinline__ void fwd_step_regs(const DevGeom& g, float* st, const Hit<float>& h, bool first,
-                                              bool last) {
+__device__ __forceinline__ void fwd_step_regs(const DevGeom& g, const float* in, float* out, const Hit<float>& h,
+                                              bool first, bool last) {
   float p[6], C[21];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) p[q] = st[q * LD];
+  for (int q = 0; q < 6; ++q) p[q] = in[q * LD];
 #pragma unroll
-  for (int q = 0; q < 21; ++q) C[q] = st[(6 + q) * LD];
+  for (int q = 0; q < 21; ++q) C[q] = in[(6 + q) * LD];
   fwd_step<float, EL>(g, p, C, h, first, last);
 #pragma unroll
-  for (int q = 0; q < 6; ++q) st[(27 + q) * LD] = p[q];
+  for (int q = 0; q < 6; ++q) out[q * LD] = p[q];
 #pragma unroll
-  for (int q = 0; q < 21; ++q) st[(27 + 6 + q) * LD] = C[q];
+  for (int q = 0; q < 21; ++q) out[(6 + q) * LD] = C[q];
 }
 
 // The same reverse step inlined into the FP32 pass, so that the adjoints stay
@@ -706,18 +708,8 @@ __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
   using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
   const int t = P.order[i];  // the track at position i of the fit's order (checkpoint column i)
-  if (!CAREFUL) {
-    // Tracks with a crossing below ADJ_CAREFUL_COS are the careful adjoint's,
-    // whose pass runs at the same time as this one.
-    if (P.careful_flag[t] == 2) return;
-    if ((P.keep && !P.keep[t]) || P.fit_status[t] != KF_FIT_OK) {
-      if (P.g_seed)  // not fitted: no contribution
-        for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
-      return;
-    }
-  } else if (P.careful_flag[t] != 2) {
-    return;  // no crossing below ADJ_CAREFUL_COS: the FP32 pass's
-  } else if (P.fit_status[t] != KF_FIT_OK) {
+  static_assert(CAREFUL, "the FP32 pass is adjoint_track_fp32");
+  if (P.fit_status[t] != KF_FIT_OK) {
     if (P.g_seed)
       for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
     return;
@@ -746,8 +738,7 @@ __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
           continue;
         }
       }
-      if constexpr (!CAREFUL) fwd_step_regs<EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
-      else fwd_step_store<float, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
+      fwd_step_store<float, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
     }
     for (int k = k1 - 1; k >= k0; --k) {
       const float* st = seg + (k - k0) * 27 * LD;
@@ -760,8 +751,7 @@ __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
         for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
         dbl = near_tangent(g, pf, g.radius[P.hlayer[hi]]);
       }
-      if constexpr (!CAREFUL) rev_step_regs<EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
-      else if (dbl) rev_step_store<double, A, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      if (dbl) rev_step_store<double, A, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
       else rev_step_store<float, A, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
       float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
       atomicAdd(gh + 0, (float)hb[0]);
@@ -774,13 +764,140 @@ __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
   }
 }
 
+// Asynchronous copy of one 4-byte word from global memory to this thread's
+// shared memory (cp.async: no register holds it in flight), and the waits.
+__device__ __forceinline__ void cp_async4(float* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared memory of the FP32 pass, in floats per thread column (LD apart):
+//   seg [stride - 1][27]  states before a segment's steps after its first
+//   ckb [2][27]           the segment's checkpoint (two buffers, by parity)
+//   hbf [2][stride][5]    its hits: x, y, z, layer and event-global index (int bits)
+//   lbf [2][stride]       event-local hit indices of a later segment
+__host__ __device__ constexpr int fp32_col_floats(int stride) { return 27 * (stride - 1) + 54 + 12 * stride; }
+
+// Reverse sweep of the track at position i of the fit's order in FP32 (the
+// tracks the fit left without a crossing below ADJ_CAREFUL_COS).  Segment c-1's
+// checkpoint and hits are copied into shared memory while segment c is
+// reversed, and segment c-2's hit indices with them, so that a segment's
+// steps wait on no global load.  col: this thread's column; s_al, s_R: the
+// layers' alignment and radii in shared memory.
+template <bool EL>
+__device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const float4* s_al, const float* s_R) {
+  const DevGeom& g = P.g;
+  const int t = P.order[i];
+  if (P.careful_flag[t]) return;  // the careful pass's, which runs beside this one
+  if ((P.keep && !P.keep[t]) || P.fit_status[t] != KF_FIT_OK) {
+    if (P.g_seed)  // not fitted: no contribution
+      for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
+    return;
+  }
+  const int n = P.n_list[t];
+  const int* lst = P.lists + (size_t)t * P.max_len;
+  const int hoff = P.hit_off[P.seed_event[t]];
+  const int stride = P.stride;
+  float* const seg = col;
+  float* const ckb = col + 27 * (stride - 1) * LD;
+  float* const hbf = ckb + 54 * LD;
+  float* const lbf = hbf + 10 * stride * LD;
+  auto seg_lists = [&](int c) {  // hit indices of segment c -> lbf[c & 1]
+    const int k0 = c * stride, k1 = min(n, k0 + stride);
+    float* d = lbf + (c & 1) * stride * LD;
+    for (int k = k0; k < k1; ++k) cp_async4(d + (k - k0) * LD, lst + k);
+  };
+  auto seg_data = [&](int c) {  // checkpoint and hits of segment c (its indices in lbf[c & 1])
+    const int k0 = c * stride, k1 = min(n, k0 + stride);
+    const float* ck = P.ckpt + (size_t)c * 27 * P.ns + i;
+    float* cd = ckb + (c & 1) * 27 * LD;
+    for (int q = 0; q < 27; ++q) cp_async4(cd + q * LD, ck + (size_t)q * P.ns);
+    const float* ls = lbf + (c & 1) * stride * LD;
+    float* hd = hbf + (c & 1) * 5 * stride * LD;
+    for (int k = k0; k < k1; ++k) {
+      const int hi = hoff + __float_as_int(ls[(k - k0) * LD]);
+      float* d = hd + (k - k0) * 5 * LD;
+      cp_async4(d, P.hx + hi);
+      cp_async4(d + LD, P.hy + hi);
+      cp_async4(d + 2 * LD, P.hz + hi);
+      cp_async4(d + 3 * LD, P.hlayer + hi);
+      d[4 * LD] = __int_as_float(hi);
+    }
+  };
+  float pb[6], Cb[6][6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    pb[a] = 0.f;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) Cb[a][b] = 0.f;
+  }
+  const int last = (n - 1) / stride;
+  seg_lists(last);
+  cp_async_commit();
+  cp_async_wait_all();
+  seg_data(last);
+  if (last > 0) seg_lists(last - 1);
+  cp_async_commit();
+  for (int c = last; c >= 0; --c) {
+    cp_async_wait_all();  // segment c's checkpoint and hits, segment c-1's indices
+    if (c > 0) {
+      seg_data(c - 1);
+      if (c > 1) seg_lists(c - 2);
+      cp_async_commit();
+    }
+    const int k0 = c * stride, k1 = min(n, k0 + stride);
+    const float* ck = ckb + (c & 1) * 27 * LD;
+    const float* hs = hbf + (c & 1) * 5 * stride * LD;
+    auto hit_of = [&](int k) {
+      const float* d = hs + (k - k0) * 5 * LD;
+      Hit<float> h;
+      h.L = __float_as_int(d[3 * LD]);
+      const float4 a = s_al[h.L];  // (cos, sin, dphi, az)
+      const float x = d[0], y = d[LD], z = d[2 * LD];
+      h.ca = a.x;
+      h.sa = a.y;
+      h.R = s_R[h.L];
+      h.mx = kfma(h.ca, x, -h.sa * y);
+      h.my = kfma(h.sa, x, h.ca * y);
+      h.mz = z - a.w;
+      return h;
+    };
+    // state before step k: the checkpoint for k0, else seg slot k - k0 - 1
+    for (int k = k0; k + 1 < k1; ++k)
+      fwd_step_regs<EL>(g, k == k0 ? ck : seg + (k - k0 - 1) * 27 * LD, seg + (k - k0) * 27 * LD, hit_of(k),
+                        k == 0, k + 1 == n);
+    for (int k = k1 - 1; k >= k0; --k) {
+      float hb[3];
+      rev_step_regs<EL>(g, k == k0 ? ck : seg + (k - k0 - 1) * 27 * LD, hit_of(k), k == 0, k + 1 == n, pb, Cb, hb);
+      const int hi = __float_as_int(hs[((k - k0) * 5 + 4) * LD]);
+      float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
+      atomicAdd(gh + 0, hb[0]);
+      atomicAdd(gh + 1, hb[1]);
+      atomicAdd(gh + 2, hb[2]);
+    }
+  }
+  if (P.g_seed) {
+    for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = pb[k];
+  }
+}
+
 template <bool CAREFUL, bool EL>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
-  extern __shared__ float seg_all[];  // [stride][27][LD]
+  extern __shared__ float seg_all[];  // careful pass: [stride][27][LD]; FP32 pass: columns of fp32_col_floats
   float* seg = seg_all + threadIdx.x;
   if constexpr (!CAREFUL) {
+    __shared__ float4 s_al[KF_MAX_LAYERS];
+    __shared__ float s_R[KF_MAX_LAYERS];
+    for (int l = threadIdx.x; l < P.g.n_layers; l += blockDim.x) {
+      const Align4 a = P.align[l];
+      s_al[l] = make_float4(a.ca, a.sa, a.dphi, a.az);
+      s_R[l] = P.g.radius[l];
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P.ns) adjoint_track<false, EL>(P, i, seg);
+    if (i < P.ns) adjoint_track_fp32<EL>(P, i, seg, s_al, s_R);
   } else {
     const unsigned n = *P.careful_count;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -831,20 +948,22 @@ cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(P.g_align_acc, 0, sizeof(double) * 2 * KF_MAX_LAYERS, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.g_hits, 0, sizeof(float) * 3 * (size_t)P.n_hits, st);
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
-  e = cudaFuncSetAttribute(k_adjoint<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int smem_c = (int)(sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS);
+  const int smem_f = (int)(sizeof(float) * fp32_col_floats(P.stride) * (size_t)ADJ_THREADS);
+  e = cudaFuncSetAttribute(k_adjoint<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_f);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_adjoint<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_adjoint<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_f);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_adjoint<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
   return e;
 }
 
 cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
-  const size_t smem = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
+  const size_t smem_c = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
+  const size_t smem_f = sizeof(float) * fp32_col_floats(P.stride) * (size_t)ADJ_THREADS;
   bool el = false;  // energy loss on any layer: the variant with its code
   for (int l = 0; l < P.g.n_layers; ++l) el = el || P.g.eloss[l] > 0.f;
   const int grid_all = (P.ns + ADJ_THREADS - 1) / ADJ_THREADS;
@@ -852,11 +971,11 @@ cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t s
   // over however many there are
   const int grid_careful = (P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1;
   if (!careful) {
-    if (el) k_adjoint<false, true><<<grid_all, ADJ_THREADS, smem, st>>>(P);
-    else k_adjoint<false, false><<<grid_all, ADJ_THREADS, smem, st>>>(P);
+    if (el) k_adjoint<false, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
+    else k_adjoint<false, false><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
   } else {
-    if (el) k_adjoint<true, true><<<grid_careful, ADJ_THREADS, smem, st>>>(P);
-    else k_adjoint<true, false><<<grid_careful, ADJ_THREADS, smem, st>>>(P);
+    if (el) k_adjoint<true, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+    else k_adjoint<true, false><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
   }
   return cudaGetLastError();
 }

@@ -45,7 +45,7 @@ struct kf_ctx {
   DevBuf sc_kin, sc_seed, clean_order, kept_cnt, sc_list, sc_list_cnt;
   // fit
   DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count, careful_flag, ckpt;
-  DevBuf fit_order, fit_order_hist;
+  DevBuf fit_order;
   bool want_ckpt = false;
   int given_max_len = 0;
   bool found = false, deduped = false, fitted = false;
@@ -65,6 +65,10 @@ struct kf_ctx {
   // Side stream (highest priority) for the careful passes that run beside
   // the main passes; fork/join events.
   cudaStream_t side = nullptr;
+  // Inside a graph capture with the adjoint: kf_fit_tracks leaves the fit's
+  // careful pass to kf_fit_adjoint, which runs it on the side stream before
+  // the careful adjoint, beside the FP32 adjoint (which needs neither).
+  bool defer_careful_fit = false, careful_fit_pending = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err = "";
 };
@@ -322,7 +326,7 @@ static std::vector<DevBuf*> all_bufs(kf_ctx* ctx) {
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
                     &ctx->clean_order, &ctx->kept_cnt, &ctx->sc_list, &ctx->sc_list_cnt, &ctx->sfit,
-                    &ctx->sflag, &ctx->skeys, &ctx->x0map, &ctx->fit_order, &ctx->fit_order_hist};
+                    &ctx->sflag, &ctx->skeys, &ctx->x0map, &ctx->fit_order};
 }
 
 int kf_destroy(kf_ctx* ctx) {
@@ -446,7 +450,6 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->careful_count, 64));
   CK(grow(ctx->careful_flag, (size_t)n));
   CK(grow(ctx->fit_order, sizeof(int) * (size_t)n));
-  CK(grow(ctx->fit_order_hist, sizeof(unsigned) * 2 * FIT_ORDER_BINS));
   if (ctx->cfg.seed_clean) {
     CK(grow(ctx->sc_kin, sizeof(float4) * (size_t)n));
     CK(grow(ctx->sc_seed, sizeof(int4) * (size_t)n));
@@ -781,7 +784,6 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   F.careful_count = ptr<unsigned>(ctx->careful_count);
   F.careful_flag = ptr<unsigned char>(ctx->careful_flag);
   F.order = ptr<int>(ctx->fit_order);
-  F.order_hist = ptr<unsigned>(ctx->fit_order_hist);
   F.ckpt_stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
   F.ckpt = nullptr;
   F.ckpt_slices = 0;
@@ -825,7 +827,13 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
     F.ckpt = ptr<float>(ctx->ckpt);
   }
   stage_mark(ctx, 6, st);
-  CK(launch_fit(F, st));
+  if (ctx->defer_careful_fit) {
+    CK(launch_fit_main(F, st));
+    ctx->careful_fit_pending = true;
+  } else {
+    CK(launch_fit(F, st));
+    ctx->careful_fit_pending = false;
+  }
   stage_mark(ctx, 7, st);
   ctx->last_fit = F;
   ctx->fitted = true;
@@ -847,7 +855,8 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
     ctx->last_fit.ckpt_slices = ckpt_slices_for(ctx->last_fit.max_len, stride);
     CK(grow(ctx->ckpt, sizeof(float) * (size_t)ctx->last_fit.ckpt_slices * 27 * (size_t)ctx->n_seeds));
     ctx->last_fit.ckpt = ptr<float>(ctx->ckpt);
-    CK(launch_fit(ctx->last_fit, st));
+    CK(launch_fit_main(ctx->last_fit, st));
+    ctx->careful_fit_pending = true;
   }
   const FitParams& F = ctx->last_fit;
   const size_t ns = (size_t)ctx->n_seeds, nh = (size_t)ctx->n_hits;
@@ -889,7 +898,11 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   stage_mark(ctx, 8, st);
   CK(launch_adjoint_begin(A, st));
   CK(fork_side(ctx, st));
-  CK(launch_adjoint_pass(A, true, ctx->side));  // near-tangent tracks beside the FP32 pass
+  // the careful tracks beside the FP32 pass: their fit (if still to run),
+  // then their adjoint
+  if (ctx->careful_fit_pending) CK(launch_fit_careful(F, ctx->side));
+  ctx->careful_fit_pending = false;
+  CK(launch_adjoint_pass(A, true, ctx->side));
   CK(launch_adjoint_pass(A, false, st));
   CK(join_side(ctx, st));
   CK(launch_adjoint_end(A, st));
@@ -1005,7 +1018,9 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = kf_find_tracks(ctx, stream);
   if (rc == KF_OK) rc = kf_remove_duplicates(ctx, stream);
+  ctx->defer_careful_fit = with_adjoint != 0;
   if (rc == KF_OK) rc = kf_fit_tracks(ctx, KF_FIT_FOUND, nullptr, nullptr, 0, 1, stream);
+  ctx->defer_careful_fit = false;
   if (rc == KF_OK && with_adjoint)  // gradient into context buffers; kf_get_gradient reads them
     rc = kf_fit_adjoint(ctx, ptr<float>(ctx->adj_align), ptr<float>(ctx->adj_hits), ptr<float>(ctx->adj_seed), 1,
                         stream);

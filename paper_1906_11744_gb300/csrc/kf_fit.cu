@@ -19,6 +19,7 @@ namespace kfg {
 namespace {
 
 constexpr float CAREFUL_COS = 0.5f;
+constexpr int FIT_THREADS = 128;  // threads per block of the FP32 pass
 
 // One Kalman step in scalar type T: propagate (unless first), update with the
 // corrected hit, scatter unless last.  Returns a KF_FIT_* status.
@@ -48,10 +49,60 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   return KF_FIT_OK;
 }
 
+// The fit's track order, per window of ORDER_WINDOW consecutive tracks: by
+// decreasing hit count (tracks removed as duplicates count 0), so that a
+// warp's tracks run about the same number of steps, while the per-track
+// reads and writes of a window stay close together in time (they meet in L2).
+// The order within a hit count is not fixed; no result depends on it.
+constexpr int ORDER_WINDOW = 4096, ORDER_THREADS = 512, ORDER_BINS = 64;
+
+__device__ __forceinline__ int order_key(const FitParams& P, int t) {
+  if (P.keep && !P.keep[t]) return 0;
+  return min(max(P.n_list[t], 0), ORDER_BINS - 1);
+}
+
+// One block per window: counts per hit count, an exclusive prefix over the
+// counts from the longest down, then each track's position (one shared-memory
+// atomic per hit count and warp).
+__global__ void __launch_bounds__(ORDER_THREADS) k_fit_order(const FitParams P) {
+  static_assert(ORDER_BINS == 64, "two bins per lane");
+  __shared__ unsigned cnt[ORDER_BINS], cur[ORDER_BINS];
+  const int w0 = blockIdx.x * ORDER_WINDOW;
+  const int w1 = min(P.ns, w0 + ORDER_WINDOW);
+  for (int b = threadIdx.x; b < ORDER_BINS; b += blockDim.x) cnt[b] = 0u;
+  __syncthreads();
+  for (int t = w0 + threadIdx.x; t < w1; t += blockDim.x) atomicAdd(&cnt[order_key(P, t)], 1u);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {  // lane j: bins 63 - 2j and 62 - 2j
+    const unsigned a = cnt[63 - 2 * lane], b = cnt[62 - 2 * lane];
+    unsigned incl = a + b;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    cur[63 - 2 * lane] = incl - a - b;
+    cur[62 - 2 * lane] = incl - b;
+  }
+  __syncthreads();
+  for (int r = 0; r < ORDER_WINDOW; r += ORDER_THREADS) {
+    const int t = w0 + r + threadIdx.x;
+    const int key = t < w1 ? order_key(P, t) : ORDER_BINS;  // ORDER_BINS: no track
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    if (key < ORDER_BINS) {
+      const int leader = __ffs(same) - 1;
+      unsigned pos = 0;
+      if (lane == leader) pos = atomicAdd(&cur[key], (unsigned)__popc(same));
+      pos = __shfl_sync(same, pos, leader) + __popc(same & ((1u << lane) - 1u));
+      P.order[w0 + pos] = t;
+    }
+  }
+}
+
 // Track at position i of the fit's order; checkpoints go to column i.
 template <bool CAREFUL>
-__device__ __forceinline__ void fit_track(const FitParams& P, int i) {
-  const int t = P.order[i];
+__device__ __forceinline__ void fit_track(const FitParams& P, int i, int t) {
   if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;  // set below if the track is left to the careful pass
   if (!CAREFUL && P.keep && !P.keep[t]) {  // removed as a duplicate: zero outputs
 #pragma unroll
@@ -79,7 +130,6 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i) {
   const int n = P.n_list[t];
   const int* lst = P.lists + (size_t)t * P.max_len;
   float chi2 = 0.f;
-  float min_cos = 1.f;
   int status = KF_FIT_OK;
 #pragma unroll 1
   for (int k = 0; k < n && status == KF_FIT_OK; ++k) {
@@ -120,7 +170,6 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i) {
         float zc, cosa;
         if (!crossing(p, g.radius[L], g.kb, zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
         careful = cosa < CAREFUL_COS;
-        min_cos = fminf(min_cos, cosa);
       }
       if (loose && k < LOOSE_STEPS) careful = true;  // the first steps against a loose prior
       status = careful ? fit_step<double>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
@@ -133,93 +182,30 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i) {
   for (int k = 0; k < 21; ++k) P.fit_C[(size_t)k * P.ns + t] = C[k];
   P.fit_chi2[t] = chi2;
   P.fit_status[t] = status;
-  if (CAREFUL && P.careful_flag) P.careful_flag[t] = min_cos < ADJOINT_CAREFUL_COS ? 2 : 1;
+
 }
 
-__global__ void __launch_bounds__(128) k_fit(const FitParams P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P.ns) fit_track<false>(P, i);
+__global__ void __launch_bounds__(FIT_THREADS) k_fit(const FitParams P) {
+  const int i = blockIdx.x * FIT_THREADS + threadIdx.x;
+  if (i < P.ns) fit_track<false>(P, i, P.order[i]);
 }
 
 // Second pass over the flagged tracks (grid-stride over their list).
 __global__ void __launch_bounds__(128) k_fit_careful(const FitParams P) {
   const unsigned n = *P.careful_count;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    fit_track<true>(P, P.careful_list[i]);
-}
-
-// The fit's track order: a counting sort by hit count, decreasing; tracks
-// removed as duplicates count as 0 hits and come last.  Positions within a
-// bin are taken by atomics (the order within a bin is not fixed; each track's
-// results do not depend on it).
-__device__ __forceinline__ int order_key(const FitParams& P, int t) {
-  if (P.keep && !P.keep[t]) return 0;
-  return min(max(P.n_list[t], 0), FIT_ORDER_BINS - 1);
-}
-
-constexpr int ORDER_THREADS = 256;
-
-__global__ void __launch_bounds__(ORDER_THREADS) k_order_count(const FitParams P) {
-  __shared__ unsigned h[FIT_ORDER_BINS];
-  for (int b = threadIdx.x; b < FIT_ORDER_BINS; b += blockDim.x) h[b] = 0u;
-  __syncthreads();
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P.ns; t += gridDim.x * blockDim.x)
-    atomicAdd(&h[order_key(P, t)], 1u);
-  __syncthreads();
-  for (int b = threadIdx.x; b < FIT_ORDER_BINS; b += blockDim.x)
-    if (h[b]) atomicAdd(&P.order_hist[b], h[b]);
-}
-
-// One track per thread: position = (tracks in bins of more hits) + the
-// track's place among its bin's tracks (one atomic per bin and warp).
-__global__ void __launch_bounds__(ORDER_THREADS) k_order_scatter(const FitParams P) {
-  static_assert(FIT_ORDER_BINS == 64, "two bins per lane");
-  __shared__ unsigned base[FIT_ORDER_BINS];
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 32) {
-    // lane j holds bins 63 - 2j and 62 - 2j; exclusive prefix over lanes
-    const unsigned a = P.order_hist[63 - 2 * lane], b = P.order_hist[62 - 2 * lane];
-    unsigned incl = a + b;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
-    }
-    const unsigned excl = incl - a - b;
-    base[63 - 2 * lane] = excl;
-    base[62 - 2 * lane] = excl + a;
-  }
-  __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int key = t < P.ns ? order_key(P, t) : FIT_ORDER_BINS;  // FIT_ORDER_BINS: no track
-  const unsigned same = __match_any_sync(0xffffffffu, key);
-  if (key < FIT_ORDER_BINS) {
-    const int leader = __ffs(same) - 1;
-    unsigned off = 0;
-    if (lane == leader) off = atomicAdd(&P.order_hist[FIT_ORDER_BINS + key], (unsigned)__popc(same));
-    off = __shfl_sync(same, off, leader);
-    const unsigned rank = __popc(same & ((1u << lane) - 1u));
-    P.order[base[key] + off + rank] = t;
-  }
+    fit_track<true>(P, P.careful_list[i], P.order[P.careful_list[i]]);
 }
 
 }  // namespace
 
 cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(P.order_hist, 0, sizeof(unsigned) * 2 * FIT_ORDER_BINS, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.careful_count, 0, sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(P.careful_count, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  const int order_blocks = (P.ns + ORDER_THREADS - 1) / ORDER_THREADS;
-  k_order_count<<<min(order_blocks, 4 * sms), ORDER_THREADS, 0, st>>>(P);
-  k_order_scatter<<<order_blocks, ORDER_THREADS, 0, st>>>(P);
-  const int threads = 128;
-  const int blocks = (P.ns + threads - 1) / threads;
-  k_fit<<<blocks, threads, 0, st>>>(P);
+  k_fit_order<<<(P.ns + ORDER_WINDOW - 1) / ORDER_WINDOW, ORDER_THREADS, 0, st>>>(P);
+  const int blocks = (P.ns + FIT_THREADS - 1) / FIT_THREADS;
+  k_fit<<<blocks, FIT_THREADS, 0, st>>>(P);
   return cudaGetLastError();
 }
 

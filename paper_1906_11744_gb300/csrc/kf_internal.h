@@ -172,19 +172,15 @@ struct FitParams {
   int* fit_status;        // [ns]
   int* careful_list;      // [ns] positions (in order) of the tracks refitted with double-precision steps
   unsigned* careful_count;  // zeroed before the launch
-  unsigned char* careful_flag;  // [ns] by track: 0, or for the tracks of careful_list 1, or 2 when
-                                // one of their crossings has cos(alpha) < ADJOINT_CAREFUL_COS
+  unsigned char* careful_flag;  // [ns] by track: 1 for the tracks of careful_list, else 0
   float* ckpt;            // [ckpt_slices][27][ns] by position: states before every ckpt_stride-th hit, or null
   int ckpt_stride;
   int ckpt_slices;        // checkpoints per track the buffer holds
-  // Tracks by decreasing hit count (duplicates last): thread i of the fit and
-  // of the adjoint takes track order[i], so that a warp's tracks run about the
-  // same number of steps and the checkpoints of a warp's step are adjacent.
+  // Tracks of each window of 4,096 by decreasing hit count (duplicates
+  // last): position i of the fit and of the adjoint takes track order[i], so
+  // that a warp's tracks run about the same number of steps.
   int* order;             // [ns] written by launch_fit_main
-  unsigned* order_hist;   // [2 * FIT_ORDER_BINS] counts and cursors
 };
-
-constexpr int FIT_ORDER_BINS = 64;  // hit counts above 63 share the last bin
 
 constexpr int MAX_CKPT = KF_MAX_LAYERS;  // checkpoints per track at most
 // Checkpoints per track for tracks of up to max_len hits.
@@ -192,7 +188,7 @@ inline int ckpt_slices_for(int max_len, int stride) {
   const int n = (max_len + stride - 1) / stride;
   return n < MAX_CKPT ? n : MAX_CKPT;
 }
-constexpr int DEFAULT_CKPT_STRIDE = 2;
+constexpr int DEFAULT_CKPT_STRIDE = 1;
 constexpr int MAX_CKPT_STRIDE = 8;
 
 struct AdjParams {
