@@ -27,10 +27,11 @@
 // respect to the raw position (x, y, z) of the hit; one pass over the hits
 // forms it from the hit gradients after the sweep.
 // The tracks of the fit's careful list (a crossing with cos(alpha) < 0.5, or
-// a loose prior) go to a second pass that keeps their adjoints in double and
-// runs their steps with cos(alpha) < 0.2 in double; it can run beside the
-// FP32 pass, after the fit's own careful pass.  The rest are reversed in FP32
-// from the checkpoints.
+// a loose prior) are reversed by separate passes, which can run beside the
+// FP32 pass after the fit's own careful pass: those with a crossing below
+// cos(alpha) = 0.2 keep their adjoints in double and run such steps in
+// double; the others run the FP32 code.  The rest are reversed in FP32 from
+// the checkpoints.
 #include <type_traits>
 
 #include "kf_common.cuh"
@@ -786,11 +787,14 @@ __host__ __device__ constexpr int fp32_col_floats(int stride) { return 27 * (str
 // reversed, and segment c-2's hit indices with them, so that a segment's
 // steps wait on no global load.  col: this thread's column; s_al, s_R: the
 // layers' alignment and radii in shared memory.
+// listed: the track comes from the fit's careful list (else careful tracks
+// are skipped: the careful passes take them).
 template <bool EL>
-__device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const float4* s_al, const float* s_R) {
+__device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const float4* s_al, const float* s_R,
+                                   bool listed) {
   const DevGeom& g = P.g;
   const int t = P.order[i];
-  if (P.careful_flag[t]) return;  // the careful pass's, which runs beside this one
+  if (!listed && P.careful_flag[t]) return;  // the careful passes', which run beside this one
   if ((P.keep && !P.keep[t]) || P.fit_status[t] != KF_FIT_OK) {
     if (P.g_seed)  // not fitted: no contribution
       for (int k = 0; k < 6; ++k) P.g_seed[(size_t)k * P.ns + t] = 0.f;
@@ -883,11 +887,16 @@ __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const 
   }
 }
 
-template <bool CAREFUL, bool EL>
+// Passes of the adjoint: the FP32 pass over every position (the tracks of
+// the fit's careful list skipped), and over the careful list the entries
+// without CAREFUL_DBL_BIT in FP32 and those with it in double.
+enum { ADJ_ALL = 0, ADJ_LIST_FP32 = 1, ADJ_LIST_DBL = 2 };
+
+template <int MODE, bool EL>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
-  extern __shared__ float seg_all[];  // careful pass: [stride][27][LD]; FP32 pass: columns of fp32_col_floats
+  extern __shared__ float seg_all[];  // double pass: [stride][27][LD]; FP32 passes: columns of fp32_col_floats
   float* seg = seg_all + threadIdx.x;
-  if constexpr (!CAREFUL) {
+  if constexpr (MODE != ADJ_LIST_DBL) {
     __shared__ float4 s_al[KF_MAX_LAYERS];
     __shared__ float s_R[KF_MAX_LAYERS];
     for (int l = threadIdx.x; l < P.g.n_layers; l += blockDim.x) {
@@ -896,12 +905,20 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
       s_R[l] = P.g.radius[l];
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P.ns) adjoint_track_fp32<EL>(P, i, seg, s_al, s_R);
-  } else {
-    const unsigned n = *P.careful_count;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      adjoint_track<true, EL>(P, P.careful_list[i], seg);
+    if constexpr (MODE == ADJ_ALL) {
+      const int i = blockIdx.x * blockDim.x + threadIdx.x;
+      if (i < P.ns) adjoint_track_fp32<EL>(P, i, seg, s_al, s_R, false);
+    } else {
+      const unsigned n = *P.careful_count;
+      for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const unsigned v = (unsigned)P.careful_list[j];
+        if (!(v & CAREFUL_DBL_BIT)) adjoint_track_fp32<EL>(P, (int)v, seg, s_al, s_R, true);
+      }
+    }
+  } else {  // packed list: the first blocks take all of them and the others end at once
+    const unsigned n = *P.dbl_count;
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+      adjoint_track<true, EL>(P, P.dbl_list[j], seg);
   }
 }
 
@@ -950,13 +967,11 @@ cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int smem_c = (int)(sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS);
   const int smem_f = (int)(sizeof(float) * fp32_col_floats(P.stride) * (size_t)ADJ_THREADS);
-  e = cudaFuncSetAttribute(k_adjoint<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_f);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_f);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
+  const void* fns[6] = {(const void*)k_adjoint<ADJ_ALL, false>,       (const void*)k_adjoint<ADJ_LIST_FP32, false>,
+                        (const void*)k_adjoint<ADJ_LIST_DBL, false>,  (const void*)k_adjoint<ADJ_ALL, true>,
+                        (const void*)k_adjoint<ADJ_LIST_FP32, true>,  (const void*)k_adjoint<ADJ_LIST_DBL, true>};
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+    e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, k % 3 == 2 ? smem_c : smem_f);
   return e;
 }
 
@@ -971,11 +986,13 @@ cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t s
   // over however many there are
   const int grid_careful = (P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1;
   if (!careful) {
-    if (el) k_adjoint<false, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
-    else k_adjoint<false, false><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
-  } else {
-    if (el) k_adjoint<true, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
-    else k_adjoint<true, false><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+    if (el) k_adjoint<ADJ_ALL, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
+    else k_adjoint<ADJ_ALL, false><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
+  } else {  // the careful list: its tracks with double steps, then the others
+    if (el) k_adjoint<ADJ_LIST_DBL, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+    else k_adjoint<ADJ_LIST_DBL, false><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+    if (el) k_adjoint<ADJ_LIST_FP32, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
+    else k_adjoint<ADJ_LIST_FP32, false><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
   }
   return cudaGetLastError();
 }

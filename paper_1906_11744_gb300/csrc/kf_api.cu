@@ -45,7 +45,7 @@ struct kf_ctx {
   DevBuf sc_kin, sc_seed, clean_order, kept_cnt, sc_list, sc_list_cnt;
   // fit
   DevBuf given_lists, given_n, fit_p, fit_C, fit_chi2, fit_status, careful_list, careful_count, careful_flag, ckpt;
-  DevBuf fit_order;
+  DevBuf fit_order, dbl_list;
   bool want_ckpt = false;
   int given_max_len = 0;
   bool found = false, deduped = false, fitted = false;
@@ -326,7 +326,7 @@ static std::vector<DevBuf*> all_bufs(kf_ctx* ctx) {
                     &ctx->careful_count, &ctx->adj_align_acc, &ctx->adj_align, &ctx->adj_hits,
                     &ctx->adj_seed, &ctx->careful_flag, &ctx->ckpt, &ctx->sc_kin, &ctx->sc_seed,
                     &ctx->clean_order, &ctx->kept_cnt, &ctx->sc_list, &ctx->sc_list_cnt, &ctx->sfit,
-                    &ctx->sflag, &ctx->skeys, &ctx->x0map, &ctx->fit_order};
+                    &ctx->sflag, &ctx->skeys, &ctx->x0map, &ctx->fit_order, &ctx->dbl_list};
 }
 
 int kf_destroy(kf_ctx* ctx) {
@@ -450,6 +450,7 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(grow(ctx->careful_count, 64));
   CK(grow(ctx->careful_flag, (size_t)n));
   CK(grow(ctx->fit_order, sizeof(int) * (size_t)n));
+  CK(grow(ctx->dbl_list, sizeof(int) * (size_t)n));
   if (ctx->cfg.seed_clean) {
     CK(grow(ctx->sc_kin, sizeof(float4) * (size_t)n));
     CK(grow(ctx->sc_seed, sizeof(int4) * (size_t)n));
@@ -784,6 +785,8 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
   F.careful_count = ptr<unsigned>(ctx->careful_count);
   F.careful_flag = ptr<unsigned char>(ctx->careful_flag);
   F.order = ptr<int>(ctx->fit_order);
+  F.dbl_list = ptr<int>(ctx->dbl_list);
+  F.dbl_count = ptr<unsigned>(ctx->careful_count) + 1;
   F.ckpt_stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
   F.ckpt = nullptr;
   F.ckpt_slices = 0;
@@ -893,6 +896,8 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   A.careful_list = F.careful_list;
   A.careful_count = F.careful_count;
   A.careful_flag = F.careful_flag;
+  A.dbl_list = F.dbl_list;
+  A.dbl_count = F.dbl_count;
   A.ckpt = F.ckpt;
   A.order = F.order;
   stage_mark(ctx, 8, st);

@@ -101,8 +101,10 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_fit_order(const FitParams P) 
 }
 
 // Track at position i of the fit's order; checkpoints go to column i.
+// Returns, in the careful pass, whether a crossing of the track has
+// cos(alpha) < ADJOINT_CAREFUL_COS (its adjoint then needs double steps).
 template <bool CAREFUL>
-__device__ __forceinline__ void fit_track(const FitParams& P, int i, int t) {
+__device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
   if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;  // set below if the track is left to the careful pass
   if (!CAREFUL && P.keep && !P.keep[t]) {  // removed as a duplicate: zero outputs
 #pragma unroll
@@ -111,7 +113,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i, int t) {
     for (int k = 0; k < 21; ++k) P.fit_C[(size_t)k * P.ns + t] = 0.f;
     P.fit_chi2[t] = 0.f;
     P.fit_status[t] = KF_FIT_SKIPPED;
-    return;
+    return false;
   }
   const DevGeom& g = P.g;
   float p[6], C[21];
@@ -124,13 +126,14 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i, int t) {
   if (!CAREFUL && loose) {
     P.careful_list[atomicAdd(P.careful_count, 1u)] = i;
     if (P.careful_flag) P.careful_flag[t] = 1;
-    return;
+    return false;
   }
   const int hoff = P.hit_off[P.seed_event[t]];
   const int n = P.n_list[t];
   const int* lst = P.lists + (size_t)t * P.max_len;
   float chi2 = 0.f;
   int status = KF_FIT_OK;
+  bool adj_dbl = false;
 #pragma unroll 1
   for (int k = 0; k < n && status == KF_FIT_OK; ++k) {
     if (P.ckpt && k % P.ckpt_stride == 0 && k / P.ckpt_stride < P.ckpt_slices) {  // state before hit k
@@ -151,7 +154,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i, int t) {
         if (cosa < CAREFUL_COS) {  // leave the track to the careful pass
           P.careful_list[atomicAdd(P.careful_count, 1u)] = i;
           if (P.careful_flag) P.careful_flag[t] = 1;
-          return;
+          return false;
         }
       }
       Frame f;
@@ -170,6 +173,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i, int t) {
         float zc, cosa;
         if (!crossing(p, g.radius[L], g.kb, zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
         careful = cosa < CAREFUL_COS;
+        adj_dbl = adj_dbl || cosa < ADJOINT_CAREFUL_COS;
       }
       if (loose && k < LOOSE_STEPS) careful = true;  // the first steps against a loose prior
       status = careful ? fit_step<double>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
@@ -182,7 +186,7 @@ __device__ __forceinline__ void fit_track(const FitParams& P, int i, int t) {
   for (int k = 0; k < 21; ++k) P.fit_C[(size_t)k * P.ns + t] = C[k];
   P.fit_chi2[t] = chi2;
   P.fit_status[t] = status;
-
+  return adj_dbl;
 }
 
 __global__ void __launch_bounds__(FIT_THREADS) k_fit(const FitParams P) {
@@ -190,11 +194,18 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(const FitParams P) {
   if (i < P.ns) fit_track<false>(P, i, P.order[i]);
 }
 
-// Second pass over the flagged tracks (grid-stride over their list).
+// Second pass over the flagged tracks (grid-stride over their list).  A
+// track whose adjoint needs double steps gets CAREFUL_DBL_BIT in its entry
+// and is listed in dbl_list.
 __global__ void __launch_bounds__(128) k_fit_careful(const FitParams P) {
   const unsigned n = *P.careful_count;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    fit_track<true>(P, P.careful_list[i], P.order[P.careful_list[i]]);
+  for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const unsigned v = (unsigned)P.careful_list[j];
+    const int pos = (int)(v & ~CAREFUL_DBL_BIT);
+    const bool dbl = fit_track<true>(P, pos, P.order[pos]);
+    P.careful_list[j] = (int)(dbl ? (v | CAREFUL_DBL_BIT) : (v & ~CAREFUL_DBL_BIT));
+    if (dbl) P.dbl_list[atomicAdd(P.dbl_count, 1u)] = pos;  // packed, so that few blocks hold them
+  }
 }
 
 }  // namespace
@@ -215,6 +226,8 @@ cudaError_t launch_fit_careful(const FitParams& P, cudaStream_t st) {
   // them, striding over however many there are
   const int threads = 128;
   const int careful_blocks = (P.ns / 20 + threads - 1) / threads + 1;
+  cudaError_t e = cudaMemsetAsync(P.dbl_count, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
   k_fit_careful<<<careful_blocks, threads, 0, st>>>(P);
   return cudaGetLastError();
 }

@@ -146,6 +146,7 @@ struct SeedCleanParams {
 // The adjoint redoes in double only the steps closer to tangent than this
 // (its tolerance is looser than the fit's; the fit's threshold is 0.5).
 constexpr float ADJOINT_CAREFUL_COS = 0.2f;
+constexpr unsigned CAREFUL_DBL_BIT = 0x80000000u;  // careful_list entry: a crossing below ADJOINT_CAREFUL_COS
 
 constexpr int DEDUP_PARTNER_CAP = 32;
 constexpr int DEDUP_CONF_CAP = 16;
@@ -170,9 +171,12 @@ struct FitParams {
   float* fit_C;           // [21][ns]
   float* fit_chi2;        // [ns]
   int* fit_status;        // [ns]
-  int* careful_list;      // [ns] positions (in order) of the tracks refitted with double-precision steps
+  int* careful_list;      // [ns] positions (in order) of the tracks refitted with double-precision steps;
+                          // the careful pass adds CAREFUL_DBL_BIT where the adjoint needs double steps
   unsigned* careful_count;  // zeroed before the launch
   unsigned char* careful_flag;  // [ns] by track: 1 for the tracks of careful_list, else 0
+  int* dbl_list;          // [ns] positions of the careful tracks with CAREFUL_DBL_BIT, packed
+  unsigned* dbl_count;    // their number (zeroed before the careful pass)
   float* ckpt;            // [ckpt_slices][27][ns] by position: states before every ckpt_stride-th hit, or null
   int ckpt_stride;
   int ckpt_slices;        // checkpoints per track the buffer holds
@@ -217,6 +221,8 @@ struct AdjParams {
   const int* careful_list;     // positions of the tracks the fit flagged as near-tangent ...
   const unsigned* careful_count;
   const unsigned char* careful_flag;  // ... and their per-track flag
+  const int* dbl_list;         // the careful tracks whose adjoint needs double steps, packed
+  const unsigned* dbl_count;
   const float* ckpt;           // the fit's checkpoints [slices][27][ns] by position
   const int* order;            // the fit's track order (position -> track)
 };
