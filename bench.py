@@ -692,7 +692,7 @@ def main():
                "config": {"workload": workload_desc(args.config) + (f" (events={args.events})" if args.events else ""),
                           "seeds_per_gpu": n_seeds, "hits_per_gpu": b.n_hits,
                           "l2": "flushed (2x L2 write) before every timed step",
-                          "launch": "one CUDA graph per step: bin (5 kernels) + find + dedup + fit (track order: 2, FP32 pass, near-tangent pass) + adjoint (FP32 pass, near-tangent pass, alignment sum over hits, finish: 4)",
+                          "launch": "one CUDA graph per step: bin (5 kernels) + find + dedup + fit (track order, FP32 pass, careful pass) + adjoint (FP32 pass, careful-list passes in double and FP32, finish: 4)",
                           "find_shape": shape or None,
                           "autotuned": None if tune is None else {
                               "lanes_per_seed": int(tune[np.argmin(tune[:, 4])][0]),

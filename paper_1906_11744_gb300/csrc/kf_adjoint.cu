@@ -24,8 +24,9 @@
 // Alignment: the corrected position depends on the layer's offsets only, and
 // a rotation keeps cross products, so the alignment gradient of layer L is
 // the sum over its hits of (-(x g_y - y g_x)/R_L, -g_z), g the gradient with
-// respect to the raw position (x, y, z) of the hit; one pass over the hits
-// forms it from the hit gradients after the sweep.
+// respect to the raw position (x, y, z) of the hit; each reverse step adds
+// its hit's share to its layer's sums (per block in shared memory, then in
+// double precision across blocks).
 // The tracks of the fit's careful list (a crossing with cos(alpha) < 0.5, or
 // a loose prior) are reversed by separate passes, which can run beside the
 // FP32 pass after the fit's own careful pass: those with a crossing below
@@ -138,6 +139,7 @@ constexpr float ADJ_CAREFUL_COS = ADJOINT_CAREFUL_COS;
 // of the segment buffer in shared memory.
 constexpr int ADJ_THREADS = 128;
 constexpr int LD = ADJ_THREADS;
+static_assert((LD & (LD - 1)) == 0, "column rotation by a mask");
 
 // Derivatives of f1 and f2 (the helix functions of kf_common.cuh) in psi:
 // f1' = -(sin psi + 2 f1)/psi, f2' = (cos psi - 2 f2)/psi, by the term-wise
@@ -758,6 +760,10 @@ __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
       atomicAdd(gh + 0, (float)hb[0]);
       atomicAdd(gh + 1, (float)hb[1]);
       atomicAdd(gh + 2, (float)hb[2]);
+      // the layer's alignment gradient (linear in the hit gradient; few tracks)
+      const int L = P.hlayer[hi];
+      atomicAdd(P.g_align_acc + 2 * L, -((double)P.hx[hi] * hb[1] - (double)P.hy[hi] * hb[0]) / g.radius[L]);
+      atomicAdd(P.g_align_acc + 2 * L + 1, -(double)hb[2]);
     }
   }
   if (P.g_seed) {
@@ -786,12 +792,13 @@ __host__ __device__ constexpr int fp32_col_floats(int stride) { return 27 * (str
 // checkpoint and hits are copied into shared memory while segment c is
 // reversed, and segment c-2's hit indices with them, so that a segment's
 // steps wait on no global load.  col: this thread's column; s_al, s_R: the
-// layers' alignment and radii in shared memory.
+// layers' alignment and radii in shared memory; ga: this thread's column of
+// alignment-gradient sums (rows 2L and 2L + 1: layer L's rotation and z).
 // listed: the track comes from the fit's careful list (else careful tracks
 // are skipped: the careful passes take them).
 template <bool EL>
 __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const float4* s_al, const float* s_R,
-                                   bool listed) {
+                                   float* ga, bool listed) {
   const DevGeom& g = P.g;
   const int t = P.order[i];
   if (!listed && P.careful_flag[t]) return;  // the careful passes', which run beside this one
@@ -875,11 +882,17 @@ __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const 
     for (int k = k1 - 1; k >= k0; --k) {
       float hb[3];
       rev_step_regs<EL>(g, k == k0 ? ck : seg + (k - k0 - 1) * 27 * LD, hit_of(k), k == 0, k + 1 == n, pb, Cb, hb);
-      const int hi = __float_as_int(hs[((k - k0) * 5 + 4) * LD]);
+      const float* hd = hs + (k - k0) * 5 * LD;
+      const int hi = __float_as_int(hd[4 * LD]);
       float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
       atomicAdd(gh + 0, hb[0]);
       atomicAdd(gh + 1, hb[1]);
       atomicAdd(gh + 2, hb[2]);
+      // the layer's alignment gradient (linear in the hit gradient), summed
+      // in this thread's column
+      const int L = __float_as_int(hd[3 * LD]);
+      ga[2 * L * LD] -= kfma(hd[0], hb[1], -hd[LD] * hb[0]) / s_R[L];
+      ga[(2 * L + 1) * LD] -= hb[2];
     }
   }
   if (P.g_seed) {
@@ -894,11 +907,17 @@ enum { ADJ_ALL = 0, ADJ_LIST_FP32 = 1, ADJ_LIST_DBL = 2 };
 
 template <int MODE, bool EL>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
-  extern __shared__ float seg_all[];  // double pass: [stride][27][LD]; FP32 passes: columns of fp32_col_floats
+  // double pass: [stride][27][LD]; FP32 passes: columns of fp32_col_floats,
+  // then 2 x layers rows of alignment-gradient sums
+  extern __shared__ float seg_all[];
   float* seg = seg_all + threadIdx.x;
   if constexpr (MODE != ADJ_LIST_DBL) {
     __shared__ float4 s_al[KF_MAX_LAYERS];
     __shared__ float s_R[KF_MAX_LAYERS];
+    const int nga = 2 * P.g.n_layers;
+    float* const ga_all = seg_all + (size_t)fp32_col_floats(P.stride) * LD;  // [nga][LD]
+    float* const ga = ga_all + threadIdx.x;
+    for (int q = 0; q < nga; ++q) ga[q * LD] = 0.f;
     for (int l = threadIdx.x; l < P.g.n_layers; l += blockDim.x) {
       const Align4 a = P.align[l];
       s_al[l] = make_float4(a.ca, a.sa, a.dphi, a.az);
@@ -907,45 +926,24 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
     __syncthreads();
     if constexpr (MODE == ADJ_ALL) {
       const int i = blockIdx.x * blockDim.x + threadIdx.x;
-      if (i < P.ns) adjoint_track_fp32<EL>(P, i, seg, s_al, s_R, false);
+      if (i < P.ns) adjoint_track_fp32<EL>(P, i, seg, s_al, s_R, ga, false);
     } else {
       const unsigned n = *P.careful_count;
       for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const unsigned v = (unsigned)P.careful_list[j];
-        if (!(v & CAREFUL_DBL_BIT)) adjoint_track_fp32<EL>(P, (int)v, seg, s_al, s_R, true);
+        if (!(v & CAREFUL_DBL_BIT)) adjoint_track_fp32<EL>(P, (int)v, seg, s_al, s_R, ga, true);
       }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nga; q += blockDim.x) {  // row q over the columns, rotated by q (banks)
+      float a = 0.f;
+      for (int c = 0; c < LD; ++c) a += ga_all[q * LD + ((c + q) & (LD - 1))];
+      if (a != 0.f) atomicAdd(P.g_align_acc + q, (double)a);
     }
   } else {  // packed list: the first blocks take all of them and the others end at once
     const unsigned n = *P.dbl_count;
     for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
       adjoint_track<true, EL>(P, P.dbl_list[j], seg);
-  }
-}
-
-// Alignment gradient from the hit gradients: per warp, per-layer sums in
-// shared memory (atomics only between lanes on the same layer), then one
-// double-precision add per block and layer.
-constexpr int ALIGN_THREADS = 256;
-__global__ void __launch_bounds__(ALIGN_THREADS) k_align_grad(const AdjParams P) {
-  constexpr int NW = ALIGN_THREADS / 32;
-  __shared__ float acc[NW][2 * KF_MAX_LAYERS];
-  const int warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < NW * 2 * KF_MAX_LAYERS; i += blockDim.x) (&acc[0][0])[i] = 0.f;
-  __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n_hits; i += gridDim.x * blockDim.x) {
-    const int L = P.hlayer[i];
-    const float gx = P.g_hits[3 * (size_t)i], gy = P.g_hits[3 * (size_t)i + 1], gz = P.g_hits[3 * (size_t)i + 2];
-    if (gx == 0.f && gy == 0.f && gz == 0.f) continue;  // hit on no fitted track
-    const float cr = fmaf(P.hx[i], gy, -P.hy[i] * gx);
-    atomicAdd(&acc[warp][2 * L], -cr / P.g.radius[L]);
-    atomicAdd(&acc[warp][2 * L + 1], -gz);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 2 * P.g.n_layers; i += blockDim.x) {
-    double a = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) a += (double)acc[w][i];
-    if (a != 0.0) atomicAdd(P.g_align_acc + i, a);
   }
 }
 
@@ -966,7 +964,7 @@ cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(P.g_hits, 0, sizeof(float) * 3 * (size_t)P.n_hits, st);
   if (e != cudaSuccess) return e;
   const int smem_c = (int)(sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS);
-  const int smem_f = (int)(sizeof(float) * fp32_col_floats(P.stride) * (size_t)ADJ_THREADS);
+  const int smem_f = (int)(sizeof(float) * (fp32_col_floats(P.stride) + 2 * P.g.n_layers) * (size_t)ADJ_THREADS);
   const void* fns[6] = {(const void*)k_adjoint<ADJ_ALL, false>,       (const void*)k_adjoint<ADJ_LIST_FP32, false>,
                         (const void*)k_adjoint<ADJ_LIST_DBL, false>,  (const void*)k_adjoint<ADJ_ALL, true>,
                         (const void*)k_adjoint<ADJ_LIST_FP32, true>,  (const void*)k_adjoint<ADJ_LIST_DBL, true>};
@@ -978,7 +976,7 @@ cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
 cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
   const size_t smem_c = sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS;
-  const size_t smem_f = sizeof(float) * fp32_col_floats(P.stride) * (size_t)ADJ_THREADS;
+  const size_t smem_f = sizeof(float) * (fp32_col_floats(P.stride) + 2 * P.g.n_layers) * (size_t)ADJ_THREADS;
   bool el = false;  // energy loss on any layer: the variant with its code
   for (int l = 0; l < P.g.n_layers; ++l) el = el || P.g.eloss[l] > 0.f;
   const int grid_all = (P.ns + ADJ_THREADS - 1) / ADJ_THREADS;
@@ -998,14 +996,6 @@ cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t s
 }
 
 cudaError_t launch_adjoint_end(const AdjParams& P, cudaStream_t st) {
-  if (P.n_hits > 0) {
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const int blocks = min((P.n_hits + ALIGN_THREADS - 1) / ALIGN_THREADS, 8 * sms);
-    k_align_grad<<<blocks, ALIGN_THREADS, 0, st>>>(P);
-  }
   k_adjoint_finish<<<1, 2 * KF_MAX_LAYERS, 0, st>>>(P);
   return cudaGetLastError();
 }

@@ -228,8 +228,9 @@ struct AdjParams {
 };
 
 // kf_adjoint.cu
-// Adjoint: zero the accumulators, the FP32 pass and the near-tangent pass
-// (independent: either order or concurrently), then the alignment sum.
+// Adjoint: zero the accumulators, the FP32 pass and the passes over the
+// fit's careful list (independent: either order or concurrently), then the
+// alignment gradient from its double-precision sums.
 cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st);
 cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t st);
 cudaError_t launch_adjoint_end(const AdjParams& P, cudaStream_t st);
