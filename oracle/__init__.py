@@ -35,7 +35,8 @@ class Detector(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int), ("radius", ctypes.c_double * 64),
                 ("x0", ctypes.c_double * 64), ("z_max", ctypes.c_double), ("bz", ctypes.c_double),
                 ("sigma_rphi", ctypes.c_double), ("sigma_z", ctypes.c_double),
-                ("n_z", ctypes.c_int), ("x0_map", ctypes.c_void_p), ("eloss", ctypes.c_double * 64)]
+                ("n_z", ctypes.c_int), ("x0_map", ctypes.c_void_p), ("eloss", ctypes.c_double * 64),
+                ("field_cz", ctypes.c_double), ("field_cr", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -51,9 +52,9 @@ def lib():
         if _lib is None:
             _lib = ctypes.CDLL(build())
             L = _lib
-            L.orc_propagate.argtypes = [ctypes.c_double, _P, ctypes.c_double, _P, _P]
+            L.orc_propagate.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, ctypes.c_double, _P, _P]
             L.orc_path_length.argtypes = [ctypes.c_double, _P, ctypes.c_double, _P]
-            L.orc_propagate_ad.argtypes = [ctypes.c_double, _P, ctypes.c_double, _P]
+            L.orc_propagate_ad.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, ctypes.c_double, _P]
             L.orc_transport.argtypes = [_P, _P, _P]
             L.orc_update.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P]
             L.orc_highland.argtypes = [_P, ctypes.c_double]
@@ -106,6 +107,8 @@ def make_detector(det) -> Detector:
     d.sigma_z = float(np.float32(det.sigma_z))
     for i, e in enumerate(getattr(det, "eloss", ()) or ()):
         d.eloss[i] = float(np.float32(e))
+    d.field_cz = float(np.float32(getattr(det, "field_cz", 0.0)))
+    d.field_cr = float(np.float32(getattr(det, "field_cr", 0.0)))
     m = getattr(det, "x0_map", None)
     if m is not None:  # float32-rounded like every other input; kept alive by the structure
         d._map = np.ascontiguousarray(np.asarray(m, np.float32).astype(np.float64).reshape(det.n_layers, -1))
@@ -119,11 +122,13 @@ def make_config(max_cands=6, max_holes=3, chi2_cut=30.0) -> Config:
 
 
 # ------------------------------------------------------------ single-state pins
-def propagate(bz: float, p, R: float):
+def propagate(bz: float, p, R: float, cz: float = 0.0, cr: float = 0.0):
+    """Helix to radius R in the axial field bz (1 + cz z^2 + cr r^2) taken at
+    the starting point; J at that field held fixed."""
     p = _c(p, np.float64)
     q = np.zeros(6)
     J = np.zeros(36)
-    ok = lib().orc_propagate(bz, _ptr(p), R, _ptr(q), _ptr(J))
+    ok = lib().orc_propagate(bz, cz, cr, _ptr(p), R, _ptr(q), _ptr(J))
     return bool(ok), q, J.reshape(6, 6)
 
 
@@ -134,10 +139,10 @@ def path_length(bz: float, p, R: float):
     return bool(ok), float(s[0])
 
 
-def propagate_ad(bz: float, p, R: float):
+def propagate_ad(bz: float, p, R: float, cz: float = 0.0, cr: float = 0.0):
     p = _c(p, np.float64)
     J = np.zeros(36)
-    ok = lib().orc_propagate_ad(bz, _ptr(p), R, _ptr(J))
+    ok = lib().orc_propagate_ad(bz, cz, cr, _ptr(p), R, _ptr(J))
     return bool(ok), J.reshape(6, 6)
 
 

@@ -9,8 +9,10 @@
 // removal, Sec. 4.3 for candidate scores; every formula below is the standard
 // Kalman-filter reading recorded in the design notes):
 //   * state p = (x, y, z, q/pT, phi, theta), symmetric 6x6 covariance C;
-//   * helix propagation to a cylinder of radius R in a uniform field Bz, with
-//     the exact Jacobian J = dF/dp + dF/ds ds/dp;
+//   * helix propagation to a cylinder of radius R in an axial field Bz, uniform
+//     or parameterized (Sec. 3) as Bz(r, z) = bz (1 + cz z^2 + cr r^2) taken at
+//     the starting point of each propagation, with the exact Jacobian of the
+//     helix J = dF/dp + dF/ds ds/dp at that field;
 //   * covariance transport C <- J C J^T;
 //   * 2D tangent-frame measurement (r-phi, z) of a 3D hit on the cylinder, chi2;
 //   * gain K = C H^T S^-1, p <- p + K r, C <- C - K H C;
@@ -25,7 +27,7 @@
 //
 // Parity status: every function here is pinned by tests under tests/ (closed
 // forms, Runge-Kutta integration, finite differences, brute force, least
-// squares, pull widths).  The finding's candidate selection (ranking key,
+// squares, pull widths; the parameterized field by tests/test_oracle_field.py).  The finding's candidate selection (ranking key,
 // truncation to N, hole limit, stop and carry rules, chi2 cut) is pinned by
 // hand-made child lists and by a brute-force beam on tiny events that
 // recomputes every path through orc_replay.
@@ -294,6 +296,13 @@ using std::sin;
 using std::sqrt;
 
 // ---------------------------------------------------------------- detector
+// Axial field (Sec. 3: the field may be constant or parameterized).
+// Reading: Bz(r, z) = bz (1 + cz z^2 + cr r^2), r^2 = x^2 + y^2 (cm); each
+// propagation is a helix in the field at its starting point.
+struct Field {
+  double bz, cz, cr;
+};
+
 struct Det {
   int n_layers;
   double radius[64];
@@ -305,6 +314,8 @@ struct Det {
   int n_z;               // material map nodes per layer (0: the per-layer x0)
   const double* x0_map;  // [n_layers][n_z] thickness at z_k = -z_max + k 2 z_max/(n_z - 1)
   double eloss[64];      // mean ionization loss per layer at normal incidence, beta -> 1 (GeV; 0: none)
+  double field_cz, field_cr;  // Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2) (0, 0: uniform)
+  Field field() const { return Field{bz, field_cz, field_cr}; }
 };
 
 struct Cfg {
@@ -404,16 +415,27 @@ bool path_to_cylinder(const T& x, const T& y, const T& h, const T& phi, double R
   return true;
 }
 
-// Propagate p to the cylinder of radius R; q = F(p), J = dq/dp (exact).
+// kb = -KCURV Bz at the point (x, y, z): the curvature per unit q/pT.
 template <class T>
-bool propagate(double bz, const T p[6], double R, T q[6], T J[6][6]) {
+T field_kb(const Field& f, const T& x, const T& y, const T& z) {
+  const double kb0 = -KCURV * f.bz;
+  if (f.cz == 0.0 && f.cr == 0.0) return T(kb0);
+  return kb0 * (1.0 + f.cz * (z * z) + f.cr * (x * x + y * y));
+}
+
+// Propagate p to the cylinder of radius R; q = F(p).  J = dq/dp with the
+// field held at its value (the exact Jacobian of a helix; with a uniform
+// field that of F itself).  The field's dependence on the starting point
+// enters q (and so every derivative taken through the fit) but not J.
+template <class T>
+bool propagate(const Field& fld, const T p[6], double R, T q[6], T J[6][6]) {
   const T& x = p[0];
   const T& y = p[1];
   const T& z = p[2];
   const T& kap = p[3];
   const T& phi = p[4];
   const T& th = p[5];
-  const double kb = -KCURV * bz;
+  const T kb = field_kb(fld, x, y, z);
   T h = kb * kap;
   T s;
   if (!path_to_cylinder(x, y, h, phi, R, s)) return false;
@@ -677,7 +699,7 @@ int fit_track(const Det& det, const T p0[6], const TC C0[6][6], int n, const T (
     const double R = det.radius[L];
     if (k > 0) {
       T q[6], J[6][6];
-      if (!propagate(det.bz, p, R, q, J)) return -1;
+      if (!propagate(det.field(), p, R, q, J)) return -1;
       for (int i = 0; i < 6; ++i) p[i] = q[i];
       transport(J, C);
     }
@@ -804,7 +826,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
       pc = c;
       double J[6][6];
       ++cnt.prop_calls;
-      if (!propagate(det.bz, c.p, R, pc.p, J) || std::fabs(pc.p[2]) > det.z_max) {
+      if (!propagate(det.field(), c.p, R, pc.p, J) || std::fabs(pc.p[2]) > det.z_max) {
         children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0});
         continue;
       }
@@ -947,6 +969,7 @@ struct orc_detector {
   int n_z;               // material map nodes per layer (0: none)
   const double* x0_map;  // [n_layers][n_z]
   double eloss[64];      // mean ionization loss per layer (GeV; 0: none)
+  double field_cz, field_cr;  // Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2)
 };
 
 struct orc_config {
@@ -966,14 +989,16 @@ static Det to_det(const orc_detector* d) {
   o.n_z = d->x0_map ? d->n_z : 0;
   o.x0_map = d->x0_map;
   for (int i = 0; i < 64; ++i) o.eloss[i] = d->eloss[i];
+  o.field_cz = d->field_cz;
+  o.field_cr = d->field_cr;
   return o;
 }
 
 // Propagation of one state to radius R.  J is row-major 6x6.  Returns 1 if a
 // crossing exists, 0 otherwise.
-int orc_propagate(double bz, const double* p, double R, double* q, double* J) {
+int orc_propagate(double bz, double cz, double cr, const double* p, double R, double* q, double* J) {
   double Jm[6][6];
-  if (!propagate<double>(bz, p, R, q, Jm)) return 0;
+  if (!propagate<double>(Field{bz, cz, cr}, p, R, q, Jm)) return 0;
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) J[i * 6 + j] = Jm[i][j];
   return 1;
@@ -985,12 +1010,13 @@ int orc_path_length(double bz, const double* p, double R, double* s) {
 }
 
 // Jacobian of the propagated state by forward-mode differentiation of the
-// propagation itself (independent of the hand-derived J).
-int orc_propagate_ad(double bz, const double* p, double R, double* Jad) {
+// propagation itself (independent of the hand-derived J; with a field that
+// varies, it includes the field's dependence on the starting point).
+int orc_propagate_ad(double bz, double cz, double cr, const double* p, double R, double* Jad) {
   g_nd = 6;
   Dual pd[6], qd[6], Jd[6][6];
   for (int k = 0; k < 6; ++k) pd[k] = make_var(p[k], k);
-  const bool ok = propagate<Dual>(bz, pd, R, qd, Jd);
+  const bool ok = propagate<Dual>(Field{bz, cz, cr}, pd, R, qd, Jd);
   if (ok)
     for (int i = 0; i < 6; ++i)
       for (int j = 0; j < 6; ++j) Jad[i * 6 + j] = qd[i].d[j];
@@ -1225,7 +1251,7 @@ int orc_census_step(const orc_detector* dptr, double chi2_cut, const double* p, 
     for (int b = a; b < 6; ++b) Cc[a][b] = Cc[b][a] = cn_input(C21[sym_index(a, b)]);
   const Cn al0 = cn_input(align[0]), al1 = cn_input(align[1]);
   const double R = det.radius[L];
-  if (!propagate(det.bz, pc, R, q, J)) return -1;
+  if (!propagate(det.field(), pc, R, q, J)) return -1;
   transport(J, Cc);
   std::vector<int> outs;
   for (int k = 0; k < 6; ++k) outs.push_back(q[k].id);
@@ -1381,7 +1407,7 @@ int orc_replay(const orc_detector* dptr, const double* hx, const double* hy, con
   for (int l = lays[2] + 1; l < L; ++l) {
     if (decisions[l] == -2) break;
     double q[6], J[6][6];
-    if (!propagate(det.bz, p, det.radius[l], q, J)) { *chi2sum = chi2; return -1; }
+    if (!propagate(det.field(), p, det.radius[l], q, J)) { *chi2sum = chi2; return -1; }
     for (int i = 0; i < 6; ++i) p[i] = q[i];
     transport(J, C);
     if (decisions[l] >= 0) {

@@ -53,6 +53,11 @@ class Detector:
     # optional mean ionization loss per layer at normal incidence for beta -> 1
     # (GeV); the simulation itself has none
     eloss: tuple = ()
+    # axial field Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2) (cm^-2; 0, 0:
+    # uniform); the simulation traces tracks through it in FIELD_SUBSTEPS
+    # helix steps per layer, each in the field at its starting point
+    field_cz: float = 0.0
+    field_cr: float = 0.0
 
     @property
     def n_layers(self) -> int:
@@ -60,9 +65,21 @@ class Detector:
 
 
 def detector_for(n_layers: int, r_min: float, r_max: float, bz: float = 3.8,
-                 x0: float = 0.02, z_max: float = 120.0) -> Detector:
+                 x0: float = 0.02, z_max: float = 120.0, field_cz: float = 0.0,
+                 field_cr: float = 0.0) -> Detector:
     radius = tuple(r_min + (r_max - r_min) * i / (n_layers - 1) for i in range(n_layers))
-    return Detector(radius=radius, z_max=z_max, x0=(x0,) * n_layers, bz=bz)
+    return Detector(radius=radius, z_max=z_max, x0=(x0,) * n_layers, bz=bz, field_cz=field_cz,
+                    field_cr=field_cr)
+
+
+#: helix steps per layer-to-layer crossing when the simulation traces tracks
+#: through a field that varies
+FIELD_SUBSTEPS = 8
+
+
+def field_at(det: Detector, x, y, z):
+    """Bz at (x, y, z) (T)."""
+    return det.bz * (1.0 + det.field_cz * z * z + det.field_cr * (x * x + y * y))
 
 
 # Workload configurations.  "tracks" may be an int or the string "pileup" for
@@ -167,6 +184,21 @@ def _cross_cylinder(x, y, z, kappa, phi, theta, R, bz):
     return ok, xn, yn, zn, phn
 
 
+def _cross_in_field(x, y, z, kappa, phi, theta, R, det: Detector):
+    """Truth tracing to radius R: one helix in a uniform field; in a field
+    that varies, FIELD_SUBSTEPS helices to radii spread evenly between the
+    start and R, each in the field at its own starting point."""
+    if det.field_cz == 0.0 and det.field_cr == 0.0:
+        return _cross_cylinder(x, y, z, kappa, phi, theta, R, det.bz)
+    r0 = np.hypot(x, y)
+    ok = np.ones(x.shape[0], dtype=bool)
+    for k in range(1, FIELD_SUBSTEPS + 1):
+        Rk = R if k == FIELD_SUBSTEPS else r0 + (R - r0) * k / FIELD_SUBSTEPS
+        okk, x, y, z, phi = _cross_cylinder(x, y, z, kappa, phi, theta, Rk, field_at(det, x, y, z))
+        ok &= okk
+    return ok, x, y, z, phi
+
+
 @dataclasses.dataclass
 class Event:
     x: np.ndarray
@@ -201,7 +233,7 @@ def simulate_event(det: Detector, n_tracks: int, eta_max: float, noise: float,
     n_hits = 0
     for li in range(L):
         R = det.radius[li]
-        ok, xn, yn, zn, phn = _cross_cylinder(x, y, z, kappa, ph, th, R, det.bz)
+        ok, xn, yn, zn, phn = _cross_in_field(x, y, z, kappa, ph, th, R, det)
         ok &= alive & (np.abs(zn) <= det.z_max)
         alive = ok
         phi_pos = np.arctan2(yn, xn)
@@ -375,7 +407,8 @@ def make_batch(name: str, n_events: Optional[int] = None, tracks: Optional[int] 
         cfg["n_events"] = n_events
     if tracks is not None:
         cfg["tracks"] = tracks
-    det = detector_for(cfg["n_layers"], 4.0, cfg["r_max"], bz=3.8 if bz is None else bz)
+    det = detector_for(cfg["n_layers"], 4.0, cfg["r_max"], bz=3.8 if bz is None else bz,
+                       field_cz=cfg.get("field_cz", 0.0), field_cr=cfg.get("field_cr", 0.0))
     L = det.n_layers
     align = np.zeros((L, 2), dtype=np.float32)
     if cfg.get("misalign_sigma"):
