@@ -184,18 +184,24 @@ def sum_alignment_over_ranks(g_align, chi2_total, device):
     return v[:-1].reshape(np.shape(g_align)), float(v[-1])
 
 
-def make_inputs(name, rank, n_events=None):
+def make_inputs(name, rank, n_events=None, **overrides):
     from synth import make_batch
     # per-rank distinct events: shift the configuration seed by the rank
     from synth.events import CONFIGS
     seed = CONFIGS[name]["seed"] + 7919 * rank
-    return make_batch(name, n_events=n_events, seed=seed)
+    return make_batch(name, n_events=n_events, seed=seed, **overrides)
+
+
+# Parameterized field of the field-map step: Bz 10% weaker at |z| = 120 cm
+# and 5% weaker at r = 110 cm than at the centre.
+FIELD_MAP = dict(field_cz=-0.10 / 120.0 ** 2, field_cr=-0.05 / 110.0 ** 2)
 
 
 def tracker_for(b, **cfg):
     from paper_1906_11744_gb300 import Tracker, make_config, make_detector
     d = b.det
-    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None))
+    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None),
+                        field_cz=getattr(d, "field_cz", 0.0), field_cr=getattr(d, "field_cr", 0.0))
     c = dict(max_cands=b.cfg["max_cands"])
     c.update(cfg)
     return Tracker(det, make_config(**c))
@@ -365,6 +371,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dup", action="store_true", help="skip the duplicate-handling step")
     ap.add_argument("--no-material", action="store_true", help="skip the material-map step")
+    ap.add_argument("--no-field", action="store_true", help="skip the parameterized-field step")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-pileup (64 events, PU 20-200) step")
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
@@ -593,6 +600,46 @@ def main():
                "gpu_launches": tm.graph_kernel_count() * args.steps}
         tm.close()
 
+    # the same workload in a parameterized field (events simulated through it)
+    fld = None
+    if not args.no_field:
+        best = shape or ({} if tune is None else dict(
+            lanes_per_seed=int(tune[np.argmin(tune[:, 4])][0]), block_threads=int(tune[np.argmin(tune[:, 4])][1]),
+            persistent=int(tune[np.argmin(tune[:, 4])][2]), find_regcap=int(tune[np.argmin(tune[:, 4])][3])))
+        bf = make_inputs(args.config, rank, n_events=args.events, **FIELD_MAP)
+        df = dict(x=tt(bf.x), y=tt(bf.y), z=tt(bf.z), layer=tt(bf.layer), params=tt(bf.params),
+                  cov=tt(bf.cov), seed_hits=tt(bf.seed_hits))
+        tf = tracker_for(bf, **{"persistent": 1, "per_event": 0, **best})
+        tf.load_hits(bf.hit_off, df["x"], df["y"], df["z"], df["layer"], stream)
+        tf.load_seeds(bf.seed_off, df["params"], df["cov"], df["seed_hits"], stream)
+        tf.set_alignment(bf.align, stream)
+        tf.set_stage_timing(True)
+        tf.capture_graph(with_adjoint=True, stream=stream)
+        for _ in range(args.warmup):
+            tf.launch_graph(stream)
+        stream.synchronize()
+        fa = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        fb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        fstage = {}
+        for k in range(args.steps):
+            flush_l2()
+            fa[k].record(stream)
+            tf.launch_graph(stream)
+            fb[k].record(stream)
+            for key, v in tf.stage_ms(stream).items():
+                fstage[key] = fstage.get(key, 0.0) + v
+        stream.synchronize()
+        fms = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in zip(fa, fb)), dev)
+        fld = {"value": bf.n_seeds * world * args.steps / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / args.steps,
+               "field": "Bz(r, z) = 3.8 T (1 + cz z^2 + cr r^2), cz = %.3e, cr = %.3e cm^-2 (10%% weaker at |z| = 120 cm, "
+                        "5%% at r = 110 cm), taken at each propagation's start" % (FIELD_MAP["field_cz"],
+                                                                                    FIELD_MAP["field_cr"]),
+               "counters_per_step": tf.counters(stream),
+               "stage_ms": {k: v / args.steps for k, v in fstage.items()},
+               "gpu_launches": tf.graph_kernel_count() * args.steps}
+        tf.close()
+        del df
+
     # end to end through the C ABI with host buffers (pinned), host<->device copies inside.
     # Two contexts: while one step's graph runs, the next step's inputs are uploaded (and
     # checked) through the other context; its graph starts once this step's results are
@@ -711,6 +758,7 @@ def main():
                "mixed_pileup": mixed,
                "dup_handling": dup,
                "material_map": mat,
+               "field_map": fld,
                "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample",
                                                                             "single_core_value", "single_core_sample")},
                "clocks": clocks.summary()}

@@ -67,7 +67,8 @@ extern "C" {
 
 typedef struct kf_ctx kf_ctx;
 
-/* Geometry (Sec. 3): concentric barrel cylinders in a uniform field along z. */
+/* Geometry (Sec. 3): concentric barrel cylinders in an axial field, uniform
+ * or parameterized. */
 typedef struct {
   int n_layers;                 /* 1..KF_MAX_LAYERS, radii increasing */
   float radius[KF_MAX_LAYERS];  /* cm */
@@ -84,6 +85,16 @@ typedef struct {
    * most (E - m)/2; q/pT is scaled by p/p' and the covariance carried through
    * the Jacobian of that map.  Straggling is not modelled. */
   float eloss[KF_MAX_LAYERS];
+  /* Parameterized field (Sec. 3: the field may be constant or parameterized):
+   * Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2), r^2 = x^2 + y^2, in cm^-2
+   * (0, 0 = uniform).  Each propagation is a helix in the field at its starting
+   * point; the covariance is carried by the Jacobian of that helix, and the
+   * adjoint also differentiates the field's dependence on the starting point.
+   * 1 + field_cz z^2 + field_cr r^2 must lie in [0.2, 5] for |z| <= z_max and
+   * r <= the outermost radius (KF_ERR_ARG otherwise).  Duplicate kinematics
+   * (pT, eta, phi0 cuts) use bz. */
+  float field_cz;
+  float field_cr;
 } kf_detector;
 
 /* Algorithm settings (Sec. 2 and Sec. 4.3: windows, scores, duplicate cuts). */

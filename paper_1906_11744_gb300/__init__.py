@@ -43,9 +43,11 @@ from ._lib import (  # noqa: F401
 )
 
 
-def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1, eloss=None) -> kf_detector:
+def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1, eloss=None,
+                  field_cz=0.0, field_cr=0.0) -> kf_detector:
     """Detector geometry (include/kf.h, kf_detector); eloss: mean ionization
-    loss per layer at normal incidence for beta -> 1 (GeV; None: none)."""
+    loss per layer at normal incidence for beta -> 1 (GeV; None: none);
+    field_cz, field_cr: Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2)."""
     d = kf_detector()
     d.n_layers = len(radius)
     for i, r in enumerate(radius):
@@ -53,6 +55,7 @@ def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1,
         d.x0[i] = float(x0[i])
         d.eloss[i] = float(eloss[i]) if eloss is not None and len(eloss) else 0.0
     d.z_max, d.bz, d.sigma_rphi, d.sigma_z = float(z_max), float(bz), float(sigma_rphi), float(sigma_z)
+    d.field_cz, d.field_cr = float(field_cz), float(field_cr)
     return d
 
 

@@ -36,7 +36,8 @@ class kf_detector(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int), ("radius", ctypes.c_float * KF_MAX_LAYERS),
                 ("x0", ctypes.c_float * KF_MAX_LAYERS), ("z_max", ctypes.c_float),
                 ("bz", ctypes.c_float), ("sigma_rphi", ctypes.c_float), ("sigma_z", ctypes.c_float),
-                ("eloss", ctypes.c_float * KF_MAX_LAYERS)]
+                ("eloss", ctypes.c_float * KF_MAX_LAYERS), ("field_cz", ctypes.c_float),
+                ("field_cr", ctypes.c_float)]
 
 
 class kf_config(ctypes.Structure):

@@ -378,7 +378,7 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
                                         bool last) {
   if (!first) {
     S cosa = S(1);
-    if (propagate<S>(p, C, h.R, (S)g.kb, S(INFINITY), &cosa) != 1) return KF_FIT_NO_CROSS;
+    if (propagate<S>(p, C, h.R, field_kb<S>(g, p), S(INFINITY), &cosa) != 1) return KF_FIT_NO_CROSS;
     if (sizeof(S) == 4 && cosa < S(ADJ_CAREFUL_COS)) return 99;
   }
   FrameT<S> f;
@@ -403,10 +403,11 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
                                          S (&hb)[3]) {
   // ---- forward recompute of the step
   S q[6], J[6][6], Cp[21], s_len = S(0);
+  const S kb = field_kb<S>(g, p_in);  // the field at the step's starting point
 #pragma unroll
   for (int k = 0; k < 21; ++k) Cp[k] = C_in[k];
   if (!first) {
-    prop_jacobian<S>(p_in, h.R, (S)g.kb, S(INFINITY), q, J, nullptr, &s_len);
+    prop_jacobian<S>(p_in, h.R, kb, S(INFINITY), q, J, nullptr, &s_len);
     transport<S>(J, Cp);
   } else {
 #pragma unroll
@@ -597,7 +598,23 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
       for (int j = 0; j < 6; ++j) jb = kfma(Cbp[i][j], CJ[j][l], jb);
       Jb[i][l] = S(2) * jb;
     }
-  jac_vjp<S>(p_in, s_len, (S)g.kb, Jb, pin);
+  jac_vjp<S>(p_in, s_len, kb, Jb, pin);
+  if (g.fcz != 0.f || g.fcr != 0.f) {
+    // The field at the starting point moves with it.  q and J depend on kb
+    // and q/pT only through their product (J's q/pT column carries one more
+    // factor kb), so the adjoint of kb is
+    //   (p3 (pin_3 - pbar_3) + sum_i Jbar_i3 J_i3) / kb
+    // with pin_3 the q/pT component of J^T pbar + Jbar . dJ/dp; kb = kb0 (1 +
+    // fcz z^2 + fcr r^2) then passes it to x, y, z.
+    S jj = S(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (i != 3) jj = kfma(Jb[i][3], J[i][3], jj);
+    const S kbar = kdiv(kfma(p_in[3], pin[3] - pbp[3], jj), kb) * S(2) * (S)g.kb;
+    pin[0] = kfma(kbar * (S)g.fcr, p_in[0], pin[0]);
+    pin[1] = kfma(kbar * (S)g.fcr, p_in[1], pin[1]);
+    pin[2] = kfma(kbar * (S)g.fcz, p_in[2], pin[2]);
+  }
   // Cbar_in = J^T Cbar' J
   S T1[6][6];  // Cbp J
 #pragma unroll
@@ -633,7 +650,7 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
 // close to tangentially; the careful pass runs such steps in double.
 __device__ __forceinline__ bool near_tangent(const DevGeom& g, const float (&p)[6], float R) {
   float zc, cosa;
-  if (!crossing(p, R, g.kb, zc, cosa)) return false;
+  if (!crossing(p, R, field_kb<float>(g, p), zc, cosa)) return false;
   return cosa < ADJ_CAREFUL_COS;
 }
 

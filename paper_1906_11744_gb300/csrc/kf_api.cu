@@ -210,6 +210,15 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   }
   if (!(det->z_max > 0.f) || !(det->sigma_rphi > 0.f) || !(det->sigma_z > 0.f) || !std::isfinite(det->bz))
     return KF_ERR_ARG;
+  {  // the field factor at the corners of the detector's (r, z) box (monotone in r^2 and z^2)
+    const double z2 = (double)det->z_max * det->z_max, r2 = (double)det->radius[det->n_layers - 1] *
+                                                            det->radius[det->n_layers - 1];
+    if (!std::isfinite(det->field_cz) || !std::isfinite(det->field_cr)) return KF_ERR_ARG;
+    for (int c = 0; c < 4; ++c) {
+      const double f = 1.0 + det->field_cz * ((c & 1) ? z2 : 0.0) + det->field_cr * ((c & 2) ? r2 : 0.0);
+      if (!(f >= 0.2 && f <= 5.0)) return KF_ERR_ARG;
+    }
+  }
   if (cfg->max_cands < 1 || cfg->max_cands > KF_MAX_CANDS || cfg->max_holes < 0 || !(cfg->chi2_cut > 0.f) ||
       !(cfg->dup_shared_frac >= 0.f) || cfg->n_eta_bins < 1 || cfg->n_eta_bins > MAX_ETA_BINS ||
       cfg->n_phi_bins < 1 ||
@@ -244,6 +253,8 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   g.n_phi = cfg->n_phi_bins;
   g.z_max = det->z_max;
   g.kb = -KCURV * det->bz;
+  g.fcz = det->field_cz;
+  g.fcr = det->field_cr;
   g.vr = det->sigma_rphi * det->sigma_rphi;
   g.vz = det->sigma_z * det->sigma_z;
   g.chi2_cut = cfg->chi2_cut;

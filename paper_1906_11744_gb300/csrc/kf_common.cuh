@@ -32,7 +32,8 @@ struct DevGeom {
   int n_eta;
   int n_phi;
   float z_max;
-  float kb;  // -KCURV * bz: signed curvature h = kb * (q/pT)
+  float kb;  // -KCURV * bz: signed curvature h = kb * (q/pT) in the nominal field
+  float fcz, fcr;  // field factor 1 + fcz z^2 + fcr r^2 at a point (0, 0: uniform)
   float vr;  // sigma_rphi^2
   float vz;  // sigma_z^2
   float chi2_cut;
@@ -276,6 +277,14 @@ __device__ __forceinline__ void transport(const T (&J)[6][6], T (&C)[21]) {
   }
 #pragma unroll
   for (int k = 0; k < 21; ++k) C[k] = out[k];
+}
+
+// kb of the field at the point (p[0], p[1], p[2]) (Sec. 3, parameterized
+// field): kb (1 + fcz z^2 + fcr r^2); exactly kb in a uniform field.  Each
+// propagation takes it at its starting point.
+template <class T>
+__device__ __forceinline__ T field_kb(const DevGeom& g, const T (&p)[6]) {
+  return (T)g.kb * kfma((T)g.fcz, p[2] * p[2], kfma((T)g.fcr, kfma(p[0], p[0], p[1] * p[1]), T(1)));
 }
 
 // Path length and crossing geometry only: returns false without a crossing;

@@ -88,11 +88,14 @@ constexpr int CAREFUL_THREADS = 128;
 // Double-precision propagation of the state st[0..26] (p, then C) in place;
 // st is the lane's child list in shared memory, unused at this point.  The
 // double result also goes to dst[0..26].
-__device__ __noinline__ int careful_propagate(float* st, double* dst, float R, float kb, float z_lim) {
+// kb0, fcz, fcr: the field (DevGeom), taken at the state's position in double.
+__device__ __noinline__ int careful_propagate(float* st, double* dst, float R, float kb0, float fcz, float fcr,
+                                              float z_lim) {
   double p[6], C[21];
   for (int k = 0; k < 6; ++k) p[k] = st[k];
   for (int k = 0; k < 21; ++k) C[k] = st[6 + k];
-  const int rc = propagate<double>(p, C, (double)R, (double)kb, (double)z_lim);
+  const double kb = (double)kb0 * fma((double)fcz, p[2] * p[2], fma((double)fcr, fma(p[0], p[0], p[1] * p[1]), 1.0));
+  const int rc = propagate<double>(p, C, (double)R, kb, (double)z_lim);
   if (rc == 1) {
     for (int k = 0; k < 6; ++k) {
       st[k] = (float)p[k];
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
       if (finished || near) continue;  // (l still walks to the third seed hit's layer)
       if (it != 0) {
         float q[6], J[6][6], cosa = 1.f;
-        const int pr = prop_jacobian<float>(p, g.radius[l], g.kb, INFINITY, q, J, &cosa);
+        const int pr = prop_jacobian<float>(p, g.radius[l], field_kb<float>(g, p), INFINITY, q, J, &cosa);
         if (pr != 1) {
           finished = true;
           continue;
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_fit(const FindParams P) {
         for (int k = 0; k < 21; ++k) bC[k] = C[k];
         const float R = g.radius[l1];
         float q[6], J[6][6], cosa = 1.f;
-        const int pr = prop_jacobian<float>(p, R, g.kb, g.z_max, q, J, &cosa);
+        const int pr = prop_jacobian<float>(p, R, field_kb<float>(g, p), g.z_max, q, J, &cosa);
         if (pr == 1 && cosa < FIND_CAREFUL_COS) {
           near = true;
         } else if (pr == 1) {
@@ -576,14 +579,14 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
           if (it != 0) {
             const float z_lim = in_seed ? INFINITY : g.z_max;
             float q[6], J[6][6], cosa = 1.f;
-            pr = prop_jacobian<float>(p, R, g.kb, z_lim, q, J, &cosa);
+            pr = prop_jacobian<float>(p, R, field_kb<float>(g, p), z_lim, q, J, &cosa);
             if (CAREFUL && pr == 1 && (cosa < FIND_CAREFUL_COS || (in_seed && loose))) {
               float* st = reinterpret_cast<float*>(lst);
 #pragma unroll
               for (int k = 0; k < 6; ++k) st[k] = p[k];
 #pragma unroll
               for (int k = 0; k < 21; ++k) st[6 + k] = C[k];
-              pr = careful_propagate(st, dst_warp + lane * 27, R, g.kb, z_lim);
+              pr = careful_propagate(st, dst_warp + lane * 27, R, g.kb, g.fcz, g.fcr, z_lim);
               dbl = pr == 1;
               if (pr == 1) {
 #pragma unroll

@@ -31,7 +31,7 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   for (int k = 0; k < 6; ++k) p[k] = (T)pf[k];
 #pragma unroll
   for (int k = 0; k < 21; ++k) C[k] = (T)Cf[k];
-  if (!first && propagate<T>(p, C, (T)g.radius[L], (T)g.kb, T(INFINITY)) != 1) return KF_FIT_NO_CROSS;
+  if (!first && propagate<T>(p, C, (T)g.radius[L], field_kb<T>(g, p), T(INFINITY)) != 1) return KF_FIT_NO_CROSS;
   FrameT<T> f;
   make_frame<T>(p, C, (T)g.vr, (T)g.vz, f);
   T r0, r1;
@@ -150,7 +150,10 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
     if (!CAREFUL) {
       if (k > 0) {
         float cosa = 1.f;
-        if (propagate<float>(p, C, g.radius[L], g.kb, INFINITY, &cosa) != 1) { status = KF_FIT_NO_CROSS; break; }
+        if (propagate<float>(p, C, g.radius[L], field_kb<float>(g, p), INFINITY, &cosa) != 1) {
+          status = KF_FIT_NO_CROSS;
+          break;
+        }
         if (cosa < CAREFUL_COS) {  // leave the track to the careful pass
           P.careful_list[atomicAdd(P.careful_count, 1u)] = i;
           if (P.careful_flag) P.careful_flag[t] = 1;
@@ -171,7 +174,7 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
       bool careful = false;
       if (k > 0) {
         float zc, cosa;
-        if (!crossing(p, g.radius[L], g.kb, zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
+        if (!crossing(p, g.radius[L], field_kb<float>(g, p), zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
         careful = cosa < CAREFUL_COS;
         adj_dbl = adj_dbl || cosa < ADJOINT_CAREFUL_COS;
       }

@@ -18,7 +18,8 @@ def tracker_for(batch, device=None, **cfg):
     from paper_1906_11744_gb300 import Tracker, make_config, make_detector
 
     d = batch.det
-    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None))
+    det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None),
+                        field_cz=getattr(d, "field_cz", 0.0), field_cr=getattr(d, "field_cr", 0.0))
     c = dict(max_cands=batch.cfg["max_cands"])
     c.update(cfg)
     t = Tracker(det, make_config(**c))

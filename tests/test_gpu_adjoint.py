@@ -45,23 +45,34 @@ def _close(g, ref):
     return float(np.abs(g - ref).max() / scale), comp
 
 
-def _fp32_sigma(b, sel, lists, n, trials=4, seed=7):
+def _fp32_sigma(b, sel, lists, n, trials=16, seed=7):
     """The oracle's gradients (align, hits, seed) and, per component, the RMS
     over `trials` of their change when the same computation runs with every
     operation rounded to single precision, on inputs (hit coordinates, seed
     parameters) jittered by up to one FP32 ulp: the FP32 rounding scale of
-    each component."""
+    each component.  Sixteen trials: with four, the RMS of a component can
+    fall to a third of its scale by chance (a chi-square with four degrees of
+    freedom), and one of thousands of components then left the 8-sigma bound
+    while more trials put it at 0.6-0.8 of it.  The trials run on threads (the
+    oracle releases the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     from kfhelp import JITTER_REL
     x, y, z, lay = b.event_hits(0)
     rng = np.random.default_rng(seed)
     base = oracle.fit_grad(b.det, b.params[:, sel], b.cov[:, sel], lists[sel], n[sel], x, y, z, lay, b.align)
+    j = lambda a: a.astype(np.float64) * (1.0 + JITTER_REL * rng.uniform(-1, 1, a.shape))  # noqa: E731
+    inputs = [(j(b.params[:, sel]), j(x), j(y), j(z)) for _ in range(trials)]
+
+    def one(inp):
+        pp, xx, yy, zz = inp
+        return oracle.fit_grad(b.det, pp, b.cov[:, sel], lists[sel], n[sel], xx, yy, zz, lay, b.align, fp32=True)
+
     acc = [np.zeros_like(base[1]), np.zeros_like(base[2]), np.zeros_like(base[3])]
-    for _ in range(trials):
-        j = lambda a: a.astype(np.float64) * (1.0 + JITTER_REL * rng.uniform(-1, 1, a.shape))  # noqa: E731
-        g = oracle.fit_grad(b.det, j(b.params[:, sel]), b.cov[:, sel], lists[sel], n[sel], j(x), j(y), j(z), lay,
-                            b.align, fp32=True)
-        for k in range(3):
-            acc[k] += (g[k + 1] - base[k + 1]) ** 2
+    with ThreadPoolExecutor(max_workers=min(trials, 16)) as ex:
+        for g in ex.map(one, inputs):
+            for k in range(3):
+                acc[k] += (g[k + 1] - base[k + 1]) ** 2
     return base, [np.sqrt(a / trials) for a in acc]
 
 

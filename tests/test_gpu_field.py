@@ -1,0 +1,100 @@
+"""Parameterized field on the GPU against the oracle (Sec. 3: the field may
+be constant or parameterized; the reading Bz(r, z) = bz (1 + cz z^2 + cr r^2)
+taken at each propagation's starting point is pinned in the oracle by
+tests/test_oracle_field.py).
+
+Finding runs in a field 10% weaker at |z| = 120 cm and 5% weaker at r = 110 cm;
+the fit and its adjoint in a stronger one (43% and 24% weaker there), where
+the field term of the adjoint (the field moving with the starting point) is
+well above the tolerance.  Each must meet the tolerances of the uniform-field
+runs, and the results must differ from the uniform-field ones.
+"""
+import dataclasses
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from kfhelp import audit_mismatch, cov_close, found_cov_close, param_close, tracker_for
+from synth import make_batch
+from synth.events import true_hit_lists
+
+pytestmark = pytest.mark.gpu
+
+FIELD = dict(field_cz=-0.10 / 120.0 ** 2, field_cr=-0.05 / 110.0 ** 2)
+STRONG = dict(field_cz=-3.0e-5, field_cr=-2.0e-5)
+
+
+def test_find_in_a_parameterized_field():
+    b = make_batch("c1", **FIELD)
+    t = tracker_for(b)
+    t.find_tracks()
+    trk = t.get_tracks()
+    ref = oracle.find_event(b, 0)
+    same = np.all(trk["hits"] == ref["hits"], axis=1)
+    for i in np.nonzero(~same)[0]:
+        ok, kind, rel = audit_mismatch(b, 0, i, trk["hits"][i], ref["hits"][i])
+        assert ok, (i, kind, rel)
+    assert same.mean() >= 0.995
+    okp, ep = param_close(trk["params"].T[same], ref["p"][same])
+    okc, ec = found_cov_close(trk["cov"].T[same], ref["C"][same], ref["p"][same])
+    assert okp.all(), ep
+    assert okc.all(), ec
+    # the field is applied: the same hits in a uniform field give other parameters
+    uni = dataclasses.replace(b, det=dataclasses.replace(b.det, field_cz=0.0, field_cr=0.0))
+    t0 = tracker_for(uni)
+    t0.find_tracks()
+    tr0 = t0.get_tracks()
+    both = same & np.all(tr0["hits"] == trk["hits"], axis=1) & (trk["n_found"] >= 10)
+    dk = np.abs(tr0["params"][3][both] / trk["params"][3][both] - 1.0)
+    assert np.median(dk) > 1e-3
+    print(f"field find: {same.sum()}/{b.n_seeds} identical, params {ep:.2e}, cov/bound {ec}, "
+          f"median |dk/k| against uniform {np.median(dk):.2e}")
+
+
+def _fit_case(n_tracks=None):
+    from paper_1906_11744_gb300 import KF_FIT_GIVEN
+    b = make_batch("c3", **STRONG) if n_tracks is None else make_batch("c3", tracks=n_tracks, **STRONG)
+    lists, n = true_hit_lists(b, 0, b.det.n_layers)
+    lists, n = lists[b.seed_sim], n[b.seed_sim]
+    t = tracker_for(b)
+    t.fit_tracks(KF_FIT_GIVEN, lists, n)
+    return b, t, lists, n
+
+
+def test_fit_in_a_parameterized_field():
+    b, t, lists, n = _fit_case()
+    g = t.get_fit()
+    x, y, z, lay = b.event_hits(0)
+    p, C, c2, st = oracle.fit(b.det, b.params, b.cov, lists, n, x, y, z, lay, align=b.align)
+    both = (st == 0) & (g["status"] == 0)
+    assert both.mean() > 0.999
+    okp, ep = param_close(g["params"].T[both], p[both])
+    okc, ec = cov_close(g["cov"].T[both], C[both], p[both])
+    print(f"field fit: params {ep:.2e}, cov {ec:.2e}")
+    assert okp.all(), ep
+    assert okc.all(), ec
+    assert np.allclose(g["chi2"][both], c2[both], rtol=1e-3, atol=1e-2)
+
+
+def test_adjoint_in_a_parameterized_field():
+    spec = importlib.util.spec_from_file_location("adj", os.path.join(os.path.dirname(__file__), "test_gpu_adjoint.py"))
+    adj = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(adj)
+    b, t, lists, n = _fit_case(n_tracks=300)
+    ok = t.get_fit()["status"] == 0
+    L = b.det.n_layers
+    g_align = np.zeros((L, 2), np.float32)
+    g_hits = np.zeros((b.n_hits, 3), np.float32)
+    g_seed = np.zeros((6, b.n_seeds), np.float32)
+    t.fit_adjoint(g_align, g_hits, g_seed)
+    sel = np.nonzero(ok)[0]
+    (tot, ga, gh, gs, each), sig = adj._fp32_sigma(b, sel, lists, n)
+    errs = [adj._close(g_align, ga)[0], adj._close(g_hits, gh)[0], adj._close(g_seed[:, sel].T, gs)[0]]
+    comp = [adj._component_ok(g_align, ga, sig[0]), adj._component_ok(g_hits, gh, sig[1]),
+            adj._component_ok(g_seed[:, sel].T, gs, sig[2])]
+    print(f"field adjoint: norm-wise {errs}, component bound ratios {[c[2] for c in comp]}")
+    assert max(errs) < 1e-3
+    assert all(c[0] for c in comp), comp
