@@ -69,6 +69,10 @@ struct kf_ctx {
   // careful pass to kf_fit_adjoint, which runs it on the side stream before
   // the careful adjoint, beside the FP32 adjoint (which needs neither).
   bool defer_careful_fit = false, careful_fit_pending = false;
+  // Inside a graph capture: kf_fit_tracks runs beside duplicate removal (its
+  // FP32 pass fits every found track; the caller then clears the removed ones)
+  // and always leaves its careful pass for later.
+  bool fit_beside_dedup = false;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err = "";
 };
@@ -806,7 +810,8 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
     F.lists = ptr<int>(ctx->out_hits);
     F.n_list = ptr<int>(ctx->out_n);
     F.max_len = ctx->g.n_layers;
-    F.keep = ctx->deduped ? ptr<unsigned char>(ctx->keep) : nullptr;
+    F.keep = ctx->deduped || ctx->fit_beside_dedup ? ptr<unsigned char>(ctx->keep) : nullptr;
+    F.keep_in_main = !ctx->fit_beside_dedup;
   } else if (source == KF_FIT_GIVEN) {
     if (!hit_lists || !n_hits || max_len < 1) return fail(ctx, KF_ERR_ARG, "kf_fit_tracks: missing hit lists");
     const size_t n = (size_t)ctx->n_seeds;
@@ -841,7 +846,7 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
     F.ckpt = ptr<float>(ctx->ckpt);
   }
   stage_mark(ctx, 6, st);
-  if (ctx->defer_careful_fit) {
+  if (ctx->defer_careful_fit || ctx->fit_beside_dedup) {
     CK(launch_fit_main(F, st));
     ctx->careful_fit_pending = true;
   } else {
@@ -1033,10 +1038,28 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   }
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = kf_find_tracks(ctx, stream);
-  if (rc == KF_OK) rc = kf_remove_duplicates(ctx, stream);
-  ctx->defer_careful_fit = with_adjoint != 0;
-  if (rc == KF_OK) rc = kf_fit_tracks(ctx, KF_FIT_FOUND, nullptr, nullptr, 0, 1, stream);
-  ctx->defer_careful_fit = false;
+  if (rc == KF_OK) {
+    // Duplicate removal (short, latency-bound kernels) on the high-priority
+    // side branch; beside it the fit's FP32 pass over every found track (it
+    // removes few), whose removed tracks are cleared once both are done.
+    cudaError_t fe = fork_side(ctx, st);
+    if (fe != cudaSuccess) rc = fail(ctx, KF_ERR_CUDA, cudaGetErrorString(fe));
+    if (rc == KF_OK) rc = kf_remove_duplicates(ctx, (void*)ctx->side);
+    ctx->fit_beside_dedup = true;
+    if (rc == KF_OK) rc = kf_fit_tracks(ctx, KF_FIT_FOUND, nullptr, nullptr, 0, 1, stream);
+    ctx->fit_beside_dedup = false;
+    if (rc == KF_OK) {
+      fe = join_side(ctx, st);
+      if (fe == cudaSuccess) fe = launch_fit_unkept(ctx->last_fit, st);
+      // the careful pass after the final keep flags: in the adjoint's side
+      // branch with the adjoint, here without it
+      if (fe == cudaSuccess && !with_adjoint) {
+        fe = launch_fit_careful(ctx->last_fit, st);
+        ctx->careful_fit_pending = false;
+      }
+      if (fe != cudaSuccess) rc = fail(ctx, KF_ERR_CUDA, cudaGetErrorString(fe));
+    }
+  }
   if (rc == KF_OK && with_adjoint)  // gradient into context buffers; kf_get_gradient reads them
     rc = kf_fit_adjoint(ctx, ptr<float>(ctx->adj_align), ptr<float>(ctx->adj_hits), ptr<float>(ctx->adj_seed), 1,
                         stream);

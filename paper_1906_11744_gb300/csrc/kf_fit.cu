@@ -57,7 +57,7 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
 constexpr int ORDER_WINDOW = 4096, ORDER_THREADS = 512, ORDER_BINS = 64;
 
 __device__ __forceinline__ int order_key(const FitParams& P, int t) {
-  if (P.keep && !P.keep[t]) return 0;
+  if (P.keep && P.keep_in_main && !P.keep[t]) return 0;
   return min(max(P.n_list[t], 0), ORDER_BINS - 1);
 }
 
@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_fit_order(const FitParams P) 
 template <bool CAREFUL>
 __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
   if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;  // set below if the track is left to the careful pass
-  if (!CAREFUL && P.keep && !P.keep[t]) {  // removed as a duplicate: zero outputs
+  // removed as a duplicate: zero outputs (the careful pass reads the final
+  // flags; the main pass only when they are written before it)
+  if (P.keep && (CAREFUL || P.keep_in_main) && !P.keep[t]) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) P.fit_p[(size_t)k * P.ns + t] = 0.f;
 #pragma unroll
@@ -211,7 +213,24 @@ __global__ void __launch_bounds__(128) k_fit_careful(const FitParams P) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_fit_unkept(const FitParams P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P.ns || P.keep[t]) return;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) P.fit_p[(size_t)k * P.ns + t] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 21; ++k) P.fit_C[(size_t)k * P.ns + t] = 0.f;
+  P.fit_chi2[t] = 0.f;
+  P.fit_status[t] = KF_FIT_SKIPPED;
+}
+
 }  // namespace
+
+cudaError_t launch_fit_unkept(const FitParams& P, cudaStream_t st) {
+  if (P.ns <= 0 || !P.keep) return cudaSuccess;
+  k_fit_unkept<<<(P.ns + 255) / 256, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;

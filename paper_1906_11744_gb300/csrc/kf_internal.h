@@ -167,6 +167,10 @@ struct FitParams {
   const int* n_list;      // [ns]
   int max_len;
   const unsigned char* keep;  // may be null
+  // false: the FP32 pass runs beside duplicate removal and fits every track
+  // (keep is still being written); launch_fit_unkept clears the removed
+  // tracks' outputs afterwards, and the careful pass reads keep as usual
+  bool keep_in_main = true;
   float* fit_p;           // [6][ns]
   float* fit_C;           // [21][ns]
   float* fit_chi2;        // [ns]
@@ -273,5 +277,8 @@ cudaError_t launch_seed_clean(const SeedCleanParams& P, int pos_begin, int pos_e
 cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st);
 cudaError_t launch_fit_careful(const FitParams& P, cudaStream_t st);
 cudaError_t launch_fit(const FitParams& P, cudaStream_t st);
+// After a main pass with keep_in_main false: the removed tracks' outputs
+// zeroed and their status KF_FIT_SKIPPED, as the main pass would have left them.
+cudaError_t launch_fit_unkept(const FitParams& P, cudaStream_t st);
 
 }  // namespace kfg

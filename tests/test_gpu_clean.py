@@ -144,9 +144,20 @@ def test_clean_dedup_fit_graph_pipeline():
     assert "seed_clean" in st and st["seed_clean"] > 0
     for k in ("hits", "n_found", "chi2", "keep"):
         assert np.array_equal(trk[k], eager_trk[k]), k
-    assert np.array_equal(fit["status"], eager_fit["status"])
-    assert np.array_equal(fit["chi2"], eager_fit["chi2"])
+    # the graph fits beside duplicate removal and clears the removed tracks
+    # afterwards: every fit output equals the eager calls'
+    for k in ("status", "chi2", "params", "cov"):
+        assert np.array_equal(fit[k], eager_fit[k]), k
     assert (trk["n_found"] == 0).sum() > 0
+    assert (~trk["keep"].astype(bool)).sum() > 0 and np.all(fit["params"][:, ~trk["keep"].astype(bool)] == 0)
+    g = tracker_for(b, device=dev, **kw)  # the same without the adjoint (careful fit in the graph's main branch)
+    g.capture_graph(with_adjoint=False, stream=s)
+    g.launch_graph(s)
+    s.synchronize()
+    fit2 = g.get_fit()
+    g.close()
+    for k in ("status", "chi2", "params", "cov"):
+        assert np.array_equal(fit2[k], eager_fit[k]), k
     for e in range(4):
         a, c = b.seed_off[e], b.seed_off[e + 1]
         ref = _dedup_ref(b, trk, a, c, (0.02, 0.02, 0.3))
