@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     // iterations: the three seed hits (careful pass only; the main pass starts
     // from the fitted seed), then the layers
     int n_iter = has_seed && !given_up ? 3 + (L - start) : 0;
-    const int it_end = __reduce_max_sync(0xffffffffu, n_iter);
+    int it_end = __reduce_max_sync(0xffffffffu, n_iter);
 
 #pragma unroll 1
     for (int it = CAREFUL ? 0 : 3; it < it_end; ++it) {
@@ -822,6 +822,15 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
           if constexpr (EL) add_eloss_ool<float>(p, C, g.eloss[l]);
         }
       }
+      // A group whose candidates are all finished (carried unchanged) or
+      // empty would only carry them on, each to its own slot, layer after
+      // layer: its seed's search ends here (the backtrack starts from the
+      // last layer searched), and the warp ends with its last live group.
+      if (!in_seed) {
+        const unsigned live = __ballot_sync(0xffffffffu, active && occ && !finished);
+        if (lane_used && active && !((live >> base) & ((1u << G) - 1u))) n_iter = min(n_iter, it + 1);
+        it_end = __reduce_max_sync(0xffffffffu, n_iter);
+      }
       __syncwarp();
     }
 
@@ -865,7 +874,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       int* oh = P.out_hits + (size_t)seed * L;
       int k = nfound - 1;
       int cur = 0;
-      for (int l = L - 1; l >= start; --l) {
+      for (int l = start + n_iter - 4; l >= start; --l) {  // from the last layer searched
         const int e = hist[(grp * L + l) * G + cur];
         if (e & 0xFFFFFF) oh[k--] = (e & 0xFFFFFF) - 1;
         cur = e >> 24;
