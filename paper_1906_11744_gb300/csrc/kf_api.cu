@@ -1043,14 +1043,18 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
     // side branch; beside it the fit's FP32 pass over every found track (it
     // removes few), whose removed tracks are cleared once both are done.
     cudaError_t fe = fork_side(ctx, st);
-    if (fe != cudaSuccess) rc = fail(ctx, KF_ERR_CUDA, cudaGetErrorString(fe));
+    const bool forked = fe == cudaSuccess;
+    if (!forked) rc = fail(ctx, KF_ERR_CUDA, cudaGetErrorString(fe));
     if (rc == KF_OK) rc = kf_remove_duplicates(ctx, (void*)ctx->side);
     ctx->fit_beside_dedup = true;
     if (rc == KF_OK) rc = kf_fit_tracks(ctx, KF_FIT_FOUND, nullptr, nullptr, 0, 1, stream);
     ctx->fit_beside_dedup = false;
-    if (rc == KF_OK) {
+    if (forked) {  // the side branch rejoins the capture on every path
       fe = join_side(ctx, st);
-      if (fe == cudaSuccess) fe = launch_fit_unkept(ctx->last_fit, st);
+      if (fe != cudaSuccess && rc == KF_OK) rc = fail(ctx, KF_ERR_CUDA, cudaGetErrorString(fe));
+    }
+    if (rc == KF_OK) {
+      fe = launch_fit_unkept(ctx->last_fit, st);
       // the careful pass after the final keep flags: in the adjoint's side
       // branch with the adjoint, here without it
       if (fe == cudaSuccess && !with_adjoint) {
