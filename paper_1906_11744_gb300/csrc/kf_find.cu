@@ -47,10 +47,12 @@ constexpr int SMEM_SLOT = 32 * 8;
 __host__ __device__ constexpr int smem_per_warp(int G, bool careful, int n_layers) {
   return smem_list(G, careful) + smem_gather(G, careful) + SMEM_SLOT + ((32 * n_layers * 4 + 15) / 16) * 16;
 }
-// The careful pass adds each lane's double-precision prediction [32][27].
+// The careful pass adds each lane's double-precision prediction [32][27] and
+// the lanes' lists of a warp-wide window search [32][KF_MAX_CANDS] u64.
 constexpr int SMEM_DSTATE = 32 * 27 * 8;
+constexpr int SMEM_COOP = 32 * KF_MAX_CANDS * 8;
 __host__ __device__ constexpr int smem_per_warp_k(int G, int n_layers, bool careful) {
-  return smem_per_warp(G, careful, n_layers) + (careful ? SMEM_DSTATE : 0);
+  return smem_per_warp(G, careful, n_layers) + (careful ? SMEM_DSTATE + SMEM_COOP : 0);
 }
 // Shared memory per block ahead of the warps' areas: the z edges of the eta
 // bins of every layer [n_layers][n_eta + 1].
@@ -287,6 +289,94 @@ __device__ __forceinline__ void scan_window(const FindParams& P, const unsigned*
   }
 }
 
+// Careful pass: a window of more than BIG_WINDOW_CELLS cells (near-tangent
+// predictions can span thousands of hits) is searched by the whole warp
+// instead of its lane alone.
+constexpr int BIG_WINDOW_CELLS = 1024;
+__device__ __forceinline__ int window_cells(const Window& w) {
+  return (w.e1 - w.e0 + 1) * (w.b1 - w.b0 + max(w.b2, 0));
+}
+
+// The warp searches the window w of lane src (all 32 lanes call this with
+// the same src; every argument is read from lane src): each lane tests every
+// 32nd hit of each range and keeps its own best max_cands children in
+// coop[lane * KF_MAX_CANDS ...]; then max_cands rounds of a warp minimum over
+// the lists' heads hand the best keys, in order, to lst (lane src's list).
+// Keys are unique, so the result is the single-lane search's.  Returns the
+// number of children on every lane.
+__device__ __noinline__ int coop_scan(const FindParams& P, int src, Window w, const unsigned* off, Align4 al,
+                                      const float* p_src, Frame f, int nf1, float chi2, int slot,
+                                      unsigned long long* coop, unsigned long long* lst, unsigned* c_chi2) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  w.e0 = __shfl_sync(FULL, w.e0, src);
+  w.e1 = __shfl_sync(FULL, w.e1, src);
+  w.b0 = __shfl_sync(FULL, w.b0, src);
+  w.b1 = __shfl_sync(FULL, w.b1, src);
+  w.b2 = __shfl_sync(FULL, w.b2, src);
+  off = reinterpret_cast<const unsigned*>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(off), src));
+  al.ca = __shfl_sync(FULL, al.ca, src);
+  al.sa = __shfl_sync(FULL, al.sa, src);
+  al.az = __shfl_sync(FULL, al.az, src);
+  float p[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = __shfl_sync(FULL, p_src[k], src);
+  f.su = __shfl_sync(FULL, f.su, src);
+  f.cu = __shfl_sync(FULL, f.cu, src);
+  f.si00 = __shfl_sync(FULL, f.si00, src);
+  f.si01 = __shfl_sync(FULL, f.si01, src);
+  f.si11 = __shfl_sync(FULL, f.si11, src);
+  nf1 = __shfl_sync(FULL, nf1, src);
+  chi2 = __shfl_sync(FULL, chi2, src);
+  slot = __shfl_sync(FULL, slot, src);
+  const int nphi = P.g.n_phi, N = P.g.max_cands;
+  const float cut = P.g.chi2_cut;
+  unsigned long long* mine = coop + lane * KF_MAX_CANDS;
+  int lc = 0;
+  unsigned n_eval = 0;
+  auto consider = [&](unsigned i) {
+    const float4 h = P.hb[i];
+    float mx, my, mz;
+    corrected_hit(al, h.x, h.y, h.z, mx, my, mz);
+    float r0, r1;
+    ++n_eval;
+    if (!residual<float>(p, f, mx, my, mz, r0, r1)) return;
+    const float c2 = chi2_of<float>(f, r0, r1);
+    if (!(c2 < cut)) return;
+    const unsigned long long key = make_key(nf1, chi2 + c2, slot, 0, __float_as_int(h.w));
+    int pos;
+    if (lc < N) pos = lc++;
+    else if (key < mine[N - 1]) pos = N - 1;
+    else return;
+    while (pos > 0 && mine[pos - 1] > key) { mine[pos] = mine[pos - 1]; --pos; }
+    mine[pos] = key;
+  };
+#pragma unroll 1
+  for (int e = w.e0; e <= w.e1; ++e) {
+    const unsigned* row = off + (size_t)e * nphi;
+    const unsigned a0 = row[w.b0], a1 = row[w.b1];
+    const unsigned c0 = w.b2 > 0 ? row[0] : 0u, c1 = w.b2 > 0 ? row[w.b2] : 0u;
+#pragma unroll 1
+    for (unsigned i = a0 + lane; i < a1; i += 32) consider(i);
+#pragma unroll 1
+    for (unsigned i = c0 + lane; i < c1; i += 32) consider(i);
+  }
+  *c_chi2 += n_eval;
+  // merge: the smallest head of the 32 lists, N times
+  int head = 0, n = 0;
+#pragma unroll 1
+  for (; n < N; ++n) {
+    const unsigned long long k = head < lc ? mine[head] : KEY_EMPTY;
+    const unsigned hi = __reduce_min_sync(FULL, (unsigned)(k >> 32));
+    const unsigned lo = __reduce_min_sync(FULL, (unsigned)(k >> 32) == hi ? (unsigned)k : 0xffffffffu);
+    const unsigned long long m = ((unsigned long long)hi << 32) | lo;
+    if (m == KEY_EMPTY) break;
+    if (k == m) ++head;
+    if (lane == src) lst[n] = m;
+  }
+  return n;
+}
+
 // Seed fit and first layer, one thread per seed of [s_begin, s_end).
 // Seed fit: at the first seed hit the update of the prior, then for the
 // second and third hit propagation, transport and update, with the
@@ -455,6 +545,8 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   constexpr int SL = smem_list(G, CAREFUL), SG = smem_gather(G, CAREFUL);
   unsigned char* ws = smem + smem_edges(L, g.n_eta) + (size_t)warp * smem_per_warp_k(G, L, CAREFUL);
   double* const dst_warp = reinterpret_cast<double*>(ws + smem_per_warp(G, CAREFUL, L));  // careful pass only
+  unsigned long long* const coop_warp =
+      reinterpret_cast<unsigned long long*>(ws + smem_per_warp(G, CAREFUL, L) + SMEM_DSTATE);  // careful pass only
   unsigned long long* lst = reinterpret_cast<unsigned long long*>(ws) + lane * LS;
   unsigned long long* gather = reinterpret_cast<unsigned long long*>(ws + SL);
   float* bak = reinterpret_cast<float*>(gather) + lane * BACKUP_STRIDE;
@@ -563,6 +655,29 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       unsigned long long tail = KEY_EMPTY;
       // main pass: the first layer after the seed was searched by the seed kernel
       const bool pre = !CAREFUL && it == 3;
+      // after the window search: the hole child, or the stop of a candidate
+      // without a compatible hit and without holes left
+      auto after_scan = [&]() {
+        if (nholes < g.max_holes) {
+          tail = make_key(nfound, chi2, gl, 1, 0);
+        } else if (cnt == 0) {
+          // no compatible hit and no hole left: the candidate stops unchanged
+          cls = 1;
+          finished = true;
+          tail = make_key(nfound, chi2, gl, 1, 0);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) p[k] = bak[k];
+#pragma unroll
+          for (int k = 0; k < 21; ++k) C[k] = bak[6 + k];
+        }
+      };
+      // careful pass: a window too large for one lane, searched by the warp
+      // after this block (its window, frame, alignment and cell offsets)
+      bool big = false;
+      Window bw{};
+      Frame bf{};
+      Align4 bal{};
+      const unsigned* boff = nullptr;
       if (active && occ && !pre) {
         if (finished) {
           cls = 1;
@@ -620,22 +735,29 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
               const Align4 al = P.align[l];
               const Window w = window_of(P, l, R, p, f, spd, al, s_edges);
               const unsigned* off = P.bin_off + ((size_t)ev * L + l) * ((size_t)g.n_eta * g.n_phi);
-              scan_window<CAREFUL>(P, off, w, al, p, f, nfound + 1, chi2, gl, lst, cnt, c_chi2);
-              if (nholes < g.max_holes) {
-                tail = make_key(nfound, chi2, gl, 1, 0);
-              } else if (cnt == 0) {
-                // no compatible hit and no hole left: the candidate stops unchanged
-                cls = 1;
-                finished = true;
-                tail = make_key(nfound, chi2, gl, 1, 0);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) p[k] = bak[k];
-#pragma unroll
-                for (int k = 0; k < 21; ++k) C[k] = bak[6 + k];
+              if (CAREFUL && window_cells(w) > BIG_WINDOW_CELLS) {
+                big = true;
+                bw = w;
+                bf = f;
+                bal = al;
+                boff = off;
+              } else {
+                scan_window<CAREFUL>(P, off, w, al, p, f, nfound + 1, chi2, gl, lst, cnt, c_chi2);
+                after_scan();
               }
             }
           }
         }
+      }
+      if constexpr (CAREFUL) {  // the large windows, one after another, by the whole warp
+        unsigned pend = __ballot_sync(0xffffffffu, big);
+        while (pend) {
+          const int src = __ffs(pend) - 1;
+          pend &= pend - 1;
+          const int n = coop_scan(P, src, bw, boff, bal, p, bf, nfound + 1, chi2, gl, coop_warp, lst, &c_chi2);
+          if (lane == src) cnt = n;
+        }
+        if (big) after_scan();
       }
 
       // Top-N of all children of each group (layers only; a group in its seed
