@@ -36,7 +36,10 @@ class Detector(ctypes.Structure):
                 ("x0", ctypes.c_double * 64), ("z_max", ctypes.c_double), ("bz", ctypes.c_double),
                 ("sigma_rphi", ctypes.c_double), ("sigma_z", ctypes.c_double),
                 ("n_z", ctypes.c_int), ("x0_map", ctypes.c_void_p), ("eloss", ctypes.c_double * 64),
-                ("field_cz", ctypes.c_double), ("field_cr", ctypes.c_double)]
+                ("field_cz", ctypes.c_double), ("field_cr", ctypes.c_double),
+                ("n_disks", ctypes.c_int), ("disk_z", ctypes.c_double * 32), ("disk_rmin", ctypes.c_double),
+                ("disk_rmax", ctypes.c_double), ("disk_x0", ctypes.c_double), ("disk_eloss", ctypes.c_double),
+                ("sigma_r", ctypes.c_double), ("eta_barrel", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -57,6 +60,14 @@ def lib():
             L.orc_propagate_ad.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, ctypes.c_double, _P]
             L.orc_transport.argtypes = [_P, _P, _P]
             L.orc_update.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P]
+            L.orc_update_disk.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P, _P]
+            L.orc_propagate_plane.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _P,
+                                              ctypes.c_double, _P, _P]
+            L.orc_propagate_plane_ad.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _P,
+                                                 ctypes.c_double, _P]
+            L.orc_eloss_disk.argtypes = [_P, _P, ctypes.c_double]
+            L.orc_highland_disk.argtypes = [_P, ctypes.c_double]
+            L.orc_highland_disk.restype = ctypes.c_double
             L.orc_highland.argtypes = [_P, ctypes.c_double]
             L.orc_x0_at.argtypes = [_P, ctypes.c_int, ctypes.c_double]
             L.orc_eloss.argtypes = [_P, _P, ctypes.c_double]
@@ -109,6 +120,16 @@ def make_detector(det) -> Detector:
         d.eloss[i] = float(np.float32(e))
     d.field_cz = float(np.float32(getattr(det, "field_cz", 0.0)))
     d.field_cr = float(np.float32(getattr(det, "field_cr", 0.0)))
+    dz = tuple(getattr(det, "disk_z", ()) or ())
+    d.n_disks = len(dz)
+    for i, v in enumerate(dz):
+        d.disk_z[i] = float(np.float32(v))
+    d.disk_rmin = float(np.float32(getattr(det, "disk_rmin", 0.0)))
+    d.disk_rmax = float(np.float32(getattr(det, "disk_rmax", 0.0)))
+    d.disk_x0 = float(np.float32(getattr(det, "disk_x0", 0.0)))
+    d.disk_eloss = float(np.float32(getattr(det, "disk_eloss", 0.0)))
+    d.sigma_r = float(np.float32(getattr(det, "sigma_r", 0.1)))
+    d.eta_barrel = float(getattr(det, "eta_barrel", 0.9))
     m = getattr(det, "x0_map", None)
     if m is not None:  # float32-rounded like every other input; kept alive by the structure
         d._map = np.ascontiguousarray(np.asarray(m, np.float32).astype(np.float64).reshape(det.n_layers, -1))
@@ -164,6 +185,43 @@ def update(p, C, m, vr, vz):
 def highland(p, x0):
     p = _c(p, np.float64)
     return lib().orc_highland(_ptr(p), x0)
+
+
+def propagate_plane(bz: float, p, zd: float, cz: float = 0.0, cr: float = 0.0):
+    """Helix to the plane z = zd (an endcap disk) in the field at the start;
+    J at that field held fixed."""
+    p = _c(p, np.float64)
+    q = np.zeros(6)
+    J = np.zeros(36)
+    ok = lib().orc_propagate_plane(bz, cz, cr, _ptr(p), zd, _ptr(q), _ptr(J))
+    return bool(ok), q, J.reshape(6, 6)
+
+
+def propagate_plane_ad(bz: float, p, zd: float, cz: float = 0.0, cr: float = 0.0):
+    p = _c(p, np.float64)
+    J = np.zeros(36)
+    ok = lib().orc_propagate_plane_ad(bz, cz, cr, _ptr(p), zd, _ptr(J))
+    return bool(ok), J.reshape(6, 6)
+
+
+def update_disk(p, C, m, vr, vrr):
+    """One Kalman update on an endcap disk: residuals along r-phi and r."""
+    p = _c(p, np.float64); C = _c(C, np.float64); m = _c(m, np.float64)
+    po, Co, c2, r = np.zeros(6), np.zeros(36), np.zeros(1), np.zeros(2)
+    ok = lib().orc_update_disk(_ptr(p), _ptr(C), _ptr(m), vr, vrr, _ptr(po), _ptr(Co), _ptr(c2), _ptr(r))
+    return bool(ok), po, Co.reshape(6, 6), float(c2[0]), r
+
+
+def highland_disk(p, x0):
+    p = _c(p, np.float64)
+    return lib().orc_highland_disk(_ptr(p), x0)
+
+
+def eloss_disk(p, C, e):
+    p = _c(p, np.float64).copy()
+    C = _c(np.asarray(C, np.float64).reshape(36), np.float64).copy()
+    lib().orc_eloss_disk(_ptr(p), _ptr(C), float(e))
+    return p, C.reshape(6, 6)
 
 
 def eloss(p, C, e):
@@ -256,7 +314,7 @@ def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=
     [n][L] (event-local, -1 padded), n_found, chi2, p [n][6], C [n][21] and
     counters."""
     det = batch.det
-    L = det.n_layers
+    L = getattr(det, "n_surfaces", det.n_layers)  # barrel layers, then endcap disks
     x, y, z, lay = batch.event_hits(e)
     prm, cov, sh = batch.event_seeds(e)
     prm = _c(prm, np.float64); cov = _c(cov, np.float64); sh = _c(sh, np.int32)

@@ -9,12 +9,17 @@
 // removal, Sec. 4.3 for candidate scores; every formula below is the standard
 // Kalman-filter reading recorded in the design notes):
 //   * state p = (x, y, z, q/pT, phi, theta), symmetric 6x6 covariance C;
+//   * barrel layers and endcap disks (Sec. 3), the event's seeds split into
+//     eta regions (Sec. 2): barrel seeds search the barrel layers, transition
+//     and endcap seeds the barrel layers and then their side's disks; a
+//     candidate passes a surface it does not cross within its bounds;
 //   * helix propagation to a cylinder of radius R in an axial field Bz, uniform
 //     or parameterized (Sec. 3) as Bz(r, z) = bz (1 + cz z^2 + cr r^2) taken at
 //     the starting point of each propagation, with the exact Jacobian of the
 //     helix J = dF/dp + dF/ds ds/dp at that field;
 //   * covariance transport C <- J C J^T;
 //   * 2D tangent-frame measurement (r-phi, z) of a 3D hit on the cylinder, chi2;
+//     on a disk: propagation to the plane z = z_k, measurement (r-phi, r);
 //   * gain K = C H^T S^-1, p <- p + K r, C <- C - K H C;
 //   * thin-scatterer multiple scattering after each layer (Highland width);
 //   * combinatorial finding with per-seed top-N candidates (Sec. 2);
@@ -27,7 +32,8 @@
 //
 // Parity status: every function here is pinned by tests under tests/ (closed
 // forms, Runge-Kutta integration, finite differences, brute force, least
-// squares, pull widths; the parameterized field by tests/test_oracle_field.py).  The finding's candidate selection (ranking key,
+// squares, pull widths; the parameterized field by tests/test_oracle_field.py,
+// the endcap disks and eta regions by tests/test_oracle_endcap.py).  The finding's candidate selection (ranking key,
 // truncation to N, hole limit, stop and carry rules, chi2 cut) is pinned by
 // hand-made child lists and by a brute-force beam on tiny events that
 // recomputes every path through orc_replay.
@@ -315,7 +321,19 @@ struct Det {
   const double* x0_map;  // [n_layers][n_z] thickness at z_k = -z_max + k 2 z_max/(n_z - 1)
   double eloss[64];      // mean ionization loss per layer at normal incidence, beta -> 1 (GeV; 0: none)
   double field_cz, field_cr;  // Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2) (0, 0: uniform)
+  // Endcap disks: planes at z = +-disk_z[k], disk_rmin <= r <= disk_rmax.
+  // Surfaces: barrel layers 0..L-1, +z disks L..L+D-1, -z disks L+D..L+2D-1.
+  int n_disks;
+  double disk_z[32];
+  double disk_rmin, disk_rmax, disk_x0, disk_eloss, sigma_r;
+  double eta_barrel;  // seeds with |eta| >= eta_barrel search their side's disks after the barrel
   Field field() const { return Field{bz, field_cz, field_cr}; }
+  int n_surfaces() const { return n_layers + 2 * n_disks; }
+  bool is_disk(int s) const { return s >= n_layers; }
+  double plane_z(int s) const {
+    const int k = s - n_layers;
+    return k < n_disks ? disk_z[k] : -disk_z[k - n_disks];
+  }
 };
 
 struct Cfg {
@@ -474,6 +492,59 @@ bool propagate(const Field& fld, const T p[6], double R, T q[6], T J[6][6]) {
   return true;
 }
 
+// Propagate p to the plane z = zd (an endcap disk): the transverse arc
+// s = (zd - z) tan(theta) > 0 (the track must move towards the plane, and
+// reach it within half a turn, |h s| < pi), the helix there in the field at
+// the starting point; q[2] = zd.  J = dq/dp at
+// that field: the partials at fixed s plus dq/ds ds/dp with ds/dz = -tan(theta),
+// ds/dtheta = (zd - z)/cos^2(theta) (so the z row of J vanishes).
+template <class T>
+bool propagate_plane(const Field& fld, const T p[6], double zd, T q[6], T J[6][6]) {
+  const T& x = p[0];
+  const T& y = p[1];
+  const T& z = p[2];
+  const T& kap = p[3];
+  const T& phi = p[4];
+  const T& th = p[5];
+  const T cot = cos(th) / sin(th);
+  if (std::fabs(val(cot)) < 1e-12) return false;
+  const T s = (zd - z) / cot;
+  if (!(val(s) > 0.0)) return false;
+  const T kb = field_kb(fld, x, y, z);
+  const T h = kb * kap;
+  const T psi = h * s;
+  // within half a turn: a looper that would reach the plane after more turns
+  // would meet the barrel layers again first, which the finding does not follow
+  if (!(std::fabs(val(psi)) < M_PI)) return false;
+  T sc, cc, f1, f2;
+  helix_functions(psi, sc, cc, f1, f2);
+  const T cf = cos(phi), sf = sin(phi);
+  const T Sx = s * sc, Cx = s * cc;
+  q[0] = x + cf * Sx - sf * Cx;
+  q[1] = y + sf * Sx + cf * Cx;
+  q[2] = z + s * cot;  // zd (its derivatives vanish)
+  q[3] = kap;
+  q[4] = phi + psi;
+  q[5] = th;
+  T F[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) F[i][j] = T(i == j ? 1.0 : 0.0);
+  const T dSdh = s * s * f1, dCdh = s * s * f2;
+  F[0][3] = kb * (cf * dSdh - sf * dCdh);
+  F[0][4] = -(q[1] - y);
+  F[1][3] = kb * (sf * dSdh + cf * dCdh);
+  F[1][4] = q[0] - x;
+  const T sth = sin(th), cth = cos(th);
+  F[2][5] = -s / (sth * sth);
+  F[4][3] = kb * s;
+  T dsdp[6] = {T(0.0), T(0.0), -1.0 / cot, T(0.0), T(0.0), (zd - z) / (cth * cth)};
+  const T cp = cos(q[4]), sp = sin(q[4]);
+  T dqds[6] = {cp, sp, cot, T(0.0), h, T(0.0)};
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) J[i][j] = F[i][j] + dqds[i] * dsdp[j];
+  return true;
+}
+
 // C <- (out + out^T) / 2.  For the operation census a symmetric result is
 // computed once: C takes the upper triangle of out (no operation).
 template <class T>
@@ -517,18 +588,27 @@ struct Meas {
   T chi2;
 };
 
+// On an endcap disk (disk = true) the second coordinate is radial:
+// r = (u.(m_xy - p_xy), w.(m_xy - p_xy)) with w = (cos phi_p, sin phi_p), and
+// vz is the radial variance.
 template <class T>
-bool measure(const T p[6], const T C[6][6], const T m[3], double vr, double vz, Meas<T>& o) {
+bool measure(const T p[6], const T C[6][6], const T m[3], double vr, double vz, Meas<T>& o,
+             bool disk = false) {
   if (val(m[0]) * val(p[0]) + val(m[1]) * val(p[1]) <= 0.0) return false;
   T phip = atan2(p[1], p[0]);
   T su = sin(phip), cu = cos(phip);
   o.r[0] = -su * (m[0] - p[0]) + cu * (m[1] - p[1]);
-  o.r[1] = m[2] - p[2];
+  o.r[1] = disk ? cu * (m[0] - p[0]) + su * (m[1] - p[1]) : m[2] - p[2];
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 6; ++j) o.H[i][j] = T(0.0);
   o.H[0][0] = -su;
   o.H[0][1] = cu;
-  o.H[1][2] = T(1.0);
+  if (disk) {
+    o.H[1][0] = cu;
+    o.H[1][1] = su;
+  } else {
+    o.H[1][2] = T(1.0);
+  }
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) {
       T acc(0.0);
@@ -576,20 +656,26 @@ void kf_update(T p[6], T C[6][6], const Meas<T>& m) {
 // Multiple scattering in a thin layer of x0 radiation lengths at the current
 // position: Highland width theta0 = 0.0136/(beta p) sqrt(t) (1 + 0.038 ln t),
 // t = x0 / |sin(theta) cos(phi - phi_p)|, p = pT/sin(theta), pion mass for beta.
+// On an endcap disk (normal along z) t = x0 / |cos(theta)|.
 template <class T>
-T highland(const T p[6], T x0) {
+T highland(const T p[6], T x0, bool disk = false) {
   T st = sin(p[5]);
   T pm = 1.0 / (fabs(p[3]) * st);
   T beta = pm / sqrt(pm * pm + MPION * MPION);
-  T phip = atan2(p[1], p[0]);
-  T t = x0 / fabs(st * cos(p[4] - phip));
+  T t;
+  if (disk) {
+    t = x0 / fabs(cos(p[5]));
+  } else {
+    T phip = atan2(p[1], p[0]);
+    t = x0 / fabs(st * cos(p[4] - phip));
+  }
   return 0.0136 / (beta * pm) * sqrt(t) * (1.0 + 0.038 * log(t));
 }
 
 template <class T>
-void add_ms(const T p[6], T C[6][6], T x0) {
+void add_ms(const T p[6], T C[6][6], T x0, bool disk = false) {
   if (val(p[3]) == 0.0 || val(x0) <= 0.0) return;
-  T th0 = highland(p, x0);
+  T th0 = highland(p, x0, disk);
   T st = sin(p[5]);
   T v = th0 * th0;
   C[4][4] += v / (st * st);
@@ -625,8 +711,10 @@ T x0_at(const Det& det, int L, const T& z) {
 // The covariance follows the map: C' = F C F^T, F the identity but for the
 // q/pT row dk'/dp (written out below; pinned against finite differences).
 // Straggling is not modelled.
+// On an endcap disk the path factor is f = 1/|cos(theta)|, so that
+// d log f = tan(theta) d theta and q/pT' depends on neither position nor phi.
 template <class T>
-void add_eloss(T p[6], T C[6][6], double e) {
+void add_eloss(T p[6], T C[6][6], double e, bool disk = false) {
   if (e <= 0.0 || val(p[3]) == 0.0) return;
   const T st = sin(p[5]), ct = cos(p[5]);
   const T pm = 1.0 / (fabs(p[3]) * st);
@@ -634,7 +722,7 @@ void add_eloss(T p[6], T C[6][6], double e) {
   const T b2 = pm * pm / (E * E);
   const T phip = atan2(p[1], p[0]);
   const T cd = cos(p[4] - phip), sd = sin(p[4] - phip);
-  const T f = 1.0 / fabs(st * cd);
+  const T f = disk ? 1.0 / fabs(ct) : 1.0 / fabs(st * cd);
   T dE = e * f / b2;
   if (val(dE) > 0.5 * (val(E) - MPION)) dE = 0.5 * (E - MPION);
   const T E1 = E - dE;
@@ -653,6 +741,10 @@ void add_eloss(T p[6], T C[6][6], double e) {
   F3[3] = k1 * A / p[3];
   F3[4] = -k1 * B * tn;
   F3[5] = k1 * (ct / st) * (A + B - 1.0);
+  if (disk) {
+    F3[0] = F3[1] = F3[4] = T(0.0);
+    F3[5] = k1 * ((ct / st) * (A - 1.0) - B * (st / ct));
+  }
   // C' = F C F^T with F = I except row 3
   T c3[6];  // row 3 of F C
   for (int j = 0; j < 6; ++j) {
@@ -694,25 +786,37 @@ int fit_track(const Det& det, const T p0[6], const TC C0[6][6], int n, const T (
   }
   chi2 = T(0.0);
   const double vr = det.sigma_rphi * det.sigma_rphi, vz = det.sigma_z * det.sigma_z;
+  const double vrr = det.sigma_r * det.sigma_r;
   for (int k = 0; k < n; ++k) {
     const int L = layers[k];
-    const double R = det.radius[L];
+    const bool disk = det.is_disk(L);  // an endcap disk: plane, radial coordinate, no alignment
+    const double R = disk ? 0.0 : det.radius[L];
     if (k > 0) {
       T q[6], J[6][6];
-      if (!propagate(det.field(), p, R, q, J)) return -1;
+      if (disk ? !propagate_plane(det.field(), p, det.plane_z(L), q, J) : !propagate(det.field(), p, R, q, J))
+        return -1;
       for (int i = 0; i < 6; ++i) p[i] = q[i];
       transport(J, C);
     }
     T m[3];
-    correct_hit(raw[k], align[L][0], align[L][1], R, m);
+    if (disk) {
+      for (int i = 0; i < 3; ++i) m[i] = raw[k][i];
+    } else {
+      correct_hit(raw[k], align[L][0], align[L][1], R, m);
+    }
     Meas<T> ms;
-    if (!measure(p, C, m, vr, vz, ms)) return -2;
+    if (!measure(p, C, m, vr, disk ? vrr : vz, ms, disk)) return -2;
     chi2 += ms.chi2;
     if (chi2_each) chi2_each[k] = ms.chi2;
     kf_update(p, C, ms);
     if (k + 1 < n || ms_after_last) {
-      add_ms(p, C, x0_at(det, L, p[2]));
-      add_eloss(p, C, det.eloss[L]);
+      if (disk) {
+        add_ms(p, C, T(det.disk_x0), true);
+        add_eloss(p, C, det.disk_eloss, true);
+      } else {
+        add_ms(p, C, x0_at(det, L, p[2]));
+        add_eloss(p, C, det.eloss[L]);
+      }
     }
   }
   return 0;
@@ -812,8 +916,21 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
   }
   std::vector<Cand> cands{c0};
   const int start = hlayer[sh[2]] + 1;
-  for (int Lyr = start; Lyr < L; ++Lyr) {
-    const double R = det.radius[Lyr];
+  // The surfaces the seed's candidates search (Sec. 2: the event is split into
+  // eta regions, each with its layers): the barrel layers after the seed, and
+  // for a seed in a forward region (|eta| >= eta_barrel; transition and endcap
+  // regions alike) then the endcap disks of its side in order of |z|.
+  std::vector<int> plan;
+  for (int l = start; l < L; ++l) plan.push_back(l);
+  const double eta0 = -std::log(std::tan(0.5 * p0[5]));
+  const bool fwd = det.n_disks > 0 && std::fabs(eta0) >= det.eta_barrel;
+  if (fwd)
+    for (int k = 0; k < det.n_disks; ++k) plan.push_back(L + k + (eta0 < 0.0 ? det.n_disks : 0));
+  const double vrr = det.sigma_r * det.sigma_r;
+  for (const int Lyr : plan) {
+    const bool disk = det.is_disk(Lyr);
+    const double R = disk ? 0.0 : det.radius[Lyr];
+    const double v2 = disk ? vrr : vz;
     std::vector<Child> children;
     std::vector<Cand> predicted(cands.size());
     for (size_t r = 0; r < cands.size(); ++r) {
@@ -826,32 +943,48 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
       pc = c;
       double J[6][6];
       ++cnt.prop_calls;
-      if (!propagate(det.field(), c.p, R, pc.p, J) || std::fabs(pc.p[2]) > det.z_max) {
-        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, 0});
+      bool crossed;
+      if (!disk) {
+        crossed = propagate(det.field(), c.p, R, pc.p, J) && std::fabs(pc.p[2]) <= det.z_max;
+      } else {
+        crossed = propagate_plane(det.field(), c.p, det.plane_z(Lyr), pc.p, J);
+        const double rr = crossed ? std::hypot(pc.p[0], pc.p[1]) : 0.0;
+        crossed = crossed && rr >= det.disk_rmin && rr <= det.disk_rmax;
+      }
+      if (!crossed) {
+        // a barrel-only plan: the candidate has left the detector (it is
+        // carried, finished); a forward plan: it passes this surface unchanged
+        // (tag 1: carried, not finished, no hole) and meets the next
+        children.push_back({c.n_found, c.chi2, (int)r, KIND_CARRIED, -1, fwd ? 1 : 0});
         continue;
       }
       transport(J, pc.C);
       ++cnt.steps;
       int n_children = 0;
       // Window on z: chi2 >= r_z^2 / S_zz for a 2x2 positive-definite S, so
-      // hits with |m_z - z| > sqrt(cut * S_zz) cannot pass the cut.
+      // hits with |m_z - z| > sqrt(cut * S_zz) cannot pass the cut.  A disk's
+      // hits are all tested.
       const double szz = pc.C[2][2] + vz;
       double lo_z = -1e300, hi_z = 1e300;
-      if (!brute) {
+      if (!brute && !disk) {
         // corrected z = raw z - a_z, so the raw-z interval is shifted by a_z
         const double w = std::sqrt(cfg.chi2_cut * szz) + 1e-9;
         lo_z = pc.p[2] + align[Lyr][1] - w;
         hi_z = pc.p[2] + align[Lyr][1] + w;
       }
       const LayerIndex& li = lidx[Lyr];
-      size_t b = std::lower_bound(li.z.begin(), li.z.end(), lo_z) - li.z.begin();
-      for (size_t k = b; k < li.idx.size() && li.z[k] <= hi_z; ++k) {
+      size_t b = disk ? 0 : std::lower_bound(li.z.begin(), li.z.end(), lo_z) - li.z.begin();
+      for (size_t k = b; k < li.idx.size() && (disk || li.z[k] <= hi_z); ++k) {
         const int hidx = li.idx[k];
         double raw[3] = {hx[hidx], hy[hidx], hz[hidx]}, m[3];
-        correct_hit(raw, align[Lyr][0], align[Lyr][1], R, m);
+        if (disk) {
+          for (int i = 0; i < 3; ++i) m[i] = raw[i];
+        } else {
+          correct_hit(raw, align[Lyr][0], align[Lyr][1], R, m);
+        }
         Meas<double> ms;
         ++cnt.chi2_evals;
-        if (!measure(pc.p, pc.C, m, vr, vz, ms)) continue;
+        if (!measure(pc.p, pc.C, m, vr, v2, ms, disk)) continue;
         if (std::fabs(ms.r[0]) < std::sqrt(cfg.chi2_cut * ms.S[0][0]) &&
             std::fabs(ms.r[1]) < std::sqrt(cfg.chi2_cut * ms.S[1][1]))
           ++cnt.window_hits;
@@ -877,16 +1010,20 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
       const Child& ch = children[k];
       if (ch.kind == KIND_CARRIED) {
         Cand c = cands[ch.parent];
-        c.finished = true;
+        if (ch.tag == 0) c.finished = true;  // tag 1: passed a surface, still searching
         next.push_back(c);
         continue;
       }
       Cand c = predicted[ch.parent];
       if (ch.kind == KIND_HIT) {
         double raw[3] = {hx[ch.hit], hy[ch.hit], hz[ch.hit]}, m[3];
-        correct_hit(raw, align[Lyr][0], align[Lyr][1], R, m);
+        if (disk) {
+          for (int i = 0; i < 3; ++i) m[i] = raw[i];
+        } else {
+          correct_hit(raw, align[Lyr][0], align[Lyr][1], R, m);
+        }
         Meas<double> ms;
-        measure(c.p, c.C, m, vr, vz, ms);
+        measure(c.p, c.C, m, vr, v2, ms, disk);
         kf_update(c.p, c.C, ms);
         c.n_found += 1;
         c.chi2 = ch.chi2;
@@ -896,15 +1033,21 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
         c.n_holes += 1;
         ++cnt.holes;
       }
-      add_ms(c.p, c.C, x0_at(det, Lyr, c.p[2]));
-      add_eloss(c.p, c.C, det.eloss[Lyr]);
+      if (disk) {
+        add_ms(c.p, c.C, det.disk_x0, true);
+        add_eloss(c.p, c.C, det.disk_eloss, true);
+      } else {
+        add_ms(c.p, c.C, x0_at(det, Lyr, c.p[2]));
+        add_eloss(c.p, c.C, det.eloss[Lyr]);
+      }
       ++cnt.ms;
       next.push_back(c);
     }
     cands.swap(next);
   }
   const Cand& best = cands[0];
-  for (int k = 0; k < L; ++k) out_hits[k] = k < (int)best.hits.size() ? best.hits[k] : -1;
+  const int S = det.n_surfaces();
+  for (int k = 0; k < S; ++k) out_hits[k] = k < (int)best.hits.size() ? best.hits[k] : -1;
   *out_n = (int)best.hits.size();
   *out_chi2 = best.chi2;
   for (int k = 0; k < 6; ++k) out_p[k] = best.p[k];
@@ -970,6 +1113,9 @@ struct orc_detector {
   const double* x0_map;  // [n_layers][n_z]
   double eloss[64];      // mean ionization loss per layer (GeV; 0: none)
   double field_cz, field_cr;  // Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2)
+  int n_disks;                // endcap disks per side (see Det)
+  double disk_z[32];
+  double disk_rmin, disk_rmax, disk_x0, disk_eloss, sigma_r, eta_barrel;
 };
 
 struct orc_config {
@@ -991,6 +1137,14 @@ static Det to_det(const orc_detector* d) {
   for (int i = 0; i < 64; ++i) o.eloss[i] = d->eloss[i];
   o.field_cz = d->field_cz;
   o.field_cr = d->field_cr;
+  o.n_disks = d->n_disks;
+  for (int i = 0; i < 32; ++i) o.disk_z[i] = d->disk_z[i];
+  o.disk_rmin = d->disk_rmin;
+  o.disk_rmax = d->disk_rmax;
+  o.disk_x0 = d->disk_x0;
+  o.disk_eloss = d->disk_eloss;
+  o.sigma_r = d->sigma_r;
+  o.eta_barrel = d->eta_barrel;
   return o;
 }
 
@@ -1034,6 +1188,54 @@ void orc_transport(const double* J, const double* C, double* C_out) {
 
 // One measurement + update at the current state.  Returns 0 if the hit is on
 // the far side, 1 otherwise.
+// Propagation to the plane z = zd (an endcap disk), J row-major 6x6; and its
+// Jacobian by forward-mode differentiation of the whole map.
+int orc_propagate_plane(double bz, double cz, double cr, const double* p, double zd, double* q, double* J) {
+  double Jm[6][6];
+  if (!propagate_plane<double>(Field{bz, cz, cr}, p, zd, q, Jm)) return 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) J[i * 6 + j] = Jm[i][j];
+  return 1;
+}
+
+int orc_propagate_plane_ad(double bz, double cz, double cr, const double* p, double zd, double* Jad) {
+  g_nd = 6;
+  Dual pd[6], qd[6], Jd[6][6];
+  for (int k = 0; k < 6; ++k) pd[k] = make_var(p[k], k);
+  const bool ok = propagate_plane<Dual>(Field{bz, cz, cr}, pd, zd, qd, Jd);
+  if (ok)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) Jad[i * 6 + j] = qd[i].d[j];
+  g_nd = 0;
+  return ok ? 1 : 0;
+}
+
+// One Kalman update on an endcap disk (radial second coordinate, variance vrr).
+int orc_update_disk(const double* p, const double* C, const double* m, double vr, double vrr,
+                    double* p_out, double* C_out, double* chi2, double* resid) {
+  double pp[6], Cm[6][6];
+  for (int i = 0; i < 6; ++i) pp[i] = p[i];
+  for (int i = 0; i < 36; ++i) Cm[i / 6][i % 6] = C[i];
+  Meas<double> ms;
+  if (!measure(pp, Cm, m, vr, vrr, ms, true)) return 0;
+  kf_update(pp, Cm, ms);
+  for (int i = 0; i < 6; ++i) p_out[i] = pp[i];
+  for (int i = 0; i < 36; ++i) C_out[i] = Cm[i / 6][i % 6];
+  *chi2 = ms.chi2;
+  if (resid) { resid[0] = ms.r[0]; resid[1] = ms.r[1]; }
+  return 1;
+}
+
+// Energy loss step on a disk (path factor 1/|cos theta|): p [6], C [36] in place.
+void orc_eloss_disk(double* p, double* C, double e) {
+  double Cm[6][6];
+  for (int i = 0; i < 36; ++i) Cm[i / 6][i % 6] = C[i];
+  add_eloss(p, Cm, e, true);
+  for (int i = 0; i < 36; ++i) C[i] = Cm[i / 6][i % 6];
+}
+
+double orc_highland_disk(const double* p, double x0) { return highland<double>(p, x0, true); }
+
 int orc_update(const double* p, const double* C, const double* m, double vr, double vz,
                double* p_out, double* C_out, double* chi2, double* resid) {
   double pp[6], Cm[6][6];
@@ -1185,7 +1387,7 @@ int orc_fit_grad32(const orc_detector* dptr, int n_tracks, const double* prior_p
 
 // Combinatorial finding for seeds [s_begin, s_end) of one event.  Hits are
 // the event's arrays (event-local indices); seeds are structure-of-arrays with
-// the given stride; seed_hits [3][stride].  out_hits [n][n_layers] (padded -1),
+// the given stride; seed_hits [3][stride].  out_hits [n][surfaces] (padded -1),
 // out_p [n][6], out_C [n][21].  counters [9]: see Counters.  brute != 0 tests every
 // hit of the layer instead of the exact z pre-selection.
 int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits, const double* hx,
@@ -1195,13 +1397,13 @@ int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits,
                    double* out_p, double* out_C, long long* counters) {
   const Det det = to_det(dptr);
   Cfg cfg{cfgp->max_cands, cfgp->max_holes, cfgp->chi2_cut};
-  const int L = det.n_layers;
+  const int L = det.n_layers, S = det.n_surfaces();
   double al[64][2];
   for (int i = 0; i < L; ++i) { al[i][0] = align[2 * i]; al[i][1] = align[2 * i + 1]; }
-  std::vector<LayerIndex> lidx(L);
+  std::vector<LayerIndex> lidx(S);
   for (int h = 0; h < n_hits; ++h)
-    if (hlayer[h] >= 0 && hlayer[h] < L) lidx[hlayer[h]].idx.push_back(h);
-  for (int l = 0; l < L; ++l) {
+    if (hlayer[h] >= 0 && hlayer[h] < S) lidx[hlayer[h]].idx.push_back(h);
+  for (int l = 0; l < S; ++l) {
     LayerIndex& li = lidx[l];
     if (!brute)
       std::stable_sort(li.idx.begin(), li.idx.end(), [&](int a, int b) { return hz[a] < hz[b]; });
@@ -1215,7 +1417,7 @@ int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits,
                        seed_hits[2 * stride + s]};
     const int o = s - s_begin;
     find_seed(det, cfg, hx, hy, hz, hlayer, lidx, brute != 0, n_hits, p0, C0, sh, al,
-              out_hits + (size_t)o * L, out_n + o, out_chi2 + o, out_p + 6 * (size_t)o,
+              out_hits + (size_t)o * S, out_n + o, out_chi2 + o, out_p + 6 * (size_t)o,
               out_C + 21 * (size_t)o, cnt);
   }
   if (counters) {

@@ -58,10 +58,33 @@ class Detector:
     # helix steps per layer, each in the field at its starting point
     field_cz: float = 0.0
     field_cr: float = 0.0
+    # endcap disks (Sec. 2 and 3: barrel layers and endcap disks, the event
+    # split into five eta regions): planes at z = +-disk_z[k] (|z| increasing)
+    # covering disk_rmin <= r <= disk_rmax, each disk_x0 radiation lengths
+    # thick (with disk_eloss mean ionization loss at normal incidence, GeV);
+    # hits measured along r-phi (sigma_rphi) and r (sigma_r).  Surfaces are
+    # numbered barrel layers 0..L-1, then the +z disks, then the -z disks.
+    # Seeds with |eta| >= eta_barrel search the disks of their side after the
+    # barrel layers.
+    disk_z: tuple = ()
+    disk_rmin: float = 15.0
+    disk_rmax: float = 110.0
+    disk_x0: float = 0.02
+    disk_eloss: float = 0.0
+    sigma_r: float = 0.1
+    eta_barrel: float = 0.9
 
     @property
     def n_layers(self) -> int:
         return len(self.radius)
+
+    @property
+    def n_disks(self) -> int:
+        return len(self.disk_z)
+
+    @property
+    def n_surfaces(self) -> int:
+        return self.n_layers + 2 * self.n_disks
 
 
 def detector_for(n_layers: int, r_min: float, r_max: float, bz: float = 3.8,
@@ -103,6 +126,12 @@ CONFIGS: Dict[str, dict] = {
     # PU-200 HL-LHC-like batch: 100 events x 8,000 tracks, 20% noise, N = 10.
     "c4": dict(n_events=100, tracks=8000, n_layers=17, r_max=110.0, eta_max=1.5,
                noise=0.20, max_cands=10, seed=1004),
+    # Barrel and endcaps: c1's barrel plus seven disks per side at |z| =
+    # 130-250 cm (r 15-110 cm), tracks over |eta| < 2.4, so that about half of
+    # the seeds lie in the forward eta regions.
+    "c5": dict(n_events=1, tracks=2500, n_layers=17, r_max=110.0, eta_max=2.4,
+               noise=0.10, max_cands=6, seed=1005,
+               disk_z=(130.0, 150.0, 170.0, 190.0, 210.0, 230.0, 250.0)),
 }
 
 
@@ -199,6 +228,38 @@ def _cross_in_field(x, y, z, kappa, phi, theta, R, det: Detector):
     return ok, x, y, z, phi
 
 
+def _cross_plane(x, y, z, kappa, phi, theta, zd, bz):
+    """Truth tracing to the plane z = zd: the transverse arc s = (zd - z) tan
+    theta (s > 0 and less than half a turn, |h s| < pi), then the helix there.
+    Returns (ok, x, y, phi)."""
+    cot = np.cos(theta) / np.sin(theta)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = (zd - z) / cot
+    ok = np.isfinite(s) & (s > 0)
+    s = np.where(ok, s, 0.0)
+    h = -K_FIELD * bz * kappa
+    straight = np.abs(h) < 1e-12
+    ok &= np.abs(h * s) < np.pi  # within half a turn (a looper would meet barrel layers again first)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        hs = h * s
+        sin_term = np.where(straight, s, np.sin(hs) / np.where(straight, 1.0, h))
+        cos_term = np.where(straight, 0.0, (1.0 - np.cos(hs)) / np.where(straight, 1.0, h))
+    xn = x + np.cos(phi) * sin_term - np.sin(phi) * cos_term
+    yn = y + np.sin(phi) * sin_term + np.cos(phi) * cos_term
+    return ok, xn, yn, phi + hs
+
+
+def _highland_disk(kappa, theta, x0):
+    """Highland width in a disk of x0 radiation lengths (path factor 1/|cos theta|)."""
+    sin_t = np.sin(theta)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        p = 1.0 / (np.abs(kappa) * sin_t)
+        beta = p / np.sqrt(p * p + M_PION * M_PION)
+        t = x0 / np.abs(np.cos(theta))
+        th0 = 0.0136 / (beta * p) * np.sqrt(t) * (1.0 + 0.038 * np.log(t))
+    return np.where(np.isfinite(th0), th0, 0.0)
+
+
 @dataclasses.dataclass
 class Event:
     x: np.ndarray
@@ -206,8 +267,8 @@ class Event:
     z: np.ndarray
     layer: np.ndarray
     sim: np.ndarray  # generating track index, -1 for noise
-    track_hits: np.ndarray  # [n_tracks][n_layers] hit index or -1
-    truth: np.ndarray  # [n_tracks][n_layers][6] state at each crossing, before the kick
+    track_hits: np.ndarray  # [n_tracks][n_surfaces] hit index or -1
+    truth: np.ndarray  # [n_tracks][n_surfaces][6] state at each crossing, before the kick
     n_tracks: int
 
 
@@ -228,8 +289,11 @@ def simulate_event(det: Detector, n_tracks: int, eta_max: float, noise: float,
     ph, th = phi.copy(), theta.copy()
     alive = np.ones(n, dtype=bool)
     hx_l, hy_l, hz_l, sim_l, lay_l = [], [], [], [], []
-    truth = np.full((n, L, 6), np.nan)
-    local_index = np.full((n, L), -1, dtype=np.int64)  # index into this event's hit list (pre-shuffle)
+    S = det.n_surfaces
+    if det.n_disks and (det.field_cz != 0.0 or det.field_cr != 0.0):
+        raise ValueError("endcap disks are simulated in a uniform field only")
+    truth = np.full((n, S, 6), np.nan)
+    local_index = np.full((n, S), -1, dtype=np.int64)  # index into this event's hit list (pre-shuffle)
     n_hits = 0
     for li in range(L):
         R = det.radius[li]
@@ -282,6 +346,53 @@ def simulate_event(det: Detector, n_tracks: int, eta_max: float, noise: float,
             sim_l.append(np.full(n_noise, -1, dtype=np.int32))
             lay_l.append(np.full(n_noise, li, dtype=np.int32))
             n_hits += n_noise
+    # Endcap disks on each track's side, from its last barrel crossing (a disk
+    # whose plane the track does not reach, or reaches outside the disk's
+    # radii, gives no hit and no scattering).
+    side = np.sign(np.cos(th))
+    for k in range(det.n_disks):
+        for sgn, si in ((1.0, det.n_layers + k), (-1.0, det.n_layers + det.n_disks + k)):
+            zd = sgn * det.disk_z[k]
+            ok, xn, yn, phn = _cross_plane(x, y, z, kappa, ph, th, zd, det.bz)
+            rn = np.hypot(xn, yn)
+            ok &= (side == sgn) & (rn >= det.disk_rmin) & (rn <= det.disk_rmax)
+            idx = np.nonzero(ok)[0]
+            phi_pos = np.arctan2(yn, xn)
+            d_rphi = rng.normal(0.0, det.sigma_rphi, size=n)
+            d_r = rng.normal(0.0, det.sigma_r, size=n)
+            kicks = rng.normal(size=(2, n))
+            truth[idx, si, 0] = xn[idx]
+            truth[idx, si, 1] = yn[idx]
+            truth[idx, si, 2] = zd
+            truth[idx, si, 3] = kappa[idx]
+            truth[idx, si, 4] = phn[idx]
+            truth[idx, si, 5] = th[idx]
+            hr = rn + d_r
+            hphi = phi_pos + d_rphi / rn
+            hx_l.append(hr[idx] * np.cos(hphi[idx]))
+            hy_l.append(hr[idx] * np.sin(hphi[idx]))
+            hz_l.append(np.full(idx.size, zd))
+            sim_l.append(idx.astype(np.int32))
+            lay_l.append(np.full(idx.size, si, dtype=np.int32))
+            local_index[idx, si] = n_hits + np.arange(idx.size)
+            n_hits += idx.size
+            th0 = _highland_disk(kappa, th, det.disk_x0)
+            sin_t = np.sin(th)
+            x = np.where(ok, xn, x)
+            y = np.where(ok, yn, y)
+            z = np.where(ok, zd, z)
+            ph = np.where(ok, phn + kicks[0] * th0 / sin_t, ph)
+            th = np.where(ok, th + kicks[1] * th0, th)
+            n_noise = int(round(noise * idx.size))
+            if n_noise:
+                nphi = rng.uniform(-np.pi, np.pi, size=n_noise)
+                nr = np.sqrt(rng.uniform(det.disk_rmin ** 2, det.disk_rmax ** 2, size=n_noise))
+                hx_l.append(nr * np.cos(nphi))
+                hy_l.append(nr * np.sin(nphi))
+                hz_l.append(np.full(n_noise, zd))
+                sim_l.append(np.full(n_noise, -1, dtype=np.int32))
+                lay_l.append(np.full(n_noise, si, dtype=np.int32))
+                n_hits += n_noise
     hx = np.concatenate(hx_l)
     hy = np.concatenate(hy_l)
     hz = np.concatenate(hz_l)
@@ -409,6 +520,9 @@ def make_batch(name: str, n_events: Optional[int] = None, tracks: Optional[int] 
         cfg["tracks"] = tracks
     det = detector_for(cfg["n_layers"], 4.0, cfg["r_max"], bz=3.8 if bz is None else bz,
                        field_cz=cfg.get("field_cz", 0.0), field_cr=cfg.get("field_cr", 0.0))
+    disk_keys = ("disk_z", "disk_rmin", "disk_rmax", "disk_x0", "disk_eloss", "sigma_r", "eta_barrel")
+    if any(k in cfg for k in disk_keys):
+        det = dataclasses.replace(det, **{k: cfg[k] for k in disk_keys if k in cfg})
     L = det.n_layers
     align = np.zeros((L, 2), dtype=np.float32)
     if cfg.get("misalign_sigma"):
