@@ -51,6 +51,7 @@ extern "C" {
 #define KF_ERR_STATE (-5)    /* calls made out of order */
 
 #define KF_MAX_LAYERS 32       /* barrel layers */
+#define KF_MAX_DISKS 16        /* endcap disks per side */
 #define KF_MAX_CANDS 16        /* candidates kept per seed */
 #define KF_MAX_EVENT_HITS (1 << 21) /* hits per event (21-bit hit index in ranking keys) */
 #define KF_SEED_MAX_DETA 1.0f       /* largest eta window of seed cleaning */
@@ -95,6 +96,32 @@ typedef struct {
    * (pT, eta, phi0 cuts) use bz. */
   float field_cz;
   float field_cr;
+  /* Endcap disks (Sec. 2: barrel layers and endcap disks, each event split
+   * into eta regions).  n_disks planes per side at z = +-disk_z[k] (0 <
+   * disk_z[0] < disk_z[1] < ..., each beyond z_max), covering disk_rmin <= r <=
+   * disk_rmax, each disk_x0 radiation lengths thick with mean ionization loss
+   * disk_eloss at normal incidence (GeV, >= 0).  Surfaces: barrel layers
+   * 0..n_layers-1, the +z disks n_layers..n_layers+n_disks-1, then the -z
+   * disks; a hit's layer index names its surface (n_surfaces = n_layers +
+   * 2 n_disks).  On a disk: the measurement is (r-phi, r) with resolutions
+   * sigma_rphi and sigma_r; propagation is the helix to the plane (transverse
+   * arc s = (z_d - z) tan(theta) > 0, less than half a turn, in the field at
+   * the starting point); scattering and energy loss take the path factor
+   * 1/|cos(theta)|; hits carry no alignment.  Finding: a seed whose prior has
+   * |eta| >= eta_barrel (a transition or endcap region) searches the barrel
+   * layers after its seed and then the disks of its side in order of |z|;
+   * along such a plan a surface that a candidate does not cross within its
+   * bounds is passed (no hole, the candidate goes on).  Other seeds search
+   * the barrel layers only, as without disks.  Seed hits lie on barrel
+   * layers.  n_disks = 0: a barrel detector (the fields below are unused).
+   * The adjoint (kf_fit_adjoint) takes barrel hits only. */
+  int n_disks;  /* 0..KF_MAX_DISKS */
+  float disk_z[KF_MAX_DISKS];
+  float disk_rmin, disk_rmax;  /* cm, 0 < disk_rmin < disk_rmax */
+  float disk_x0;               /* radiation lengths at normal incidence, >= 0 */
+  float disk_eloss;            /* GeV, >= 0 */
+  float sigma_r;               /* radial hit resolution on a disk, cm, > 0 */
+  float eta_barrel;            /* > 0 */
 } kf_detector;
 
 /* Algorithm settings (Sec. 2 and Sec. 4.3: windows, scores, duplicate cuts). */
@@ -148,7 +175,7 @@ int kf_destroy(kf_ctx* ctx);
 /* Load hits of n_events events.
  * ev_offsets: HOST array [n_events+1], CSR offsets into the hit arrays.
  * x, y, z: float [n_hits] global positions (cm); layer: int [n_hits] in
- * [0, n_layers).  A hit is referred to by its index within its event
+ * [0, n_surfaces): a barrel layer or an endcap disk (kf_detector).  A hit is referred to by its index within its event
  * (0 .. ev_offsets[e+1]-ev_offsets[e]-1), in the order given here.
  * Loading hits unloads the seeds (their hit indices refer to the previous
  * hits): call kf_load_seeds again before finding, fitting, tuning or a graph
@@ -160,7 +187,7 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
 /* Load seeds: prior state at the first seed hit and three seed hits.
  * ev_offsets: HOST array [n_events+1] (same n_events as the hits).
  * params: float [6][n_seeds]; cov: float [21][n_seeds]; seed_hits: int
- * [3][n_seeds] event-local hit indices on increasing layers. */
+ * [3][n_seeds] event-local hit indices on increasing barrel layers. */
 int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* params,
                   const float* cov, const int* seed_hits, int device_ptrs, void* stream);
 
@@ -183,9 +210,10 @@ int kf_set_alignment(kf_ctx* ctx, const float* offsets, int device_ptrs, void* s
 
 /* Bin hits, clean the seeds (with seed_clean) and run the combinatorial
  * Kalman-filter finding for every (kept) seed (Sec. 2): seed fit over the
- * three seed hits, then per layer propagation, covariance transport, chi2 of
- * every compatible hit, per-seed top-N ranking, update and multiple
- * scattering.  Asynchronous.  Errors of seed cleaning (more than 16
+ * three seed hits, then per surface of the seed's region plan (barrel
+ * layers; then the disks of its side for a forward seed) propagation,
+ * covariance transport, chi2 of every compatible hit, per-seed top-N ranking,
+ * update and multiple scattering.  Asynchronous.  Errors of seed cleaning (more than 16
  * lower-index duplicates of one seed: KF_ERR_CAPACITY) surface at the next
  * synchronizing call. */
 int kf_find_tracks(kf_ctx* ctx, void* stream);
@@ -211,12 +239,14 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
  * may be NULL) and seed parameters (g_seed float [6][n_seeds], may be NULL):
  * the adjoint of the fit, one thread per track.  Forward states are kept
  * every ckpt_stride hits and recomputed in between; ckpt_stride (1..8) must
- * satisfy hits per track <= 32 * ckpt_stride (KF_ERR_CAPACITY otherwise). */
+ * satisfy hits per track <= 32 * ckpt_stride (KF_ERR_CAPACITY otherwise).
+ * A detector with endcap disks: KF_ERR_ARG (the adjoint takes barrel hits). */
 int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs,
                    void* stream);
 
-/* Copy out the found tracks.  hits int [n_seeds][n_layers] (event-local
- * indices, -1 padded), n_found int [n_seeds], chi2 float [n_seeds], params
+/* Copy out the found tracks.  hits int [n_seeds][n_surfaces] (n_surfaces =
+ * n_layers + 2 n_disks; event-local indices in search order, -1 padded),
+ * n_found int [n_seeds], chi2 float [n_seeds], params
  * float [6][n_seeds], cov float [21][n_seeds], keep uint8 [n_seeds] (1 when
  * duplicate removal did not run).  Any pointer may be NULL. */
 int kf_get_tracks(kf_ctx* ctx, int* hits, int* n_found, float* chi2, float* params, float* cov,

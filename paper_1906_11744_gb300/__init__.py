@@ -44,11 +44,20 @@ from ._lib import (  # noqa: F401
 
 
 def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1, eloss=None,
-                  field_cz=0.0, field_cr=0.0) -> kf_detector:
+                  field_cz=0.0, field_cr=0.0, disk_z=(), disk_rmin=15.0, disk_rmax=110.0, disk_x0=0.02,
+                  disk_eloss=0.0, sigma_r=0.1, eta_barrel=0.9) -> kf_detector:
     """Detector geometry (include/kf.h, kf_detector); eloss: mean ionization
     loss per layer at normal incidence for beta -> 1 (GeV; None: none);
-    field_cz, field_cr: Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2)."""
+    field_cz, field_cr: Bz(r, z) = bz (1 + field_cz z^2 + field_cr r^2);
+    disk_z: |z| of the endcap disks of each side (empty: a barrel detector),
+    with their radii, thickness, loss, radial resolution and the |eta| from
+    which a seed searches them."""
     d = kf_detector()
+    d.n_disks = len(disk_z)
+    for i, z in enumerate(disk_z):
+        d.disk_z[i] = float(z)
+    d.disk_rmin, d.disk_rmax, d.disk_x0 = float(disk_rmin), float(disk_rmax), float(disk_x0)
+    d.disk_eloss, d.sigma_r, d.eta_barrel = float(disk_eloss), float(sigma_r), float(eta_barrel)
     d.n_layers = len(radius)
     for i, r in enumerate(radius):
         d.radius[i] = float(r)
@@ -99,6 +108,11 @@ class Tracker:
     def n_layers(self):
         return self.det.n_layers
 
+    @property
+    def n_surfaces(self):
+        """Barrel layers plus the endcap disks of both sides (a found track's hit-list row)."""
+        return self.det.n_layers + 2 * self.det.n_disks
+
     def load_hits(self, ev_offsets, x, y, z, layer, stream=None):
         kf_load_hits(self.ctx, ev_offsets, x, y, z, layer, stream)
         self.n_hits = int(np.asarray(ev_offsets)[-1])
@@ -128,7 +142,7 @@ class Tracker:
 
     def get_tracks(self, device=None, stream=None):
         """Found tracks as numpy arrays (device=None) or torch tensors on `device`."""
-        n, L = self.n_seeds, self.n_layers
+        n, L = self.n_seeds, self.n_surfaces
         out = self._alloc(device, hits=((n, L), "i4"), n_found=((n,), "i4"), chi2=((n,), "f4"),
                           params=((6, n), "f4"), cov=((21, n), "f4"), keep=((n,), "u1"))
         kf_get_tracks(self.ctx, **out, stream=stream)

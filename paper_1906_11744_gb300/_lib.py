@@ -30,6 +30,7 @@ KF_NOALLOC_MAX_TRACKS = 16384
 KF_NOALLOC_MAX_HITS = 262144
 KF_SEED_MAX_DETA = 1.0
 KF_MAX_MATERIAL_NODES = 4096
+KF_MAX_DISKS = 16
 
 
 class kf_detector(ctypes.Structure):
@@ -37,7 +38,10 @@ class kf_detector(ctypes.Structure):
                 ("x0", ctypes.c_float * KF_MAX_LAYERS), ("z_max", ctypes.c_float),
                 ("bz", ctypes.c_float), ("sigma_rphi", ctypes.c_float), ("sigma_z", ctypes.c_float),
                 ("eloss", ctypes.c_float * KF_MAX_LAYERS), ("field_cz", ctypes.c_float),
-                ("field_cr", ctypes.c_float)]
+                ("field_cr", ctypes.c_float), ("n_disks", ctypes.c_int),
+                ("disk_z", ctypes.c_float * KF_MAX_DISKS), ("disk_rmin", ctypes.c_float),
+                ("disk_rmax", ctypes.c_float), ("disk_x0", ctypes.c_float), ("disk_eloss", ctypes.c_float),
+                ("sigma_r", ctypes.c_float), ("eta_barrel", ctypes.c_float)]
 
 
 class kf_config(ctypes.Structure):

@@ -132,14 +132,17 @@ __global__ void k_check_range(const int* v, int n, int hi, int* bad) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     if (v[i] < 0 || v[i] >= hi) *bad = 1;
 }
-// Seed hit indices (three per seed, [3][n]) against their event's hit count.
-__global__ void k_check_seed_hits(const int* sh, const int* seed_event, const int* hit_off, int n, int* bad) {
+// Seed hit indices (three per seed, [3][n]) against their event's hit count;
+// the hits must lie on barrel layers (*bad = 2 otherwise).
+__global__ void k_check_seed_hits(const int* sh, const int* seed_event, const int* hit_off, const int* hlayer,
+                                  int n_layers, int n, int* bad) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const int e = seed_event[s];
     const int nh = hit_off[e + 1] - hit_off[e];
     for (int k = 0; k < 3; ++k) {
       const int h = sh[(size_t)k * n + s];
       if (h < 0 || h >= nh) *bad = 1;
+      else if (hlayer[hit_off[e] + h] >= n_layers) atomicMax(bad, 2);
     }
   }
 }
@@ -214,9 +217,23 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   }
   if (!(det->z_max > 0.f) || !(det->sigma_rphi > 0.f) || !(det->sigma_z > 0.f) || !std::isfinite(det->bz))
     return KF_ERR_ARG;
+  if (det->n_disks < 0 || det->n_disks > KF_MAX_DISKS) return KF_ERR_ARG;
+  if (det->n_disks > 0) {
+    for (int k = 0; k < det->n_disks; ++k)
+      if (!(det->disk_z[k] > 0.f) || !std::isfinite(det->disk_z[k]) ||
+          (k > 0 && !(det->disk_z[k] > det->disk_z[k - 1])))
+        return KF_ERR_ARG;
+    if (!(det->disk_rmin > 0.f) || !(det->disk_rmax > det->disk_rmin) || !std::isfinite(det->disk_rmax) ||
+        !(det->disk_x0 >= 0.f) || !std::isfinite(det->disk_x0) || !(det->disk_eloss >= 0.f) ||
+        !std::isfinite(det->disk_eloss) || !(det->sigma_r > 0.f) || !std::isfinite(det->sigma_r) ||
+        !(det->eta_barrel > 0.f) || !std::isfinite(det->eta_barrel))
+      return KF_ERR_ARG;
+  }
   {  // the field factor at the corners of the detector's (r, z) box (monotone in r^2 and z^2)
-    const double z2 = (double)det->z_max * det->z_max, r2 = (double)det->radius[det->n_layers - 1] *
-                                                            det->radius[det->n_layers - 1];
+    const double zm = det->n_disks > 0 ? std::max(det->z_max, det->disk_z[det->n_disks - 1]) : det->z_max;
+    const double rm = det->n_disks > 0 ? std::max(det->radius[det->n_layers - 1], det->disk_rmax)
+                                       : det->radius[det->n_layers - 1];
+    const double z2 = zm * zm, r2 = rm * rm;
     if (!std::isfinite(det->field_cz) || !std::isfinite(det->field_cr)) return KF_ERR_ARG;
     for (int c = 0; c < 4; ++c) {
       const double f = 1.0 + det->field_cz * ((c & 1) ? z2 : 0.0) + det->field_cr * ((c & 2) ? r2 : 0.0);
@@ -264,6 +281,19 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   g.chi2_cut = cfg->chi2_cut;
   g.phi_scale = (float)cfg->n_phi_bins / TWO_PI_F;
   g.eta_lut_scale = (float)ETA_LUT / (2.f * det->z_max);
+  g.n_disks = det->n_disks;
+  g.n_surf = det->n_layers + 2 * det->n_disks;
+  g.n_plan = det->n_layers + det->n_disks;
+  if (det->n_disks > 0) {
+    for (int k = 0; k < det->n_disks; ++k) g.disk_z[k] = det->disk_z[k];
+    g.disk_rmin = det->disk_rmin;
+    g.disk_rmax = det->disk_rmax;
+    g.disk_x0 = det->disk_x0;
+    g.disk_eloss = det->disk_eloss;
+    g.vrr = det->sigma_r * det->sigma_r;
+    g.disk_rscale = (float)cfg->n_eta_bins / (det->disk_rmax - det->disk_rmin);
+    g.eta_barrel = det->eta_barrel;
+  }
   for (int l = 0; l < det->n_layers; ++l) {
     g.radius[l] = det->radius[l];
     g.x0[l] = det->x0[l];
@@ -276,7 +306,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = find_prepare(ctx->lanes, ctx->regcap, ctx->threads, ctx->g.n_layers, ctx->g.n_eta, &ctx->blocks_per_sm);
+    e = find_prepare(ctx->lanes, ctx->regcap, ctx->threads, ctx->g, &ctx->blocks_per_sm);
   if (e == cudaSuccess) e = grow(ctx->align4, sizeof(Align4) * KF_MAX_LAYERS);
   if (e == cudaSuccess) {
     // z edges of the eta bins per layer: edge_k = R sinh(-eta_max + k * 2 eta_max / n_eta)
@@ -371,7 +401,7 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   }
   const int n = ev_offsets[n_events];
   const size_t nb = (size_t)ctx->g.n_eta * ctx->g.n_phi;
-  const size_t n_bins = (size_t)n_events * ctx->g.n_layers * nb;
+  const size_t n_bins = (size_t)n_events * ctx->g.n_surf * nb;
   if (n_bins >= 0xFFFFFFFFull) return fail(ctx, KF_ERR_CAPACITY, "kf_load_hits: too many hit-grid cells");
   cudaStream_t st = S(stream);
   CK(grow(ctx->hx, sizeof(float) * n));
@@ -385,7 +415,7 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   CK(grow(ctx->bin_cnt, sizeof(unsigned) * (n_bins + 1)));
   CK(grow(ctx->scan_tmp, sizeof(unsigned) * scan_tmp_elems(n_bins)));
   CK(grow(ctx->bin_grouped, sizeof(float4) * n));
-  CK(grow(ctx->bin_gtab, sizeof(unsigned) * bin_group_elems(n_events, ctx->g.n_layers, ctx->g.n_eta, ctx->g.n_phi)));
+  CK(grow(ctx->bin_gtab, sizeof(unsigned) * bin_group_elems(n_events, ctx->g.n_surf, ctx->g.n_eta, ctx->g.n_phi)));
   CK(grow(ctx->dd_hit_cnt, sizeof(unsigned) * ((size_t)n + n_events + 1)));
   CK(grow(ctx->dd_scan_tmp, sizeof(unsigned) * scan_tmp_elems((size_t)n + n_events)));
   CK(put(ctx->hx.p, x, sizeof(float) * n, device_ptrs, st));
@@ -406,7 +436,7 @@ int kf_load_hits(kf_ctx* ctx, int n_events, const int* ev_offsets, const float* 
   CK(cudaMemsetAsync(ctx->check.p, 0, sizeof(int), st));
   if (n > 0) {
     k_check_range<<<std::min((n + 255) / 256, 4 * ctx->num_sms), 256, 0, st>>>(ptr<int>(ctx->hlayer), n,
-                                                                               ctx->g.n_layers, ptr<int>(ctx->check));
+                                                                               ctx->g.n_surf, ptr<int>(ctx->check));
     CK(cudaGetLastError());
   }
   CK(cudaMemcpyAsync(&bad, ctx->check.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -436,7 +466,7 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
     if (ev_offsets[e + 1] < ev_offsets[e]) return fail(ctx, KF_ERR_ARG, "kf_load_seeds: decreasing ev_offsets");
   const int n = ev_offsets[n_events];
   cudaStream_t st = S(stream);
-  const int L = ctx->g.n_layers;
+  const int L = ctx->g.n_surf;  // hit-list row: one entry per surface at most
   CK(grow(ctx->sp, sizeof(float) * 6 * (size_t)n));
   CK(grow(ctx->sc, sizeof(float) * 21 * (size_t)n));
   CK(grow(ctx->sh, sizeof(int) * 3 * (size_t)n));
@@ -494,14 +524,16 @@ int kf_load_seeds(kf_ctx* ctx, int n_events, const int* ev_offsets, const float*
   CK(cudaMemsetAsync(ctx->check.p, 0, sizeof(int), st));
   if (n > 0) {
     k_check_seed_hits<<<std::min((n + 255) / 256, 4 * ctx->num_sms), 256, 0, st>>>(
-        ptr<int>(ctx->sh), ptr<int>(ctx->seed_event), ptr<int>(ctx->hit_off), n, ptr<int>(ctx->check));
+        ptr<int>(ctx->sh), ptr<int>(ctx->seed_event), ptr<int>(ctx->hit_off), ptr<int>(ctx->hlayer),
+        ctx->g.n_layers, n, ptr<int>(ctx->check));
     CK(cudaGetLastError());
   }
   CK(cudaMemcpyAsync(&bad, ctx->check.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (bad) {
     ctx->n_seed_events = -1;
-    return fail(ctx, KF_ERR_ARG, "kf_load_seeds: seed hit index out of range");
+    return fail(ctx, KF_ERR_ARG, bad == 1 ? "kf_load_seeds: seed hit index out of range"
+                                          : "kf_load_seeds: seed hits must lie on barrel layers");
   }
   ctx->n_seeds = n;
   ctx->n_seed_events = n_events;
@@ -621,7 +653,7 @@ static SeedCleanParams clean_params(kf_ctx* ctx) {
   C.seed_event = ptr<int>(ctx->seed_event);
   C.order = ptr<int>(ctx->seed_order);
   C.ns = ctx->n_seeds;
-  C.L = ctx->g.n_layers;
+  C.L = ctx->g.n_surf;
   C.deta = ctx->cfg.seed_deta;
   C.dphi = ctx->cfg.seed_dphi;
   C.dpt = ctx->cfg.seed_dpt;
@@ -680,7 +712,7 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
   if (ctx->n_hits < 0 || ctx->n_seed_events != ctx->n_events || ctx->n_events < 1)
     return fail(ctx, KF_ERR_STATE, "kf_find_tracks: load hits and seeds first");
   cudaStream_t st = S(stream);
-  const size_t cells = (size_t)ctx->g.n_layers * ctx->g.n_eta * ctx->g.n_phi;
+  const size_t cells = (size_t)ctx->g.n_surf * ctx->g.n_eta * ctx->g.n_phi;
   CK(cudaMemsetAsync(ctx->counters.p, 0, 64, st));
   CK(cudaMemsetAsync(ctx->keep.p, 1, (size_t)ctx->n_seeds, st));
   const int grid_cap = ctx->num_sms * ctx->blocks_per_sm;
@@ -740,7 +772,7 @@ int kf_remove_duplicates(kf_ctx* ctx, void* stream) {
   D.hit_off = ptr<int>(ctx->hit_off);
   D.seed_off = ptr<int>(ctx->seed_off);
   D.seed_event = ptr<int>(ctx->seed_event);
-  D.L = ctx->g.n_layers;
+  D.L = ctx->g.n_surf;
   D.ns = ctx->n_seeds;
   D.frac = ctx->cfg.dup_shared_frac;
   D.e_begin = 0;
@@ -809,7 +841,7 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
     if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_fit_tracks: no found tracks");
     F.lists = ptr<int>(ctx->out_hits);
     F.n_list = ptr<int>(ctx->out_n);
-    F.max_len = ctx->g.n_layers;
+    F.max_len = ctx->g.n_surf;
     F.keep = ctx->deduped || ctx->fit_beside_dedup ? ptr<unsigned char>(ctx->keep) : nullptr;
     F.keep_in_main = !ctx->fit_beside_dedup;
   } else if (source == KF_FIT_GIVEN) {
@@ -864,6 +896,7 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   if (!ctx) return KF_ERR_ARG;
   if (!ctx->fitted) return fail(ctx, KF_ERR_STATE, "kf_fit_adjoint: run kf_fit_tracks first");
   if (!g_align) return fail(ctx, KF_ERR_ARG, "kf_fit_adjoint: g_align is required");
+  if (ctx->g.n_disks > 0) return fail(ctx, KF_ERR_ARG, "kf_fit_adjoint: the adjoint takes barrel detectors");
   const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
   if (!adjoint_stride_ok(stride, ctx->last_fit.max_len))
     return fail(ctx, KF_ERR_CAPACITY, "kf_fit_adjoint: ckpt_stride must be 1..8 with hits per track <= 32 * stride");
@@ -950,7 +983,7 @@ int kf_get_tracks(kf_ctx* ctx, int* hits, int* n_found, float* chi2, float* para
   if (!ctx) return KF_ERR_ARG;
   if (!ctx->found) return fail(ctx, KF_ERR_STATE, "kf_get_tracks: run kf_find_tracks first");
   cudaStream_t st = S(stream);
-  const size_t n = (size_t)ctx->n_seeds, L = (size_t)ctx->g.n_layers;
+  const size_t n = (size_t)ctx->n_seeds, L = (size_t)ctx->g.n_surf;
   if (hits) CK(get(hits, ctx->out_hits.p, sizeof(int) * n * L, device_ptrs, st));
   if (n_found) CK(get(n_found, ctx->out_n.p, sizeof(int) * n, device_ptrs, st));
   if (chi2) CK(get(chi2, ctx->out_chi2.p, sizeof(float) * n, device_ptrs, st));
@@ -1025,6 +1058,8 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   if (!ctx) return KF_ERR_ARG;
   cudaStream_t st = S(stream);
   if (!st) return fail(ctx, KF_ERR_ARG, "kf_capture_graph: capture needs a non-default stream");
+  if (with_adjoint && ctx->g.n_disks > 0)
+    return fail(ctx, KF_ERR_ARG, "kf_capture_graph: the adjoint takes barrel detectors");
   if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
   if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
   if (with_adjoint) {  // every buffer the captured work uses exists before capture starts
@@ -1148,7 +1183,7 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
     for (int threads : thread_opts)
     for (int regcap = 0; regcap < 2; ++regcap) {
       int bps = 1;
-      if (find_prepare(lanes, regcap, threads, ctx->g.n_layers, ctx->g.n_eta, &bps) != cudaSuccess || bps < 1)
+      if (find_prepare(lanes, regcap, threads, ctx->g, &bps) != cudaSuccess || bps < 1)
         continue;
       for (int pers = 0; pers < 2 && rc == KF_OK; ++pers) {
         ctx->lanes = lanes;
@@ -1195,7 +1230,7 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
   ctx->persistent = best_p;
   ctx->blocks_per_sm = best_b;
   ctx->regcap = best_rc;
-  CK(find_prepare(best_l, best_rc, best_t, ctx->g.n_layers, ctx->g.n_eta, &ctx->blocks_per_sm));
+  CK(find_prepare(best_l, best_rc, best_t, ctx->g, &ctx->blocks_per_sm));
   if (n_results) *n_results = nr;
   if (rc != KF_OK) return rc;
   return KF_OK;

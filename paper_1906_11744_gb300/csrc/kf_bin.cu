@@ -1,8 +1,9 @@
-// Hit binning: counting sort of every hit into its (event, layer, eta bin,
-// phi bin) cell, so that a search window is a few contiguous ranges of the
+// Hit binning: counting sort of every hit into its (event, surface, row, phi
+// bin) cell, so that a search window is a few contiguous ranges of the
 // binned array (the GPU form of the paper's per-layer hit search windows,
-// Sec. 3).  The grid is n_eta bins in eta = asinh(z/R_layer) over
-// [-asinh(z_max/R), +asinh(z_max/R)] (as z edges per layer) times n_phi bins
+// Sec. 3).  On a barrel layer the grid is n_eta rows in eta = asinh(z/R_layer)
+// over [-asinh(z_max/R), +asinh(z_max/R)] (as z edges per layer), on an
+// endcap disk n_eta rows in r over [disk_rmin, disk_rmax]; times n_phi bins
 // in phi = atan2(y, x).
 //
 // Layer-grouped form (grids of at most 65,536 cells per layer):
@@ -35,13 +36,20 @@ __device__ __forceinline__ int event_of(const int* hit_off, int n_events, int i)
   return lo;
 }
 
-// Cell of a hit within its layer's grid.
+// Row of a hit in the grid of its surface l: the eta bin on a layer, the r
+// bin on a disk.
+__device__ __forceinline__ int row_of(const BinParams& P, int l, float x, float y, float z) {
+  const DevGeom& g = P.g;
+  if (is_disk(g, l)) return r_bin(g, disk_r(x, y));
+  return eta_bin(z, g.n_eta, g.z_max, g.eta_lut_scale, P.eta_lut + (size_t)l * ETA_LUT,
+                 P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1));
+}
+
+// Cell of a hit within its surface's grid.
 __device__ __forceinline__ int cell_of(const BinParams& P, int l, float x, float y, float z) {
   const DevGeom& g = P.g;
   const int pb = wrap_bin(phi_bin_raw(atan2f(y, x), g.phi_scale), g.n_phi);
-  const int eb = eta_bin(z, g.n_eta, g.z_max, g.eta_lut_scale, P.eta_lut + (size_t)l * ETA_LUT,
-                         P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1));
-  return eb * g.n_phi + pb;
+  return row_of(P, l, x, y, z) * g.n_phi + pb;
 }
 
 __global__ void k_bin_count(const BinParams P) {
@@ -50,8 +58,8 @@ __global__ void k_bin_count(const BinParams P) {
   const DevGeom& g = P.g;
   const int ev = event_of(P.hit_off, P.n_events, i);
   int l = P.hlayer[i];
-  l = min(max(l, 0), g.n_layers - 1);
-  const unsigned key = (unsigned)(((size_t)ev * g.n_layers + l) * ((size_t)g.n_eta * g.n_phi) +
+  l = min(max(l, 0), g.n_surf - 1);
+  const unsigned key = (unsigned)(((size_t)ev * g.n_surf + l) * ((size_t)g.n_eta * g.n_phi) +
                                   cell_of(P, l, P.hx[i], P.hy[i], P.hz[i]));
   P.key[i] = key;
   P.rank[i] = atomicAdd(&P.cnt[key], 1u);
@@ -170,16 +178,10 @@ __host__ __device__ inline Chunks chunks_of(int n_eta, int n_phi) {
   return c;
 }
 
-__device__ __forceinline__ int eta_bin_of(const BinParams& P, int l, float z) {
-  const DevGeom& g = P.g;
-  return eta_bin(z, g.n_eta, g.z_max, g.eta_lut_scale, P.eta_lut + (size_t)l * ETA_LUT,
-                 P.eta_edges + (size_t)l * (MAX_ETA_BINS + 1));
-}
-
-// Bucket of hit i of event ev within the event (layer, chunk).
+// Bucket of hit i of event ev within the event (surface, chunk).
 __device__ __forceinline__ int bucket_in_event(const BinParams& P, int i, Chunks ch) {
-  const int l = min(max(P.hlayer[i], 0), P.g.n_layers - 1);
-  return l * ch.n + eta_bin_of(P, l, P.hz[i]) / ch.rows;
+  const int l = min(max(P.hlayer[i], 0), P.g.n_surf - 1);
+  return l * ch.n + row_of(P, l, P.hx[i], P.hy[i], P.hz[i]) / ch.rows;
 }
 
 // Grid (ceil(max event hits / GROUP_HITS), events of the launch): block (c, e)
@@ -191,7 +193,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(GROUP_THREADS) k_group(const BinParams P, int e_first, int n_buckets) {
   extern __shared__ unsigned hist[];  // buckets of one event
   const Chunks ch = chunks_of(P.g.n_eta, P.g.n_phi);
-  const int nb_ev = P.g.n_layers * ch.n;
+  const int nb_ev = P.g.n_surf * ch.n;
   const int ev = e_first + blockIdx.y;
   const int h0 = P.hit_off[ev] + blockIdx.x * GROUP_HITS;
   const int h1 = min(P.hit_off[ev + 1], h0 + GROUP_HITS);
@@ -258,8 +260,8 @@ __global__ void __launch_bounds__(CELL_THREADS) k_cells(const BinParams P, int e
   const Chunks ch = chunks_of(P.g.n_eta, P.g.n_phi);
   const int b = blockIdx.x;
   const int chunk = b % ch.n;
-  const int l = (b / ch.n) % P.g.n_layers;
-  const int ev_rel = b / (ch.n * P.g.n_layers);
+  const int l = (b / ch.n) % P.g.n_surf;
+  const int ev_rel = b / (ch.n * P.g.n_surf);
   const int n_phi = P.g.n_phi;
   const int row0 = chunk * ch.rows;
   const int C = min(ch.rows, P.g.n_eta - row0) * n_phi;  // cells of the chunk
@@ -267,11 +269,11 @@ __global__ void __launch_bounds__(CELL_THREADS) k_cells(const BinParams P, int e
   const unsigned g0 = P.gtab[n_buckets + 1 + b], g1 = P.gtab[n_buckets + 2 + b];
   const int n = (int)(g1 - g0);
   const float4* hits = P.grouped + (g0 - first);
-  unsigned* off = P.cnt + ((size_t)(e_first + ev_rel) * P.g.n_layers + l) * ((size_t)P.g.n_eta * n_phi) +
+  unsigned* off = P.cnt + ((size_t)(e_first + ev_rel) * P.g.n_surf + l) * ((size_t)P.g.n_eta * n_phi) +
                   (size_t)row0 * n_phi;
   const int tid = threadIdx.x;
   auto cell = [&](const float4& h) {
-    return (eta_bin_of(P, l, h.z) - row0) * n_phi + wrap_bin(phi_bin_raw(atan2f(h.y, h.x), P.g.phi_scale), n_phi);
+    return (row_of(P, l, h.x, h.y, h.z) - row0) * n_phi + wrap_bin(phi_bin_raw(atan2f(h.y, h.x), P.g.phi_scale), n_phi);
   };
   if (n > 65535) {
     for (int c = tid; c < C; c += CELL_THREADS) off[c] = 0u;
@@ -367,10 +369,10 @@ cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsi
   const int n_hits = P.h_end - P.h_begin;
   if (P.g.n_phi <= CHUNK_CELLS && P.grouped && P.gtab) {
     const Chunks ch = chunks_of(P.g.n_eta, P.g.n_phi);
-    const size_t per_event = (size_t)P.g.n_layers * P.g.n_eta * P.g.n_phi;
+    const size_t per_event = (size_t)P.g.n_surf * P.g.n_eta * P.g.n_phi;
     const int e_first = (int)(bin_begin / per_event);
     const int n_ev = (int)(n_bins / per_event);
-    const int nb_ev = P.g.n_layers * ch.n;
+    const int nb_ev = P.g.n_surf * ch.n;
     const int nb = n_ev * nb_ev;  // buckets of the launch
     cudaError_t err = cudaMemsetAsync(P.gtab, 0, sizeof(unsigned) * (size_t)nb, st);
     if (err != cudaSuccess) return err;

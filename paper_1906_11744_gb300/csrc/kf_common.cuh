@@ -50,6 +50,16 @@ struct DevGeom {
   const float* x0map;
   int n_z;
   float z_node_inv;
+  // Endcap disks (n_disks = 0: a barrel detector): surfaces n_layers .. are
+  // the +z disks at disk_z[k], then the -z disks at -disk_z[k].
+  int n_surf;  // n_layers + 2 n_disks
+  int n_plan;  // the longest search plan: n_layers + n_disks
+  int n_disks;
+  float disk_z[KF_MAX_DISKS];
+  float disk_rmin, disk_rmax, disk_x0, disk_eloss;
+  float vrr;          // sigma_r^2
+  float disk_rscale;  // n_eta / (disk_rmax - disk_rmin): rows of a disk's hit grid, in r
+  float eta_barrel;   // seeds with |eta| >= eta_barrel search their side's disks after the barrel
 };
 
 // Per-layer alignment: (cos a, sin a) of the correction rotation a = -a_rphi/R,
@@ -508,7 +518,10 @@ __device__ __forceinline__ T x0_at(const DevGeom& g, int l, T z, T* slope = null
 // adjoint can take its derivatives in forward mode (Dir6 below).
 __device__ __forceinline__ float kval(float x) { return x; }
 __device__ __forceinline__ double kval(double x) { return x; }
-template <class T>
+// DISK: an endcap disk, whose path factor is f = 1/|cos(theta)| (normal along
+// z): d log f = tan(theta) dtheta, so u = k' (0, 0, 0, A/k, 0, (A - 1)
+// cot(theta) - B tan(theta)).
+template <class T, bool DISK = false>
 __device__ __forceinline__ void eloss_row(const T (&p)[6], T e, T& k1, T (&u)[6]) {
   T sth, cth, sph, cph;
   ksincos(p[5], &sth, &cth);
@@ -522,7 +535,7 @@ __device__ __forceinline__ void eloss_row(const T (&p)[6], T e, T& k1, T (&u)[6]
   const T p2 = pm * pm;
   const T E2 = p2 + m2;
   const T E = ksqrt(E2);
-  T dE = kdiv(e * E2, p2 * kabs(sth * cd));  // e f / beta^2
+  T dE = kdiv(e * E2, p2 * (DISK ? kabs(cth) : kabs(sth * cd)));  // e f / beta^2
   const T cap = T(0.5) * (E - T(MPION));
   if (kval(dE) > kval(cap)) dE = cap;
   // The terms near 1 and 0 are formed without cancellation (at high momentum
@@ -539,6 +552,17 @@ __device__ __forceinline__ void eloss_row(const T (&p)[6], T e, T& k1, T (&u)[6]
   const T Am1 = kdiv(dE * (kdiv(p2 + T(4) * m2, E) - dE * (T(1) + kdiv(T(2) * m2, E2))), p1sq);
   const T ApBm1 = kdiv(dE * m2 * (T(3) * E - T(2) * dE), E2 * p1sq);
   const T B = -kdiv((E - dE) * dE, p1sq);
+  if constexpr (DISK) {
+    u[0] = T(0);
+    u[1] = T(0);
+    u[2] = T(0);
+    u[3] = (T(1) + Am1) * ratio;
+    u[4] = T(0);
+    u[5] = k1 * (kdiv(cth, sth) * Am1 - B * kdiv(sth, cth));
+    (void)ApBm1;
+    (void)sd;
+    return;
+  }
   const T kbt = k1 * B * kdiv(sd, cd);
   const T ir2 = ir * ir;
   u[0] = -(kbt * p[1]) * ir2;
@@ -550,11 +574,11 @@ __device__ __forceinline__ void eloss_row(const T (&p)[6], T e, T& k1, T (&u)[6]
 }
 
 // Energy loss of a layer with loss e (GeV; 0: none) on the state (p, C).
-template <class T>
+template <class T, bool DISK = false>
 __device__ __forceinline__ void add_eloss(T (&p)[6], T (&C)[21], T e) {
   if (!(e > T(0)) || p[3] == T(0)) return;
   T k1, u[6];
-  eloss_row<T>(p, e, k1, u);
+  eloss_row<T, DISK>(p, e, k1, u);
   T cu[6];  // (F C) row 3 = u^T C
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -582,9 +606,9 @@ template <class T>
 struct State27 {
   T p[6], C[21];
 };
-template <class T>
-static __device__ __noinline__ void eloss_record(State27<T>* s, T e) { add_eloss<T>(s->p, s->C, e); }
-template <class T>
+template <class T, bool DISK>
+static __device__ __noinline__ void eloss_record(State27<T>* s, T e) { add_eloss<T, DISK>(s->p, s->C, e); }
+template <class T, bool DISK = false>
 __device__ __forceinline__ void add_eloss_ool(T (&p)[6], T (&C)[21], T e) {
   if (!(e > T(0))) return;
   State27<T> s;
@@ -592,7 +616,7 @@ __device__ __forceinline__ void add_eloss_ool(T (&p)[6], T (&C)[21], T e) {
   for (int k = 0; k < 6; ++k) s.p[k] = p[k];
 #pragma unroll
   for (int k = 0; k < 21; ++k) s.C[k] = C[k];
-  eloss_record<T>(&s, e);
+  eloss_record<T, DISK>(&s, e);
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = s.p[k];
 #pragma unroll
@@ -610,6 +634,218 @@ __device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
   const T pm = kdiv(T(1), kabs(p[3]) * sth);
   const T beta = kdiv(pm, ksqrt(kfma(pm, pm, T(MPION * MPION))));
   const T t = kdiv(x0, kabs(sth * cdiff));
+  const T th0 = kdiv(T(0.0136), beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
+  const T v = th0 * th0;
+  C[S6(4, 4)] += kdiv(v, sth * sth);
+  C[S6(5, 5)] += v;
+}
+
+// ---------------------------------------------------------------- endcap disks
+// (Sec. 2: the detector's barrel layers and endcap disks.)
+__device__ __forceinline__ bool is_disk(const DevGeom& g, int s) { return s >= g.n_layers; }
+// z of the plane of disk surface s (+z disks first, then -z).
+__device__ __forceinline__ float plane_z(const DevGeom& g, int s) {
+  const int k = s - g.n_layers;
+  return k < g.n_disks ? g.disk_z[k] : -g.disk_z[k - g.n_disks];
+}
+// Surface searched at position pos of a seed's plan: barrel layers
+// 0..n_layers-1, then disk pos - n_layers of the seed's side.
+__device__ __forceinline__ int plan_surface(const DevGeom& g, int pos, bool neg) {
+  return pos < g.n_layers ? pos : pos + (neg ? g.n_disks : 0);
+}
+// Region of a seed (Sec. 2: the event is split into eta regions): a prior
+// with |eta| >= eta_barrel (transition and endcap regions) searches its
+// side's disks after the barrel layers.  eta in double, as -log tan(theta/2).
+__device__ __forceinline__ bool seed_forward(const DevGeom& g, float theta) {
+  if (g.n_disks == 0) return false;
+  const double eta = -log(tan(0.5 * (double)theta));
+  return fabs(eta) >= (double)g.eta_barrel;
+}
+// The seed's side: eta < 0 (the -z disks).
+__device__ __forceinline__ bool seed_eta_negative(float theta) { return -log(tan(0.5 * (double)theta)) < 0.0; }
+
+// Structure of the Jacobian of the step to a plane z = z_d: rows q/pT and
+// theta unit; row z zero (z' = z_d whatever the start); x' has a unit entry
+// in x and values in (z, q/pT, phi, theta), y' likewise in y, phi' a unit
+// entry in phi and values in (z, q/pT, theta).
+__host__ __device__ constexpr int JSP(int i, int j) {
+  return (i == 3) ? (j == 3 ? 1 : 0)
+         : (i == 5) ? (j == 5 ? 1 : 0)
+         : (i == 2) ? 0
+         : (i == 0) ? (j == 0 ? 1 : (j == 1 ? 0 : 2))
+         : (i == 1) ? (j == 1 ? 1 : (j == 0 ? 0 : 2))
+         : (j == 4 ? 1 : ((j == 0 || j == 1) ? 0 : 2));
+}
+
+// Propagation to the plane z = zd (an endcap disk): transverse arc s = (zd -
+// z) tan(theta), which must be positive (the track moves towards the plane)
+// and reach the plane within half a turn (|h s| < pi); the helix in the field
+// of curvature factor kb.  J = dq/dp at that field: the partials at fixed s
+// plus (dq/ds)(ds/dp) with ds/dz = -tan(theta), ds/dtheta = (zd - z)/cos^2
+// theta = s/(sin theta cos theta) and dq/ds = (cos phi', sin phi', cot theta,
+// 0, h, 0); the z row vanishes.  Returns false (p untouched) without such a
+// crossing.
+template <class T>
+__device__ __forceinline__ bool prop_plane_jacobian(const T (&p)[6], T zd, T kb, T (&q)[6], T (&J)[6][6]) {
+  T sth, cth;
+  ksincos(p[5], &sth, &cth);
+  if (!(kabs(cth) > T(1e-12) * sth)) return false;
+  const T s = kdiv((zd - p[2]) * sth, cth);
+  if (!(s > T(0))) return false;
+  const T h = kb * p[3];
+  const T psi = h * s;
+  if (!(kabs(psi) < T(3.14159265358979323846))) return false;
+  T sf, cf;
+  ksincos(p[4], &sf, &cf);
+  T sc, cc, f1, f2;
+  helix_fns<T>(psi, sc, cc, f1, f2);
+  const T Sx = s * sc, Cx = s * cc;
+  const T dx = kfma(cf, Sx, -sf * Cx);
+  const T dy = kfma(sf, Sx, cf * Cx);
+  const T cpsi = kfma(-psi, cc, T(1)), spsi = psi * sc;
+  const T cp = kfma(cf, cpsi, -sf * spsi);
+  const T sp = kfma(sf, cpsi, cf * spsi);
+  const T s2 = s * s;
+  const T dSdh = s2 * f1, dCdh = s2 * f2;
+  const T ds2 = -kdiv(sth, cth);
+  const T ds5 = kdiv(s, sth * cth);
+  J[0][2] = cp * ds2; J[0][3] = kb * kfma(cf, dSdh, -sf * dCdh); J[0][4] = -dy; J[0][5] = cp * ds5;
+  J[1][2] = sp * ds2; J[1][3] = kb * kfma(sf, dSdh, cf * dCdh); J[1][4] = dx; J[1][5] = sp * ds5;
+  J[4][2] = h * ds2; J[4][3] = kb * s; J[4][5] = h * ds5;
+  q[0] = p[0] + dx;
+  q[1] = p[1] + dy;
+  q[2] = zd;
+  q[3] = p[3];
+  q[4] = p[4] + psi;
+  q[5] = p[5];
+  return true;
+}
+
+// C <- J C J^T for a plane step's Jacobian (structure JSP): rows 0, 1, 4 one
+// at a time as in transport; the z row and column of the result are zero.
+template <class T>
+__device__ __forceinline__ void transport_plane(const T (&J)[6][6], T (&C)[21]) {
+  constexpr int ORD[3] = {0, 1, 4};
+  T out[21];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) out[S6(2, k)] = T(0);
+  out[S6(3, 3)] = C[S6(3, 3)];
+  out[S6(3, 5)] = C[S6(3, 5)];
+  out[S6(5, 5)] = C[S6(5, 5)];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int i = ORD[a];
+    T t[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      T acc = T(0);
+      bool first = true;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (JSP(i, j) == 0) continue;
+        const T c = C[S6(j, k)];
+        if (JSP(i, j) == 1) acc = first ? c : acc + c;
+        else acc = first ? J[i][j] * c : kfma(J[i][j], c, acc);
+        first = false;
+      }
+      t[k] = acc;
+    }
+    out[S6(i, 3)] = t[3];
+    out[S6(i, 5)] = t[5];
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      const int kr = ORD[b];
+      T acc = T(0);
+      bool first = true;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        if (JSP(kr, m) == 0) continue;
+        if (JSP(kr, m) == 1) acc = first ? t[m] : acc + t[m];
+        else acc = first ? t[m] * J[kr][m] : kfma(t[m], J[kr][m], acc);
+        first = false;
+      }
+      out[S6(i, kr)] = acc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = out[k];
+}
+
+template <class T>
+__device__ __forceinline__ bool propagate_plane(T (&p)[6], T (&C)[21], T zd, T kb) {
+  T q[6], J[6][6];
+  if (!prop_plane_jacobian<T>(p, zd, kb, q, J)) return false;
+  transport_plane<T>(J, C);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = q[k];
+  return true;
+}
+
+// Measurement on a disk: (r-phi, r) at the prediction, H0 = (-su, cu, 0, ..),
+// H1 = (cu, su, 0, ..) with (cu, su) = (x, y)/r; a0 = C H0^T, a1 = C H1^T,
+// S = H C H^T + diag(vr, vrr).  The frame's f carries S^-1 (and the window's
+// S00, S11) as for a layer.
+template <class T>
+struct DiskFrameT {
+  FrameT<T> f;
+  T a1[6];
+};
+template <class T>
+__device__ __forceinline__ void make_frame_disk(const T (&p)[6], const T (&C)[21], T vr, T vrr, DiskFrameT<T>& d) {
+  FrameT<T>& f = d.f;
+  const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
+  f.cu = p[0] * ir;
+  f.su = p[1] * ir;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    f.a0[i] = kfma(-f.su, C[S6(i, 0)], f.cu * C[S6(i, 1)]);
+    d.a1[i] = kfma(f.cu, C[S6(i, 0)], f.su * C[S6(i, 1)]);
+  }
+  const T s00 = kfma(-f.su, f.a0[0], kfma(f.cu, f.a0[1], vr));
+  const T s01 = kfma(f.cu, f.a0[0], f.su * f.a0[1]);
+  const T s11 = kfma(f.cu, d.a1[0], kfma(f.su, d.a1[1], vrr));
+  const T idet = kdiv(T(1), kfma(s00, s11, -s01 * s01));
+  f.s00 = s00;
+  f.s11 = s11;
+  f.si00 = s11 * idet;
+  f.si01 = -s01 * idet;
+  f.si11 = s00 * idet;
+}
+// Residual (r-phi, r) of hit (mx, my) on a disk; false on the far half.
+template <class T>
+__device__ __forceinline__ bool residual_disk(const T (&p)[6], const FrameT<T>& f, T mx, T my, T& r0, T& r1) {
+  if (kfma(mx, p[0], my * p[1]) <= T(0)) return false;
+  const T dx = mx - p[0], dy = my - p[1];
+  r0 = kfma(-f.su, dx, f.cu * dy);
+  r1 = kfma(f.cu, dx, f.su * dy);
+  return true;
+}
+template <class T>
+__device__ __forceinline__ void kf_update_disk(T (&p)[6], T (&C)[21], const DiskFrameT<T>& d, T r0, T r1) {
+  const FrameT<T>& f = d.f;
+  T k0[6], k1[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    k0[i] = kfma(f.a0[i], f.si00, d.a1[i] * f.si01);
+    k1[i] = kfma(f.a0[i], f.si01, d.a1[i] * f.si11);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[i] = kfma(k0[i], r0, kfma(k1[i], r1, p[i]));
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i; j < 6; ++j) C[S6(i, j)] -= kfma(k0[i], f.a0[j], k1[i] * d.a1[j]);
+}
+// Scattering in a disk of x0 radiation lengths: the Highland width with the
+// path factor 1/|cos(theta)|.
+template <class T>
+__device__ __forceinline__ void add_ms_disk(const T (&p)[6], T (&C)[21], T x0) {
+  if (p[3] == T(0) || x0 <= T(0)) return;
+  T sth, cth;
+  ksincos(p[5], &sth, &cth);
+  const T pm = kdiv(T(1), kabs(p[3]) * sth);
+  const T beta = kdiv(pm, ksqrt(kfma(pm, pm, T(MPION * MPION))));
+  const T t = kdiv(x0, kabs(cth));
   const T th0 = kdiv(T(0.0136), beta * pm) * ksqrt(t) * kfma(T(0.038), klog(t), T(1));
   const T v = th0 * th0;
   C[S6(4, 4)] += kdiv(v, sth * sth);
@@ -678,6 +914,14 @@ __device__ __forceinline__ int eta_bin(float z, int n_eta, float z_max, float lu
   while (b < n_eta - 1 && z >= __ldg(edges + b + 1)) ++b;
   return b;
 }
+
+// Row of a disk hit at radius r in its disk's grid: n_eta equal steps of r
+// over [disk_rmin, disk_rmax], clamped (monotone in r, identical for hits and
+// search windows); r = sqrt(x^2 + y^2) as disk_r computes it.
+__device__ __forceinline__ int r_bin(const DevGeom& g, float r) {
+  return min(max((int)floorf((r - g.disk_rmin) * g.disk_rscale), 0), g.n_eta - 1);
+}
+__device__ __forceinline__ float disk_r(float x, float y) { return sqrtf(fmaf(x, x, y * y)); }
 
 // Square root of a non-negative x through the hardware reciprocal square
 // root (a few ulp; 0 for x <= 0): for window bounds, which are padded.

@@ -21,9 +21,28 @@ namespace {
 constexpr float CAREFUL_COS = 0.5f;
 constexpr int FIT_THREADS = 128;  // threads per block of the FP32 pass
 
+// One Kalman step on an endcap disk in scalar type T (the plane, the (r-phi, r)
+// measurement, the disk's scattering and loss).
+template <class T>
+__device__ __forceinline__ int disk_step(const DevGeom& g, T (&p)[6], T (&C)[21], bool first, bool last, int L,
+                                         float mx, float my, float& chi2) {
+  if (!first && !propagate_plane<T>(p, C, (T)plane_z(g, L), field_kb<T>(g, p))) return KF_FIT_NO_CROSS;
+  DiskFrameT<T> d;
+  make_frame_disk<T>(p, C, (T)g.vr, (T)g.vrr, d);
+  T r0, r1;
+  if (!residual_disk<T>(p, d.f, (T)mx, (T)my, r0, r1)) return KF_FIT_FAR_SIDE;
+  chi2 += (float)chi2_of<T>(d.f, r0, r1);
+  kf_update_disk<T>(p, C, d, r0, r1);
+  if (!last) {
+    add_ms_disk<T>(p, C, (T)g.disk_x0);
+    add_eloss_ool<T, true>(p, C, (T)g.disk_eloss);
+  }
+  return KF_FIT_OK;
+}
+
 // One Kalman step in scalar type T: propagate (unless first), update with the
 // corrected hit, scatter unless last.  Returns a KF_FIT_* status.
-template <class T>
+template <class T, bool DISK>
 __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float (&Cf)[21], bool first,
                                         bool last, int L, float mx, float my, float mz, float& chi2) {
   T p[6], C[21];
@@ -31,6 +50,15 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   for (int k = 0; k < 6; ++k) p[k] = (T)pf[k];
 #pragma unroll
   for (int k = 0; k < 21; ++k) C[k] = (T)Cf[k];
+  if (DISK && is_disk(g, L)) {
+    const int rc = disk_step<T>(g, p, C, first, last, L, mx, my, chi2);
+    if (rc != KF_FIT_OK) return rc;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pf[k] = (float)p[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Cf[k] = (float)C[k];
+    return KF_FIT_OK;
+  }
   if (!first && propagate<T>(p, C, (T)g.radius[L], field_kb<T>(g, p), T(INFINITY)) != 1) return KF_FIT_NO_CROSS;
   FrameT<T> f;
   make_frame<T>(p, C, (T)g.vr, (T)g.vz, f);
@@ -103,7 +131,9 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_fit_order(const FitParams P) 
 // Track at position i of the fit's order; checkpoints go to column i.
 // Returns, in the careful pass, whether a crossing of the track has
 // cos(alpha) < ADJOINT_CAREFUL_COS (its adjoint then needs double steps).
-template <bool CAREFUL>
+// DISK: the detector has endcap disks (hits on surfaces >= n_layers take the
+// plane step; they carry no alignment).
+template <bool CAREFUL, bool DISK>
 __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
   if (!CAREFUL && P.careful_flag) P.careful_flag[t] = 0;  // set below if the track is left to the careful pass
   // removed as a duplicate: zero outputs (the careful pass reads the final
@@ -147,9 +177,18 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
     }
     const int hi = hoff + lst[k];
     const int L = P.hlayer[hi];
+    const bool disk = DISK && is_disk(g, L);
     float mx, my, mz;
-    corrected_hit(P.align[L], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
-    if (!CAREFUL) {
+    if (disk) {
+      mx = P.hx[hi];
+      my = P.hy[hi];
+      mz = P.hz[hi];
+    } else {
+      corrected_hit(P.align[L], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
+    }
+    if (!CAREFUL && disk) {
+      status = disk_step<float>(g, p, C, k == 0, k + 1 == n, L, mx, my, chi2);
+    } else if (!CAREFUL) {
       if (k > 0) {
         float cosa = 1.f;
         if (propagate<float>(p, C, g.radius[L], field_kb<float>(g, p), INFINITY, &cosa) != 1) {
@@ -174,15 +213,15 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
       }
     } else {
       bool careful = false;
-      if (k > 0) {
+      if (k > 0 && !disk) {
         float zc, cosa;
         if (!crossing(p, g.radius[L], field_kb<float>(g, p), zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
         careful = cosa < CAREFUL_COS;
         adj_dbl = adj_dbl || cosa < ADJOINT_CAREFUL_COS;
       }
       if (loose && k < LOOSE_STEPS) careful = true;  // the first steps against a loose prior
-      status = careful ? fit_step<double>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
-                       : fit_step<float>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2);
+      status = careful ? fit_step<double, DISK>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
+                       : fit_step<float, DISK>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2);
     }
   }
 #pragma unroll
@@ -194,20 +233,22 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
   return adj_dbl;
 }
 
+template <bool DISK>
 __global__ void __launch_bounds__(FIT_THREADS) k_fit(const FitParams P) {
   const int i = blockIdx.x * FIT_THREADS + threadIdx.x;
-  if (i < P.ns) fit_track<false>(P, i, P.order[i]);
+  if (i < P.ns) fit_track<false, DISK>(P, i, P.order[i]);
 }
 
 // Second pass over the flagged tracks (grid-stride over their list).  A
 // track whose adjoint needs double steps gets CAREFUL_DBL_BIT in its entry
 // and is listed in dbl_list.
+template <bool DISK>
 __global__ void __launch_bounds__(128) k_fit_careful(const FitParams P) {
   const unsigned n = *P.careful_count;
   for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const unsigned v = (unsigned)P.careful_list[j];
     const int pos = (int)(v & ~CAREFUL_DBL_BIT);
-    const bool dbl = fit_track<true>(P, pos, P.order[pos]);
+    const bool dbl = fit_track<true, DISK>(P, pos, P.order[pos]);
     P.careful_list[j] = (int)(dbl ? (v | CAREFUL_DBL_BIT) : (v & ~CAREFUL_DBL_BIT));
     if (dbl) P.dbl_list[atomicAdd(P.dbl_count, 1u)] = pos;  // packed, so that few blocks hold them
   }
@@ -238,7 +279,8 @@ cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_fit_order<<<(P.ns + ORDER_WINDOW - 1) / ORDER_WINDOW, ORDER_THREADS, 0, st>>>(P);
   const int blocks = (P.ns + FIT_THREADS - 1) / FIT_THREADS;
-  k_fit<<<blocks, FIT_THREADS, 0, st>>>(P);
+  if (P.g.n_disks > 0) k_fit<true><<<blocks, FIT_THREADS, 0, st>>>(P);
+  else k_fit<false><<<blocks, FIT_THREADS, 0, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -250,7 +292,8 @@ cudaError_t launch_fit_careful(const FitParams& P, cudaStream_t st) {
   const int careful_blocks = (P.ns / 20 + threads - 1) / threads + 1;
   cudaError_t e = cudaMemsetAsync(P.dbl_count, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  k_fit_careful<<<careful_blocks, threads, 0, st>>>(P);
+  if (P.g.n_disks > 0) k_fit_careful<true><<<careful_blocks, threads, 0, st>>>(P);
+  else k_fit_careful<false><<<careful_blocks, threads, 0, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -252,7 +252,13 @@ size_t find_smem_bytes(int threads, int n_layers, int n_eta);
 bool find_lanes_supported(int lanes);
 // Sets the dynamic shared-memory limit of the kernel variant (must run
 // outside stream capture) and reports resident blocks per SM.
-cudaError_t find_prepare(int lanes, int regcap, int threads, int n_layers, int n_eta, int* blocks_per_sm);
+cudaError_t find_prepare(int lanes, int regcap, int threads, const DevGeom& g, int* blocks_per_sm);
+// The disk variants (kf_find_disk.cu), called by the entry points above for a
+// detector with endcap disks.
+cudaError_t find_prepare_disk(int lanes, int regcap, int threads, const DevGeom& g, int* blocks_per_sm);
+cudaError_t launch_find_main_disk(const FindParams& P, int lanes, int regcap, int threads, int grid_cap,
+                                  cudaStream_t st);
+cudaError_t launch_find_careful_disk(const FindParams& P, int lanes, int grid, cudaStream_t st);
 // kf_bin.cu
 cudaError_t launch_bin(const BinParams& P, size_t bin_begin, size_t n_bins, unsigned first_pos, int max_event_hits,
                        unsigned* scan_tmp, size_t scan_tmp_elems, cudaStream_t st);

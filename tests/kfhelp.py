@@ -18,8 +18,10 @@ def tracker_for(batch, device=None, **cfg):
     from paper_1906_11744_gb300 import Tracker, make_config, make_detector
 
     d = batch.det
+    disks = dict(disk_z=tuple(d.disk_z), disk_rmin=d.disk_rmin, disk_rmax=d.disk_rmax, disk_x0=d.disk_x0,
+                 disk_eloss=d.disk_eloss, sigma_r=d.sigma_r, eta_barrel=d.eta_barrel) if getattr(d, "disk_z", ()) else {}
     det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None),
-                        field_cz=getattr(d, "field_cz", 0.0), field_cr=getattr(d, "field_cr", 0.0))
+                        field_cz=getattr(d, "field_cz", 0.0), field_cr=getattr(d, "field_cr", 0.0), **disks)
     c = dict(max_cands=batch.cfg["max_cands"])
     c.update(cfg)
     t = Tracker(det, make_config(**c))
