@@ -113,8 +113,7 @@ typedef struct {
    * along such a plan a surface that a candidate does not cross within its
    * bounds is passed (no hole, the candidate goes on).  Other seeds search
    * the barrel layers only, as without disks.  Seed hits lie on barrel
-   * layers.  n_disks = 0: a barrel detector (the fields below are unused).
-   * The adjoint (kf_fit_adjoint) takes barrel hits only. */
+   * layers.  n_disks = 0: a barrel detector (the fields below are unused). */
   int n_disks;  /* 0..KF_MAX_DISKS */
   float disk_z[KF_MAX_DISKS];
   float disk_rmin, disk_rmax;  /* cm, 0 < disk_rmin < disk_rmax */
@@ -240,7 +239,8 @@ int kf_fit_tracks(kf_ctx* ctx, int source, const int* hit_lists, const int* n_hi
  * the adjoint of the fit, one thread per track.  Forward states are kept
  * every ckpt_stride hits and recomputed in between; ckpt_stride (1..8) must
  * satisfy hits per track <= 32 * ckpt_stride (KF_ERR_CAPACITY otherwise).
- * A detector with endcap disks: KF_ERR_ARG (the adjoint takes barrel hits). */
+ * Disk hits contribute to g_hits (their x and y; z is 0) and not to g_align
+ * (disks carry no alignment). */
 int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, int device_ptrs,
                    void* stream);
 

@@ -27,12 +27,13 @@
 // respect to the raw position (x, y, z) of the hit; each reverse step adds
 // its hit's share to its layer's sums (per block in shared memory, then in
 // double precision across blocks).
-// The tracks of the fit's careful list (a crossing with cos(alpha) < 0.5, or
-// a loose prior) are reversed by separate passes, which can run beside the
-// FP32 pass after the fit's own careful pass: those with a crossing below
-// cos(alpha) = 0.2 keep their adjoints in double and run such steps in
-// double; the others run the FP32 code.  The rest are reversed in FP32 from
-// the checkpoints.
+// The tracks of the fit's careful list (a crossing with cos(alpha) < 0.5, a
+// plane step along more than half a radian, or a loose prior) are reversed
+// by separate passes, which can run beside the FP32 pass after the fit's own
+// careful pass: those with a crossing below cos(alpha) = 0.2 or such a plane
+// step keep their adjoints in double and run those steps in double; the
+// others run the FP32 code.  The rest are reversed in FP32 from the
+// checkpoints.
 #include <type_traits>
 
 #include "kf_common.cuh"
@@ -130,6 +131,18 @@ __device__ __forceinline__ void ksincos(const Dir6<S>& a, Dir6<S>* s, Dir6<S>* c
 }
 template <class S>
 __device__ __forceinline__ S kval(const Dir6<S>& a) { return a.v; }
+template <class S>
+__device__ __forceinline__ void ksincos_acc(const Dir6<S>& a, Dir6<S>* s, Dir6<S>* c) {
+  S sv, cv;
+  ksincos_acc(a.v, &sv, &cv);
+  *s = Dir6<S>(sv);
+  *c = Dir6<S>(cv);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    s->d[k] = cv * a.d[k];
+    c->d[k] = -sv * a.d[k];
+  }
+}
 
 
 namespace {
@@ -173,8 +186,8 @@ template <class T>
 __device__ __forceinline__ void jac_vjp(const T (&p)[6], T s, T kb, const T (&Jb)[6][6], T (&v)[6]) {
   const T x = p[0], y = p[1], h = kb * p[3];
   T sf, cf, sth, cth;
-  ksincos(p[4], &sf, &cf);
-  ksincos(p[5], &sth, &cth);
+  ksincos_acc(p[4], &sf, &cf);
+  ksincos_acc(p[5], &sth, &cth);
   const T ist = T(1) / sth;
   const T cot = cth * ist;
   const T psi = h * s;
@@ -258,8 +271,8 @@ template <class T>
 __device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T dx0dz, T b44, T b55, T (&v)[6]) {
   if (p[3] == T(0) || x0 <= T(0)) return;
   T sth, cth, sph, cph;
-  ksincos(p[5], &sth, &cth);
-  ksincos(p[4], &sph, &cph);
+  ksincos_acc(p[5], &sth, &cth);
+  ksincos_acc(p[4], &sph, &cph);
   const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
   const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;   // cos(phi - phi_p)
   const T sdiff = kfma(sph, p[0], -cph * p[1]) * ir;  // sin(phi - phi_p)
@@ -284,6 +297,100 @@ __device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T dx0dz, T b44, T 
   v[2] = kfma(W * bt, dx0dz / x0, v[2]);
 }
 
+// v += sum_il Jb_il dJ_il/dp for the Jacobian of the plane step
+// (prop_plane_jacobian, to z = zd): rows x, y, phi over columns z and theta
+// are (cos phi', sin phi', h) (ds/dz, ds/dtheta) with ds/dz = -tan(theta),
+// ds/dtheta = s/(sin theta cos theta); column q/pT is kb R(phi) (dS/dh,
+// dC/dh) and kb s; column phi is (-dy, dx).  s = (zd - z) tan(theta) depends
+// on z and theta only.  Reverse sweep in the opposite order of the forward
+// computation.
+template <class T>
+__device__ __forceinline__ void jac_vjp_plane(const T (&p)[6], T zd, T kb, const T (&Jb)[6][6], T (&v)[6]) {
+  T sf, cf, sth, cth;
+  ksincos_acc(p[4], &sf, &cf);
+  ksincos_polar(p[5], &sth, &cth);
+  const T tn = sth / cth;
+  const T dzp = zd - p[2];
+  const T s = dzp * tn;
+  const T h = kb * p[3];
+  const T psi = h * s;
+  T sc, cc, f1, f2, df1, df2;
+  helix_fns<T>(psi, sc, cc, f1, f2);
+  helix_dfns<T>(psi, f1, f2, df1, df2);
+  const T Sx = s * sc, Cx = s * cc;
+  const T cpsi = kfma(-psi, cc, T(1)), spsi = psi * sc;
+  const T cp = kfma(cf, cpsi, -sf * spsi), sp = kfma(sf, cpsi, cf * spsi);
+  const T s2 = s * s, dSdh = s2 * f1, dCdh = s2 * f2;
+  const T isc = T(1) / (sth * cth);
+  const T ds2 = -tn, ds5 = s * isc;
+  T cpb = kfma(Jb[0][2], ds2, Jb[0][5] * ds5);
+  T spb = kfma(Jb[1][2], ds2, Jb[1][5] * ds5);
+  T hb = kfma(Jb[4][2], ds2, Jb[4][5] * ds5);
+  const T ds2b = kfma(Jb[0][2], cp, kfma(Jb[1][2], sp, Jb[4][2] * h));
+  const T ds5b = kfma(Jb[0][5], cp, kfma(Jb[1][5], sp, Jb[4][5] * h));
+  const T dSdhb = kb * kfma(Jb[0][3], cf, Jb[1][3] * sf);
+  const T dCdhb = kb * kfma(-Jb[0][3], sf, Jb[1][3] * cf);
+  T cfb = kb * kfma(Jb[0][3], dSdh, Jb[1][3] * dCdh);
+  T sfb = kb * kfma(-Jb[0][3], dCdh, Jb[1][3] * dSdh);
+  T sb = Jb[4][3] * kb;
+  const T dxb = Jb[1][4], dyb = -Jb[0][4];
+  // ds5 = s / (sin cos), ds2 = -sin / cos
+  sb = kfma(ds5b, isc, sb);
+  T sthb = -(ds5b * ds5 / sth) - ds2b / cth;
+  T cthb = -(ds5b * ds5 / cth) + ds2b * tn / cth;
+  // dS/dh = s^2 f1, dC/dh = s^2 f2
+  sb = kfma(T(2) * s, kfma(dSdhb, f1, dCdhb * f2), sb);
+  const T f1b = dSdhb * s2, f2b = dCdhb * s2;
+  // (cp, sp) = R(phi) (cos psi, sin psi)
+  cfb = kfma(cpb, cpsi, kfma(spb, spsi, cfb));
+  sfb = kfma(-cpb, spsi, kfma(spb, cpsi, sfb));
+  const T cpsib = kfma(cpb, cf, spb * sf), spsib = kfma(-cpb, sf, spb * cf);
+  T psib = kfma(-cpsib, cc, spsib * sc);
+  T ccb = -cpsib * psi, scb = spsib * psi;
+  // (dx, dy) = R(phi) (S, C) with S = s sinc, C = s cosc
+  cfb = kfma(dxb, Sx, kfma(dyb, Cx, cfb));
+  sfb = kfma(-dxb, Cx, kfma(dyb, Sx, sfb));
+  const T Sxb = kfma(dxb, cf, dyb * sf), Cxb = kfma(-dxb, sf, dyb * cf);
+  sb = kfma(Sxb, sc, kfma(Cxb, cc, sb));
+  scb = kfma(Sxb, s, scb);
+  ccb = kfma(Cxb, s, ccb);
+  psib = kfma(scb, f1, kfma(ccb, f2, kfma(f1b, df1, kfma(f2b, df2, psib))));
+  hb = kfma(psib, s, hb);
+  sb = kfma(psib, h, sb);
+  // s = (zd - z) tan(theta), tan = sin / cos
+  const T tnb = sb * dzp;
+  sthb = kfma(tnb, T(1) / cth, sthb);
+  cthb = kfma(-tnb, tn / cth, cthb);
+  v[2] -= sb * tn;
+  v[3] = kfma(kb, hb, v[3]);
+  v[4] += kfma(sfb, cf, -cfb * sf);
+  v[5] += kfma(sthb, cth, -cthb * sth);
+}
+
+// v += b44 dq44/dp + b55 dq55/dp for the scattering of a disk (add_ms_disk):
+// as ms_vjp with t = x0/|cos(theta)|, so that d log t = tan(theta) dtheta and
+// the variances depend on q/pT and theta only.
+template <class T>
+__device__ __forceinline__ void ms_vjp_disk(const T (&p)[6], T x0, T b44, T b55, T (&v)[6]) {
+  if (p[3] == T(0) || x0 <= T(0)) return;
+  T sth, cth;
+  ksincos_polar(p[5], &sth, &cth);
+  const T pm = T(1) / (kabs(p[3]) * sth);
+  const T e2 = kfma(pm, pm, T(MPION * MPION));
+  const T beta = pm / ksqrt(e2);
+  const T t = x0 / kabs(cth);
+  const T lt = klog(t);
+  const T th0 = T(0.0136) / (beta * pm) * ksqrt(t) * kfma(T(0.038), lt, T(1));
+  const T q55 = th0 * th0;
+  const T q44 = q55 / (sth * sth);
+  const T W = T(2) * kfma(b55, q55, b44 * q44);
+  const T a = pm * pm / e2 - T(2);
+  const T bt = T(0.5) + T(0.038) / kfma(T(0.038), lt, T(1));
+  const T cot = cth / sth;
+  v[3] += -W * a / p[3];
+  v[5] += kfma(W, kfma(bt, sth / cth, -a * cot), T(-2) * b44 * q44 * cot);
+}
+
 // Reverse of add_eloss, out of line and through a record in local memory, so
 // that the reverse step keeps its registers for the path without loss.  In:
 // the step's prediction (p = the updated state, Cp the predicted covariance,
@@ -301,7 +408,7 @@ struct ElossRev {
   S p[6], Cp[21], U[6][2], si00, si01, si11, x0, e;
   S pb[6], Cb[21];
 };
-template <class S>
+template <class S, bool DISK = false>
 __device__ __noinline__ void eloss_vjp(ElossRev<S>* io) {
   S C[21];
   for (int i = 0; i < 6; ++i) {
@@ -311,14 +418,15 @@ __device__ __noinline__ void eloss_vjp(ElossRev<S>* io) {
   }
   S p[6];
   for (int k = 0; k < 6; ++k) p[k] = io->p[k];
-  add_ms<S>(p, C, io->x0);
+  if (DISK) add_ms_disk<S>(p, C, io->x0);
+  else add_ms<S, true>(p, C, io->x0);
   Dir6<S> pd[6];
   for (int k = 0; k < 6; ++k) {
     pd[k] = Dir6<S>(p[k]);
     pd[k].d[k] = S(1);
   }
   Dir6<S> k1, u[6];
-  eloss_row<Dir6<S>>(pd, Dir6<S>(io->e), k1, u);
+  eloss_row<Dir6<S>, DISK, true>(pd, Dir6<S>(io->e), k1, u);
   S uv[6], Cu[6], ub[6], pn[6];
   for (int j = 0; j < 6; ++j) uv[j] = u[j].v;
   for (int j = 0; j < 6; ++j) {
@@ -358,6 +466,15 @@ template <class S>
 __device__ __forceinline__ Hit<S> load_hit(const AdjParams& P, int hi) {
   Hit<S> h;
   h.L = P.hlayer[hi];
+  if (is_disk(P.g, h.L)) {  // an endcap disk: the raw position, no alignment
+    h.ca = S(1);
+    h.sa = S(0);
+    h.R = S(0);
+    h.mx = (S)P.hx[hi];
+    h.my = (S)P.hy[hi];
+    h.mz = (S)P.hz[hi];
+    return h;
+  }
   const Align4 a = P.align[h.L];
   const S x = (S)P.hx[hi], y = (S)P.hy[hi], z = (S)P.hz[hi];
   h.ca = (S)a.ca;
@@ -373,12 +490,25 @@ __device__ __forceinline__ Hit<S> load_hit(const AdjParams& P, int hi) {
 // for float, when the crossing is near-tangent (the track then goes to the
 // double-precision pass).
 // EL: the detector has energy loss (kernels without it carry none of its code).
-template <class S, bool EL>
+template <class S, bool EL, bool DISK = false>
 __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21], const Hit<S>& h, bool first,
                                         bool last) {
+  if (DISK && is_disk(g, h.L)) {  // the plane step and the (r-phi, r) measurement
+    if (!first && !propagate_plane<S, true>(p, C, (S)plane_z(g, h.L), field_kb<S>(g, p))) return KF_FIT_NO_CROSS;
+    DiskFrameT<S> d;
+    make_frame_disk<S>(p, C, (S)g.vr, (S)g.vrr, d);
+    S r0, r1;
+    if (!residual_disk<S>(p, d.f, h.mx, h.my, r0, r1)) return KF_FIT_FAR_SIDE;
+    kf_update_disk<S>(p, C, d, r0, r1);
+    if (!last) {
+      add_ms_disk<S>(p, C, (S)g.disk_x0);
+      add_eloss_ool<S, true, true>(p, C, (S)g.disk_eloss);
+    }
+    return KF_FIT_OK;
+  }
   if (!first) {
     S cosa = S(1);
-    if (propagate<S>(p, C, h.R, field_kb<S>(g, p), S(INFINITY), &cosa) != 1) return KF_FIT_NO_CROSS;
+    if (propagate<S, true>(p, C, h.R, field_kb<S>(g, p), S(INFINITY), &cosa) != 1) return KF_FIT_NO_CROSS;
     if (sizeof(S) == 4 && cosa < S(ADJ_CAREFUL_COS)) return 99;
   }
   FrameT<S> f;
@@ -387,27 +517,242 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
   if (!residual<S>(p, f, h.mx, h.my, h.mz, r0, r1)) return KF_FIT_FAR_SIDE;
   kf_update<S>(p, C, f, r0, r1);
   if (!last) {
-    add_ms<S>(p, C, x0_at<S>(g, h.L, p[2]));
-    if constexpr (EL) add_eloss_ool<S>(p, C, (S)g.eloss[h.L]);
+    add_ms<S, true>(p, C, x0_at<S>(g, h.L, p[2]));
+    if constexpr (EL) add_eloss_ool<S, false, true>(p, C, (S)g.eloss[h.L]);
   }
   return KF_FIT_OK;
+}
+
+// Reverse of one step onto an endcap disk (as rev_step below, out of line):
+// the plane step (jac_vjp_plane), the measurement H = ((-su, cu, 0..), (cu,
+// su, 0..)) whose rows and residual r = H (m - q) turn with the position
+// angle phi_p of the prediction (dH0/dphi_p = -H1, dH1/dphi_p = H0, dr0/dphi_p
+// = -r1, dr1/dphi_p = r0, dphi_p = (x dy - y dx)/rho^2), the disk's
+// scattering and energy loss.  The hit gradient is with respect to its raw
+// position (disks carry no alignment); its z component is zero.
+template <class S, bool EL>
+__device__ __noinline__ void rev_step_disk(const DevGeom& g, const S (&p_in)[6], const S (&C_in)[21],
+                                           const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
+                                           S (&hb)[3]) {
+  // ---- forward recompute of the step
+  S q[6], J[6][6], Cp[21];
+  const S kb = field_kb<S>(g, p_in);
+  const S zd = (S)plane_z(g, h.L);
+  for (int k = 0; k < 21; ++k) Cp[k] = C_in[k];
+  if (!first) {
+    prop_plane_jacobian<S, true>(p_in, zd, kb, q, J);
+    transport_plane<S>(J, Cp);
+  } else {
+    for (int k = 0; k < 6; ++k) q[k] = p_in[k];
+  }
+  const S rho2 = kfma(q[0], q[0], q[1] * q[1]);
+  const S irho = krsqrt(rho2);
+  const S cu = q[0] * irho, su = q[1] * irho;
+  S U[6][2];
+  for (int i = 0; i < 6; ++i) {
+    U[i][0] = kfma(-su, Cp[S6(i, 0)], cu * Cp[S6(i, 1)]);
+    U[i][1] = kfma(cu, Cp[S6(i, 0)], su * Cp[S6(i, 1)]);
+  }
+  const S s00 = kfma(-su, U[0][0], kfma(cu, U[1][0], (S)g.vr));
+  const S s01 = kfma(-su, U[0][1], cu * U[1][1]);
+  const S s11 = kfma(cu, U[0][1], kfma(su, U[1][1], (S)g.vrr));
+  const S idet = S(1) / kfma(s00, s11, -s01 * s01);
+  const S si00 = s11 * idet, si01 = -s01 * idet, si11 = s00 * idet;
+  const S dx = h.mx - q[0], dy = h.my - q[1];
+  const S r0 = kfma(-su, dx, cu * dy);
+  const S r1 = kfma(cu, dx, su * dy);
+  const S sir0 = kfma(si00, r0, si01 * r1), sir1 = kfma(si01, r0, si11 * r1);
+  S pu[6];
+  for (int i = 0; i < 6; ++i) pu[i] = q[i] + kfma(U[i][0], sir0, U[i][1] * sir1);
+
+  // ---- reverse: energy loss and scattering
+  S pbu[6];
+  for (int i = 0; i < 6; ++i) pbu[i] = pb[i];
+  if (!last) {
+    const S e = (S)g.disk_eloss;
+    if (EL && e > S(0) && pu[3] != S(0)) {
+      ElossRev<S> io;
+      for (int i = 0; i < 6; ++i) {
+        io.p[i] = pu[i];
+        io.pb[i] = pbu[i];
+        io.U[i][0] = U[i][0];
+        io.U[i][1] = U[i][1];
+      }
+      for (int k = 0; k < 21; ++k) io.Cp[k] = Cp[k];
+      for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) io.Cb[S6(i, j)] = Cb[i][j];
+      io.si00 = si00;
+      io.si01 = si01;
+      io.si11 = si11;
+      io.x0 = (S)g.disk_x0;
+      io.e = e;
+      eloss_vjp<S, true>(&io);
+      for (int i = 0; i < 6; ++i) pbu[i] = io.pb[i];
+      for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) Cb[i][j] = Cb[j][i] = io.Cb[S6(i, j)];
+    }
+    ms_vjp_disk<S>(pu, (S)g.disk_x0, Cb[4][4], Cb[5][5], pbu);
+  }
+  // ---- reverse: update and chi2 (chi2 adjoint 1); the algebra of rev_step
+  S w0 = S(0), w1 = S(0);
+  for (int i = 0; i < 6; ++i) {
+    w0 = kfma(U[i][0], pbu[i], w0);
+    w1 = kfma(U[i][1], pbu[i], w1);
+  }
+  const S rb0 = kfma(si00, w0, si01 * w1) + S(2) * sir0;
+  const S rb1 = kfma(si01, w0, si11 * w1) + S(2) * sir1;
+  S CbU[6][2];
+  for (int i = 0; i < 6; ++i) {
+    S a0 = S(0), a1 = S(0);
+    for (int j = 0; j < 6; ++j) {
+      a0 = kfma(Cb[i][j], U[j][0], a0);
+      a1 = kfma(Cb[i][j], U[j][1], a1);
+    }
+    CbU[i][0] = a0;
+    CbU[i][1] = a1;
+  }
+  S UCU00 = S(0), UCU01 = S(0), UCU10 = S(0), UCU11 = S(0);
+  for (int i = 0; i < 6; ++i) {
+    UCU00 = kfma(U[i][0], CbU[i][0], UCU00);
+    UCU01 = kfma(U[i][0], CbU[i][1], UCU01);
+    UCU10 = kfma(U[i][1], CbU[i][0], UCU10);
+    UCU11 = kfma(U[i][1], CbU[i][1], UCU11);
+  }
+  const S Sib00 = w0 * r0 - UCU00 + r0 * r0, Sib01 = w0 * r1 - UCU01 + r0 * r1;
+  const S Sib10 = w1 * r0 - UCU10 + r1 * r0, Sib11 = w1 * r1 - UCU11 + r1 * r1;
+  const S t00 = kfma(si00, Sib00, si01 * Sib10), t01 = kfma(si00, Sib01, si01 * Sib11);
+  const S t10 = kfma(si01, Sib00, si11 * Sib10), t11 = kfma(si01, Sib01, si11 * Sib11);
+  const S Sb00 = -kfma(t00, si00, t01 * si01), Sb01 = -kfma(t00, si01, t01 * si11);
+  const S Sb10 = -kfma(t10, si00, t11 * si01), Sb11 = -kfma(t10, si01, t11 * si11);
+  S Ub[6][2];
+  for (int i = 0; i < 6; ++i) {
+    Ub[i][0] = pbu[i] * sir0 - S(2) * kfma(CbU[i][0], si00, CbU[i][1] * si01);
+    Ub[i][1] = pbu[i] * sir1 - S(2) * kfma(CbU[i][0], si01, CbU[i][1] * si11);
+  }
+  // + H^T Sbar (H rows (-su, cu) and (cu, su) on x, y)
+  Ub[0][0] += kfma(-su, Sb00, cu * Sb10);
+  Ub[0][1] += kfma(-su, Sb01, cu * Sb11);
+  Ub[1][0] += kfma(cu, Sb00, su * Sb10);
+  Ub[1][1] += kfma(cu, Sb01, su * Sb11);
+  // Hbar (columns x, y) = Sbar U^T + Ubar^T C_pred
+  S Hb00 = kfma(Sb00, U[0][0], Sb01 * U[0][1]);
+  S Hb01 = kfma(Sb00, U[1][0], Sb01 * U[1][1]);
+  S Hb10 = kfma(Sb10, U[0][0], Sb11 * U[0][1]);
+  S Hb11 = kfma(Sb10, U[1][0], Sb11 * U[1][1]);
+  for (int i = 0; i < 6; ++i) {
+    Hb00 = kfma(Ub[i][0], Cp[S6(i, 0)], Hb00);
+    Hb01 = kfma(Ub[i][0], Cp[S6(i, 1)], Hb01);
+    Hb10 = kfma(Ub[i][1], Cp[S6(i, 0)], Hb10);
+    Hb11 = kfma(Ub[i][1], Cp[S6(i, 1)], Hb11);
+  }
+  // Cbar_pred = Cb + sym(Ubar H)
+  S Cbp[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) Cbp[i][j] = Cb[i][j];
+  for (int i = 0; i < 6; ++i) {
+    const S v0 = S(0.5) * kfma(-su, Ub[i][0], cu * Ub[i][1]);
+    const S v1 = S(0.5) * kfma(cu, Ub[i][0], su * Ub[i][1]);
+    Cbp[i][0] += v0; Cbp[0][i] += v0;
+    Cbp[i][1] += v1; Cbp[1][i] += v1;
+  }
+  // pbar of the prediction: pass-through, the residual's direct terms, and
+  // the position angle through the residual and the rows of H
+  S pbp[6];
+  for (int i = 0; i < 6; ++i) pbp[i] = pbu[i];
+  const S phib = kfma(-rb0, r1, rb1 * r0) + kfma(-Hb00, cu, -Hb01 * su) + kfma(-Hb10, su, Hb11 * cu);
+  const S irho2 = irho * irho;
+  pbp[0] += kfma(su, rb0, -cu * rb1) - phib * q[1] * irho2;
+  pbp[1] += kfma(-cu, rb0, -su * rb1) + phib * q[0] * irho2;
+  hb[0] = kfma(-su, rb0, cu * rb1);
+  hb[1] = kfma(cu, rb0, su * rb1);
+  hb[2] = S(0);
+  // ---- reverse: the plane step
+  if (first) {
+    for (int i = 0; i < 6; ++i) pb[i] = pbp[i];
+    return;
+  }
+  S CJ[6][6];  // (J C_in)_jk
+  for (int j = 0; j < 6; ++j)
+    for (int k = 0; k < 6; ++k) {
+      S a = S(0);
+      for (int l = 0; l < 6; ++l) {
+        if (JSP(j, l) == 0) continue;
+        a = JSP(j, l) == 1 ? a + C_in[S6(l, k)] : kfma(J[j][l], C_in[S6(l, k)], a);
+      }
+      CJ[j][k] = a;
+    }
+  S pin[6];
+  for (int k = 0; k < 6; ++k) {
+    S a = S(0);
+    for (int i = 0; i < 6; ++i) {
+      if (JSP(i, k) == 0) continue;
+      a = JSP(i, k) == 1 ? a + pbp[i] : kfma(J[i][k], pbp[i], a);
+    }
+    pin[k] = a;
+  }
+  S Jb[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int l = 0; l < 6; ++l) {
+      Jb[i][l] = S(0);
+      if (JSP(i, l) != 2) continue;
+      S jb = S(0);
+      for (int j = 0; j < 6; ++j) jb = kfma(Cbp[i][j], CJ[j][l], jb);
+      Jb[i][l] = S(2) * jb;
+    }
+  jac_vjp_plane<S>(p_in, zd, kb, Jb, pin);
+  if (g.fcz != 0.f || g.fcr != 0.f) {  // the field moves with the starting point (as in rev_step)
+    S jj = S(0);
+    for (int i = 0; i < 6; ++i)
+      if (JSP(i, 3) == 2) jj = kfma(Jb[i][3], J[i][3], jj);
+    const S kbar = kdiv(kfma(p_in[3], pin[3] - pbp[3], jj), kb) * S(2) * (S)g.kb;
+    pin[0] = kfma(kbar * (S)g.fcr, p_in[0], pin[0]);
+    pin[1] = kfma(kbar * (S)g.fcr, p_in[1], pin[1]);
+    pin[2] = kfma(kbar * (S)g.fcz, p_in[2], pin[2]);
+  }
+  // Cbar_in = J^T Cbar' J
+  S T1[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int k = 0; k < 6; ++k) {
+      S a = S(0);
+      for (int j = 0; j < 6; ++j) {
+        if (JSP(j, k) == 0) continue;
+        a = JSP(j, k) == 1 ? a + Cbp[i][j] : kfma(Cbp[i][j], J[j][k], a);
+      }
+      T1[i][k] = a;
+    }
+  for (int k = 0; k < 6; ++k)
+    for (int m = k; m < 6; ++m) {
+      S a = S(0);
+      for (int i = 0; i < 6; ++i) {
+        if (JSP(i, k) == 0) continue;
+        a = JSP(i, k) == 1 ? a + T1[i][m] : kfma(J[i][k], T1[i][m], a);
+      }
+      Cb[k][m] = a;
+      Cb[m][k] = a;
+    }
+  for (int i = 0; i < 6; ++i) pb[i] = pin[i];
 }
 
 // Reverse of one step.  In: the state before the step (p_in, C_in), the
 // adjoints of the state after it (pb, Cb: Cb a full symmetric 6x6).  Out: pb,
 // Cb replaced by the adjoints of the state before it; the gradient of this
-// step with respect to the raw hit position in hb[3].
-template <class S, bool EL>
+// step with respect to the raw hit position in hb[3].  DISK: the detector has
+// endcap disks (a disk hit's step goes to rev_step_disk).
+template <class S, bool EL, bool DISK = false>
 __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], const S (&C_in)[21],
                                          const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
                                          S (&hb)[3]) {
+  if (DISK && is_disk(g, h.L)) {
+    rev_step_disk<S, EL>(g, p_in, C_in, h, first, last, pb, Cb, hb);
+    return;
+  }
   // ---- forward recompute of the step
   S q[6], J[6][6], Cp[21], s_len = S(0);
   const S kb = field_kb<S>(g, p_in);  // the field at the step's starting point
 #pragma unroll
   for (int k = 0; k < 21; ++k) Cp[k] = C_in[k];
   if (!first) {
-    prop_jacobian<S>(p_in, h.R, kb, S(INFINITY), q, J, nullptr, &s_len);
+    prop_jacobian<S, true>(p_in, h.R, kb, S(INFINITY), q, J, nullptr, &s_len);
     transport<S>(J, Cp);
   } else {
 #pragma unroll
@@ -656,19 +1001,19 @@ __device__ __forceinline__ bool near_tangent(const DevGeom& g, const float (&p)[
 
 // Forward step in precision S on float storage: the state before the step at
 // st[q * LD], q < 27; the state after it goes to st[(27 + q) * LD].
-template <class S, bool EL>
+template <class S, bool EL, bool DISK>
 __device__ __noinline__ void fwd_step_store(const DevGeom& g, float* st, const Hit<S>& h, bool first, bool last) {
   S p[6], C[21];
   for (int q = 0; q < 6; ++q) p[q] = (S)st[q * LD];
   for (int q = 0; q < 21; ++q) C[q] = (S)st[(6 + q) * LD];
-  fwd_step<S, EL>(g, p, C, h, first, last);
+  fwd_step<S, EL, DISK>(g, p, C, h, first, last);
   for (int q = 0; q < 6; ++q) st[(27 + q) * LD] = (float)p[q];
   for (int q = 0; q < 21; ++q) st[(27 + 6 + q) * LD] = (float)C[q];
 }
 
 // Reverse step in precision S with the adjoints kept in A (double in the
 // careful pass, float otherwise); the state before the step at st[q * LD].
-template <class S, class A, bool EL>
+template <class S, class A, bool EL, bool DISK>
 __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, const Hit<S>& h, bool first,
                                             bool last, A (&pbA)[6], A (&CbA)[6][6], A (&hbA)[3]) {
   S p[6], C[21], pb[6], Cb[6][6], hb[3];
@@ -678,7 +1023,7 @@ __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, c
     pb[i] = (S)pbA[i];
     for (int j = 0; j < 6; ++j) Cb[i][j] = (S)CbA[i][j];
   }
-  rev_step<S, EL>(g, p, C, h, first, last, pb, Cb, hb);
+  rev_step<S, EL, DISK>(g, p, C, h, first, last, pb, Cb, hb);
   for (int i = 0; i < 6; ++i) {
     pbA[i] = (A)pb[i];
     for (int j = 0; j < 6; ++j) CbA[i][j] = (A)Cb[i][j];
@@ -688,7 +1033,7 @@ __device__ __noinline__ void rev_step_store(const DevGeom& g, const float* st, c
 
 // Forward step of the FP32 pass, inlined (as rev_step_regs): the state
 // before it at in[q * LD], the state after it to out[q * LD].
-template <bool EL>
+template <bool EL, bool DISK>
 __device__ __forceinline__ void fwd_step_regs(const DevGeom& g, const float* in, float* out, const Hit<float>& h,
                                               bool first, bool last) {
   float p[6], C[21];
@@ -696,7 +1041,7 @@ __device__ __forceinline__ void fwd_step_regs(const DevGeom& g, const float* in,
   for (int q = 0; q < 6; ++q) p[q] = in[q * LD];
 #pragma unroll
   for (int q = 0; q < 21; ++q) C[q] = in[(6 + q) * LD];
-  fwd_step<float, EL>(g, p, C, h, first, last);
+  fwd_step<float, EL, DISK>(g, p, C, h, first, last);
 #pragma unroll
   for (int q = 0; q < 6; ++q) out[q * LD] = p[q];
 #pragma unroll
@@ -706,7 +1051,7 @@ __device__ __forceinline__ void fwd_step_regs(const DevGeom& g, const float* in,
 // The same reverse step inlined into the FP32 pass, so that the adjoints stay
 // in registers (an out-of-line call takes them by reference, through local
 // memory).
-template <bool EL>
+template <bool EL, bool DISK>
 __device__ __forceinline__ void rev_step_regs(const DevGeom& g, const float* st, const Hit<float>& h, bool first,
                                               bool last, float (&pb)[6], float (&Cb)[6][6], float (&hb)[3]) {
   float p[6], C[21];
@@ -714,7 +1059,7 @@ __device__ __forceinline__ void rev_step_regs(const DevGeom& g, const float* st,
   for (int q = 0; q < 6; ++q) p[q] = st[q * LD];
 #pragma unroll
   for (int q = 0; q < 21; ++q) C[q] = st[(6 + q) * LD];
-  rev_step<float, EL>(g, p, C, h, first, last, pb, Cb, hb);
+  rev_step<float, EL, DISK>(g, p, C, h, first, last, pb, Cb, hb);
 }
 
 // Reverse sweep of the track at position i of the fit's order, from the
@@ -723,7 +1068,7 @@ __device__ __forceinline__ void rev_step_regs(const DevGeom& g, const float* st,
 // double precision and its adjoints are kept in double.  seg: this thread's
 // column of the block's segment buffer in shared memory (states before each
 // step of a segment, [slot][27][LD]).
-template <bool CAREFUL, bool EL>
+template <bool CAREFUL, bool EL, bool DISK>
 __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
   using A = typename std::conditional<CAREFUL, double, float>::type;
   const DevGeom& g = P.g;
@@ -753,12 +1098,13 @@ __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
       if (CAREFUL && k > 0) {
         float pf[6];
         for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
-        if (near_tangent(g, pf, g.radius[P.hlayer[hi]])) {
-          fwd_step_store<double, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n);
+        const int Lh = P.hlayer[hi];
+        if (is_disk(g, Lh) ? plane_careful(g, pf, plane_z(g, Lh)) : near_tangent(g, pf, g.radius[Lh])) {
+          fwd_step_store<double, EL, DISK>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n);
           continue;
         }
       }
-      fwd_step_store<float, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
+      fwd_step_store<float, EL, DISK>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n);
     }
     for (int k = k1 - 1; k >= k0; --k) {
       const float* st = seg + (k - k0) * 27 * LD;
@@ -769,18 +1115,24 @@ __device__ void adjoint_track(const AdjParams& P, int i, float* seg) {
       if (CAREFUL && k > 0) {
         float pf[6];
         for (int q = 0; q < 6; ++q) pf[q] = st[q * LD];
-        dbl = near_tangent(g, pf, g.radius[P.hlayer[hi]]);
+        const int Lh = P.hlayer[hi];
+        dbl = is_disk(g, Lh) ? plane_careful(g, pf, plane_z(g, Lh)) : near_tangent(g, pf, g.radius[Lh]);
       }
-      if (dbl) rev_step_store<double, A, EL>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
-      else rev_step_store<float, A, EL>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      if (dbl)
+        rev_step_store<double, A, EL, DISK>(g, st, load_hit<double>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
+      else
+        rev_step_store<float, A, EL, DISK>(g, st, load_hit<float>(P, hi), k == 0, k + 1 == n, pb, Cb, hb);
       float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
       atomicAdd(gh + 0, (float)hb[0]);
       atomicAdd(gh + 1, (float)hb[1]);
       atomicAdd(gh + 2, (float)hb[2]);
-      // the layer's alignment gradient (linear in the hit gradient; few tracks)
+      // the layer's alignment gradient (linear in the hit gradient; few
+      // tracks); disks carry no alignment
       const int L = P.hlayer[hi];
-      atomicAdd(P.g_align_acc + 2 * L, -((double)P.hx[hi] * hb[1] - (double)P.hy[hi] * hb[0]) / g.radius[L]);
-      atomicAdd(P.g_align_acc + 2 * L + 1, -(double)hb[2]);
+      if (!is_disk(g, L)) {
+        atomicAdd(P.g_align_acc + 2 * L, -((double)P.hx[hi] * hb[1] - (double)P.hy[hi] * hb[0]) / g.radius[L]);
+        atomicAdd(P.g_align_acc + 2 * L + 1, -(double)hb[2]);
+      }
     }
   }
   if (P.g_seed) {
@@ -813,7 +1165,7 @@ __host__ __device__ constexpr int fp32_col_floats(int stride) { return 27 * (str
 // alignment-gradient sums (rows 2L and 2L + 1: layer L's rotation and z).
 // listed: the track comes from the fit's careful list (else careful tracks
 // are skipped: the careful passes take them).
-template <bool EL>
+template <bool EL, bool DISK>
 __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const float4* s_al, const float* s_R,
                                    float* ga, bool listed) {
   const DevGeom& g = P.g;
@@ -882,8 +1234,17 @@ __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const 
       const float* d = hs + (k - k0) * 5 * LD;
       Hit<float> h;
       h.L = __float_as_int(d[3 * LD]);
-      const float4 a = s_al[h.L];  // (cos, sin, dphi, az)
       const float x = d[0], y = d[LD], z = d[2 * LD];
+      if (DISK && is_disk(g, h.L)) {  // raw position: disks carry no alignment
+        h.ca = 1.f;
+        h.sa = 0.f;
+        h.R = 0.f;
+        h.mx = x;
+        h.my = y;
+        h.mz = z;
+        return h;
+      }
+      const float4 a = s_al[h.L];  // (cos, sin, dphi, az)
       h.ca = a.x;
       h.sa = a.y;
       h.R = s_R[h.L];
@@ -894,11 +1255,12 @@ __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const 
     };
     // state before step k: the checkpoint for k0, else seg slot k - k0 - 1
     for (int k = k0; k + 1 < k1; ++k)
-      fwd_step_regs<EL>(g, k == k0 ? ck : seg + (k - k0 - 1) * 27 * LD, seg + (k - k0) * 27 * LD, hit_of(k),
-                        k == 0, k + 1 == n);
+      fwd_step_regs<EL, DISK>(g, k == k0 ? ck : seg + (k - k0 - 1) * 27 * LD, seg + (k - k0) * 27 * LD,
+                              hit_of(k), k == 0, k + 1 == n);
     for (int k = k1 - 1; k >= k0; --k) {
       float hb[3];
-      rev_step_regs<EL>(g, k == k0 ? ck : seg + (k - k0 - 1) * 27 * LD, hit_of(k), k == 0, k + 1 == n, pb, Cb, hb);
+      rev_step_regs<EL, DISK>(g, k == k0 ? ck : seg + (k - k0 - 1) * 27 * LD, hit_of(k), k == 0, k + 1 == n, pb, Cb,
+                              hb);
       const float* hd = hs + (k - k0) * 5 * LD;
       const int hi = __float_as_int(hd[4 * LD]);
       float* gh = P.g_hits + 3 * (size_t)hi;  // a hit can be on several tracks
@@ -908,8 +1270,10 @@ __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const 
       // the layer's alignment gradient (linear in the hit gradient), summed
       // in this thread's column
       const int L = __float_as_int(hd[3 * LD]);
-      ga[2 * L * LD] -= kfma(hd[0], hb[1], -hd[LD] * hb[0]) / s_R[L];
-      ga[(2 * L + 1) * LD] -= hb[2];
+      if (!DISK || !is_disk(g, L)) {
+        ga[2 * L * LD] -= kfma(hd[0], hb[1], -hd[LD] * hb[0]) / s_R[L];
+        ga[(2 * L + 1) * LD] -= hb[2];
+      }
     }
   }
   if (P.g_seed) {
@@ -922,7 +1286,7 @@ __device__ void adjoint_track_fp32(const AdjParams& P, int i, float* col, const 
 // without CAREFUL_DBL_BIT in FP32 and those with it in double.
 enum { ADJ_ALL = 0, ADJ_LIST_FP32 = 1, ADJ_LIST_DBL = 2 };
 
-template <int MODE, bool EL>
+template <int MODE, bool EL, bool DISK = false>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
   // double pass: [stride][27][LD]; FP32 passes: columns of fp32_col_floats,
   // then 2 x layers rows of alignment-gradient sums
@@ -943,12 +1307,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
     __syncthreads();
     if constexpr (MODE == ADJ_ALL) {
       const int i = blockIdx.x * blockDim.x + threadIdx.x;
-      if (i < P.ns) adjoint_track_fp32<EL>(P, i, seg, s_al, s_R, ga, false);
+      if (i < P.ns) adjoint_track_fp32<EL, DISK>(P, i, seg, s_al, s_R, ga, false);
     } else {
       const unsigned n = *P.careful_count;
       for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const unsigned v = (unsigned)P.careful_list[j];
-        if (!(v & CAREFUL_DBL_BIT)) adjoint_track_fp32<EL>(P, (int)v, seg, s_al, s_R, ga, true);
+        if (!(v & CAREFUL_DBL_BIT)) adjoint_track_fp32<EL, DISK>(P, (int)v, seg, s_al, s_R, ga, true);
       }
     }
     __syncthreads();
@@ -960,7 +1324,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const AdjParams P) {
   } else {  // packed list: the first blocks take all of them and the others end at once
     const unsigned n = *P.dbl_count;
     for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-      adjoint_track<true, EL>(P, P.dbl_list[j], seg);
+      adjoint_track<true, EL, DISK>(P, P.dbl_list[j], seg);
   }
 }
 
@@ -982,10 +1346,12 @@ cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int smem_c = (int)(sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS);
   const int smem_f = (int)(sizeof(float) * (fp32_col_floats(P.stride) + 2 * P.g.n_layers) * (size_t)ADJ_THREADS);
-  const void* fns[6] = {(const void*)k_adjoint<ADJ_ALL, false>,       (const void*)k_adjoint<ADJ_LIST_FP32, false>,
+  const void* fns[9] = {(const void*)k_adjoint<ADJ_ALL, false>,       (const void*)k_adjoint<ADJ_LIST_FP32, false>,
                         (const void*)k_adjoint<ADJ_LIST_DBL, false>,  (const void*)k_adjoint<ADJ_ALL, true>,
-                        (const void*)k_adjoint<ADJ_LIST_FP32, true>,  (const void*)k_adjoint<ADJ_LIST_DBL, true>};
-  for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+                        (const void*)k_adjoint<ADJ_LIST_FP32, true>,  (const void*)k_adjoint<ADJ_LIST_DBL, true>,
+                        (const void*)k_adjoint<ADJ_ALL, true, true>,  (const void*)k_adjoint<ADJ_LIST_FP32, true, true>,
+                        (const void*)k_adjoint<ADJ_LIST_DBL, true, true>};
+  for (int k = 0; k < 9 && e == cudaSuccess; ++k)
     e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, k % 3 == 2 ? smem_c : smem_f);
   return e;
 }
@@ -1000,7 +1366,14 @@ cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t s
   // flagged tracks are a few percent: a grid for a twentieth of all, striding
   // over however many there are
   const int grid_careful = (P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1;
-  if (!careful) {
+  if (P.g.n_disks > 0) {  // the disk variants (with the energy-loss code, tested at run time)
+    if (!careful) {
+      k_adjoint<ADJ_ALL, true, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
+    } else {
+      k_adjoint<ADJ_LIST_DBL, true, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+      k_adjoint<ADJ_LIST_FP32, true, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
+    }
+  } else if (!careful) {
     if (el) k_adjoint<ADJ_ALL, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
     else k_adjoint<ADJ_ALL, false><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
   } else {  // the careful list: its tracks with double steps, then the others

@@ -896,7 +896,6 @@ int kf_fit_adjoint(kf_ctx* ctx, float* g_align, float* g_hits, float* g_seed, in
   if (!ctx) return KF_ERR_ARG;
   if (!ctx->fitted) return fail(ctx, KF_ERR_STATE, "kf_fit_adjoint: run kf_fit_tracks first");
   if (!g_align) return fail(ctx, KF_ERR_ARG, "kf_fit_adjoint: g_align is required");
-  if (ctx->g.n_disks > 0) return fail(ctx, KF_ERR_ARG, "kf_fit_adjoint: the adjoint takes barrel detectors");
   const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
   if (!adjoint_stride_ok(stride, ctx->last_fit.max_len))
     return fail(ctx, KF_ERR_CAPACITY, "kf_fit_adjoint: ckpt_stride must be 1..8 with hits per track <= 32 * stride");
@@ -1058,14 +1057,12 @@ int kf_capture_graph(kf_ctx* ctx, int with_adjoint, void* stream) {
   if (!ctx) return KF_ERR_ARG;
   cudaStream_t st = S(stream);
   if (!st) return fail(ctx, KF_ERR_ARG, "kf_capture_graph: capture needs a non-default stream");
-  if (with_adjoint && ctx->g.n_disks > 0)
-    return fail(ctx, KF_ERR_ARG, "kf_capture_graph: the adjoint takes barrel detectors");
   if (ctx->exec) { cudaGraphExecDestroy(ctx->exec); ctx->exec = nullptr; }
   if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
   if (with_adjoint) {  // every buffer the captured work uses exists before capture starts
     ctx->want_ckpt = true;
     const int stride = ctx->cfg.ckpt_stride > 0 ? ctx->cfg.ckpt_stride : DEFAULT_CKPT_STRIDE;
-    CK(grow(ctx->ckpt, sizeof(float) * (size_t)ckpt_slices_for(ctx->g.n_layers, stride) * 27 * (size_t)ctx->n_seeds));
+    CK(grow(ctx->ckpt, sizeof(float) * (size_t)ckpt_slices_for(ctx->g.n_surf, stride) * 27 * (size_t)ctx->n_seeds));
     CK(grow(ctx->adj_align_acc, sizeof(double) * 2 * KF_MAX_LAYERS));
     CK(grow(ctx->adj_align, sizeof(float) * 2 * KF_MAX_LAYERS));
     CK(grow(ctx->adj_hits, sizeof(float) * 3 * (size_t)ctx->n_hits));

@@ -97,6 +97,20 @@ __device__ __forceinline__ void ksincos(float x, float* s, float* c) {
   __sincosf(fmaf(-k, TWO_PI_F, x), s, c);
 }
 __device__ __forceinline__ void ksincos(double x, double* s, double* c) { sincos(x, s, c); }
+// The library's sine and cosine (a relative error of a few ulp at every
+// angle).  The hardware approximation's absolute error (about 4e-7) is a
+// large relative error where the sine or cosine is small: a direction near
+// an axis then moves a step's position across the axis by the step length
+// times 4e-7, which single precision would resolve 30 times more finely.
+// The fit and its adjoint take these (ACC); the finding, whose hit lists and
+// parameters do not see the difference, the hardware approximation.
+__device__ __forceinline__ void ksincos_acc(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void ksincos_acc(double x, double* s, double* c) { sincos(x, s, c); }
+template <bool ACC, class T>
+__device__ __forceinline__ void ksc(T x, T* s, T* c) {
+  if constexpr (ACC) ksincos_acc(x, s, c);
+  else ksincos(x, s, c);
+}
 __device__ __forceinline__ float ksqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double ksqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float krsqrt(float x) { return rsqrtf(x); }
@@ -328,17 +342,18 @@ __device__ __forceinline__ bool crossing(const float (&p)[6], float R, float kb,
 // untouched unless 1 is returned.  cos_out (optional) receives |cos| of the
 // angle between the direction and the radial direction at the crossing,
 // s_out (optional) the transverse path length.
-template <class T>
+// ACC: the library's sine and cosine (ksincos_acc).
+template <class T, bool ACC = false>
 __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim, T (&q)[6], T (&J)[6][6],
                                              T* cos_out = nullptr, T* s_out = nullptr) {
   const T x = p[0], y = p[1], kap = p[3], phi = p[4], th = p[5];
   T sf, cf;
-  ksincos(phi, &sf, &cf);
+  ksc<ACC>(phi, &sf, &cf);
   const T h = kb * kap;
   T s;
   if (!path_length<T>(x, y, h, cf, sf, R, s)) return 0;
   T sth, cth;
-  ksincos(th, &sth, &cth);
+  ksc<ACC>(th, &sth, &cth);
   const T cot = kdiv(cth, sth);
   const T zn = kfma(s, cot, p[2]);
   if (kabs(zn) > z_lim) return 2;
@@ -379,10 +394,10 @@ __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim
   return 1;
 }
 
-template <class T>
+template <class T, bool ACC = false>
 __device__ __forceinline__ int propagate(T (&p)[6], T (&C)[21], T R, T kb, T z_lim, T* cos_out = nullptr) {
   T q[6], J[6][6];
-  const int rc = prop_jacobian<T>(p, R, kb, z_lim, q, J, cos_out);
+  const int rc = prop_jacobian<T, ACC>(p, R, kb, z_lim, q, J, cos_out);
   if (rc != 1) return rc;
   transport<T>(J, C);
 #pragma unroll
@@ -456,7 +471,7 @@ __device__ __forceinline__ void kf_update(T (&p)[6], T (&C)[21], const FrameT<T>
 // Thin-scatterer multiple scattering (Highland width, pion mass for beta):
 // Var(phi) += theta0^2 / sin^2(theta), Var(theta) += theta0^2.
 // The two variance terms (phi-phi, theta-theta) the scattering adds.
-template <class T>
+template <class T, bool ACC = false>
 __device__ __forceinline__ void ms_terms(const T (&p)[6], T x0, T& q44, T& q55) {
   if (p[3] == T(0) || x0 <= T(0)) {
     q44 = T(0);
@@ -464,8 +479,8 @@ __device__ __forceinline__ void ms_terms(const T (&p)[6], T x0, T& q44, T& q55) 
     return;
   }
   T sth, cth, sph, cph;
-  ksincos(p[5], &sth, &cth);
-  ksincos(p[4], &sph, &cph);
+  ksc<ACC>(p[5], &sth, &cth);
+  ksc<ACC>(p[4], &sph, &cph);
   const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
   const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;  // cos(phi - phi_p)
   const T pm = kdiv(T(1), kabs(p[3]) * sth);
@@ -521,11 +536,11 @@ __device__ __forceinline__ double kval(double x) { return x; }
 // DISK: an endcap disk, whose path factor is f = 1/|cos(theta)| (normal along
 // z): d log f = tan(theta) dtheta, so u = k' (0, 0, 0, A/k, 0, (A - 1)
 // cot(theta) - B tan(theta)).
-template <class T, bool DISK = false>
+template <class T, bool DISK = false, bool ACC = false>
 __device__ __forceinline__ void eloss_row(const T (&p)[6], T e, T& k1, T (&u)[6]) {
   T sth, cth, sph, cph;
-  ksincos(p[5], &sth, &cth);
-  ksincos(p[4], &sph, &cph);
+  ksc<ACC>(p[5], &sth, &cth);
+  ksc<ACC>(p[4], &sph, &cph);
   const T r2 = kfma(p[0], p[0], p[1] * p[1]);
   const T ir = krsqrt(r2);
   const T cd = kfma(cph, p[0], sph * p[1]) * ir;     // cos(phi - phi_p)
@@ -574,11 +589,11 @@ __device__ __forceinline__ void eloss_row(const T (&p)[6], T e, T& k1, T (&u)[6]
 }
 
 // Energy loss of a layer with loss e (GeV; 0: none) on the state (p, C).
-template <class T, bool DISK = false>
+template <class T, bool DISK = false, bool ACC = false>
 __device__ __forceinline__ void add_eloss(T (&p)[6], T (&C)[21], T e) {
   if (!(e > T(0)) || p[3] == T(0)) return;
   T k1, u[6];
-  eloss_row<T, DISK>(p, e, k1, u);
+  eloss_row<T, DISK, ACC>(p, e, k1, u);
   T cu[6];  // (F C) row 3 = u^T C
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -606,9 +621,9 @@ template <class T>
 struct State27 {
   T p[6], C[21];
 };
-template <class T, bool DISK>
-static __device__ __noinline__ void eloss_record(State27<T>* s, T e) { add_eloss<T, DISK>(s->p, s->C, e); }
-template <class T, bool DISK = false>
+template <class T, bool DISK, bool ACC>
+static __device__ __noinline__ void eloss_record(State27<T>* s, T e) { add_eloss<T, DISK, ACC>(s->p, s->C, e); }
+template <class T, bool DISK = false, bool ACC = false>
 __device__ __forceinline__ void add_eloss_ool(T (&p)[6], T (&C)[21], T e) {
   if (!(e > T(0))) return;
   State27<T> s;
@@ -616,19 +631,19 @@ __device__ __forceinline__ void add_eloss_ool(T (&p)[6], T (&C)[21], T e) {
   for (int k = 0; k < 6; ++k) s.p[k] = p[k];
 #pragma unroll
   for (int k = 0; k < 21; ++k) s.C[k] = C[k];
-  eloss_record<T, DISK>(&s, e);
+  eloss_record<T, DISK, ACC>(&s, e);
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = s.p[k];
 #pragma unroll
   for (int k = 0; k < 21; ++k) C[k] = s.C[k];
 }
 
-template <class T>
+template <class T, bool ACC = false>
 __device__ __forceinline__ void add_ms(const T (&p)[6], T (&C)[21], T x0) {
   if (p[3] == T(0) || x0 <= T(0)) return;
   T sth, cth, sph, cph;
-  ksincos(p[5], &sth, &cth);
-  ksincos(p[4], &sph, &cph);
+  ksc<ACC>(p[5], &sth, &cth);
+  ksc<ACC>(p[4], &sph, &cph);
   const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
   const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;  // cos(phi - phi_p)
   const T pm = kdiv(T(1), kabs(p[3]) * sth);
@@ -664,6 +679,14 @@ __device__ __forceinline__ bool seed_forward(const DevGeom& g, float theta) {
 // The seed's side: eta < 0 (the -z disks).
 __device__ __forceinline__ bool seed_eta_negative(float theta) { return -log(tan(0.5 * (double)theta)) < 0.0; }
 
+// Sine and cosine of the polar angle in the disk computations: the plane
+// step's length s = (z_d - z) tan(theta) carries the relative error of
+// sin(theta), which the hardware approximation (absolute error about 4e-7)
+// makes about 2e-6 for the forward tracks that reach the disks (theta of
+// 0.1-0.4 rad); the library's sincosf keeps it at a few ulp.
+__device__ __forceinline__ void ksincos_polar(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void ksincos_polar(double x, double* s, double* c) { sincos(x, s, c); }
+
 // Structure of the Jacobian of the step to a plane z = z_d: rows q/pT and
 // theta unit; row z zero (z' = z_d whatever the start); x' has a unit entry
 // in x and values in (z, q/pT, phi, theta), y' likewise in y, phi' a unit
@@ -685,10 +708,10 @@ __host__ __device__ constexpr int JSP(int i, int j) {
 // theta = s/(sin theta cos theta) and dq/ds = (cos phi', sin phi', cot theta,
 // 0, h, 0); the z row vanishes.  Returns false (p untouched) without such a
 // crossing.
-template <class T>
+template <class T, bool ACC = false>
 __device__ __forceinline__ bool prop_plane_jacobian(const T (&p)[6], T zd, T kb, T (&q)[6], T (&J)[6][6]) {
   T sth, cth;
-  ksincos(p[5], &sth, &cth);
+  ksincos_polar(p[5], &sth, &cth);
   if (!(kabs(cth) > T(1e-12) * sth)) return false;
   const T s = kdiv((zd - p[2]) * sth, cth);
   if (!(s > T(0))) return false;
@@ -696,7 +719,7 @@ __device__ __forceinline__ bool prop_plane_jacobian(const T (&p)[6], T zd, T kb,
   const T psi = h * s;
   if (!(kabs(psi) < T(3.14159265358979323846))) return false;
   T sf, cf;
-  ksincos(p[4], &sf, &cf);
+  ksc<ACC>(p[4], &sf, &cf);
   T sc, cc, f1, f2;
   helix_fns<T>(psi, sc, cc, f1, f2);
   const T Sx = s * sc, Cx = s * cc;
@@ -771,10 +794,24 @@ __device__ __forceinline__ void transport_plane(const T (&J)[6][6], T (&C)[21]) 
   for (int k = 0; k < 21; ++k) C[k] = out[k];
 }
 
-template <class T>
+// Plane steps along more than PLANE_CAREFUL_PSI rad of the helix (loopers
+// that reach a disk after much of a half-turn): the predicted (r-phi, r)
+// variance then exceeds the hit's by 10^3-10^4, and the update C - K H C
+// cancels as many digits, which FP32 cannot spare; the fit's careful pass
+// runs such steps (and the adjoint their reverse) in double.  |psi| below
+// 0.5 rad covers 99% of the steps onto disks of the barrel-plus-endcap event.
+constexpr float PLANE_CAREFUL_PSI = 0.5f;
+__device__ __forceinline__ bool plane_careful(const DevGeom& g, const float (&p)[6], float zd) {
+  float sth, cth;
+  ksincos_polar(p[5], &sth, &cth);
+  const float psi = field_kb<float>(g, p) * p[3] * ((zd - p[2]) * sth / cth);
+  return fabsf(psi) > PLANE_CAREFUL_PSI;
+}
+
+template <class T, bool ACC = false>
 __device__ __forceinline__ bool propagate_plane(T (&p)[6], T (&C)[21], T zd, T kb) {
   T q[6], J[6][6];
-  if (!prop_plane_jacobian<T>(p, zd, kb, q, J)) return false;
+  if (!prop_plane_jacobian<T, ACC>(p, zd, kb, q, J)) return false;
   transport_plane<T>(J, C);
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = q[k];
@@ -842,7 +879,7 @@ template <class T>
 __device__ __forceinline__ void add_ms_disk(const T (&p)[6], T (&C)[21], T x0) {
   if (p[3] == T(0) || x0 <= T(0)) return;
   T sth, cth;
-  ksincos(p[5], &sth, &cth);
+  ksincos_polar(p[5], &sth, &cth);
   const T pm = kdiv(T(1), kabs(p[3]) * sth);
   const T beta = kdiv(pm, ksqrt(kfma(pm, pm, T(MPION * MPION))));
   const T t = kdiv(x0, kabs(cth));

@@ -12,6 +12,9 @@
 // crossings has cos(alpha) below CAREFUL_COS; a second pass refits only the
 // flagged tracks, running those steps' propagation and update in double
 // precision (a small fraction of tracks: loopers near their maximum radius).
+// On a detector with endcap disks, a plane step along more than half a
+// radian of the helix (a looper reaching a disk) flags its track the same
+// way (PLANE_CAREFUL_PSI).
 #include "kf_internal.h"
 
 namespace kfg {
@@ -26,7 +29,7 @@ constexpr int FIT_THREADS = 128;  // threads per block of the FP32 pass
 template <class T>
 __device__ __forceinline__ int disk_step(const DevGeom& g, T (&p)[6], T (&C)[21], bool first, bool last, int L,
                                          float mx, float my, float& chi2) {
-  if (!first && !propagate_plane<T>(p, C, (T)plane_z(g, L), field_kb<T>(g, p))) return KF_FIT_NO_CROSS;
+  if (!first && !propagate_plane<T, true>(p, C, (T)plane_z(g, L), field_kb<T>(g, p))) return KF_FIT_NO_CROSS;
   DiskFrameT<T> d;
   make_frame_disk<T>(p, C, (T)g.vr, (T)g.vrr, d);
   T r0, r1;
@@ -35,13 +38,14 @@ __device__ __forceinline__ int disk_step(const DevGeom& g, T (&p)[6], T (&C)[21]
   kf_update_disk<T>(p, C, d, r0, r1);
   if (!last) {
     add_ms_disk<T>(p, C, (T)g.disk_x0);
-    add_eloss_ool<T, true>(p, C, (T)g.disk_eloss);
+    add_eloss_ool<T, true, true>(p, C, (T)g.disk_eloss);
   }
   return KF_FIT_OK;
 }
 
 // One Kalman step in scalar type T: propagate (unless first), update with the
-// corrected hit, scatter unless last.  Returns a KF_FIT_* status.
+// corrected hit, scatter unless last.  Returns a KF_FIT_* status.  The fit
+// takes the library's sine and cosine throughout (ACC).
 template <class T, bool DISK>
 __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float (&Cf)[21], bool first,
                                         bool last, int L, float mx, float my, float mz, float& chi2) {
@@ -59,7 +63,8 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
     for (int k = 0; k < 21; ++k) Cf[k] = (float)C[k];
     return KF_FIT_OK;
   }
-  if (!first && propagate<T>(p, C, (T)g.radius[L], field_kb<T>(g, p), T(INFINITY)) != 1) return KF_FIT_NO_CROSS;
+  if (!first && propagate<T, true>(p, C, (T)g.radius[L], field_kb<T>(g, p), T(INFINITY)) != 1)
+    return KF_FIT_NO_CROSS;
   FrameT<T> f;
   make_frame<T>(p, C, (T)g.vr, (T)g.vz, f);
   T r0, r1;
@@ -67,8 +72,8 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, float (&pf)[6], float 
   chi2 += (float)chi2_of<T>(f, r0, r1);
   kf_update<T>(p, C, f, r0, r1);
   if (!last) {
-    add_ms<T>(p, C, x0_at<T>(g, L, p[2]));
-    add_eloss_ool<T>(p, C, (T)g.eloss[L]);
+    add_ms<T, true>(p, C, x0_at<T>(g, L, p[2]));
+    add_eloss_ool<T, false, true>(p, C, (T)g.eloss[L]);
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) pf[k] = (float)p[k];
@@ -187,11 +192,16 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
       corrected_hit(P.align[L], P.hx[hi], P.hy[hi], P.hz[hi], mx, my, mz);
     }
     if (!CAREFUL && disk) {
+      if (k > 0 && plane_careful(g, p, plane_z(g, L))) {  // a long arc onto the disk: the careful pass
+        P.careful_list[atomicAdd(P.careful_count, 1u)] = i;
+        if (P.careful_flag) P.careful_flag[t] = 1;
+        return false;
+      }
       status = disk_step<float>(g, p, C, k == 0, k + 1 == n, L, mx, my, chi2);
     } else if (!CAREFUL) {
       if (k > 0) {
         float cosa = 1.f;
-        if (propagate<float>(p, C, g.radius[L], field_kb<float>(g, p), INFINITY, &cosa) != 1) {
+        if (propagate<float, true>(p, C, g.radius[L], field_kb<float>(g, p), INFINITY, &cosa) != 1) {
           status = KF_FIT_NO_CROSS;
           break;
         }
@@ -208,8 +218,8 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
       chi2 += chi2_of<float>(f, r0, r1);
       kf_update<float>(p, C, f, r0, r1);
       if (k + 1 < n) {
-        add_ms<float>(p, C, x0_at<float>(g, L, p[2]));
-        add_eloss_ool<float>(p, C, g.eloss[L]);
+        add_ms<float, true>(p, C, x0_at<float>(g, L, p[2]));
+        add_eloss_ool<float, false, true>(p, C, g.eloss[L]);
       }
     } else {
       bool careful = false;
@@ -218,6 +228,9 @@ __device__ __forceinline__ bool fit_track(const FitParams& P, int i, int t) {
         if (!crossing(p, g.radius[L], field_kb<float>(g, p), zc, cosa)) { status = KF_FIT_NO_CROSS; break; }
         careful = cosa < CAREFUL_COS;
         adj_dbl = adj_dbl || cosa < ADJOINT_CAREFUL_COS;
+      } else if (k > 0) {  // a long arc onto a disk: in double here and in the adjoint
+        careful = plane_careful(g, p, plane_z(g, L));
+        adj_dbl = adj_dbl || careful;
       }
       if (loose && k < LOOSE_STEPS) careful = true;  // the first steps against a loose prior
       status = careful ? fit_step<double, DISK>(g, p, C, k == 0, k + 1 == n, L, mx, my, mz, chi2)
