@@ -200,8 +200,10 @@ FIELD_MAP = dict(field_cz=-0.10 / 120.0 ** 2, field_cr=-0.05 / 110.0 ** 2)
 def tracker_for(b, **cfg):
     from paper_1906_11744_gb300 import Tracker, make_config, make_detector
     d = b.det
+    disks = dict(disk_z=tuple(d.disk_z), disk_rmin=d.disk_rmin, disk_rmax=d.disk_rmax, disk_x0=d.disk_x0,
+                 disk_eloss=d.disk_eloss, sigma_r=d.sigma_r, eta_barrel=d.eta_barrel) if getattr(d, "disk_z", ()) else {}
     det = make_detector(d.radius, d.x0, d.z_max, d.bz, d.sigma_rphi, d.sigma_z, eloss=getattr(d, "eloss", None),
-                        field_cz=getattr(d, "field_cz", 0.0), field_cr=getattr(d, "field_cr", 0.0))
+                        field_cz=getattr(d, "field_cz", 0.0), field_cr=getattr(d, "field_cr", 0.0), **disks)
     c = dict(max_cands=b.cfg["max_cands"])
     c.update(cfg)
     return Tracker(det, make_config(**c))
@@ -372,6 +374,7 @@ def main():
     ap.add_argument("--no-dup", action="store_true", help="skip the duplicate-handling step")
     ap.add_argument("--no-material", action="store_true", help="skip the material-map step")
     ap.add_argument("--no-field", action="store_true", help="skip the parameterized-field step")
+    ap.add_argument("--no-endcap", action="store_true", help="skip the barrel-plus-endcap step (c6)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-pileup (64 events, PU 20-200) step")
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
@@ -640,6 +643,55 @@ def main():
         tf.close()
         del df
 
+    # PU-200-like barrel plus endcaps (c6: 20 events x 8,000 tracks, |eta| < 2.4, seven disks
+    # per side): finding over the region plans, duplicate removal, fit and adjoint in one graph
+    endcap = None
+    if not args.no_endcap:
+        be = make_inputs("c6", rank)
+        de = dict(x=tt(be.x), y=tt(be.y), z=tt(be.z), layer=tt(be.layer), params=tt(be.params),
+                  cov=tt(be.cov), seed_hits=tt(be.seed_hits))
+        te = tracker_for(be, persistent=1, per_event=0)
+        te.load_hits(be.hit_off, de["x"], de["y"], de["z"], de["layer"], stream)
+        te.load_seeds(be.seed_off, de["params"], de["cov"], de["seed_hits"], stream)
+        te.set_alignment(be.align, stream)
+        te.set_stage_timing(True)
+        te.capture_graph(with_adjoint=True, stream=stream)
+        for _ in range(args.warmup):
+            te.launch_graph(stream)
+        stream.synchronize()
+        ea = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        eb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        estage = {}
+        for k in range(args.steps):
+            flush_l2()
+            ea[k].record(stream)
+            te.launch_graph(stream)
+            eb[k].record(stream)
+            for key, v in te.stage_ms(stream).items():
+                estage[key] = estage.get(key, 0.0) + v
+        stream.synchronize()
+        ems = max_over_ranks(sum(a.elapsed_time(bb) for a, bb in zip(ea, eb)), dev)
+        eta0 = -np.log(np.tan(0.5 * be.params[5].astype(np.float64)))
+        trk = te.get_tracks()
+        lay_all = be.layer
+        n_disk_hits = 0
+        for e in range(be.n_events):
+            a0, a1 = be.seed_off[e], be.seed_off[e + 1]
+            h = trk["hits"][a0:a1]
+            lay_e = lay_all[be.hit_off[e]:be.hit_off[e + 1]]
+            n_disk_hits += int((lay_e[h[h >= 0]] >= be.det.n_layers).sum())
+        endcap = {"workload": "c6: %d events x 8,000 tracks, |eta| < 2.4, 17 barrel layers + 2 x 7 disks "
+                              "(|z| 130-250 cm, r 15-110 cm), 20%% noise, N=10" % be.n_events,
+                  "value": be.n_seeds * world * args.steps / (ems / 1e3), "unit": UNIT,
+                  "ms_per_step": ems / args.steps,
+                  "forward_seed_fraction": float(np.mean(np.abs(eta0) >= be.det.eta_barrel)),
+                  "found_disk_hits_per_step": n_disk_hits,
+                  "counters_per_step": te.counters(stream),
+                  "stage_ms": {k: v / args.steps for k, v in estage.items()},
+                  "gpu_launches": te.graph_kernel_count() * args.steps}
+        te.close()
+        del de
+
     # end to end through the C ABI with host buffers (pinned), host<->device copies inside.
     # Two contexts: while one step's graph runs, the next step's inputs are uploaded (and
     # checked) through the other context, and its graph starts as soon as this one ends
@@ -766,6 +818,7 @@ def main():
                "dup_handling": dup,
                "material_map": mat,
                "field_map": fld,
+               "endcap": endcap,
                "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample",
                                                                             "single_core_value", "single_core_sample")},
                "clocks": clocks.summary()}

@@ -502,7 +502,7 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
     kf_update_disk<S>(p, C, d, r0, r1);
     if (!last) {
       add_ms_disk<S>(p, C, (S)g.disk_x0);
-      add_eloss_ool<S, true, true>(p, C, (S)g.disk_eloss);
+      if constexpr (EL) add_eloss_ool<S, true, true>(p, C, (S)g.disk_eloss);
     }
     return KF_FIT_OK;
   }
@@ -531,9 +531,9 @@ __device__ __forceinline__ int fwd_step(const DevGeom& g, S (&p)[6], S (&C)[21],
 // scattering and energy loss.  The hit gradient is with respect to its raw
 // position (disks carry no alignment); its z component is zero.
 template <class S, bool EL>
-__device__ __noinline__ void rev_step_disk(const DevGeom& g, const S (&p_in)[6], const S (&C_in)[21],
-                                           const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
-                                           S (&hb)[3]) {
+__device__ __forceinline__ void rev_step_disk(const DevGeom& g, const S (&p_in)[6], const S (&C_in)[21],
+                                              const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
+                                              S (&hb)[3]) {
   // ---- forward recompute of the step
   S q[6], J[6][6], Cp[21];
   const S kb = field_kb<S>(g, p_in);
@@ -733,6 +733,18 @@ __device__ __noinline__ void rev_step_disk(const DevGeom& g, const S (&p_in)[6],
   for (int i = 0; i < 6; ++i) pb[i] = pin[i];
 }
 
+// The disk step's reverse out of line, through a record in local memory, so
+// that the caller's adjoints stay in registers on its barrel steps.
+template <class S>
+struct DiskRev {
+  S p[6], C[21], pb[6], Cb[6][6], hb[3];
+  Hit<S> h;
+};
+template <class S, bool EL>
+__device__ __noinline__ void rev_step_disk_rec(const DevGeom& g, DiskRev<S>* r, bool first, bool last) {
+  rev_step_disk<S, EL>(g, r->p, r->C, r->h, first, last, r->pb, r->Cb, r->hb);
+}
+
 // Reverse of one step.  In: the state before the step (p_in, C_in), the
 // adjoints of the state after it (pb, Cb: Cb a full symmetric 6x6).  Out: pb,
 // Cb replaced by the adjoints of the state before it; the gradient of this
@@ -743,7 +755,27 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
                                          const Hit<S>& h, bool first, bool last, S (&pb)[6], S (&Cb)[6][6],
                                          S (&hb)[3]) {
   if (DISK && is_disk(g, h.L)) {
-    rev_step_disk<S, EL>(g, p_in, C_in, h, first, last, pb, Cb, hb);
+    DiskRev<S> r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r.p[k] = p_in[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) r.C[k] = C_in[k];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      r.pb[i] = pb[i];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) r.Cb[i][j] = Cb[i][j];
+    }
+    r.h = h;
+    rev_step_disk_rec<S, EL>(g, &r, first, last);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      pb[i] = r.pb[i];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) Cb[i][j] = r.Cb[i][j];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) hb[i] = r.hb[i];
     return;
   }
   // ---- forward recompute of the step
@@ -1346,12 +1378,13 @@ cudaError_t launch_adjoint_begin(const AdjParams& P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int smem_c = (int)(sizeof(float) * 27 * (size_t)P.stride * ADJ_THREADS);
   const int smem_f = (int)(sizeof(float) * (fp32_col_floats(P.stride) + 2 * P.g.n_layers) * (size_t)ADJ_THREADS);
-  const void* fns[9] = {(const void*)k_adjoint<ADJ_ALL, false>,       (const void*)k_adjoint<ADJ_LIST_FP32, false>,
-                        (const void*)k_adjoint<ADJ_LIST_DBL, false>,  (const void*)k_adjoint<ADJ_ALL, true>,
-                        (const void*)k_adjoint<ADJ_LIST_FP32, true>,  (const void*)k_adjoint<ADJ_LIST_DBL, true>,
-                        (const void*)k_adjoint<ADJ_ALL, true, true>,  (const void*)k_adjoint<ADJ_LIST_FP32, true, true>,
-                        (const void*)k_adjoint<ADJ_LIST_DBL, true, true>};
-  for (int k = 0; k < 9 && e == cudaSuccess; ++k)
+  const void* fns[12] = {(const void*)k_adjoint<ADJ_ALL, false>,        (const void*)k_adjoint<ADJ_LIST_FP32, false>,
+                         (const void*)k_adjoint<ADJ_LIST_DBL, false>,   (const void*)k_adjoint<ADJ_ALL, true>,
+                         (const void*)k_adjoint<ADJ_LIST_FP32, true>,   (const void*)k_adjoint<ADJ_LIST_DBL, true>,
+                         (const void*)k_adjoint<ADJ_ALL, false, true>,  (const void*)k_adjoint<ADJ_LIST_FP32, false, true>,
+                         (const void*)k_adjoint<ADJ_LIST_DBL, false, true>, (const void*)k_adjoint<ADJ_ALL, true, true>,
+                         (const void*)k_adjoint<ADJ_LIST_FP32, true, true>, (const void*)k_adjoint<ADJ_LIST_DBL, true, true>};
+  for (int k = 0; k < 12 && e == cudaSuccess; ++k)
     e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, k % 3 == 2 ? smem_c : smem_f);
   return e;
 }
@@ -1366,12 +1399,16 @@ cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t s
   // flagged tracks are a few percent: a grid for a twentieth of all, striding
   // over however many there are
   const int grid_careful = (P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1;
-  if (P.g.n_disks > 0) {  // the disk variants (with the energy-loss code, tested at run time)
+  if (P.g.n_disks > 0) {  // the disk variants; energy loss on a layer or on the disks
+    if (P.g.disk_eloss > 0.f) el = true;
     if (!careful) {
-      k_adjoint<ADJ_ALL, true, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
+      if (el) k_adjoint<ADJ_ALL, true, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
+      else k_adjoint<ADJ_ALL, false, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
     } else {
-      k_adjoint<ADJ_LIST_DBL, true, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
-      k_adjoint<ADJ_LIST_FP32, true, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
+      if (el) k_adjoint<ADJ_LIST_DBL, true, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+      else k_adjoint<ADJ_LIST_DBL, false, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+      if (el) k_adjoint<ADJ_LIST_FP32, true, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
+      else k_adjoint<ADJ_LIST_FP32, false, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
     }
   } else if (!careful) {
     if (el) k_adjoint<ADJ_ALL, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);

@@ -896,6 +896,13 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         par = 0;
         p_holes = 0;
         p_cls = first_cls;
+      } else if (DISK && __any_sync(0xffffffffu, active && !in_seed) &&
+                 !__any_sync(0xffffffffu, active && !in_seed && occ && cls == 2)) {
+        // Every candidate of the warp is carried unchanged (a surface passed
+        // on a forward plan, or finished): the selection would keep each in
+        // its slot -- the slots are in key order, and a carried child's key
+        // (hits, chi2 sum, its own slot) keeps that order -- so it is skipped.
+        mine = (active && occ) ? make_key(nfound, chi2, gl, 1, 0) : KEY_EMPTY;
       } else if (__any_sync(0xffffffffu, active && !in_seed)) {
         // Rank of each child = its position in its own sorted list + the
         // number of smaller keys in the other lists of the group (keys are

@@ -132,6 +132,11 @@ CONFIGS: Dict[str, dict] = {
     "c5": dict(n_events=1, tracks=2500, n_layers=17, r_max=110.0, eta_max=2.4,
                noise=0.10, max_cands=6, seed=1005,
                disk_z=(130.0, 150.0, 170.0, 190.0, 210.0, 230.0, 250.0)),
+    # PU-200-like barrel plus endcaps: 20 events x 8,000 tracks over |eta| <
+    # 2.4, 20% noise on every surface, N = 10 (the benchmark's endcap step).
+    "c6": dict(n_events=20, tracks=8000, n_layers=17, r_max=110.0, eta_max=2.4,
+               noise=0.20, max_cands=10, seed=1006,
+               disk_z=(130.0, 150.0, 170.0, 190.0, 210.0, 230.0, 250.0)),
 }
 
 
