@@ -178,16 +178,32 @@ __device__ __forceinline__ void helix_dfns(T psi, T f1, T f2, T& df1, T& df2) {
   }
 }
 
+// Sine and cosine of a + d from those of a (sa, ca), for the small change d
+// that an update makes to an angle: sin d and cos d by their Taylor series
+// (|d| <= 0.1: truncation below 1e-9), else from the angle a + d itself.
+template <class T>
+__device__ __forceinline__ void rotate_small(T sa, T ca, T d, T angle, T& so, T& co) {
+  if (kabs(d) > T(0.1)) {
+    ksincos_acc(angle, &so, &co);
+    return;
+  }
+  const T d2 = d * d;
+  const T sd = d * kfma(d2, kfma(d2, T(1.0 / 120.0), T(-1.0 / 6.0)), T(1));
+  const T cd = kfma(d2, kfma(d2, kfma(d2, T(-1.0 / 720.0), T(1.0 / 24.0)), T(-0.5)), T(1));
+  so = kfma(sa, cd, ca * sd);
+  co = kfma(ca, cd, -(sa * sd));
+}
+
 // v += sum_il Jb_il dJ_il/dp for the propagation Jacobian J(p) of
 // prop_jacobian (to the layer it crossed at transverse path length s).  Jb
 // is read at the structural non-zeros (JS == 2) only.  Reverse sweep through
 // the Jacobian's intermediates in the opposite order of their computation.
+// trig: sin, cos of phi and of theta at the start (as prop_jacobian gives them).
 template <class T>
-__device__ __forceinline__ void jac_vjp(const T (&p)[6], T s, T kb, const T (&Jb)[6][6], T (&v)[6]) {
+__device__ __forceinline__ void jac_vjp(const T (&p)[6], T s, T kb, const T (&Jb)[6][6], T (&v)[6],
+                                        const T* trig) {
   const T x = p[0], y = p[1], h = kb * p[3];
-  T sf, cf, sth, cth;
-  ksincos_acc(p[4], &sf, &cf);
-  ksincos_acc(p[5], &sth, &cth);
+  const T sf = trig[0], cf = trig[1], sth = trig[2], cth = trig[3];
   const T ist = T(1) / sth;
   const T cot = cth * ist;
   const T psi = h * s;
@@ -267,12 +283,11 @@ __device__ __forceinline__ void jac_vjp(const T (&p)[6], T s, T kb, const T (&Jb
 // phi_p the position angle; dq55 = 2 q55 dL, dq44 = q44 (2 dL - 2 dsin/sin).
 // The thickness x0 may depend on z (material map): dlog t gains
 // (dx0/dz)/x0 dz.
+// sth, cth, sph, cph: sin, cos of theta and phi of p.
 template <class T>
-__device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T dx0dz, T b44, T b55, T (&v)[6]) {
+__device__ __forceinline__ void ms_vjp(const T (&p)[6], T x0, T dx0dz, T b44, T b55, T (&v)[6], T sth, T cth,
+                                       T sph, T cph) {
   if (p[3] == T(0) || x0 <= T(0)) return;
-  T sth, cth, sph, cph;
-  ksincos_acc(p[5], &sth, &cth);
-  ksincos_acc(p[4], &sph, &cph);
   const T ir = krsqrt(kfma(p[0], p[0], p[1] * p[1]));
   const T cdiff = kfma(cph, p[0], sph * p[1]) * ir;   // cos(phi - phi_p)
   const T sdiff = kfma(sph, p[0], -cph * p[1]) * ir;  // sin(phi - phi_p)
@@ -780,15 +795,18 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
   }
   // ---- forward recompute of the step
   S q[6], J[6][6], Cp[21], s_len = S(0);
+  S trig[6];  // sin, cos of phi and theta at the start, of phi after the propagation
   const S kb = field_kb<S>(g, p_in);  // the field at the step's starting point
 #pragma unroll
   for (int k = 0; k < 21; ++k) Cp[k] = C_in[k];
   if (!first) {
-    prop_jacobian<S, true>(p_in, h.R, kb, S(INFINITY), q, J, nullptr, &s_len);
+    prop_jacobian<S, true>(p_in, h.R, kb, S(INFINITY), q, J, nullptr, &s_len, trig);
     transport<S>(J, Cp);
   } else {
 #pragma unroll
     for (int k = 0; k < 6; ++k) q[k] = p_in[k];
+    ksincos_acc(p_in[4], &trig[4], &trig[5]);
+    ksincos_acc(p_in[5], &trig[2], &trig[3]);
   }
   const S rho2 = kfma(q[0], q[0], q[1] * q[1]);
   const S irho = krsqrt(rho2);
@@ -847,7 +865,11 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
     }
     S dx0dz;
     const S x0 = x0_at<S>(g, h.L, pu[2], &dx0dz);
-    ms_vjp<S>(pu, x0, dx0dz, Cb[4][4], Cb[5][5], pbu);
+    // the angles after the update, from those of the prediction
+    S sph, cph, sth, cth;
+    rotate_small<S>(trig[4], trig[5], pu[4] - q[4], pu[4], sph, cph);
+    rotate_small<S>(trig[2], trig[3], pu[5] - q[5], pu[5], sth, cth);
+    ms_vjp<S>(pu, x0, dx0dz, Cb[4][4], Cb[5][5], pbu, sth, cth, sph, cph);
   }
   // ---- reverse: update and chi2 (chi2 adjoint 1)
   const S w0 = [&] { S a = S(0); for (int i = 0; i < 6; ++i) a = kfma(U[i][0], pbu[i], a); return a; }();
@@ -975,7 +997,7 @@ __device__ __forceinline__ void rev_step(const DevGeom& g, const S (&p_in)[6], c
       for (int j = 0; j < 6; ++j) jb = kfma(Cbp[i][j], CJ[j][l], jb);
       Jb[i][l] = S(2) * jb;
     }
-  jac_vjp<S>(p_in, s_len, kb, Jb, pin);
+  jac_vjp<S>(p_in, s_len, kb, Jb, pin, trig);
   if (g.fcz != 0.f || g.fcr != 0.f) {
     // The field at the starting point moves with it.  q and J depend on kb
     // and q/pT only through their product (J's q/pT column carries one more

@@ -341,11 +341,12 @@ __device__ __forceinline__ bool crossing(const float (&p)[6], float R, float kb,
 // 0 without a crossing, 2 when |z| at the crossing exceeds z_lim; p and C are
 // untouched unless 1 is returned.  cos_out (optional) receives |cos| of the
 // angle between the direction and the radial direction at the crossing,
-// s_out (optional) the transverse path length.
+// s_out (optional) the transverse path length, trig (optional, 6 values) the
+// sine and cosine of phi and theta at the start and of phi at the crossing.
 // ACC: the library's sine and cosine (ksincos_acc).
 template <class T, bool ACC = false>
 __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim, T (&q)[6], T (&J)[6][6],
-                                             T* cos_out = nullptr, T* s_out = nullptr) {
+                                             T* cos_out = nullptr, T* s_out = nullptr, T* trig = nullptr) {
   const T x = p[0], y = p[1], kap = p[3], phi = p[4], th = p[5];
   T sf, cf;
   ksc<ACC>(phi, &sf, &cf);
@@ -376,6 +377,14 @@ __device__ __forceinline__ int prop_jacobian(const T (&p)[6], T R, T kb, T z_lim
   const T dgds = kfma(xn, cp, yn * sp);
   if (cos_out) *cos_out = kabs(dgds) / R;
   if (s_out) *s_out = s;
+  if (trig) {
+    trig[0] = sf;
+    trig[1] = cf;
+    trig[2] = sth;
+    trig[3] = cth;
+    trig[4] = sp;
+    trig[5] = cp;
+  }
   const T inv = kdiv(T(-1), dgds);
   const T ds0 = xn * inv, ds1 = yn * inv;
   const T ds3 = kfma(xn, Fx3, yn * Fy3) * inv;

