@@ -650,7 +650,10 @@ def main():
         be = make_inputs("c6", rank)
         de = dict(x=tt(be.x), y=tt(be.y), z=tt(be.z), layer=tt(be.layer), params=tt(be.params),
                   cov=tt(be.cov), seed_hits=tt(be.seed_hits))
-        te = tracker_for(be, persistent=1, per_event=0)
+        best_e = shape or ({} if tune is None else dict(
+            lanes_per_seed=int(tune[np.argmin(tune[:, 4])][0]), block_threads=int(tune[np.argmin(tune[:, 4])][1]),
+            persistent=int(tune[np.argmin(tune[:, 4])][2]), find_regcap=int(tune[np.argmin(tune[:, 4])][3])))
+        te = tracker_for(be, **{"persistent": 1, "per_event": 0, **best_e})
         te.load_hits(be.hit_off, de["x"], de["y"], de["z"], de["layer"], stream)
         te.load_seeds(be.seed_off, de["params"], de["cov"], de["seed_hits"], stream)
         te.set_alignment(be.align, stream)
@@ -682,6 +685,7 @@ def main():
             n_disk_hits += int((lay_e[h[h >= 0]] >= be.det.n_layers).sum())
         endcap = {"workload": "c6: %d events x 8,000 tracks, |eta| < 2.4, 17 barrel layers + 2 x 7 disks "
                               "(|z| 130-250 cm, r 15-110 cm), 20%% noise, N=10" % be.n_events,
+                  "find_shape": best_e or None,
                   "value": be.n_seeds * world * args.steps / (ems / 1e3), "unit": UNIT,
                   "ms_per_step": ems / args.steps,
                   "forward_seed_fraction": float(np.mean(np.abs(eta0) >= be.det.eta_barrel)),

@@ -1421,14 +1421,18 @@ cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t s
   // flagged tracks are a few percent: a grid for a twentieth of all, striding
   // over however many there are
   const int grid_careful = (P.ns / 20 + ADJ_THREADS - 1) / ADJ_THREADS + 1;
+  // the double pass: blocks of 32 threads (its tracks' double-precision
+  // steps are bound by the SM's FP64 rate, so they spread over many SMs)
+  constexpr int DBL_THREADS = 32;
+  const int grid_dbl = (P.ns / 20 + DBL_THREADS - 1) / DBL_THREADS + 1;
   if (P.g.n_disks > 0) {  // the disk variants; energy loss on a layer or on the disks
     if (P.g.disk_eloss > 0.f) el = true;
     if (!careful) {
       if (el) k_adjoint<ADJ_ALL, true, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
       else k_adjoint<ADJ_ALL, false, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
     } else {
-      if (el) k_adjoint<ADJ_LIST_DBL, true, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
-      else k_adjoint<ADJ_LIST_DBL, false, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+      if (el) k_adjoint<ADJ_LIST_DBL, true, true><<<grid_dbl, DBL_THREADS, smem_c, st>>>(P);
+      else k_adjoint<ADJ_LIST_DBL, false, true><<<grid_dbl, DBL_THREADS, smem_c, st>>>(P);
       if (el) k_adjoint<ADJ_LIST_FP32, true, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
       else k_adjoint<ADJ_LIST_FP32, false, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
     }
@@ -1436,8 +1440,8 @@ cudaError_t launch_adjoint_pass(const AdjParams& P, bool careful, cudaStream_t s
     if (el) k_adjoint<ADJ_ALL, true><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
     else k_adjoint<ADJ_ALL, false><<<grid_all, ADJ_THREADS, smem_f, st>>>(P);
   } else {  // the careful list: its tracks with double steps, then the others
-    if (el) k_adjoint<ADJ_LIST_DBL, true><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
-    else k_adjoint<ADJ_LIST_DBL, false><<<grid_careful, ADJ_THREADS, smem_c, st>>>(P);
+    if (el) k_adjoint<ADJ_LIST_DBL, true><<<grid_dbl, DBL_THREADS, smem_c, st>>>(P);
+    else k_adjoint<ADJ_LIST_DBL, false><<<grid_dbl, DBL_THREADS, smem_c, st>>>(P);
     if (el) k_adjoint<ADJ_LIST_FP32, true><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
     else k_adjoint<ADJ_LIST_FP32, false><<<grid_careful, ADJ_THREADS, smem_f, st>>>(P);
   }

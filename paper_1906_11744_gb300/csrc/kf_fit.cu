@@ -299,9 +299,11 @@ cudaError_t launch_fit_main(const FitParams& P, cudaStream_t st) {
 
 cudaError_t launch_fit_careful(const FitParams& P, cudaStream_t st) {
   if (P.ns <= 0) return cudaSuccess;
-  // flagged tracks are a few percent of all: a grid sized for a twentieth of
-  // them, striding over however many there are
-  const int threads = 128;
+  // flagged tracks are a few percent of all, and their double-precision
+  // steps are bound by the SM's FP64 rate: blocks of 32 threads, so that they
+  // spread over many SMs; a grid for a twentieth of all tracks, striding over
+  // however many there are
+  const int threads = 32;
   const int careful_blocks = (P.ns / 20 + threads - 1) / threads + 1;
   cudaError_t e = cudaMemsetAsync(P.dbl_count, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
