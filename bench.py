@@ -54,9 +54,9 @@ WINDOW_HITS_PER_STEP = CENSUS["window_hits_per_step"]
 
 # DRAM traffic (read + write) of one k_find launch on the 100-event batch,
 # scaled by events from an ncu capture of the same kernel on 20 of its events
-# (192.09 MB: 170.41 read + 21.68 written).
+# (191.46 MB: 169.83 read + 21.62 written).
 # None whenever k_find changes until it is captured again.
-FIND_TRAFFIC_BYTES = 192.09e6 * 5
+FIND_TRAFFIC_BYTES = 191.46e6 * 5
 
 # Duplicate handling measured beside the headline step (Sec. 4.2): seed
 # cleaning on kinematics alone (eta, phi0 within 0.01, pT within 20%) and
