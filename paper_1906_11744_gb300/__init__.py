@@ -10,11 +10,12 @@ from __future__ import annotations
 import numpy as np
 
 from . import _lib
-from ._lib import (  # noqa: F401
+from ._lib import (
     KF_FIT_FOUND,
     KF_FIT_GIVEN,
     KF_FIT_OK,
     KF_FIT_SKIPPED,
+    KF_MAX_DISKS,
     KFError,
     kf_autotune,
     kf_capture_graph,
@@ -53,6 +54,8 @@ def make_detector(radius, x0, z_max=120.0, bz=3.8, sigma_rphi=0.01, sigma_z=0.1,
     with their radii, thickness, loss, radial resolution and the |eta| from
     which a seed searches them."""
     d = kf_detector()
+    if len(disk_z) > KF_MAX_DISKS:
+        raise ValueError(f"at most {KF_MAX_DISKS} disks per side")
     d.n_disks = len(disk_z)
     for i, z in enumerate(disk_z):
         d.disk_z[i] = float(z)

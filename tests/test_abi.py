@@ -89,3 +89,58 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(_lib.KFError):
         _lib.load()
+
+
+def test_detector_struct_layout_matches_the_header(tmp_path):
+    """The binding's kf_detector has the header's size and field offsets
+    (a C program compiled against include/kf.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_1906_11744_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in _lib.kf_detector._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "kf.h"\nint main(void) {\n'
+                    '  printf("size %zu\\n", sizeof(kf_detector));\n' +
+                    "".join(f'  printf("{f} %zu\\n", offsetof(kf_detector, {f}));\n' for f in fields) +
+                    "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(_lib.kf_detector)
+    for f in fields:
+        assert int(out[f]) == getattr(_lib.kf_detector, f).offset, f
+
+
+def test_disk_geometry_argument_errors_without_gpu():
+    """kf_create rejects a bad endcap geometry before touching the device:
+    too many disks, disk planes not increasing in |z| or at z <= 0, radii out
+    of order, a non-positive radial resolution or eta_barrel, a negative
+    thickness or loss, and a field factor outside [0.2, 5] over the disks'
+    reach."""
+    import ctypes
+
+    from paper_1906_11744_gb300 import _lib, make_config, make_detector
+    lib = _lib.load()
+    ctx = ctypes.c_void_p()
+    good = dict(disk_z=(130.0, 150.0), disk_rmin=15.0, disk_rmax=110.0, disk_x0=0.02, disk_eloss=0.0,
+                sigma_r=0.1, eta_barrel=0.9)
+    too_many = make_detector([5.0, 10.0], [0.02, 0.02], **good)
+    too_many.n_disks = 17  # beyond KF_MAX_DISKS (the binding refuses to build such a detector)
+    assert lib.kf_create(ctypes.byref(too_many), ctypes.byref(make_config()), ctypes.byref(ctx)) == _lib.KF_ERR_ARG
+    with pytest.raises(ValueError):
+        make_detector([5.0, 10.0], [0.02, 0.02], disk_z=tuple(130.0 + 10 * k for k in range(17)))
+    bad = [dict(disk_z=(150.0, 130.0)),
+           dict(disk_z=(-130.0, 150.0)), dict(disk_rmin=110.0, disk_rmax=15.0), dict(disk_rmin=0.0),
+           dict(sigma_r=0.0), dict(eta_barrel=0.0), dict(disk_x0=-0.01), dict(disk_eloss=-1e-3),
+           dict(disk_z=(130.0, 1000.0))]
+    for b in bad:
+        kw = {**good, **b}
+        field = dict(field_cz=-1.0e-6) if b.get("disk_z") == (130.0, 1000.0) else {}
+        det = make_detector([5.0, 10.0], [0.02, 0.02], **field, **kw)
+        assert lib.kf_create(ctypes.byref(det), ctypes.byref(make_config()), ctypes.byref(ctx)) == _lib.KF_ERR_ARG, b
