@@ -668,6 +668,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     bool loose = false;  // careful pass: the seed's prior is loose (its steps in double)
     int nfound = 3, nholes = 0;
     bool finished = false;
+    bool bdone = false;  // DISK: a forward candidate past the barrel's reach (it passed a barrel layer)
     bool occ = has_seed && gl == 0;
     int sh0 = 0, sh1 = 0, sh2 = 0, sl0 = 0, sl1 = 0, sl2 = 0;
     bool fwd = false, neg = false;  // the seed's region: forward (its side's disks after the barrel), -z side
@@ -781,6 +782,8 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
 #pragma unroll
               for (int k = 0; k < 6; ++k) p[k] = q[k];
             }
+          } else if (DISK && fwd && !in_seed && bdone) {
+            pr = 0;  // it passed an earlier barrel layer, so it passes this one
           } else if (it != 0) {
             const float z_lim = in_seed ? INFINITY : g.z_max;
             float q[6], J[6][6], cosa = 1.f;
@@ -985,13 +988,16 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             do_update = true;
             hit = key_hit(mine);
             finished = false;
+            bdone = false;
           } else if (p_cls == 2) {
             nholes += 1;
             do_ms = true;
             finished = false;
+            bdone = false;
             c_holes++;
           } else {
             finished = p_cls != 3;  // 3: the surface was passed, the search goes on
+            bdone = DISK && p_cls == 3;
           }
           hist[(grp * HL + pos) * G + gl] = (par << 24) | (do_update ? hit + 1 : 0);
         }
@@ -1078,6 +1084,24 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         const unsigned live = __ballot_sync(0xffffffffu, active && occ && !finished);
         if (lane_used && active && !((live >> base) & ((1u << G) - 1u))) n_iter = min(n_iter, it + 1);
         it_end = __reduce_max_sync(0xffffffffu, n_iter);
+      }
+      if constexpr (DISK) {
+        // A forward candidate that passed a barrel layer passes every later
+        // one: it moves outward from its last crossing, so a larger radius
+        // comes later along the helix (or never), and |z|, already beyond
+        // z_max, grows along it.  When every live candidate of the warp has
+        // passed one, the warp goes on at the first disk of its plans; each
+        // position skipped carries every candidate in its slot (what the
+        // passes would do).
+        if (!in_seed && __any_sync(0xffffffffu, lane_used && active && occ && !finished) &&
+            !__any_sync(0xffffffffu, lane_used && active && occ && !finished && !bdone)) {
+          const int first_disk = __reduce_min_sync(0xffffffffu, lane_used && active ? 3 + (L - start) : 0x7fffffff);
+          if (first_disk > it + 1 && first_disk != 0x7fffffff) {
+            for (int q = it + 1; q < first_disk; ++q)
+              if (lane_used && q < n_iter) hist[(grp * HL + start + (q - 3)) * G + gl] = gl << 24;
+            it = first_disk - 1;
+          }
+        }
       }
       __syncwarp();
     }
