@@ -30,7 +30,9 @@
 // forward seed the disks of its side; a disk is reached by the plane step and
 // searched in an r x phi grid with the (r-phi, r) measurement; along a
 // forward plan a surface not crossed within its bounds is passed (the
-// candidate is carried on unchanged, neither a hole nor finished).
+// candidate is carried on unchanged, neither a hole nor finished).  Their
+// seed kernel fits the seed only; the plan's first surface is searched in the
+// group loop.
 //
 // The kernel templates live in this header; kf_find.cu instantiates the
 // barrel variants and kf_find_disk.cu the disk variants.
