@@ -51,6 +51,13 @@ F_UPDATE = CENSUS["flops"]["F_UPDATE"]
 F_MS = CENSUS["flops"]["F_MS"]
 F_SEED = CENSUS["flops"]["F_SEED"]
 WINDOW_HITS_PER_STEP = CENSUS["window_hits_per_step"]
+# Steps onto endcap disks (plane step, (r-phi, r) frame and r window, disk
+# update and scattering), counted apart on a barrel-plus-endcap event.
+F_DISK_STEP = CENSUS["disks"]["flops"]["F_DISK_STEP"]
+F_DISK_HIT = CENSUS["disks"]["flops"]["F_DISK_HIT"]
+F_DISK_UPDATE = CENSUS["disks"]["flops"]["F_DISK_UPDATE"]
+F_DISK_MS = CENSUS["disks"]["flops"]["F_DISK_MS"]
+WINDOW_HITS_PER_DISK_STEP = CENSUS["disks"]["window_hits_per_disk_step"]
 
 # DRAM traffic (read + write) of one k_find launch on the 100-event batch,
 # scaled by events from an ncu capture of the same kernel on 20 of its events
@@ -646,6 +653,7 @@ def main():
     # PU-200-like barrel plus endcaps (c6: 20 events x 8,000 tracks, |eta| < 2.4, seven disks
     # per side): finding over the region plans, duplicate removal, fit and adjoint in one graph
     endcap = None
+    endcap_batch = None
     if not args.no_endcap:
         be = make_inputs("c6", rank)
         de = dict(x=tt(be.x), y=tt(be.y), z=tt(be.z), layer=tt(be.layer), params=tt(be.params),
@@ -683,14 +691,34 @@ def main():
             h = trk["hits"][a0:a1]
             lay_e = lay_all[be.hit_off[e]:be.hit_off[e + 1]]
             n_disk_hits += int((lay_e[h[h >= 0]] >= be.det.n_layers).sum())
+        ec = te.counters(stream)
+        # roofline of the disk finding kernel: barrel and disk steps, updates
+        # and scatterings at their own census counts (the disk counters are
+        # parts of the totals; barrel window hits at the barrel batch's rate)
+        e_find_ms = estage["find"] / args.steps
+        nd, ndu, ndh = ec["disk_steps"], ec["disk_updates"], ec["disk_holes"]
+        e_flops = ((ec["steps"] - nd) * (F_STEP + WINDOW_HITS_PER_STEP * F_HIT)
+                   + nd * (F_DISK_STEP + WINDOW_HITS_PER_DISK_STEP * F_DISK_HIT)
+                   + (ec["updates"] - ndu) * F_UPDATE + ndu * F_DISK_UPDATE
+                   + (ec["updates"] - ndu + ec["holes"] - ndh) * F_MS + (ndu + ndh) * F_DISK_MS
+                   + ec["seeds"] * F_SEED)
+        e_ach = e_flops / (e_find_ms / 1e3) / 1e12
+        endcap_batch = be
         endcap = {"workload": "c6: %d events x 8,000 tracks, |eta| < 2.4, 17 barrel layers + 2 x 7 disks "
                               "(|z| 130-250 cm, r 15-110 cm), 20%% noise, N=10" % be.n_events,
+                  "roofline": {"bound": "alu", "achieved": e_ach, "peak": peak, "unit": "TFLOP/s",
+                               "frac": e_ach / peak, "traffic": None, "kernel": "k_find (disk variant)",
+                               "flops_per_launch": e_flops, "find_ms": e_find_ms,
+                               "flops_per_unit": {"disk_step": F_DISK_STEP, "disk_window_hit": F_DISK_HIT,
+                                                  "window_hits_per_disk_step": WINDOW_HITS_PER_DISK_STEP,
+                                                  "disk_update": F_DISK_UPDATE, "disk_scatter": F_DISK_MS,
+                                                  "source": "oracle operation census (oracle/flop_census.json)"}},
                   "find_shape": best_e or None,
                   "value": be.n_seeds * world * args.steps / (ems / 1e3), "unit": UNIT,
                   "ms_per_step": ems / args.steps,
                   "forward_seed_fraction": float(np.mean(np.abs(eta0) >= be.det.eta_barrel)),
                   "found_disk_hits_per_step": n_disk_hits,
-                  "counters_per_step": te.counters(stream),
+                  "counters_per_step": ec,
                   "stage_ms": {k: v / args.steps for k, v in estage.items()},
                   "gpu_launches": te.graph_kernel_count() * args.steps}
         te.close()
@@ -794,6 +822,9 @@ def main():
         one = oracle_sample(b, budget_s=1.0, threads=1)                   # one event, one core
         cpu["single_core_value"] = one["value"]
         cpu["single_core_sample"] = one["sample"]
+        if endcap is not None and endcap_batch is not None:  # the oracle beside the endcap step
+            ce = oracle_sample(endcap_batch, budget_s=5.0)
+            endcap["cpu_baseline"] = {k: ce[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

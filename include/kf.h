@@ -292,6 +292,14 @@ int kf_autotune(kf_ctx* ctx, float* results, int max_results, int* n_results, vo
  * pass (their candidates met such a crossing). */
 int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream);
 
+/* The same counters and those of the endcap disks, synchronous: the first n
+ * (1..KF_N_COUNTERS) of [0..7] as kf_get_counters, [8] the candidate-layer
+ * steps onto endcap disks (a part of [0]), [9] the hit-children updated on
+ * disks (a part of [1]), [10] the hole-children on disks (a part of [4]).
+ * Errors: KF_ERR_ARG (n out of range). */
+#define KF_N_COUNTERS 11
+int kf_get_counters_n(kf_ctx* ctx, long long* counters, int n, void* stream);
+
 /* Stage timing: with enable = 1, CUDA events are recorded around the
  * binning, finding, duplicate removal, fit, adjoint and seed-cleaning
  * launches of the batched form (also inside a captured graph).

@@ -85,6 +85,7 @@ def lib():
             L.orc_replay.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
             L.orc_select_children.argtypes = [ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int, _P]
             L.orc_census_step.argtypes = [_P, ctypes.c_double, _P, _P, ctypes.c_int, _P, _P, _P, _P]
+            L.orc_census_disk_step.argtypes = [_P, ctypes.c_double, _P, _P, ctypes.c_int, _P, _P, _P]
             L.orc_census_fit.argtypes = [_P, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
             L.orc_census_transport.argtypes = [_P, _P, _P]
             L.orc_dedup.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_double,
@@ -326,7 +327,7 @@ def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=
     out_c2 = np.zeros(n)
     out_p = np.zeros((n, 6))
     out_C = np.zeros((n, 21))
-    cnt = np.zeros(9, np.int64)
+    cnt = np.zeros(13, np.int64)
     mc = batch.cfg["max_cands"] if max_cands is None else max_cands
     d = make_detector(det)
     cfg = make_config(mc, max_holes, chi2_cut)
@@ -339,7 +340,9 @@ def find_event(batch, e: int, max_cands=None, chi2_cut=30.0, max_holes=3, seeds=
     return dict(hits=out_hits, n_found=out_n, chi2=out_c2, p=out_p, C=out_C,
                 counters=dict(steps=int(cnt[0]), prop_calls=int(cnt[1]), updates=int(cnt[2]),
                               ms=int(cnt[3]), chi2_evals=int(cnt[4]), seeds=int(cnt[5]),
-                              children=int(cnt[6]), holes=int(cnt[7]), window_hits=int(cnt[8])))
+                              children=int(cnt[6]), holes=int(cnt[7]), window_hits=int(cnt[8]),
+                              disk_steps=int(cnt[9]), disk_updates=int(cnt[10]), disk_holes=int(cnt[11]),
+                              disk_window_hits=int(cnt[12])))
 
 
 def dedup(hits, n_hits, chi2, frac=0.5, brute=False, params=None, bz=0.0, deta=0.0, dphi=0.0, dpt=0.0):
@@ -457,6 +460,19 @@ def census_step(det, p, C21, layer, m1, m2, align=(0.0, 0.0), chi2_cut=30.0):
     rc = lib().orc_census_step(ctypes.byref(d), float(chi2_cut), _ptr(_c(p, np.float64)), _ptr(_c(C21, np.float64)),
                                int(layer), _ptr(_c(m1, np.float64)), _ptr(_c(m2, np.float64)),
                                _ptr(_c(align, np.float64)), _ptr(out))
+    return None if rc != 0 else out.reshape(5, 4)
+
+
+def census_disk_step(det, p, C21, surface, m1, m2, chi2_cut=30.0):
+    """Operations of one finding step onto an endcap disk (orc_census_disk_step),
+    as census_step: a [5][4] array, rows CENSUS_PARTS (the window row: the
+    frame and the r window of the chi2 < cut ellipse); None without a crossing
+    or with a hit on the far side."""
+    out = np.zeros(20, np.int64)
+    d = make_detector(det)
+    rc = lib().orc_census_disk_step(ctypes.byref(d), float(chi2_cut), _ptr(_c(p, np.float64)),
+                                    _ptr(_c(C21, np.float64)), int(surface), _ptr(_c(m1, np.float64)),
+                                    _ptr(_c(m2, np.float64)), _ptr(out))
     return None if rc != 0 else out.reshape(5, 4)
 
 

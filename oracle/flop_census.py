@@ -10,6 +10,10 @@ square root, logarithm) counts one operation.  The benchmark multiplies them
 by the work counters, which tests pin to the oracle's, so that its
 algorithmic flop count depends on neither the kernels nor hand counts.
 
+The steps onto endcap disks (the plane step, the (r-phi, r) frame and r
+window, the disk's update and scattering) are counted apart, on the disk
+steps of true forward tracks of a barrel-plus-endcap PU-200-like event.
+
 Writes flop_census.json beside this file:  python oracle/flop_census.py
 """
 from __future__ import annotations
@@ -106,6 +110,65 @@ def census(n_tracks: int = N_TRACKS) -> dict:
     }
 
 
+def census_disks(n_tracks: int = N_TRACKS) -> dict:
+    """Per-unit counts of the steps onto endcap disks: every disk step of the
+    true hit lists of forward seeds of event 0 of the barrel-plus-endcap
+    configuration (20 x 8,000 tracks, |eta| < 2.4), from the fitted state
+    before the step; window hits per disk step from the oracle's finding on
+    a quarter of the event's seeds."""
+    import oracle
+    from synth import make_batch
+    from synth.events import true_hit_lists
+    b = make_batch("c6", n_events=1)
+    det = b.det
+    S, L = det.n_surfaces, det.n_layers
+    x, y, z, lay = b.event_hits(0)
+    prm, cov, _ = b.event_seeds(0)
+    lists, n = true_hit_lists(b, 0, S)
+    eta = -np.log(np.tan(0.5 * prm[5].astype(np.float64)))
+    fwd = np.nonzero(np.abs(eta) >= det.eta_barrel)[0]
+    seeds = fwd[np.arange(0, fwd.size, max(1, fwd.size // n_tracks))[:n_tracks]]
+    steps = []
+    for s in seeds:
+        hl = lists[b.seed_sim[s]][None, :]
+        nh = int(n[b.seed_sim[s]])
+        for j in range(3, nh):
+            h = int(hl[0, j])
+            if lay[h] < L:
+                continue
+            p, C, _, st = oracle.fit(det, prm[:, s:s + 1], cov[:, s:s + 1], hl, np.array([j]), x, y, z, lay,
+                                     align=b.align, ms_after_last=True)
+            if st[0] != 0:
+                break
+            m1 = np.array([x[h], y[h], z[h]], np.float64)
+            c = oracle.census_disk_step(det, p[0], C[0], int(lay[h]), m1, m1 + np.array([SECOND_HIT_DZ, 0.0, 0.0]))
+            if c is not None:
+                steps.append(c)
+    steps = np.array(steps, np.float64)
+    mean = steps.mean(axis=0)
+    parts = dict(zip(oracle.CENSUS_PARTS, mean))
+    ns = b.n_seeds
+    chunks = [(lo, min(lo + 250, ns)) for lo in range(0, ns, 1000)]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        cnts = list(ex.map(lambda c: oracle.find_event(b, 0, seeds=c)["counters"], chunks))
+    n_dsteps = sum(c["disk_steps"] for c in cnts)
+    n_dwin = sum(c["disk_window_hits"] for c in cnts)
+    kinds = ["adds", "multiplies", "divides", "special"]
+    return {
+        "sample": f"{len(steps)} disk steps along {len(seeds)} true forward tracks of barrel-plus-endcap event 0 "
+                  f"(20 x 8,000 tracks, |eta| < 2.4, seven disks per side)",
+        "per_step_parts": {k: {kk: float(v) for kk, v in zip(kinds, parts[k])} for k in parts},
+        "flops": {
+            "F_DISK_STEP": float(parts["propagate_transport"].sum() + parts["frame_window"].sum()),
+            "F_DISK_HIT": float(parts["hit_chi2"].sum()),
+            "F_DISK_UPDATE": float(parts["update"].sum()),
+            "F_DISK_MS": float(parts["scatter"].sum()),
+        },
+        "window_hits_per_disk_step": n_dwin / n_dsteps,
+        "window_hits_sample": f"{n_dsteps} oracle disk steps of event 0, seeds [lo, lo + 250) every 1,000",
+    }
+
+
 def load() -> dict:
     with open(OUT) as f:
         return json.load(f)
@@ -113,7 +176,9 @@ def load() -> dict:
 
 if __name__ == "__main__":
     res = census()
+    res["disks"] = census_disks()
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1)
         f.write("\n")
     print(json.dumps(res["flops"], indent=1), res["window_hits_per_step"])
+    print(json.dumps(res["disks"]["flops"], indent=1), res["disks"]["window_hits_per_disk_step"])

@@ -881,6 +881,10 @@ struct Counters {
   long long window_hits;  // hits inside the bounding box of the chi2 < cut ellipse of the
                           // prediction (|r_rphi| and |r_z| within sqrt(cut S) each): the
                           // method's search window, implementation-independent
+  long long disk_steps;   // the steps among `steps` onto endcap disks
+  long long disk_updates;  // the updates among `updates` on endcap disks
+  long long disk_holes;    // the holes among `holes` on endcap disks
+  long long disk_window_hits;  // the window hits among `window_hits` on endcap disks
 };
 
 void seed_state(const double* params, const double* cov, long stride, long i, double p[6],
@@ -960,6 +964,7 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
       }
       transport(J, pc.C);
       ++cnt.steps;
+      if (disk) ++cnt.disk_steps;
       int n_children = 0;
       // Window on z: chi2 >= r_z^2 / S_zz for a 2x2 positive-definite S, so
       // hits with |m_z - z| > sqrt(cut * S_zz) cannot pass the cut.  A disk's
@@ -986,8 +991,10 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
         ++cnt.chi2_evals;
         if (!measure(pc.p, pc.C, m, vr, v2, ms, disk)) continue;
         if (std::fabs(ms.r[0]) < std::sqrt(cfg.chi2_cut * ms.S[0][0]) &&
-            std::fabs(ms.r[1]) < std::sqrt(cfg.chi2_cut * ms.S[1][1]))
+            std::fabs(ms.r[1]) < std::sqrt(cfg.chi2_cut * ms.S[1][1])) {
           ++cnt.window_hits;
+          if (disk) ++cnt.disk_window_hits;
+        }
         if (ms.chi2 < cfg.chi2_cut) {
           children.push_back({c.n_found + 1, c.chi2 + ms.chi2, (int)r, KIND_HIT, hidx, 0});
           ++n_children;
@@ -1029,9 +1036,11 @@ void find_seed(const Det& det, const Cfg& cfg, const double* hx, const double* h
         c.chi2 = ch.chi2;
         c.hits.push_back(ch.hit);
         ++cnt.updates;
+        if (disk) ++cnt.disk_updates;
       } else {
         c.n_holes += 1;
         ++cnt.holes;
+        if (disk) ++cnt.disk_holes;
       }
       if (disk) {
         add_ms(c.p, c.C, det.disk_x0, true);
@@ -1388,7 +1397,7 @@ int orc_fit_grad32(const orc_detector* dptr, int n_tracks, const double* prior_p
 // Combinatorial finding for seeds [s_begin, s_end) of one event.  Hits are
 // the event's arrays (event-local indices); seeds are structure-of-arrays with
 // the given stride; seed_hits [3][stride].  out_hits [n][surfaces] (padded -1),
-// out_p [n][6], out_C [n][21].  counters [9]: see Counters.  brute != 0 tests every
+// out_p [n][6], out_C [n][21].  counters [13]: see Counters.  brute != 0 tests every
 // hit of the layer instead of the exact z pre-selection.
 int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits, const double* hx,
                    const double* hy, const double* hz, const int* hlayer, const double* params,
@@ -1424,6 +1433,8 @@ int orc_find_event(const orc_detector* dptr, const orc_config* cfgp, int n_hits,
     counters[0] += cnt.steps; counters[1] += cnt.prop_calls; counters[2] += cnt.updates;
     counters[3] += cnt.ms; counters[4] += cnt.chi2_evals; counters[5] += cnt.seeds;
     counters[6] += cnt.children; counters[7] += cnt.holes; counters[8] += cnt.window_hits;
+    counters[9] += cnt.disk_steps; counters[10] += cnt.disk_updates; counters[11] += cnt.disk_holes;
+    counters[12] += cnt.disk_window_hits;
   }
   return 0;
 }
@@ -1489,6 +1500,73 @@ int orc_census_step(const orc_detector* dptr, double chi2_cut, const double* p, 
   cn_count(outs, c3);
   add_ms(pu, Cu, x0_at(det, L, pu[2]));
   add_eloss(pu, Cu, det.eloss[L]);
+  outs.resize(n_before);
+  for (int k = 0; k < 6; ++k) outs.push_back(pu[k].id);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(Cu[a][b].id);
+  cn_count(outs, c4);
+  for (int c = 0; c < 4; ++c) {
+    const long long hit = c2[c] - c1[c];
+    out[0 + c] = c0[c];
+    out[4 + c] = c1[c] - c0[c] - hit;
+    out[8 + c] = hit;
+    out[12 + c] = c3[c] - c2[c];
+    out[16 + c] = c4[c] - c3[c];
+  }
+  g_tape.clear();
+  g_cse.clear();
+  return 0;
+}
+
+// Operation census of one finding step onto endcap disk surface S (as
+// orc_census_step): the plane step and transport; the frame and the bounds
+// of the r window of the chi2 < cut ellipse (r_p -+ sqrt(cut S_rr), the
+// disk's analogue of the z window) with the first hit's chi2; one more hit's
+// chi2; the update; the disk's scattering and energy loss.  out [5][4].
+int orc_census_disk_step(const orc_detector* dptr, double chi2_cut, const double* p, const double* C21, int S,
+                         const double* m1, const double* m2, long long* out) {
+  const Det det = to_det(dptr);
+  if (!det.is_disk(S)) return -3;
+  g_tape.clear();
+  g_cse.clear();
+  Cn pc[6], Cc[6][6], q[6], J[6][6];
+  for (int k = 0; k < 6; ++k) pc[k] = cn_input(p[k]);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) Cc[a][b] = Cc[b][a] = cn_input(C21[sym_index(a, b)]);
+  if (!propagate_plane(det.field(), pc, det.plane_z(S), q, J)) return -1;
+  transport(J, Cc);
+  std::vector<int> outs;
+  for (int k = 0; k < 6; ++k) outs.push_back(q[k].id);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(Cc[a][b].id);
+  long long c0[4], c1[4], c2[4], c3[4], c4[4];
+  cn_count(outs, c0);
+  const double vr = det.sigma_rphi * det.sigma_rphi, vrr = det.sigma_r * det.sigma_r;
+  Cn mm1[3], mm2[3];
+  for (int k = 0; k < 3; ++k) mm1[k] = cn_input(m1[k]), mm2[k] = cn_input(m2[k]);
+  Meas<Cn> ms1, ms2;
+  if (!measure(q, Cc, mm1, vr, vrr, ms1, true) || !measure(q, Cc, mm2, vr, vrr, ms2, true)) return -2;
+  const Cn rp = sqrt(q[0] * q[0] + q[1] * q[1]);
+  const Cn w = sqrt(chi2_cut * ms1.S[1][1]);
+  const Cn lo = rp - w, hi = rp + w;
+  outs.push_back(lo.id);
+  outs.push_back(hi.id);
+  outs.push_back(ms1.chi2.id);
+  cn_count(outs, c1);
+  outs.push_back(ms2.chi2.id);
+  cn_count(outs, c2);
+  Cn pu[6], Cu[6][6];
+  for (int k = 0; k < 6; ++k) pu[k] = q[k];
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) Cu[a][b] = Cc[a][b];
+  kf_update(pu, Cu, ms1);
+  const size_t n_before = outs.size();
+  for (int k = 0; k < 6; ++k) outs.push_back(pu[k].id);
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) outs.push_back(Cu[a][b].id);
+  cn_count(outs, c3);
+  add_ms(pu, Cu, Cn(det.disk_x0), true);
+  add_eloss(pu, Cu, det.disk_eloss, true);
   outs.resize(n_before);
   for (int k = 0; k < 6; ++k) outs.push_back(pu[k].id);
   for (int a = 0; a < 6; ++a)

@@ -31,6 +31,7 @@ KF_NOALLOC_MAX_HITS = 262144
 KF_SEED_MAX_DETA = 1.0
 KF_MAX_MATERIAL_NODES = 4096
 KF_MAX_DISKS = 16
+KF_N_COUNTERS = 11
 
 
 class kf_detector(ctypes.Structure):
@@ -79,6 +80,7 @@ _SIGS = {
     "kf_launch_graph": ([_P, _P], _I),
     "kf_autotune": ([_P, _P, _I, _P, _P], _I),
     "kf_get_counters": ([_P, _P, _P], _I),
+    "kf_get_counters_n": ([_P, _P, _I, _P], _I),
     "kf_sync": ([_P, _P], _I),
     "kf_set_stage_timing": ([_P, _I], _I),
     "kf_get_stage_ms": ([_P, _P, _P], _I),
@@ -265,10 +267,13 @@ def kf_autotune(ctx, stream=None, max_results=128):
 
 
 def kf_get_counters(ctx, stream=None):
-    c = np.zeros(8, np.int64)
-    _check(ctx, load().kf_get_counters(ctx, c.ctypes.data_as(_P), _stream(stream)), "kf_get_counters")
+    """The finding's counters (kf_get_counters_n, all KF_N_COUNTERS of them)."""
+    c = np.zeros(KF_N_COUNTERS, np.int64)
+    _check(ctx, load().kf_get_counters_n(ctx, c.ctypes.data_as(_P), KF_N_COUNTERS, _stream(stream)),
+           "kf_get_counters_n")
     return dict(steps=int(c[0]), updates=int(c[1]), chi2_evals=int(c[2]), seeds=int(c[3]),
-                holes=int(c[4]), careful=int(c[5]), not_pd=int(c[6]), redone=int(c[7]))
+                holes=int(c[4]), careful=int(c[5]), not_pd=int(c[6]), redone=int(c[7]),
+                disk_steps=int(c[8]), disk_updates=int(c[9]), disk_holes=int(c[10]))
 
 
 def kf_set_stage_timing(ctx, enable=True):

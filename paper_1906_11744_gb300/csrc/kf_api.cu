@@ -342,7 +342,7 @@ int kf_create(const kf_detector* det, const kf_config* cfg, kf_ctx** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = grow(ctx->counters, 64);
+  if (e == cudaSuccess) e = grow(ctx->counters, 8 * KF_N_COUNTERS);
   if (e == cudaSuccess) e = grow(ctx->status, 64);
   if (e == cudaSuccess) {
     k_align<<<1, KF_MAX_LAYERS>>>(nullptr, g, ptr<Align4>(ctx->align4));
@@ -713,7 +713,7 @@ int kf_find_tracks(kf_ctx* ctx, void* stream) {
     return fail(ctx, KF_ERR_STATE, "kf_find_tracks: load hits and seeds first");
   cudaStream_t st = S(stream);
   const size_t cells = (size_t)ctx->g.n_surf * ctx->g.n_eta * ctx->g.n_phi;
-  CK(cudaMemsetAsync(ctx->counters.p, 0, 64, st));
+  CK(cudaMemsetAsync(ctx->counters.p, 0, 8 * KF_N_COUNTERS, st));
   CK(cudaMemsetAsync(ctx->keep.p, 1, (size_t)ctx->n_seeds, st));
   const int grid_cap = ctx->num_sms * ctx->blocks_per_sm;
   if (!ctx->per_event) {
@@ -1006,10 +1006,12 @@ int kf_get_fit(kf_ctx* ctx, float* params, float* cov, float* chi2, int* status,
   return KF_OK;
 }
 
-int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream) {
-  if (!ctx || !counters8) return KF_ERR_ARG;
+int kf_get_counters(kf_ctx* ctx, long long* counters8, void* stream) { return kf_get_counters_n(ctx, counters8, 8, stream); }
+
+int kf_get_counters_n(kf_ctx* ctx, long long* counters, int n, void* stream) {
+  if (!ctx || !counters || n < 1 || n > KF_N_COUNTERS) return KF_ERR_ARG;
   cudaStream_t st = S(stream);
-  CK(cudaMemcpyAsync(counters8, ctx->counters.p, 8 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(counters, ctx->counters.p, (size_t)n * sizeof(long long), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return KF_OK;
 }

@@ -626,8 +626,8 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   unsigned* const queue = P.queue + (CAREFUL ? 1 : 0);
   // Counters: per-warp sums in shared memory (lane 0 of the warp owns its
   // row), added to the global counters once when the warp ends.
-  __shared__ unsigned long long s_cnt[8][8];
-  if (lane < 8) s_cnt[warp][lane] = 0ull;
+  __shared__ unsigned long long s_cnt[8][11];  // [7..10]: (unused), disk steps, disk updates, disk holes
+  if (lane < 11) s_cnt[warp][lane] = 0ull;
   unsigned c_redo = 0;  // seeds given up (kept across tasks: not a per-task count)
   __syncwarp();
 
@@ -659,6 +659,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
     }
     // counters of this task (dropped for a seed given up)
     unsigned c_steps = 0, c_updates = 0, c_chi2 = 0, c_seeds = 0, c_holes = 0, c_careful = 0, c_npd = 0;
+    unsigned c_dsteps = 0, c_dupdates = 0, c_dholes = 0;  // DISK: the steps, updates and holes on disks
     bool near = false, given_up = false;
     // main pass: the first layer's children, found by the seed kernel (this
     // lane's child and whether their parent was carried or propagated)
@@ -822,6 +823,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             cls = 2;
             if (!in_seed && disk) {
               c_steps++;
+              c_dsteps++;
               DiskFrameT<float> d;
               make_frame_disk<float>(p, C, g.vr, g.vrr, d);
               const bool spd = d.f.s00 > 0.f && d.f.si00 > 0.f && d.f.si11 > 0.f;
@@ -997,6 +999,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             finished = false;
             bdone = false;
             c_holes++;
+            if (disk) c_dholes++;
           } else {
             finished = p_cls != 3;  // 3: the surface was passed, the search goes on
             bdone = DISK && p_cls == 3;
@@ -1044,6 +1047,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
             kf_update_disk<float>(p, C, d, r0, r1);
             do_ms = true;
             c_updates++;
+            c_dupdates++;
           }
           do_update = false;
         }
@@ -1122,6 +1126,7 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
         ++c_redo;
       }
       c_steps = c_updates = c_chi2 = c_seeds = c_holes = c_npd = 0;
+      c_dsteps = c_dupdates = c_dholes = 0;
     }
     // Counters of the task: summed over the warp into its shared row.
 #pragma unroll
@@ -1133,6 +1138,11 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       c_holes += __shfl_xor_sync(0xffffffffu, c_holes, off);
       c_careful += __shfl_xor_sync(0xffffffffu, c_careful, off);
       c_npd += __shfl_xor_sync(0xffffffffu, c_npd, off);
+      if constexpr (DISK) {
+        c_dsteps += __shfl_xor_sync(0xffffffffu, c_dsteps, off);
+        c_dupdates += __shfl_xor_sync(0xffffffffu, c_dupdates, off);
+        c_dholes += __shfl_xor_sync(0xffffffffu, c_dholes, off);
+      }
     }
     if (lane == 0) {
       s_cnt[warp][0] += c_steps;
@@ -1142,6 +1152,11 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       s_cnt[warp][4] += c_holes;
       s_cnt[warp][5] += c_careful;
       s_cnt[warp][6] += c_npd;
+      if constexpr (DISK) {
+        s_cnt[warp][8] += c_dsteps;
+        s_cnt[warp][9] += c_dupdates;
+        s_cnt[warp][10] += c_dholes;
+      }
     }
     // The best candidate sits in slot 0: rebuild its hit list.
     if (has_seed && gl == 0 && !given_up) {
@@ -1176,6 +1191,8 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   }
   __syncwarp();
   if (lane < 7 && P.counters && s_cnt[warp][lane]) atomicAdd(&P.counters[lane], s_cnt[warp][lane]);
+  if (DISK && lane >= 8 && lane < 11 && P.counters && s_cnt[warp][lane])
+    atomicAdd(&P.counters[lane], s_cnt[warp][lane]);
   if (c_redo && P.counters) atomicAdd(&P.counters[7], (unsigned long long)c_redo);
 }
 

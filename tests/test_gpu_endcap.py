@@ -269,3 +269,23 @@ def test_duplicate_handling_on_endcap_tracks():
     print(f"endcap duplicates: {int((ref_seeds == 0).sum())} seeds cleaned, {int(removed.sum())} tracks "
           f"removed ({int((removed & fwd).sum())} forward)")
     assert (removed & fwd).sum() > 0
+
+
+def test_endcap_work_counters_equal_the_oracles():
+    """The finding's work counters on the barrel-plus-endcap event equal the
+    oracle's on the same inputs (the multipliers of the endcap step's
+    algorithmic flop count): candidate-layer steps, seeds and the steps onto
+    disks exactly; updates and holes, with their disk parts, within 1e-4
+    (near-tied children of candidates that do not win may move)."""
+    b = make_batch("c5")
+    t = tracker_for(b)
+    t.find_tracks()
+    c = t.counters()
+    r = oracle.find_event(b, 0)["counters"]
+    print("endcap counters:", {k: (c[k], r[k]) for k in ("steps", "disk_steps", "updates", "disk_updates",
+                                                         "holes", "disk_holes", "seeds")})
+    for k in ("steps", "seeds", "disk_steps"):
+        assert c[k] == r[k], (k, c[k], r[k])
+    for k in ("updates", "holes", "disk_updates", "disk_holes"):
+        assert abs(c[k] - r[k]) <= 1e-4 * r[k] + 2, (k, c[k], r[k])
+    assert r["disk_steps"] > 0.2 * r["steps"]
