@@ -626,8 +626,10 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   unsigned* const queue = P.queue + (CAREFUL ? 1 : 0);
   // Counters: per-warp sums in shared memory (lane 0 of the warp owns its
   // row), added to the global counters once when the warp ends.
-  __shared__ unsigned long long s_cnt[8][11];  // [7..10]: (unused), disk steps, disk updates, disk holes
-  if (lane < 11) s_cnt[warp][lane] = 0ull;
+  // per warp: counters 0-6, then (DISK) [8..10] the disk steps, updates, holes
+  constexpr int NCNT = DISK ? 11 : 8;
+  __shared__ unsigned long long s_cnt[8][NCNT];
+  if (lane < NCNT) s_cnt[warp][lane] = 0ull;
   unsigned c_redo = 0;  // seeds given up (kept across tasks: not a per-task count)
   __syncwarp();
 
@@ -1153,9 +1155,9 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
       s_cnt[warp][5] += c_careful;
       s_cnt[warp][6] += c_npd;
       if constexpr (DISK) {
-        s_cnt[warp][8] += c_dsteps;
-        s_cnt[warp][9] += c_dupdates;
-        s_cnt[warp][10] += c_dholes;
+        s_cnt[warp][NCNT - 3] += c_dsteps;
+        s_cnt[warp][NCNT - 2] += c_dupdates;
+        s_cnt[warp][NCNT - 1] += c_dholes;
       }
     }
     // The best candidate sits in slot 0: rebuild its hit list.
@@ -1191,8 +1193,9 @@ __global__ void __launch_bounds__(CAP ? 128 : 256, CAP ? 5 : 1) k_find(const Fin
   }
   __syncwarp();
   if (lane < 7 && P.counters && s_cnt[warp][lane]) atomicAdd(&P.counters[lane], s_cnt[warp][lane]);
-  if (DISK && lane >= 8 && lane < 11 && P.counters && s_cnt[warp][lane])
-    atomicAdd(&P.counters[lane], s_cnt[warp][lane]);
+  if constexpr (DISK) {
+    if (lane >= 8 && lane < NCNT && P.counters && s_cnt[warp][lane]) atomicAdd(&P.counters[lane], s_cnt[warp][lane]);
+  }
   if (c_redo && P.counters) atomicAdd(&P.counters[7], (unsigned long long)c_redo);
 }
 
