@@ -306,3 +306,54 @@ def test_barrel_only_detector_unchanged_by_the_plans():
     r1 = oracle.find_event(b, 0)
     r2 = oracle.find_event(b, 0, brute=True)
     assert np.array_equal(r1["hits"], r2["hits"]) and np.array_equal(r1["chi2"], r2["chi2"])
+
+
+def test_plane_reached_only_within_half_a_turn():
+    """A looper reaches the plane z = z_d after the transverse arc s = (z_d -
+    z) tan(theta): within half a turn (|h s| < pi) the step exists, beyond it
+    (or with the plane behind the track) it does not; the crossing lies on
+    the plane and at the closed-form helix position."""
+    kb = C_LIGHT * BZ
+    th = 2 * math.atan(math.exp(-1.5))  # eta 1.5, cot(theta) = sinh(1.5)
+    cot = math.cos(th) / math.sin(th)
+    # (q/pT, plane): 3.98 rad of arc; 0.02; 0.04; the plane behind the track
+    for kap, zd, expect in ((3.0, 250.0, False), (0.05, 130.0, True), (1.0, 10.0, True), (0.5, -50.0, False)):
+        p = np.array([3.0, 1.0, 2.0, kap, 0.4, th])
+        ok, q, _ = oracle.propagate_plane(BZ, p, zd)
+        s = (zd - p[2]) / cot
+        assert ok == (s > 0 and abs(kb * kap * s) < math.pi), (kap, zd)
+        assert ok == expect, (kap, zd)
+        if ok:
+            h = -kb * kap
+            phi1 = p[4] + h * s
+            x = p[0] + (math.sin(phi1) - math.sin(p[4])) / h
+            y = p[1] - (math.cos(phi1) - math.cos(p[4])) / h
+            assert abs(q[2] - zd) < 1e-9 and abs(q[0] - x) < 1e-9 and abs(q[1] - y) < 1e-9
+
+
+def test_passes_are_neither_holes_nor_stops():
+    """Forward seeds pass the barrel layers beyond their reach (a dozen for
+    |eta| near 2) and the disks they meet outside the disks' radii.  Were a
+    pass a hole or a stop, a candidate allowed no hole would stop at its
+    first one and never reach the disks: with max_holes = 0 the noise-free
+    forward seeds still find their true hits (as with 3 holes allowed) and
+    the disks' hits."""
+    b = make_batch("c5", tracks=400, noise=0.0)
+    r0 = oracle.find_event(b, 0, max_holes=0)
+    r3 = oracle.find_event(b, 0, max_holes=3)
+    prm, _, _ = b.event_seeds(0)
+    x, y, z, lay = b.event_hits(0)
+    L = b.det.n_layers
+    fwd = same = with_disk = equal_holes = 0
+    for s in range(b.n_seeds):
+        tt, eta = _plan_truth(b, s, prm)
+        if abs(eta) < b.det.eta_barrel:
+            continue
+        fwd += 1
+        f = r0["hits"][s, :r0["n_found"][s]]
+        same += np.array_equal(f, tt)
+        with_disk += (lay[f] >= L).any()
+        equal_holes += np.array_equal(r0["hits"][s], r3["hits"][s])
+    assert fwd > 200
+    assert same >= 0.98 * fwd and with_disk >= 0.9 * fwd and equal_holes >= 0.99 * fwd, (fwd, same, with_disk,
+                                                                                         equal_holes)
