@@ -254,6 +254,27 @@ def _cross_plane(x, y, z, kappa, phi, theta, zd, bz):
     return ok, xn, yn, phi + hs
 
 
+def _cross_plane_in_field(x, y, z, kappa, phi, theta, zd, det: Detector):
+    """Truth tracing to the plane z = zd: one helix in a uniform field; in a
+    field that varies, FIELD_SUBSTEPS helices to planes spread evenly in z
+    between the start and zd, each in the field at its own starting point,
+    the whole arc within half a turn.  Returns (ok, x, y, phi)."""
+    if det.field_cz == 0.0 and det.field_cr == 0.0:
+        return _cross_plane(x, y, z, kappa, phi, theta, zd, det.bz)
+    ok = np.ones(x.shape[0], dtype=bool)
+    turn = np.zeros(x.shape[0])
+    z0 = z.copy()
+    for k in range(1, FIELD_SUBSTEPS + 1):
+        zk = np.full_like(z0, zd) if k == FIELD_SUBSTEPS else z0 + (zd - z0) * k / FIELD_SUBSTEPS
+        okk, xn, yn, phn = _cross_plane(x, y, z, kappa, phi, theta, zk, field_at(det, x, y, z))
+        ok &= okk
+        turn += np.where(okk, phn - phi, 0.0)
+        x, y, z, phi = (np.where(okk, xn, x), np.where(okk, yn, y), np.where(okk, zk, z),
+                        np.where(okk, phn, phi))
+    ok &= np.abs(turn) < np.pi
+    return ok, x, y, phi
+
+
 def _highland_disk(kappa, theta, x0):
     """Highland width in a disk of x0 radiation lengths (path factor 1/|cos theta|)."""
     sin_t = np.sin(theta)
@@ -295,8 +316,6 @@ def simulate_event(det: Detector, n_tracks: int, eta_max: float, noise: float,
     alive = np.ones(n, dtype=bool)
     hx_l, hy_l, hz_l, sim_l, lay_l = [], [], [], [], []
     S = det.n_surfaces
-    if det.n_disks and (det.field_cz != 0.0 or det.field_cr != 0.0):
-        raise ValueError("endcap disks are simulated in a uniform field only")
     truth = np.full((n, S, 6), np.nan)
     local_index = np.full((n, S), -1, dtype=np.int64)  # index into this event's hit list (pre-shuffle)
     n_hits = 0
@@ -358,7 +377,7 @@ def simulate_event(det: Detector, n_tracks: int, eta_max: float, noise: float,
     for k in range(det.n_disks):
         for sgn, si in ((1.0, det.n_layers + k), (-1.0, det.n_layers + det.n_disks + k)):
             zd = sgn * det.disk_z[k]
-            ok, xn, yn, phn = _cross_plane(x, y, z, kappa, ph, th, zd, det.bz)
+            ok, xn, yn, phn = _cross_plane_in_field(x, y, z, kappa, ph, th, zd, det)
             rn = np.hypot(xn, yn)
             ok &= (side == sgn) & (rn >= det.disk_rmin) & (rn <= det.disk_rmax)
             idx = np.nonzero(ok)[0]

@@ -357,3 +357,20 @@ def test_passes_are_neither_holes_nor_stops():
     assert fwd > 200
     assert same >= 0.98 * fwd and with_disk >= 0.9 * fwd and equal_holes >= 0.99 * fwd, (fwd, same, with_disk,
                                                                                          equal_holes)
+
+
+def test_endcap_finding_in_a_parameterized_field():
+    """The barrel-plus-endcap event simulated in the moderate parameterized
+    field (the truth traced in eight helix steps per surface, each in the
+    field at its own start; Bz 10% weaker at |z| = 120 cm, 43% at 250 cm):
+    the oracle, whose steps take the field at their start, still finds the
+    true hits of the plan for at least 99% of the seeds.  (Its q/pT pull on
+    tracks that end on a disk widens to about 4 there: one helix per step in
+    a field that changes by several percent along the step.)"""
+    field = dict(field_cz=-0.10 / 120.0 ** 2, field_cr=-0.05 / 110.0 ** 2)
+    b = make_batch("c5", noise=0.10, **field)
+    r = oracle.find_event(b, 0)
+    prm, _, _ = b.event_seeds(0)
+    good = sum(np.array_equal(r["hits"][s, :r["n_found"][s]], _plan_truth(b, s, prm)[0])
+               for s in range(b.n_seeds))
+    assert good >= 0.99 * b.n_seeds, good
