@@ -98,7 +98,9 @@ typedef struct {
   float field_cr;
   /* Endcap disks (Sec. 2: barrel layers and endcap disks, each event split
    * into eta regions).  n_disks planes per side at z = +-disk_z[k] (0 <
-   * disk_z[0] < disk_z[1] < ..., each beyond z_max), covering disk_rmin <= r <=
+   * disk_z[0] < disk_z[1] < ...; a forward plan searches the barrel layers
+   * before the disks, the order of a track's crossings when the disks lie
+   * beyond the barrel's ends, |z| > z_max), covering disk_rmin <= r <=
    * disk_rmax, each disk_x0 radiation lengths thick with mean ionization loss
    * disk_eloss at normal incidence (GeV, >= 0).  Surfaces: barrel layers
    * 0..n_layers-1, the +z disks n_layers..n_layers+n_disks-1, then the -z
